@@ -1,0 +1,535 @@
+"""FP64 CPU oracle of the contact-smoothed quasi-static rope/cloth simulator.
+
+TEST INFRASTRUCTURE ONLY.  This package is imported by tests/, by __graft_entry__.smoke() and
+by bench.py's cpu_baseline leg and reference arm -- nothing else.  It shares no code with the
+CUDA path (no kernels, headers, helpers or constants); both are fed from the seeded generator
+in paper_2606_14188_b300/scenes.py, which holds no simulator arithmetic.
+
+What is computed, in the paper's order (Sec. 4.1, "Differentiable Deformable Object Simulator
+with Contact Smoothing"):
+
+* Eq. (dynamics): the implicit quasi-static step  M (q+ - q)/dt^2 + dE/dq(q+) = tau(u) + sum J^T lam.
+  State q = [x_1..x_nv, g_1, g_2] (3-D node positions, then the two 3-D gripper positions).
+* Eq. (dynamics-first-stage): stage 1.  q* is the root of
+      F(q*) = M (q* - q)/dt^2 + dE/dq(q*) - tau(u) + sum_i J_i^T D_i (J_i (q* - q) + c_i(q)),
+  found by Newton's method.  The grasp constraint c_i(q) = g_i - x_a(i) is linear, so the grasp
+  term is a zero-rest-length spring of stiffness d_i(q) between g_i* and x*_a(i).
+* Eq. (dynamics-second-stage): stage 2.  q+ = q* + Delta minimises 1/2 Delta^T P Delta subject to
+  J_i(q*) Delta + [phi_i(q*), 0, 0] in the dual friction cone, P = dF/dq*(q*).
+* "Contact Smoothing": D_i = D_max exp(-|c_i(q)|/kappa_h) (smooth) or D_max 1[|c_i| <= r_grasp]
+  (nonsmooth), and the complementarity s^T lam = 0 relaxed to s^T lam = kappa_c.
+
+Readings taken where the paper is silent (the same readings drive the CUDA path):
+
+* E is a mass-spring energy sum_s k_s/2 (|x_b - x_a| - L_s)^2 (stretch + bend for a rope,
+  structural + shear + bend for a cloth; the paper names stretching and bending only).
+* M is lumped: node_mass per node.  The grippers are kinematic (the limit of an infinite gripper
+  mass with actuation tau_g = m_g u/dt^2), so g+ = g* = g + u exactly and contact acts on nodes only.
+* The relaxed complementarity is realised by the log barrier -kappa/2 log(s_n^2 - mu^2 |s_t|^2)
+  of the dual cone {s_n >= mu |s_t|}.  Its stationarity gives lam = kappa (s_n, -mu^2 s_t)/(...),
+  a point of the friction cone with s^T lam = kappa exactly.  The barrier depends on the tangent
+  plane only through |s_t|^2 = |sigma|^2 - (n.sigma)^2 with sigma = Delta_j + phi n in world
+  coordinates, so no tangent basis is needed.
+* The nonsmooth stage 2 (an SOCP) is solved by the same barrier followed along its central path
+  to kappa_hard; when every phi_i(q*) >= 0, Delta = 0 is the exact optimum and is returned as is.
+* Stage-2 feasibility: an infeasible-start Newton method on (Delta, sigma) with the linear
+  equality sigma_i = Delta_j + phi_i n_i (Boyd & Vandenberghe, Convex Optimization, Sec. 10.3).
+* Newton directions use the exact Hessian when it is positive definite, else the Hessian with
+  each spring's transverse factor (1 - L/l) clamped at 0; a backtracking Armijo search on the
+  stage-1 potential Psi (whose gradient is F) globalises it.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import cholesky_banded, cho_solve_banded, LinAlgError
+
+HARD, SMOOTH = "hard", "smooth"
+
+# per-rollout status bits (sticky over a rollout)
+ST_NEWTON = 1      # stage-1 Newton hit its iteration cap
+ST_CONTACT = 2     # stage-2 interior point hit its iteration cap or found no interior
+ST_NONFINITE = 4
+ST_NOTPD = 8       # a stage-2 / adjoint system was not positive definite
+
+# oracle tolerances: far tighter than any GPU tolerance, so the oracle's result is the exact
+# root / optimum to FP64 accuracy
+TOL_X = 1e-13
+NEWTON_MAX = 100
+IPM_MAX = 200
+
+
+class Scene:
+    """Topology, parameters and obstacles of one rope or cloth."""
+
+    def __init__(self, params: dict, rest_x: np.ndarray):
+        p = params
+        self.p = p
+        self.kind = p["kind"]
+        rest_x = np.asarray(rest_x, dtype=np.float64)
+        self.nv = rest_x.shape[0]
+        a, b, k = [], [], []
+        if self.kind == "rope":
+            n = self.nv
+            for j in range(n - 1):
+                a.append(j); b.append(j + 1); k.append(p["k_stretch"])
+            for j in range(n - 2):
+                a.append(j); b.append(j + 2); k.append(p["k_bend"])
+        else:
+            R, C = p["rows"], p["cols"]
+            idx = lambda r, c: r * C + c
+            for r in range(R):
+                for c in range(C):
+                    if c + 1 < C:
+                        a.append(idx(r, c)); b.append(idx(r, c + 1)); k.append(p["k_stretch"])
+                    if r + 1 < R:
+                        a.append(idx(r, c)); b.append(idx(r + 1, c)); k.append(p["k_stretch"])
+                    if r + 1 < R and c + 1 < C:
+                        a.append(idx(r, c)); b.append(idx(r + 1, c + 1)); k.append(p["k_shear"])
+                        a.append(idx(r, c + 1)); b.append(idx(r + 1, c)); k.append(p["k_shear"])
+                    if c + 2 < C:
+                        a.append(idx(r, c)); b.append(idx(r, c + 2)); k.append(p["k_bend"])
+                    if r + 2 < R:
+                        a.append(idx(r, c)); b.append(idx(r + 2, c)); k.append(p["k_bend"])
+        self.a = np.array(a, dtype=np.int64)
+        self.b = np.array(b, dtype=np.int64)
+        assert np.all(self.b > self.a)
+        self.k = np.array(k, dtype=np.float64)
+        self.L = np.linalg.norm(rest_x[self.b] - rest_x[self.a], axis=1)
+        self.m = float(p["node_mass"])
+        self.dt = float(p["dt"])
+        self.w = self.m / self.dt ** 2                     # M/dt^2 per node DoF
+        self.grav = np.asarray(p["gravity"], dtype=np.float64)
+        self.grasp = np.array(p["grasp_nodes"], dtype=np.int64)
+        self.obstacles = list(p["obstacles"])
+        self.n = 3 * self.nv
+        self.nq = self.n + 6
+        # half bandwidth (scalar) of every node-coupled matrix
+        self.bw = 3 * int(np.max(self.b - self.a)) + 2 if len(self.a) else 2
+
+
+# ------------------------------------------------------------------------------------------
+# elastic energy (mass-spring), its gradient and Hessian
+# ------------------------------------------------------------------------------------------
+
+def spring_geometry(sc: Scene, X):
+    d = X[sc.b] - X[sc.a]
+    l = np.sqrt((d * d).sum(axis=1))
+    return d, l
+
+
+def elastic_energy(sc: Scene, X) -> float:
+    _, l = spring_geometry(sc, X)
+    return 0.5 * float(np.sum(sc.k * (l - sc.L) ** 2))
+
+
+def elastic_gradient(sc: Scene, X) -> np.ndarray:
+    d, l = spring_geometry(sc, X)
+    f = (sc.k * (l - sc.L) / l)[:, None] * d        # dE/dx_b ; dE/dx_a = -f
+    G = np.zeros_like(X)
+    np.add.at(G, sc.b, f)
+    np.add.at(G, sc.a, -f)
+    return G
+
+
+def spring_hessian_d(k, L, d, project=False):
+    """d^2/dd^2 of k/2 (|d| - L)^2 = k [u u^T + (1 - L/l)(I - u u^T)], u = d/|d| (vectorised;
+    works for complex d, which the derivative checks use)."""
+    l = np.sqrt((d * d).sum(axis=-1))
+    u = d / l[..., None]
+    c = 1.0 - L / l
+    if project:
+        c = np.maximum(c, 0.0)
+    I = np.eye(3)
+    uu = u[..., :, None] * u[..., None, :]
+    return k[..., None, None] * (uu + c[..., None, None] * (I - uu))
+
+
+def spring_hessians(sc: Scene, X, project=False):
+    d, _ = spring_geometry(sc, X)
+    return spring_hessian_d(sc.k, sc.L, d, project)
+
+
+# ------------------------------------------------------------------------------------------
+# grasp stiffness (Sec. 4.1 "Contact Smoothing")
+# ------------------------------------------------------------------------------------------
+
+def grasp_offsets(sc: Scene, x, g):
+    """c_i(q) = g_i - x_a(i) (the holonomic constraint of eq. holonomic-constraint)."""
+    return g - x[sc.grasp]
+
+
+def grasp_stiffness_of_c(sc: Scene, c, mode):
+    """d_i = D_max exp(-|c_i|/kappa_h) (smooth) or D_max 1[|c_i| <= r_grasp] (nonsmooth).
+    |c| is written sqrt(c.c) so the complex-step derivative checks pass through it."""
+    rho = np.sqrt((c * c).sum(axis=-1))
+    p = sc.p
+    if mode == SMOOTH:
+        return p["D_max"] * np.exp(-rho / p["kappa_h"])
+    return np.where(np.real(rho) <= p["r_grasp"], p["D_max"], 0.0)
+
+
+def grasp_stiffness(sc: Scene, x, g, mode):
+    return grasp_stiffness_of_c(sc, grasp_offsets(sc, x, g), mode)
+
+
+# ------------------------------------------------------------------------------------------
+# stage 1: F, Psi differences, banded Hessian
+# ------------------------------------------------------------------------------------------
+
+def stage1_residual(sc: Scene, X, x, gstar, d):
+    """F(q*; q, u) of eq. (dynamics-first-stage), node rows (the gripper rows are satisfied by
+    g* = g + u exactly)."""
+    F = sc.w * (X - x) + elastic_gradient(sc, X) - sc.m * sc.grav[None, :]
+    for i in range(2):
+        F[sc.grasp[i]] += d[i] * (X[sc.grasp[i]] - gstar[i])
+    return F
+
+
+def psi_difference(sc: Scene, X, D, x, gstar, d):
+    """Psi(X + D) - Psi(X) for the stage-1 potential
+         Psi(z) = 1/(2 dt^2) |z - x|_M^2 + E(z) - m grav . sum z_j + sum_i d_i/2 |g*_i - z_a(i)|^2,
+    whose gradient is F.  Each term is written in terms of the step D itself (e.g. a spring
+    length change is (D_b - D_a).(2 d_X + D_b - D_a)/(l_Y + l_X)), so that the difference stays
+    accurate when the step is tiny."""
+    val = 0.5 * sc.w * float(np.sum(D * (2.0 * (X - x) + D)))
+    val -= sc.m * float(np.sum(D @ sc.grav))
+    dX = X[sc.b] - X[sc.a]
+    dD = D[sc.b] - D[sc.a]
+    dY = dX + dD
+    lX = np.sqrt((dX * dX).sum(1))
+    lY = np.sqrt((dY * dY).sum(1))
+    dl = (dD * (2.0 * dX + dD)).sum(1) / (lY + lX)
+    val += 0.5 * float(np.sum(sc.k * dl * (lY + lX - 2.0 * sc.L)))
+    for i in range(2):
+        j = sc.grasp[i]
+        val += 0.5 * d[i] * float(np.dot(D[j], D[j] - 2.0 * (gstar[i] - X[j])))
+    return val
+
+
+def band_zeros(sc: Scene):
+    return np.zeros((sc.bw + 1, sc.n))
+
+
+def band_add_node_blocks(sc: Scene, ab, nodes, blocks):
+    """ab (lower band storage, ab[I-J, J] = A[I, J]) += block-diagonal 3x3 `blocks` at `nodes`."""
+    for al in range(3):
+        for be in range(al + 1):
+            np.add.at(ab[al - be], 3 * nodes + be, blocks[:, al, be])
+
+
+def band_add_springs(sc: Scene, ab, Hs):
+    for al in range(3):
+        for be in range(3):
+            if al >= be:
+                np.add.at(ab[al - be], 3 * sc.a + be, Hs[:, al, be])
+                np.add.at(ab[al - be], 3 * sc.b + be, Hs[:, al, be])
+            # off-diagonal block: rows of b, columns of a (b > a), value -Hs
+            np.add.at(ab, (3 * (sc.b - sc.a) + al - be, 3 * sc.a + be), -Hs[:, al, be])
+
+
+def stage1_hessian_band(sc: Scene, X, d, project=False):
+    """dF/dq* = M/dt^2 + d^2E(q*) + sum_i d_i J_i^T J_i (node block), in lower band storage."""
+    ab = band_zeros(sc)
+    ab[0, :] += sc.w
+    band_add_springs(sc, ab, spring_hessians(sc, X, project))
+    gb = np.zeros((2, 3, 3))
+    gb[:, [0, 1, 2], [0, 1, 2]] = np.asarray(d)[:, None]
+    band_add_node_blocks(sc, ab, sc.grasp, gb)
+    return ab
+
+
+def stage1_hessian_vec(sc: Scene, X, d, v):
+    """(dF/dq*) v without forming the matrix."""
+    Hs = spring_hessians(sc, X)
+    dv = v[sc.b] - v[sc.a]
+    f = np.einsum("sij,sj->si", Hs, dv)
+    out = sc.w * v.copy()
+    np.add.at(out, sc.b, f)
+    np.add.at(out, sc.a, -f)
+    for i in range(2):
+        out[sc.grasp[i]] += d[i] * v[sc.grasp[i]]
+    return out
+
+
+def band_factor(ab):
+    return cholesky_banded(ab, lower=True)
+
+
+def band_solve(cb, rhs):
+    """Solve with a banded Cholesky factor; rhs is node-shaped [nv, 3]."""
+    return cho_solve_banded((cb, True), rhs.reshape(-1)).reshape(rhs.shape)
+
+
+def band_solve_cols(cb, R):
+    """Solve with a banded Cholesky factor for the columns of R [n, k]."""
+    return cho_solve_banded((cb, True), R)
+
+
+def stage1_solve(sc: Scene, x, gstar, d, tol=TOL_X, maxit=NEWTON_MAX):
+    """Damped Newton for the root q* of F, started at q (Sec. 4.1, "solved using Newton's
+    method").  Stops when the Newton step is below `tol` in every coordinate (the step is then
+    taken).  Returns (q*, iterations, status)."""
+    X = x.copy()
+    for it in range(maxit):
+        F = stage1_residual(sc, X, x, gstar, d)
+        if not np.all(np.isfinite(F)):
+            return X, it, ST_NONFINITE
+        try:
+            cb = band_factor(stage1_hessian_band(sc, X, d))
+        except LinAlgError:
+            cb = band_factor(stage1_hessian_band(sc, X, d, project=True))
+        p = -band_solve(cb, F)
+        if np.max(np.abs(p)) <= tol:
+            return X + p, it + 1, 0
+        slope = float(np.sum(F * p))
+        alpha = 1.0
+        for _ in range(60):
+            if psi_difference(sc, X, alpha * p, x, gstar, d) <= 1e-4 * alpha * slope:
+                break
+            alpha *= 0.5
+        X = X + alpha * p
+    return X, maxit, ST_NEWTON
+
+
+# ------------------------------------------------------------------------------------------
+# contact geometry: signed distances and normals (Sec. 4.1, eq. contact-constraint)
+# ------------------------------------------------------------------------------------------
+
+def _sqrt_dot(v):
+    return np.sqrt((v * v).sum(axis=-1))
+
+
+def obstacle_phi_normal(ob: dict, X, radius):
+    """phi = sdf(x) - node radius and n = grad sdf for one obstacle, vectorised over points.
+    Branch decisions use real parts only, so the functions also accept complex X."""
+    if ob["type"] == "plane":
+        nrm = np.asarray(ob["normal"], dtype=np.float64)
+        phi = X @ nrm - ob["offset"] - radius
+        n = np.broadcast_to(nrm, X.shape) + 0.0 * X
+        return phi, n
+    if ob["type"] == "sphere":
+        r = X - np.asarray(ob["center"])
+        dist = _sqrt_dot(r)
+        return dist - ob["radius"] - radius, r / dist[..., None]
+    if ob["type"] == "box":
+        rel = X - np.asarray(ob["center"])
+        s = np.where(np.real(rel) >= 0, 1.0, -1.0)
+        q = rel * s - np.asarray(ob["half"])           # per-axis distance outside the faces
+        out_mask = np.real(q) > 0
+        qpos = np.where(out_mask, q, 0.0)
+        any_out = out_mask.any(axis=-1)
+        dist_out = _sqrt_dot(qpos)
+        safe = np.where(any_out, dist_out, 1.0)
+        n_out = s * qpos / safe[..., None]
+        kmax = np.argmax(np.real(q), axis=-1)
+        q_in = np.take_along_axis(q, kmax[..., None], axis=-1)[..., 0]
+        n_in = np.zeros_like(q)
+        np.put_along_axis(n_in, kmax[..., None], 1.0, axis=-1)
+        n_in = n_in * s
+        phi = np.where(any_out, dist_out, q_in) - radius
+        n = np.where(any_out[..., None], n_out, n_in)
+        return phi, n
+    raise ValueError(ob["type"])
+
+
+def contact_geometry(sc: Scene, X):
+    """phi[j, o], n[j, o, :] for every node j and obstacle o (all pairs enter stage 2)."""
+    r = sc.p["node_radius"]
+    if not sc.obstacles:
+        return np.zeros((X.shape[0], 0)), np.zeros((X.shape[0], 0, 3))
+    phis, ns = [], []
+    for ob in sc.obstacles:
+        ph, nn = obstacle_phi_normal(ob, X, r)
+        phis.append(ph); ns.append(nn)
+    return np.stack(phis, axis=1), np.stack(ns, axis=1)
+
+
+# ------------------------------------------------------------------------------------------
+# stage 2: the contact problem and its log-barrier (relaxed complementarity)
+# ------------------------------------------------------------------------------------------
+
+def cone_gap(sig, n, mu):
+    """g = (1+mu^2)(n.sigma)^2 - mu^2|sigma|^2 = s_n^2 - mu^2 |s_t|^2 and s_n = n.sigma."""
+    sn = (n * sig).sum(-1)
+    g = (1.0 + mu * mu) * sn * sn - mu * mu * (sig * sig).sum(-1)
+    return sn, g
+
+
+def contact_force(sig, n, kappa, mu):
+    """lam = -grad_sigma b(sigma), b = -kappa/2 log g: the contact force of a pair."""
+    sn, g = cone_gap(sig, n, mu)
+    a = (1.0 + mu * mu) * sn[..., None] * n - mu * mu * sig
+    return kappa * a / g[..., None]
+
+
+def contact_force_jacobian(sig, n, kappa, mu):
+    """W = d^2 b / d sigma^2 = -d lam / d sigma (3x3 per pair)."""
+    sn, g = cone_gap(sig, n, mu)
+    a = (1.0 + mu * mu) * sn[..., None] * n - mu * mu * sig
+    I = np.eye(3)
+    nn = n[..., :, None] * n[..., None, :]
+    aa = a[..., :, None] * a[..., None, :]
+    return (kappa / g)[..., None, None] * (mu * mu * I - (1.0 + mu * mu) * nn) \
+        + (2.0 * kappa / g ** 2)[..., None, None] * aa
+
+
+def in_cone_interior(sig, n, mu):
+    sn, g = cone_gap(sig, n, mu)
+    return bool(np.all(sn > 0) and np.all(g > 0))
+
+
+def stage2_barrier(sc: Scene, xs, d, kappa, phi, n, Delta, sig, tol=TOL_X, maxit=IPM_MAX):
+    """Minimise 1/2 Delta^T P Delta + sum_i b(sigma_i) s.t. sigma_i = Delta_j + phi_i n_i by an
+    infeasible-start Newton method (the equality residual r_p is driven to zero; every iterate
+    keeps sigma strictly inside the cone).  Merit: |r_D|^2 + (M/dt^2)^2 |r_p|^2.
+    Returns (Delta, sigma, iterations, status)."""
+    mu = sc.p["mu"]
+    c2 = sc.w ** 2
+    P_ab = stage1_hessian_band(sc, xs, d)
+
+    def residuals(Dl, sg):
+        lam = contact_force(sg, n, kappa, mu)
+        rD = stage1_hessian_vec(sc, xs, d, Dl) - lam.sum(axis=1)
+        rp = sg - Dl[:, None, :] - phi[..., None] * n
+        return rD, rp
+
+    for it in range(maxit):
+        rD, rp = residuals(Delta, sig)
+        W = contact_force_jacobian(sig, n, kappa, mu)
+        ab = P_ab.copy()
+        band_add_node_blocks(sc, ab, np.arange(sc.nv), W.sum(axis=1))
+        try:
+            cb = band_factor(ab)
+        except LinAlgError:
+            return Delta, sig, it, ST_NOTPD
+        rhs = -rD + np.einsum("joab,job->ja", W, rp)
+        dD = band_solve(cb, rhs)
+        dS = dD[:, None, :] - rp
+        if np.max(np.abs(dD)) <= tol and np.max(np.abs(dS), initial=0.0) <= tol \
+                and in_cone_interior(sig + dS, n, mu):
+            return Delta + dD, sig + dS, it + 1, 0
+        t = 1.0
+        for _ in range(80):
+            if in_cone_interior(sig + t * dS, n, mu):
+                break
+            t *= 0.5
+        m0 = float(np.sum(rD * rD) + c2 * np.sum(rp * rp))
+        for _ in range(80):
+            r1, p1 = residuals(Delta + t * dD, sig + t * dS)
+            m1 = float(np.sum(r1 * r1) + c2 * np.sum(p1 * p1))
+            if m1 <= (1.0 - 0.01 * t) ** 2 * m0 or m1 == 0.0:
+                break
+            t *= 0.5
+        Delta = Delta + t * dD
+        sig = sig + t * dS
+    return Delta, sig, maxit, ST_CONTACT
+
+
+def stage2_init(sc: Scene, xs, d, kappa, phi, n):
+    """Interior start.  For each node, the pairs are first treated one at a time as if P were
+    the node's own normal stiffness a = n^T P_jj n: the single-pair optimum of
+    a/2 D^2 - kappa log(phi + D) is D = (-phi + sqrt(phi^2 + 4 kappa/a))/2 along n.  Pushes of
+    penetrating pairs (phi < 0) are summed into Delta_j; then sigma_i = Delta_j + phi_i n_i where
+    that point lies inside the cone with a margin, else sigma_i = max(phi_i, sigma0) n_i (an
+    infeasible start that the Newton iteration repairs)."""
+    mu = sc.p["mu"]
+    Delta = np.zeros((sc.nv, 3))
+    if phi.shape[1] == 0:
+        return Delta, np.zeros((sc.nv, 0, 3))
+    e = np.zeros((sc.nv, 3))
+    Pd = np.zeros((sc.nv, phi.shape[1]))
+    for al in range(3):
+        e[:] = 0.0
+        e[:, al] = 1.0
+        col = stage1_hessian_vec_diag(sc, xs, d)[:, :, al]      # P_jj[:, :, al]
+        Pd += n[..., al] * np.einsum("job,jb->jo", n, col)
+    push = 0.5 * (-phi + np.sqrt(phi * phi + 4.0 * kappa / Pd))
+    Delta = np.einsum("jo,joa->ja", np.where(phi < 0.0, push, 0.0), n)
+    sig = Delta[:, None, :] + phi[..., None] * n
+    sn, g = cone_gap(sig, n, mu)
+    ok = (sn > 0.0) & (g > 0.25 * sn * sn)
+    fallback = np.maximum(phi, sc.p["sigma0"])[..., None] * n
+    sig = np.where(ok[..., None], sig, fallback)
+    return Delta, sig
+
+
+def stage1_hessian_vec_diag(sc: Scene, X, d):
+    """The 3x3 diagonal blocks P_jj of dF/dq*."""
+    Hs = spring_hessians(sc, X)
+    D = np.zeros((sc.nv, 3, 3))
+    D[:, [0, 1, 2], [0, 1, 2]] = sc.w
+    np.add.at(D, sc.a, Hs)
+    np.add.at(D, sc.b, Hs)
+    for i in range(2):
+        D[sc.grasp[i]] += d[i] * np.eye(3)
+    return D
+
+
+def stage2_smooth(sc: Scene, xs, d, tol=TOL_X):
+    phi, n = contact_geometry(sc, xs)
+    Delta, sig = stage2_init(sc, xs, d, sc.p["kappa_c"], phi, n)
+    Delta, sig, it, st = stage2_barrier(sc, xs, d, sc.p["kappa_c"], phi, n, Delta, sig, tol)
+    return Delta, sig, phi, n, it, st
+
+
+def stage2_hard(sc: Scene, xs, d, tol=TOL_X):
+    """The nonsmooth contact SOCP of eq. (dynamics-second-stage).  Delta = 0 when no pair
+    penetrates; otherwise the barrier is followed from kappa_c down to kappa_hard."""
+    phi, n = contact_geometry(sc, xs)
+    if np.all(phi >= 0.0):
+        return np.zeros((sc.nv, 3)), None, phi, n, 0, 0
+    kappa = sc.p["kappa_c"]
+    Delta, sig = stage2_init(sc, xs, d, kappa, phi, n)
+    its = 0
+    while True:
+        Delta, sig, it, st = stage2_barrier(sc, xs, d, kappa, phi, n, Delta, sig, tol)
+        its += it
+        if st or kappa <= sc.p["kappa_hard"]:
+            return Delta, sig, phi, n, its, st
+        kappa = kappa * sc.p["kappa_decay"]
+        if kappa < sc.p["kappa_hard"] * (1.0 + 1e-6):
+            kappa = sc.p["kappa_hard"]
+
+
+# ------------------------------------------------------------------------------------------
+# one step and a rollout
+# ------------------------------------------------------------------------------------------
+
+def split_q(sc: Scene, q):
+    q = np.asarray(q, dtype=np.float64)
+    return q[: sc.n].reshape(sc.nv, 3), q[sc.n:].reshape(2, 3)
+
+
+def join_q(x, g):
+    return np.concatenate([x.ravel(), g.ravel()])
+
+
+def step(sc: Scene, q, u, mode, tol=TOL_X, info=None):
+    """(q, u) -> q+ : stage 1 then stage 2 (Sec. 4.1, "Simulation Solver")."""
+    x, g = split_q(sc, q)
+    gstar = g + np.asarray(u, dtype=np.float64).reshape(2, 3)
+    d = grasp_stiffness(sc, x, g, mode)
+    xs, it1, st1 = stage1_solve(sc, x, gstar, d, tol)
+    if mode == HARD:
+        Delta, sig, phi, n, it2, st2 = stage2_hard(sc, xs, d, tol)
+    else:
+        Delta, sig, phi, n, it2, st2 = stage2_smooth(sc, xs, d, tol)
+    if info is not None:
+        info.update(xs=xs, Delta=Delta, sig=sig, phi=phi, n=n, d=d, gstar=gstar,
+                    newton_it=it1, ipm_it=it2, status=st1 | st2)
+    return join_q(xs + Delta, gstar), st1 | st2
+
+
+def rollout(sc: Scene, q0, U, mode, tol=TOL_X):
+    """q_0 .. q_H for controls U[H, 6].  Returns (traj[H+1, nq], status, newton/ipm counts)."""
+    H = U.shape[0]
+    traj = np.zeros((H + 1, sc.nq))
+    traj[0] = q0
+    status = 0
+    counts = []
+    for t in range(H):
+        info = {}
+        traj[t + 1], st = step(sc, traj[t], U[t], mode, tol, info)
+        status |= st
+        counts.append((info["newton_it"], info["ipm_it"]))
+    return traj, status, counts

@@ -1,0 +1,220 @@
+"""Seeded synthetic scenes and control sequences.
+
+This module draws random numbers and lays out initial geometry; it holds none of the
+simulator's arithmetic (no springs, no energies, no contact model).  Both the CUDA path and
+the FP64 CPU oracle are fed from the arrays it returns, so the two sides see bit-identical
+inputs.
+
+The scenes stand in for the paper's rope and cloth tasks (Lift/Drag Rope, Fold/Flatten Cloth,
+Sec. 5 and Table 1): the paper's hardware data are not public, so each scene is a seeded
+synthetic layout with the sizes and structure the workloads call for (a 0.8 m rope, App. B.1;
+a 0.38 m square cloth, App. B.2; grasped ends/corners; a table plane and sphere/box obstacles).
+
+Parameter values are not printed in the paper; the defaults below are the readings used by
+both implementations (gravity 9.81 m/s^2 along -z, rope mass 0.1 kg, cloth mass 0.05 kg,
+k_stretch 500 N/m, k_shear 250 N/m, k_bend 25 N/m, D_max 1e4 N/m, kappa_h 0.01 m,
+kappa_c 1e-4 N m, mu 0.5, dt 0.01 s).
+"""
+from __future__ import annotations
+
+import copy
+import numpy as np
+
+BASE_SEED = 260614188
+
+HARD, SMOOTH = "hard", "smooth"
+SURROGATE, CONSISTENT = "surrogate", "consistent"
+
+
+def default_params(kind: str = "rope") -> dict:
+    """Physical and solver parameters shared by the oracle and the CUDA path."""
+    p = dict(
+        kind=kind,
+        n_nodes=0, rows=0, cols=0,
+        grasp_nodes=(0, 0),
+        dt=0.01,
+        gravity=(0.0, 0.0, -9.81),
+        node_mass=0.0,
+        k_stretch=500.0, k_shear=250.0, k_bend=25.0,
+        D_max=1.0e4,
+        kappa_h=0.01,          # grasp smoothing length [m]
+        kappa_c=1.0e-4,        # contact smoothing (relaxed complementarity) [N m]
+        kappa_hard=1.0e-8,     # barrier weight at which the nonsmooth SOCP is declared solved
+        kappa_decay=0.1,       # path-following decrease of the barrier weight per stage
+        mu=0.5,
+        r_grasp=0.01,
+        node_radius=0.005,
+        sigma0=1.0e-3,         # interior start of a penetrating contact slack [m]
+        obstacles=[],
+        fwd_mode=HARD,
+        grad_mode=SURROGATE,
+        newton_max=30, newton_tol=2.0e-7,
+        ipm_max=60, ipm_tol=2.0e-7,
+        checkpoint_every=1,
+        loss=dict(goal_nodes=(), goal_pos=np.zeros((0, 3)), w_goal=1.0,
+                  w_pen=100.0, pen_margin=0.02, w_u=0.01),
+    )
+    return p
+
+
+def plane(normal=(0.0, 0.0, 1.0), offset=0.0) -> dict:
+    n = np.asarray(normal, dtype=np.float64)
+    return dict(type="plane", normal=tuple(n / np.linalg.norm(n)), offset=float(offset))
+
+
+def sphere(center, radius) -> dict:
+    return dict(type="sphere", center=tuple(float(c) for c in center), radius=float(radius))
+
+
+def box(center, half) -> dict:
+    return dict(type="box", center=tuple(float(c) for c in center),
+                half=tuple(float(h) for h in half))
+
+
+def _point_clear(points: np.ndarray, ob: dict, clearance: float) -> bool:
+    """Scene-generation rejection test: is every point at least `clearance` from the shape."""
+    if ob["type"] == "sphere":
+        c = np.asarray(ob["center"])
+        return bool(np.all(np.linalg.norm(points - c, axis=1) - ob["radius"] >= clearance))
+    if ob["type"] == "box":
+        c = np.asarray(ob["center"]); h = np.asarray(ob["half"])
+        outside = np.maximum(np.abs(points - c) - h, 0.0)
+        return bool(np.all(np.linalg.norm(outside, axis=1) >= clearance))
+    return True
+
+
+def rope_scene(n_nodes: int, n_spheres: int = 1, n_boxes: int = 0, seed: int = BASE_SEED,
+               length: float = 0.8, height: float = 0.3, total_mass: float = 0.1,
+               sphere_box=((0.2, 0.6), (-0.1, 0.1), (0.05, 0.25)),
+               box_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)),
+               sphere_r=(0.05, 0.15), box_half=(0.03, 0.1)) -> dict:
+    """A straight rope along +x at height `height`, both ends grasped, ground plane z = 0.
+
+    Obstacles are drawn uniformly in the given boxes and redrawn while they touch the initial
+    rope (clearance of one node radius plus 1 cm).
+    """
+    rng = np.random.default_rng(seed)
+    p = default_params("rope")
+    p["n_nodes"] = n_nodes
+    p["node_mass"] = total_mass / n_nodes
+    p["grasp_nodes"] = (0, n_nodes - 1)
+    p["node_radius"] = 0.005
+    xs = np.linspace(0.1, 0.1 + length, n_nodes)
+    rest = np.stack([xs, np.zeros(n_nodes), np.full(n_nodes, height)], axis=1)
+    obs = [plane((0, 0, 1), 0.0)]
+    clear = p["node_radius"] + 0.01
+    for _ in range(n_spheres):
+        while True:
+            c = [rng.uniform(*sphere_box[k]) for k in range(3)]
+            r = rng.uniform(*sphere_r)
+            ob = sphere(c, r)
+            if _point_clear(rest, ob, clear):
+                break
+        obs.append(ob)
+    for _ in range(n_boxes):
+        while True:
+            c = [rng.uniform(*box_box[k]) for k in range(3)]
+            h = [rng.uniform(*box_half) for _ in range(3)]
+            ob = box(c, h)
+            if _point_clear(rest, ob, clear):
+                break
+        obs.append(ob)
+    p["obstacles"] = obs
+    goal_nodes = (0, n_nodes - 1)
+    p["loss"] = dict(goal_nodes=goal_nodes,
+                     goal_pos=rest[list(goal_nodes)] + np.array([0.0, 0.0, 0.1]),
+                     w_goal=1.0, w_pen=100.0, pen_margin=0.02, w_u=0.01)
+    q0 = np.concatenate([rest.ravel(), rest[0], rest[-1]])
+    return dict(params=p, rest_x=rest, q0=q0)
+
+
+def cloth_scene(rows: int, cols: int, n_spheres: int = 2, seed: int = BASE_SEED,
+                side: float = 0.38, height: float = 0.05, total_mass: float = 0.05) -> dict:
+    """A flat square cloth at height `height` over the table z = 0; corners (0,0) and
+    (0,cols-1) grasped; spheres drawn below/beside the cloth and redrawn while they touch it.
+    The loss folds row 0 onto row rows-1."""
+    rng = np.random.default_rng(seed)
+    p = default_params("cloth")
+    p["rows"], p["cols"] = rows, cols
+    n = rows * cols
+    p["n_nodes"] = n
+    p["node_mass"] = total_mass / n
+    p["grasp_nodes"] = (0, cols - 1)
+    p["node_radius"] = 0.002
+    p["k_stretch"], p["k_shear"], p["k_bend"] = 500.0, 250.0, 25.0
+    r_idx, c_idx = np.meshgrid(np.arange(rows), np.arange(cols), indexing="ij")
+    rest = np.stack([r_idx.ravel() * side / (rows - 1), c_idx.ravel() * side / (cols - 1),
+                     np.full(n, height)], axis=1)
+    obs = [plane((0, 0, 1), 0.0)]
+    clear = p["node_radius"] + 0.01
+    for _ in range(n_spheres):
+        while True:
+            c = [rng.uniform(-0.1, side + 0.1), rng.uniform(-0.1, side + 0.1),
+                 rng.uniform(-0.1, 0.0)]
+            r = rng.uniform(0.05, 0.15)
+            ob = sphere(c, r)
+            if _point_clear(rest, ob, clear):
+                break
+        obs.append(ob)
+    p["obstacles"] = obs
+    goal_nodes = tuple(range(cols))
+    goal_pos = rest[(rows - 1) * cols + np.arange(cols)].copy()
+    p["loss"] = dict(goal_nodes=goal_nodes, goal_pos=goal_pos, w_goal=1.0, w_pen=100.0,
+                     pen_margin=0.02, w_u=0.01)
+    q0 = np.concatenate([rest.ravel(), rest[0], rest[cols - 1]])
+    return dict(params=p, rest_x=rest, q0=q0)
+
+
+def controls_uniform(B: int, H: int, n_u: int = 6, lo: float = -0.05, hi: float = 0.05,
+                     seed: int = BASE_SEED) -> np.ndarray:
+    rng = np.random.default_rng(seed + 7919)
+    return rng.uniform(lo, hi, size=(B, H, n_u))
+
+
+def controls_normal(B: int, H: int, n_u: int = 6, sigma: float = 0.02,
+                    seed: int = BASE_SEED) -> np.ndarray:
+    rng = np.random.default_rng(seed + 7919)
+    return rng.normal(0.0, sigma, size=(B, H, n_u))
+
+
+def batch_q0(scene: dict, B: int) -> np.ndarray:
+    return np.repeat(scene["q0"][None, :], B, axis=0)
+
+
+# ------------------------------------------------------------------------------------------
+# The five workloads.  Each returns a dict with the scene, batch size, horizon, controls and
+# precision.  `small=True` shrinks the batch so the oracle can finish in seconds.
+# ------------------------------------------------------------------------------------------
+
+def workload(i: int, B: int | None = None, H: int | None = None) -> dict:
+    seed = BASE_SEED + i
+    if i == 1:    # one 20-node rope, FP64, horizon 10, one sphere, uniform controls
+        sc = rope_scene(20, n_spheres=1, n_boxes=0, seed=seed)
+        B = B or 1; H = H or 10
+        U = controls_uniform(B, H, seed=seed)
+        real = 8
+        ck = 1
+    elif i == 2:  # 1024 rollouts x 64-node rope, FP32, horizon 50, 2 spheres + 2 boxes
+        sc = rope_scene(64, n_spheres=2, n_boxes=2, seed=seed,
+                        sphere_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)))
+        B = B or 1024; H = H or 50
+        U = controls_normal(B, H, seed=seed)
+        real = 4
+        ck = 7
+    elif i == 3:  # 512 rollouts of a 32x32 cloth, FP32, horizon 30, table + 2 spheres
+        sc = cloth_scene(32, 32, n_spheres=2, seed=seed)
+        B = B or 512; H = H or 30
+        U = controls_normal(B, H, seed=seed)
+        real = 4
+        ck = 5
+    elif i == 4:  # 256 nominal trajectories of a 40-node rope, horizon 20 (linearisation)
+        sc = rope_scene(40, n_spheres=1, n_boxes=0, seed=seed)
+        B = B or 256; H = H or 20
+        U = controls_normal(B, H, seed=seed)
+        real = 4
+        ck = 1
+    else:
+        raise ValueError(f"unknown workload {i}")
+    sc = copy.deepcopy(sc)
+    sc["params"]["checkpoint_every"] = ck
+    return dict(scene=sc, B=B, H=H, U=U, q0=batch_q0(sc, B), real_bytes=real, seed=seed)
