@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: forward rollout + checkpointed adjoint of the batched rope workload
+(1024 rollouts x 64-node rope, horizon 50, FP32, 2 spheres + 2 boxes + ground, checkpoint every
+7 steps, nonsmooth forward with surrogate gradients), metric node-steps/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is device-timed (CUDA events on the launching stream, inputs
+resident in HBM, L2 flushed between timed steps outside the timed intervals); `e2e` times the
+same call from pinned host buffers with the host<->device copies inside the timed region.  With
+N > 1 (torchrun), every rank runs its own 1024 rollouts (weak scaling, no collective on the data
+path) and the slowest rank's time is used.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import glob
+import io
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_14188_b300 import scenes, flops  # noqa: E402
+
+METRIC = "sim+adjoint node-steps/s"
+UNIT = "node-steps/s"
+WORKLOAD = "rope64_b1024_h50"
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+# ------------------------------------------------------------------------------------------
+# oracle work (CPU baseline, reference arm, iteration counts for the flop model)
+# ------------------------------------------------------------------------------------------
+
+def _oracle_vjp(args):
+    b, tol = args
+    from oracle import sim as osim, grad as ograd
+    w = scenes.workload(2)
+    sc = osim.Scene(w["scene"]["params"], w["scene"]["rest_x"])
+    t0 = time.perf_counter()
+    r = ograd.rollout_vjp(sc, w["q0"][b], w["U"][b], "surrogate", tol=tol) if tol else \
+        ograd.rollout_vjp(sc, w["q0"][b], w["U"][b], "surrogate")
+    dt = time.perf_counter() - t0
+    fwd = np.array(r["fwd_counts"], dtype=float).mean(axis=0)
+    sm = np.array(r["smooth_counts"], dtype=float).mean(axis=0)
+    return dict(seconds=dt, fwd_newton=fwd[0], fwd_ipm=fwd[1], sm_newton=sm[0], sm_ipm=sm[1])
+
+
+def oracle_sample(rollouts, tol, procs):
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_vjp, [(b, tol) for b in rollouts])
+    wall = time.perf_counter() - t0
+    return res, wall
+
+
+def counts_mean(res):
+    return {k: float(np.mean([r[k] for r in res])) for k in ("fwd_newton", "fwd_ipm", "sm_newton", "sm_ipm")}
+
+
+# ------------------------------------------------------------------------------------------
+# helpers
+# ------------------------------------------------------------------------------------------
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2606_14188_b300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str):
+    """dram bytes per launch from a committed ncu summary, if it was taken on this exact kernel
+    source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        e = d.get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash() and e.get("workload") == WORKLOAD:
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+    return None
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_FIELDS}", "--format=csv",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if not getattr(self, "out", ""):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = list(csv.reader(io.StringIO(self.out)))
+        hdr = [h.strip() for h in rows[0]]
+        sm, smax, reasons = [], [], set()
+        for r in rows[1:]:
+            if len(r) != len(hdr):
+                continue
+            d = dict(zip(hdr, [x.strip() for x in r]))
+            try:
+                sm.append(float(d["clocks.current.sm [MHz]"].split()[0]))
+                smax.append(float(d["clocks.max.sm [MHz]"].split()[0]))
+            except Exception:
+                continue
+            for k, v in d.items():
+                if k.startswith("clocks_event_reasons.") and k != "clocks_event_reasons.active" \
+                        and v.lower() == "active":
+                    reasons.add(k.split(".", 1)[1])
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# arms
+# ------------------------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = scenes.workload(2)
+    nv, H = w["scene"]["params"]["n_nodes"], w["H"]
+    cores = os.cpu_count() or 1
+    per_step = max(1, min(cores, 8))          # rollouts per step (one per core)
+    for s in range(args.warmup):
+        oracle_sample(list(range(s * per_step, (s + 1) * per_step)), None, per_step)
+    t = 0.0
+    for s in range(args.steps):
+        b0 = (args.warmup + s) * per_step
+        _, wall = oracle_sample(list(range(b0, b0 + per_step)), None, per_step)
+        t += wall
+    value = args.steps * per_step * nv * H / t
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * t / args.steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, rollouts_per_step=per_step, nodes=nv, horizon=H),
+                impl="reference",
+                cpu_baseline=dict(value=value, unit=UNIT, cores=per_step, kind="oracle",
+                                  sample=f"{per_step} rollouts of the workload per step, full "
+                                         f"horizon, one process per rollout"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # CPU work first (spawned pool, before any CUDA call): the oracle baseline and the oracle's
+    # iteration counts at the GPU tolerance for the flop model
+    cpu = None
+    counts = None
+    if rank == 0 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        procs = max(1, min(cores, 16))
+        res, wall = oracle_sample(list(range(procs)), None, procs)
+        w0 = scenes.workload(2)
+        ns = procs * w0["scene"]["params"]["n_nodes"] * w0["H"]
+        cpu = dict(value=ns / wall, unit=UNIT, cores=procs, kind="oracle",
+                   sample=f"{procs} of the 1024 rollouts (full horizon 50, forward + adjoint), one "
+                          f"process per rollout; {wall:.1f} s wall")
+        cres, _ = oracle_sample([0, 341, 682, 1023], 1e-7, 4)
+        counts = counts_mean(cres)
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    from paper_2606_14188_b300.sim import Sim
+    from paper_2606_14188_b300 import _lib
+
+    w = scenes.workload(2)
+    sc, B, H = w["scene"], w["B"], w["H"]
+    nv = sc["params"]["n_nodes"]
+    k = sc["params"]["checkpoint_every"]
+    nobs = len(sc["params"]["obstacles"])
+    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H)
+    q0 = torch.tensor(w["q0"], dtype=torch.float32, device="cuda")
+    U = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        s.rollout_vjp(q0, U, want_dq0=False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _lib.lib().cs_launch_count()
+    barrier()
+    with ClockSampler(dev) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            starts[i].record(stream)
+            Lv, dU, _, st = s.rollout_vjp(q0, U, want_dq0=False)
+            ends[i].record(stream)
+        barrier()
+    launches = int(_lib.lib().cs_launch_count())
+    per = [a.elapsed_time(b) * 1e-3 for a, b in zip(starts, ends)]
+    t = sum(per)
+    if world > 1:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt)
+    status = st.cpu().numpy()
+
+    # end to end through the public call from pinned host buffers
+    q0_h = torch.tensor(w["q0"], dtype=torch.float32).pin_memory()
+    U_h = torch.tensor(w["U"], dtype=torch.float32).pin_memory()
+    L_h = torch.empty(B, dtype=torch.float32).pin_memory()
+    dU_h = torch.empty(B, H, 6, dtype=torch.float32).pin_memory()
+    q0_d = torch.empty_like(q0)
+    U_d = torch.empty_like(U)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        q0_d.copy_(q0_h, non_blocking=True)
+        U_d.copy_(U_h, non_blocking=True)
+        Lv2, dU2, _, _ = s.rollout_vjp(q0_d, U_d, want_dq0=False)
+        L_h.copy_(Lv2, non_blocking=True)
+        dU_h.copy_(dU2, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    te = e0.elapsed_time(e1) * 1e-3
+    if world > 1:
+        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        te = float(tt)
+
+    if rank == 0:
+        node_steps = B * nv * H
+        value = world * args.steps * node_steps / t
+        e2e_value = world * args.steps * node_steps / te
+        avg_launch = t / args.steps
+        clocks = clk.summary()
+        sm_mhz = clocks["sm_max_mhz"] or 2032.0
+        props = torch.cuda.get_device_properties(dev)
+        sms = props.multi_processor_count
+        peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12           # FP32 FMA peak [TFLOP/s]
+        roof = None
+        if counts is not None:
+            f_ns = flops.rollout_vjp_flops_per_node_step(counts, nobs, k)
+            achieved = f_ns * node_steps / avg_launch / 1e12
+            roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
+                        frac=achieved / peak, traffic=load_traffic("rope_vjp_kernel"),
+                        peak_source=f"FP32 FMA: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
+                                    "(recipe unit counts and the max SM clock)",
+                        flops_per_node_step=f_ns, oracle_iterations_per_step=counts)
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=1e3 * t / args.steps, higher_is_better=True,
+                    scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                    config=dict(workload=WORKLOAD, rollouts=B, nodes=nv, horizon=H,
+                                checkpoint_every=k, obstacles=nobs, grad_mode="surrogate",
+                                parallelism=f"rollouts sharded, dp{world}",
+                                l2="256 MB write between timed steps, outside the timed intervals"),
+                    roofline=roof, cpu_baseline=cpu,
+                    e2e=dict(value=e2e_value, unit=UNIT,
+                             h2d_bytes_per_step=int(q0.numel() * 4 + U.numel() * 4),
+                             d2h_bytes_per_step=int(B * 4 + B * H * 6 * 4)),
+                    gpu_launches=launches, clocks=clocks,
+                    status_nonzero=int(np.count_nonzero(status)),
+                    per_step_ms=[round(x * 1e3, 4) for x in per])
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * cordsim.h -- C ABI of the B300-native contact-smoothed differentiable rope/cloth simulator.
+ *
+ * The library implements the simulator of arxiv 2606.14188, Sec. 4.1 ("Differentiable Deformable
+ * Object Simulator with Contact Smoothing") and the calls its planners make (Sec. 3, Problem 1:
+ * q_{k+1} = f(q_k, u_k); Sec. 4.2: the linearisation A(z,v), B(z,v); Sec. 4.1 eq. (diff-sim):
+ * the adjoint dL/dtheta).
+ *
+ * Conventions for every entry point
+ *   - State layout (Sec. 4.1): q = [x_0 .. x_{nv-1}, g_0, g_1], n_q = 3 n_v + 6; node positions
+ *     (cloth nodes row-major), then the two 3-D gripper positions.  Controls u = [du_0, du_1]
+ *     (n_u = 6): gripper displacement commands, g+ = g + u (kinematic grippers).
+ *   - Array arguments are caller-owned DEVICE pointers unless stated otherwise, row-major and
+ *     contiguous, in the handle's real type (float when real_bytes = 4, double when 8).
+ *     int32 status arrays are device pointers too.  The library never frees caller memory.
+ *   - Calls are asynchronous and ordered on the given CUDA stream (`stream` is a cudaStream_t;
+ *     NULL = the legacy default stream).  A handle may be used by one stream at a time.
+ *   - Every function returns a cs_status.  Argument errors are reported before any launch and
+ *     leave outputs untouched; per-rollout numerical failures are reported as bits in status[b]
+ *     (CS_ST_*) and do not fail the call.  cs_last_error() gives a message for the calling thread.
+ *   - Nothing aborts the process; device loops are bounded by the iteration caps in cs_params.
+ */
+#ifndef CORDSIM_H
+#define CORDSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CS_OK = 0,
+  CS_ERR_INVALID_ARG = 1,
+  CS_ERR_OOM = 2,
+  CS_ERR_NOCONVERGE = 3,
+  CS_ERR_NONFINITE = 4,
+  CS_ERR_TIMEOUT = 5,
+  CS_ERR_PENDING = 6,
+  CS_ERR_CUDA = 7,
+  CS_ERR_CANCELLED = 8,
+  CS_ERR_UNSUPPORTED = 9
+} cs_status;
+
+/* per-rollout status bits written to status[b] */
+#define CS_ST_NEWTON 1     /* stage-1 Newton reached newton_max before converging          */
+#define CS_ST_CONTACT 2    /* stage-2 interior point reached ipm_max / found no interior    */
+#define CS_ST_NONFINITE 4  /* a non-finite value appeared                                   */
+#define CS_ST_NOTPD 8      /* a stage-2 or adjoint system was not positive definite         */
+
+#define CS_MAX_OBSTACLES 8
+#define CS_MAX_GOAL 64
+
+enum { CS_ROPE = 0, CS_CLOTH = 1 };
+enum { CS_PLANE = 0, CS_SPHERE = 1, CS_BOX = 2 };
+enum { CS_HARD = 0, CS_SMOOTH = 1 };          /* fwd_mode */
+enum { CS_SURROGATE = 0, CS_CONSISTENT = 1 }; /* grad_mode */
+
+/* Obstacle: plane p = {n_x, n_y, n_z, offset} (phi = n.x - offset - r, |n| = 1);
+ * sphere p = {c_x, c_y, c_z, R}; axis-aligned box p = {c_x, c_y, c_z, h_x, h_y, h_z}. */
+typedef struct {
+  int type;
+  double p[6];
+} cs_obstacle;
+
+/* Simulator parameters (Sec. 4.1; values are not printed in the paper and are inputs here). */
+typedef struct {
+  int kind;                 /* CS_ROPE: chain of n_nodes; CS_CLOTH: rows x cols grid          */
+  int n_nodes, rows, cols;
+  int grasp_node[2];        /* node a(i) held by gripper i                                   */
+  double dt;                /* time step delta t [s]                                         */
+  double gravity[3];        /* [m/s^2]                                                       */
+  double node_mass;         /* lumped mass per node [kg]; M = node_mass I                    */
+  double k_stretch, k_shear, k_bend;  /* spring stiffnesses [N/m]; rest lengths from rest_x  */
+  double D_max;             /* grasp stiffness D_max [N/m]                                   */
+  double kappa_h;           /* grasp smoothing length kappa in D = D_max exp(-|c|/kappa) [m] */
+  double kappa_c;           /* relaxed complementarity s^T lambda = kappa_c [N m]            */
+  double kappa_hard;        /* barrier weight at which the nonsmooth SOCP is declared solved */
+  double kappa_decay;       /* barrier decrease per path-following stage (0 < . < 1)         */
+  double mu;                /* friction coefficient                                          */
+  double r_grasp;           /* nonsmooth grasp active while |c_i| <= r_grasp [m]             */
+  double node_radius;       /* contact radius of a node [m]                                  */
+  double sigma0;            /* interior start of a penetrating contact slack [m]             */
+  int n_obstacles;
+  cs_obstacle obstacles[CS_MAX_OBSTACLES];
+  int fwd_mode;             /* CS_HARD (paper forward) or CS_SMOOTH                          */
+  int grad_mode;            /* CS_SURROGATE (paper) or CS_CONSISTENT (smooth fwd + exact grad)*/
+  int newton_max, ipm_max;  /* iteration caps                                                */
+  double newton_tol;        /* stage-1 stop: max |Newton step| <= newton_tol [m]             */
+  double ipm_tol;           /* stage-2 stop: max |Newton step| <= ipm_tol [m]                */
+  int checkpoint_every;     /* adjoint checkpoint interval k (>= 1)                          */
+  int real_bytes;           /* 4 = FP32, 8 = FP64                                            */
+  int max_batch, max_horizon; /* size the handle's workspace                                 */
+} cs_params;
+
+/* Planning loss (the paper's cost J is not printed):
+ *   L = w_goal sum_{j in goal} |x_j(H) - goal_pos_j|^2
+ *     + w_pen sum_{t=1..H} sum_{j, non-plane obstacles o} max(0, pen_margin - phi_jo(q_t))^2
+ *     + w_u sum_{t=0..H-1} |u_t|^2 */
+typedef struct {
+  int n_goal;
+  int goal_nodes[CS_MAX_GOAL];
+  double goal_pos[CS_MAX_GOAL][3];
+  double w_goal, w_pen, pen_margin, w_u;
+} cs_loss;
+
+typedef struct cs_sim cs_sim;
+
+/* Create a simulator for one scene.  rest_x: HOST array [n_v][3] of rest node positions (the
+ * spring rest lengths are taken from it).  Allocates the handle's device workspace for
+ * max_batch rollouts of up to max_horizon steps.  Errors: CS_ERR_INVALID_ARG (bad sizes,
+ * n_v beyond the kernel's limit, unknown obstacle), CS_ERR_OOM, CS_ERR_CUDA. */
+cs_status sim_create(const cs_params* params, const double* rest_x, cs_sim** out);
+
+/* Release the handle and its workspace (synchronises the device first).  NULL is accepted. */
+cs_status sim_destroy(cs_sim* sim);
+
+/* Forward rollout q_{t+1} = f(q_t, u_t), t = 0..H-1, in fwd_mode (Sec. 3 eq. (dynamics_sim);
+ * Sec. 4.1 two-stage solve).
+ *   q0   [B][n_q]          initial states
+ *   u    [B][H][6]         controls
+ *   traj [B][H+1][n_q]     all states (may be NULL)
+ *   qH   [B][n_q]          final state (may be NULL)
+ *   status [B]             CS_ST_* bits
+ * Errors: CS_ERR_INVALID_ARG if B > max_batch, H > max_horizon, or a required pointer is NULL. */
+cs_status sim_rollout(cs_sim* sim, int B, int H, const void* q0, const void* u, void* traj,
+                      void* qH, int32_t* status, void* stream);
+
+/* Forward rollout + checkpointed adjoint (Sec. 4.1 eq. (diff-sim), composed over the horizon).
+ * The forward runs in the nonsmooth model (grad_mode CS_SURROGATE) or the smooth model
+ * (CS_CONSISTENT); the backward applies the smooth step's Jacobians along the forward states
+ * (the paper's surrogate gradient).  States are checkpointed every checkpoint_every steps and the
+ * steps in between are recomputed.
+ *   dL_dtraj [B][H+1][n_q] seeds dL/dq_t (may be NULL; then `loss` must be given)
+ *   loss     HOST pointer to the planning loss (may be NULL when dL_dtraj is given; if both are
+ *            given the seeds are added)
+ *   L        [B] loss values (may be NULL)
+ *   dL_du    [B][H][6] (required)
+ *   dL_dq0   [B][n_q] (may be NULL)
+ *   status   [B]
+ * Errors: as sim_rollout; CS_ERR_INVALID_ARG when both dL_dtraj and loss are NULL. */
+cs_status sim_rollout_vjp(cs_sim* sim, int B, int H, const void* q0, const void* u,
+                          const void* dL_dtraj, const cs_loss* loss, void* L, void* dL_du,
+                          void* dL_dq0, int32_t* status, void* stream);
+
+/* Per-step linearisation of the smooth step about a nominal trajectory (Sec. 4.2: A(z,v),
+ * B(z,v)), by forward-mode tangents of the implicit two-stage solve.
+ *   z  [B][H+1][n_q] nominal states (only z_0..z_{H-1} are read)
+ *   v  [B][H][6]     nominal controls
+ *   A  [B][H][n_q][n_q]  A_t[i][j] = d q_{t+1,i} / d q_{t,j}
+ *   Bm [B][H][n_q][6]    B_t[i][j] = d q_{t+1,i} / d u_{t,j}
+ *   status [B] (OR over the steps)
+ * Errors: as sim_rollout. */
+cs_status sim_linearize(cs_sim* sim, int B, int H, const void* z, const void* v, void* A,
+                        void* Bm, int32_t* status, void* stream);
+
+/* Number of kernel launches the library made on the calling thread since the last call
+ * (instrumentation for benchmarks). */
+int64_t cs_launch_count(void);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* cs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORDSIM_H */

@@ -62,6 +62,7 @@ class SmoothStepJacobian:
         info = {}
         qp, st = sim.step(sc, q, u, SMOOTH, tol, info)
         self.q_next = qp
+        self.counts = (info["newton_it"], info["ipm_it"])
         self.status = st
         x, g = sim.split_q(sc, q)
         self.x, self.g = x, g
@@ -205,7 +206,7 @@ def rollout_vjp(sc: sim.Scene, q0, U, grad_mode="surrogate", dL_dtraj=None, tol=
     along it; 'consistent': smooth forward and its exact gradient.  With dL_dtraj given, those
     seeds replace the planning loss.  Returns dict(traj, L, dL_du, dL_dq0, status)."""
     fwd = HARD if grad_mode == "surrogate" else SMOOTH
-    traj, status, _ = sim.rollout(sc, q0, U, fwd, tol)
+    traj, status, fwd_counts = sim.rollout(sc, q0, U, fwd, tol)
     H = U.shape[0]
     if dL_dtraj is None:
         L, seeds, dU = loss_and_seeds(sc, traj, U)
@@ -213,13 +214,16 @@ def rollout_vjp(sc: sim.Scene, q0, U, grad_mode="surrogate", dL_dtraj=None, tol=
         L, seeds, dU = 0.0, np.asarray(dL_dtraj, dtype=np.float64), np.zeros_like(U)
     qbar = seeds[H].copy()
     dL_du = np.zeros_like(U)
+    smooth_counts = []
     for t in range(H - 1, -1, -1):
         jac = SmoothStepJacobian(sc, traj[t], U[t], tol)
         status |= jac.status
+        smooth_counts.append(jac.counts)
         qb, ub = jac.vjp(qbar)
         dL_du[t] = ub + dU[t]
         qbar = qb + seeds[t]
-    return dict(traj=traj, L=L, dL_du=dL_du, dL_dq0=qbar, status=status)
+    return dict(traj=traj, L=L, dL_du=dL_du, dL_dq0=qbar, status=status, fwd_counts=fwd_counts,
+                smooth_counts=smooth_counts[::-1])
 
 
 def linearize(sc: sim.Scene, Z, V, tol=sim.TOL_X):

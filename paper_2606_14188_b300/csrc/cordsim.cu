@@ -1,0 +1,188 @@
+// C-ABI host side of libcordsim: argument checking, workspace, scene upload, kernel launches.
+// Every entry point is declared (with its contract) in include/cordsim.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cordsim.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+thread_local int64_t g_launches = 0;
+
+}  // namespace
+
+cs_status cs_fail(cs_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+cs_status cs_cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return CS_ERR_CUDA;
+}
+
+void cs_count_launch() { ++g_launches; }
+
+using namespace csi;
+
+static cs_status check_common(cs_sim* s, int B, int H) {
+  if (!s) return cs_fail(CS_ERR_INVALID_ARG, "null handle");
+  if (B < 0 || H < 1) return cs_fail(CS_ERR_INVALID_ARG, "B must be >= 0 and H >= 1");
+  if (B > s->P.max_batch) return cs_fail(CS_ERR_INVALID_ARG, "B exceeds max_batch");
+  if (H > s->P.max_horizon) return cs_fail(CS_ERR_INVALID_ARG, "H exceeds max_horizon");
+  return CS_OK;
+}
+
+
+extern "C" {
+
+cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
+  if (!P || !rest_x || !out) return cs_fail(CS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (P->kind != CS_ROPE) return cs_fail(CS_ERR_UNSUPPORTED, "only kind = CS_ROPE is built");
+  const int nv = P->n_nodes;
+  if (nv < 2 || nv > 256) return cs_fail(CS_ERR_INVALID_ARG, "rope n_nodes must be in [2, 256]");
+  for (int i = 0; i < 2; ++i)
+    if (P->grasp_node[i] < 0 || P->grasp_node[i] >= nv)
+      return cs_fail(CS_ERR_INVALID_ARG, "grasp_node out of range");
+  if (P->grasp_node[0] == P->grasp_node[1])
+    return cs_fail(CS_ERR_INVALID_ARG, "the two grippers must hold different nodes");
+  if (P->real_bytes != 4 && P->real_bytes != 8)
+    return cs_fail(CS_ERR_INVALID_ARG, "real_bytes must be 4 or 8");
+  if (P->n_obstacles < 0 || P->n_obstacles > CS_MAX_OBSTACLES)
+    return cs_fail(CS_ERR_INVALID_ARG, "n_obstacles out of range");
+  for (int o = 0; o < P->n_obstacles; ++o) {
+    const int t = P->obstacles[o].type;
+    if (t != CS_PLANE && t != CS_SPHERE && t != CS_BOX)
+      return cs_fail(CS_ERR_INVALID_ARG, "unknown obstacle type");
+  }
+  if (!(P->dt > 0) || !(P->node_mass > 0)) return cs_fail(CS_ERR_INVALID_ARG, "dt and node_mass must be > 0");
+  if (P->checkpoint_every < 1) return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every must be >= 1");
+  if (P->max_batch < 1 || P->max_horizon < 1) return cs_fail(CS_ERR_INVALID_ARG, "max_batch/max_horizon must be >= 1");
+  if (P->newton_max < 1 || P->ipm_max < 1) return cs_fail(CS_ERR_INVALID_ARG, "iteration caps must be >= 1");
+  if (!(P->kappa_decay > 0 && P->kappa_decay < 1)) return cs_fail(CS_ERR_INVALID_ARG, "kappa_decay must be in (0,1)");
+  if (!(P->kappa_c > 0) || !(P->kappa_hard > 0) || P->kappa_hard > P->kappa_c)
+    return cs_fail(CS_ERR_INVALID_ARG, "need 0 < kappa_hard <= kappa_c");
+
+  cs_sim* s = new cs_sim();
+  s->P = *P;
+  s->nv = nv;
+  s->npair = (nv + 1) / 2;
+  s->nq = 3 * nv + 6;
+  s->real_bytes = P->real_bytes;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { delete s; return cs_cuda_fail(e, "cudaGetDevice"); }
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  s->sms = v;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  s->smem_optin = (size_t)v;
+  if (smem_bytes(s, 1, false) > s->smem_optin) {
+    delete s;
+    return cs_fail(CS_ERR_INVALID_ARG, "scene too large for one warp's shared memory");
+  }
+
+  // rest lengths in the kernels' real type
+  std::vector<double> L1(nv - 1), L2(nv > 2 ? nv - 2 : 1, 0.0);
+  auto dist = [&](int a, int b) {
+    double d0 = rest_x[3 * b] - rest_x[3 * a], d1 = rest_x[3 * b + 1] - rest_x[3 * a + 1],
+           d2 = rest_x[3 * b + 2] - rest_x[3 * a + 2];
+    return std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  };
+  for (int j = 0; j + 1 < nv; ++j) L1[j] = dist(j, j + 1);
+  for (int j = 0; j + 2 < nv; ++j) L2[j] = dist(j, j + 2);
+  const size_t rb = (size_t)s->real_bytes;
+  auto upload = [&](const std::vector<double>& h, void** d) -> cudaError_t {
+    cudaError_t er = cudaMalloc(d, h.size() * rb);
+    if (er != cudaSuccess) return er;
+    if (rb == 8) return cudaMemcpy(*d, h.data(), h.size() * 8, cudaMemcpyHostToDevice);
+    std::vector<float> f(h.begin(), h.end());
+    return cudaMemcpy(*d, f.data(), f.size() * 4, cudaMemcpyHostToDevice);
+  };
+  if ((e = upload(L1, &s->d_L1)) != cudaSuccess || (e = upload(L2, &s->d_L2)) != cudaSuccess) {
+    sim_destroy(s);
+    return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "rest lengths") : cs_cuda_fail(e, "upload");
+  }
+  const int k = P->checkpoint_every;
+  const int nseg = (P->max_horizon + k - 1) / k;
+  s->ws_stride = (size_t)(nseg + 1 + k) * s->nq;
+  e = cudaMalloc(&s->d_ws, s->ws_stride * (size_t)P->max_batch * rb);
+  if (e != cudaSuccess) {
+    sim_destroy(s);
+    return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "adjoint workspace") : cs_cuda_fail(e, "cudaMalloc");
+  }
+  *out = s;
+  g_err.clear();
+  return CS_OK;
+}
+
+cs_status sim_destroy(cs_sim* s) {
+  if (!s) return CS_OK;
+  cudaDeviceSynchronize();
+  if (s->d_L1) cudaFree(s->d_L1);
+  if (s->d_L2) cudaFree(s->d_L2);
+  if (s->d_ws) cudaFree(s->d_ws);
+  delete s;
+  return CS_OK;
+}
+
+cs_status sim_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj, void* qH,
+                      int32_t* status, void* stream) {
+  cs_status r = check_common(s, B, H);
+  if (r) return r;
+  if (!q0 || !u) return cs_fail(CS_ERR_INVALID_ARG, "q0 and u are required");
+  if (B == 0) return CS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return s->real_bytes == 4 ? launch_rollout<float>(s, B, H, q0, u, traj, qH, status, st)
+                            : launch_rollout<double>(s, B, H, q0, u, traj, qH, status, st);
+}
+
+cs_status sim_rollout_vjp(cs_sim* s, int B, int H, const void* q0, const void* u,
+                          const void* dL_dtraj, const cs_loss* loss, void* L, void* dL_du,
+                          void* dL_dq0, int32_t* status, void* stream) {
+  cs_status r = check_common(s, B, H);
+  if (r) return r;
+  if (!q0 || !u || !dL_du) return cs_fail(CS_ERR_INVALID_ARG, "q0, u and dL_du are required");
+  if (!dL_dtraj && !loss) return cs_fail(CS_ERR_INVALID_ARG, "give dL_dtraj or a loss");
+  if (loss) {
+    if (loss->n_goal < 0 || loss->n_goal > CS_MAX_GOAL) return cs_fail(CS_ERR_INVALID_ARG, "n_goal out of range");
+    for (int g = 0; g < loss->n_goal; ++g)
+      if (loss->goal_nodes[g] < 0 || loss->goal_nodes[g] >= s->nv)
+        return cs_fail(CS_ERR_INVALID_ARG, "goal node out of range");
+  }
+  if (B == 0) return CS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return s->real_bytes == 4
+             ? launch_vjp<float>(s, B, H, q0, u, dL_dtraj, loss, L, dL_du, dL_dq0, status, st)
+             : launch_vjp<double>(s, B, H, q0, u, dL_dtraj, loss, L, dL_du, dL_dq0, status, st);
+}
+
+cs_status sim_linearize(cs_sim* s, int B, int H, const void* z, const void* v, void* A, void* Bm,
+                        int32_t* status, void* stream) {
+  cs_status r = check_common(s, B, H);
+  if (r) return r;
+  if (!z || !v || !A || !Bm) return cs_fail(CS_ERR_INVALID_ARG, "z, v, A and Bm are required");
+  if (B == 0) return CS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return s->real_bytes == 4 ? launch_linearize<float>(s, B, H, z, v, A, Bm, status, st)
+                            : launch_linearize<double>(s, B, H, z, v, A, Bm, status, st);
+}
+
+int64_t cs_launch_count(void) {
+  const int64_t n = g_launches;
+  g_launches = 0;
+  return n;
+}
+
+const char* cs_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

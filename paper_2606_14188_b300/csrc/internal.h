@@ -1,0 +1,122 @@
+// Internal host-side definitions shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+
+#include "cordsim.h"
+#include "common.cuh"
+#include "rope.cuh"
+
+cs_status cs_fail(cs_status s, const std::string& msg);
+cs_status cs_cuda_fail(cudaError_t e, const char* where);
+void cs_count_launch();
+
+struct cs_sim {
+  cs_params P;
+  int nv, npair, nq;
+  int real_bytes;
+  void* d_L1 = nullptr;   // rest lengths (stretch)
+  void* d_L2 = nullptr;   // rest lengths (bend)
+  void* d_ws = nullptr;   // adjoint workspace: checkpoints + segment states per rollout
+  size_t ws_stride = 0;   // elements per rollout
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+
+namespace csi {
+
+
+template <typename R>
+cs::Scene<R> make_scene(const cs_sim* s, const cs_loss* loss) {
+  cs::Scene<R> S;
+  std::memset(&S, 0, sizeof(S));
+  const cs_params& P = s->P;
+  S.nv = s->nv;
+  S.npair = s->npair;
+  S.nobs = P.n_obstacles;
+  S.grasp[0] = P.grasp_node[0];
+  S.grasp[1] = P.grasp_node[1];
+  S.kind = P.kind;
+  S.rows = P.rows;
+  S.cols = P.cols;
+  S.fwd_mode = P.fwd_mode;
+  S.grad_mode = P.grad_mode;
+  S.newton_max = P.newton_max;
+  S.ipm_max = P.ipm_max;
+  S.ckpt = P.checkpoint_every;
+  S.w = (R)(P.node_mass / (P.dt * P.dt));
+  S.m = (R)P.node_mass;
+  for (int i = 0; i < 3; ++i) S.grav[i] = (R)P.gravity[i];
+  S.Dmax = (R)P.D_max;
+  S.kh = (R)P.kappa_h;
+  S.kc = (R)P.kappa_c;
+  S.khard = (R)P.kappa_hard;
+  S.kdecay = (R)P.kappa_decay;
+  S.mu = (R)P.mu;
+  S.rgrasp = (R)P.r_grasp;
+  S.rad = (R)P.node_radius;
+  S.sig0 = (R)P.sigma0;
+  S.ntol = (R)P.newton_tol;
+  S.itol = (R)P.ipm_tol;
+  S.k1 = (R)P.k_stretch;
+  S.k2 = (R)P.k_bend;
+  S.k3 = (R)P.k_shear;
+  for (int o = 0; o < P.n_obstacles; ++o) {
+    S.ob_type[o] = P.obstacles[o].type;
+    for (int i = 0; i < 6; ++i) S.ob[o][i] = (R)P.obstacles[o].p[i];
+  }
+  S.L1 = static_cast<const R*>(s->d_L1);
+  S.L2 = static_cast<const R*>(s->d_L2);
+  if (loss) {
+    S.has_loss = 1;
+    S.n_goal = loss->n_goal;
+    for (int g = 0; g < loss->n_goal; ++g) {
+      S.goal[g] = loss->goal_nodes[g];
+      for (int i = 0; i < 3; ++i) S.goal_pos[g][i] = (R)loss->goal_pos[g][i];
+    }
+    S.w_goal = (R)loss->w_goal;
+    S.w_pen = (R)loss->w_pen;
+    S.pen_m = (R)loss->pen_margin;
+    S.w_u = (R)loss->w_u;
+  }
+  return S;
+}
+
+inline size_t smem_bytes(const cs_sim* s, int H, bool lin) {
+  const size_t rb = (size_t)s->real_bytes;
+  size_t n = cs::wm_size(s->nv, s->npair, s->P.n_obstacles, lin ? 1 : H, lin);
+  if (lin) n += (size_t)2 * 6 * s->npair * 32;
+  return n * rb;
+}
+
+template <typename Kern>
+cs_status prep_kernel(Kern k, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cs_cuda_fail(e, "cudaFuncSetAttribute");
+  return CS_OK;
+}
+
+inline cs_status check_launch(const char* what) {
+  cs_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cs_cuda_fail(e, what);
+  return CS_OK;
+}
+
+
+
+// launchers (one translation unit per kernel and real type)
+template <typename R>
+cs_status launch_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj,
+                         void* qH, int32_t* status, cudaStream_t st);
+template <typename R>
+cs_status launch_vjp(cs_sim* s, int B, int H, const void* q0, const void* u, const void* dLdtraj,
+                     const cs_loss* loss, void* L, void* dLdu, void* dLdq0, int32_t* status,
+                     cudaStream_t st);
+template <typename R>
+cs_status launch_linearize(cs_sim* s, int B, int H, const void* z, const void* v, void* A,
+                           void* Bm, int32_t* status, cudaStream_t st);
+
+}  // namespace csi

@@ -1,0 +1,6 @@
+// rollout kernel, float instantiation.
+#include "launch_rope.cuh"
+
+namespace csi {
+template cs_status launch_rollout<float>(cs_sim*, int, int, const void*, const void*, void*, void*, int32_t*, cudaStream_t);
+}  // namespace csi

@@ -1,0 +1,57 @@
+"""Algorithmic floating-point work of the rope hot path (the roofline numerator).
+
+The count is per node and per solver iteration of the algorithm (not of the implementation):
+one stage-1 Newton iteration assembles the residual and Hessian, factors the node-coupled matrix
+with a banded LDL^T of half bandwidth p = 8 (n (p^2 + 3p) flops for n unknowns) and solves with
+it (n (4p + 1)), and evaluates the Armijo merit; one stage-2 barrier iteration adds the contact
+terms of every (node, obstacle) pair to the same assembly, factorisation and solve; one adjoint
+step is a smooth re-solve plus two solves and the VJP products.  Iteration counts come from the
+FP64 oracle on the same inputs, so extra iterations of the GPU earn no credit.
+
+Per-operation counts (flops, an FMA counted as 2) of the formulas the method evaluates:
+  spring force + 3x3 Hessian block ......................... 40
+  scatter of a spring block into the matrix (4 blocks) ..... 36
+  residual / matvec of one spring ........................... 24
+  contact pair: signed distance, normal, force and 3x3 W ... 60
+  contact pair: barrier merit evaluation .................... 25
+  spring third-derivative contraction ....................... 30
+  contact pair adjoint product ............................. 70
+"""
+from __future__ import annotations
+
+P_BAND = 8                          # scalar half bandwidth of a rope's node-coupled matrix
+FACT_PER_DOF = P_BAND * P_BAND + 3 * P_BAND    # banded LDL^T
+SOLVE_PER_DOF = 4 * P_BAND + 1
+
+
+def newton_iter_per_node(springs_per_node: float = 2.0) -> float:
+    assembly = springs_per_node * (40 + 36) + 10
+    linalg = 3 * (FACT_PER_DOF + SOLVE_PER_DOF)
+    merit = 1.5 * (springs_per_node * 24 + 12)     # ~1.5 Armijo evaluations per iteration
+    return assembly + linalg + merit
+
+
+def barrier_iter_per_node(nobs: int, springs_per_node: float = 2.0) -> float:
+    assembly = springs_per_node * (40 + 36 + 24) + 10 + nobs * 60
+    linalg = 3 * (FACT_PER_DOF + SOLVE_PER_DOF)
+    merit = 1.5 * (springs_per_node * 24 + nobs * 25)
+    return assembly + linalg + merit
+
+
+def adjoint_per_node(nobs: int, springs_per_node: float = 2.0) -> float:
+    solves = 2 * 3 * SOLVE_PER_DOF
+    refactor = 3 * FACT_PER_DOF + springs_per_node * (40 + 36)
+    vjp = springs_per_node * 30 + nobs * 70 + 12
+    return solves + refactor + vjp
+
+
+def rollout_vjp_flops_per_node_step(counts: dict, nobs: int, k: int) -> float:
+    """counts: mean per step of the oracle's iterations over the sampled rollouts:
+      fwd_newton, fwd_ipm   (nonsmooth forward),
+      sm_newton, sm_ipm     (smooth re-solve of the backward).
+    The forward is run twice except at checkpoints (recompute of k-1 of every k steps)."""
+    fwd = counts["fwd_newton"] * newton_iter_per_node() + counts["fwd_ipm"] * barrier_iter_per_node(nobs)
+    recompute = fwd * (k - 1) / k
+    back = counts["sm_newton"] * newton_iter_per_node() + counts["sm_ipm"] * barrier_iter_per_node(nobs) \
+        + adjoint_per_node(nobs)
+    return fwd + recompute + back

@@ -1,0 +1,66 @@
+"""The C-ABI library loads and exports every entry point include/cordsim.h declares, and the
+ctypes mirrors of its structs have the C layout (CPU only: no compute call is made)."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2606_14188_b300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cordsim.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                       text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.lib()
+    names = declared_functions()
+    assert {"sim_create", "sim_destroy", "sim_rollout", "sim_rollout_vjp", "sim_linearize",
+            "cs_last_error"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in L.SIGNATURES, f"{n} has no ctypes signature"
+
+
+def test_struct_layout_matches_c():
+    src = r"""
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "cordsim.h"
+    int main(void) {
+      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(cs_params), sizeof(cs_loss), sizeof(cs_obstacle),
+             offsetof(cs_params, obstacles), offsetof(cs_params, max_horizon),
+             offsetof(cs_loss, goal_pos), offsetof(cs_params, newton_tol));
+      return 0;
+    }
+    """
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    vals = [int(v) for v in out]
+    assert vals == [C.sizeof(L.cs_params), C.sizeof(L.cs_loss), C.sizeof(L.cs_obstacle),
+                    L.cs_params.obstacles.offset, L.cs_params.max_horizon.offset,
+                    L.cs_loss.goal_pos.offset, L.cs_params.newton_tol.offset]
+
+
+def test_argument_errors_without_gpu():
+    """Argument errors are reported before any device work (null arguments, bad kinds)."""
+    lib = L.lib()
+    h = C.c_void_p()
+    assert lib.sim_create(None, None, C.byref(h)) == 1
+    assert b"null" in lib.cs_last_error()
+    assert lib.sim_rollout(None, 1, 1, None, None, None, None, None, None) == 1
+    assert lib.sim_destroy(None) == 0

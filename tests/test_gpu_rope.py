@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP32 states within 1e-4 relative (max-abs error over a rollout / max |q|), FP32
+gradients within 1e-3 relative (2-norm) with cosine >= 0.999; FP64 within 1e-8 relative.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import sim as osim, grad as ograd  # noqa: E402
+from paper_2606_14188_b300 import scenes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL_STATE32, TOL_GRAD32, COS32 = 1e-4, 1e-3, 0.999
+TOL64 = 1e-8
+
+
+def _sim(scene, real_bytes, B, H, **kw):
+    from paper_2606_14188_b300.sim import Sim
+    return Sim(scene, real_bytes=real_bytes, max_batch=max(B, 1), max_horizon=H, **kw)
+
+
+def _t(x, rb):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float32 if rb == 4 else torch.float64,
+                        device="cuda")
+
+
+def _oscene(scene):
+    return osim.Scene(scene["params"], scene["rest_x"])
+
+
+def rel_state(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def check_grad(g, ref, tol, cos_min):
+    g, ref = g.ravel(), ref.ravel()
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    cos = g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref))
+    assert rel <= tol and cos >= cos_min, (rel, cos)
+
+
+# ------------------------------------------------------------------------------------------
+# one 20-node rope, FP64, horizon 10 (ground plane + one sphere)
+# ------------------------------------------------------------------------------------------
+
+def test_rope20_fp64_rollout_hard_and_smooth():
+    w = scenes.workload(1)
+    sc = w["scene"]
+    osc = _oscene(sc)
+    for mode in ("hard", "smooth"):
+        s = _sim(sc, 8, 1, 10, fwd_mode=mode)
+        traj, qH, st = s.rollout(_t(w["q0"], 8), _t(w["U"], 8))
+        ref, ost, _ = osim.rollout(osc, w["q0"][0], w["U"][0], mode)
+        assert int(st[0]) == 0 and ost == 0
+        assert rel_state(traj[0].cpu().numpy(), ref) <= TOL64
+        assert rel_state(qH[0].cpu().numpy(), ref[-1]) <= TOL64
+
+
+@pytest.mark.parametrize("grad_mode", ["surrogate", "consistent"])
+def test_rope20_fp64_vjp(grad_mode):
+    w = scenes.workload(1)
+    sc = w["scene"]
+    s = _sim(sc, 8, 1, 10, grad_mode=grad_mode)
+    Lv, dU, dq0, st = s.rollout_vjp(_t(w["q0"], 8), _t(w["U"], 8))
+    ref = ograd.rollout_vjp(_oscene(sc), w["q0"][0], w["U"][0], grad_mode)
+    assert int(st[0]) == 0
+    assert abs(float(Lv[0]) - ref["L"]) <= TOL64 * abs(ref["L"])
+    check_grad(dU[0].cpu().numpy(), ref["dL_du"], TOL64, 1 - 1e-12)
+    check_grad(dq0[0].cpu().numpy(), ref["dL_dq0"], TOL64, 1 - 1e-12)
+
+
+# ------------------------------------------------------------------------------------------
+# batched 64-node rope, FP32, horizon 50, 2 spheres + 2 boxes, checkpoint every 7 steps
+# ------------------------------------------------------------------------------------------
+
+def _rope64(B):
+    w = scenes.workload(2)
+    return w, w["scene"], w["q0"][:B], w["U"][:B]
+
+
+def test_rope64_fp32_rollout_vs_oracle():
+    B = 6
+    w, sc, q0, U = _rope64(B)
+    s = _sim(sc, 4, B, 50)
+    traj, qH, st = s.rollout(_t(q0, 4), _t(U, 4))
+    traj = traj.cpu().numpy()
+    osc = _oscene(sc)
+    for b in range(B):
+        ref, ost, _ = osim.rollout(osc, q0[b], U[b], "hard")
+        assert ost == 0 and int(st[b]) == 0
+        assert rel_state(traj[b], ref) <= TOL_STATE32, b
+
+
+def test_rope64_fp32_vjp_vs_oracle():
+    B = 4
+    w, sc, q0, U = _rope64(B)
+    s = _sim(sc, 4, B, 50)
+    Lv, dU, dq0, st = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    osc = _oscene(sc)
+    for b in range(B):
+        ref = ograd.rollout_vjp(osc, q0[b], U[b], "surrogate")
+        assert int(st[b]) == 0
+        assert abs(float(Lv[b]) - ref["L"]) <= TOL_STATE32 * abs(ref["L"])
+        check_grad(dU[b].cpu().numpy(), ref["dL_du"], TOL_GRAD32, COS32)
+
+
+def test_rope64_full_batch_sampled():
+    """The launch the benchmark times (1024 rollouts x 50 steps); sampled rollouts against the
+    oracle, and all statuses clean."""
+    w = scenes.workload(2)
+    sc = w["scene"]
+    B, H = w["B"], w["H"]
+    s = _sim(sc, 4, B, H)
+    Lv, dU, _, st = s.rollout_vjp(_t(w["q0"], 4), _t(w["U"], 4), want_dq0=False)
+    st = st.cpu().numpy()
+    assert np.count_nonzero(st) == 0, np.unique(st, return_counts=True)
+    osc = _oscene(sc)
+    for b in (0, 517, B - 1):
+        ref = ograd.rollout_vjp(osc, w["q0"][b], w["U"][b], "surrogate")
+        assert abs(float(Lv[b]) - ref["L"]) <= TOL_STATE32 * abs(ref["L"])
+        check_grad(dU[b].cpu().numpy(), ref["dL_du"], TOL_GRAD32, COS32)
+
+
+def test_rope64_deterministic():
+    B = 32
+    w, sc, q0, U = _rope64(B)
+    s = _sim(sc, 4, B, 50)
+    a = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    b = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+# ------------------------------------------------------------------------------------------
+# linearisation, 40-node rope
+# ------------------------------------------------------------------------------------------
+
+def test_rope40_linearize_vs_oracle():
+    w = scenes.workload(4)
+    sc = w["scene"]
+    B, H = 2, 3
+    osc = _oscene(sc)
+    Z = np.zeros((B, H + 1, osc.nq))
+    V = w["U"][:B, :H]
+    for b in range(B):
+        Z[b], _, _ = osim.rollout(osc, w["q0"][b], V[b], "hard")
+    s = _sim(sc, 4, B, H)
+    A, Bm, st = s.linearize(_t(Z, 4), _t(V, 4))
+    A, Bm = A.cpu().numpy(), Bm.cpu().numpy()
+    assert np.all(st.cpu().numpy() == 0)
+    for b in range(B):
+        Ar, Br = ograd.linearize(osc, Z[b], V[b])
+        for t in range(H):
+            assert np.linalg.norm(A[b, t] - Ar[t]) <= 1e-3 * np.linalg.norm(Ar[t])
+            assert np.linalg.norm(Bm[b, t] - Br[t]) <= 1e-3 * np.linalg.norm(Br[t])
+
+
+def test_rope20_fp64_linearize_vs_oracle():
+    w = scenes.workload(1)
+    sc = w["scene"]
+    osc = _oscene(sc)
+    H = 10
+    Z, _, _ = osim.rollout(osc, w["q0"][0], w["U"][0], "hard")
+    s = _sim(sc, 8, 1, H)
+    A, Bm, st = s.linearize(_t(Z[None], 8), _t(w["U"], 8))
+    Ar, Br = ograd.linearize(osc, Z, w["U"][0])
+    assert int(st[0]) == 0
+    assert np.max(np.abs(A[0].cpu().numpy() - Ar)) <= TOL64 * np.max(np.abs(Ar))
+    assert np.max(np.abs(Bm[0].cpu().numpy() - Br)) <= TOL64 * np.max(np.abs(Br))
+
+
+# ------------------------------------------------------------------------------------------
+# edge cases
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nv", [2, 3, 21, 33, 100])
+def test_odd_and_small_chains_fp64(nv):
+    """Chains whose pair count is not a power of two, odd chains (a padded dummy node), the
+    two-node chain and a chain longer than one pair per lane."""
+    sc = scenes.rope_scene(nv, n_spheres=1, n_boxes=1, seed=17 + nv)
+    H = 4
+    U = scenes.controls_uniform(2, H, seed=nv)
+    q0 = scenes.batch_q0(sc, 2)
+    s = _sim(sc, 8, 2, H)
+    traj, _, st = s.rollout(_t(q0, 8), _t(U, 8))
+    osc = _oscene(sc)
+    for b in range(2):
+        ref, ost, _ = osim.rollout(osc, q0[b], U[b], "hard")
+        assert int(st[b]) == ost == 0
+        assert rel_state(traj[b].cpu().numpy(), ref) <= TOL64
+    Lv, dU, _, st = s.rollout_vjp(_t(q0, 8), _t(U, 8))
+    ref = ograd.rollout_vjp(osc, q0[1], U[1], "surrogate")
+    check_grad(dU[1].cpu().numpy(), ref["dL_du"], TOL64, 1 - 1e-12)
+
+
+def test_ragged_checkpoint_segments_and_no_obstacles():
+    sc = scenes.rope_scene(16, n_spheres=1, seed=5)
+    H = 10
+    U = scenes.controls_uniform(3, H, seed=3)
+    q0 = scenes.batch_q0(sc, 3)
+    osc = _oscene(sc)
+    ref = ograd.rollout_vjp(osc, q0[2], U[2], "surrogate")
+    for k in (1, 3, 4, 10, 13):
+        sc["params"]["checkpoint_every"] = k
+        s = _sim(sc, 8, 3, H)
+        _, dU, dq0, st = s.rollout_vjp(_t(q0, 8), _t(U, 8))
+        check_grad(dU[2].cpu().numpy(), ref["dL_du"], TOL64, 1 - 1e-12)
+    sc2 = scenes.rope_scene(16, n_spheres=0, seed=5)
+    sc2["params"]["obstacles"] = []
+    s = _sim(sc2, 8, 3, H)
+    _, dU, _, st = s.rollout_vjp(_t(q0, 8), _t(U, 8))
+    ref = ograd.rollout_vjp(_oscene(sc2), q0[0], U[0], "surrogate")
+    check_grad(dU[0].cpu().numpy(), ref["dL_du"], TOL64, 1 - 1e-12)
+
+
+def test_dL_dtraj_seeds_and_autograd():
+    """The autograd layer's backward equals sim_rollout_vjp with the same dL/dtraj seeds, which
+    equals the oracle's adjoint with those seeds."""
+    from paper_2606_14188_b300.sim import RolloutFn
+    sc = scenes.rope_scene(12, n_spheres=1, seed=9)
+    H = 6
+    U = scenes.controls_uniform(2, H, seed=2)
+    q0 = scenes.batch_q0(sc, 2)
+    s = _sim(sc, 8, 2, H)
+    rng = np.random.default_rng(0)
+    Wt = rng.normal(size=(2, H + 1, s.nq))
+    qt = _t(q0, 8).requires_grad_(True)
+    Ut = _t(U, 8).requires_grad_(True)
+    traj, _ = RolloutFn.apply(qt, Ut, s)
+    (traj * _t(Wt, 8)).sum().backward()
+    ref = ograd.rollout_vjp(_oscene(sc), q0[1], U[1], "surrogate", dL_dtraj=Wt[1])
+    check_grad(Ut.grad[1].cpu().numpy(), ref["dL_du"], TOL64, 1 - 1e-12)
+    check_grad(qt.grad[1].cpu().numpy(), ref["dL_dq0"], TOL64, 1 - 1e-12)
+
+
+def test_argument_errors_and_empty_batch():
+    from paper_2606_14188_b300._lib import CordsimError
+    sc = scenes.rope_scene(8, seed=1)
+    s = _sim(sc, 4, 4, 5)
+    q0 = _t(scenes.batch_q0(sc, 5), 4)
+    U = _t(np.zeros((5, 5, 6)), 4)
+    with pytest.raises(CordsimError) as e:
+        s.rollout(q0, U)                     # B = 5 > max_batch = 4
+    assert e.value.code == 1
+    with pytest.raises(CordsimError):
+        s.rollout(_t(scenes.batch_q0(sc, 1), 4), _t(np.zeros((1, 6, 6)), 4))   # H > max_horizon
+    traj, qH, st = s.rollout(_t(np.zeros((0, s.nq)), 4), _t(np.zeros((0, 5, 6)), 4))
+    assert qH.shape == (0, s.nq)
