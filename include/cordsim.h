@@ -126,6 +126,13 @@ cs_status sim_destroy(cs_sim* sim);
 cs_status sim_rollout(cs_sim* sim, int B, int H, const void* q0, const void* u, void* traj,
                       void* qH, int32_t* status, void* stream);
 
+/* sim_rollout with solver instrumentation: counters [B][H][3] (device int32, may be NULL)
+ * receives, per rollout and step, the stage-1 Newton iterations, the stage-2 interior-point
+ * iterations (summed over the path-following stages) and the step's CS_ST_* bits. */
+cs_status sim_rollout_counters(cs_sim* sim, int B, int H, const void* q0, const void* u,
+                               void* traj, void* qH, int32_t* status, int32_t* counters,
+                               void* stream);
+
 /* Forward rollout + checkpointed adjoint (Sec. 4.1 eq. (diff-sim), composed over the horizon).
  * The forward runs in the nonsmooth model (grad_mode CS_SURROGATE) or the smooth model
  * (CS_CONSISTENT); the backward applies the smooth step's Jacobians along the forward states

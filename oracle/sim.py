@@ -30,10 +30,10 @@ Readings taken where the paper is silent (the same readings drive the CUDA path)
   a point of the friction cone with s^T lam = kappa exactly.  The barrier depends on the tangent
   plane only through |s_t|^2 = |sigma|^2 - (n.sigma)^2 with sigma = Delta_j + phi n in world
   coordinates, so no tangent basis is needed.
-* The nonsmooth stage 2 (an SOCP) is solved by the same barrier followed along its central path
-  to kappa_hard; when every phi_i(q*) >= 0, Delta = 0 is the exact optimum and is returned as is.
-* Stage-2 feasibility: an infeasible-start Newton method on (Delta, sigma) with the linear
-  equality sigma_i = Delta_j + phi_i n_i (Boyd & Vandenberghe, Convex Optimization, Sec. 10.3).
+* Stage 2 is solved by a primal-dual interior point with Nesterov-Todd scaling (Vandenberghe's
+  cone QP method).  Its central path at kappa is exactly the smoothed model (s o z = kappa e,
+  s^T lam = kappa); the nonsmooth SOCP is the end of the path, declared reached at kappa_hard.
+  When every phi_i(q*) >= 0, Delta = 0 is the exact nonsmooth optimum and is returned as is.
 * Newton directions use the exact Hessian when it is positive definite, else the Hessian with
   each spring's transverse factor (1 - L/l) clamped at 0; a backtracking Armijo search on the
   stage-1 potential Psi (whose gradient is F) globalises it.
@@ -56,6 +56,8 @@ ST_NOTPD = 8       # a stage-2 / adjoint system was not positive definite
 TOL_X = 1e-13
 NEWTON_MAX = 100
 IPM_MAX = 200
+STALL_ALPHA = 1e-6     # stage-2 step length counted as a stall
+STALL_MAX = 5          # consecutive stalls after which stage 2 reports no solution
 
 
 class Scene:
@@ -378,79 +380,162 @@ def in_cone_interior(sig, n, mu):
     return bool(np.all(sn > 0) and np.all(g > 0))
 
 
-def stage2_barrier(sc: Scene, xs, d, kappa, phi, n, Delta, sig, tol=TOL_X, maxit=IPM_MAX):
-    """Minimise 1/2 Delta^T P Delta + sum_i b(sigma_i) s.t. sigma_i = Delta_j + phi_i n_i by an
-    infeasible-start Newton method (the equality residual r_p is driven to zero; every iterate
-    keeps sigma strictly inside the cone).  Merit: |r_D|^2 + (M/dt^2)^2 |r_p|^2.
-    Returns (Delta, sigma, iterations, status)."""
+def tangent_frame(n):
+    """Unit tangents t1, t2 completing the unit normal n to an orthonormal basis, by the
+    branchless construction of Duff et al., "Building an Orthonormal Basis, Revisited" (JCGT
+    2017).  The solution of stage 2 does not depend on the choice of tangent basis."""
+    sgn = np.where(n[..., 2] >= 0.0, 1.0, -1.0)
+    a = -1.0 / (sgn + n[..., 2])
+    b = n[..., 0] * n[..., 1] * a
+    t1 = np.stack([1.0 + sgn * n[..., 0] ** 2 * a, sgn * b, -sgn * n[..., 0]], axis=-1)
+    t2 = np.stack([b, sgn + n[..., 1] ** 2 * a, -n[..., 1]], axis=-1)
+    return t1, t2
+
+
+def cone_frames(n, mu):
+    """A = [n; mu t1; mu t2]: maps a world vector sigma to the scaled cone coordinates
+    s = (s_n, mu s_t), for which the dual friction cone {s_n >= mu |s_t|} is the standard
+    second-order cone Q = {s_0 >= |s_{1:2}|}.  The contact force is lam = A^T z, z in Q."""
+    t1, t2 = tangent_frame(n)
+    return np.stack([n, mu * t1, mu * t2], axis=-2)
+
+
+J3 = np.diag([1.0, -1.0, -1.0])
+
+
+def soc_det(x):
+    return x[..., 0] ** 2 - (x[..., 1:] ** 2).sum(-1)
+
+
+def soc_interior(x):
+    return bool(np.all(x[..., 0] > 0.0) and np.all(soc_det(x) > 0.0))
+
+
+def jordan(x, y):
+    """Jordan product of the second-order cone: x o y = (x.y, x_0 y_1 + y_0 x_1)."""
+    return np.concatenate([(x * y).sum(-1, keepdims=True),
+                           x[..., :1] * y[..., 1:] + y[..., :1] * x[..., 1:]], axis=-1)
+
+
+def jordan_solve(x, r):
+    """v with x o v = r (x in the interior of Q)."""
+    v0 = (x[..., 0] * r[..., 0] - (x[..., 1:] * r[..., 1:]).sum(-1)) / soc_det(x)
+    v1 = (r[..., 1:] - x[..., 1:] * v0[..., None]) / x[..., :1]
+    return np.concatenate([v0[..., None], v1], axis=-1)
+
+
+def jordan_inverse(x):
+    return np.concatenate([x[..., :1], -x[..., 1:]], axis=-1) / soc_det(x)[..., None]
+
+
+def nt_scaling(s, z):
+    """Nesterov-Todd scaling of a pair s, z in int Q (Vandenberghe, "The CVXOPT linear and
+    quadratic cone program solvers", 2010, second-order cone case): the symmetric W with
+    W z = W^{-1} s.  Returns W, W^{-1} and the scaled point lam = W z."""
+    ds, dz = soc_det(s), soc_det(z)
+    sb = s / np.sqrt(ds)[..., None]
+    zb = z / np.sqrt(dz)[..., None]
+    gam = np.sqrt(0.5 * (1.0 + (sb * zb).sum(-1)))
+    wb = (sb + zb @ J3) / (2.0 * gam)[..., None]
+    e = np.zeros_like(wb); e[..., 0] = 1.0
+    v = (wb + e) / np.sqrt(2.0 * (wb[..., 0] + 1.0))[..., None]
+    beta = (ds / dz) ** 0.25
+    vv = v[..., :, None] * v[..., None, :]
+    W = beta[..., None, None] * (2.0 * vv - J3)
+    Jv = v @ J3
+    Winv = (1.0 / beta)[..., None, None] * (2.0 * Jv[..., :, None] * Jv[..., None, :] - J3)
+    lam = np.einsum("...ab,...b->...a", W, z)
+    return W, Winv, lam
+
+
+def max_step(x, dx):
+    """Largest alpha with x + alpha dx in Q (np.inf if unbounded), per cone."""
+    a = dx[..., 0] ** 2 - (dx[..., 1:] ** 2).sum(-1)
+    b = 2.0 * (x[..., 0] * dx[..., 0] - (x[..., 1:] * dx[..., 1:]).sum(-1))
+    c = soc_det(x)
+    out = np.full(a.shape, np.inf)
+    disc = b * b - 4.0 * a * c
+    with np.errstate(divide="ignore", invalid="ignore"):
+        sq = np.sqrt(np.maximum(disc, 0.0))
+        r1 = np.where(a != 0.0, (-b - sq) / (2.0 * a), np.where(b < 0.0, -c / b, np.inf))
+        r2 = np.where(a != 0.0, (-b + sq) / (2.0 * a), np.inf)
+    for r in (r1, r2):
+        ok = (disc >= 0.0) & (r > 0.0)
+        out = np.where(ok, np.minimum(out, r), out)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t0 = np.where(dx[..., 0] < 0.0, -x[..., 0] / dx[..., 0], np.inf)
+    return np.minimum(out, t0)
+
+
+def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IPM_MAX):
+    """Primal-dual interior point with Nesterov-Todd scaling (the cone QP method of Vandenberghe
+    2010) for
+        min 1/2 Delta^T P Delta  s.t.  s_i = A_i Delta_j + phi_i e1 in Q,
+    with multipliers z_i in Q (contact forces lam_i = A_i^T z_i) and the centering condition
+    s_i o z_i = kappa e, i.e. the relaxed complementarity s^T lam = kappa of the smoothed model.
+    The target is kappa throughout when kappa_final is None (smooth model); otherwise it is
+    lowered each iteration to max(kappa_final, 0.1 <s, z>/m) and the solve ends at the central
+    point of kappa_final.  Each Newton step solves H2 dDelta = rhs with the banded SPD matrix
+    H2 = P + sum_i E_j A_i^T W_i^{-2} A_i E_j^T; steps keep s, z strictly inside Q
+    (fraction to the boundary 0.99).  Returns (Delta, sigma_world, iterations, status)."""
     mu = sc.p["mu"]
-    c2 = sc.w ** 2
+    nv, no = phi.shape
+    Delta = np.zeros((nv, 3))
+    if no == 0:
+        return Delta, np.zeros((nv, 0, 3)), 0, 0
+    A = cone_frames(n, mu)
     P_ab = stage1_hessian_band(sc, xs, d)
-
-    def residuals(Dl, sg):
-        lam = contact_force(sg, n, kappa, mu)
-        rD = stage1_hessian_vec(sc, xs, d, Dl) - lam.sum(axis=1)
-        rp = sg - Dl[:, None, :] - phi[..., None] * n
-        return rD, rp
-
+    e1 = np.zeros((nv, no, 3)); e1[..., 0] = 1.0
+    # interior start: the per-node closed form along each penetrating normal, then s from it
+    # where it lies well inside Q, else (max(phi, sigma0), 0, 0); z central for that s
+    Pd = np.einsum("joa,jab,job->jo", n, stage1_hessian_vec_diag(sc, xs, d), n)
+    push = 0.5 * (-phi + np.sqrt(phi * phi + 4.0 * kappa / Pd))
+    Delta = np.einsum("jo,joa->ja", np.where(phi < 0.0, push, 0.0), n)
+    s = np.einsum("joab,jb->joa", A, Delta) + phi[..., None] * e1
+    ok = (s[..., 0] > 0.0) & (soc_det(s) > 0.25 * s[..., 0] ** 2)
+    s = np.where(ok[..., None], s, np.maximum(phi, sc.p["sigma0"])[..., None] * e1)
+    z = kappa * jordan_inverse(s)
+    m = nv * no
+    stalls = 0
     for it in range(maxit):
-        rD, rp = residuals(Delta, sig)
-        W = contact_force_jacobian(sig, n, kappa, mu)
+        target = kappa if kappa_final is None else \
+            max(kappa_final, min(kappa, 0.1 * float((s * z).sum()) / m))
+        lam_w = np.einsum("joab,joa->job", A, z)
+        r_d = stage1_hessian_vec(sc, xs, d, Delta) - lam_w.sum(axis=1)
+        r_z = s - np.einsum("joab,jb->joa", A, Delta) - phi[..., None] * e1
+        W, Winv, lam = nt_scaling(s, z)
+        d_s = jordan_solve(lam, target * e1 - jordan(lam, lam))
+        M = Winv @ Winv
+        AMA = np.einsum("joba,jobc,jocd->joad", A, M, A)     # A^T M A
         ab = P_ab.copy()
-        band_add_node_blocks(sc, ab, np.arange(sc.nv), W.sum(axis=1))
+        band_add_node_blocks(sc, ab, np.arange(nv), AMA.sum(axis=1))
         try:
             cb = band_factor(ab)
         except LinAlgError:
-            return Delta, sig, it, ST_NOTPD
-        rhs = -rD + np.einsum("joab,job->ja", W, rp)
+            return Delta, None, it, ST_NOTPD
+        g = r_z + np.einsum("joab,job->joa", W, d_s)
+        rhs = -r_d + np.einsum("joba,job->ja", A, np.einsum("joab,job->joa", M, g))
         dD = band_solve(cb, rhs)
-        dS = dD[:, None, :] - rp
-        if np.max(np.abs(dD)) <= tol and np.max(np.abs(dS), initial=0.0) <= tol \
-                and in_cone_interior(sig + dS, n, mu):
-            return Delta + dD, sig + dS, it + 1, 0
-        t = 1.0
-        for _ in range(80):
-            if in_cone_interior(sig + t * dS, n, mu):
-                break
-            t *= 0.5
-        m0 = float(np.sum(rD * rD) + c2 * np.sum(rp * rp))
-        for _ in range(80):
-            r1, p1 = residuals(Delta + t * dD, sig + t * dS)
-            m1 = float(np.sum(r1 * r1) + c2 * np.sum(p1 * p1))
-            if m1 <= (1.0 - 0.01 * t) ** 2 * m0 or m1 == 0.0:
-                break
-            t *= 0.5
-        Delta = Delta + t * dD
-        sig = sig + t * dS
-    return Delta, sig, maxit, ST_CONTACT
-
-
-def stage2_init(sc: Scene, xs, d, kappa, phi, n):
-    """Interior start.  For each node, the pairs are first treated one at a time as if P were
-    the node's own normal stiffness a = n^T P_jj n: the single-pair optimum of
-    a/2 D^2 - kappa log(phi + D) is D = (-phi + sqrt(phi^2 + 4 kappa/a))/2 along n.  Pushes of
-    penetrating pairs (phi < 0) are summed into Delta_j; then sigma_i = Delta_j + phi_i n_i where
-    that point lies inside the cone with a margin, else sigma_i = max(phi_i, sigma0) n_i (an
-    infeasible start that the Newton iteration repairs)."""
-    mu = sc.p["mu"]
-    Delta = np.zeros((sc.nv, 3))
-    if phi.shape[1] == 0:
-        return Delta, np.zeros((sc.nv, 0, 3))
-    e = np.zeros((sc.nv, 3))
-    Pd = np.zeros((sc.nv, phi.shape[1]))
-    for al in range(3):
-        e[:] = 0.0
-        e[:, al] = 1.0
-        col = stage1_hessian_vec_diag(sc, xs, d)[:, :, al]      # P_jj[:, :, al]
-        Pd += n[..., al] * np.einsum("job,jb->jo", n, col)
-    push = 0.5 * (-phi + np.sqrt(phi * phi + 4.0 * kappa / Pd))
-    Delta = np.einsum("jo,joa->ja", np.where(phi < 0.0, push, 0.0), n)
-    sig = Delta[:, None, :] + phi[..., None] * n
-    sn, g = cone_gap(sig, n, mu)
-    ok = (sn > 0.0) & (g > 0.25 * sn * sn)
-    fallback = np.maximum(phi, sc.p["sigma0"])[..., None] * n
-    sig = np.where(ok[..., None], sig, fallback)
-    return Delta, sig
+        ADd = np.einsum("joab,jb->joa", A, dD)
+        dz = np.einsum("joab,job->joa", M, -ADd + np.einsum("joab,job->joa", W, d_s) + r_z)
+        dsv = ADd - r_z
+        if not (np.all(np.isfinite(dD)) and np.all(np.isfinite(dz))):
+            return Delta, None, it, ST_NONFINITE
+        alpha = min(1.0, 0.99 * float(min(max_step(s, dsv).min(), max_step(z, dz).min())))
+        # a linearised cone set can be empty (a node driven between two obstacles whose friction
+        # cones do not meet); steps then collapse: give up after STALL_MAX tiny steps
+        stalls = stalls + 1 if alpha < STALL_ALPHA else 0
+        if stalls >= STALL_MAX:
+            return Delta, Delta[:, None, :] + phi[..., None] * n, it + 1, ST_CONTACT
+        Delta = Delta + alpha * dD
+        s = s + alpha * dsv
+        z = z + alpha * dz
+        if not (soc_interior(s) and soc_interior(z)):
+            return Delta, Delta[:, None, :] + phi[..., None] * n, it + 1, ST_CONTACT
+        if target == (kappa if kappa_final is None else kappa_final) and alpha == 1.0 \
+                and np.max(np.abs(dD)) <= tol and np.max(np.abs(dsv)) <= tol:
+            return Delta, Delta[:, None, :] + phi[..., None] * n, it + 1, 0
+    return Delta, Delta[:, None, :] + phi[..., None] * n, maxit, ST_CONTACT
 
 
 def stage1_hessian_vec_diag(sc: Scene, X, d):
@@ -466,29 +551,20 @@ def stage1_hessian_vec_diag(sc: Scene, X, d):
 
 
 def stage2_smooth(sc: Scene, xs, d, tol=TOL_X):
+    """Smoothed stage 2: the central point at kappa_c (relaxed complementarity s^T lam = kappa_c)."""
     phi, n = contact_geometry(sc, xs)
-    Delta, sig = stage2_init(sc, xs, d, sc.p["kappa_c"], phi, n)
-    Delta, sig, it, st = stage2_barrier(sc, xs, d, sc.p["kappa_c"], phi, n, Delta, sig, tol)
+    Delta, sig, it, st = stage2_ipm(sc, xs, d, phi, n, sc.p["kappa_c"], None, tol)
     return Delta, sig, phi, n, it, st
 
 
 def stage2_hard(sc: Scene, xs, d, tol=TOL_X):
     """The nonsmooth contact SOCP of eq. (dynamics-second-stage).  Delta = 0 when no pair
-    penetrates; otherwise the barrier is followed from kappa_c down to kappa_hard."""
+    penetrates; otherwise the primal-dual path is followed from kappa_c down to kappa_hard."""
     phi, n = contact_geometry(sc, xs)
     if np.all(phi >= 0.0):
         return np.zeros((sc.nv, 3)), None, phi, n, 0, 0
-    kappa = sc.p["kappa_c"]
-    Delta, sig = stage2_init(sc, xs, d, kappa, phi, n)
-    its = 0
-    while True:
-        Delta, sig, it, st = stage2_barrier(sc, xs, d, kappa, phi, n, Delta, sig, tol)
-        its += it
-        if st or kappa <= sc.p["kappa_hard"]:
-            return Delta, sig, phi, n, its, st
-        kappa = kappa * sc.p["kappa_decay"]
-        if kappa < sc.p["kappa_hard"] * (1.0 + 1e-6):
-            kappa = sc.p["kappa_hard"]
+    Delta, sig, it, st = stage2_ipm(sc, xs, d, phi, n, sc.p["kappa_c"], sc.p["kappa_hard"], tol)
+    return Delta, sig, phi, n, it, st
 
 
 # ------------------------------------------------------------------------------------------

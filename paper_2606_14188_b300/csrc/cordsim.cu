@@ -137,13 +137,18 @@ cs_status sim_destroy(cs_sim* s) {
 
 cs_status sim_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj, void* qH,
                       int32_t* status, void* stream) {
+  return sim_rollout_counters(s, B, H, q0, u, traj, qH, status, nullptr, stream);
+}
+
+cs_status sim_rollout_counters(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj,
+                               void* qH, int32_t* status, int32_t* counters, void* stream) {
   cs_status r = check_common(s, B, H);
   if (r) return r;
   if (!q0 || !u) return cs_fail(CS_ERR_INVALID_ARG, "q0 and u are required");
   if (B == 0) return CS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  return s->real_bytes == 4 ? launch_rollout<float>(s, B, H, q0, u, traj, qH, status, st)
-                            : launch_rollout<double>(s, B, H, q0, u, traj, qH, status, st);
+  return s->real_bytes == 4 ? launch_rollout<float>(s, B, H, q0, u, traj, qH, status, counters, st)
+                            : launch_rollout<double>(s, B, H, q0, u, traj, qH, status, counters, st);
 }
 
 cs_status sim_rollout_vjp(cs_sim* s, int B, int H, const void* q0, const void* u,

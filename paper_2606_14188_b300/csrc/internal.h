@@ -110,7 +110,7 @@ inline cs_status check_launch(const char* what) {
 // launchers (one translation unit per kernel and real type)
 template <typename R>
 cs_status launch_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj,
-                         void* qH, int32_t* status, cudaStream_t st);
+                         void* qH, int32_t* status, int32_t* counters, cudaStream_t st);
 template <typename R>
 cs_status launch_vjp(cs_sim* s, int B, int H, const void* q0, const void* u, const void* dLdtraj,
                      const cs_loss* loss, void* L, void* dLdu, void* dLdq0, int32_t* status,

@@ -7,14 +7,14 @@ namespace csi {
 
 template <typename R>
 cs_status launch_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj,
-                         void* qH, int32_t* status, cudaStream_t st) {
+                         void* qH, int32_t* status, int32_t* counters, cudaStream_t st) {
   cs::Scene<R> S = make_scene<R>(s, nullptr);
   const size_t smem = smem_bytes(s, H, false);
   if (smem > s->smem_optin) return cs_fail(CS_ERR_INVALID_ARG, "horizon too long for shared memory");
   cs_status r = prep_kernel(cs::rope_rollout_kernel<R>, smem);
   if (r) return r;
   cs::rope_rollout_kernel<R><<<B, 32, smem, st>>>(S, B, H, (const R*)q0, (const R*)u, (R*)traj,
-                                                   (R*)qH, status);
+                                                   (R*)qH, status, counters);
   return check_launch("rope_rollout_kernel");
 }
 

@@ -784,7 +784,8 @@ extern __shared__ __align__(16) unsigned char cs_smem[];
 
 template <typename R>
 __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int H, const R* q0,
-                                                         const R* U, R* traj, R* qH, int32_t* status) {
+                                                         const R* U, R* traj, R* qH, int32_t* status,
+                                                         int32_t* counters) {
   const int lane = threadIdx.x;
   const int nq = 3 * S.nv + 6;
   WM<R> m = wm_carve<R>(reinterpret_cast<R*>(cs_smem), S.nv, S.npair, S.nobs, H, false);
@@ -799,7 +800,12 @@ __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int
       if (lane < 6) m.misc[M_U + lane] = m.u[6 * t + lane];
       __syncwarp();
       int ni, ii;
-      st |= sim_step(S, m, lane, smooth, &ni, &ii);
+      const int s1 = sim_step(S, m, lane, smooth, &ni, &ii);
+      st |= s1;
+      if (counters && lane == 0) {
+        int32_t* c = counters + ((size_t)b * H + t) * 3;
+        c[0] = ni; c[1] = ii; c[2] = s1;
+      }
       advance_state(S, m, lane);
       if (traj) store_q(S, m, traj + ((size_t)b * (H + 1) + t + 1) * nq, lane);
     }

@@ -39,7 +39,7 @@ def default_params(kind: str = "rope") -> dict:
         D_max=1.0e4,
         kappa_h=0.01,          # grasp smoothing length [m]
         kappa_c=1.0e-4,        # contact smoothing (relaxed complementarity) [N m]
-        kappa_hard=1.0e-8,     # barrier weight at which the nonsmooth SOCP is declared solved
+        kappa_hard=1.0e-6,     # central-path weight at which the nonsmooth SOCP is declared solved
         kappa_decay=0.1,       # path-following decrease of the barrier weight per stage
         mu=0.5,
         r_grasp=0.01,

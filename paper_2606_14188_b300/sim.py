@@ -147,6 +147,20 @@ class Sim:
                                     _ptr(status), _stream()), "sim_rollout")
         return traj, qH, status
 
+    def rollout_counters(self, q0, U):
+        """rollout plus per-step solver counters [B, H, 3] = (Newton its, IPM its, status)."""
+        B, H = U.shape[0], U.shape[1]
+        self._t(q0, (B, self.nq), "q0")
+        self._t(U, (B, H, 6), "U")
+        traj = self._new(B, H + 1, self.nq)
+        qH = self._new(B, self.nq)
+        status = torch.zeros(B, dtype=torch.int32, device="cuda")
+        counters = torch.zeros(B, H, 3, dtype=torch.int32, device="cuda")
+        L.check(L.lib().sim_rollout_counters(self._h, B, H, _ptr(q0), _ptr(U), _ptr(traj),
+                                             _ptr(qH), _ptr(status), _ptr(counters), _stream()),
+                "sim_rollout_counters")
+        return traj, qH, status, counters
+
     def rollout_vjp(self, q0, U, dL_dtraj=None, use_loss=True, want_dq0=True):
         B, H = U.shape[0], U.shape[1]
         self._t(q0, (B, self.nq), "q0")

@@ -241,6 +241,7 @@ def test_stage2_hard_kkt_and_independent_solver(mu):
     (P Delta = sum J^T lambda, lambda in F_mu, s in F*_mu, s.lambda ~ 0) and matches an
     independent general-purpose solver (SciPy SLSQP) on the same small SOCP."""
     sc, q, u = _contact_case(mu)
+    sc.p["kappa_hard"] = 1e-10          # the FP64 oracle can follow the path this far here
     info = {}
     qp, st = sim.step(sc, q, u, sim.HARD, info=info)
     assert st == 0
@@ -275,12 +276,21 @@ def test_stage2_hard_kkt_and_independent_solver(mu):
     res = minimize(lambda z: 0.5 * z @ P @ z, np.abs(phi.min()) * np.tile([0, 0, 1.0], sc.nv),
                    jac=lambda z: P @ z, constraints=cons, method="SLSQP",
                    options=dict(ftol=1e-15, maxiter=500))
+    # SLSQP meets the nonsmooth cone constraints only to ~1e-6, so the two agree to that; the
+    # KKT checks above pin the interior-point solution itself
     np.testing.assert_allclose(Delta.ravel(), res.x, atol=2e-6)
+    # the default end of the path (kappa_hard = 1e-6 N m) is within O(kappa_hard / lam_n)
+    sc.p["kappa_hard"] = 1e-6
+    info2 = {}
+    sim.step(sc, q, u, sim.HARD, info=info2)
+    lam_min = max(1e-3, float(np.min(np.linalg.norm(lam.sum(1), axis=1)[phi.min(1) < 0])))
+    assert np.max(np.abs(info2["Delta"] - Delta)) <= 10 * 1e-6 / lam_min
 
 
 def test_hard_contact_limit():
     """As kappa_c -> 0 the smooth step tends to the nonsmooth one, with error O(kappa)."""
     sc, q, u = _contact_case(0.5)
+    sc.p["kappa_hard"] = 1e-11             # the nonsmooth reference, far down the path
     qh, _ = sim.step(sc, q, u, sim.HARD)
     errs = []
     for kap in (1e-4, 1e-5, 1e-6, 1e-7):
@@ -479,3 +489,86 @@ def test_state_dimensions_printed_in_paper():
             rest = np.stack([np.arange(a) * 0.05, np.zeros(a), np.zeros(a)], 1)
         p["grasp_nodes"] = (0, 1)
         assert sim.Scene(p, rest).nq == nq
+
+
+# ------------------------------------------------------------------------------------------
+# second-order cone machinery of the stage-2 interior point
+# ------------------------------------------------------------------------------------------
+
+def _random_cone_pairs(seed, k=20):
+    rng = np.random.default_rng(seed)
+    s = np.concatenate([np.ones((k, 1)), 0.6 * rng.uniform(-1, 1, (k, 2))], axis=1) * rng.uniform(0.1, 3, (k, 1))
+    z = np.concatenate([np.ones((k, 1)), 0.6 * rng.uniform(-1, 1, (k, 2))], axis=1) * rng.uniform(0.1, 3, (k, 1))
+    return s, z
+
+
+def test_tangent_frame_orthonormal():
+    rng = np.random.default_rng(7)
+    n = rng.normal(size=(200, 3))
+    n[:5] = [[0, 0, 1], [0, 0, -1], [1, 0, 0], [0, -1, 0], [0, 0, -1 + 1e-12]]
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    t1, t2 = sim.tangent_frame(n)
+    F = np.stack([n, t1, t2], axis=1)
+    np.testing.assert_allclose(F @ np.swapaxes(F, 1, 2), np.broadcast_to(np.eye(3), F.shape), atol=1e-12)
+
+
+def test_nesterov_todd_scaling_properties():
+    """W is symmetric positive definite with W z = W^{-1} s (the defining NT property)."""
+    s, z = _random_cone_pairs(8)
+    W, Winv, lam = sim.nt_scaling(s, z)
+    np.testing.assert_allclose(np.einsum("kab,kb->ka", W, z), np.einsum("kab,kb->ka", Winv, s), atol=1e-12)
+    np.testing.assert_allclose(W @ Winv, np.broadcast_to(np.eye(3), W.shape), atol=1e-12)
+    assert np.all(np.linalg.eigvalsh(W) > 0)
+
+
+def test_jordan_algebra_and_step_to_boundary():
+    s, z = _random_cone_pairs(9)
+    r = np.random.default_rng(10).normal(size=s.shape)
+    v = sim.jordan_solve(s, r)
+    np.testing.assert_allclose(sim.jordan(s, v), r, atol=1e-12)
+    np.testing.assert_allclose(sim.jordan(s, sim.jordan_inverse(s)), np.tile([1.0, 0, 0], (len(s), 1)), atol=1e-12)
+    d = np.random.default_rng(11).normal(size=s.shape)
+    a = sim.max_step(s, d)
+    fin = np.isfinite(a)
+    edge = s[fin] + a[fin, None] * d[fin]
+    np.testing.assert_allclose(sim.soc_det(edge), 0.0, atol=1e-10)
+    assert np.all(edge[:, 0] >= -1e-12)
+    # just inside / outside
+    assert sim.soc_interior(s[fin] + 0.999 * a[fin, None] * d[fin])
+    big = s[~fin] + 1e6 * d[~fin]
+    assert np.all(big[:, 0] >= np.linalg.norm(big[:, 1:], axis=1) - 1e-6)
+
+
+def test_central_point_scaling_equals_barrier_hessian():
+    """On the central path s o z = kappa e, A^T W^{-2} A is the Hessian of the relaxed
+    complementarity barrier and A^T z its force: the primal-dual iteration and the smoothed
+    model share one definition."""
+    rng = np.random.default_rng(12)
+    n = rng.normal(size=(15, 3)); n /= np.linalg.norm(n, axis=1, keepdims=True)
+    for mu in (0.2, 0.5, 1.3):
+        A = sim.cone_frames(n, mu)
+        tang = rng.normal(size=(15, 3))
+        tang -= (tang * n).sum(1, keepdims=True) * n
+        tang *= (0.6 * 0.01 / mu) / np.linalg.norm(tang, axis=1, keepdims=True)
+        sig = n * 0.01 + tang
+        s = np.einsum("iab,ib->ia", A, sig)
+        assert sim.soc_interior(s)
+        kap = 3e-4
+        z = kap * sim.jordan_inverse(s)
+        _, Winv, _ = sim.nt_scaling(s, z)
+        AMA = np.einsum("iba,ibc,icd->iad", A, Winv @ Winv, A)
+        np.testing.assert_allclose(AMA, sim.contact_force_jacobian(sig, n, kap, mu), rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(np.einsum("iab,ia->ib", A, z), sim.contact_force(sig, n, kap, mu), atol=1e-14)
+
+
+def test_infeasible_cone_set_is_flagged():
+    """A node pushed deep between two obstacles whose friction cones do not meet has no stage-2
+    solution: the step is flagged CS_ST_CONTACT quickly instead of running to the cap."""
+    X0 = np.array([[0.0, 0.0, 0.0], [0.3, 0.0, 0.3]])
+    obs = [scenes.sphere((0.03, 0.0, 0.0), 0.04), scenes.sphere((-0.03, 0.0, 0.0), 0.04)]
+    sc, q = rope(2, X0, k_s=0.0, k_b=0.0, m=0.01, dt=0.05, D=1e4, obstacles=obs, mu=0.8,
+                 grippers=[[0.0, 0.0, 0.0], [5.0, 5.0, 5.0]])
+    info = {}
+    qp, st = sim.step(sc, q, np.zeros(6), sim.HARD, info=info)
+    assert st & sim.ST_CONTACT
+    assert info["ipm_it"] < 60
