@@ -240,9 +240,9 @@ def stage1_hessian_band(sc: Scene, X, d, project=False):
     return ab
 
 
-def stage1_hessian_vec(sc: Scene, X, d, v):
-    """(dF/dq*) v without forming the matrix."""
-    Hs = spring_hessians(sc, X)
+def stage1_hessian_vec(sc: Scene, X, d, v, project=False):
+    """(dF/dq*) v without forming the matrix (the projected Hessian when `project`)."""
+    Hs = spring_hessians(sc, X, project)
     dv = v[sc.b] - v[sc.a]
     f = np.einsum("sij,sj->si", Hs, dv)
     out = sc.w * v.copy()
@@ -485,6 +485,7 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
         return Delta, np.zeros((nv, 0, 3)), 0, 0
     A = cone_frames(n, mu)
     P_ab = stage1_hessian_band(sc, xs, d)
+    projected = False       # P falls back to the projected spring Hessian if H2 is not PD
     e1 = np.zeros((nv, no, 3)); e1[..., 0] = 1.0
     # interior start: the per-node closed form along each penetrating normal, then s from it
     # where it lies well inside Q, else (max(phi, sigma0), 0, 0); z central for that s
@@ -501,7 +502,7 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
         target = kappa if kappa_final is None else \
             max(kappa_final, min(kappa, 0.1 * float((s * z).sum()) / m))
         lam_w = np.einsum("joab,joa->job", A, z)
-        r_d = stage1_hessian_vec(sc, xs, d, Delta) - lam_w.sum(axis=1)
+        r_d = stage1_hessian_vec(sc, xs, d, Delta, projected) - lam_w.sum(axis=1)
         r_z = s - np.einsum("joab,jb->joa", A, Delta) - phi[..., None] * e1
         W, Winv, lam = nt_scaling(s, z)
         d_s = jordan_solve(lam, target * e1 - jordan(lam, lam))
@@ -512,7 +513,19 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
         try:
             cb = band_factor(ab)
         except LinAlgError:
-            return Delta, None, it, ST_NOTPD
+            if projected:
+                return Delta, None, it, ST_NOTPD
+            # stage 1 ended where d^2E is indefinite: use the Hessian with each spring's
+            # transverse factor clamped at 0 (as stage 1 does), for the rest of this solve
+            projected = True
+            P_ab = stage1_hessian_band(sc, xs, d, project=True)
+            r_d = r_d - stage1_hessian_vec(sc, xs, d, Delta) + stage1_hessian_vec(sc, xs, d, Delta, True)
+            ab = P_ab.copy()
+            band_add_node_blocks(sc, ab, np.arange(nv), AMA.sum(axis=1))
+            try:
+                cb = band_factor(ab)
+            except LinAlgError:
+                return Delta, None, it, ST_NOTPD
         g = r_z + np.einsum("joab,job->joa", W, d_s)
         rhs = -r_d + np.einsum("joba,job->ja", A, np.einsum("joab,job->joa", M, g))
         dD = band_solve(cb, rhs)

@@ -178,6 +178,87 @@ __device__ __forceinline__ void cone_force_dn(const R sg[3], const R n[3], R kap
   for (int i = 0; i < 3; ++i) out[i] = c1 * (n[i] * sv + sn * v[i]) - c2 * a[i] * sv;
 }
 
+// ---- second-order cone machinery of the stage-2 interior point.
+//      The dual friction cone {s_n >= mu |s_t|} becomes the standard cone Q = {x0 >= |x_{1:2}|}
+//      in the scaled coordinates s = A sigma, A = [n; mu t1; mu t2]; contact force lam = A^T z.
+
+// unit tangents completing n (Duff et al., "Building an Orthonormal Basis, Revisited", JCGT 2017)
+template <typename R>
+__device__ __forceinline__ void tangent_frame(const R n[3], R t1[3], R t2[3]) {
+  const R sg = n[2] >= R(0) ? R(1) : R(-1);
+  const R a = R(-1) / (sg + n[2]);
+  const R b = n[0] * n[1] * a;
+  t1[0] = R(1) + sg * n[0] * n[0] * a; t1[1] = sg * b; t1[2] = -sg * n[0];
+  t2[0] = b; t2[1] = sg + n[1] * n[1] * a; t2[2] = -n[1];
+}
+
+template <typename R>
+__device__ __forceinline__ void cone_frame(const R n[3], R mu, R A[9]) {
+  R t1[3], t2[3];
+  tangent_frame(n, t1, t2);
+  for (int i = 0; i < 3; ++i) { A[i] = n[i]; A[3 + i] = mu * t1[i]; A[6 + i] = mu * t2[i]; }
+}
+
+template <typename R>
+__device__ __forceinline__ R soc_det(const R x[3]) { return x[0] * x[0] - x[1] * x[1] - x[2] * x[2]; }
+
+template <typename R>
+__device__ __forceinline__ bool soc_inside(const R x[3]) { return x[0] > R(0) && soc_det(x) > R(0); }
+
+// v with x o v = r (Jordan product x o v = (x.v, x0 v1 + v0 x1))
+template <typename R>
+__device__ __forceinline__ void jordan_solve(const R x[3], const R r[3], R v[3]) {
+  const R v0 = (x[0] * r[0] - x[1] * r[1] - x[2] * r[2]) / soc_det(x);
+  v[0] = v0;
+  v[1] = (r[1] - x[1] * v0) / x[0];
+  v[2] = (r[2] - x[2] * v0) / x[0];
+}
+
+// Nesterov-Todd scaling of s, z in int Q: symmetric W with W z = W^{-1} s (Vandenberghe 2010)
+template <typename R>
+__device__ __forceinline__ void nt_scaling(const R s[3], const R z[3], R W[9], R Wi[9], R lam[3]) {
+  const R ds = soc_det(s), dz = soc_det(z);
+  const R rs = R(1) / sqrt(ds), rz = R(1) / sqrt(dz);
+  R sb[3] = {s[0] * rs, s[1] * rs, s[2] * rs};
+  R zb[3] = {z[0] * rz, z[1] * rz, z[2] * rz};
+  const R gam = sqrt(R(0.5) * (R(1) + sb[0] * zb[0] + sb[1] * zb[1] + sb[2] * zb[2]));
+  const R ig = R(1) / (R(2) * gam);
+  R wb[3] = {(sb[0] + zb[0]) * ig, (sb[1] - zb[1]) * ig, (sb[2] - zb[2]) * ig};
+  const R iv = R(1) / sqrt(R(2) * (wb[0] + R(1)));
+  R v[3] = {(wb[0] + R(1)) * iv, wb[1] * iv, wb[2] * iv};
+  const R beta = sqrt(sqrt(ds / dz));
+  R Jv[3] = {v[0], -v[1], -v[2]};
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      const R J = i == k ? (i == 0 ? R(1) : R(-1)) : R(0);
+      W[i * 3 + k] = beta * (R(2) * v[i] * v[k] - J);
+      Wi[i * 3 + k] = (R(2) * Jv[i] * Jv[k] - J) / beta;
+    }
+  for (int i = 0; i < 3; ++i) lam[i] = W[i * 3] * z[0] + W[i * 3 + 1] * z[1] + W[i * 3 + 2] * z[2];
+}
+
+// largest alpha with x + alpha dx in Q (1e30 when unbounded)
+template <typename R>
+__device__ __forceinline__ R soc_max_step(const R x[3], const R dx[3]) {
+  const R a = soc_det(dx);
+  const R b = R(2) * (x[0] * dx[0] - x[1] * dx[1] - x[2] * dx[2]);
+  const R c = soc_det(x);
+  R out = R(1e30);
+  const R disc = b * b - R(4) * a * c;
+  if (a != R(0)) {
+    if (disc >= R(0)) {
+      const R sq = sqrt(disc);
+      const R r1 = (-b - sq) / (R(2) * a), r2 = (-b + sq) / (R(2) * a);
+      if (r1 > R(0)) out = fmin(out, r1);
+      if (r2 > R(0)) out = fmin(out, r2);
+    }
+  } else if (b < R(0)) {
+    out = fmin(out, -c / b);
+  }
+  if (dx[0] < R(0)) out = fmin(out, -x[0] / dx[0]);
+  return out;
+}
+
 // ---- spring k/2 (|d| - L)^2 with d = x_b - x_a: force on b (f = dE/dx_b), and the Hessian
 //      block H = k [u u^T + c (I - u u^T)], c = 1 - L/l (clamped at 0 when `proj`).
 template <typename R>

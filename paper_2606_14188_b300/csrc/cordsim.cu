@@ -114,7 +114,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   }
   const int k = P->checkpoint_every;
   const int nseg = (P->max_horizon + k - 1) / k;
-  s->ws_stride = (size_t)(nseg + 1 + k) * s->nq;
+  s->ws_stride = (size_t)(nseg + 1 + k) * (s->nq + 6);   // checkpoint records: state + grasp offsets
   e = cudaMalloc(&s->d_ws, s->ws_stride * (size_t)P->max_batch * rb);
   if (e != cudaSuccess) {
     sim_destroy(s);
@@ -144,8 +144,8 @@ cs_status sim_rollout_counters(cs_sim* s, int B, int H, const void* q0, const vo
                                void* qH, int32_t* status, int32_t* counters, void* stream) {
   cs_status r = check_common(s, B, H);
   if (r) return r;
-  if (!q0 || !u) return cs_fail(CS_ERR_INVALID_ARG, "q0 and u are required");
   if (B == 0) return CS_OK;
+  if (!q0 || !u) return cs_fail(CS_ERR_INVALID_ARG, "q0 and u are required");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return s->real_bytes == 4 ? launch_rollout<float>(s, B, H, q0, u, traj, qH, status, counters, st)
                             : launch_rollout<double>(s, B, H, q0, u, traj, qH, status, counters, st);
@@ -156,8 +156,8 @@ cs_status sim_rollout_vjp(cs_sim* s, int B, int H, const void* q0, const void* u
                           void* dL_dq0, int32_t* status, void* stream) {
   cs_status r = check_common(s, B, H);
   if (r) return r;
-  if (!q0 || !u || !dL_du) return cs_fail(CS_ERR_INVALID_ARG, "q0, u and dL_du are required");
   if (!dL_dtraj && !loss) return cs_fail(CS_ERR_INVALID_ARG, "give dL_dtraj or a loss");
+  if (B > 0 && (!q0 || !u || !dL_du)) return cs_fail(CS_ERR_INVALID_ARG, "q0, u and dL_du are required");
   if (loss) {
     if (loss->n_goal < 0 || loss->n_goal > CS_MAX_GOAL) return cs_fail(CS_ERR_INVALID_ARG, "n_goal out of range");
     for (int g = 0; g < loss->n_goal; ++g)
@@ -175,8 +175,8 @@ cs_status sim_linearize(cs_sim* s, int B, int H, const void* z, const void* v, v
                         int32_t* status, void* stream) {
   cs_status r = check_common(s, B, H);
   if (r) return r;
-  if (!z || !v || !A || !Bm) return cs_fail(CS_ERR_INVALID_ARG, "z, v, A and Bm are required");
   if (B == 0) return CS_OK;
+  if (!z || !v || !A || !Bm) return cs_fail(CS_ERR_INVALID_ARG, "z, v, A and Bm are required");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return s->real_bytes == 4 ? launch_linearize<float>(s, B, H, z, v, A, Bm, status, st)
                             : launch_linearize<double>(s, B, H, z, v, A, Bm, status, st);

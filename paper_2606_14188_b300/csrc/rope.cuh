@@ -22,7 +22,7 @@ namespace cs {
 template <typename R>
 struct WM {
   R *x0, *dx, *p, *F, *Dl, *PD, *v1, *v2, *v3;  // node vectors [3 nv]
-  R *sig, *phi, *nrm;                            // per (node, obstacle): [3], [1], [3]
+  R *sig, *zz, *phi, *nrm;                       // per (node, obstacle): s [3], z [3], phi, n [3]
   R *T, *B, *V, *r;                              // cyclic-reduction storage
   R *T2, *B2, *V2;                               // second factorisation (linearisation only)
   R *u, *ub;                                     // controls / their adjoint [6 H]
@@ -41,7 +41,7 @@ enum {
 };
 
 __host__ __device__ inline size_t wm_size(int nv, int npair, int nobs, int H, bool two_fact) {
-  size_t s = 9 * 3 * (size_t)nv + (size_t)nv * nobs * 7 + (size_t)npair * (3 * 36 + 6) + 64;
+  size_t s = 9 * 3 * (size_t)nv + (size_t)nv * nobs * 10 + (size_t)npair * (3 * 36 + 6) + 64;
   s = ((s + 3) & ~(size_t)3) + 12 * (size_t)H;
   if (two_fact) s += (size_t)npair * 3 * 36;
   return s;
@@ -55,7 +55,8 @@ __device__ WM<R> wm_carve(R* base, int nv, int npair, int nobs, int H, bool two_
   m.x0 = take(3 * nv); m.dx = take(3 * nv); m.p = take(3 * nv); m.F = take(3 * nv);
   m.Dl = take(3 * nv); m.PD = take(3 * nv); m.v1 = take(3 * nv); m.v2 = take(3 * nv);
   m.v3 = take(3 * nv);
-  m.sig = take((size_t)nv * nobs * 3); m.phi = take((size_t)nv * nobs);
+  m.sig = take((size_t)nv * nobs * 3); m.zz = take((size_t)nv * nobs * 3);
+  m.phi = take((size_t)nv * nobs);
   m.nrm = take((size_t)nv * nobs * 3);
   m.T = take(npair * 36); m.B = take(npair * 36); m.V = take(npair * 36); m.r = take(npair * 6);
   m.misc = take(64);
@@ -158,7 +159,8 @@ __device__ void assemble_pair(const Scene<R>& S, const WM<R>& m, int p, R* T, R*
 
 // y = P v for the nodes of pair p (P the exact stage-1 Hessian at x0 + dx)
 template <typename R>
-__device__ void hess_vec_pair(const Scene<R>& S, const WM<R>& m, int p, const R* v, R* y) {
+__device__ void hess_vec_pair(const Scene<R>& S, const WM<R>& m, int p, const R* v, R* y,
+                              bool proj = false) {
   const R* d = m.misc + M_D;
   for (int h = 0; h < 2; ++h) {
     const int j = 2 * p + h;
@@ -173,7 +175,7 @@ __device__ void hess_vec_pair(const Scene<R>& S, const WM<R>& m, int p, const R*
     spring_params(S, a, o, k, L);
     R dv[3], f[3], H[9];
     spring_vec(m, a, b, dv);
-    spring_eval(dv, k, L, false, f, H);
+    spring_eval(dv, k, L, proj, f, H);
     R dd[3] = {v[3 * b] - v[3 * a], v[3 * b + 1] - v[3 * a + 1], v[3 * b + 2] - v[3 * a + 2]};
     R hv[3];
     for (int i = 0; i < 3; ++i) hv[i] = H[i * 3] * dd[0] + H[i * 3 + 1] * dd[1] + H[i * 3 + 2] * dd[2];
@@ -364,10 +366,63 @@ __device__ void diag_block(const Scene<R>& S, const WM<R>& m, int j, R D[9]) {
     }
 }
 
-// interior start (per-node closed form of the single-pair problem with stiffness n^T P_jj n)
+// Stage 2: primal-dual interior point with Nesterov-Todd scaling (Vandenberghe, "The CVXOPT
+// linear and quadratic cone program solvers", 2010) for
+//     min 1/2 D^T P D   s.t.  s_i = A_i D_j + phi_i e1 in Q,   z_i in Q (forces lam_i = A_i^T z_i),
+// with the centering s_i o z_i = kappa e (the relaxed complementarity of the smoothed model).
+// kfinal < 0: fixed target kappa (smooth model); else the target falls each iteration to
+// max(kfinal, min(kappa, 0.1 <s,z>/m)) and the solve ends at the central point of kfinal.
+// On exit (T, B, V) hold the factorisation of the last Newton matrix H2 = P + sum A^T W^-2 A.
 template <typename R>
-__device__ void stage2_init(const Scene<R>& S, WM<R>& m, R kappa, int lane) {
-  const R mu = S.mu;
+__device__ __forceinline__ void pair_frame(const Scene<R>& S, const WM<R>& m, int q, R A[9]) {
+  R n[3] = {m.nrm[3 * q], m.nrm[3 * q + 1], m.nrm[3 * q + 2]};
+  cone_frame(n, S.mu, A);
+}
+
+// per pair: residual r_z = s - A D_j - phi e1, NT scaling, d_s = lam^{-1} o (target e - lam o lam)
+template <typename R>
+__device__ __forceinline__ void pair_newton_terms(const Scene<R>& S, const WM<R>& m, int j, int q,
+                                                  R target, R A[9], R W[9], R M[9], R rz[3],
+                                                  R Wds[3]) {
+  pair_frame(S, m, q, A);
+  const R* s = m.sig + 3 * q;
+  const R* z = m.zz + 3 * q;
+  for (int a = 0; a < 3; ++a)
+    rz[a] = s[a] - (A[a * 3] * m.Dl[3 * j] + A[a * 3 + 1] * m.Dl[3 * j + 1] +
+                    A[a * 3 + 2] * m.Dl[3 * j + 2]) - (a == 0 ? m.phi[q] : R(0));
+  R Wi[9], lam[3];
+  nt_scaling(s, z, W, Wi, lam);
+  R ll[3] = {lam[0] * lam[0] + lam[1] * lam[1] + lam[2] * lam[2], R(2) * lam[0] * lam[1],
+             R(2) * lam[0] * lam[2]};
+  R rhs[3] = {target - ll[0], -ll[1], -ll[2]};
+  R ds[3];
+  jordan_solve(lam, rhs, ds);
+  for (int a = 0; a < 3; ++a) Wds[a] = W[a * 3] * ds[0] + W[a * 3 + 1] * ds[1] + W[a * 3 + 2] * ds[2];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      M[a * 3 + b] = Wi[a * 3] * Wi[b] + Wi[a * 3 + 1] * Wi[3 + b] + Wi[a * 3 + 2] * Wi[6 + b];
+}
+
+// step of one pair from dDelta_j (in m.p): dz = M(-A dD + W d_s + r_z), ds = A dD - r_z
+template <typename R>
+__device__ __forceinline__ void pair_step(const Scene<R>& S, const WM<R>& m, int j, int q, R target,
+                                          R dsv[3], R dz[3]) {
+  R A[9], W[9], M[9], rz[3], Wds[3];
+  pair_newton_terms(S, m, j, q, target, A, W, M, rz, Wds);
+  R ADd[3], g[3];
+  for (int a = 0; a < 3; ++a) {
+    ADd[a] = A[a * 3] * m.p[3 * j] + A[a * 3 + 1] * m.p[3 * j + 1] + A[a * 3 + 2] * m.p[3 * j + 2];
+    dsv[a] = ADd[a] - rz[a];
+    g[a] = -ADd[a] + Wds[a] + rz[a];
+  }
+  for (int a = 0; a < 3; ++a) dz[a] = M[a * 3] * g[0] + M[a * 3 + 1] * g[1] + M[a * 3 + 2] * g[2];
+}
+
+template <typename R>
+__device__ int stage2_ipm(const Scene<R>& S, WM<R>& m, R kappa, R kfinal, int lane, int* iters) {
+  const int nobs = S.nobs;
+  const R mm = R(S.nv * nobs);
+  // interior start: per-node closed form along each penetrating normal, then s, z = kappa s^-1
   for (int p = lane; p < S.npair; p += 32)
     for (int h = 0; h < 2; ++h) {
       const int j = 2 * p + h;
@@ -375,8 +430,8 @@ __device__ void stage2_init(const Scene<R>& S, WM<R>& m, R kappa, int lane) {
       R D[9];
       diag_block(S, m, j, D);
       R Dj[3] = {0, 0, 0};
-      for (int o = 0; o < S.nobs; ++o) {
-        const int q = j * S.nobs + o;
+      for (int o = 0; o < nobs; ++o) {
+        const int q = j * nobs + o;
         const R ph = m.phi[q];
         if (ph < R(0)) {
           const R* n = m.nrm + 3 * q;
@@ -388,73 +443,84 @@ __device__ void stage2_init(const Scene<R>& S, WM<R>& m, R kappa, int lane) {
         }
       }
       for (int i = 0; i < 3; ++i) m.Dl[3 * j + i] = Dj[i];
-      for (int o = 0; o < S.nobs; ++o) {
-        const int q = j * S.nobs + o;
-        const R ph = m.phi[q];
-        const R* n = m.nrm + 3 * q;
-        R sg[3];
-        for (int i = 0; i < 3; ++i) sg[i] = Dj[i] + ph * n[i];
-        const R sn = dot3(n, sg);
-        const R g = (R(1) + mu * mu) * sn * sn - mu * mu * dot3(sg, sg);
-        const bool ok = sn > R(0) && g > R(0.25) * sn * sn;
-        const R f = ph > S.sig0 ? ph : S.sig0;
-        for (int i = 0; i < 3; ++i) m.sig[3 * q + i] = ok ? sg[i] : f * n[i];
+      for (int o = 0; o < nobs; ++o) {
+        const int q = j * nobs + o;
+        R A[9];
+        pair_frame(S, m, q, A);
+        R sv[3];
+        for (int a = 0; a < 3; ++a)
+          sv[a] = A[a * 3] * Dj[0] + A[a * 3 + 1] * Dj[1] + A[a * 3 + 2] * Dj[2] + (a == 0 ? m.phi[q] : R(0));
+        const bool ok = sv[0] > R(0) && soc_det(sv) > R(0.25) * sv[0] * sv[0];
+        if (!ok) { sv[0] = m.phi[q] > S.sig0 ? m.phi[q] : S.sig0; sv[1] = sv[2] = R(0); }
+        const R dt = soc_det(sv);
+        for (int a = 0; a < 3; ++a) m.sig[3 * q + a] = sv[a];
+        m.zz[3 * q] = kappa * sv[0] / dt;
+        m.zz[3 * q + 1] = -kappa * sv[1] / dt;
+        m.zz[3 * q + 2] = -kappa * sv[2] / dt;
       }
     }
   __syncwarp();
-}
-
-// Infeasible-start Newton on (Delta, sigma) for min 1/2 D^T P D + sum b(sigma), sigma = D_j +
-// phi n (Boyd & Vandenberghe, Sec. 10.3).  Merit |rD|^2 + w^2 |rp|^2.  On exit the
-// factorisation of the last Newton matrix H2 = P + sum W is in (T, B, V).
-template <typename R>
-__device__ int stage2_barrier(const Scene<R>& S, WM<R>& m, R kappa, int lane, int* iters) {
-  const R mu = S.mu;
-  const R c2 = S.w * S.w;
+  int stalls = 0;
+  bool proj = false;
   for (int it = 0; it < S.ipm_max; ++it) {
-    // P Delta into v3
-    for (int p = lane; p < S.npair; p += 32) hess_vec_pair(S, m, p, m.Dl, m.v3);
+    R target = kappa;
+    if (kfinal >= R(0)) {
+      R gap = R(0);
+      for (int p = lane; p < S.npair; p += 32)
+        for (int h = 0; h < 2; ++h) {
+          const int j = 2 * p + h;
+          if (j >= S.nv) continue;
+          for (int o = 0; o < nobs; ++o) gap += dot3(m.sig + 3 * (j * nobs + o), m.zz + 3 * (j * nobs + o));
+        }
+      gap = wsum(gap);
+      target = fmax(kfinal, fmin(kappa, R(0.1) * gap / mm));
+    }
+    const bool final_target = kfinal < R(0) || target == kfinal;
+    // assemble H2 and the right-hand side; if H2 is not positive definite with the exact P
+    // (stage 1 ended where d^2E is indefinite), P becomes the projected spring Hessian for the
+    // rest of this solve
+    for (int attempt = 0; attempt < 2; ++attempt) {
+    for (int p = lane; p < S.npair; p += 32) hess_vec_pair(S, m, p, m.Dl, m.v3, proj);
     __syncwarp();
-    R m0 = R(0);
     for (int p = lane; p < S.npair; p += 32) {
-      assemble_pair(S, m, p, m.T + p * 36, m.B + p * 36, false, false, (R*)nullptr);
+      R* T = m.T + p * 36;
+      assemble_pair(S, m, p, T, m.B + p * 36, proj, false, (R*)nullptr);
       for (int h = 0; h < 2; ++h) {
         const int j = 2 * p + h;
         if (j >= S.nv) { for (int i = 0; i < 3; ++i) m.r[p * 6 + 3 * h + i] = R(0); continue; }
-        R rD[3] = {m.v3[3 * j], m.v3[3 * j + 1], m.v3[3 * j + 2]};
-        R rhs[3] = {0, 0, 0};
-        R* T = m.T + p * 36;
-        for (int o = 0; o < S.nobs; ++o) {
-          const int q = j * S.nobs + o;
-          const R* n = m.nrm + 3 * q;
-          const R* sg = m.sig + 3 * q;
-          R lam[3], W[9];
-          cone_force_jac(sg, n, kappa, mu, lam, W);
-          R rp[3];
-          for (int i = 0; i < 3; ++i) rp[i] = sg[i] - m.Dl[3 * j + i] - m.phi[q] * n[i];
+        R rhs[3] = {-m.v3[3 * j], -m.v3[3 * j + 1], -m.v3[3 * j + 2]};
+        for (int o = 0; o < nobs; ++o) {
+          const int q = j * nobs + o;
+          R A[9], W[9], M[9], rz[3], Wds[3];
+          pair_newton_terms(S, m, j, q, target, A, W, M, rz, Wds);
+          const R* z = m.zz + 3 * q;
+          R g[3], Mg[3];
+          for (int a = 0; a < 3; ++a) g[a] = rz[a] + Wds[a];
+          for (int a = 0; a < 3; ++a) Mg[a] = M[a * 3] * g[0] + M[a * 3 + 1] * g[1] + M[a * 3 + 2] * g[2];
+          // MA = M A ; T += A^T M A ; rhs += A^T z (force) + A^T M g
+          R MA[9];
+          for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c)
+              MA[a * 3 + c] = M[a * 3] * A[c] + M[a * 3 + 1] * A[3 + c] + M[a * 3 + 2] * A[6 + c];
           for (int i = 0; i < 3; ++i) {
-            rD[i] -= lam[i];
-            rhs[i] += W[i * 3] * rp[0] + W[i * 3 + 1] * rp[1] + W[i * 3 + 2] * rp[2];
-            for (int k = 0; k < 3; ++k) T[(3 * h + i) * 6 + 3 * h + k] += W[i * 3 + k];
+            rhs[i] += A[i] * (z[0] + Mg[0]) + A[3 + i] * (z[1] + Mg[1]) + A[6 + i] * (z[2] + Mg[2]);
+            for (int c = 0; c < 3; ++c)
+              T[(3 * h + i) * 6 + 3 * h + c] += A[i] * MA[c] + A[3 + i] * MA[3 + c] + A[6 + i] * MA[6 + c];
           }
-          m0 += c2 * dot3(rp, rp);
         }
-        for (int i = 0; i < 3; ++i) {
-          m.F[3 * j + i] = rD[i];
-          m.r[p * 6 + 3 * h + i] = rhs[i] - rD[i];
-          m0 += rD[i] * rD[i];
-        }
+        for (int i = 0; i < 3; ++i) m.r[p * 6 + 3 * h + i] = rhs[i];
       }
     }
-    m0 = wsum(m0);
     __syncwarp();
-    if (!cr_factor(m.T, m.B, m.V, S.npair, lane)) { *iters = it + 1; return ST_NOTPD; }
+    if (cr_factor(m.T, m.B, m.V, S.npair, lane)) break;
+    if (proj) { *iters = it + 1; return ST_NOTPD; }
+    proj = true;
+    }
     cr_solve(m.T, m.B, m.V, m.r, S.npair, lane);
     from_rhs(S, m.r, m.p, lane);          // p = dDelta
     __syncwarp();
-    // step sizes and the full-step cone test
-    R dmax = R(0);
-    bool inside_full = true;
+    // step length to the cone boundaries, step sizes
+    R amin = R(1e30), dmax = R(0);
     bool bad = false;
     for (int p = lane; p < S.npair; p += 32)
       for (int h = 0; h < 2; ++h) {
@@ -464,96 +530,44 @@ __device__ int stage2_barrier(const Scene<R>& S, WM<R>& m, R kappa, int lane, in
           dmax = fmax(dmax, fabs(m.p[3 * j + i]));
           bad = bad || !(fabs(m.p[3 * j + i]) <= R(1e30));
         }
-        for (int o = 0; o < S.nobs; ++o) {
-          const int q = j * S.nobs + o;
-          const R* n = m.nrm + 3 * q;
-          const R* sg = m.sig + 3 * q;
-          R s1[3];
-          for (int i = 0; i < 3; ++i) {
-            const R rp = sg[i] - m.Dl[3 * j + i] - m.phi[q] * n[i];
-            const R ds = m.p[3 * j + i] - rp;
-            dmax = fmax(dmax, fabs(ds));
-            s1[i] = sg[i] + ds;
+        for (int o = 0; o < nobs; ++o) {
+          const int q = j * nobs + o;
+          R dsv[3], dz[3];
+          pair_step(S, m, j, q, target, dsv, dz);
+          for (int a = 0; a < 3; ++a) {
+            dmax = fmax(dmax, fabs(dsv[a]));
+            bad = bad || !(fabs(dz[a]) <= R(1e30)) || !(fabs(dsv[a]) <= R(1e30));
           }
-          inside_full = inside_full && cone_inside(s1, n, mu);
+          amin = fmin(amin, soc_max_step(m.sig + 3 * q, dsv));
+          amin = fmin(amin, soc_max_step(m.zz + 3 * q, dz));
         }
       }
     dmax = wmax(dmax);
-    inside_full = __all_sync(FULL, inside_full);
+    amin = -wmax(-amin);
     if (__any_sync(FULL, bad)) { *iters = it + 1; return ST_NONFINITE; }
-    R t = R(1);
-    if (!(dmax <= S.itol && inside_full)) {
-      // domain backtracking
-      for (int ls = 0; ls < 60; ++ls) {
-        bool ins = true;
-        for (int p = lane; p < S.npair; p += 32)
-          for (int h = 0; h < 2; ++h) {
-            const int j = 2 * p + h;
-            if (j >= S.nv) continue;
-            for (int o = 0; o < S.nobs; ++o) {
-              const int q = j * S.nobs + o;
-              const R* n = m.nrm + 3 * q;
-              const R* sg = m.sig + 3 * q;
-              R s1[3];
-              for (int i = 0; i < 3; ++i) {
-                const R rp = sg[i] - m.Dl[3 * j + i] - m.phi[q] * n[i];
-                s1[i] = sg[i] + t * (m.p[3 * j + i] - rp);
-              }
-              ins = ins && cone_inside(s1, n, mu);
-            }
-          }
-        if (__all_sync(FULL, ins)) break;
-        t *= R(0.5);
-      }
-      // P dDelta into PD, then merit backtracking
-      for (int p = lane; p < S.npair; p += 32) hess_vec_pair(S, m, p, m.p, m.PD);
-      __syncwarp();
-      for (int ls = 0; ls < 60; ++ls) {
-        R m1 = R(0);
-        for (int p = lane; p < S.npair; p += 32)
-          for (int h = 0; h < 2; ++h) {
-            const int j = 2 * p + h;
-            if (j >= S.nv) continue;
-            R rD[3];
-            for (int i = 0; i < 3; ++i) rD[i] = m.v3[3 * j + i] + t * m.PD[3 * j + i];
-            for (int o = 0; o < S.nobs; ++o) {
-              const int q = j * S.nobs + o;
-              const R* n = m.nrm + 3 * q;
-              const R* sg = m.sig + 3 * q;
-              R s1[3], rp[3], lam[3];
-              for (int i = 0; i < 3; ++i) {
-                rp[i] = sg[i] - m.Dl[3 * j + i] - m.phi[q] * n[i];
-                s1[i] = sg[i] + t * (m.p[3 * j + i] - rp[i]);
-              }
-              cone_force(s1, n, kappa, mu, lam);
-              for (int i = 0; i < 3; ++i) rD[i] -= lam[i];
-              m1 += c2 * (R(1) - t) * (R(1) - t) * dot3(rp, rp);
-            }
-            m1 += dot3(rD, rD);
-          }
-        m1 = wsum(m1);
-        if (m1 <= (R(1) - R(0.01) * t) * (R(1) - R(0.01) * t) * m0 || m1 == R(0)) break;
-        t *= R(0.5);
-      }
-    }
-    // update sigma first (it reads Delta), then Delta
+    const R alpha = fmin(R(1), R(0.99) * amin);
+    stalls = alpha < R(1e-6) ? stalls + 1 : 0;
+    if (stalls >= 5) { *iters = it + 1; return ST_CONTACT; }
+    // update s, z (they read Delta), then Delta
+    bool inside = true;
     for (int p = lane; p < S.npair; p += 32)
       for (int h = 0; h < 2; ++h) {
         const int j = 2 * p + h;
         if (j >= S.nv) continue;
-        for (int o = 0; o < S.nobs; ++o) {
-          const int q = j * S.nobs + o;
-          const R* n = m.nrm + 3 * q;
-          R* sg = m.sig + 3 * q;
-          for (int i = 0; i < 3; ++i) {
-            const R rp = sg[i] - m.Dl[3 * j + i] - m.phi[q] * n[i];
-            sg[i] += t * (m.p[3 * j + i] - rp);
-          }
+        for (int o = 0; o < nobs; ++o) {
+          const int q = j * nobs + o;
+          R dsv[3], dz[3];
+          pair_step(S, m, j, q, target, dsv, dz);
+          R* sq = m.sig + 3 * q;
+          R* zq = m.zz + 3 * q;
+          for (int a = 0; a < 3; ++a) { sq[a] += alpha * dsv[a]; zq[a] += alpha * dz[a]; }
+          inside = inside && soc_inside(sq) && soc_inside(zq);
         }
-        for (int i = 0; i < 3; ++i) m.Dl[3 * j + i] += t * m.p[3 * j + i];
+        for (int i = 0; i < 3; ++i) m.Dl[3 * j + i] += alpha * m.p[3 * j + i];
       }
     __syncwarp();
-    if (t == R(1) && dmax <= S.itol && inside_full) { *iters = it + 1; return 0; }
+    if (!__all_sync(FULL, inside)) { *iters = it + 1; return ST_CONTACT; }
+    if (final_target && alpha == R(1) && dmax <= S.itol) { *iters = it + 1; return 0; }
   }
   *iters = S.ipm_max;
   return ST_CONTACT;
@@ -573,11 +587,10 @@ __device__ int sim_step(const Scene<R>& S, WM<R>& m, int lane, bool smooth, int*
   R* c = m.misc + M_C;
   R* d = m.misc + M_D;
   R* gd = m.misc + M_GD;
-  const R* g = m.misc + M_G;
   if (lane < 2) {
-    const int a = S.grasp[lane];
-    R cc[3];
-    for (int i = 0; i < 3; ++i) cc[i] = g[3 * lane + i] - m.x0[3 * a + i];
+    // c_i = g_i - x0_a(i), maintained by the caller (see advance_state) so that it keeps its
+    // relative precision when it is small next to the absolute coordinates
+    R cc[3] = {c[3 * lane], c[3 * lane + 1], c[3 * lane + 2]};
     const R rho = sqrt(dot3(cc, cc));
     R dd;
     if (smooth) {
@@ -589,7 +602,6 @@ __device__ int sim_step(const Scene<R>& S, WM<R>& m, int lane, bool smooth, int*
       for (int i = 0; i < 3; ++i) gd[3 * lane + i] = R(0);
     }
     d[lane] = dd;
-    for (int i = 0; i < 3; ++i) c[3 * lane + i] = cc[i];
   }
   zero_nodes(S, m.dx, lane);
   zero_nodes(S, m.Dl, lane);
@@ -598,29 +610,20 @@ __device__ int sim_step(const Scene<R>& S, WM<R>& m, int lane, bool smooth, int*
   *iit = 0;
   if (S.nobs == 0) return st;
   const R pmin = contact_geometry(S, m, lane);
-  if (!smooth) {
-    if (pmin >= R(0)) return st;
-    R kappa = S.kc;
-    stage2_init(S, m, kappa, lane);
-    while (true) {
-      int its = 0;
-      const int s2 = stage2_barrier(S, m, kappa, lane, &its);
-      *iit += its;
-      st |= s2;
-      if (s2 || kappa <= S.khard) break;
-      kappa *= S.kdecay;
-      if (kappa < S.khard * R(1.000001)) kappa = S.khard;
-    }
-  } else {
-    stage2_init(S, m, S.kc, lane);
-    st |= stage2_barrier(S, m, S.kc, lane, iit);
-  }
+  if (!smooth && pmin >= R(0)) return st;
+  st |= stage2_ipm(S, m, S.kc, smooth ? R(-1) : S.khard, lane, iit);
   return st;
 }
 
-// x0 <- x0 + dx + Dl ; g <- g + u
+// x0 <- x0 + dx + Dl ; g <- g + u ; c <- c + u - (dx_a + Dl_a) (formed from the small
+// increments, not from the absolute coordinates)
 template <typename R>
 __device__ void advance_state(const Scene<R>& S, WM<R>& m, int lane) {
+  if (lane < 6) {
+    const int a = S.grasp[lane / 3], i = lane % 3;
+    m.misc[M_C + lane] += m.misc[M_U + lane] - (m.dx[3 * a + i] + m.Dl[3 * a + i]);
+  }
+  __syncwarp();
   for (int i = lane; i < 3 * S.nv; i += 32) m.x0[i] += m.dx[i] + m.Dl[i];
   if (lane < 6) m.misc[M_G + lane] += m.misc[M_U + lane];
   __syncwarp();
@@ -659,7 +662,8 @@ __device__ void adjoint_step(const Scene<R>& S, WM<R>& m, int lane, R* ub6) {
         const int q = j * S.nobs + o;
         R ph, n[3], N[9];
         obstacle_eval(S.ob_type[o], S.ob[o], X, S.rad, ph, n, N);
-        const R* sg = m.sig + 3 * q;
+        R sg[3];     // world slack of the converged (primal-feasible) point
+        for (int i = 0; i < 3; ++i) sg[i] = m.Dl[3 * j + i] + ph * n[i];
         R lam[3], W[9];
         cone_force_jac(sg, n, kappa, mu, lam, W);
         R Wm[3];
@@ -755,10 +759,15 @@ __device__ R penalty_lane(const Scene<R>& S, const WM<R>& m, R* seed, int lane) 
 // ------------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------------
+// state q = [x, g] from global memory; the grasp offsets c = g - x_a are formed from it
 template <typename R>
 __device__ __forceinline__ void load_q(const Scene<R>& S, WM<R>& m, const R* q, int lane) {
   for (int i = lane; i < 3 * S.nv; i += 32) m.x0[i] = q[i];
-  if (lane < 6) m.misc[M_G + lane] = q[3 * S.nv + lane];
+  if (lane < 6) {
+    const R g = q[3 * S.nv + lane];
+    m.misc[M_G + lane] = g;
+    m.misc[M_C + lane] = g - q[3 * S.grasp[lane / 3] + lane % 3];
+  }
   __syncwarp();
 }
 
@@ -766,6 +775,23 @@ template <typename R>
 __device__ __forceinline__ void store_q(const Scene<R>& S, const WM<R>& m, R* q, int lane) {
   for (int i = lane; i < 3 * S.nv; i += 32) q[i] = m.x0[i];
   if (lane < 6) q[3 * S.nv + lane] = m.misc[M_G + lane];
+}
+
+// checkpoint record [nq + 6]: the state and the tracked grasp offsets
+template <typename R>
+__device__ __forceinline__ void store_rec(const Scene<R>& S, const WM<R>& m, R* r, int lane) {
+  store_q(S, m, r, lane);
+  if (lane < 6) r[3 * S.nv + 6 + lane] = m.misc[M_C + lane];
+}
+
+template <typename R>
+__device__ __forceinline__ void load_rec(const Scene<R>& S, WM<R>& m, const R* r, int lane) {
+  for (int i = lane; i < 3 * S.nv; i += 32) m.x0[i] = r[i];
+  if (lane < 6) {
+    m.misc[M_G + lane] = r[3 * S.nv + lane];
+    m.misc[M_C + lane] = r[3 * S.nv + 6 + lane];
+  }
+  __syncwarp();
 }
 
 template <typename R>
@@ -826,13 +852,14 @@ __global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, 
   const int nseg = (H + k - 1) / k;
   WM<R> m = wm_carve<R>(reinterpret_cast<R*>(cs_smem), S.nv, S.npair, S.nobs, H, false);
   const bool fwd_smooth = S.grad_mode == CS_CONSISTENT;
+  const int rl = nq + 6;                       // checkpoint record length
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
-    R* ck = ws + (size_t)b * ws_stride;        // checkpoints [nseg + 1][nq]
-    R* seg = ck + (size_t)(nseg + 1) * nq;     // segment states [k][nq]
+    R* ck = ws + (size_t)b * ws_stride;        // checkpoints [nseg + 1][rl]
+    R* seg = ck + (size_t)(nseg + 1) * rl;     // segment states [k][rl]
     load_q(S, m, q0 + (size_t)b * nq, lane);
     load_controls(m.u, U + (size_t)b * H * 6, 6 * H, lane);
     __syncwarp();
-    store_q(S, m, ck, lane);
+    store_rec(S, m, ck, lane);
     int st = 0;
     R Lacc = R(0);
     for (int t = 0; t < H; ++t) {
@@ -841,7 +868,7 @@ __global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, 
       int ni, ii;
       st |= sim_step(S, m, lane, fwd_smooth, &ni, &ii);
       advance_state(S, m, lane);
-      if ((t + 1) % k == 0) store_q(S, m, ck + (size_t)((t + 1) / k) * nq, lane);
+      if ((t + 1) % k == 0) store_rec(S, m, ck + (size_t)((t + 1) / k) * rl, lane);
       if (S.has_loss) Lacc += penalty_lane(S, m, (R*)nullptr, lane);
     }
     // seeds at q_H: goal + penalty + dL/dtraj[H]
@@ -876,19 +903,19 @@ __global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, 
       const int t1 = min(t0 + k, H);
       // recompute states t0 .. t1-1 into seg (keep v1 / gbar: sim_step does not touch them)
       R gb_save = lane < 6 ? m.misc[M_GB + lane] : R(0);
-      load_q(S, m, ck + (size_t)sgi * nq, lane);
-      store_q(S, m, seg, lane);
+      load_rec(S, m, ck + (size_t)sgi * rl, lane);
+      store_rec(S, m, seg, lane);
       for (int t = t0; t < t1 - 1; ++t) {
         if (lane < 6) m.misc[M_U + lane] = m.u[6 * t + lane];
         __syncwarp();
         int ni, ii;
         st |= sim_step(S, m, lane, fwd_smooth, &ni, &ii);
         advance_state(S, m, lane);
-        store_q(S, m, seg + (size_t)(t + 1 - t0) * nq, lane);
+        store_rec(S, m, seg + (size_t)(t + 1 - t0) * rl, lane);
       }
       __syncwarp();
       for (int t = t1 - 1; t >= t0; --t) {
-        load_q(S, m, seg + (size_t)(t - t0) * nq, lane);
+        load_rec(S, m, seg + (size_t)(t - t0) * rl, lane);
         if (lane < 6) { m.misc[M_U + lane] = m.u[6 * t + lane]; m.misc[M_GB + lane] = gb_save; }
         __syncwarp();
         int ni, ii;
@@ -997,7 +1024,8 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
           const int q = j * S.nobs + o;
           R ph, n[3], Nm[9];
           obstacle_eval(S.ob_type[o], S.ob[o], X, S.rad, ph, n, Nm);
-          const R* sg = m.sig + 3 * q;
+          R sg[3];
+          for (int i = 0; i < 3; ++i) sg[i] = m.Dl[3 * j + i] + ph * n[i];
           R lam[3], W[9];
           cone_force_jac(sg, n, S.kc, S.mu, lam, W);
           // G v = -W (n (n.v) + phi N v) + dlam/dn N v ; Rx contact = -G

@@ -177,6 +177,44 @@ def controls_normal(B: int, H: int, n_u: int = 6, sigma: float = 0.02,
     return rng.normal(0.0, sigma, size=(B, H, n_u))
 
 
+def _gripper_clear(p: np.ndarray, obstacles, clearance: float) -> np.ndarray:
+    """Scene-generation test: gripper positions p [..., 3] at least `clearance` from every
+    sphere and box and above every plane (no simulator arithmetic)."""
+    ok = np.ones(p.shape[:-1], dtype=bool)
+    for ob in obstacles:
+        if ob["type"] == "plane":
+            ok &= p @ np.asarray(ob["normal"]) - ob["offset"] >= clearance
+        elif ob["type"] == "sphere":
+            ok &= np.linalg.norm(p - np.asarray(ob["center"]), axis=-1) - ob["radius"] >= clearance
+        else:
+            out = np.maximum(np.abs(p - np.asarray(ob["center"])) - np.asarray(ob["half"]), 0.0)
+            ok &= np.linalg.norm(out, axis=-1) >= clearance
+    return ok
+
+
+def controls_normal_clear(scene: dict, B: int, H: int, sigma: float = 0.02,
+                          clearance: float = 0.02, seed: int = BASE_SEED) -> np.ndarray:
+    """Gripper displacements ~ N(0, sigma^2) per coordinate, redrawn (up to 20 times, else 0)
+    whenever a gripper would come within `clearance` of an obstacle or the table: a planner's
+    candidates move the grippers in free space, as the robots of the paper's tasks do."""
+    rng = np.random.default_rng(seed + 7919)
+    g = np.repeat(scene["q0"][None, -6:].reshape(1, 2, 3), B, axis=0)
+    obs = scene["params"]["obstacles"]
+    U = np.zeros((B, H, 2, 3))
+    for t in range(H):
+        u = rng.normal(0.0, sigma, size=(B, 2, 3))
+        bad = ~_gripper_clear(g + u, obs, clearance)
+        for _ in range(20):
+            if not bad.any():
+                break
+            u[bad] = rng.normal(0.0, sigma, size=(int(bad.sum()), 3))
+            bad = ~_gripper_clear(g + u, obs, clearance)
+        u[bad] = 0.0
+        U[:, t] = u
+        g = g + u
+    return U.reshape(B, H, 6)
+
+
 def batch_q0(scene: dict, B: int) -> np.ndarray:
     return np.repeat(scene["q0"][None, :], B, axis=0)
 
@@ -198,19 +236,19 @@ def workload(i: int, B: int | None = None, H: int | None = None) -> dict:
         sc = rope_scene(64, n_spheres=2, n_boxes=2, seed=seed,
                         sphere_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)))
         B = B or 1024; H = H or 50
-        U = controls_normal(B, H, seed=seed)
+        U = controls_normal_clear(sc, B, H, seed=seed)
         real = 4
         ck = 7
     elif i == 3:  # 512 rollouts of a 32x32 cloth, FP32, horizon 30, table + 2 spheres
         sc = cloth_scene(32, 32, n_spheres=2, seed=seed)
         B = B or 512; H = H or 30
-        U = controls_normal(B, H, seed=seed)
+        U = controls_normal_clear(sc, B, H, seed=seed)
         real = 4
         ck = 5
     elif i == 4:  # 256 nominal trajectories of a 40-node rope, horizon 20 (linearisation)
         sc = rope_scene(40, n_spheres=1, n_boxes=0, seed=seed)
         B = B or 256; H = H or 20
-        U = controls_normal(B, H, seed=seed)
+        U = controls_normal_clear(sc, B, H, seed=seed)
         real = 4
         ck = 1
     else:
