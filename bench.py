@@ -198,7 +198,7 @@ def run_ours(args):
         cpu = dict(value=ns / wall, unit=UNIT, cores=procs, kind="oracle",
                    sample=f"{procs} of the 1024 rollouts (full horizon 50, forward + adjoint), one "
                           f"process per rollout; {wall:.1f} s wall")
-        cres, _ = oracle_sample([0, 341, 682, 1023], 1e-7, 4)
+        cres, _ = oracle_sample([0, 341, 682, 1023], 1e-5, 4)
         counts = counts_mean(cres)
 
     import torch

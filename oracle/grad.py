@@ -57,10 +57,10 @@ def _blocks_to_sparse(rows, cols, blocks, shape):
 class SmoothStepJacobian:
     """Everything needed to apply the smooth step's Jacobian at (q, u), both ways."""
 
-    def __init__(self, sc: sim.Scene, q, u, tol=sim.TOL_X):
+    def __init__(self, sc: sim.Scene, q, u, tol=sim.TOL_X, x_start=None):
         self.sc = sc
         info = {}
-        qp, st = sim.step(sc, q, u, SMOOTH, tol, info)
+        qp, st = sim.step(sc, q, u, SMOOTH, tol, info, x_start=x_start)
         self.q_next = qp
         self.counts = (info["newton_it"], info["ipm_it"])
         self.status = st
@@ -203,10 +203,12 @@ def loss_and_seeds(sc: sim.Scene, traj, U):
 
 def rollout_vjp(sc: sim.Scene, q0, U, grad_mode="surrogate", dL_dtraj=None, tol=sim.TOL_X):
     """Forward rollout + adjoint.  grad_mode 'surrogate': nonsmooth forward, smooth Jacobians
-    along it; 'consistent': smooth forward and its exact gradient.  With dL_dtraj given, those
+    along it; 'consistent': smooth forward and its exact gradient.  The smooth re-solve of each
+    step starts its Newton iteration at the forward step's stage-1 solution.  With dL_dtraj given, those
     seeds replace the planning loss.  Returns dict(traj, L, dL_du, dL_dq0, status)."""
     fwd = HARD if grad_mode == "surrogate" else SMOOTH
-    traj, status, fwd_counts = sim.rollout(sc, q0, U, fwd, tol)
+    xs_fwd = []
+    traj, status, fwd_counts = sim.rollout(sc, q0, U, fwd, tol, xs_out=xs_fwd)
     H = U.shape[0]
     if dL_dtraj is None:
         L, seeds, dU = loss_and_seeds(sc, traj, U)
@@ -216,7 +218,8 @@ def rollout_vjp(sc: sim.Scene, q0, U, grad_mode="surrogate", dL_dtraj=None, tol=
     dL_du = np.zeros_like(U)
     smooth_counts = []
     for t in range(H - 1, -1, -1):
-        jac = SmoothStepJacobian(sc, traj[t], U[t], tol)
+        # the smooth re-solve starts its Newton iteration at the forward step's stage-1 solution
+        jac = SmoothStepJacobian(sc, traj[t], U[t], tol, x_start=xs_fwd[t])
         status |= jac.status
         smooth_counts.append(jac.counts)
         qb, ub = jac.vjp(qbar)

@@ -267,11 +267,11 @@ def band_solve_cols(cb, R):
     return cho_solve_banded((cb, True), R)
 
 
-def stage1_solve(sc: Scene, x, gstar, d, tol=TOL_X, maxit=NEWTON_MAX):
+def stage1_solve(sc: Scene, x, gstar, d, tol=TOL_X, maxit=NEWTON_MAX, x_start=None):
     """Damped Newton for the root q* of F, started at q (Sec. 4.1, "solved using Newton's
-    method").  Stops when the Newton step is below `tol` in every coordinate (the step is then
-    taken).  Returns (q*, iterations, status)."""
-    X = x.copy()
+    method") or at x_start when given.  Stops when the Newton step is below `tol` in every
+    coordinate (the step is then taken).  Returns (q*, iterations, status)."""
+    X = x.copy() if x_start is None else np.array(x_start, dtype=np.float64)
     for it in range(maxit):
         F = stage1_residual(sc, X, x, gstar, d)
         if not np.all(np.isfinite(F)):
@@ -593,12 +593,13 @@ def join_q(x, g):
     return np.concatenate([x.ravel(), g.ravel()])
 
 
-def step(sc: Scene, q, u, mode, tol=TOL_X, info=None):
-    """(q, u) -> q+ : stage 1 then stage 2 (Sec. 4.1, "Simulation Solver")."""
+def step(sc: Scene, q, u, mode, tol=TOL_X, info=None, x_start=None):
+    """(q, u) -> q+ : stage 1 then stage 2 (Sec. 4.1, "Simulation Solver").  x_start: optional
+    start of the stage-1 Newton iteration (the root it converges to is the same)."""
     x, g = split_q(sc, q)
     gstar = g + np.asarray(u, dtype=np.float64).reshape(2, 3)
     d = grasp_stiffness(sc, x, g, mode)
-    xs, it1, st1 = stage1_solve(sc, x, gstar, d, tol)
+    xs, it1, st1 = stage1_solve(sc, x, gstar, d, tol, x_start=x_start)
     if mode == HARD:
         Delta, sig, phi, n, it2, st2 = stage2_hard(sc, xs, d, tol)
     else:
@@ -609,8 +610,9 @@ def step(sc: Scene, q, u, mode, tol=TOL_X, info=None):
     return join_q(xs + Delta, gstar), st1 | st2
 
 
-def rollout(sc: Scene, q0, U, mode, tol=TOL_X):
-    """q_0 .. q_H for controls U[H, 6].  Returns (traj[H+1, nq], status, newton/ipm counts)."""
+def rollout(sc: Scene, q0, U, mode, tol=TOL_X, xs_out=None):
+    """q_0 .. q_H for controls U[H, 6].  Returns (traj[H+1, nq], status, newton/ipm counts);
+    xs_out, if a list, receives each step's stage-1 solution q*."""
     H = U.shape[0]
     traj = np.zeros((H + 1, sc.nq))
     traj[0] = q0
@@ -621,4 +623,6 @@ def rollout(sc: Scene, q0, U, mode, tol=TOL_X):
         traj[t + 1], st = step(sc, traj[t], U[t], mode, tol, info)
         status |= st
         counts.append((info["newton_it"], info["ipm_it"]))
+        if xs_out is not None:
+            xs_out.append(info["xs"])
     return traj, status, counts

@@ -49,7 +49,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   *out = nullptr;
   if (P->kind != CS_ROPE) return cs_fail(CS_ERR_UNSUPPORTED, "only kind = CS_ROPE is built");
   const int nv = P->n_nodes;
-  if (nv < 2 || nv > 256) return cs_fail(CS_ERR_INVALID_ARG, "rope n_nodes must be in [2, 256]");
+  if (nv < 2 || nv > 128) return cs_fail(CS_ERR_INVALID_ARG, "rope n_nodes must be in [2, 128]");
   for (int i = 0; i < 2; ++i)
     if (P->grasp_node[i] < 0 || P->grasp_node[i] >= nv)
       return cs_fail(CS_ERR_INVALID_ARG, "grasp_node out of range");
@@ -114,7 +114,8 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   }
   const int k = P->checkpoint_every;
   const int nseg = (P->max_horizon + k - 1) / k;
-  s->ws_stride = (size_t)(nseg + 1 + k) * (s->nq + 6);   // checkpoint records: state + grasp offsets
+  // checkpoint records: state, grasp offsets, stage-1 offset of the producing step
+  s->ws_stride = (size_t)(nseg + 1 + k) * (s->nq + 6 + 3 * nv);
   e = cudaMalloc(&s->d_ws, s->ws_stride * (size_t)P->max_batch * rb);
   if (e != cudaSuccess) {
     sim_destroy(s);

@@ -3,50 +3,92 @@
 //
 // A rope's node-coupled matrices (dF/dq*, the stage-2 Newton matrix) couple node j with j+1
 // (stretch) and j+2 (bend): block-pentadiagonal in 3x3 node blocks, i.e. block-tridiagonal in
-// 6x6 blocks of node pairs (2p, 2p+1).  Storage per pair row p:
-//   T[p]  6x6 diagonal block (lower triangle used; overwritten by its Cholesky factor with the
-//         reciprocal on the diagonal),
-//   B[p]  6x6 coupling block (row p, column p-s) at the current reduction level,
-//   V[p]  6x6 work block,
-//   r[p]  6-vector right-hand side / solution.
-// Odd-even reduction: at level s the rows k = s (mod 2s) are eliminated in parallel; each
+// 6x6 blocks of node pairs (2p, 2p+1).  Storage is element-major so that lanes working on
+// different rows touch different banks: entry e of row p is X[e * NP + p].
+//   T  6x6 diagonal block (lower triangle; replaced by its Cholesky factor, reciprocal diagonal)
+//   B  6x6 coupling of row p with row p - s at the current reduction level
+//   V  6x6 work block
+//   r  6-vector right-hand side / solution
+// Odd-even reduction: at level s the rows k = s (mod 2s) are eliminated in parallel and each
 // survivor absorbs its two eliminated neighbours' Schur complements.  This is a Cholesky
-// factorisation in the odd-even ordering, so it fails (returns false) exactly when the matrix
-// is not positive definite.  Depth is log2(npair) instead of npair.
+// factorisation in the odd-even ordering, so it fails (returns false) exactly when the matrix is
+// not positive definite; depth log2(N) instead of N.
 #pragma once
 #include "common.cuh"
 
 namespace cs {
 
 template <typename R>
-__device__ bool cr_factor(R* T, R* B, R* V, int N, int lane) {
+__device__ __forceinline__ void ld36(const R* X, int NP, int row, R* a) {
+#pragma unroll
+  for (int e = 0; e < 36; ++e) a[e] = X[e * NP + row];
+}
+
+template <typename R>
+__device__ __forceinline__ void st36(R* X, int NP, int row, const R* a) {
+#pragma unroll
+  for (int e = 0; e < 36; ++e) X[e * NP + row] = a[e];
+}
+
+template <typename R>
+__device__ __forceinline__ void ld_lower(const R* X, int NP, int row, R* a) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int k = 0; k <= i; ++k) a[i * 6 + k] = X[(i * 6 + k) * NP + row];
+}
+
+template <typename R>
+__device__ __forceinline__ void st_lower(R* X, int NP, int row, const R* a) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int k = 0; k <= i; ++k) X[(i * 6 + k) * NP + row] = a[i * 6 + k];
+}
+
+// columns of a 6x6 register matrix: M <- L^{-1} M
+template <typename R>
+__device__ __forceinline__ void lsolve6_cols(const R* L, R* M) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) lsolve6(L, M + c, 6);
+}
+
+template <typename R>
+__device__ __forceinline__ bool cr_factor(R* T, R* B, R* V, int N, int NP, int lane) {
   bool ok = true;
   for (int s = 1; s < N; s <<= 1) {
     const int cnt = (N - s + 2 * s - 1) / (2 * s);
     for (int idx = lane; idx < cnt; idx += 32) {
       const int k = s + 2 * s * idx;
-      R* L = T + k * 36;
+      R L[36], U[36];
+      ld_lower(T, NP, k, L);
       ok = chol6(L) && ok;
-      R* U = B + k * 36;                       // U_k = L_k^{-1} B_k   (B_k couples k to k-s)
-#pragma unroll 1
-      for (int c = 0; c < 6; ++c) lsolve6(L, U + c, 6);
-      if (k + s < N) {                         // V_k = L_k^{-1} B_{k+s}^T
-        const R* Bn = B + (k + s) * 36;
-        R* Vk = V + k * 36;
+      st_lower(T, NP, k, L);
+      ld36(B, NP, k, U);                 // U_k = L_k^{-1} B_k (B_k couples k to k - s)
+      lsolve6_cols(L, U);
+      st36(B, NP, k, U);
+      if (k + s < N) {                   // V_k = L_k^{-1} B_{k+s}^T
+        R W[36];
+#pragma unroll
         for (int c = 0; c < 6; ++c)
-          for (int i = 0; i < 6; ++i) Vk[i * 6 + c] = Bn[c * 6 + i];
-#pragma unroll 1
-        for (int c = 0; c < 6; ++c) lsolve6(L, Vk + c, 6);
+#pragma unroll
+          for (int i = 0; i < 6; ++i) W[i * 6 + c] = B[(c * 6 + i) * NP + k + s];
+        lsolve6_cols(L, W);
+        st36(V, NP, k, W);
       }
     }
     __syncwarp();
     const int cnt2 = (N + 2 * s - 1) / (2 * s);
     for (int idx = lane; idx < cnt2; idx += 32) {
       const int i = 2 * s * idx;
-      R* Ti = T + i * 36;
-      if (i + s < N) {                         // T_i -= U_{i+s}^T U_{i+s}
-        const R* U = B + (i + s) * 36;
+      R Ti[36];
+      ld_lower(T, NP, i, Ti);
+      if (i + s < N) {                   // T_i -= U_{i+s}^T U_{i+s}
+        R U[36];
+        ld36(B, NP, i + s, U);
+#pragma unroll
         for (int a = 0; a < 6; ++a)
+#pragma unroll
           for (int b = 0; b <= a; ++b) {
             R t = R(0);
 #pragma unroll
@@ -54,17 +96,20 @@ __device__ bool cr_factor(R* T, R* B, R* V, int N, int lane) {
             Ti[a * 6 + b] -= t;
           }
       }
-      if (i - s >= 0) {                        // T_i -= V^T V ; B_i = -V^T U   (k = i - s)
-        const R* Vl = V + (i - s) * 36;
-        const R* Ul = B + (i - s) * 36;
-        R* Bi = B + i * 36;
+      if (i - s >= 0) {                  // T_i -= V^T V ; B_i = -V^T U   (k = i - s)
+        R Vl[36], Ul[36], Bi[36];
+        ld36(V, NP, i - s, Vl);
+        ld36(B, NP, i - s, Ul);
+#pragma unroll
         for (int a = 0; a < 6; ++a) {
+#pragma unroll
           for (int b = 0; b <= a; ++b) {
             R t = R(0);
 #pragma unroll
             for (int r = 0; r < 6; ++r) t += Vl[r * 6 + a] * Vl[r * 6 + b];
             Ti[a * 6 + b] -= t;
           }
+#pragma unroll
           for (int b = 0; b < 6; ++b) {
             R t = R(0);
 #pragma unroll
@@ -72,125 +117,155 @@ __device__ bool cr_factor(R* T, R* B, R* V, int N, int lane) {
             Bi[a * 6 + b] = -t;
           }
         }
+        st36(B, NP, i, Bi);
       }
+      st_lower(T, NP, i, Ti);
     }
     __syncwarp();
   }
-  if (lane == 0) ok = chol6(T) && ok;
+  if (lane == 0) {
+    R L[36];
+    ld_lower(T, NP, 0, L);
+    ok = chol6(L) && ok;
+    st_lower(T, NP, 0, L);
+  }
   __syncwarp();
   return __all_sync(FULL, ok);
 }
 
-// Solve with the factorisation left by cr_factor; r [N][6] is overwritten by the solution.
+// Solve with the factorisation left by cr_factor; r [6][NP] is overwritten by the solution.
 template <typename R>
-__device__ void cr_solve(const R* T, const R* B, const R* V, R* r, int N, int lane) {
+__device__ __forceinline__ void cr_solve(const R* T, const R* B, const R* V, R* r, int N, int NP, int lane) {
   int top = 1;
   while (top < N) top <<= 1;
   for (int s = 1; s < N; s <<= 1) {
     const int cnt = (N - s + 2 * s - 1) / (2 * s);
     for (int idx = lane; idx < cnt; idx += 32) {
       const int k = s + 2 * s * idx;
-      lsolve6(T + k * 36, r + k * 6, 1);
+      R L[36], y[6];
+      ld_lower(T, NP, k, L);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) y[a] = r[a * NP + k];
+      lsolve6(L, y, 1);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) r[a * NP + k] = y[a];
     }
     __syncwarp();
     const int cnt2 = (N + 2 * s - 1) / (2 * s);
     for (int idx = lane; idx < cnt2; idx += 32) {
       const int i = 2 * s * idx;
-      R* ri = r + i * 6;
       R acc[6] = {0, 0, 0, 0, 0, 0};
       if (i + s < N) {
-        const R* U = B + (i + s) * 36;
-        const R* w = r + (i + s) * 6;
+        R w[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) w[q] = r[q * NP + i + s];
+#pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
-          for (int q = 0; q < 6; ++q) acc[a] += U[q * 6 + a] * w[q];
+          for (int q = 0; q < 6; ++q) acc[a] += B[(q * 6 + a) * NP + i + s] * w[q];
       }
       if (i - s >= 0) {
-        const R* Vl = V + (i - s) * 36;
-        const R* w = r + (i - s) * 6;
+        R w[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) w[q] = r[q * NP + i - s];
+#pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
-          for (int q = 0; q < 6; ++q) acc[a] += Vl[q * 6 + a] * w[q];
+          for (int q = 0; q < 6; ++q) acc[a] += V[(q * 6 + a) * NP + i - s] * w[q];
       }
-      for (int a = 0; a < 6; ++a) ri[a] -= acc[a];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) r[a * NP + i] -= acc[a];
     }
     __syncwarp();
   }
   if (lane == 0) {
-    lsolve6(T, r, 1);
-    ltsolve6(T, r, 1);
+    R L[36], y[6];
+    ld_lower(T, NP, 0, L);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) y[a] = r[a * NP];
+    lsolve6(L, y, 1);
+    ltsolve6(L, y, 1);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) r[a * NP] = y[a];
   }
   __syncwarp();
   for (int s = top >> 1; s >= 1; s >>= 1) {
     const int cnt = (N - s + 2 * s - 1) / (2 * s);
     for (int idx = lane; idx < cnt; idx += 32) {
       const int k = s + 2 * s * idx;
-      R y[6];
-      for (int a = 0; a < 6; ++a) y[a] = r[k * 6 + a];
-      const R* U = B + k * 36;
-      const R* xl = r + (k - s) * 6;
+      R y[6], xl[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) { y[a] = r[a * NP + k]; xl[a] = r[a * NP + k - s]; }
+#pragma unroll
       for (int a = 0; a < 6; ++a)
 #pragma unroll
-        for (int q = 0; q < 6; ++q) y[a] -= U[a * 6 + q] * xl[q];
+        for (int q = 0; q < 6; ++q) y[a] -= B[(a * 6 + q) * NP + k] * xl[q];
       if (k + s < N) {
-        const R* Vk = V + k * 36;
-        const R* xr = r + (k + s) * 6;
+        R xr[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) xr[a] = r[a * NP + k + s];
+#pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
-          for (int q = 0; q < 6; ++q) y[a] -= Vk[a * 6 + q] * xr[q];
+          for (int q = 0; q < 6; ++q) y[a] -= V[(a * 6 + q) * NP + k] * xr[q];
       }
-      ltsolve6(T + k * 36, y, 1);
-      for (int a = 0; a < 6; ++a) r[k * 6 + a] = y[a];
+      R L[36];
+      ld_lower(T, NP, k, L);
+      ltsolve6(L, y, 1);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) r[a * NP + k] = y[a];
     }
     __syncwarp();
   }
 }
 
-// The same solve run by a single thread on its own right-hand side, stored with element stride
-// `st` (r[(p*6 + a) * st]); used to solve many right-hand sides at once, one per lane.
+// The same solve run by a single thread on its own right-hand side rr[a * NP + row] stored with
+// element stride `st` (rr[(a * NP + row) * st]); many right-hand sides at once, one per lane.
 template <typename R>
-__device__ void cr_solve_serial(const R* T, const R* B, const R* V, R* r, int st, int N) {
+__device__ __forceinline__ void cr_solve_serial(const R* T, const R* B, const R* V, R* rr, int st, int N, int NP) {
+  auto at = [&](int a, int row) -> R& { return rr[((size_t)a * NP + row) * st]; };
   int top = 1;
   while (top < N) top <<= 1;
   for (int s = 1; s < N; s <<= 1) {
-    for (int k = s; k < N; k += 2 * s) lsolve6(T + k * 36, r + k * 6 * st, st);
+    for (int k = s; k < N; k += 2 * s) {
+      R L[36], y[6];
+      ld_lower(T, NP, k, L);
+      for (int a = 0; a < 6; ++a) y[a] = at(a, k);
+      lsolve6(L, y, 1);
+      for (int a = 0; a < 6; ++a) at(a, k) = y[a];
+    }
     for (int i = 0; i < N; i += 2 * s) {
       R acc[6] = {0, 0, 0, 0, 0, 0};
-      if (i + s < N) {
-        const R* U = B + (i + s) * 36;
-        const R* w = r + (i + s) * 6 * st;
+      if (i + s < N)
         for (int a = 0; a < 6; ++a)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) acc[a] += U[q * 6 + a] * w[q * st];
-      }
-      if (i - s >= 0) {
-        const R* Vl = V + (i - s) * 36;
-        const R* w = r + (i - s) * 6 * st;
+          for (int q = 0; q < 6; ++q) acc[a] += B[(q * 6 + a) * NP + i + s] * at(q, i + s);
+      if (i - s >= 0)
         for (int a = 0; a < 6; ++a)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) acc[a] += Vl[q * 6 + a] * w[q * st];
-      }
-      for (int a = 0; a < 6; ++a) r[(i * 6 + a) * st] -= acc[a];
+          for (int q = 0; q < 6; ++q) acc[a] += V[(q * 6 + a) * NP + i - s] * at(q, i - s);
+      for (int a = 0; a < 6; ++a) at(a, i) -= acc[a];
     }
   }
-  lsolve6(T, r, st);
-  ltsolve6(T, r, st);
+  {
+    R L[36], y[6];
+    ld_lower(T, NP, 0, L);
+    for (int a = 0; a < 6; ++a) y[a] = at(a, 0);
+    lsolve6(L, y, 1);
+    ltsolve6(L, y, 1);
+    for (int a = 0; a < 6; ++a) at(a, 0) = y[a];
+  }
   for (int s = top >> 1; s >= 1; s >>= 1) {
     for (int k = s; k < N; k += 2 * s) {
       R y[6];
-      for (int a = 0; a < 6; ++a) y[a] = r[(k * 6 + a) * st];
-      const R* U = B + k * 36;
+      for (int a = 0; a < 6; ++a) y[a] = at(a, k);
       for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int q = 0; q < 6; ++q) y[a] -= U[a * 6 + q] * r[((k - s) * 6 + q) * st];
-      if (k + s < N) {
-        const R* Vk = V + k * 36;
+        for (int q = 0; q < 6; ++q) y[a] -= B[(a * 6 + q) * NP + k] * at(q, k - s);
+      if (k + s < N)
         for (int a = 0; a < 6; ++a)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) y[a] -= Vk[a * 6 + q] * r[((k + s) * 6 + q) * st];
-      }
-      ltsolve6(T + k * 36, y, 1);
-      for (int a = 0; a < 6; ++a) r[(k * 6 + a) * st] = y[a];
+          for (int q = 0; q < 6; ++q) y[a] -= V[(a * 6 + q) * NP + k] * at(q, k + s);
+      R L[36];
+      ld_lower(T, NP, k, L);
+      ltsolve6(L, y, 1);
+      for (int a = 0; a < 6; ++a) at(a, k) = y[a];
     }
   }
 }

@@ -86,8 +86,9 @@ cs::Scene<R> make_scene(const cs_sim* s, const cs_loss* loss) {
 
 inline size_t smem_bytes(const cs_sim* s, int H, bool lin) {
   const size_t rb = (size_t)s->real_bytes;
-  size_t n = cs::wm_size(s->nv, s->npair, s->P.n_obstacles, lin ? 1 : H, lin);
-  if (lin) n += (size_t)2 * 6 * s->npair * 32;
+  const int NP = s->npair <= 32 ? 32 : 64;
+  size_t n = cs::ws_size(NP, s->P.n_obstacles, lin ? 1 : H, lin);
+  if (lin) n += (size_t)2 * 6 * NP * 32;
   return n * rb;
 }
 

@@ -1,313 +1,443 @@
-// Rope (particle chain) kernels: one warp per rollout, the rollout's whole state in shared memory
-// across the horizon, node pairs (2p, 2p+1) owned by lane p (mod 32).
+// Rope (particle chain) kernels: one warp per rollout for the whole horizon.  Node pair
+// p = lane + 32 k (nodes 2p, 2p+1) lives in registers of its lane (slot k < PPL); the springs to
+// the neighbouring pairs read their nodes through warp shuffles; the pair-block matrices and the
+// contact variables live in element-major shared memory (lane-contiguous, conflict free).
 //
 // One step (arxiv 2606.14188, Sec. 4.1, "Simulation Solver"):
 //   stage 1  Newton for q* with F(q*) = M(q*-q)/dt^2 + dE(q*) - tau(u) + sum_i d_i (x*_a - g*_i) = 0
 //            (eq. dynamics-first-stage; kinematic grippers g* = g + u; d_i the grasp stiffness,
 //            D_max 1[|c_i| <= r_grasp] nonsmooth, D_max exp(-|c_i|/kappa_h) smooth);
 //   stage 2  Delta = argmin 1/2 Delta^T P Delta over the dual friction cones (eq.
-//            dynamics-second-stage), by the log barrier of the relaxed complementarity
-//            s^T lam = kappa (Sec. 4.1 "Contact Smoothing"): one barrier solve at kappa_c
-//            (smooth) or a path-following sequence down to kappa_hard (nonsmooth, skipped when
-//            no pair penetrates).
-// Newton iterates are kept as offsets dx from the step's start state x0 (x* = x0 + dx) so the
-// stiff grasp and spring forces are evaluated without absolute-coordinate cancellation.
+//            dynamics-second-stage) by a primal-dual interior point whose central path at kappa is
+//            the relaxed complementarity s^T lam = kappa (Sec. 4.1 "Contact Smoothing"): fixed
+//            kappa_c (smooth) or followed down to kappa_hard (nonsmooth; skipped when no pair
+//            penetrates, where Delta = 0 is exact).
+// Newton iterates are offsets dx from the step's start x0 (x* = x0 + dx), and the grasp offsets
+// c_i = g_i - x_a(i) are carried from step to step as sums of small increments, so that stiff
+// springs see no absolute-coordinate cancellation in FP32.
 #pragma once
 #include "common.cuh"
 #include "cr.cuh"
 
 namespace cs {
 
-// per-warp shared-memory views
+// ------------------------------------------------------------------------------------------
+// shared-memory layout of one warp
+// ------------------------------------------------------------------------------------------
 template <typename R>
-struct WM {
-  R *x0, *dx, *p, *F, *Dl, *PD, *v1, *v2, *v3;  // node vectors [3 nv]
-  R *sig, *zz, *phi, *nrm;                       // per (node, obstacle): s [3], z [3], phi, n [3]
-  R *T, *B, *V, *r;                              // cyclic-reduction storage
-  R *T2, *B2, *V2;                               // second factorisation (linearisation only)
-  R *u, *ub;                                     // controls / their adjoint [6 H]
-  R *misc;                                       // [64]
+struct WS {
+  int NP;                     // pair slots (32 PPL)
+  R *T, *B, *V, *r;           // cyclic-reduction storage [36][NP] x3, [6][NP]
+  R *s, *z, *phi, *nrm;       // contact pairs: [(o*2+h)*3+c][NP] for vectors, [(o*2+h)][NP]
+  R *pm, *pg, *prz;           // per-pair Newton terms of the current iteration: M (6), g (3), r_z (3)
+  R *misc;                    // [64]
+  R *u, *ub;                  // controls and their adjoint [6 H]
+  // linearisation only
+  R *T2, *B2, *V2;            // second factorisation
+  R *xs, *Dn;                 // x* - x0 and Delta of every node [6][NP]
 };
 
-// misc layout
 enum {
   M_G = 0,      // g [6]   gripper positions at the step start
   M_U = 6,      // u [6]   control of the step
-  M_C = 12,     // c [6]   c_i = g_i - x0_a(i)
+  M_C = 12,     // c [6]   c_i = g_i - x0_a(i), carried across steps
   M_D = 18,     // d [2]   grasp stiffness
   M_GD = 20,    // gd [6]  d d_i / d c_i (smooth)
   M_GB = 26,    // gbar [6] adjoint of the gripper positions
-  M_TMP = 32
+  M_UB = 32,    // ubar [6] adjoint of the control (one step)
 };
 
-__host__ __device__ inline size_t wm_size(int nv, int npair, int nobs, int H, bool two_fact) {
-  size_t s = 9 * 3 * (size_t)nv + (size_t)nv * nobs * 10 + (size_t)npair * (3 * 36 + 6) + 64;
+__host__ __device__ inline size_t ws_size(int NP, int nobs, int H, bool lin) {
+  size_t s = (size_t)NP * (3 * 36 + 6) + (size_t)nobs * 2 * NP * 22 + 64;
   s = ((s + 3) & ~(size_t)3) + 12 * (size_t)H;
-  if (two_fact) s += (size_t)npair * 3 * 36;
+  if (lin) s += (size_t)NP * 3 * 36 + 2 * 6 * (size_t)NP;
   return s;
 }
 
 template <typename R>
-__device__ WM<R> wm_carve(R* base, int nv, int npair, int nobs, int H, bool two_fact) {
-  WM<R> m;
+__device__ __forceinline__ WS<R> ws_carve(R* base, int NP, int nobs, int H, bool lin) {
+  WS<R> w;
+  w.NP = NP;
   R* p = base;
   auto take = [&](size_t n) { R* q = p; p += n; return q; };
-  m.x0 = take(3 * nv); m.dx = take(3 * nv); m.p = take(3 * nv); m.F = take(3 * nv);
-  m.Dl = take(3 * nv); m.PD = take(3 * nv); m.v1 = take(3 * nv); m.v2 = take(3 * nv);
-  m.v3 = take(3 * nv);
-  m.sig = take((size_t)nv * nobs * 3); m.zz = take((size_t)nv * nobs * 3);
-  m.phi = take((size_t)nv * nobs);
-  m.nrm = take((size_t)nv * nobs * 3);
-  m.T = take(npair * 36); m.B = take(npair * 36); m.V = take(npair * 36); m.r = take(npair * 6);
-  m.misc = take(64);
-  p = base + (((size_t)(p - base) + 3) & ~(size_t)3);   // 16-byte align the control rows
-  m.u = take(6 * H); m.ub = take(6 * H);
-  if (two_fact) { m.T2 = take(npair * 36); m.B2 = take(npair * 36); m.V2 = take(npair * 36); }
-  else { m.T2 = m.B2 = m.V2 = nullptr; }
-  return m;
+  w.T = take(36 * (size_t)NP); w.B = take(36 * (size_t)NP); w.V = take(36 * (size_t)NP);
+  w.r = take(6 * (size_t)NP);
+  w.s = take((size_t)nobs * 2 * 3 * NP); w.z = take((size_t)nobs * 2 * 3 * NP);
+  w.phi = take((size_t)nobs * 2 * NP); w.nrm = take((size_t)nobs * 2 * 3 * NP);
+  w.pm = take((size_t)nobs * 2 * 6 * NP); w.pg = take((size_t)nobs * 2 * 3 * NP);
+  w.prz = take((size_t)nobs * 2 * 3 * NP);
+  w.misc = take(64);
+  p = base + (((size_t)(p - base) + 3) & ~(size_t)3);
+  w.u = take(6 * (size_t)H); w.ub = take(6 * (size_t)H);
+  if (lin) {
+    w.T2 = take(36 * (size_t)NP); w.B2 = take(36 * (size_t)NP); w.V2 = take(36 * (size_t)NP);
+    w.xs = take(6 * (size_t)NP); w.Dn = take(6 * (size_t)NP);
+  } else {
+    w.T2 = w.B2 = w.V2 = w.xs = w.Dn = nullptr;
+  }
+  return w;
 }
 
+// contact-pair element addresses
+__device__ __forceinline__ int cv(int o, int h, int c, int p, int NP) { return ((o * 2 + h) * 3 + c) * NP + p; }
+__device__ __forceinline__ int cs1(int o, int h, int p, int NP) { return (o * 2 + h) * NP + p; }
+__device__ __forceinline__ int cm6(int o, int h, int c, int p, int NP) { return ((o * 2 + h) * 6 + c) * NP + p; }
+
 // ------------------------------------------------------------------------------------------
-// springs of the chain touching pair p: (a, b = a + o), o = 1 stretch, o = 2 bend
+// per-lane register state
 // ------------------------------------------------------------------------------------------
-template <typename R, typename Fn>
-__device__ __forceinline__ void springs_of_pair(const Scene<R>& S, int p, Fn fn) {
-  for (int o = 1; o <= 2; ++o)
-    for (int a = 2 * p - o; a <= 2 * p + 1; ++a) {
-      const int b = a + o;
-      if (a < 0 || b >= S.nv) continue;
-      if ((a >> 1) != p && (b >> 1) != p) continue;
-      fn(a, b, o);
+template <typename R, int PPL>
+struct Lane {
+  R x0[PPL][6];               // own pair at the step start
+  R xm[PPL][6], xp[PPL][6];   // neighbouring pairs (p - 1, p + 1) at the step start
+  R dx[PPL][6];               // x* - x0
+  R Dl[PPL][6];               // Delta (stage 2)
+  R pv[PPL][6];               // step / work vector
+  R F[PPL][6];                // residual
+  R Ls[PPL][3];               // rest lengths (2p-1,2p), (2p,2p+1), (2p+1,2p+2)
+  R Lb[PPL][4];               // rest lengths (2p-2,2p), (2p-1,2p+1), (2p,2p+2), (2p+1,2p+3)
+};
+
+// value of the neighbouring pairs p - 1 and p + 1 of every slot
+template <typename R, int PPL>
+__device__ __forceinline__ void nbr(const R v[PPL][6], R vm[PPL][6], R vp[PPL][6], int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const R up = __shfl_up_sync(FULL, v[k][e], 1);
+      const R dn = __shfl_down_sync(FULL, v[k][e], 1);
+      R wm = R(0), wp = R(0);
+      if (k > 0) wm = __shfl_sync(FULL, v[k > 0 ? k - 1 : 0][e], 31);
+      if (k + 1 < PPL) wp = __shfl_sync(FULL, v[k + 1 < PPL ? k + 1 : 0][e], 0);
+      vm[k][e] = lane == 0 ? wm : up;
+      vp[k][e] = lane == 31 ? wp : dn;
     }
 }
 
-template <typename R>
-__device__ __forceinline__ void spring_params(const Scene<R>& S, int a, int o, R& k, R& L) {
-  if (o == 1) { k = S.k1; L = S.L1[a]; } else { k = S.k2; L = S.L2[a]; }
+template <typename R, int PPL>
+__device__ __forceinline__ void zero6(R v[PPL][6]) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) v[k][e] = R(0);
 }
 
-// d = (x0_b + dx_b) - (x0_a + dx_a), formed as (x0_b - x0_a) + (dx_b - dx_a)
-template <typename R>
-__device__ __forceinline__ void spring_vec(const WM<R>& m, int a, int b, R d[3]) {
-  for (int i = 0; i < 3; ++i)
-    d[i] = (m.x0[3 * b + i] - m.x0[3 * a + i]) + (m.dx[3 * b + i] - m.dx[3 * a + i]);
+// The seven springs touching pair p, sid 0..6:
+//   (2p-1,2p) (2p,2p+1) (2p+1,2p+2) stretch;  (2p-2,2p) (2p-1,2p+1) (2p,2p+2) (2p+1,2p+3) bend.
+// For node a and b of spring sid: where (0 previous pair, 1 own pair, 2 next pair) and h.
+__host__ __device__ constexpr int spr_wa(int s) { return (s == 0 || s == 3 || s == 4) ? 0 : 1; }
+__host__ __device__ constexpr int spr_ha(int s) { return (s == 0 || s == 2 || s == 4 || s == 6) ? 1 : 0; }
+__host__ __device__ constexpr int spr_wb(int s) { return (s == 2 || s == 5 || s == 6) ? 2 : 1; }
+__host__ __device__ constexpr int spr_hb(int s) { return (s == 1 || s == 4 || s == 6) ? 1 : 0; }
+
+__host__ __device__ constexpr int spr_node(int p, int where, int h) { return 2 * p + 2 * (where - 1) + h; }
+
+template <typename R, int PPL>
+__device__ __forceinline__ R pick(const R own[PPL][6], const R m[PPL][6], const R n[PPL][6],
+                                  int k, int where, int e) {
+  return where == 0 ? m[k][e] : (where == 1 ? own[k][e] : n[k][e]);
 }
 
-// Hessian P = dF/dq* of pair p into (T, Bk): w I + spring blocks + grasp d I; dummy node of an
-// odd-length chain gets the identity.  Optionally also the residual F of the pair's nodes.
-template <typename R>
-__device__ void assemble_pair(const Scene<R>& S, const WM<R>& m, int p, R* T, R* Bk, bool proj,
-                              bool want_F, R* Fout) {
-  for (int i = 0; i < 36; ++i) { T[i] = R(0); Bk[i] = R(0); }
-  const R* d = m.misc + M_D;
-  const R* c = m.misc + M_C;
-  const R* u = m.misc + M_U;
-  R Fl[6] = {0, 0, 0, 0, 0, 0};
+template <typename R, int PPL>
+__device__ __forceinline__ void spring_rest(const Lane<R, PPL>& L, int k, int sid, R& kk, R& Lr,
+                                            const Scene<R>& S) {
+  if (sid < 3) { kk = S.k1; Lr = L.Ls[k][sid]; } else { kk = S.k2; Lr = L.Lb[k][sid - 3]; }
+}
+
+template <typename R, int PPL>
+__device__ __forceinline__ void load_rest(const Scene<R>& S, Lane<R, PPL>& L, int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+    for (int i = 0; i < 3; ++i) {
+      const int a = 2 * p - 1 + i;
+      L.Ls[k][i] = (a >= 0 && a + 1 < S.nv) ? S.L1[a] : R(1);
+    }
+    for (int i = 0; i < 4; ++i) {
+      const int a = 2 * p - 2 + i;
+      L.Lb[k][i] = (a >= 0 && a + 2 < S.nv) ? S.L2[a] : R(1);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// stage-1 assembly: T (lower 6x6), coupling B to pair p - 1, residual F of pair p (slot k).
+// dxm/dxp: neighbours' dx.  grasp offsets and stiffness from misc.
+// ------------------------------------------------------------------------------------------
+template <typename R, int PPL>
+__device__ __forceinline__ void assemble1(const Scene<R>& S, const Lane<R, PPL>& L, const R dxm[PPL][6],
+                          const R dxp[PPL][6], const R* misc, int k, int p, bool proj,
+                          R T[36], R Bc[36], R F[6]) {
+#pragma unroll
+  for (int e = 0; e < 36; ++e) { T[e] = R(0); Bc[e] = R(0); }
+  const R* d = misc + M_D;
+  const R* c = misc + M_C;
+  const R* u = misc + M_U;
+#pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int j = 2 * p + h;
     if (j >= S.nv) {
-      for (int i = 0; i < 3; ++i) T[(3 * h + i) * 6 + 3 * h + i] = R(1);
+      for (int i = 0; i < 3; ++i) { T[(3 * h + i) * 7] = R(1); F[3 * h + i] = R(0); }
       continue;
     }
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
-      T[(3 * h + i) * 6 + 3 * h + i] += S.w;
-      Fl[3 * h + i] = S.w * m.dx[3 * j + i] - S.m * S.grav[i];
+      T[(3 * h + i) * 7] = S.w;
+      F[3 * h + i] = S.w * L.dx[k][3 * h + i] - S.m * S.grav[i];
     }
+#pragma unroll
     for (int gi = 0; gi < 2; ++gi)
       if (S.grasp[gi] == j) {
+#pragma unroll
         for (int i = 0; i < 3; ++i) {
-          T[(3 * h + i) * 6 + 3 * h + i] += d[gi];
-          // x*_a - g*_i = dx_a - (c_i + u_i)
-          Fl[3 * h + i] += d[gi] * (m.dx[3 * j + i] - (c[3 * gi + i] + u[3 * gi + i]));
+          T[(3 * h + i) * 7] += d[gi];
+          F[3 * h + i] += d[gi] * (L.dx[k][3 * h + i] - (c[3 * gi + i] + u[3 * gi + i]));
         }
       }
   }
-  springs_of_pair(S, p, [&](int a, int b, int o) {
-    R k, L;
-    spring_params(S, a, o, k, L);
+#pragma unroll
+  for (int sid = 0; sid < 7; ++sid) {
+    const int wa = spr_wa(sid), ha = spr_ha(sid), wb = spr_wb(sid), hb = spr_hb(sid);
+    const int a = spr_node(p, wa, ha), b = spr_node(p, wb, hb);
+    if (a < 0 || b >= S.nv) continue;
+    R kk, Lr;
+    spring_rest(L, k, sid, kk, Lr, S);
     R dv[3], f[3], H[9];
-    spring_vec(m, a, b, dv);
-    spring_eval(dv, k, L, proj, f, H);
-    const bool ina = (a >> 1) == p, inb = (b >> 1) == p;
-    const int ha = a - 2 * p, hb = b - 2 * p;
-    if (ina) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      dv[i] = (pick<R, PPL>(L.x0, L.xm, L.xp, k, wb, 3 * hb + i) - pick<R, PPL>(L.x0, L.xm, L.xp, k, wa, 3 * ha + i)) +
+              (pick<R, PPL>(L.dx, dxm, dxp, k, wb, 3 * hb + i) - pick<R, PPL>(L.dx, dxm, dxp, k, wa, 3 * ha + i));
+    spring_eval(dv, kk, Lr, proj, f, H);
+    if (wa == 1) {
+#pragma unroll
       for (int i = 0; i < 3; ++i) {
-        Fl[3 * ha + i] -= f[i];
-        for (int q = 0; q < 3; ++q) T[(3 * ha + i) * 6 + 3 * ha + q] += H[i * 3 + q];
+        F[3 * ha + i] -= f[i];
+#pragma unroll
+        for (int q = 0; q <= i; ++q) T[(3 * ha + i) * 6 + 3 * ha + q] += H[i * 3 + q];
       }
     }
-    if (inb) {
+    if (wb == 1) {
+#pragma unroll
       for (int i = 0; i < 3; ++i) {
-        Fl[3 * hb + i] += f[i];
-        for (int q = 0; q < 3; ++q) T[(3 * hb + i) * 6 + 3 * hb + q] += H[i * 3 + q];
+        F[3 * hb + i] += f[i];
+#pragma unroll
+        for (int q = 0; q <= i; ++q) T[(3 * hb + i) * 6 + 3 * hb + q] += H[i * 3 + q];
       }
     }
-    if (ina && inb) {
+    if (wa == 1 && wb == 1) {          // (2p, 2p+1): lower block row hb = 1, column ha = 0
+#pragma unroll
       for (int i = 0; i < 3; ++i)
-        for (int q = 0; q < 3; ++q) {
-          T[(3 * hb + i) * 6 + 3 * ha + q] -= H[i * 3 + q];
-          T[(3 * ha + i) * 6 + 3 * hb + q] -= H[i * 3 + q];
-        }
-    } else if (inb && (a >> 1) == p - 1) {
-      const int hl = a - 2 * (p - 1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) T[(3 * hb + i) * 6 + 3 * ha + q] -= H[i * 3 + q];
+    } else if (wb == 1 && wa == 0) {   // coupling with the previous pair
+#pragma unroll
       for (int i = 0; i < 3; ++i)
-        for (int q = 0; q < 3; ++q) Bk[(3 * hb + i) * 6 + 3 * hl + q] -= H[i * 3 + q];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Bc[(3 * hb + i) * 6 + 3 * ha + q] -= H[i * 3 + q];
     }
-  });
-  if (want_F) for (int i = 0; i < 6; ++i) Fout[i] = Fl[i];
+  }
 }
 
-// y = P v for the nodes of pair p (P the exact stage-1 Hessian at x0 + dx)
-template <typename R>
-__device__ void hess_vec_pair(const Scene<R>& S, const WM<R>& m, int p, const R* v, R* y,
-                              bool proj = false) {
-  const R* d = m.misc + M_D;
+// y = P v for pair p (P = exact or projected stage-1 Hessian at x0 + dx)
+template <typename R, int PPL>
+__device__ __forceinline__ void hessvec(const Scene<R>& S, const Lane<R, PPL>& L, const R dxm[PPL][6],
+                        const R dxp[PPL][6], const R v[PPL][6], const R vm[PPL][6],
+                        const R vp[PPL][6], const R* misc, int k, int p, bool proj, R y[6]) {
+  const R* d = misc + M_D;
+#pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int j = 2 * p + h;
-    if (j >= S.nv) continue;
-    for (int i = 0; i < 3; ++i) y[3 * j + i] = S.w * v[3 * j + i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[3 * h + i] = j < S.nv ? S.w * v[k][3 * h + i] : R(0);
+#pragma unroll
     for (int gi = 0; gi < 2; ++gi)
       if (S.grasp[gi] == j)
-        for (int i = 0; i < 3; ++i) y[3 * j + i] += d[gi] * v[3 * j + i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) y[3 * h + i] += d[gi] * v[k][3 * h + i];
   }
-  springs_of_pair(S, p, [&](int a, int b, int o) {
-    R k, L;
-    spring_params(S, a, o, k, L);
-    R dv[3], f[3], H[9];
-    spring_vec(m, a, b, dv);
-    spring_eval(dv, k, L, proj, f, H);
-    R dd[3] = {v[3 * b] - v[3 * a], v[3 * b + 1] - v[3 * a + 1], v[3 * b + 2] - v[3 * a + 2]};
-    R hv[3];
-    for (int i = 0; i < 3; ++i) hv[i] = H[i * 3] * dd[0] + H[i * 3 + 1] * dd[1] + H[i * 3 + 2] * dd[2];
-    if ((b >> 1) == p) for (int i = 0; i < 3; ++i) y[3 * b + i] += hv[i];
-    if ((a >> 1) == p) for (int i = 0; i < 3; ++i) y[3 * a + i] -= hv[i];
-  });
+#pragma unroll
+  for (int sid = 0; sid < 7; ++sid) {
+    const int wa = spr_wa(sid), ha = spr_ha(sid), wb = spr_wb(sid), hb = spr_hb(sid);
+    const int a = spr_node(p, wa, ha), b = spr_node(p, wb, hb);
+    if (a < 0 || b >= S.nv) continue;
+    R kk, Lr;
+    spring_rest(L, k, sid, kk, Lr, S);
+    R dv[3], f[3], H[9], dd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dv[i] = (pick<R, PPL>(L.x0, L.xm, L.xp, k, wb, 3 * hb + i) - pick<R, PPL>(L.x0, L.xm, L.xp, k, wa, 3 * ha + i)) +
+              (pick<R, PPL>(L.dx, dxm, dxp, k, wb, 3 * hb + i) - pick<R, PPL>(L.dx, dxm, dxp, k, wa, 3 * ha + i));
+      dd[i] = pick<R, PPL>(v, vm, vp, k, wb, 3 * hb + i) - pick<R, PPL>(v, vm, vp, k, wa, 3 * ha + i);
+    }
+    spring_eval(dv, kk, Lr, proj, f, H);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const R hv = H[i * 3] * dd[0] + H[i * 3 + 1] * dd[1] + H[i * 3 + 2] * dd[2];
+      if (wb == 1) y[3 * hb + i] += hv;
+      if (wa == 1) y[3 * ha + i] -= hv;
+    }
+  }
 }
 
-// copy node vector <-> pair-ordered right-hand side (dummy node rows set to 0)
 template <typename R>
-__device__ __forceinline__ void to_rhs(const Scene<R>& S, const R* v, R* r, int lane, R sign) {
-  for (int p = lane; p < S.npair; p += 32)
-    for (int t = 0; t < 6; ++t) {
-      const int j = 2 * p + t / 3;
-      r[p * 6 + t] = j < S.nv ? sign * v[6 * p + t] : R(0);
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ void from_rhs(const Scene<R>& S, const R* r, R* v, int lane) {
-  for (int p = lane; p < S.npair; p += 32)
-    for (int t = 0; t < 6; ++t) {
-      const int j = 2 * p + t / 3;
-      if (j < S.nv) v[6 * p + t] = r[p * 6 + t];
-    }
+__device__ __forceinline__ void put_rows(WS<R>& w, int p, const R T[36], const R Bc[36]) {
+  st_lower(w.T, w.NP, p, T);
+  st36(w.B, w.NP, p, Bc);
 }
 
 // ------------------------------------------------------------------------------------------
 // stage 1
 // ------------------------------------------------------------------------------------------
-
-// Psi(x0+dx+alpha p) - Psi(x0+dx), lane's share (nodes of its pairs; springs a -> a + o)
-template <typename R>
-__device__ R psi_diff_lane(const Scene<R>& S, const WM<R>& m, R alpha, int lane) {
+template <typename R, int PPL>
+__device__ __forceinline__ R psi_diff(const Scene<R>& S, const Lane<R, PPL>& L, const R dxp[PPL][6],
+                      const R pvp[PPL][6], const R* misc, R alpha, int lane) {
+  const R* d = misc + M_D;
+  const R* c = misc + M_C;
+  const R* u = misc + M_U;
   R val = R(0);
-  const R* d = m.misc + M_D;
-  const R* c = m.misc + M_C;
-  const R* u = m.misc + M_U;
-  for (int p = lane; p < S.npair; p += 32)
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int j = 2 * p + h;
       if (j >= S.nv) continue;
+#pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const R D = alpha * m.p[3 * j + i];
-        val += R(0.5) * S.w * D * (R(2) * m.dx[3 * j + i] + D) - S.m * S.grav[i] * D;
+        const R D = alpha * L.pv[k][3 * h + i];
+        val += R(0.5) * S.w * D * (R(2) * L.dx[k][3 * h + i] + D) - S.m * S.grav[i] * D;
       }
+#pragma unroll
       for (int gi = 0; gi < 2; ++gi)
         if (S.grasp[gi] == j)
+#pragma unroll
           for (int i = 0; i < 3; ++i) {
-            const R D = alpha * m.p[3 * j + i];
-            // g* - X_a = (c + u) - dx_a
-            val += R(0.5) * d[gi] * D * (D - R(2) * ((c[3 * gi + i] + u[3 * gi + i]) - m.dx[3 * j + i]));
+            const R D = alpha * L.pv[k][3 * h + i];
+            val += R(0.5) * d[gi] * D * (D - R(2) * ((c[3 * gi + i] + u[3 * gi + i]) - L.dx[k][3 * h + i]));
           }
-      for (int o = 1; o <= 2; ++o) {
-        const int a = j, b = j + o;
-        if (b >= S.nv) continue;
-        R k, L;
-        spring_params(S, a, o, k, L);
-        R dX[3], dD[3], dY[3];
-        spring_vec(m, a, b, dX);
-        for (int i = 0; i < 3; ++i) {
-          dD[i] = alpha * (m.p[3 * b + i] - m.p[3 * a + i]);
-          dY[i] = dX[i] + dD[i];
-        }
-        const R lX = sqrt(dot3(dX, dX)), lY = sqrt(dot3(dY, dY));
-        const R dl = (dD[0] * (R(2) * dX[0] + dD[0]) + dD[1] * (R(2) * dX[1] + dD[1]) +
-                      dD[2] * (R(2) * dX[2] + dD[2])) / (lY + lX);
-        val += R(0.5) * k * dl * (lY + lX - R(2) * L);
-      }
     }
+    // springs whose first node is in pair p: sid 1, 2, 5, 6
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int sid = t < 2 ? 1 + t : 3 + t;
+      const int wa = spr_wa(sid), ha = spr_ha(sid), wb = spr_wb(sid), hb = spr_hb(sid);
+      const int a = spr_node(p, wa, ha), b = spr_node(p, wb, hb);
+      if (a < 0 || b >= S.nv) continue;
+      R kk, Lr;
+      spring_rest(L, k, sid, kk, Lr, S);
+      R dX[3], dD[3], dY[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const R xb = wb == 1 ? L.x0[k][3 * hb + i] : L.xp[k][3 * hb + i];
+        const R db = wb == 1 ? L.dx[k][3 * hb + i] : dxp[k][3 * hb + i];
+        const R pb = wb == 1 ? L.pv[k][3 * hb + i] : pvp[k][3 * hb + i];
+        dX[i] = (xb - L.x0[k][3 * ha + i]) + (db - L.dx[k][3 * ha + i]);
+        dD[i] = alpha * (pb - L.pv[k][3 * ha + i]);
+        dY[i] = dX[i] + dD[i];
+      }
+      const R lX = sqrt(dot3(dX, dX)), lY = sqrt(dot3(dY, dY));
+      const R dl = (dD[0] * (R(2) * dX[0] + dD[0]) + dD[1] * (R(2) * dX[1] + dD[1]) +
+                    dD[2] * (R(2) * dX[2] + dD[2])) / (lY + lX);
+      val += R(0.5) * kk * dl * (lY + lX - R(2) * Lr);
+    }
+  }
   return val;
 }
 
-// Damped Newton for stage 1; dx must be zero on entry (start at q).  Leaves the factorisation
-// of the Hessian at the last iterate in (T, B, V).
-template <typename R>
-__device__ int stage1_newton(const Scene<R>& S, WM<R>& m, int lane, int* iters) {
+// registers -> CR right-hand side (zero rows for nodes past the chain)
+template <typename R, int PPL>
+__device__ __forceinline__ void put_rhs(const Scene<R>& S, WS<R>& w, const R v[PPL][6], R sign, int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+    if (p >= S.npair) continue;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) w.r[e * w.NP + p] = (2 * p + e / 3 < S.nv) ? sign * v[k][e] : R(0);
+  }
+}
+
+template <typename R, int PPL>
+__device__ __forceinline__ void get_rhs(const Scene<R>& S, const WS<R>& w, R v[PPL][6], int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) v[k][e] = (p < S.npair && 2 * p + e / 3 < S.nv) ? w.r[e * w.NP + p] : R(0);
+  }
+}
+
+// assemble P = dF/dq* at x0 + dx into the CR arrays (optionally keeping the residual in L.F)
+template <typename R, int PPL>
+__device__ __forceinline__ void assemble_P(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, const R dxm[PPL][6],
+                           const R dxp[PPL][6], bool proj, bool keepF, int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+    if (p >= S.npair) continue;
+    R T[36], Bc[36], F[6];
+    assemble1(S, L, dxm, dxp, w.misc, k, p, proj, T, Bc, F);
+    put_rows(w, p, T, Bc);
+    if (keepF)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) L.F[k][e] = F[e];
+  }
+}
+
+// Damped Newton for stage 1 from dx = 0.  On exit the factorisation of the Hessian at the last
+// iterate is in (T, B, V).
+template <typename R, int PPL>
+__device__ __forceinline__ int stage1_newton(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, int lane, int* iters,
+                                             bool warm) {
+  if (!warm) zero6<R, PPL>(L.dx);
+  R dxm[PPL][6], dxp[PPL][6];
   for (int it = 0; it < S.newton_max; ++it) {
-    R Fl[6];
-    for (int p = lane; p < S.npair; p += 32) {
-      assemble_pair(S, m, p, m.T + p * 36, m.B + p * 36, false, true, Fl);
-      for (int t = 0; t < 6; ++t) {
-        const int j = 2 * p + t / 3;
-        if (j < S.nv) m.F[6 * p + t] = Fl[t];
-        m.r[p * 6 + t] = j < S.nv ? -Fl[t] : R(0);
-      }
-    }
-    __syncwarp();
-    bool ok = cr_factor(m.T, m.B, m.V, S.npair, lane);
-    if (!ok) {
-      for (int p = lane; p < S.npair; p += 32)
-        assemble_pair(S, m, p, m.T + p * 36, m.B + p * 36, true, false, (R*)nullptr);
+    nbr<R, PPL>(L.dx, dxm, dxp, lane);
+    bool ok = false;
+    // exact Hessian; if it is not positive definite, the projected one (same call site)
+    for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+      assemble_P(S, L, w, dxm, dxp, attempt == 1, attempt == 0, lane);
+      if (attempt == 0) put_rhs<R, PPL>(S, w, L.F, R(-1), lane);
       __syncwarp();
-      ok = cr_factor(m.T, m.B, m.V, S.npair, lane);
-      if (!ok) { *iters = it + 1; return ST_NOTPD; }
+      ok = cr_factor(w.T, w.B, w.V, S.npair, w.NP, lane);
     }
-    cr_solve(m.T, m.B, m.V, m.r, S.npair, lane);
+    if (!ok) { *iters = it + 1; return ST_NOTPD; }
+    cr_solve(w.T, w.B, w.V, w.r, S.npair, w.NP, lane);
+    get_rhs<R, PPL>(S, w, L.pv, lane);
     R pm = R(0), sl = R(0);
     bool bad = false;
-    for (int p = lane; p < S.npair; p += 32)
-      for (int t = 0; t < 6; ++t) {
-        const int j = 2 * p + t / 3;
-        if (j >= S.nv) continue;
-        const R pv = m.r[p * 6 + t];
-        m.p[6 * p + t] = pv;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const R pv = L.pv[k][e];
         bad = bad || !(fabs(pv) <= R(1e30));
         pm = fmax(pm, fabs(pv));
-        sl += m.F[6 * p + t] * pv;
+        sl += L.F[k][e] * pv;
       }
     pm = wmax(pm);
     sl = wsum(sl);
-    bad = __any_sync(FULL, bad);
-    __syncwarp();
-    if (bad) { *iters = it + 1; return ST_NONFINITE; }
+    if (__any_sync(FULL, bad)) { *iters = it + 1; return ST_NONFINITE; }
     if (pm <= S.ntol) {
-      for (int p = lane; p < S.npair; p += 32)
-        for (int t = 0; t < 6; ++t)
-          if (2 * p + t / 3 < S.nv) m.dx[6 * p + t] += m.p[6 * p + t];
-      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < PPL; ++k)
+#pragma unroll
+        for (int e = 0; e < 6; ++e) L.dx[k][e] += L.pv[k][e];
       *iters = it + 1;
       return 0;
     }
+    R pvm[PPL][6], pvp[PPL][6];
+    nbr<R, PPL>(L.pv, pvm, pvp, lane);
     R alpha = R(1);
     for (int ls = 0; ls < 40; ++ls) {
-      const R dv = wsum(psi_diff_lane(S, m, alpha, lane));
+      const R dv = wsum(psi_diff(S, L, dxp, pvp, w.misc, alpha, lane));
       if (dv <= R(1e-4) * alpha * sl) break;
       alpha *= R(0.5);
     }
-    for (int p = lane; p < S.npair; p += 32)
-      for (int t = 0; t < 6; ++t)
-        if (2 * p + t / 3 < S.nv) m.dx[6 * p + t] += alpha * m.p[6 * p + t];
-    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < PPL; ++k)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) L.dx[k][e] += alpha * L.pv[k][e];
   }
   *iters = S.newton_max;
   return ST_NEWTON;
@@ -317,255 +447,309 @@ __device__ int stage1_newton(const Scene<R>& S, WM<R>& m, int lane, int* iters) 
 // stage 2
 // ------------------------------------------------------------------------------------------
 
-template <typename R>
-__device__ __forceinline__ void node_pos(const WM<R>& m, int j, R X[3]) {
-  for (int i = 0; i < 3; ++i) X[i] = m.x0[3 * j + i] + m.dx[3 * j + i];
-}
-
-// phi, n of every (node, obstacle) pair at x* = x0 + dx; returns min phi over the warp
-template <typename R>
-__device__ R contact_geometry(const Scene<R>& S, WM<R>& m, int lane) {
+// phi, n of the lane's (node, obstacle) pairs at x* = x0 + dx; returns the warp's min phi
+template <typename R, int PPL>
+__device__ __forceinline__ R contact_geometry(const Scene<R>& S, const Lane<R, PPL>& L, WS<R>& w, int lane) {
   R pmin = R(1e30);
-  for (int p = lane; p < S.npair; p += 32)
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int j = 2 * p + h;
-      if (j >= S.nv) continue;
-      R X[3];
-      node_pos(m, j, X);
+      if (2 * p + h >= S.nv) continue;
+      R X[3] = {L.x0[k][3 * h] + L.dx[k][3 * h], L.x0[k][3 * h + 1] + L.dx[k][3 * h + 1],
+                L.x0[k][3 * h + 2] + L.dx[k][3 * h + 2]};
       for (int o = 0; o < S.nobs; ++o) {
         R ph, n[3];
         obstacle_eval(S.ob_type[o], S.ob[o], X, S.rad, ph, n, (R*)nullptr);
-        const int q = j * S.nobs + o;
-        m.phi[q] = ph;
-        for (int i = 0; i < 3; ++i) m.nrm[3 * q + i] = n[i];
+        w.phi[cs1(o, h, p, w.NP)] = ph;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) w.nrm[cv(o, h, i, p, w.NP)] = n[i];
         pmin = fmin(pmin, ph);
       }
     }
-  pmin = -wmax(-pmin);
-  __syncwarp();
-  return pmin;
+  }
+  return -wmax(-pmin);
 }
 
-// diagonal 3x3 block P_jj of the stage-1 Hessian at x*
 template <typename R>
-__device__ void diag_block(const Scene<R>& S, const WM<R>& m, int j, R D[9]) {
-  const R* d = m.misc + M_D;
-  for (int i = 0; i < 9; ++i) D[i] = R(0);
-  for (int i = 0; i < 3; ++i) D[i * 4] = S.w;
-  for (int gi = 0; gi < 2; ++gi)
-    if (S.grasp[gi] == j) for (int i = 0; i < 3; ++i) D[i * 4] += d[gi];
-  for (int o = 1; o <= 2; ++o)
-    for (int a = j - o; a <= j; a += o) {
-      const int b = a + o;
-      if (a < 0 || b >= S.nv) continue;
-      R k, L, dv[3], f[3], H[9];
-      spring_params(S, a, o, k, L);
-      spring_vec(m, a, b, dv);
-      spring_eval(dv, k, L, false, f, H);
-      for (int i = 0; i < 9; ++i) D[i] += H[i];
-    }
+__device__ __forceinline__ void pair_frame(const WS<R>& w, int o, int h, int p, R mu, R A[9]) {
+  R n[3] = {w.nrm[cv(o, h, 0, p, w.NP)], w.nrm[cv(o, h, 1, p, w.NP)], w.nrm[cv(o, h, 2, p, w.NP)]};
+  cone_frame(n, mu, A);
 }
 
-// Stage 2: primal-dual interior point with Nesterov-Todd scaling (Vandenberghe, "The CVXOPT
-// linear and quadratic cone program solvers", 2010) for
-//     min 1/2 D^T P D   s.t.  s_i = A_i D_j + phi_i e1 in Q,   z_i in Q (forces lam_i = A_i^T z_i),
-// with the centering s_i o z_i = kappa e (the relaxed complementarity of the smoothed model).
-// kfinal < 0: fixed target kappa (smooth model); else the target falls each iteration to
-// max(kfinal, min(kappa, 0.1 <s,z>/m)) and the solve ends at the central point of kfinal.
-// On exit (T, B, V) hold the factorisation of the last Newton matrix H2 = P + sum A^T W^-2 A.
+// per pair: A, M = W^-2, r_z = s - A D - phi e1, W d_s with d_s = lam^{-1} o (target e - lam o lam)
 template <typename R>
-__device__ __forceinline__ void pair_frame(const Scene<R>& S, const WM<R>& m, int q, R A[9]) {
-  R n[3] = {m.nrm[3 * q], m.nrm[3 * q + 1], m.nrm[3 * q + 2]};
-  cone_frame(n, S.mu, A);
-}
-
-// per pair: residual r_z = s - A D_j - phi e1, NT scaling, d_s = lam^{-1} o (target e - lam o lam)
-template <typename R>
-__device__ __forceinline__ void pair_newton_terms(const Scene<R>& S, const WM<R>& m, int j, int q,
-                                                  R target, R A[9], R W[9], R M[9], R rz[3],
-                                                  R Wds[3]) {
-  pair_frame(S, m, q, A);
-  const R* s = m.sig + 3 * q;
-  const R* z = m.zz + 3 * q;
+__device__ __forceinline__ void pair_terms(const Scene<R>& S, const WS<R>& w, int o, int h, int p,
+                                           const R D[3], R target, R A[9], R M[9], R rz[3],
+                                           R Wds[3]) {
+  pair_frame(w, o, h, p, S.mu, A);
+  R s[3], z[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { s[c] = w.s[cv(o, h, c, p, w.NP)]; z[c] = w.z[cv(o, h, c, p, w.NP)]; }
+  const R ph = w.phi[cs1(o, h, p, w.NP)];
+#pragma unroll
   for (int a = 0; a < 3; ++a)
-    rz[a] = s[a] - (A[a * 3] * m.Dl[3 * j] + A[a * 3 + 1] * m.Dl[3 * j + 1] +
-                    A[a * 3 + 2] * m.Dl[3 * j + 2]) - (a == 0 ? m.phi[q] : R(0));
-  R Wi[9], lam[3];
+    rz[a] = s[a] - (A[a * 3] * D[0] + A[a * 3 + 1] * D[1] + A[a * 3 + 2] * D[2]) - (a == 0 ? ph : R(0));
+  R W[9], Wi[9], lam[3];
   nt_scaling(s, z, W, Wi, lam);
-  R ll[3] = {lam[0] * lam[0] + lam[1] * lam[1] + lam[2] * lam[2], R(2) * lam[0] * lam[1],
-             R(2) * lam[0] * lam[2]};
-  R rhs[3] = {target - ll[0], -ll[1], -ll[2]};
+  R rhs[3] = {target - (lam[0] * lam[0] + lam[1] * lam[1] + lam[2] * lam[2]), R(-2) * lam[0] * lam[1],
+              R(-2) * lam[0] * lam[2]};
   R ds[3];
   jordan_solve(lam, rhs, ds);
+#pragma unroll
   for (int a = 0; a < 3; ++a) Wds[a] = W[a * 3] * ds[0] + W[a * 3 + 1] * ds[1] + W[a * 3 + 2] * ds[2];
+#pragma unroll
   for (int a = 0; a < 3; ++a)
+#pragma unroll
     for (int b = 0; b < 3; ++b)
       M[a * 3 + b] = Wi[a * 3] * Wi[b] + Wi[a * 3 + 1] * Wi[3 + b] + Wi[a * 3 + 2] * Wi[6 + b];
 }
 
-// step of one pair from dDelta_j (in m.p): dz = M(-A dD + W d_s + r_z), ds = A dD - r_z
+// step of one pair from dD (the node's Delta step) with the terms stored by the assembly:
+// ds = A dD - r_z, dz = M (g - A dD), g = r_z + W d_s
 template <typename R>
-__device__ __forceinline__ void pair_step(const Scene<R>& S, const WM<R>& m, int j, int q, R target,
-                                          R dsv[3], R dz[3]) {
-  R A[9], W[9], M[9], rz[3], Wds[3];
-  pair_newton_terms(S, m, j, q, target, A, W, M, rz, Wds);
-  R ADd[3], g[3];
+__device__ __forceinline__ void pair_step(const Scene<R>& S, const WS<R>& w, int o, int h, int p,
+                                          const R dD[3], R dsv[3], R dz[3]) {
+  R A[9];
+  pair_frame(w, o, h, p, S.mu, A);
+  const int NP = w.NP;
+  R m6[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) m6[c] = w.pm[cm6(o, h, c, p, NP)];
+  const R M[9] = {m6[0], m6[1], m6[2], m6[1], m6[3], m6[4], m6[2], m6[4], m6[5]};
+  R g[3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    ADd[a] = A[a * 3] * m.p[3 * j] + A[a * 3 + 1] * m.p[3 * j + 1] + A[a * 3 + 2] * m.p[3 * j + 2];
-    dsv[a] = ADd[a] - rz[a];
-    g[a] = -ADd[a] + Wds[a] + rz[a];
+    const R ADd = A[a * 3] * dD[0] + A[a * 3 + 1] * dD[1] + A[a * 3 + 2] * dD[2];
+    dsv[a] = ADd - w.prz[cv(o, h, a, p, NP)];
+    g[a] = w.pg[cv(o, h, a, p, NP)] - ADd;
   }
+#pragma unroll
   for (int a = 0; a < 3; ++a) dz[a] = M[a * 3] * g[0] + M[a * 3 + 1] * g[1] + M[a * 3 + 2] * g[2];
 }
 
-template <typename R>
-__device__ int stage2_ipm(const Scene<R>& S, WM<R>& m, R kappa, R kfinal, int lane, int* iters) {
+// diagonal 3x3 block of P for node (k, h): w I + grasp + incident spring Hessians
+template <typename R, int PPL>
+__device__ __forceinline__ void diag_block(const Scene<R>& S, const Lane<R, PPL>& L, const R dxm[PPL][6],
+                           const R dxp[PPL][6], const R* misc, int k, int p, int h, R D[9]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) D[i] = R(0);
+  const int j = 2 * p + h;
+  for (int i = 0; i < 3; ++i) D[i * 4] = S.w;
+  for (int gi = 0; gi < 2; ++gi)
+    if (S.grasp[gi] == j) for (int i = 0; i < 3; ++i) D[i * 4] += misc[M_D + gi];
+#pragma unroll
+  for (int sid = 0; sid < 7; ++sid) {
+    const int wa = spr_wa(sid), ha = spr_ha(sid), wb = spr_wb(sid), hb = spr_hb(sid);
+    const int a = spr_node(p, wa, ha), b = spr_node(p, wb, hb);
+    if (a < 0 || b >= S.nv) continue;
+    if (!((wa == 1 && ha == h) || (wb == 1 && hb == h))) continue;
+    R kk, Lr;
+    spring_rest(L, k, sid, kk, Lr, S);
+    R dv[3], f[3], H[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      dv[i] = (pick<R, PPL>(L.x0, L.xm, L.xp, k, wb, 3 * hb + i) - pick<R, PPL>(L.x0, L.xm, L.xp, k, wa, 3 * ha + i)) +
+              (pick<R, PPL>(L.dx, dxm, dxp, k, wb, 3 * hb + i) - pick<R, PPL>(L.dx, dxm, dxp, k, wa, 3 * ha + i));
+    spring_eval(dv, kk, Lr, false, f, H);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) D[i] += H[i];
+  }
+}
+
+// Primal-dual interior point with Nesterov-Todd scaling (Vandenberghe, "The CVXOPT linear and
+// quadratic cone program solvers", 2010) for
+//   min 1/2 D^T P D  s.t.  s_i = A_i D_j + phi_i e1 in Q,  z_i in Q  (forces lam_i = A_i^T z_i),
+// centering s_i o z_i = kappa e.  kfinal < 0: fixed target kappa (smooth model); else the target
+// falls each iteration to max(kfinal, min(kappa, 0.1 <s,z>/m)) and the solve ends at the central
+// point of kfinal.  On exit (T, B, V) hold the factorisation of the last H2 = P + sum A^T W^-2 A.
+template <typename R, int PPL>
+__device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, R kappa, R kfinal,
+                          int lane, int* iters) {
   const int nobs = S.nobs;
   const R mm = R(S.nv * nobs);
-  // interior start: per-node closed form along each penetrating normal, then s, z = kappa s^-1
-  for (int p = lane; p < S.npair; p += 32)
+  const int NP = w.NP;
+  R dxm[PPL][6], dxp[PPL][6];
+  nbr<R, PPL>(L.dx, dxm, dxp, lane);
+  // interior start
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int j = 2 * p + h;
-      if (j >= S.nv) continue;
+      if (2 * p + h >= S.nv) { for (int i = 0; i < 3; ++i) L.Dl[k][3 * h + i] = R(0); continue; }
       R D[9];
-      diag_block(S, m, j, D);
+      diag_block(S, L, dxm, dxp, w.misc, k, p, h, D);
       R Dj[3] = {0, 0, 0};
       for (int o = 0; o < nobs; ++o) {
-        const int q = j * nobs + o;
-        const R ph = m.phi[q];
+        const R ph = w.phi[cs1(o, h, p, NP)];
         if (ph < R(0)) {
-          const R* n = m.nrm + 3 * q;
+          R n[3] = {w.nrm[cv(o, h, 0, p, NP)], w.nrm[cv(o, h, 1, p, NP)], w.nrm[cv(o, h, 2, p, NP)]};
           R a = R(0);
-          for (int i = 0; i < 3; ++i)
-            a += n[i] * (D[i * 3] * n[0] + D[i * 3 + 1] * n[1] + D[i * 3 + 2] * n[2]);
+          for (int i = 0; i < 3; ++i) a += n[i] * (D[i * 3] * n[0] + D[i * 3 + 1] * n[1] + D[i * 3 + 2] * n[2]);
           const R push = R(0.5) * (-ph + sqrt(ph * ph + R(4) * kappa / a));
           for (int i = 0; i < 3; ++i) Dj[i] += push * n[i];
         }
       }
-      for (int i = 0; i < 3; ++i) m.Dl[3 * j + i] = Dj[i];
+      for (int i = 0; i < 3; ++i) L.Dl[k][3 * h + i] = Dj[i];
       for (int o = 0; o < nobs; ++o) {
-        const int q = j * nobs + o;
         R A[9];
-        pair_frame(S, m, q, A);
+        pair_frame(w, o, h, p, S.mu, A);
+        const R ph = w.phi[cs1(o, h, p, NP)];
         R sv[3];
         for (int a = 0; a < 3; ++a)
-          sv[a] = A[a * 3] * Dj[0] + A[a * 3 + 1] * Dj[1] + A[a * 3 + 2] * Dj[2] + (a == 0 ? m.phi[q] : R(0));
+          sv[a] = A[a * 3] * Dj[0] + A[a * 3 + 1] * Dj[1] + A[a * 3 + 2] * Dj[2] + (a == 0 ? ph : R(0));
         const bool ok = sv[0] > R(0) && soc_det(sv) > R(0.25) * sv[0] * sv[0];
-        if (!ok) { sv[0] = m.phi[q] > S.sig0 ? m.phi[q] : S.sig0; sv[1] = sv[2] = R(0); }
+        if (!ok) { sv[0] = ph > S.sig0 ? ph : S.sig0; sv[1] = sv[2] = R(0); }
         const R dt = soc_det(sv);
-        for (int a = 0; a < 3; ++a) m.sig[3 * q + a] = sv[a];
-        m.zz[3 * q] = kappa * sv[0] / dt;
-        m.zz[3 * q + 1] = -kappa * sv[1] / dt;
-        m.zz[3 * q + 2] = -kappa * sv[2] / dt;
+        for (int a = 0; a < 3; ++a) w.s[cv(o, h, a, p, NP)] = sv[a];
+        w.z[cv(o, h, 0, p, NP)] = kappa * sv[0] / dt;
+        w.z[cv(o, h, 1, p, NP)] = -kappa * sv[1] / dt;
+        w.z[cv(o, h, 2, p, NP)] = -kappa * sv[2] / dt;
       }
     }
-  __syncwarp();
+  }
   int stalls = 0;
   bool proj = false;
   for (int it = 0; it < S.ipm_max; ++it) {
     R target = kappa;
     if (kfinal >= R(0)) {
       R gap = R(0);
-      for (int p = lane; p < S.npair; p += 32)
+#pragma unroll
+      for (int k = 0; k < PPL; ++k) {
+        const int p = lane + 32 * k;
+#pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int j = 2 * p + h;
-          if (j >= S.nv) continue;
-          for (int o = 0; o < nobs; ++o) gap += dot3(m.sig + 3 * (j * nobs + o), m.zz + 3 * (j * nobs + o));
+          if (2 * p + h >= S.nv) continue;
+          for (int o = 0; o < nobs; ++o)
+            for (int c = 0; c < 3; ++c) gap += w.s[cv(o, h, c, p, NP)] * w.z[cv(o, h, c, p, NP)];
         }
+      }
       gap = wsum(gap);
       target = fmax(kfinal, fmin(kappa, R(0.1) * gap / mm));
     }
     const bool final_target = kfinal < R(0) || target == kfinal;
-    // assemble H2 and the right-hand side; if H2 is not positive definite with the exact P
-    // (stage 1 ended where d^2E is indefinite), P becomes the projected spring Hessian for the
-    // rest of this solve
+    R Dlm[PPL][6], Dlp[PPL][6];
+    nbr<R, PPL>(L.Dl, Dlm, Dlp, lane);
+    // assemble H2 and the right-hand side -P D + sum A^T (z + M g), g = r_z + W d_s.  If H2 is
+    // not positive definite with the exact P (stage 1 ended where d^2E is indefinite), P becomes
+    // the projected spring Hessian for the rest of this solve.
     for (int attempt = 0; attempt < 2; ++attempt) {
-    for (int p = lane; p < S.npair; p += 32) hess_vec_pair(S, m, p, m.Dl, m.v3, proj);
-    __syncwarp();
-    for (int p = lane; p < S.npair; p += 32) {
-      R* T = m.T + p * 36;
-      assemble_pair(S, m, p, T, m.B + p * 36, proj, false, (R*)nullptr);
-      for (int h = 0; h < 2; ++h) {
-        const int j = 2 * p + h;
-        if (j >= S.nv) { for (int i = 0; i < 3; ++i) m.r[p * 6 + 3 * h + i] = R(0); continue; }
-        R rhs[3] = {-m.v3[3 * j], -m.v3[3 * j + 1], -m.v3[3 * j + 2]};
-        for (int o = 0; o < nobs; ++o) {
-          const int q = j * nobs + o;
-          R A[9], W[9], M[9], rz[3], Wds[3];
-          pair_newton_terms(S, m, j, q, target, A, W, M, rz, Wds);
-          const R* z = m.zz + 3 * q;
-          R g[3], Mg[3];
-          for (int a = 0; a < 3; ++a) g[a] = rz[a] + Wds[a];
-          for (int a = 0; a < 3; ++a) Mg[a] = M[a * 3] * g[0] + M[a * 3 + 1] * g[1] + M[a * 3 + 2] * g[2];
-          // MA = M A ; T += A^T M A ; rhs += A^T z (force) + A^T M g
-          R MA[9];
-          for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 3; ++c)
-              MA[a * 3 + c] = M[a * 3] * A[c] + M[a * 3 + 1] * A[3 + c] + M[a * 3 + 2] * A[6 + c];
-          for (int i = 0; i < 3; ++i) {
-            rhs[i] += A[i] * (z[0] + Mg[0]) + A[3 + i] * (z[1] + Mg[1]) + A[6 + i] * (z[2] + Mg[2]);
-            for (int c = 0; c < 3; ++c)
-              T[(3 * h + i) * 6 + 3 * h + c] += A[i] * MA[c] + A[3 + i] * MA[3 + c] + A[6 + i] * MA[6 + c];
+#pragma unroll
+      for (int k = 0; k < PPL; ++k) {
+        const int p = lane + 32 * k;
+        if (p >= S.npair) continue;
+        R T[36], Bc[36], F[6], PD[6];
+        assemble1(S, L, dxm, dxp, w.misc, k, p, proj, T, Bc, F);
+        hessvec(S, L, dxm, dxp, L.Dl, Dlm, Dlp, w.misc, k, p, proj, PD);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          R rhs[3] = {-PD[3 * h], -PD[3 * h + 1], -PD[3 * h + 2]};
+          if (2 * p + h < S.nv) {
+            const R D[3] = {L.Dl[k][3 * h], L.Dl[k][3 * h + 1], L.Dl[k][3 * h + 2]};
+            for (int o = 0; o < nobs; ++o) {
+              R A[9], M[9], rz[3], Wds[3];
+              pair_terms(S, w, o, h, p, D, target, A, M, rz, Wds);
+              const R g0 = rz[0] + Wds[0], g1 = rz[1] + Wds[1], g2 = rz[2] + Wds[2];
+              w.pm[cm6(o, h, 0, p, NP)] = M[0]; w.pm[cm6(o, h, 1, p, NP)] = M[1];
+              w.pm[cm6(o, h, 2, p, NP)] = M[2]; w.pm[cm6(o, h, 3, p, NP)] = M[4];
+              w.pm[cm6(o, h, 4, p, NP)] = M[5]; w.pm[cm6(o, h, 5, p, NP)] = M[8];
+              w.pg[cv(o, h, 0, p, NP)] = g0; w.pg[cv(o, h, 1, p, NP)] = g1; w.pg[cv(o, h, 2, p, NP)] = g2;
+              w.prz[cv(o, h, 0, p, NP)] = rz[0]; w.prz[cv(o, h, 1, p, NP)] = rz[1];
+              w.prz[cv(o, h, 2, p, NP)] = rz[2];
+              R zg[3];
+#pragma unroll
+              for (int a = 0; a < 3; ++a)
+                zg[a] = w.z[cv(o, h, a, p, NP)] + M[a * 3] * g0 + M[a * 3 + 1] * g1 + M[a * 3 + 2] * g2;
+              R MA[9];
+#pragma unroll
+              for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                  MA[a * 3 + c] = M[a * 3] * A[c] + M[a * 3 + 1] * A[3 + c] + M[a * 3 + 2] * A[6 + c];
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                rhs[i] += A[i] * zg[0] + A[3 + i] * zg[1] + A[6 + i] * zg[2];
+#pragma unroll
+                for (int c = 0; c <= i; ++c)
+                  T[(3 * h + i) * 6 + 3 * h + c] += A[i] * MA[c] + A[3 + i] * MA[3 + c] + A[6 + i] * MA[6 + c];
+              }
+            }
+          } else {
+            rhs[0] = rhs[1] = rhs[2] = R(0);
           }
+#pragma unroll
+          for (int i = 0; i < 3; ++i) w.r[(3 * h + i) * NP + p] = rhs[i];
         }
-        for (int i = 0; i < 3; ++i) m.r[p * 6 + 3 * h + i] = rhs[i];
+        put_rows(w, p, T, Bc);
       }
+      __syncwarp();
+      if (cr_factor(w.T, w.B, w.V, S.npair, NP, lane)) break;
+      if (proj) { *iters = it + 1; return ST_NOTPD; }
+      proj = true;
     }
-    __syncwarp();
-    if (cr_factor(m.T, m.B, m.V, S.npair, lane)) break;
-    if (proj) { *iters = it + 1; return ST_NOTPD; }
-    proj = true;
-    }
-    cr_solve(m.T, m.B, m.V, m.r, S.npair, lane);
-    from_rhs(S, m.r, m.p, lane);          // p = dDelta
-    __syncwarp();
-    // step length to the cone boundaries, step sizes
+    cr_solve(w.T, w.B, w.V, w.r, S.npair, NP, lane);
+    get_rhs<R, PPL>(S, w, L.pv, lane);            // dDelta
+    // step length to the cone boundaries
     R amin = R(1e30), dmax = R(0);
     bool bad = false;
-    for (int p = lane; p < S.npair; p += 32)
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      const int p = lane + 32 * k;
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int j = 2 * p + h;
-        if (j >= S.nv) continue;
+        if (2 * p + h >= S.nv) continue;
+        const R D[3] = {L.Dl[k][3 * h], L.Dl[k][3 * h + 1], L.Dl[k][3 * h + 2]};
+        const R dD[3] = {L.pv[k][3 * h], L.pv[k][3 * h + 1], L.pv[k][3 * h + 2]};
         for (int i = 0; i < 3; ++i) {
-          dmax = fmax(dmax, fabs(m.p[3 * j + i]));
-          bad = bad || !(fabs(m.p[3 * j + i]) <= R(1e30));
+          dmax = fmax(dmax, fabs(dD[i]));
+          bad = bad || !(fabs(dD[i]) <= R(1e30));
         }
         for (int o = 0; o < nobs; ++o) {
-          const int q = j * nobs + o;
-          R dsv[3], dz[3];
-          pair_step(S, m, j, q, target, dsv, dz);
+          R dsv[3], dz[3], sv[3], zv[3];
+          pair_step(S, w, o, h, p, dD, dsv, dz);
           for (int a = 0; a < 3; ++a) {
             dmax = fmax(dmax, fabs(dsv[a]));
             bad = bad || !(fabs(dz[a]) <= R(1e30)) || !(fabs(dsv[a]) <= R(1e30));
+            sv[a] = w.s[cv(o, h, a, p, NP)];
+            zv[a] = w.z[cv(o, h, a, p, NP)];
           }
-          amin = fmin(amin, soc_max_step(m.sig + 3 * q, dsv));
-          amin = fmin(amin, soc_max_step(m.zz + 3 * q, dz));
+          amin = fmin(amin, soc_max_step(sv, dsv));
+          amin = fmin(amin, soc_max_step(zv, dz));
         }
       }
+    }
     dmax = wmax(dmax);
     amin = -wmax(-amin);
     if (__any_sync(FULL, bad)) { *iters = it + 1; return ST_NONFINITE; }
     const R alpha = fmin(R(1), R(0.99) * amin);
     stalls = alpha < R(1e-6) ? stalls + 1 : 0;
     if (stalls >= 5) { *iters = it + 1; return ST_CONTACT; }
-    // update s, z (they read Delta), then Delta
     bool inside = true;
-    for (int p = lane; p < S.npair; p += 32)
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      const int p = lane + 32 * k;
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int j = 2 * p + h;
-        if (j >= S.nv) continue;
+        if (2 * p + h >= S.nv) continue;
+        const R D[3] = {L.Dl[k][3 * h], L.Dl[k][3 * h + 1], L.Dl[k][3 * h + 2]};
+        const R dD[3] = {L.pv[k][3 * h], L.pv[k][3 * h + 1], L.pv[k][3 * h + 2]};
         for (int o = 0; o < nobs; ++o) {
-          const int q = j * nobs + o;
-          R dsv[3], dz[3];
-          pair_step(S, m, j, q, target, dsv, dz);
-          R* sq = m.sig + 3 * q;
-          R* zq = m.zz + 3 * q;
-          for (int a = 0; a < 3; ++a) { sq[a] += alpha * dsv[a]; zq[a] += alpha * dz[a]; }
-          inside = inside && soc_inside(sq) && soc_inside(zq);
+          R dsv[3], dz[3], sv[3], zv[3];
+          pair_step(S, w, o, h, p, dD, dsv, dz);
+          for (int a = 0; a < 3; ++a) {
+            sv[a] = w.s[cv(o, h, a, p, NP)] + alpha * dsv[a];
+            zv[a] = w.z[cv(o, h, a, p, NP)] + alpha * dz[a];
+            w.s[cv(o, h, a, p, NP)] = sv[a];
+            w.z[cv(o, h, a, p, NP)] = zv[a];
+          }
+          inside = inside && soc_inside(sv) && soc_inside(zv);
         }
-        for (int i = 0; i < 3; ++i) m.Dl[3 * j + i] += alpha * m.p[3 * j + i];
       }
-    __syncwarp();
+#pragma unroll
+      for (int e = 0; e < 6; ++e) L.Dl[k][e] += alpha * L.pv[k][e];
+    }
     if (!__all_sync(FULL, inside)) { *iters = it + 1; return ST_CONTACT; }
     if (final_target && alpha == R(1) && dmax <= S.itol) { *iters = it + 1; return 0; }
   }
@@ -573,23 +757,17 @@ __device__ int stage2_ipm(const Scene<R>& S, WM<R>& m, R kappa, R kfinal, int la
   return ST_CONTACT;
 }
 
-template <typename R>
-__device__ void zero_nodes(const Scene<R>& S, R* v, int lane) {
-  for (int i = lane; i < 3 * S.nv; i += 32) v[i] = R(0);
-}
-
 // ------------------------------------------------------------------------------------------
-// one step.  Inputs: x0 (nodes), misc g, u.  Outputs: dx (x* - x0), Dl (Delta), sig, phi, nrm,
-// misc d, c, gd.  smooth = use the smooth grasp and the single smooth barrier solve.
+// one step: inputs x0 (registers + neighbours), misc g, u, c.  Outputs dx, Dl, contact data,
+// misc d, gd.  smooth = the smooth grasp and the smooth (kappa_c) contact solve.
 // ------------------------------------------------------------------------------------------
-template <typename R>
-__device__ int sim_step(const Scene<R>& S, WM<R>& m, int lane, bool smooth, int* nit, int* iit) {
-  R* c = m.misc + M_C;
-  R* d = m.misc + M_D;
-  R* gd = m.misc + M_GD;
+template <typename R, int PPL>
+__device__ __forceinline__ int sim_step(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, int lane, bool smooth,
+                        int* nit, int* iit, bool warm = false) {
+  R* d = w.misc + M_D;
+  R* gd = w.misc + M_GD;
+  const R* c = w.misc + M_C;
   if (lane < 2) {
-    // c_i = g_i - x0_a(i), maintained by the caller (see advance_state) so that it keeps its
-    // relative precision when it is small next to the absolute coordinates
     R cc[3] = {c[3 * lane], c[3 * lane + 1], c[3 * lane + 2]};
     const R rho = sqrt(dot3(cc, cc));
     R dd;
@@ -603,201 +781,270 @@ __device__ int sim_step(const Scene<R>& S, WM<R>& m, int lane, bool smooth, int*
     }
     d[lane] = dd;
   }
-  zero_nodes(S, m.dx, lane);
-  zero_nodes(S, m.Dl, lane);
   __syncwarp();
-  int st = stage1_newton(S, m, lane, nit);
+  zero6<R, PPL>(L.Dl);
+  int st = stage1_newton(S, L, w, lane, nit, warm);
   *iit = 0;
   if (S.nobs == 0) return st;
-  const R pmin = contact_geometry(S, m, lane);
+  const R pmin = contact_geometry(S, L, w, lane);
+  __syncwarp();
   if (!smooth && pmin >= R(0)) return st;
-  st |= stage2_ipm(S, m, S.kc, smooth ? R(-1) : S.khard, lane, iit);
+  st |= stage2_ipm(S, L, w, S.kc, smooth ? R(-1) : S.khard, lane, iit);
   return st;
 }
 
-// x0 <- x0 + dx + Dl ; g <- g + u ; c <- c + u - (dx_a + Dl_a) (formed from the small
-// increments, not from the absolute coordinates)
-template <typename R>
-__device__ void advance_state(const Scene<R>& S, WM<R>& m, int lane) {
-  if (lane < 6) {
-    const int a = S.grasp[lane / 3], i = lane % 3;
-    m.misc[M_C + lane] += m.misc[M_U + lane] - (m.dx[3 * a + i] + m.Dl[3 * a + i]);
+// x0 <- x0 + dx + Dl ; g <- g + u ; c <- c + u - (dx_a + Dl_a)
+template <typename R, int PPL>
+__device__ __forceinline__ void advance_state(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int gi = 0; gi < 2; ++gi)
+        if (S.grasp[gi] == 2 * p + h)
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            w.misc[M_C + 3 * gi + i] += w.misc[M_U + 3 * gi + i] - (L.dx[k][3 * h + i] + L.Dl[k][3 * h + i]);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) L.x0[k][e] += L.dx[k][e] + L.Dl[k][e];
   }
   __syncwarp();
-  for (int i = lane; i < 3 * S.nv; i += 32) m.x0[i] += m.dx[i] + m.Dl[i];
-  if (lane < 6) m.misc[M_G + lane] += m.misc[M_U + lane];
+  if (lane < 6) w.misc[M_G + lane] += w.misc[M_U + lane];
+  nbr<R, PPL>(L.x0, L.xm, L.xp, lane);
   __syncwarp();
 }
 
 // ------------------------------------------------------------------------------------------
 // adjoint of one smooth step (eq. diff-sim with the total derivative).
-//   in : v1 = xbar+ (adjoint of x+), misc GB = gbar+, the smooth solution of the step and the
-//        factorisation of H2 in (T, B, V)
-//   out: v1 = xbar (adjoint of x), misc GB = gbar, ub6 = ubar (6)
+//   in : xb = xbar+ (adjoint of x+), misc GB = gbar+, the smooth solution in the lane state and
+//        the factorisation of H2 in (T, B, V)
+//   out: xb = xbar (adjoint of x), misc GB = gbar, misc UB = ubar
 // ------------------------------------------------------------------------------------------
-template <typename R>
-__device__ void adjoint_step(const Scene<R>& S, WM<R>& m, int lane, R* ub6) {
-  const R mu = S.mu;
+template <typename R, int PPL>
+__device__ __forceinline__ void adjoint_step(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, R xb[PPL][6], int lane) {
+  const R mu_f = S.mu;
   const R kappa = S.kc;
-  const R* d = m.misc + M_D;
-  const R* c = m.misc + M_C;
-  const R* u = m.misc + M_U;
-  const R* gd = m.misc + M_GD;
-  // mu = H2^{-1} xbar+  -> v2
-  to_rhs(S, m.v1, m.r, lane, R(1));
+  const R* d = w.misc + M_D;
+  const R* c = w.misc + M_C;
+  const R* u = w.misc + M_U;
+  const R* gd = w.misc + M_GD;
+  // mu = H2^{-1} xbar+
+  R mu[PPL][6];
+  put_rhs<R, PPL>(S, w, xb, R(1), lane);
   __syncwarp();
-  cr_solve(m.T, m.B, m.V, m.r, S.npair, lane);
-  from_rhs(S, m.r, m.v2, lane);
-  __syncwarp();
-  // xbar* = xbar+ - (dR/dx*)^T mu  -> p
-  for (int p = lane; p < S.npair; p += 32) {
+  cr_solve(w.T, w.B, w.V, w.r, S.npair, w.NP, lane);
+  get_rhs<R, PPL>(S, w, mu, lane);
+  R mum[PPL][6], mup[PPL][6], Dlm[PPL][6], Dlp[PPL][6], dxm[PPL][6], dxp[PPL][6];
+  nbr<R, PPL>(mu, mum, mup, lane);
+  nbr<R, PPL>(L.Dl, Dlm, Dlp, lane);
+  nbr<R, PPL>(L.dx, dxm, dxp, lane);
+  // xbar* = xbar+ - (dR/dx*)^T mu
+  R xs[PPL][6];
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) xs[k][e] = xb[k][e];
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int j = 2 * p + h;
-      if (j >= S.nv) continue;
-      R acc[3] = {0, 0, 0};
-      R X[3];
-      node_pos(m, j, X);
-      const R* mj = m.v2 + 3 * j;
+      if (2 * p + h >= S.nv) continue;
+      R X[3] = {L.x0[k][3 * h] + L.dx[k][3 * h], L.x0[k][3 * h + 1] + L.dx[k][3 * h + 1],
+                L.x0[k][3 * h + 2] + L.dx[k][3 * h + 2]};
+      const R mj[3] = {mu[k][3 * h], mu[k][3 * h + 1], mu[k][3 * h + 2]};
       for (int o = 0; o < S.nobs; ++o) {
-        const int q = j * S.nobs + o;
         R ph, n[3], N[9];
         obstacle_eval(S.ob_type[o], S.ob[o], X, S.rad, ph, n, N);
-        R sg[3];     // world slack of the converged (primal-feasible) point
-        for (int i = 0; i < 3; ++i) sg[i] = m.Dl[3 * j + i] + ph * n[i];
+        R sg[3];
+        for (int i = 0; i < 3; ++i) sg[i] = L.Dl[k][3 * h + i] + ph * n[i];
         R lam[3], W[9];
-        cone_force_jac(sg, n, kappa, mu, lam, W);
-        R Wm[3];
+        cone_force_jac(sg, n, kappa, mu_f, lam, W);
+        R Wm[3], Lm[3];
         for (int i = 0; i < 3; ++i) Wm[i] = W[i * 3] * mj[0] + W[i * 3 + 1] * mj[1] + W[i * 3 + 2] * mj[2];
-        R Lm[3];
-        cone_force_dn_T(sg, n, kappa, mu, mj, Lm);
-        // G^T mu = -(n (n.W mu) + phi N W mu) + N (dlam/dn)^T mu ; dR/dx* contact = -G
+        cone_force_dn_T(sg, n, kappa, mu_f, mj, Lm);
         const R nWm = dot3(n, Wm);
         for (int i = 0; i < 3; ++i) {
-          R NW = N[i * 3] * Wm[0] + N[i * 3 + 1] * Wm[1] + N[i * 3 + 2] * Wm[2];
-          R NL = N[i * 3] * Lm[0] + N[i * 3 + 1] * Lm[1] + N[i * 3 + 2] * Lm[2];
-          const R GTm = -(n[i] * nWm + ph * NW) + NL;
-          acc[i] -= GTm;      // (dR/dx*)^T mu contact part = -G^T mu
+          const R NW = N[i * 3] * Wm[0] + N[i * 3 + 1] * Wm[1] + N[i * 3 + 2] * Wm[2];
+          const R NL = N[i * 3] * Lm[0] + N[i * 3 + 1] * Lm[1] + N[i * 3 + 2] * Lm[2];
+          // (dR/dx*)^T mu contact part = -G^T mu, G^T mu = -(n (n.W mu) + phi N W mu) + N dlam/dn^T mu
+          xs[k][3 * h + i] += -(n[i] * nWm + ph * NW) + NL;
         }
       }
-      for (int i = 0; i < 3; ++i) m.p[3 * j + i] = m.v1[3 * j + i] - acc[i];
     }
-    springs_of_pair(S, p, [&](int a, int b, int o) {
-      R k, L, dv[3];
-      spring_params(S, a, o, k, L);
-      spring_vec(m, a, b, dv);
-      R mt[3], dl[3], t3[3];
+#pragma unroll
+    for (int sid = 0; sid < 7; ++sid) {
+      const int wa = spr_wa(sid), ha = spr_ha(sid), wb = spr_wb(sid), hb = spr_hb(sid);
+      const int a = spr_node(p, wa, ha), b = spr_node(p, wb, hb);
+      if (a < 0 || b >= S.nv) continue;
+      R kk, Lr;
+      spring_rest(L, k, sid, kk, Lr, S);
+      R dv[3], mt[3], dl[3], t3[3];
+#pragma unroll
       for (int i = 0; i < 3; ++i) {
-        mt[i] = m.v2[3 * b + i] - m.v2[3 * a + i];
-        dl[i] = m.Dl[3 * b + i] - m.Dl[3 * a + i];
+        dv[i] = (pick<R, PPL>(L.x0, L.xm, L.xp, k, wb, 3 * hb + i) - pick<R, PPL>(L.x0, L.xm, L.xp, k, wa, 3 * ha + i)) +
+                (pick<R, PPL>(L.dx, dxm, dxp, k, wb, 3 * hb + i) - pick<R, PPL>(L.dx, dxm, dxp, k, wa, 3 * ha + i));
+        mt[i] = pick<R, PPL>(mu, mum, mup, k, wb, 3 * hb + i) - pick<R, PPL>(mu, mum, mup, k, wa, 3 * ha + i);
+        dl[i] = pick<R, PPL>(L.Dl, Dlm, Dlp, k, wb, 3 * hb + i) - pick<R, PPL>(L.Dl, Dlm, Dlp, k, wa, 3 * ha + i);
       }
-      spring_d3(dv, k, L, mt, dl, t3);
-      if ((b >> 1) == p) for (int i = 0; i < 3; ++i) m.p[3 * b + i] -= t3[i];
-      if ((a >> 1) == p) for (int i = 0; i < 3; ++i) m.p[3 * a + i] += t3[i];
-    });
-  }
-  __syncwarp();
-  // nu = H1^{-1} xbar*  (factorise dF/dq* at x*)  -> v3
-  for (int p = lane; p < S.npair; p += 32)
-    assemble_pair(S, m, p, m.T + p * 36, m.B + p * 36, false, false, (R*)nullptr);
-  to_rhs(S, m.p, m.r, lane, R(1));
-  __syncwarp();
-  cr_factor(m.T, m.B, m.V, S.npair, lane);
-  cr_solve(m.T, m.B, m.V, m.r, S.npair, lane);
-  from_rhs(S, m.r, m.v3, lane);
-  __syncwarp();
-  // grasp coefficients gamma_i = (x*_a - g*_i).nu_a + mu_a.Delta_a
-  R gam[2];
-  for (int gi = 0; gi < 2; ++gi) {
-    const int a = S.grasp[gi];
-    R s = R(0);
-    for (int i = 0; i < 3; ++i)
-      s += (m.dx[3 * a + i] - (c[3 * gi + i] + u[3 * gi + i])) * m.v3[3 * a + i] +
-           m.v2[3 * a + i] * m.Dl[3 * a + i];
-    gam[gi] = s;
-  }
-  __syncwarp();
-  // xbar = w nu (+ grasp terms at a(i))
-  for (int i = lane; i < 3 * S.nv; i += 32) m.v1[i] = S.w * m.v3[i];
-  __syncwarp();
-  if (lane == 0) {
-    for (int gi = 0; gi < 2; ++gi) {
-      const int a = S.grasp[gi];
+      spring_d3(dv, kk, Lr, mt, dl, t3);
+#pragma unroll
       for (int i = 0; i < 3; ++i) {
-        m.v1[3 * a + i] += gam[gi] * gd[3 * gi + i];
-        const R gbp = m.misc[M_GB + 3 * gi + i];
-        const R dnu = d[gi] * m.v3[3 * a + i];
-        m.misc[M_GB + 3 * gi + i] = gbp + dnu - gam[gi] * gd[3 * gi + i];
-        ub6[3 * gi + i] = gbp + dnu;
+        if (wb == 1) xs[k][3 * hb + i] -= t3[i];
+        if (wa == 1) xs[k][3 * ha + i] += t3[i];
       }
     }
+  }
+  // nu = H1^{-1} xbar*  (factorise dF/dq* at x*)
+  __syncwarp();
+  assemble_P(S, L, w, dxm, dxp, false, false, lane);
+  put_rhs<R, PPL>(S, w, xs, R(1), lane);
+  __syncwarp();
+  cr_factor(w.T, w.B, w.V, S.npair, w.NP, lane);
+  cr_solve(w.T, w.B, w.V, w.r, S.npair, w.NP, lane);
+  R nu[PPL][6];
+  get_rhs<R, PPL>(S, w, nu, lane);
+  // xbar = w nu + grasp terms; gbar, ubar
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) xb[k][e] = S.w * nu[k][e];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int gi = 0; gi < 2; ++gi)
+        if (S.grasp[gi] == 2 * p + h) {
+          R gam = R(0);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+            gam += (L.dx[k][3 * h + i] - (c[3 * gi + i] + u[3 * gi + i])) * nu[k][3 * h + i] +
+                   mu[k][3 * h + i] * L.Dl[k][3 * h + i];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            xb[k][3 * h + i] += gam * gd[3 * gi + i];
+            const R gbp = w.misc[M_GB + 3 * gi + i];
+            const R dnu = d[gi] * nu[k][3 * h + i];
+            w.misc[M_GB + 3 * gi + i] = gbp + dnu - gam * gd[3 * gi + i];
+            w.misc[M_UB + 3 * gi + i] = gbp + dnu;
+          }
+        }
   }
   __syncwarp();
 }
 
-// penalty part of the planning loss at the current state x0: value (lane share) and seeds
-// added to `seed` (node vector) when non-null
-template <typename R>
-__device__ R penalty_lane(const Scene<R>& S, const WM<R>& m, R* seed, int lane) {
+// penalty part of the planning loss at the state x0: value (lane share) and seeds added to sd
+template <typename R, int PPL>
+__device__ __forceinline__ R penalty(const Scene<R>& S, const Lane<R, PPL>& L, R sd[PPL][6], bool seeds, int lane) {
   R val = R(0);
-  for (int p = lane; p < S.npair; p += 32)
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int j = 2 * p + h;
-      if (j >= S.nv) continue;
-      R X[3] = {m.x0[3 * j], m.x0[3 * j + 1], m.x0[3 * j + 2]};
+      if (2 * p + h >= S.nv) continue;
+      R X[3] = {L.x0[k][3 * h], L.x0[k][3 * h + 1], L.x0[k][3 * h + 2]};
       for (int o = 0; o < S.nobs; ++o) {
         if (S.ob_type[o] == CS_PLANE) continue;
         R ph, n[3];
         obstacle_eval(S.ob_type[o], S.ob[o], X, S.rad, ph, n, (R*)nullptr);
         const R v = S.pen_m - ph > R(0) ? S.pen_m - ph : R(0);
         val += S.w_pen * v * v;
-        if (seed) for (int i = 0; i < 3; ++i) seed[3 * j + i] += R(-2) * S.w_pen * v * n[i];
+        if (seeds) for (int i = 0; i < 3; ++i) sd[k][3 * h + i] += R(-2) * S.w_pen * v * n[i];
       }
     }
+  }
   return val;
 }
 
 // ------------------------------------------------------------------------------------------
-// kernels
+// state transfer: q = [x, g]; checkpoint records [nq + 6] also carry the grasp offsets c
 // ------------------------------------------------------------------------------------------
-// state q = [x, g] from global memory; the grasp offsets c = g - x_a are formed from it
-template <typename R>
-__device__ __forceinline__ void load_q(const Scene<R>& S, WM<R>& m, const R* q, int lane) {
-  for (int i = lane; i < 3 * S.nv; i += 32) m.x0[i] = q[i];
+template <typename R, int PPL>
+__device__ __forceinline__ void load_nodes(const Scene<R>& S, Lane<R, PPL>& L, const R* q, int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) L.x0[k][e] = (2 * p + e / 3 < S.nv) ? q[6 * p + e] : R(0);
+  }
+  nbr<R, PPL>(L.x0, L.xm, L.xp, lane);
+}
+
+template <typename R, int PPL>
+__device__ __forceinline__ void load_q(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, const R* q, int lane) {
+  load_nodes(S, L, q, lane);
   if (lane < 6) {
     const R g = q[3 * S.nv + lane];
-    m.misc[M_G + lane] = g;
-    m.misc[M_C + lane] = g - q[3 * S.grasp[lane / 3] + lane % 3];
+    w.misc[M_G + lane] = g;
+    w.misc[M_C + lane] = g - q[3 * S.grasp[lane / 3] + lane % 3];
   }
   __syncwarp();
 }
 
-template <typename R>
-__device__ __forceinline__ void store_q(const Scene<R>& S, const WM<R>& m, R* q, int lane) {
-  for (int i = lane; i < 3 * S.nv; i += 32) q[i] = m.x0[i];
-  if (lane < 6) q[3 * S.nv + lane] = m.misc[M_G + lane];
+template <typename R, int PPL>
+__device__ __forceinline__ void store_q(const Scene<R>& S, const Lane<R, PPL>& L, const WS<R>& w, R* q, int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+      if (2 * p + e / 3 < S.nv) q[6 * p + e] = L.x0[k][e];
+  }
+  if (lane < 6) q[3 * S.nv + lane] = w.misc[M_G + lane];
 }
 
-// checkpoint record [nq + 6]: the state and the tracked grasp offsets
-template <typename R>
-__device__ __forceinline__ void store_rec(const Scene<R>& S, const WM<R>& m, R* r, int lane) {
-  store_q(S, m, r, lane);
-  if (lane < 6) r[3 * S.nv + 6 + lane] = m.misc[M_C + lane];
+// record layout: q [nq] | c [6] | dx [3 nv] (the stage-1 offset x* - x of the step that
+// produced q, used to start the smooth re-solve of the backward pass)
+template <typename R, int PPL>
+__device__ __forceinline__ void store_rec(const Scene<R>& S, const Lane<R, PPL>& L, const WS<R>& w, R* r, int lane) {
+  store_q(S, L, w, r, lane);
+  if (lane < 6) r[3 * S.nv + 6 + lane] = w.misc[M_C + lane];
+  R* rd = r + 3 * S.nv + 12;
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+      if (2 * p + e / 3 < S.nv) rd[6 * p + e] = L.dx[k][e];
+  }
 }
 
-template <typename R>
-__device__ __forceinline__ void load_rec(const Scene<R>& S, WM<R>& m, const R* r, int lane) {
-  for (int i = lane; i < 3 * S.nv; i += 32) m.x0[i] = r[i];
+template <typename R, int PPL>
+__device__ __forceinline__ void load_rec_dx(const Scene<R>& S, Lane<R, PPL>& L, const R* r, int lane) {
+  const R* rd = r + 3 * S.nv + 12;
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) L.dx[k][e] = (2 * p + e / 3 < S.nv) ? rd[6 * p + e] : R(0);
+  }
+}
+
+template <typename R, int PPL>
+__device__ __forceinline__ void load_rec(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, const R* r, int lane) {
+  load_nodes(S, L, r, lane);
   if (lane < 6) {
-    m.misc[M_G + lane] = r[3 * S.nv + lane];
-    m.misc[M_C + lane] = r[3 * S.nv + 6 + lane];
+    w.misc[M_G + lane] = r[3 * S.nv + lane];
+    w.misc[M_C + lane] = r[3 * S.nv + 6 + lane];
   }
   __syncwarp();
 }
 
 template <typename R>
 __device__ __forceinline__ void load_controls(R* dst, const R* src, int n, int lane) {
-  // 16-byte vector loads when aligned (FP32 rows of 6 H floats: H even keeps rows aligned)
   if (sizeof(R) == 4 && (((uintptr_t)src) & 15) == 0 && (n & 3) == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int i = lane; i < n / 4; i += 32) d4[i] = s4[i];
+  } else {
+    for (int i = lane; i < n; i += 32) dst[i] = src[i];
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void store_controls(R* dst, const R* src, int n, int lane) {
+  if (sizeof(R) == 4 && (((uintptr_t)dst) & 15) == 0 && (n & 3) == 0) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     float4* d4 = reinterpret_cast<float4*>(dst);
     for (int i = lane; i < n / 4; i += 32) d4[i] = s4[i];
@@ -808,140 +1055,169 @@ __device__ __forceinline__ void load_controls(R* dst, const R* src, int n, int l
 
 extern __shared__ __align__(16) unsigned char cs_smem[];
 
-template <typename R>
+// ------------------------------------------------------------------------------------------
+// kernels
+// ------------------------------------------------------------------------------------------
+template <typename R, int PPL>
 __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int H, const R* q0,
                                                          const R* U, R* traj, R* qH, int32_t* status,
                                                          int32_t* counters) {
   const int lane = threadIdx.x;
   const int nq = 3 * S.nv + 6;
-  WM<R> m = wm_carve<R>(reinterpret_cast<R*>(cs_smem), S.nv, S.npair, S.nobs, H, false);
+  WS<R> w = ws_carve<R>(reinterpret_cast<R*>(cs_smem), 32 * PPL, S.nobs, H, false);
+  Lane<R, PPL> L;
+  load_rest(S, L, lane);
   const bool smooth = S.fwd_mode == CS_SMOOTH;
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
-    load_q(S, m, q0 + (size_t)b * nq, lane);
-    load_controls(m.u, U + (size_t)b * H * 6, 6 * H, lane);
+    load_q(S, L, w, q0 + (size_t)b * nq, lane);
+    load_controls(w.u, U + (size_t)b * H * 6, 6 * H, lane);
     __syncwarp();
-    if (traj) store_q(S, m, traj + (size_t)b * (H + 1) * nq, lane);
+    if (traj) store_q(S, L, w, traj + (size_t)b * (H + 1) * nq, lane);
     int st = 0;
     for (int t = 0; t < H; ++t) {
-      if (lane < 6) m.misc[M_U + lane] = m.u[6 * t + lane];
+      if (lane < 6) w.misc[M_U + lane] = w.u[6 * t + lane];
       __syncwarp();
       int ni, ii;
-      const int s1 = sim_step(S, m, lane, smooth, &ni, &ii);
+      const int s1 = sim_step(S, L, w, lane, smooth, &ni, &ii);
       st |= s1;
       if (counters && lane == 0) {
         int32_t* c = counters + ((size_t)b * H + t) * 3;
         c[0] = ni; c[1] = ii; c[2] = s1;
       }
-      advance_state(S, m, lane);
-      if (traj) store_q(S, m, traj + ((size_t)b * (H + 1) + t + 1) * nq, lane);
+      advance_state(S, L, w, lane);
+      if (traj) store_q(S, L, w, traj + ((size_t)b * (H + 1) + t + 1) * nq, lane);
     }
-    if (qH) store_q(S, m, qH + (size_t)b * nq, lane);
+    if (qH) store_q(S, L, w, qH + (size_t)b * nq, lane);
     if (lane == 0 && status) status[b] = st;
     __syncwarp();
   }
 }
 
-// forward + checkpointed adjoint.  ws: per-rollout workspace [ (nck + k) * nq ]
-template <typename R>
+// forward + checkpointed adjoint.  ws: per-rollout workspace of checkpoint records.
+// The steps run through one loop over a schedule -- the H forward steps, then for each segment
+// (last to first) the recomputed steps and the backward steps -- so that the step and its
+// adjoint are each inlined once.
+template <typename R, int PPL>
 __global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, const R* q0,
                                                      const R* U, const R* dLdtraj, R* Lout, R* dLdu,
                                                      R* dLdq0, int32_t* status, R* ws, size_t ws_stride) {
   const int lane = threadIdx.x;
   const int nq = 3 * S.nv + 6;
+  const int rl = nq + 6 + 3 * S.nv;
   const int k = S.ckpt;
   const int nseg = (H + k - 1) / k;
-  WM<R> m = wm_carve<R>(reinterpret_cast<R*>(cs_smem), S.nv, S.npair, S.nobs, H, false);
+  WS<R> w = ws_carve<R>(reinterpret_cast<R*>(cs_smem), 32 * PPL, S.nobs, H, false);
+  Lane<R, PPL> L;
+  load_rest(S, L, lane);
   const bool fwd_smooth = S.grad_mode == CS_CONSISTENT;
-  const int rl = nq + 6;                       // checkpoint record length
+  enum { FWD = 0, RECOMP = 1, BACK = 2 };
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
-    R* ck = ws + (size_t)b * ws_stride;        // checkpoints [nseg + 1][rl]
-    R* seg = ck + (size_t)(nseg + 1) * rl;     // segment states [k][rl]
-    load_q(S, m, q0 + (size_t)b * nq, lane);
-    load_controls(m.u, U + (size_t)b * H * 6, 6 * H, lane);
+    R* ck = ws + (size_t)b * ws_stride;        // checkpoint records [nseg + 1][rl]
+    R* seg = ck + (size_t)(nseg + 1) * rl;     // segment records [k][rl]
+    load_q(S, L, w, q0 + (size_t)b * nq, lane);
+    load_controls(w.u, U + (size_t)b * H * 6, 6 * H, lane);
     __syncwarp();
-    store_rec(S, m, ck, lane);
+    store_rec(S, L, w, ck, lane);
     int st = 0;
     R Lacc = R(0);
-    for (int t = 0; t < H; ++t) {
-      if (lane < 6) m.misc[M_U + lane] = m.u[6 * t + lane];
+    R xb[PPL][6];
+    zero6<R, PPL>(xb);
+    // schedule state
+    int kind = FWD, t = 0, sgi = nseg - 1, t0 = 0, t1 = 0;
+    while (true) {
+      if (kind == BACK) {
+        load_rec(S, L, w, seg + (size_t)(t - t0) * rl, lane);
+        // start the smooth re-solve at the forward step's stage-1 solution (record of q_{t+1})
+        load_rec_dx(S, L, t + 1 < t1 ? seg + (size_t)(t + 1 - t0) * rl : ck + (size_t)(sgi + 1) * rl, lane);
+      }
+      if (lane < 6) w.misc[M_U + lane] = w.u[6 * t + lane];
       __syncwarp();
       int ni, ii;
-      st |= sim_step(S, m, lane, fwd_smooth, &ni, &ii);
-      advance_state(S, m, lane);
-      if ((t + 1) % k == 0) store_rec(S, m, ck + (size_t)((t + 1) / k) * rl, lane);
-      if (S.has_loss) Lacc += penalty_lane(S, m, (R*)nullptr, lane);
-    }
-    // seeds at q_H: goal + penalty + dL/dtraj[H]
-    for (int i = lane; i < 3 * S.nv; i += 32) m.v1[i] = R(0);
-    if (lane < 6) m.misc[M_GB + lane] = R(0);
-    __syncwarp();
-    if (S.has_loss) {
-      penalty_lane(S, m, m.v1, lane);
-      __syncwarp();
-      if (lane == 0) {
-        for (int gi = 0; gi < S.n_goal; ++gi) {
-          const int j = S.goal[gi];
-          for (int i = 0; i < 3; ++i) {
-            const R e = m.x0[3 * j + i] - S.goal_pos[gi][i];
-            Lacc += S.w_goal * e * e;
-            m.v1[3 * j + i] += R(2) * S.w_goal * e;
+      st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK);
+      if (kind != BACK) {
+        advance_state(S, L, w, lane);
+        if (kind == FWD) {
+          if ((t + 1) % k == 0 || t == H - 1) store_rec(S, L, w, ck + (size_t)((t + k) / k) * rl, lane);
+          if (S.has_loss) Lacc += penalty(S, L, xb, false, lane);
+        } else {
+          store_rec(S, L, w, seg + (size_t)(t + 1 - t0) * rl, lane);
+        }
+      } else {
+        adjoint_step(S, L, w, xb, lane);
+        if (lane < 6)
+          w.ub[6 * t + lane] = w.misc[M_UB + lane] + (S.has_loss ? R(2) * S.w_u * w.u[6 * t + lane] : R(0));
+      }
+      // seeds dL/dq_t of the state the adjoint reaches next (q_H after the forward, q_t after a
+      // backward step); x0 holds that state in both cases
+      const bool seed_now = (kind == FWD && t == H - 1) || kind == BACK;
+      if (seed_now) {
+        if (kind == FWD) {
+          if (lane < 6) w.misc[M_GB + lane] = R(0);
+          __syncwarp();
+          if (S.has_loss) {
+#pragma unroll
+            for (int kk = 0; kk < PPL; ++kk) {
+              const int p = lane + 32 * kk;
+              for (int gi = 0; gi < S.n_goal; ++gi) {
+                const int j = S.goal[gi];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  if (j != 2 * p + h) continue;
+#pragma unroll
+                  for (int i = 0; i < 3; ++i) {
+                    const R e = L.x0[kk][3 * h + i] - S.goal_pos[gi][i];
+                    Lacc += S.w_goal * e * e;
+                    xb[kk][3 * h + i] += R(2) * S.w_goal * e;
+                  }
+                }
+              }
+            }
+            for (int i = lane; i < 6 * H; i += 32) Lacc += S.w_u * w.u[i] * w.u[i];
           }
         }
-      }
-      for (int i = lane; i < 6 * H; i += 32) Lacc += S.w_u * m.u[i] * m.u[i];
-    }
-    if (dLdtraj) {
-      const R* sd = dLdtraj + ((size_t)b * (H + 1) + H) * nq;
-      __syncwarp();
-      for (int i = lane; i < 3 * S.nv; i += 32) m.v1[i] += sd[i];
-      if (lane < 6) m.misc[M_GB + lane] += sd[3 * S.nv + lane];
-    }
-    __syncwarp();
-    // backward over segments
-    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-      const int t0 = sgi * k;
-      const int t1 = min(t0 + k, H);
-      // recompute states t0 .. t1-1 into seg (keep v1 / gbar: sim_step does not touch them)
-      R gb_save = lane < 6 ? m.misc[M_GB + lane] : R(0);
-      load_rec(S, m, ck + (size_t)sgi * rl, lane);
-      store_rec(S, m, seg, lane);
-      for (int t = t0; t < t1 - 1; ++t) {
-        if (lane < 6) m.misc[M_U + lane] = m.u[6 * t + lane];
-        __syncwarp();
-        int ni, ii;
-        st |= sim_step(S, m, lane, fwd_smooth, &ni, &ii);
-        advance_state(S, m, lane);
-        store_rec(S, m, seg + (size_t)(t + 1 - t0) * rl, lane);
-      }
-      __syncwarp();
-      for (int t = t1 - 1; t >= t0; --t) {
-        load_rec(S, m, seg + (size_t)(t - t0) * rl, lane);
-        if (lane < 6) { m.misc[M_U + lane] = m.u[6 * t + lane]; m.misc[M_GB + lane] = gb_save; }
-        __syncwarp();
-        int ni, ii;
-        st |= sim_step(S, m, lane, true, &ni, &ii);     // smooth step at the forward state
-        R ub6[6];
-        adjoint_step(S, m, lane, ub6);
-        if (lane == 0)
-          for (int i = 0; i < 6; ++i)
-            m.ub[6 * t + i] = ub6[i] + (S.has_loss ? R(2) * S.w_u * m.u[6 * t + i] : R(0));
-        // seeds at q_t
-        if (t >= 1 && S.has_loss) penalty_lane(S, m, m.v1, lane);
-        __syncwarp();
+        const int ts = kind == FWD ? H : t;        // index of the seeded state
+        if (ts >= 1 && S.has_loss) penalty(S, L, xb, true, lane);
         if (dLdtraj) {
-          const R* sd = dLdtraj + ((size_t)b * (H + 1) + t) * nq;
-          for (int i = lane; i < 3 * S.nv; i += 32) m.v1[i] += sd[i];
-          if (lane < 6) m.misc[M_GB + lane] += sd[3 * S.nv + lane];
+          const R* sd = dLdtraj + ((size_t)b * (H + 1) + ts) * nq;
+#pragma unroll
+          for (int kk = 0; kk < PPL; ++kk) {
+            const int p = lane + 32 * kk;
+#pragma unroll
+            for (int e = 0; e < 6; ++e)
+              if (2 * p + e / 3 < S.nv) xb[kk][e] += sd[6 * p + e];
+          }
+          if (lane < 6) w.misc[M_GB + lane] += sd[3 * S.nv + lane];
         }
         __syncwarp();
-        gb_save = lane < 6 ? m.misc[M_GB + lane] : R(0);
+      }
+      // next schedule entry
+      bool start_seg = false;
+      if (kind == FWD) {
+        if (++t == H) start_seg = true;
+      } else if (kind == RECOMP) {
+        if (++t == t1 - 1) { kind = BACK; t = t1 - 1; }
+      } else {
+        if (--t < t0) { if (--sgi < 0) break; start_seg = true; }
+      }
+      if (start_seg) {
+        t0 = sgi * k;
+        t1 = min(t0 + k, H);
+        load_rec(S, L, w, ck + (size_t)sgi * rl, lane);
+        store_rec(S, L, w, seg, lane);
+        if (t1 - t0 > 1) { kind = RECOMP; t = t0; } else { kind = BACK; t = t0; }
       }
     }
     __syncwarp();
-    for (int i = lane; i < 6 * H; i += 32) dLdu[(size_t)b * H * 6 + i] = m.ub[i];
+    store_controls(dLdu + (size_t)b * H * 6, w.ub, 6 * H, lane);
     if (dLdq0) {
-      for (int i = lane; i < 3 * S.nv; i += 32) dLdq0[(size_t)b * nq + i] = m.v1[i];
-      if (lane < 6) dLdq0[(size_t)b * nq + 3 * S.nv + lane] = m.misc[M_GB + lane];
+#pragma unroll
+      for (int kk = 0; kk < PPL; ++kk) {
+        const int p = lane + 32 * kk;
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+          if (2 * p + e / 3 < S.nv) dLdq0[(size_t)b * nq + 6 * p + e] = xb[kk][e];
+      }
+      if (lane < 6) dLdq0[(size_t)b * nq + 3 * S.nv + lane] = w.misc[M_GB + lane];
     }
     Lacc = wsum(Lacc);
     if (lane == 0) {
@@ -953,133 +1229,137 @@ __global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, 
 }
 
 // ------------------------------------------------------------------------------------------
-// linearisation: one warp per (trajectory, step); tangents of the smooth step, 32 directions
-// at a time (one per lane), each lane running its own solves on the shared factorisations.
+// linearisation: one warp per (trajectory, step); tangents of the smooth step, 32 directions at
+// a time (one per lane), each lane running its own solves on the two shared factorisations.
 // ------------------------------------------------------------------------------------------
-template <typename R>
+template <typename R, int PPL>
 __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, int H, const R* Z,
                                                            const R* Vc, R* A, R* Bm, int32_t* status) {
   const int lane = threadIdx.x;
   const int nv = S.nv, nq = 3 * nv + 6, N = S.npair;
-  WM<R> m = wm_carve<R>(reinterpret_cast<R*>(cs_smem), nv, N, S.nobs, 1, true);
-  // per-lane tangent vectors, interleaved by lane: [ (6 N) ][32]
-  R* tv1 = m.T2 + (size_t)N * 3 * 36;       // placed after the carve (host sizes the region)
-  R* tv2 = tv1 + (size_t)6 * N * 32;
+  const int NP = 32 * PPL;
+  WS<R> w = ws_carve<R>(reinterpret_cast<R*>(cs_smem), NP, S.nobs, 1, true);
+  // per-lane tangent vectors in element-major pair layout, interleaved by lane
+  R* tv1 = w.Dn + 6 * (size_t)NP;
+  R* tv2 = tv1 + (size_t)6 * NP * 32;
+  Lane<R, PPL> L;
+  load_rest(S, L, lane);
   const int ndir = nq + 6;
   for (int job = blockIdx.x; job < B * H; job += gridDim.x) {
     const int b = job / H, t = job % H;
-    load_q(S, m, Z + ((size_t)b * (H + 1) + t) * nq, lane);
-    if (lane < 6) m.misc[M_U + lane] = Vc[((size_t)b * H + t) * 6 + lane];
+    const R* z = Z + ((size_t)b * (H + 1) + t) * nq;
+    load_q(S, L, w, z, lane);
+    if (lane < 6) w.misc[M_U + lane] = Vc[((size_t)b * H + t) * 6 + lane];
     __syncwarp();
     int ni, ii;
-    int st = sim_step(S, m, lane, true, &ni, &ii);
-    // H2 factor is in (T,B,V) after a barrier solve; with no obstacles it is the stage-1 one.
-    // Copy it to the second slot, then factorise H1 at x* into the first.
-    for (int i = lane; i < N * 36; i += 32) { m.T2[i] = m.T[i]; m.B2[i] = m.B[i]; m.V2[i] = m.V[i]; }
-    for (int p = lane; p < N; p += 32)
-      assemble_pair(S, m, p, m.T + p * 36, m.B + p * 36, false, false, (R*)nullptr);
+    int st = sim_step(S, L, w, lane, true, &ni, &ii);
+    // keep H2's factorisation; factorise H1 at x* into the first slot
+    for (int i = lane; i < 36 * NP; i += 32) { w.T2[i] = w.T[i]; w.B2[i] = w.B[i]; w.V2[i] = w.V[i]; }
+    R dxm[PPL][6], dxp[PPL][6];
+    nbr<R, PPL>(L.dx, dxm, dxp, lane);
+    assemble_P(S, L, w, dxm, dxp, false, false, lane);
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      const int p = lane + 32 * k;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        w.xs[e * NP + p] = L.dx[k][e];
+        w.Dn[e * NP + p] = L.Dl[k][e];
+      }
+    }
     __syncwarp();
-    if (!cr_factor(m.T, m.B, m.V, N, lane)) st |= ST_NOTPD;
-    const R* d = m.misc + M_D;
-    const R* c = m.misc + M_C;
-    const R* u = m.misc + M_U;
-    const R* gd = m.misc + M_GD;
+    if (!cr_factor(w.T, w.B, w.V, N, NP, lane)) st |= ST_NOTPD;
+    const R* d = w.misc + M_D;
+    const R* c = w.misc + M_C;
+    const R* u = w.misc + M_U;
+    const R* gd = w.misc + M_GD;
+    auto node_dx = [&](int j, int i) -> R { return w.xs[(3 * (j & 1) + i) * NP + (j >> 1)]; };
+    auto node_D = [&](int j, int i) -> R { return w.Dn[(3 * (j & 1) + i) * NP + (j >> 1)]; };
+    auto T1 = [&](int j, int i) -> R& { return tv1[((size_t)(3 * (j & 1) + i) * NP + (j >> 1)) * 32 + lane]; };
+    auto T2v = [&](int j, int i) -> R& { return tv2[((size_t)(3 * (j & 1) + i) * NP + (j >> 1)) * 32 + lane]; };
     for (int d0 = 0; d0 < ndir; d0 += 32) {
       const int dir = d0 + lane;
       const bool act = dir < ndir;
-      // classify the direction: x (node jn, comp cc), g_i comp cc, or u_i comp cc
       int kind = 0, jn = 0, cc = 0, gi = 0;
       if (dir < 3 * nv) { kind = 0; jn = dir / 3; cc = dir % 3; }
       else if (dir < nq) { kind = 1; gi = (dir - 3 * nv) / 3; cc = (dir - 3 * nv) % 3; }
-      else { kind = 2; gi = (dir - nq) / 3; cc = (dir - nq) % 3; }
-      // rhs1 = -(dF/dtheta) e_dir   (then dx* = H1^{-1} rhs1)
-      for (int r = 0; r < 6 * N; ++r) tv1[r * 32 + lane] = R(0);
+      else { kind = 2; gi = (dir - nq) / 3; cc = (dir - nq) % 3; if (gi > 1) gi = 1; }
+      for (int r = 0; r < 6 * NP; ++r) { tv1[(size_t)r * 32 + lane] = R(0); tv2[(size_t)r * 32 + lane] = R(0); }
+      // rhs1 = -(dF/dtheta) e_dir ; dx* = H1^{-1} rhs1
       if (act) {
         if (kind == 0) {
-          tv1[(3 * jn + cc) * 32 + lane] += S.w;
+          T1(jn, cc) += S.w;
           for (int g2 = 0; g2 < 2; ++g2)
             if (S.grasp[g2] == jn) {
-              const R dd = -gd[3 * g2 + cc];     // d d / d x_a = -gd
-              for (int i = 0; i < 3; ++i)
-                tv1[(3 * jn + i) * 32 + lane] -= (m.dx[3 * jn + i] - (c[3 * g2 + i] + u[3 * g2 + i])) * dd;
+              const R dd = -gd[3 * g2 + cc];
+              for (int i = 0; i < 3; ++i) T1(jn, i) -= (node_dx(jn, i) - (c[3 * g2 + i] + u[3 * g2 + i])) * dd;
             }
         } else {
           const int a = S.grasp[gi];
-          tv1[(3 * a + cc) * 32 + lane] += d[gi];
+          T1(a, cc) += d[gi];
           if (kind == 1)
-            for (int i = 0; i < 3; ++i)
-              tv1[(3 * a + i) * 32 + lane] -= (m.dx[3 * a + i] - (c[3 * gi + i] + u[3 * gi + i])) * gd[3 * gi + cc];
+            for (int i = 0; i < 3; ++i) T1(a, i) -= (node_dx(a, i) - (c[3 * gi + i] + u[3 * gi + i])) * gd[3 * gi + cc];
         }
       }
-      // dummy node rows stay 0
-      cr_solve_serial(m.T, m.B, m.V, tv1 + lane, 32, N);       // tv1 = dx*
+      cr_solve_serial(w.T, w.B, w.V, tv1 + lane, 32, N, NP);
       // rhs2 = -(Rx dx* + Rq theta)
-      for (int r = 0; r < 6 * N; ++r) tv2[r * 32 + lane] = R(0);
       for (int j = 0; j < nv; ++j) {
         R X[3];
-        node_pos(m, j, X);
-        R v[3] = {tv1[(3 * j) * 32 + lane], tv1[(3 * j + 1) * 32 + lane], tv1[(3 * j + 2) * 32 + lane]};
-        R acc[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i) X[i] = z[3 * j + i] + node_dx(j, i);
+        R v[3] = {T1(j, 0), T1(j, 1), T1(j, 2)};
         for (int o = 0; o < S.nobs; ++o) {
-          const int q = j * S.nobs + o;
           R ph, n[3], Nm[9];
           obstacle_eval(S.ob_type[o], S.ob[o], X, S.rad, ph, n, Nm);
           R sg[3];
-          for (int i = 0; i < 3; ++i) sg[i] = m.Dl[3 * j + i] + ph * n[i];
+          for (int i = 0; i < 3; ++i) sg[i] = node_D(j, i) + ph * n[i];
           R lam[3], W[9];
           cone_force_jac(sg, n, S.kc, S.mu, lam, W);
-          // G v = -W (n (n.v) + phi N v) + dlam/dn N v ; Rx contact = -G
           R Nv[3], dsg[3], Wd[3], Ld[3];
           for (int i = 0; i < 3; ++i) Nv[i] = Nm[i * 3] * v[0] + Nm[i * 3 + 1] * v[1] + Nm[i * 3 + 2] * v[2];
           const R nv_ = dot3(n, v);
           for (int i = 0; i < 3; ++i) dsg[i] = n[i] * nv_ + ph * Nv[i];
           for (int i = 0; i < 3; ++i) Wd[i] = W[i * 3] * dsg[0] + W[i * 3 + 1] * dsg[1] + W[i * 3 + 2] * dsg[2];
           cone_force_dn(sg, n, S.kc, S.mu, Nv, Ld);
-          for (int i = 0; i < 3; ++i) acc[i] -= (-Wd[i] + Ld[i]);
+          for (int i = 0; i < 3; ++i) T2v(j, i) -= (-Wd[i] + Ld[i]);
         }
-        for (int i = 0; i < 3; ++i) tv2[(3 * j + i) * 32 + lane] += acc[i];
         for (int o = 1; o <= 2; ++o) {
           const int a = j, b2 = j + o;
           if (b2 >= nv) continue;
-          R k, L, dv[3], mt[3], dl[3], t3[3];
-          spring_params(S, a, o, k, L);
-          spring_vec(m, a, b2, dv);
+          const R kk = o == 1 ? S.k1 : S.k2;
+          const R Lr = o == 1 ? S.L1[a] : S.L2[a];
+          R dv[3], mt[3], dl[3], t3[3];
           for (int i = 0; i < 3; ++i) {
-            mt[i] = tv1[(3 * b2 + i) * 32 + lane] - tv1[(3 * a + i) * 32 + lane];
-            dl[i] = m.Dl[3 * b2 + i] - m.Dl[3 * a + i];
+            dv[i] = (z[3 * b2 + i] - z[3 * a + i]) + (node_dx(b2, i) - node_dx(a, i));
+            mt[i] = T1(b2, i) - T1(a, i);
+            dl[i] = node_D(b2, i) - node_D(a, i);
           }
-          spring_d3(dv, k, L, mt, dl, t3);
-          for (int i = 0; i < 3; ++i) {
-            tv2[(3 * b2 + i) * 32 + lane] += t3[i];
-            tv2[(3 * a + i) * 32 + lane] -= t3[i];
-          }
+          spring_d3(dv, kk, Lr, mt, dl, t3);
+          for (int i = 0; i < 3; ++i) { T2v(b2, i) += t3[i]; T2v(a, i) -= t3[i]; }
         }
       }
       if (act && kind != 2) {
-        // Rq theta: node a(i) gets Delta_a (dd_i . theta)
         for (int g2 = 0; g2 < 2; ++g2) {
           const int a = S.grasp[g2];
           R dd = R(0);
           if (kind == 1 && gi == g2) dd = gd[3 * g2 + cc];
           if (kind == 0 && jn == a) dd = -gd[3 * g2 + cc];
-          for (int i = 0; i < 3; ++i) tv2[(3 * a + i) * 32 + lane] += m.Dl[3 * a + i] * dd;
+          for (int i = 0; i < 3; ++i) T2v(a, i) += node_D(a, i) * dd;
         }
       }
-      for (int r = 0; r < 3 * nv; ++r) tv2[r * 32 + lane] = -tv2[r * 32 + lane];
-      cr_solve_serial(m.T2, m.B2, m.V2, tv2 + lane, 32, N);     // tv2 = dDelta
-      // column dir of [A | B]: rows 0..3nv-1 = dx* + dDelta, gripper rows = identity part
+      for (int j = 0; j < nv; ++j)
+        for (int i = 0; i < 3; ++i) T2v(j, i) = -T2v(j, i);
+      cr_solve_serial(w.T2, w.B2, w.V2, tv2 + lane, 32, N, NP);
       if (act) {
         R* out;
         size_t ld;
         int col;
         if (dir < nq) { out = A + ((size_t)b * H + t) * nq * nq; ld = nq; col = dir; }
         else { out = Bm + ((size_t)b * H + t) * nq * 6; ld = 6; col = dir - nq; }
-        for (int r = 0; r < 3 * nv; ++r)
-          out[(size_t)r * ld + col] = tv1[r * 32 + lane] + tv2[r * 32 + lane];
+        for (int j = 0; j < nv; ++j)
+          for (int i = 0; i < 3; ++i) out[(size_t)(3 * j + i) * ld + col] = T1(j, i) + T2v(j, i);
         for (int r = 0; r < 6; ++r) {
           R v = R(0);
-          if (kind == 1 && r == 3 * gi + cc) v = R(1);
-          if (kind == 2 && r == 3 * gi + cc) v = R(1);
+          if (kind >= 1 && r == 3 * gi + cc) v = R(1);
           out[(size_t)(3 * nv + r) * ld + col] = v;
         }
       }

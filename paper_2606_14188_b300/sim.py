@@ -12,7 +12,7 @@ import torch
 
 from . import _lib as L
 
-DEFAULT_TOL = {4: dict(newton_tol=1e-7, ipm_tol=1e-7, newton_max=40, ipm_max=80),
+DEFAULT_TOL = {4: dict(newton_tol=1e-5, ipm_tol=1e-6, newton_max=40, ipm_max=80),
                8: dict(newton_tol=1e-12, ipm_tol=1e-12, newton_max=60, ipm_max=200)}
 
 
