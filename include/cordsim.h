@@ -161,6 +161,27 @@ cs_status sim_rollout_vjp(cs_sim* sim, int B, int H, const void* q0, const void*
 cs_status sim_linearize(cs_sim* sim, int B, int H, const void* z, const void* v, void* A,
                         void* Bm, int32_t* status, void* stream);
 
+/* Allocation-free rollout adjoint (no counterpart in the paper; an interface for callers that
+ * cannot allocate device memory: a real-time control loop that must not block on a driver
+ * allocation, which can take milliseconds and synchronise the device, or a process whose device
+ * memory is already owned by another allocator).  Same computation and argument conventions as
+ * sim_rollout_vjp, but without a handle: params and rest_x (HOST, [n_v][3]) are passed directly,
+ * and the spring rest lengths and checkpoint records live in a file-scope device array of
+ * CS_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds until the process
+ * exits.  No cudaMalloc, cudaFree or allocating library routine is called.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) for
+ *     that device; make that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; nothing in it needs to
+ *     start at zero (each call writes every element it reads).  Calls that overlap on the GPU
+ *     (different streams, or different host threads on one device) race on it.
+ *   - Errors: CS_ERR_INVALID_ARG when the checkpoint records of B rollouts of H steps do not fit
+ *     in CS_NOALLOC_SCRATCH_BYTES, plus the errors of sim_create and sim_rollout_vjp. */
+#define CS_NOALLOC_SCRATCH_BYTES (32u << 20)
+cs_status sim_rollout_vjp_noalloc(const cs_params* params, const double* rest_x, int B, int H,
+                                  const void* q0, const void* u, const void* dL_dtraj,
+                                  const cs_loss* loss, void* L, void* dL_du, void* dL_dq0,
+                                  int32_t* status, void* stream);
+
 /* Number of kernel launches the library made on the calling thread since the last call
  * (instrumentation for benchmarks). */
 int64_t cs_launch_count(void);

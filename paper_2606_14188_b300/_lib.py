@@ -63,6 +63,10 @@ SIGNATURES = {
     "sim_rollout_vjp": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.POINTER(cs_loss), C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sim_rollout_vjp_noalloc": (C.c_int, [C.POINTER(cs_params), C.POINTER(C.c_double), C.c_int,
+                                          C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.POINTER(cs_loss), C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
     "sim_linearize": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "cs_launch_count": (C.c_int64, []),
