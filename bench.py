@@ -210,7 +210,7 @@ def run_ours(args):
     from paper_2606_14188_b300.sim import Sim
     from paper_2606_14188_b300 import _lib
 
-    w = scenes.workload(2)
+    w = scenes.workload(2, B=args.rollouts)
     sc, B, H = w["scene"], w["B"], w["H"]
     nv = sc["params"]["n_nodes"]
     k = sc["params"]["checkpoint_every"]
@@ -297,7 +297,7 @@ def run_ours(args):
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=1e3 * t / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                    config=dict(workload=WORKLOAD, rollouts=B, nodes=nv, horizon=H,
+                    config=dict(workload=WORKLOAD if B == 1024 else f"rope64_b{B}_h50", rollouts=B, nodes=nv, horizon=H,
                                 checkpoint_every=k, obstacles=nobs, grad_mode="surrogate",
                                 parallelism=f"rollouts sharded, dp{world}",
                                 l2="256 MB write between timed steps, outside the timed intervals"),
@@ -320,6 +320,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--rollouts", type=int, default=None,
+                    help="rollouts per GPU (default 1024; smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
