@@ -180,6 +180,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_device(fn, steps, flush, stream):
+    """per-call seconds of fn() by CUDA events on the launching stream, L2 flushed between calls
+    outside the timed intervals"""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) * 1e-3 for a, b in zip(starts, ends)]
+
+
+def max_over_ranks(t, world):
+    if world > 1:
+        import torch
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt)
+    return t
+
+
+def measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def linearize_leg(args, flush, stream, world):
+    """sim_linearize on 256 nominal trajectories of a 40-node rope (horizon 20): every A_t, B_t of
+    the smooth step written to HBM.  Bound: HBM writes of A and B."""
+    import torch
+    from paper_2606_14188_b300.sim import Sim
+    w = scenes.workload(4)
+    sc, B, H = w["scene"], w["B"], w["H"]
+    nv = sc["params"]["n_nodes"]
+    nq = 3 * nv + 6
+    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H)
+    q0 = torch.tensor(w["q0"], dtype=torch.float32, device="cuda")
+    V = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
+    Z, _, _ = s.rollout(q0, V)                   # nominal trajectories (not timed)
+    for _ in range(max(1, args.warmup)):
+        A, Bm, st = s.linearize(Z, V)
+    per = time_device(lambda: s.linearize(Z, V), args.steps, flush, stream)
+    t = max_over_ranks(sum(per), world)
+    avg = t / args.steps
+    out_bytes = B * H * (nq * nq + nq * 6) * 4
+    in_bytes = B * (H + 1) * nq * 4 + B * H * 6 * 4
+    peak, src = measured_hbm_peak()
+    gbs = (out_bytes + in_bytes) / avg / 1e9
+    return dict(workload=f"rope{nv}_b{B}_h{H}", value=world * B * H / avg, unit="step Jacobians/s",
+                ms_per_step=1e3 * avg, bytes_per_launch=out_bytes + in_bytes,
+                status_nonzero=int(torch.count_nonzero(st).item()),
+                roofline=dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=gbs / peak,
+                              traffic=None, peak_source=f"{src} HBM copy bandwidth"))
+
+
 def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -275,6 +337,12 @@ def run_ours(args):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         te = float(tt)
 
+    # forward alone (the same rollouts, nonsmooth forward, trajectory written)
+    t_fwd = max_over_ranks(sum(time_device(lambda: s.rollout(q0, U), args.steps, flush, stream)),
+                           world)
+    # linearisation workload: 256 nominal trajectories of a 40-node rope, horizon 20
+    lin = linearize_leg(args, flush, stream, world)
+
     if rank == 0:
         node_steps = B * nv * H
         value = world * args.steps * node_steps / t
@@ -305,6 +373,10 @@ def run_ours(args):
                     e2e=dict(value=e2e_value, unit=UNIT,
                              h2d_bytes_per_step=int(q0.numel() * 4 + U.numel() * 4),
                              d2h_bytes_per_step=int(B * 4 + B * H * 6 * 4)),
+                    forward=dict(value=world * args.steps * node_steps / t_fwd, unit=UNIT,
+                                 ms_per_step=1e3 * t_fwd / args.steps,
+                                 what="sim_rollout alone on the same rollouts"),
+                    linearize=lin,
                     gpu_launches=launches, clocks=clocks,
                     status_nonzero=int(np.count_nonzero(status)),
                     per_step_ms=[round(x * 1e3, 4) for x in per])

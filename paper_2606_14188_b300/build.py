@@ -23,7 +23,10 @@ LIB = os.path.join(PKG, "libcordsim.so")
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# single precision divide and square root take the hardware approximations (within 2 ulp) instead
+# of the IEEE-rounded sequences; double precision is unaffected
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-prec-div=false", "-prec-sqrt=false", "-Xcompiler", "-fPIC",
+         "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _headers():

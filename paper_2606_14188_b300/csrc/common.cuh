@@ -57,6 +57,10 @@ __device__ __forceinline__ R wmax(R v) {
   return v;
 }
 
+// reciprocal square root (hardware approximation, within 2 ulp in single precision)
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
 template <typename R>
 __device__ __forceinline__ R dot3(const R* a, const R* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
@@ -301,7 +305,7 @@ __device__ __forceinline__ bool chol6(R* T) {
 #pragma unroll
     for (int k = 0; k < j; ++k) s -= T[j * 6 + k] * T[j * 6 + k];
     ok = ok && (s > R(0));
-    R iv = R(1) / sqrt(s > R(0) ? s : R(1));
+    R iv = rsq(s > R(0) ? s : R(1));
     T[j * 6 + j] = iv;
 #pragma unroll
     for (int i = j + 1; i < 6; ++i) {

@@ -27,7 +27,7 @@ namespace cs {
 template <typename R>
 struct WS {
   int NP;                     // pair slots (32 PPL)
-  R *T, *B, *V, *r;           // cyclic-reduction storage [36][NP] x3, [6][NP]
+  R *T, *B, *V, *r;           // cyclic-reduction storage, row strides CR_LDM (blocks), CR_LDV (vector)
   R *s, *z, *phi, *nrm;       // contact pairs: [(o*2+h)*3+c][NP] for vectors, [(o*2+h)][NP]
   R *pm, *pg, *prz;           // per-pair Newton terms of the current iteration: M (6), g (3), r_z (3)
   R *misc;                    // [64]
@@ -48,9 +48,9 @@ enum {
 };
 
 __host__ __device__ inline size_t ws_size(int NP, int nobs, int H, bool lin) {
-  size_t s = (size_t)NP * (3 * 36 + 6) + (size_t)nobs * 2 * NP * 22 + 64;
+  size_t s = (size_t)NP * (3 * CR_LDM + CR_LDV) + (size_t)nobs * 2 * NP * 22 + 64;
   s = ((s + 3) & ~(size_t)3) + 12 * (size_t)H;
-  if (lin) s += (size_t)NP * 3 * 36 + 2 * 6 * (size_t)NP;
+  if (lin) s += (size_t)NP * 3 * CR_LDM + 2 * 6 * (size_t)NP;
   return s;
 }
 
@@ -60,8 +60,8 @@ __device__ __forceinline__ WS<R> ws_carve(R* base, int NP, int nobs, int H, bool
   w.NP = NP;
   R* p = base;
   auto take = [&](size_t n) { R* q = p; p += n; return q; };
-  w.T = take(36 * (size_t)NP); w.B = take(36 * (size_t)NP); w.V = take(36 * (size_t)NP);
-  w.r = take(6 * (size_t)NP);
+  w.T = take(CR_LDM * (size_t)NP); w.B = take(CR_LDM * (size_t)NP); w.V = take(CR_LDM * (size_t)NP);
+  w.r = take(CR_LDV * (size_t)NP);
   w.s = take((size_t)nobs * 2 * 3 * NP); w.z = take((size_t)nobs * 2 * 3 * NP);
   w.phi = take((size_t)nobs * 2 * NP); w.nrm = take((size_t)nobs * 2 * 3 * NP);
   w.pm = take((size_t)nobs * 2 * 6 * NP); w.pg = take((size_t)nobs * 2 * 3 * NP);
@@ -70,7 +70,7 @@ __device__ __forceinline__ WS<R> ws_carve(R* base, int NP, int nobs, int H, bool
   p = base + (((size_t)(p - base) + 3) & ~(size_t)3);
   w.u = take(6 * (size_t)H); w.ub = take(6 * (size_t)H);
   if (lin) {
-    w.T2 = take(36 * (size_t)NP); w.B2 = take(36 * (size_t)NP); w.V2 = take(36 * (size_t)NP);
+    w.T2 = take(CR_LDM * (size_t)NP); w.B2 = take(CR_LDM * (size_t)NP); w.V2 = take(CR_LDM * (size_t)NP);
     w.xs = take(6 * (size_t)NP); w.Dn = take(6 * (size_t)NP);
   } else {
     w.T2 = w.B2 = w.V2 = w.xs = w.Dn = nullptr;
@@ -97,6 +97,17 @@ struct Lane {
   R Ls[PPL][3];               // rest lengths (2p-1,2p), (2p,2p+1), (2p+1,2p+2)
   R Lb[PPL][4];               // rest lengths (2p-2,2p), (2p-1,2p+1), (2p,2p+2), (2p+1,2p+3)
 };
+
+// every register array of the lane starts at zero: slots past the chain (p >= npair) are never
+// assembled but take part in warp reductions (max step, slope) and must contribute nothing
+template <typename R, int PPL>
+__device__ __forceinline__ void zero_lane(Lane<R, PPL>& L) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k)
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+      L.x0[k][e] = L.xm[k][e] = L.xp[k][e] = L.dx[k][e] = L.Dl[k][e] = L.pv[k][e] = L.F[k][e] = R(0);
+}
 
 // value of the neighbouring pairs p - 1 and p + 1 of every slot
 template <typename R, int PPL>
@@ -282,8 +293,8 @@ __device__ __forceinline__ void hessvec(const Scene<R>& S, const Lane<R, PPL>& L
 
 template <typename R>
 __device__ __forceinline__ void put_rows(WS<R>& w, int p, const R T[36], const R Bc[36]) {
-  st_lower(w.T, w.NP, p, T);
-  st36(w.B, w.NP, p, Bc);
+  st_lower(w.T, p, T);
+  st36(w.B, p, Bc);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -353,7 +364,7 @@ __device__ __forceinline__ void put_rhs(const Scene<R>& S, WS<R>& w, const R v[P
     const int p = lane + 32 * k;
     if (p >= S.npair) continue;
 #pragma unroll
-    for (int e = 0; e < 6; ++e) w.r[e * w.NP + p] = (2 * p + e / 3 < S.nv) ? sign * v[k][e] : R(0);
+    for (int e = 0; e < 6; ++e) w.r[cr_v(p, e)] = (2 * p + e / 3 < S.nv) ? sign * v[k][e] : R(0);
   }
 }
 
@@ -363,7 +374,7 @@ __device__ __forceinline__ void get_rhs(const Scene<R>& S, const WS<R>& w, R v[P
   for (int k = 0; k < PPL; ++k) {
     const int p = lane + 32 * k;
 #pragma unroll
-    for (int e = 0; e < 6; ++e) v[k][e] = (p < S.npair && 2 * p + e / 3 < S.nv) ? w.r[e * w.NP + p] : R(0);
+    for (int e = 0; e < 6; ++e) v[k][e] = (p < S.npair && 2 * p + e / 3 < S.nv) ? w.r[cr_v(p, e)] : R(0);
   }
 }
 
@@ -374,7 +385,12 @@ __device__ __forceinline__ void assemble_P(const Scene<R>& S, Lane<R, PPL>& L, W
 #pragma unroll
   for (int k = 0; k < PPL; ++k) {
     const int p = lane + 32 * k;
-    if (p >= S.npair) continue;
+    if (p >= S.npair) {
+      if (keepF)
+#pragma unroll
+        for (int e = 0; e < 6; ++e) L.F[k][e] = R(0);
+      continue;
+    }
     R T[36], Bc[36], F[6];
     assemble1(S, L, dxm, dxp, w.misc, k, p, proj, T, Bc, F);
     put_rows(w, p, T, Bc);
@@ -399,10 +415,10 @@ __device__ __forceinline__ int stage1_newton(const Scene<R>& S, Lane<R, PPL>& L,
       assemble_P(S, L, w, dxm, dxp, attempt == 1, attempt == 0, lane);
       if (attempt == 0) put_rhs<R, PPL>(S, w, L.F, R(-1), lane);
       __syncwarp();
-      ok = cr_factor(w.T, w.B, w.V, S.npair, w.NP, lane);
+      ok = cr_factor(w.T, w.B, w.V, S.npair, lane);
     }
     if (!ok) { *iters = it + 1; return ST_NOTPD; }
-    cr_solve(w.T, w.B, w.V, w.r, S.npair, w.NP, lane);
+    cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
     get_rhs<R, PPL>(S, w, L.pv, lane);
     R pm = R(0), sl = R(0);
     bool bad = false;
@@ -680,16 +696,16 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
             rhs[0] = rhs[1] = rhs[2] = R(0);
           }
 #pragma unroll
-          for (int i = 0; i < 3; ++i) w.r[(3 * h + i) * NP + p] = rhs[i];
+          for (int i = 0; i < 3; ++i) w.r[cr_v(p, 3 * h + i)] = rhs[i];
         }
         put_rows(w, p, T, Bc);
       }
       __syncwarp();
-      if (cr_factor(w.T, w.B, w.V, S.npair, NP, lane)) break;
+      if (cr_factor(w.T, w.B, w.V, S.npair, lane)) break;
       if (proj) { *iters = it + 1; return ST_NOTPD; }
       proj = true;
     }
-    cr_solve(w.T, w.B, w.V, w.r, S.npair, NP, lane);
+    cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
     get_rhs<R, PPL>(S, w, L.pv, lane);            // dDelta
     // step length to the cone boundaries
     R amin = R(1e30), dmax = R(0);
@@ -834,7 +850,7 @@ __device__ __forceinline__ void adjoint_step(const Scene<R>& S, Lane<R, PPL>& L,
   R mu[PPL][6];
   put_rhs<R, PPL>(S, w, xb, R(1), lane);
   __syncwarp();
-  cr_solve(w.T, w.B, w.V, w.r, S.npair, w.NP, lane);
+  cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
   get_rhs<R, PPL>(S, w, mu, lane);
   R mum[PPL][6], mup[PPL][6], Dlm[PPL][6], Dlp[PPL][6], dxm[PPL][6], dxp[PPL][6];
   nbr<R, PPL>(mu, mum, mup, lane);
@@ -900,8 +916,8 @@ __device__ __forceinline__ void adjoint_step(const Scene<R>& S, Lane<R, PPL>& L,
   assemble_P(S, L, w, dxm, dxp, false, false, lane);
   put_rhs<R, PPL>(S, w, xs, R(1), lane);
   __syncwarp();
-  cr_factor(w.T, w.B, w.V, S.npair, w.NP, lane);
-  cr_solve(w.T, w.B, w.V, w.r, S.npair, w.NP, lane);
+  cr_factor(w.T, w.B, w.V, S.npair, lane);
+  cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
   R nu[PPL][6];
   get_rhs<R, PPL>(S, w, nu, lane);
   // xbar = w nu + grasp terms; gbar, ubar
@@ -1066,6 +1082,7 @@ __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int
   const int nq = 3 * S.nv + 6;
   WS<R> w = ws_carve<R>(reinterpret_cast<R*>(cs_smem), 32 * PPL, S.nobs, H, false);
   Lane<R, PPL> L;
+  zero_lane(L);
   load_rest(S, L, lane);
   const bool smooth = S.fwd_mode == CS_SMOOTH;
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
@@ -1108,6 +1125,7 @@ __global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, 
   const int nseg = (H + k - 1) / k;
   WS<R> w = ws_carve<R>(reinterpret_cast<R*>(cs_smem), 32 * PPL, S.nobs, H, false);
   Lane<R, PPL> L;
+  zero_lane(L);
   load_rest(S, L, lane);
   const bool fwd_smooth = S.grad_mode == CS_CONSISTENT;
   enum { FWD = 0, RECOMP = 1, BACK = 2 };
@@ -1243,6 +1261,7 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
   R* tv1 = w.Dn + 6 * (size_t)NP;
   R* tv2 = tv1 + (size_t)6 * NP * 32;
   Lane<R, PPL> L;
+  zero_lane(L);
   load_rest(S, L, lane);
   const int ndir = nq + 6;
   for (int job = blockIdx.x; job < B * H; job += gridDim.x) {
@@ -1254,7 +1273,7 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
     int ni, ii;
     int st = sim_step(S, L, w, lane, true, &ni, &ii);
     // keep H2's factorisation; factorise H1 at x* into the first slot
-    for (int i = lane; i < 36 * NP; i += 32) { w.T2[i] = w.T[i]; w.B2[i] = w.B[i]; w.V2[i] = w.V[i]; }
+    for (int i = lane; i < CR_LDM * NP; i += 32) { w.T2[i] = w.T[i]; w.B2[i] = w.B[i]; w.V2[i] = w.V[i]; }
     R dxm[PPL][6], dxp[PPL][6];
     nbr<R, PPL>(L.dx, dxm, dxp, lane);
     assemble_P(S, L, w, dxm, dxp, false, false, lane);
@@ -1268,7 +1287,7 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
       }
     }
     __syncwarp();
-    if (!cr_factor(w.T, w.B, w.V, N, NP, lane)) st |= ST_NOTPD;
+    if (!cr_factor(w.T, w.B, w.V, N, lane)) st |= ST_NOTPD;
     const R* d = w.misc + M_D;
     const R* c = w.misc + M_C;
     const R* u = w.misc + M_U;

@@ -171,6 +171,47 @@ def test_rope40_linearize_vs_oracle():
             assert np.linalg.norm(Bm[b, t] - Br[t]) <= 1e-3 * np.linalg.norm(Br[t])
 
 
+def test_rope40_fp32_rollout_and_vjp_vs_oracle():
+    """FP32 with a partly filled warp (20 node pairs on 32 lanes)."""
+    w = scenes.workload(4)
+    sc, H = w["scene"], w["H"]
+    B = 4
+    osc = _oscene(sc)
+    s = _sim(sc, 4, B, H)
+    q0, U = _t(w["q0"][:B], 4), _t(w["U"][:B], 4)
+    traj, _, st = s.rollout(q0, U)
+    Lv, dU, _, st2 = s.rollout_vjp(q0, U)
+    assert np.all(st.cpu().numpy() == 0) and np.all(st2.cpu().numpy() == 0)
+    for b in range(B):
+        ref, ost, _ = osim.rollout(osc, w["q0"][b], w["U"][b], "hard")
+        assert ost == 0
+        assert rel_state(traj[b].cpu().numpy(), ref) <= TOL_STATE32, b
+        g = ograd.rollout_vjp(osc, w["q0"][b], w["U"][b], "surrogate")
+        assert abs(float(Lv[b]) - g["L"]) <= TOL_STATE32 * abs(g["L"])
+        check_grad(dU[b].cpu().numpy(), g["dL_du"], TOL_GRAD32, COS32)
+
+
+def test_rope40_linearize_full_size_sampled():
+    """The launch the benchmark times (256 nominal trajectories x horizon 20, 40-node rope, the
+    nominal states rolled out by the oracle), sampled: A_t, B_t at 12 (b, t) against the oracle."""
+    w = scenes.workload(4)
+    sc, B, H = w["scene"], w["B"], w["H"]
+    osc = _oscene(sc)
+    V = w["U"]
+    Z = np.stack([osim.rollout(osc, w["q0"][b], V[b], "hard")[0] for b in range(B)])
+    picks = [0, 85, 170, 255]
+    s = _sim(sc, 4, B, H)
+    A, Bm, st = s.linearize(_t(Z, 4), _t(V, 4))
+    st = st.cpu().numpy()
+    assert np.count_nonzero(st) == 0
+    for b in picks:
+        for t in (0, 7, H - 1):
+            Ar, Br = ograd.SmoothStepJacobian(osc, Z[b, t], V[b, t]).jacobians()
+            Ag, Bg = A[b, t].cpu().numpy(), Bm[b, t].cpu().numpy()
+            assert np.linalg.norm(Ag - Ar) <= 1e-3 * np.linalg.norm(Ar), (b, t)
+            assert np.linalg.norm(Bg - Br) <= 1e-3 * np.linalg.norm(Br), (b, t)
+
+
 def test_rope20_fp64_linearize_vs_oracle():
     w = scenes.workload(1)
     sc = w["scene"]
