@@ -182,6 +182,81 @@ cs_status sim_rollout_vjp_noalloc(const cs_params* params, const double* rest_x,
                                   const cs_loss* loss, void* L, void* dL_du, void* dL_dq0,
                                   int32_t* status, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Served plan solves (MPC).  The paper's planners optimise a nominal control sequence by
+ * gradients of the simulator at every MPC update (Sec. 4.2 nominal trajectory generation;
+ * Sec. 5 planning experiments); the optimiser is not printed.  A plan solve here:
+ *   candidates  u^(0) = clip(w), u^(r) = clip(w + sigma eps^(r)), r = 1..R-1, w the warm start,
+ *               eps^(r)[t][d] standard normals from Philox4x32-10 (Salmon et al., SC 2011)
+ *               keyed by (seed, r, 6 t + d) through Box-Muller;
+ *   iterations  G evaluations (forward + surrogate-gradient adjoint of every candidate, the
+ *               planning loss cs_loss); after evaluations 1..G-1 a bias-corrected Adam step
+ *               (beta 0.9 / 0.999, eps 1e-8, step lr) and the clip to [-u_max, u_max] on every
+ *               candidate whose rollout succeeded;
+ *   result      the evaluated candidate with the lowest loss over all evaluations (ties: earlier
+ *               evaluation, then lower r).
+ * A server owns one CUDA stream and a scheduler thread.  Requests wait in FIFO order until a
+ * slot and device memory for them are free, then join the running set at the next tick; every
+ * tick runs one evaluation (one packed forward + adjoint launch over the candidates of every
+ * running request, then the selection and Adam kernels), replayed from a captured CUDA graph
+ * while the running set does not change.  Results are independent of what else is running.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct cs_mpc cs_mpc;
+
+typedef struct {
+  size_t mem_budget_bytes;  /* device memory for running requests; 0 = half the free memory   */
+  int max_slots;            /* most requests running at once (0 = 64)                         */
+  int real_bytes;           /* 4 (FP32) or 8 (FP64)                                           */
+  int batched;              /* 1: continuous batching; 0: one request at a time, no graphs
+                               (the one-launch-per-request form)                              */
+  int use_graphs;           /* 1: replay captured CUDA graphs while the running set is stable */
+  int autotune;             /* 1: time the packed launch's warps per CTA at creation          */
+  const char* tuner_cache;  /* file holding tuned launch shapes (read, then written); or NULL  */
+} cs_mpc_config;
+
+typedef struct {
+  cs_params params;         /* scene and solver settings (real_bytes, max_* are ignored)      */
+  const double* rest_x;     /* HOST [n_nodes][3] rest positions                               */
+  const double* q0;         /* HOST [n_q] state to plan from                                  */
+  const double* warm;       /* HOST [H][6] warm start, or NULL: the session's previous plan
+                               shifted by one step (last control repeated), else zeros        */
+  cs_loss loss;             /* planning loss                                                  */
+  int H, R, G;              /* horizon, candidates, evaluations                               */
+  double lr, sigma, u_max;  /* Adam step, candidate spread, control bound                     */
+  uint64_t seed;
+  uint64_t session_id;      /* nonzero: keep this plan on the device for the session's next
+                               request                                                        */
+} cs_mpc_request;
+
+typedef struct {
+  double* u;                /* caller-owned HOST [H][6]: the plan (filled by mpc_poll)        */
+  double L;                 /* its loss                                                       */
+  int32_t status;           /* 0; else CS_ST_* bits of the last evaluation when no candidate
+                               ever succeeded (u is then the warm start)                      */
+  int32_t best_iter;        /* evaluation (1..G) and candidate of the plan                    */
+  int32_t best_candidate;
+  int64_t t_submit_ns, t_start_ns, t_done_ns;  /* steady clock: submitted, admitted, result on
+                                                  the host                                    */
+} cs_mpc_result;
+
+/* Create a server on the current device.  Errors: CS_ERR_INVALID_ARG, CS_ERR_OOM, CS_ERR_CUDA. */
+cs_status mpc_create(const cs_mpc_config* config, cs_mpc** out);
+/* Queue a plan solve; the request and its host arrays are copied before the call returns.
+ * Errors: CS_ERR_INVALID_ARG (sizes, unsupported scene, a request larger than the memory
+ * budget). */
+cs_status mpc_submit(cs_mpc* mpc, const cs_mpc_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms (0: do not wait, < 0: no limit) for a result.  CS_OK fills `out` and
+ * forgets the ticket; CS_ERR_PENDING if it is not done yet; CS_ERR_CANCELLED; CS_ERR_INVALID_ARG
+ * for an unknown ticket; CS_ERR_CUDA if the server's stream failed. */
+cs_status mpc_poll(cs_mpc* mpc, uint64_t ticket, int timeout_ms, cs_mpc_result* out);
+/* Cancel a queued or running solve (a running one stops at the next tick boundary). */
+cs_status mpc_cancel(cs_mpc* mpc, uint64_t ticket);
+/* Stop the scheduler (running solves are abandoned) and release everything. */
+cs_status mpc_destroy(cs_mpc* mpc);
+/* Counters of a server: ticks run, graph launches, kernel launches, graphs captured. */
+cs_status mpc_stats(cs_mpc* mpc, int64_t* ticks, int64_t* graph_launches, int64_t* kernel_launches,
+                    int64_t* graphs_built);
+
 /* Number of kernel launches the library made on the calling thread since the last call
  * (instrumentation for benchmarks). */
 int64_t cs_launch_count(void);

@@ -52,6 +52,26 @@ class cs_loss(C.Structure):
                 ("w_u", C.c_double)]
 
 
+class cs_mpc_config(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_slots", C.c_int), ("real_bytes", C.c_int),
+                ("batched", C.c_int), ("use_graphs", C.c_int), ("autotune", C.c_int),
+                ("tuner_cache", C.c_char_p)]
+
+
+class cs_mpc_request(C.Structure):
+    _fields_ = [("params", cs_params), ("rest_x", C.POINTER(C.c_double)),
+                ("q0", C.POINTER(C.c_double)), ("warm", C.POINTER(C.c_double)), ("loss", cs_loss),
+                ("H", C.c_int), ("R", C.c_int), ("G", C.c_int),
+                ("lr", C.c_double), ("sigma", C.c_double), ("u_max", C.c_double),
+                ("seed", C.c_uint64), ("session_id", C.c_uint64)]
+
+
+class cs_mpc_result(C.Structure):
+    _fields_ = [("u", C.POINTER(C.c_double)), ("L", C.c_double), ("status", C.c_int32),
+                ("best_iter", C.c_int32), ("best_candidate", C.c_int32),
+                ("t_submit_ns", C.c_int64), ("t_start_ns", C.c_int64), ("t_done_ns", C.c_int64)]
+
+
 # exported symbols and their signatures: (restype, argtypes)
 SIGNATURES = {
     "sim_create": (C.c_int, [C.POINTER(cs_params), C.POINTER(C.c_double), C.POINTER(C.c_void_p)]),
@@ -69,6 +89,13 @@ SIGNATURES = {
                                           C.c_void_p, C.c_void_p]),
     "sim_linearize": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mpc_create": (C.c_int, [C.POINTER(cs_mpc_config), C.POINTER(C.c_void_p)]),
+    "mpc_submit": (C.c_int, [C.c_void_p, C.POINTER(cs_mpc_request), C.POINTER(C.c_uint64)]),
+    "mpc_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(cs_mpc_result)]),
+    "mpc_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "mpc_destroy": (C.c_int, [C.c_void_p]),
+    "mpc_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                            C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "cs_launch_count": (C.c_int64, []),
     "cs_last_error": (C.c_char_p, []),
 }

@@ -8,8 +8,9 @@
 //   B  6x6 coupling of row p with row p - s at the current reduction level
 //   V  6x6 work block
 //   r  6-vector right-hand side / solution
-// Storage: entry e = 6 i + j of row p's block at X[p * CR_LDM + e], entry a of its vector at
-// r[p * CR_LDV + a].  Both strides are odd, so a warp with one lane per row touches 32 distinct
+// Storage: entry e = 6 i + j of row p's B or V block at X[p * CR_LDM + e], the lower triangle
+// of T packed row by row at T[p * CR_LDT + i (i + 1) / 2 + j], entry a of the vector at
+// r[p * CR_LDV + a].  All strides are odd, so a warp with one lane per row touches 32 distinct
 // banks.  The factorisation and the solve are called (not inlined) from every solver phase so
 // that one copy of their code serves the whole kernel.
 // Odd-even reduction: at level s the rows k = s (mod 2s) are eliminated in parallel and each
@@ -22,9 +23,11 @@
 namespace cs {
 
 constexpr int CR_LDM = 37;   // row stride of a 6x6 block
+constexpr int CR_LDT = 21 + 2;  // row stride of a packed lower triangle (21 entries; odd)
 constexpr int CR_LDV = 7;    // row stride of a 6-vector
 
 __device__ __forceinline__ int cr_m(int p, int e) { return p * CR_LDM + e; }
+__device__ __forceinline__ int cr_t(int p, int i, int j) { return p * CR_LDT + i * (i + 1) / 2 + j; }
 __device__ __forceinline__ int cr_v(int p, int a) { return p * CR_LDV + a; }
 
 template <typename R>
@@ -39,20 +42,21 @@ __device__ __forceinline__ void st36(R* X, int row, const R* a) {
   for (int e = 0; e < 36; ++e) X[cr_m(row, e)] = a[e];
 }
 
+// lower triangle of a diagonal block: packed in shared memory, row-major 6x6 in registers
 template <typename R>
-__device__ __forceinline__ void ld_lower(const R* X, int row, R* a) {
+__device__ __forceinline__ void ld_lower(const R* T, int row, R* a) {
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int k = 0; k <= i; ++k) a[i * 6 + k] = X[cr_m(row, i * 6 + k)];
+    for (int k = 0; k <= i; ++k) a[i * 6 + k] = T[cr_t(row, i, k)];
 }
 
 template <typename R>
-__device__ __forceinline__ void st_lower(R* X, int row, const R* a) {
+__device__ __forceinline__ void st_lower(R* T, int row, const R* a) {
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int k = 0; k <= i; ++k) X[cr_m(row, i * 6 + k)] = a[i * 6 + k];
+    for (int k = 0; k <= i; ++k) T[cr_t(row, i, k)] = a[i * 6 + k];
 }
 
 // Factorise in place; lane i handles rows i, i + 32, ... of each reduction level.

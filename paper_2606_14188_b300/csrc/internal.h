@@ -28,13 +28,13 @@ struct cs_sim {
 namespace csi {
 
 
+// the kernels' scene from the parameters, the device rest lengths and an optional loss
 template <typename R>
-cs::Scene<R> make_scene(const cs_sim* s, const cs_loss* loss) {
+cs::Scene<R> make_scene_from(const cs_params& P, const void* d_L1, const void* d_L2, const cs_loss* loss) {
   cs::Scene<R> S;
   std::memset(&S, 0, sizeof(S));
-  const cs_params& P = s->P;
-  S.nv = s->nv;
-  S.npair = s->npair;
+  S.nv = P.n_nodes;
+  S.npair = (P.n_nodes + 1) / 2;
   S.nobs = P.n_obstacles;
   S.grasp[0] = P.grasp_node[0];
   S.grasp[1] = P.grasp_node[1];
@@ -67,8 +67,8 @@ cs::Scene<R> make_scene(const cs_sim* s, const cs_loss* loss) {
     S.ob_type[o] = P.obstacles[o].type;
     for (int i = 0; i < 6; ++i) S.ob[o][i] = (R)P.obstacles[o].p[i];
   }
-  S.L1 = static_cast<const R*>(s->d_L1);
-  S.L2 = static_cast<const R*>(s->d_L2);
+  S.L1 = static_cast<const R*>(d_L1);
+  S.L2 = static_cast<const R*>(d_L2);
   if (loss) {
     S.has_loss = 1;
     S.n_goal = loss->n_goal;
@@ -82,6 +82,11 @@ cs::Scene<R> make_scene(const cs_sim* s, const cs_loss* loss) {
     S.w_u = (R)loss->w_u;
   }
   return S;
+}
+
+template <typename R>
+cs::Scene<R> make_scene(const cs_sim* s, const cs_loss* loss) {
+  return make_scene_from<R>(s->P, s->d_L1, s->d_L2, loss);
 }
 
 inline size_t smem_bytes(const cs_sim* s, int H, bool lin) {

@@ -27,7 +27,7 @@ namespace cs {
 template <typename R>
 struct WS {
   int NP;                     // pair slots (32 PPL)
-  R *T, *B, *V, *r;           // cyclic-reduction storage, row strides CR_LDM (blocks), CR_LDV (vector)
+  R *T, *B, *V, *r;           // cyclic-reduction storage, row strides CR_LDT, CR_LDM, CR_LDM, CR_LDV
   R *s, *z, *phi, *nrm;       // contact pairs: [(o*2+h)*3+c][NP] for vectors, [(o*2+h)][NP]
   R *pm, *pg, *prz;           // per-pair Newton terms of the current iteration: M (6), g (3), r_z (3)
   R *misc;                    // [64]
@@ -48,9 +48,9 @@ enum {
 };
 
 __host__ __device__ inline size_t ws_size(int NP, int nobs, int H, bool lin) {
-  size_t s = (size_t)NP * (3 * CR_LDM + CR_LDV) + (size_t)nobs * 2 * NP * 22 + 64;
+  size_t s = (size_t)NP * (CR_LDT + 2 * CR_LDM + CR_LDV) + (size_t)nobs * 2 * NP * 22 + 64;
   s = ((s + 3) & ~(size_t)3) + 12 * (size_t)H;
-  if (lin) s += (size_t)NP * 3 * CR_LDM + 2 * 6 * (size_t)NP;
+  if (lin) s += (size_t)NP * (CR_LDT + 2 * CR_LDM) + 2 * 6 * (size_t)NP;
   return s;
 }
 
@@ -60,7 +60,7 @@ __device__ __forceinline__ WS<R> ws_carve(R* base, int NP, int nobs, int H, bool
   w.NP = NP;
   R* p = base;
   auto take = [&](size_t n) { R* q = p; p += n; return q; };
-  w.T = take(CR_LDM * (size_t)NP); w.B = take(CR_LDM * (size_t)NP); w.V = take(CR_LDM * (size_t)NP);
+  w.T = take(CR_LDT * (size_t)NP); w.B = take(CR_LDM * (size_t)NP); w.V = take(CR_LDM * (size_t)NP);
   w.r = take(CR_LDV * (size_t)NP);
   w.s = take((size_t)nobs * 2 * 3 * NP); w.z = take((size_t)nobs * 2 * 3 * NP);
   w.phi = take((size_t)nobs * 2 * NP); w.nrm = take((size_t)nobs * 2 * 3 * NP);
@@ -70,7 +70,7 @@ __device__ __forceinline__ WS<R> ws_carve(R* base, int NP, int nobs, int H, bool
   p = base + (((size_t)(p - base) + 3) & ~(size_t)3);
   w.u = take(6 * (size_t)H); w.ub = take(6 * (size_t)H);
   if (lin) {
-    w.T2 = take(CR_LDM * (size_t)NP); w.B2 = take(CR_LDM * (size_t)NP); w.V2 = take(CR_LDM * (size_t)NP);
+    w.T2 = take(CR_LDT * (size_t)NP); w.B2 = take(CR_LDM * (size_t)NP); w.V2 = take(CR_LDM * (size_t)NP);
     w.xs = take(6 * (size_t)NP); w.Dn = take(6 * (size_t)NP);
   } else {
     w.T2 = w.B2 = w.V2 = w.xs = w.Dn = nullptr;
@@ -1110,140 +1110,151 @@ __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int
   }
 }
 
-// forward + checkpointed adjoint.  ws: per-rollout workspace of checkpoint records.
+// Forward rollout + checkpointed adjoint of one rollout by one warp.  Pointers are this
+// rollout's: q0 [n_q], U [H][6], dLdtraj [H+1][n_q] (or null), Lout (or null), dLdu [H][6],
+// dLdq0 [n_q] (or null), status (or null), ck: its workspace of checkpoint records.
 // The steps run through one loop over a schedule -- the H forward steps, then for each segment
 // (last to first) the recomputed steps and the backward steps -- so that the step and its
 // adjoint are each inlined once.
+template <typename R, int PPL>
+__device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R, PPL>& L, int lane, int H,
+                                            const R* q0, const R* U, const R* dLdtraj, R* Lout, R* dLdu,
+                                            R* dLdq0, int32_t* status, R* ck) {
+  const int nq = 3 * S.nv + 6;
+  const int rl = nq + 6 + 3 * S.nv;
+  const int k = S.ckpt;
+  const int nseg = (H + k - 1) / k;
+  const bool fwd_smooth = S.grad_mode == CS_CONSISTENT;
+  enum { FWD = 0, RECOMP = 1, BACK = 2 };
+  R* seg = ck + (size_t)(nseg + 1) * rl;     // segment records [k][rl]
+  load_q(S, L, w, q0, lane);
+  load_controls(w.u, U, 6 * H, lane);
+  __syncwarp();
+  store_rec(S, L, w, ck, lane);
+  int st = 0;
+  R Lacc = R(0);
+  R xb[PPL][6];
+  zero6<R, PPL>(xb);
+  // schedule state
+  int kind = FWD, t = 0, sgi = nseg - 1, t0 = 0, t1 = 0;
+  while (true) {
+    if (kind == BACK) {
+      load_rec(S, L, w, seg + (size_t)(t - t0) * rl, lane);
+      // start the smooth re-solve at the forward step's stage-1 solution (record of q_{t+1})
+      load_rec_dx(S, L, t + 1 < t1 ? seg + (size_t)(t + 1 - t0) * rl : ck + (size_t)(sgi + 1) * rl, lane);
+    }
+    if (lane < 6) w.misc[M_U + lane] = w.u[6 * t + lane];
+    __syncwarp();
+    int ni, ii;
+    st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK);
+    if (kind != BACK) {
+      advance_state(S, L, w, lane);
+      if (kind == FWD) {
+        if ((t + 1) % k == 0 || t == H - 1) store_rec(S, L, w, ck + (size_t)((t + k) / k) * rl, lane);
+        if (S.has_loss) Lacc += penalty(S, L, xb, false, lane);
+      } else {
+        store_rec(S, L, w, seg + (size_t)(t + 1 - t0) * rl, lane);
+      }
+    } else {
+      adjoint_step(S, L, w, xb, lane);
+      if (lane < 6)
+        w.ub[6 * t + lane] = w.misc[M_UB + lane] + (S.has_loss ? R(2) * S.w_u * w.u[6 * t + lane] : R(0));
+    }
+    // seeds dL/dq_t of the state the adjoint reaches next (q_H after the forward, q_t after a
+    // backward step); x0 holds that state in both cases
+    const bool seed_now = (kind == FWD && t == H - 1) || kind == BACK;
+    if (seed_now) {
+      if (kind == FWD) {
+        if (lane < 6) w.misc[M_GB + lane] = R(0);
+        __syncwarp();
+        if (S.has_loss) {
+#pragma unroll
+          for (int kk = 0; kk < PPL; ++kk) {
+            const int p = lane + 32 * kk;
+            for (int gi = 0; gi < S.n_goal; ++gi) {
+              const int j = S.goal[gi];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                if (j != 2 * p + h) continue;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                  const R e = L.x0[kk][3 * h + i] - S.goal_pos[gi][i];
+                  Lacc += S.w_goal * e * e;
+                  xb[kk][3 * h + i] += R(2) * S.w_goal * e;
+                }
+              }
+            }
+          }
+          for (int i = lane; i < 6 * H; i += 32) Lacc += S.w_u * w.u[i] * w.u[i];
+        }
+      }
+      const int ts = kind == FWD ? H : t;        // index of the seeded state
+      if (ts >= 1 && S.has_loss) penalty(S, L, xb, true, lane);
+      if (dLdtraj) {
+        const R* sd = dLdtraj + (size_t)ts * nq;
+#pragma unroll
+        for (int kk = 0; kk < PPL; ++kk) {
+          const int p = lane + 32 * kk;
+#pragma unroll
+          for (int e = 0; e < 6; ++e)
+            if (2 * p + e / 3 < S.nv) xb[kk][e] += sd[6 * p + e];
+        }
+        if (lane < 6) w.misc[M_GB + lane] += sd[3 * S.nv + lane];
+      }
+      __syncwarp();
+    }
+    // next schedule entry
+    bool start_seg = false;
+    if (kind == FWD) {
+      if (++t == H) start_seg = true;
+    } else if (kind == RECOMP) {
+      if (++t == t1 - 1) { kind = BACK; t = t1 - 1; }
+    } else {
+      if (--t < t0) { if (--sgi < 0) break; start_seg = true; }
+    }
+    if (start_seg) {
+      t0 = sgi * k;
+      t1 = min(t0 + k, H);
+      load_rec(S, L, w, ck + (size_t)sgi * rl, lane);
+      store_rec(S, L, w, seg, lane);
+      if (t1 - t0 > 1) { kind = RECOMP; t = t0; } else { kind = BACK; t = t0; }
+    }
+  }
+  __syncwarp();
+  store_controls(dLdu, w.ub, 6 * H, lane);
+  if (dLdq0) {
+#pragma unroll
+    for (int kk = 0; kk < PPL; ++kk) {
+      const int p = lane + 32 * kk;
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+        if (2 * p + e / 3 < S.nv) dLdq0[6 * p + e] = xb[kk][e];
+    }
+    if (lane < 6) dLdq0[3 * S.nv + lane] = w.misc[M_GB + lane];
+  }
+  Lacc = wsum(Lacc);
+  if (lane == 0) {
+    if (Lout) *Lout = Lacc;
+    if (status) *status = st;
+  }
+  __syncwarp();
+}
+
 template <typename R, int PPL>
 __global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, const R* q0,
                                                      const R* U, const R* dLdtraj, R* Lout, R* dLdu,
                                                      R* dLdq0, int32_t* status, R* ws, size_t ws_stride) {
   const int lane = threadIdx.x;
   const int nq = 3 * S.nv + 6;
-  const int rl = nq + 6 + 3 * S.nv;
-  const int k = S.ckpt;
-  const int nseg = (H + k - 1) / k;
   WS<R> w = ws_carve<R>(reinterpret_cast<R*>(cs_smem), 32 * PPL, S.nobs, H, false);
   Lane<R, PPL> L;
   zero_lane(L);
   load_rest(S, L, lane);
-  const bool fwd_smooth = S.grad_mode == CS_CONSISTENT;
-  enum { FWD = 0, RECOMP = 1, BACK = 2 };
-  for (int b = blockIdx.x; b < B; b += gridDim.x) {
-    R* ck = ws + (size_t)b * ws_stride;        // checkpoint records [nseg + 1][rl]
-    R* seg = ck + (size_t)(nseg + 1) * rl;     // segment records [k][rl]
-    load_q(S, L, w, q0 + (size_t)b * nq, lane);
-    load_controls(w.u, U + (size_t)b * H * 6, 6 * H, lane);
-    __syncwarp();
-    store_rec(S, L, w, ck, lane);
-    int st = 0;
-    R Lacc = R(0);
-    R xb[PPL][6];
-    zero6<R, PPL>(xb);
-    // schedule state
-    int kind = FWD, t = 0, sgi = nseg - 1, t0 = 0, t1 = 0;
-    while (true) {
-      if (kind == BACK) {
-        load_rec(S, L, w, seg + (size_t)(t - t0) * rl, lane);
-        // start the smooth re-solve at the forward step's stage-1 solution (record of q_{t+1})
-        load_rec_dx(S, L, t + 1 < t1 ? seg + (size_t)(t + 1 - t0) * rl : ck + (size_t)(sgi + 1) * rl, lane);
-      }
-      if (lane < 6) w.misc[M_U + lane] = w.u[6 * t + lane];
-      __syncwarp();
-      int ni, ii;
-      st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK);
-      if (kind != BACK) {
-        advance_state(S, L, w, lane);
-        if (kind == FWD) {
-          if ((t + 1) % k == 0 || t == H - 1) store_rec(S, L, w, ck + (size_t)((t + k) / k) * rl, lane);
-          if (S.has_loss) Lacc += penalty(S, L, xb, false, lane);
-        } else {
-          store_rec(S, L, w, seg + (size_t)(t + 1 - t0) * rl, lane);
-        }
-      } else {
-        adjoint_step(S, L, w, xb, lane);
-        if (lane < 6)
-          w.ub[6 * t + lane] = w.misc[M_UB + lane] + (S.has_loss ? R(2) * S.w_u * w.u[6 * t + lane] : R(0));
-      }
-      // seeds dL/dq_t of the state the adjoint reaches next (q_H after the forward, q_t after a
-      // backward step); x0 holds that state in both cases
-      const bool seed_now = (kind == FWD && t == H - 1) || kind == BACK;
-      if (seed_now) {
-        if (kind == FWD) {
-          if (lane < 6) w.misc[M_GB + lane] = R(0);
-          __syncwarp();
-          if (S.has_loss) {
-#pragma unroll
-            for (int kk = 0; kk < PPL; ++kk) {
-              const int p = lane + 32 * kk;
-              for (int gi = 0; gi < S.n_goal; ++gi) {
-                const int j = S.goal[gi];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  if (j != 2 * p + h) continue;
-#pragma unroll
-                  for (int i = 0; i < 3; ++i) {
-                    const R e = L.x0[kk][3 * h + i] - S.goal_pos[gi][i];
-                    Lacc += S.w_goal * e * e;
-                    xb[kk][3 * h + i] += R(2) * S.w_goal * e;
-                  }
-                }
-              }
-            }
-            for (int i = lane; i < 6 * H; i += 32) Lacc += S.w_u * w.u[i] * w.u[i];
-          }
-        }
-        const int ts = kind == FWD ? H : t;        // index of the seeded state
-        if (ts >= 1 && S.has_loss) penalty(S, L, xb, true, lane);
-        if (dLdtraj) {
-          const R* sd = dLdtraj + ((size_t)b * (H + 1) + ts) * nq;
-#pragma unroll
-          for (int kk = 0; kk < PPL; ++kk) {
-            const int p = lane + 32 * kk;
-#pragma unroll
-            for (int e = 0; e < 6; ++e)
-              if (2 * p + e / 3 < S.nv) xb[kk][e] += sd[6 * p + e];
-          }
-          if (lane < 6) w.misc[M_GB + lane] += sd[3 * S.nv + lane];
-        }
-        __syncwarp();
-      }
-      // next schedule entry
-      bool start_seg = false;
-      if (kind == FWD) {
-        if (++t == H) start_seg = true;
-      } else if (kind == RECOMP) {
-        if (++t == t1 - 1) { kind = BACK; t = t1 - 1; }
-      } else {
-        if (--t < t0) { if (--sgi < 0) break; start_seg = true; }
-      }
-      if (start_seg) {
-        t0 = sgi * k;
-        t1 = min(t0 + k, H);
-        load_rec(S, L, w, ck + (size_t)sgi * rl, lane);
-        store_rec(S, L, w, seg, lane);
-        if (t1 - t0 > 1) { kind = RECOMP; t = t0; } else { kind = BACK; t = t0; }
-      }
-    }
-    __syncwarp();
-    store_controls(dLdu + (size_t)b * H * 6, w.ub, 6 * H, lane);
-    if (dLdq0) {
-#pragma unroll
-      for (int kk = 0; kk < PPL; ++kk) {
-        const int p = lane + 32 * kk;
-#pragma unroll
-        for (int e = 0; e < 6; ++e)
-          if (2 * p + e / 3 < S.nv) dLdq0[(size_t)b * nq + 6 * p + e] = xb[kk][e];
-      }
-      if (lane < 6) dLdq0[(size_t)b * nq + 3 * S.nv + lane] = w.misc[M_GB + lane];
-    }
-    Lacc = wsum(Lacc);
-    if (lane == 0) {
-      if (Lout) Lout[b] = Lacc;
-      if (status) status[b] = st;
-    }
-    __syncwarp();
-  }
+  for (int b = blockIdx.x; b < B; b += gridDim.x)
+    vjp_rollout<R, PPL>(S, w, L, lane, H, q0 + (size_t)b * nq, U + (size_t)b * H * 6,
+                        dLdtraj ? dLdtraj + (size_t)b * (H + 1) * nq : nullptr, Lout ? Lout + b : nullptr,
+                        dLdu + (size_t)b * H * 6, dLdq0 ? dLdq0 + (size_t)b * nq : nullptr,
+                        status ? status + b : nullptr, ws + (size_t)b * ws_stride);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1273,7 +1284,8 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
     int ni, ii;
     int st = sim_step(S, L, w, lane, true, &ni, &ii);
     // keep H2's factorisation; factorise H1 at x* into the first slot
-    for (int i = lane; i < CR_LDM * NP; i += 32) { w.T2[i] = w.T[i]; w.B2[i] = w.B[i]; w.V2[i] = w.V[i]; }
+    for (int i = lane; i < CR_LDT * NP; i += 32) w.T2[i] = w.T[i];
+    for (int i = lane; i < CR_LDM * NP; i += 32) { w.B2[i] = w.B[i]; w.V2[i] = w.V[i]; }
     R dxm[PPL][6], dxp[PPL][6];
     nbr<R, PPL>(L.dx, dxm, dxp, lane);
     assemble_P(S, L, w, dxm, dxp, false, false, lane);

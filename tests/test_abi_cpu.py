@@ -56,6 +56,32 @@ def test_struct_layout_matches_c():
                     L.cs_loss.goal_pos.offset, L.cs_params.newton_tol.offset]
 
 
+def test_mpc_struct_layout_matches_c():
+    src = r"""
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "cordsim.h"
+    int main(void) {
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cs_mpc_config), sizeof(cs_mpc_request),
+             sizeof(cs_mpc_result), offsetof(cs_mpc_config, tuner_cache), offsetof(cs_mpc_request, loss),
+             offsetof(cs_mpc_request, H), offsetof(cs_mpc_request, session_id),
+             offsetof(cs_mpc_result, best_candidate), offsetof(cs_mpc_result, t_done_ns));
+      return 0;
+    }
+    """
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    vals = [int(v) for v in out]
+    assert vals == [C.sizeof(L.cs_mpc_config), C.sizeof(L.cs_mpc_request), C.sizeof(L.cs_mpc_result),
+                    L.cs_mpc_config.tuner_cache.offset, L.cs_mpc_request.loss.offset,
+                    L.cs_mpc_request.H.offset, L.cs_mpc_request.session_id.offset,
+                    L.cs_mpc_result.best_candidate.offset, L.cs_mpc_result.t_done_ns.offset]
+
+
 def test_argument_errors_without_gpu():
     """Argument errors are reported before any device work (null arguments, bad kinds)."""
     lib = L.lib()
@@ -64,3 +90,8 @@ def test_argument_errors_without_gpu():
     assert b"null" in lib.cs_last_error()
     assert lib.sim_rollout(None, 1, 1, None, None, None, None, None, None) == 1
     assert lib.sim_destroy(None) == 0
+    assert lib.mpc_create(None, C.byref(h)) == 1
+    assert lib.mpc_submit(None, None, None) == 1
+    assert lib.mpc_poll(None, 1, 0, None) == 1
+    assert lib.mpc_cancel(None, 1) == 1
+    assert lib.mpc_destroy(None) == 0

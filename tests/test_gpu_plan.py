@@ -1,0 +1,141 @@
+"""GPU: the served plan solve (mpc_* through the C ABI) against the oracle planner, and the
+serving properties: each result is the same alone and in a mix, under memory admission, with
+graphs; cancellation; session warm starts."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import plan as oplan, sim as osim  # noqa: E402
+from paper_2606_14188_b300 import scenes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _server(**kw):
+    from paper_2606_14188_b300.serve import PlanServer
+    kw.setdefault("mem_budget_bytes", 256 << 20)
+    srv = PlanServer(**kw)
+    poll = srv.poll
+
+    def bounded_poll(ticket, timeout_ms=120000):
+        out = poll(ticket, timeout_ms)
+        assert out is not None or timeout_ms == 0, "no result within the time limit"
+        return out
+    srv.poll = bounded_poll
+    return srv
+
+
+def _oscene(sc):
+    return osim.Scene(sc["params"], sc["rest_x"])
+
+
+@pytest.mark.parametrize("case", [
+    dict(nv=8, spheres=0, H=4, R=3, G=4, lr=0.01, seed=7),
+    dict(nv=13, spheres=1, H=6, R=5, G=3, lr=0.005, seed=11),
+])
+def test_plan_fp64_matches_oracle(case):
+    sc = scenes.rope_scene(case["nv"], n_spheres=case["spheres"], seed=case["seed"])
+    ref = oplan.plan_solve(_oscene(sc), sc["q0"], np.zeros((case["H"], 6)), case["R"], case["G"],
+                           lr=case["lr"], seed=case["seed"])
+    with _server(real_bytes=8) as srv:
+        t = srv.submit(sc, sc["q0"], case["H"], case["R"], case["G"], lr=case["lr"], seed=case["seed"])
+        out = srv.poll(t)
+    assert out["status"] == 0
+    assert (out["best_iter"], out["best_candidate"]) == (ref["it"], ref["r"])
+    assert abs(out["L"] - ref["L"]) <= 1e-8 * abs(ref["L"])
+    np.testing.assert_allclose(out["u"], ref["u"], rtol=0, atol=1e-9)
+
+
+def test_plan_fp32_first_evaluation_vs_oracle():
+    """G = 1: the plan is the best initial candidate (warm start plus counter-based normals)."""
+    sc = scenes.rope_scene(24, n_spheres=1, seed=3)
+    H, R = 8, 12
+    ref = oplan.plan_solve(_oscene(sc), sc["q0"], np.zeros((H, 6)), R, 1, seed=99)
+    with _server(real_bytes=4) as srv:
+        out = srv.poll(srv.submit(sc, sc["q0"], H, R, 1, seed=99))
+    L = np.sort(ref["losses"][0])
+    assert out["status"] == 0 and out["best_iter"] == 1
+    assert abs(out["L"] - ref["L"]) <= 1e-4 * abs(ref["L"])
+    if L[1] - L[0] > 1e-3 * abs(L[0]):
+        assert out["best_candidate"] == ref["r"]
+    cand = oplan.initial_candidates(np.zeros((H, 6)), R, 0.02, 0.05, 99)
+    np.testing.assert_allclose(out["u"], cand[out["best_candidate"]], rtol=0, atol=1e-7)
+
+
+def _mix():
+    reqs = []
+    for i, (nv, H, R) in enumerate([(12, 5, 8), (20, 8, 24), (40, 6, 16), (64, 7, 40), (80, 5, 12),
+                                    (100, 9, 20)]):
+        sc = scenes.rope_scene(nv, n_spheres=1 + (i % 2), seed=100 + i)
+        reqs.append(dict(scene=sc, q0=sc["q0"], H=H, R=R, G=3, seed=1000 + i))
+    return reqs
+
+
+def _run(srv, reqs):
+    ts = [srv.submit(r["scene"], r["q0"], r["H"], r["R"], r["G"], seed=r["seed"]) for r in reqs]
+    return [srv.poll(t) for t in ts]
+
+
+def _same(a, b):
+    assert (a["best_iter"], a["best_candidate"], a["status"]) == (b["best_iter"], b["best_candidate"], b["status"])
+    assert a["L"] == b["L"]
+    assert np.array_equal(a["u"], b["u"])
+
+
+def test_plan_alone_vs_mixed_bit_identical():
+    reqs = _mix()
+    with _server(real_bytes=4, batched=False) as srv:
+        alone = [_run(srv, [r])[0] for r in reqs]
+    with _server(real_bytes=4, batched=True, use_graphs=True) as srv:
+        mixed = _run(srv, reqs)
+        st = srv.stats()
+    for a, b in zip(alone, mixed):
+        _same(a, b)
+    assert st["graphs_built"] >= 1 and st["graph_launches"] >= 1
+    # overlapping: the six requests were served in fewer ticks than one after another
+    assert st["ticks"] < sum(r["G"] for r in reqs)
+
+
+def test_plan_memory_admission_and_staggered_arrivals():
+    """A budget that holds about two requests: the others wait for memory, join as it frees,
+    and still give the results they give alone."""
+    reqs = _mix()
+    with _server(real_bytes=4, batched=False) as srv:
+        alone = [_run(srv, [r])[0] for r in reqs]
+    with _server(real_bytes=4, batched=True, mem_budget_bytes=1310720) as srv:
+        ts = []
+        for r in reqs:
+            ts.append(srv.submit(r["scene"], r["q0"], r["H"], r["R"], r["G"], seed=r["seed"]))
+        mixed = [srv.poll(t) for t in ts]
+    for a, b in zip(alone, mixed):
+        _same(a, b)
+        assert b["t_start_ns"] >= b["t_submit_ns"] and b["t_done_ns"] >= b["t_start_ns"]
+
+
+def test_plan_cancel_and_pending():
+    from paper_2606_14188_b300._lib import CordsimError
+    reqs = _mix()
+    with _server(real_bytes=4, batched=True, max_slots=1) as srv:
+        r0, r1 = reqs[3], reqs[1]
+        t0 = srv.submit(r0["scene"], r0["q0"], r0["H"], r0["R"], 6, seed=1)
+        t1 = srv.submit(r1["scene"], r1["q0"], r1["H"], r1["R"], r1["G"], seed=2)
+        assert srv.poll(t1, timeout_ms=0) is None          # queued behind t0
+        srv.cancel(t1)
+        with pytest.raises(CordsimError) as e:
+            srv.poll(t1)
+        assert e.value.code == 8
+        out = srv.poll(t0)
+        assert out["status"] == 0
+
+
+def test_plan_session_warm_start():
+    """A session's next request starts from its previous plan shifted by one step."""
+    sc = scenes.rope_scene(16, n_spheres=0, seed=5)
+    H = 6
+    with _server(real_bytes=4) as srv:
+        first = srv.poll(srv.submit(sc, sc["q0"], H, 8, 3, seed=4, session_id=77))
+        # R = 1, G = 1: the plan is candidate 0, i.e. the warm start itself
+        nxt = srv.poll(srv.submit(sc, sc["q0"], H, 1, 1, seed=4, session_id=77))
+    shifted = np.concatenate([first["u"][1:], first["u"][-1:]])
+    np.testing.assert_array_equal(nxt["u"], shifted)
