@@ -37,6 +37,7 @@ from paper_2606_14188_b300 import scenes, flops  # noqa: E402
 METRIC = "sim+adjoint node-steps/s"
 UNIT = "node-steps/s"
 WORKLOAD = "rope64_b1024_h50"
+BASE_SERVED_SEED = 260614188 + 5
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -242,6 +243,83 @@ def linearize_leg(args, flush, stream, world):
                               traffic=None, peak_source=f"{src} HBM copy bandwidth"))
 
 
+def served_stream(n, seed):
+    """The served workload: n plan solves with rope sizes U{16..128}, horizons U{20..60}, candidates
+    log-uniform in {64, ..., 1024}, 10 evaluations each, Poisson arrival order (times set later)."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        nv = int(rng.integers(16, 129))
+        H = int(rng.integers(20, 61))
+        R = int(2 ** rng.integers(6, 11))
+        sc = scenes.rope_scene(nv, n_spheres=int(rng.integers(1, 3)), n_boxes=int(rng.integers(0, 2)),
+                               seed=seed + 1 + i, sphere_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)))
+        sc["params"]["checkpoint_every"] = max(1, int(round(H ** 0.5)))
+        reqs.append(dict(scene=sc, q0=sc["q0"], H=H, R=R, G=10, seed=seed + 7919 * i, nv=nv))
+    return reqs
+
+
+def serve_stream(reqs, gaps, batched):
+    """Submit reqs with the given inter-arrival gaps [s]; returns (results, makespan [s])."""
+    from paper_2606_14188_b300.serve import PlanServer
+    srv = PlanServer(real_bytes=4, mem_budget_bytes=8 << 30, batched=batched, use_graphs=True)
+    try:
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for r, g in zip(reqs, gaps):
+            due += g
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(due - now, 0.002))
+            tickets.append(srv.submit(r["scene"], r["q0"], r["H"], r["R"], r["G"], seed=r["seed"]))
+        out = [srv.poll(t, -1) for t in tickets]
+        makespan = (max(o["t_done_ns"] for o in out) - min(o["t_submit_ns"] for o in out)) * 1e-9
+        stats = srv.stats()
+    finally:
+        srv.close()
+    return out, makespan, stats
+
+
+def served_leg(args):
+    """Served MPC plan solves: capacity of the batched server on the whole stream at once, then the
+    same stream arriving as a Poisson process at 70 % and 95 % of that capacity, served batched and
+    one request at a time (one launch per kernel per evaluation, no graphs)."""
+    n = args.served_requests
+    reqs = served_stream(n, BASE_SERVED_SEED)
+    node_steps = sum(r["R"] * r["H"] * r["nv"] * r["G"] for r in reqs)
+    out_cap, t_cap, _ = serve_stream(reqs, [0.0] * n, True)
+    cap = n / t_cap
+    rng = np.random.default_rng(BASE_SERVED_SEED + 1)
+    res = dict(workload=f"{n} rope plan solves, nodes U{{16..128}}, horizon U{{20..60}}, "
+                        "candidates log-U{64..1024}, 10 evaluations each, FP32",
+               requests=n, node_steps=node_steps, capacity_solves_per_s=cap,
+               capacity_node_steps_per_s=node_steps / t_cap)
+
+    def lat(out):
+        ms = np.array([(o["t_done_ns"] - o["t_submit_ns"]) * 1e-6 for o in out])
+        return dict(p50_ms=float(np.percentile(ms, 50)), p99_ms=float(np.percentile(ms, 99)))
+
+    same = True
+    for load in (0.7, 0.95):
+        gaps = rng.exponential(1.0 / (load * cap), n)
+        gaps[0] = 0.0
+        ob, tb, sb = serve_stream(reqs, gaps, True)
+        entry = dict(rate_solves_per_s=load * cap,
+                     batched=dict(**lat(ob), throughput_solves_per_s=n / tb, ticks=sb["ticks"],
+                                  graph_launches=sb["graph_launches"]))
+        if load == 0.7:
+            op, tp, sp = serve_stream(reqs, gaps, False)
+            entry["per_request"] = dict(**lat(op), throughput_solves_per_s=n / tp, ticks=sp["ticks"])
+            for a, b in zip(ob, op):
+                same = same and a["L"] == b["L"] and np.array_equal(a["u"], b["u"])
+        res[f"load_{int(load * 100)}"] = entry
+    res["results_identical_batched_vs_per_request"] = bool(same)
+    return res
+
+
 def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -254,12 +332,13 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu:
         cores = os.cpu_count() or 1
         procs = max(1, min(cores, 16))
-        res, wall = oracle_sample(list(range(procs)), None, procs)
+        nroll = 6 * procs
+        res, wall = oracle_sample(list(range(nroll)), None, procs)
         w0 = scenes.workload(2)
-        ns = procs * w0["scene"]["params"]["n_nodes"] * w0["H"]
+        ns = nroll * w0["scene"]["params"]["n_nodes"] * w0["H"]
         cpu = dict(value=ns / wall, unit=UNIT, cores=procs, kind="oracle",
-                   sample=f"{procs} of the 1024 rollouts (full horizon 50, forward + adjoint), one "
-                          f"process per rollout; {wall:.1f} s wall")
+                   sample=f"{nroll} of the 1024 rollouts (full horizon 50, forward + adjoint) on "
+                          f"{procs} processes; {wall:.1f} s wall")
         cres, _ = oracle_sample([0, 341, 682, 1023], 1e-5, 4)
         counts = counts_mean(cres)
 
@@ -342,6 +421,7 @@ def run_ours(args):
                            world)
     # linearisation workload: 256 nominal trajectories of a 40-node rope, horizon 20
     lin = linearize_leg(args, flush, stream, world)
+    served = served_leg(args) if args.served_requests > 0 else None
 
     if rank == 0:
         node_steps = B * nv * H
@@ -376,7 +456,7 @@ def run_ours(args):
                     forward=dict(value=world * args.steps * node_steps / t_fwd, unit=UNIT,
                                  ms_per_step=1e3 * t_fwd / args.steps,
                                  what="sim_rollout alone on the same rollouts"),
-                    linearize=lin,
+                    linearize=lin, served=served,
                     gpu_launches=launches, clocks=clocks,
                     status_nonzero=int(np.count_nonzero(status)),
                     per_step_ms=[round(x * 1e3, 4) for x in per])
@@ -392,6 +472,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--served-requests", type=int, default=48,
+                    help="plan solves in the served stream (0: skip the served leg)")
     ap.add_argument("--rollouts", type=int, default=None,
                     help="rollouts per GPU (default 1024; smaller only for profiling captures)")
     args = ap.parse_args()
