@@ -332,7 +332,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu:
         cores = os.cpu_count() or 1
         procs = max(1, min(cores, 16))
-        nroll = 6 * procs
+        nroll = 16 * procs
         res, wall = oracle_sample(list(range(nroll)), None, procs)
         w0 = scenes.workload(2)
         ns = nroll * w0["scene"]["params"]["n_nodes"] * w0["H"]
