@@ -145,6 +145,8 @@ cs_status sim_rollout_counters(cs_sim* sim, int B, int H, const void* q0, const 
  *   dL_du    [B][H][6] (required)
  *   dL_dq0   [B][n_q] (may be NULL)
  *   status   [B]
+ * A rollout whose status becomes nonzero stops at the failing step: its L is NaN and its dL_du
+ * and dL_dq0 are zero.
  * Errors: as sim_rollout; CS_ERR_INVALID_ARG when both dL_dtraj and loss are NULL. */
 cs_status sim_rollout_vjp(cs_sim* sim, int B, int H, const void* q0, const void* u,
                           const void* dL_dtraj, const cs_loss* loss, void* L, void* dL_du,

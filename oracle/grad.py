@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.sparse as sp
+from numpy.linalg import LinAlgError
 
 from . import sim
 from .sim import SMOOTH, HARD
@@ -73,12 +74,20 @@ class SmoothStepJacobian:
         kc, mu = p["kappa_c"], p["mu"]
         nv, N = sc.nv, sc.n
 
-        # factorizations of dF/dq* and of the stage-2 Newton matrix H2 at the solution
-        self.cb1 = sim.band_factor(sim.stage1_hessian_band(sc, xs, d))
-        W = sim.contact_force_jacobian(sig, n, kc, mu)
-        ab2 = sim.stage1_hessian_band(sc, xs, d)
-        sim.band_add_node_blocks(sc, ab2, np.arange(nv), W.sum(axis=1))
-        self.cb2 = sim.band_factor(ab2)
+        # factorizations of dF/dq* and of the stage-2 Newton matrix H2 at the solution.  When
+        # either is not positive definite (the stage-1 root is a saddle of the potential: an
+        # unstable, buckled equilibrium) the step's Jacobian is reported as undefined (ST_NOTPD).
+        self.defined = False
+        try:
+            self.cb1 = sim.band_factor(sim.stage1_hessian_band(sc, xs, d))
+            W = sim.contact_force_jacobian(sig, n, kc, mu)
+            ab2 = sim.stage1_hessian_band(sc, xs, d)
+            sim.band_add_node_blocks(sc, ab2, np.arange(nv), W.sum(axis=1))
+            self.cb2 = sim.band_factor(ab2)
+        except LinAlgError:
+            self.status |= sim.ST_NOTPD
+            return
+        self.defined = True
 
         # dR/dq*: spring third-derivative part
         dS = xs[sc.b] - xs[sc.a]
@@ -222,6 +231,9 @@ def rollout_vjp(sc: sim.Scene, q0, U, grad_mode="surrogate", dL_dtraj=None, tol=
         jac = SmoothStepJacobian(sc, traj[t], U[t], tol, x_start=xs_fwd[t])
         status |= jac.status
         smooth_counts.append(jac.counts)
+        if not jac.defined:          # no gradient through a step without a defined Jacobian
+            L, dL_du[:], qbar = np.nan, np.nan, np.full_like(qbar, np.nan)
+            break
         qb, ub = jac.vjp(qbar)
         dL_du[t] = ub + dU[t]
         qbar = qb + seeds[t]
@@ -236,5 +248,9 @@ def linearize(sc: sim.Scene, Z, V, tol=sim.TOL_X):
     A = np.zeros((H, sc.nq, sc.nq))
     Bm = np.zeros((H, sc.nq, 6))
     for t in range(H):
-        A[t], Bm[t] = SmoothStepJacobian(sc, Z[t], V[t], tol).jacobians()
+        jac = SmoothStepJacobian(sc, Z[t], V[t], tol)
+        if jac.defined:
+            A[t], Bm[t] = jac.jacobians()
+        else:
+            A[t], Bm[t] = np.nan, np.nan
     return A, Bm

@@ -473,11 +473,16 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
         min 1/2 Delta^T P Delta  s.t.  s_i = A_i Delta_j + phi_i e1 in Q,
     with multipliers z_i in Q (contact forces lam_i = A_i^T z_i) and the centering condition
     s_i o z_i = kappa e, i.e. the relaxed complementarity s^T lam = kappa of the smoothed model.
-    The target is kappa throughout when kappa_final is None (smooth model); otherwise it is
-    lowered each iteration to max(kappa_final, 0.1 <s, z>/m) and the solve ends at the central
-    point of kappa_final.  Each Newton step solves H2 dDelta = rhs with the banded SPD matrix
-    H2 = P + sum_i E_j A_i^T W_i^{-2} A_i E_j^T; steps keep s, z strictly inside Q
-    (fraction to the boundary 0.99).  Returns (Delta, sigma_world, iterations, status)."""
+    The target is kappa throughout when kappa_final is None (smooth model).  Otherwise each
+    iteration is a Mehrotra predictor-corrector step, as in the cited method: the affine
+    direction (target 0) with its largest feasible step alpha_a gives the centring
+    sigma = (1 - alpha_a)^3 and the target max(kappa_final, sigma <s, z>/m), and the combined
+    direction adds the second-order term (W^{-1} ds_a) o (W dz_a) to the complementarity
+    right-hand side.  Once the target has reached kappa_final, plain Newton steps towards that
+    central point follow (no predictor, no correction), and the solve ends there.  Each direction solves
+    H2 dDelta = rhs with the banded SPD matrix H2 = P + sum_i E_j A_i^T W_i^{-2} A_i E_j^T (one
+    factorisation per iteration); steps keep s, z strictly inside Q (fraction to the boundary
+    0.99).  Returns (Delta, sigma_world, iterations, status)."""
     mu = sc.p["mu"]
     nv, no = phi.shape
     Delta = np.zeros((nv, 3))
@@ -498,14 +503,12 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
     z = kappa * jordan_inverse(s)
     m = nv * no
     stalls = 0
+    centring = False        # the target has reached kappa_final
     for it in range(maxit):
-        target = kappa if kappa_final is None else \
-            max(kappa_final, min(kappa, 0.1 * float((s * z).sum()) / m))
         lam_w = np.einsum("joab,joa->job", A, z)
         r_d = stage1_hessian_vec(sc, xs, d, Delta, projected) - lam_w.sum(axis=1)
         r_z = s - np.einsum("joab,jb->joa", A, Delta) - phi[..., None] * e1
         W, Winv, lam = nt_scaling(s, z)
-        d_s = jordan_solve(lam, target * e1 - jordan(lam, lam))
         M = Winv @ Winv
         AMA = np.einsum("joba,jobc,jocd->joad", A, M, A)     # A^T M A
         ab = P_ab.copy()
@@ -526,12 +529,28 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
                 cb = band_factor(ab)
             except LinAlgError:
                 return Delta, None, it, ST_NOTPD
-        g = r_z + np.einsum("joab,job->joa", W, d_s)
-        rhs = -r_d + np.einsum("joba,job->ja", A, np.einsum("joab,job->joa", M, g))
-        dD = band_solve(cb, rhs)
-        ADd = np.einsum("joab,jb->joa", A, dD)
-        dz = np.einsum("joab,job->joa", M, -ADd + np.einsum("joab,job->joa", W, d_s) + r_z)
-        dsv = ADd - r_z
+
+        def direction(d_s):
+            # W^{-1} ds + W dz = d_s, ds = A dDelta - r_z, P dDelta - sum A^T dz = -r_d
+            g = r_z + np.einsum("joab,job->joa", W, d_s)
+            rhs = -r_d + np.einsum("joba,job->ja", A, np.einsum("joab,job->joa", M, g))
+            dD = band_solve(cb, rhs)
+            ADd = np.einsum("joab,jb->joa", A, dD)
+            return dD, ADd - r_z, np.einsum("joab,job->joa", M, g - ADd)
+
+        if kappa_final is None or centring:
+            target = kappa if kappa_final is None else kappa_final
+            corr = 0.0
+        else:
+            _, dsa, dza = direction(-lam)                   # affine direction: target 0
+            alpha_a = min(1.0, float(min(max_step(s, dsa).min(), max_step(z, dza).min())))
+            target = max(kappa_final, (1.0 - alpha_a) ** 3 * float((s * z).sum()) / m)
+            corr = jordan(np.einsum("joab,job->joa", Winv, dsa), np.einsum("joab,job->joa", W, dza))
+            centring = target == kappa_final
+            if centring:
+                corr = 0.0
+        d_s = jordan_solve(lam, target * e1 - jordan(lam, lam) - corr)
+        dD, dsv, dz = direction(d_s)
         if not (np.all(np.isfinite(dD)) and np.all(np.isfinite(dz))):
             return Delta, None, it, ST_NONFINITE
         alpha = min(1.0, 0.99 * float(min(max_step(s, dsv).min(), max_step(z, dz).min())))

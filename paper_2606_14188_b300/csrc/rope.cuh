@@ -628,24 +628,12 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
   }
   int stalls = 0;
   bool proj = false;
+  bool centring = false;      // the target has reached kfinal: plain centring steps from now on
   for (int it = 0; it < S.ipm_max; ++it) {
-    R target = kappa;
-    if (kfinal >= R(0)) {
-      R gap = R(0);
-#pragma unroll
-      for (int k = 0; k < PPL; ++k) {
-        const int p = lane + 32 * k;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (2 * p + h >= S.nv) continue;
-          for (int o = 0; o < nobs; ++o)
-            for (int c = 0; c < 3; ++c) gap += w.s[cv(o, h, c, p, NP)] * w.z[cv(o, h, c, p, NP)];
-        }
-      }
-      gap = wsum(gap);
-      target = fmax(kfinal, fmin(kappa, R(0.1) * gap / mm));
-    }
-    const bool final_target = kfinal < R(0) || target == kfinal;
+    // predictor-corrector iteration (towards kfinal, not yet centring): assemble with the affine
+    // right-hand side (target 0); otherwise with the fixed target
+    const bool pc = kfinal >= R(0) && !centring;
+    R target = kfinal < R(0) ? kappa : kfinal;
     R Dlm[PPL][6], Dlp[PPL][6];
     nbr<R, PPL>(L.Dl, Dlm, Dlp, lane);
     // assemble H2 and the right-hand side -P D + sum A^T (z + M g), g = r_z + W d_s.  If H2 is
@@ -666,7 +654,7 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
             const R D[3] = {L.Dl[k][3 * h], L.Dl[k][3 * h + 1], L.Dl[k][3 * h + 2]};
             for (int o = 0; o < nobs; ++o) {
               R A[9], M[9], rz[3], Wds[3];
-              pair_terms(S, w, o, h, p, D, target, A, M, rz, Wds);
+              pair_terms(S, w, o, h, p, D, pc ? R(0) : target, A, M, rz, Wds);
               const R g0 = rz[0] + Wds[0], g1 = rz[1] + Wds[1], g2 = rz[2] + Wds[2];
               w.pm[cm6(o, h, 0, p, NP)] = M[0]; w.pm[cm6(o, h, 1, p, NP)] = M[1];
               w.pm[cm6(o, h, 2, p, NP)] = M[2]; w.pm[cm6(o, h, 3, p, NP)] = M[4];
@@ -706,7 +694,92 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
       proj = true;
     }
     cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
-    get_rhs<R, PPL>(S, w, L.pv, lane);            // dDelta
+    get_rhs<R, PPL>(S, w, L.pv, lane);            // dDelta (affine when pc)
+    if (pc) {
+      // affine step length and duality measure -> centring target
+      R aa = R(1e30), gap = R(0);
+#pragma unroll
+      for (int k = 0; k < PPL; ++k) {
+        const int p = lane + 32 * k;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (2 * p + h >= S.nv) continue;
+          const R dD[3] = {L.pv[k][3 * h], L.pv[k][3 * h + 1], L.pv[k][3 * h + 2]};
+          for (int o = 0; o < nobs; ++o) {
+            R dsa[3], dza[3], sv[3], zv[3];
+            pair_step(S, w, o, h, p, dD, dsa, dza);
+            for (int a = 0; a < 3; ++a) {
+              sv[a] = w.s[cv(o, h, a, p, NP)];
+              zv[a] = w.z[cv(o, h, a, p, NP)];
+              gap += sv[a] * zv[a];
+            }
+            aa = fmin(aa, fmin(soc_max_step(sv, dsa), soc_max_step(zv, dza)));
+          }
+        }
+      }
+      aa = fmin(R(1), -wmax(-aa));
+      gap = wsum(gap);
+      const R om = R(1) - aa;
+      target = fmax(kfinal, om * om * om * gap / mm);
+      centring = target == kfinal;
+      // combined right-hand side: d_s = lam^-1 o (target e - lam o lam - (W^-1 ds_a) o (W dz_a)),
+      // the second-order term dropped once the target is kfinal; same factorisation
+#pragma unroll
+      for (int k = 0; k < PPL; ++k) {
+        const int p = lane + 32 * k;
+        if (p >= S.npair) continue;
+        R PD[6];
+        hessvec(S, L, dxm, dxp, L.Dl, Dlm, Dlp, w.misc, k, p, proj, PD);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          R rhs[3] = {-PD[3 * h], -PD[3 * h + 1], -PD[3 * h + 2]};
+          if (2 * p + h < S.nv) {
+            const R dD[3] = {L.pv[k][3 * h], L.pv[k][3 * h + 1], L.pv[k][3 * h + 2]};
+            for (int o = 0; o < nobs; ++o) {
+              R dsa[3], dza[3], sv[3], zv[3], A[9], W[9], Wi[9], lam[3];
+              pair_step(S, w, o, h, p, dD, dsa, dza);
+              pair_frame(w, o, h, p, S.mu, A);
+              for (int a = 0; a < 3; ++a) { sv[a] = w.s[cv(o, h, a, p, NP)]; zv[a] = w.z[cv(o, h, a, p, NP)]; }
+              nt_scaling(sv, zv, W, Wi, lam);
+              R c3[3] = {R(0), R(0), R(0)};
+              if (!centring) {
+                R a1[3], a2[3];
+                for (int a = 0; a < 3; ++a) {
+                  a1[a] = Wi[a * 3] * dsa[0] + Wi[a * 3 + 1] * dsa[1] + Wi[a * 3 + 2] * dsa[2];
+                  a2[a] = W[a * 3] * dza[0] + W[a * 3 + 1] * dza[1] + W[a * 3 + 2] * dza[2];
+                }
+                c3[0] = a1[0] * a2[0] + a1[1] * a2[1] + a1[2] * a2[2];
+                c3[1] = a1[0] * a2[1] + a2[0] * a1[1];
+                c3[2] = a1[0] * a2[2] + a2[0] * a1[2];
+              }
+              const R r3[3] = {target - (lam[0] * lam[0] + lam[1] * lam[1] + lam[2] * lam[2]) - c3[0],
+                               R(-2) * lam[0] * lam[1] - c3[1], R(-2) * lam[0] * lam[2] - c3[2]};
+              R ds[3];
+              jordan_solve(lam, r3, ds);
+              R g[3], zg[3];
+              const R m6[6] = {w.pm[cm6(o, h, 0, p, NP)], w.pm[cm6(o, h, 1, p, NP)], w.pm[cm6(o, h, 2, p, NP)],
+                               w.pm[cm6(o, h, 3, p, NP)], w.pm[cm6(o, h, 4, p, NP)], w.pm[cm6(o, h, 5, p, NP)]};
+              const R M[9] = {m6[0], m6[1], m6[2], m6[1], m6[3], m6[4], m6[2], m6[4], m6[5]};
+              for (int a = 0; a < 3; ++a)
+                g[a] = w.prz[cv(o, h, a, p, NP)] + W[a * 3] * ds[0] + W[a * 3 + 1] * ds[1] + W[a * 3 + 2] * ds[2];
+              for (int a = 0; a < 3; ++a) {
+                w.pg[cv(o, h, a, p, NP)] = g[a];
+                zg[a] = zv[a] + M[a * 3] * g[0] + M[a * 3 + 1] * g[1] + M[a * 3 + 2] * g[2];
+              }
+              for (int i = 0; i < 3; ++i) rhs[i] += A[i] * zg[0] + A[3 + i] * zg[1] + A[6 + i] * zg[2];
+            }
+          } else {
+            rhs[0] = rhs[1] = rhs[2] = R(0);
+          }
+#pragma unroll
+          for (int i = 0; i < 3; ++i) w.r[cr_v(p, 3 * h + i)] = rhs[i];
+        }
+      }
+      __syncwarp();
+      cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
+      get_rhs<R, PPL>(S, w, L.pv, lane);          // dDelta (combined)
+    }
+    const bool final_target = kfinal < R(0) || target == kfinal;
     // step length to the cone boundaries
     R amin = R(1e30), dmax = R(0);
     bool bad = false;
@@ -839,7 +912,7 @@ __device__ __forceinline__ void advance_state(const Scene<R>& S, Lane<R, PPL>& L
 //   out: xb = xbar (adjoint of x), misc GB = gbar, misc UB = ubar
 // ------------------------------------------------------------------------------------------
 template <typename R, int PPL>
-__device__ __forceinline__ void adjoint_step(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, R xb[PPL][6], int lane) {
+__device__ __forceinline__ int adjoint_step(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, R xb[PPL][6], int lane) {
   const R mu_f = S.mu;
   const R kappa = S.kc;
   const R* d = w.misc + M_D;
@@ -916,7 +989,9 @@ __device__ __forceinline__ void adjoint_step(const Scene<R>& S, Lane<R, PPL>& L,
   assemble_P(S, L, w, dxm, dxp, false, false, lane);
   put_rhs<R, PPL>(S, w, xs, R(1), lane);
   __syncwarp();
-  cr_factor(w.T, w.B, w.V, S.npair, lane);
+  // not positive definite: the stage-1 root is a saddle of the potential (a buckled, unstable
+  // equilibrium); the step's Jacobian is reported as undefined
+  if (!cr_factor(w.T, w.B, w.V, S.npair, lane)) return ST_NOTPD;
   cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
   R nu[PPL][6];
   get_rhs<R, PPL>(S, w, nu, lane);
@@ -947,6 +1022,7 @@ __device__ __forceinline__ void adjoint_step(const Scene<R>& S, Lane<R, PPL>& L,
         }
   }
   __syncwarp();
+  return 0;
 }
 
 // penalty part of the planning loss at the state x0: value (lane share) and seeds added to sd
@@ -1147,6 +1223,7 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
     __syncwarp();
     int ni, ii;
     st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK);
+    if (st) break;                 // a failed step: the rollout's loss and gradient are undefined
     if (kind != BACK) {
       advance_state(S, L, w, lane);
       if (kind == FWD) {
@@ -1156,7 +1233,8 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
         store_rec(S, L, w, seg + (size_t)(t + 1 - t0) * rl, lane);
       }
     } else {
-      adjoint_step(S, L, w, xb, lane);
+      st |= adjoint_step(S, L, w, xb, lane);
+      if (st) break;
       if (lane < 6)
         w.ub[6 * t + lane] = w.misc[M_UB + lane] + (S.has_loss ? R(2) * S.w_u * w.u[6 * t + lane] : R(0));
     }
@@ -1221,6 +1299,13 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
     }
   }
   __syncwarp();
+  if (st) {                        // failed rollout: L = NaN, gradients zero
+    for (int i = lane; i < 6 * H; i += 32) w.ub[i] = R(0);
+    zero6<R, PPL>(xb);
+    if (lane < 6) w.misc[M_GB + lane] = R(0);
+    Lacc = sizeof(R) == 4 ? R(nanf("")) : R(nan(""));
+    __syncwarp();
+  }
   store_controls(dLdu, w.ub, 6 * H, lane);
   if (dLdq0) {
 #pragma unroll

@@ -16,6 +16,9 @@ Per-operation counts (flops, an FMA counted as 2) of the formulas the method eva
   contact pair: barrier merit evaluation .................... 25
   spring third-derivative contraction ....................... 30
   contact pair adjoint product ............................. 70
+  contact pair: predictor step, scaling, second-order term .. 90
+A predictor-corrector barrier iteration of the nonsmooth stage 2 adds a second solve with the same
+factorisation, a second residual and the per-pair predictor terms.
 """
 from __future__ import annotations
 
@@ -38,6 +41,12 @@ def barrier_iter_per_node(nobs: int, springs_per_node: float = 2.0) -> float:
     return assembly + linalg + merit
 
 
+def pc_barrier_iter_per_node(nobs: int, springs_per_node: float = 2.0) -> float:
+    """barrier iteration of the nonsmooth stage 2 (Mehrotra predictor-corrector)"""
+    extra = 3 * SOLVE_PER_DOF + springs_per_node * 24 + nobs * 90
+    return barrier_iter_per_node(nobs, springs_per_node) + extra
+
+
 def adjoint_per_node(nobs: int, springs_per_node: float = 2.0) -> float:
     solves = 2 * 3 * SOLVE_PER_DOF
     refactor = 3 * FACT_PER_DOF + springs_per_node * (40 + 36)
@@ -50,7 +59,7 @@ def rollout_vjp_flops_per_node_step(counts: dict, nobs: int, k: int) -> float:
       fwd_newton, fwd_ipm   (nonsmooth forward),
       sm_newton, sm_ipm     (smooth re-solve of the backward).
     The forward is run twice except at checkpoints (recompute of k-1 of every k steps)."""
-    fwd = counts["fwd_newton"] * newton_iter_per_node() + counts["fwd_ipm"] * barrier_iter_per_node(nobs)
+    fwd = counts["fwd_newton"] * newton_iter_per_node() + counts["fwd_ipm"] * pc_barrier_iter_per_node(nobs)
     recompute = fwd * (k - 1) / k
     back = counts["sm_newton"] * newton_iter_per_node() + counts["sm_ipm"] * barrier_iter_per_node(nobs) \
         + adjoint_per_node(nobs)

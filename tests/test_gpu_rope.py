@@ -129,6 +129,10 @@ def test_rope64_full_batch_sampled():
     Lv, dU, _, st = s.rollout_vjp(_t(w["q0"], 4), _t(w["U"], 4), want_dq0=False)
     st = st.cpu().numpy()
     assert np.count_nonzero(st) <= B // 16, np.unique(st, return_counts=True)
+    # a failed rollout stops at its failing step: L is NaN, the gradient zero
+    fl = st != 0
+    assert np.all(np.isnan(Lv.cpu().numpy()[fl])) and np.all(dU.cpu().numpy()[fl] == 0)
+    assert np.all(np.isfinite(Lv.cpu().numpy()[~fl])) and np.all(np.isfinite(dU.cpu().numpy()[~fl]))
     osc = _oscene(sc)
     for b in (0, 517, 777, B - 1):
         ref = ograd.rollout_vjp(osc, w["q0"][b], w["U"][b], "surrogate")
@@ -144,7 +148,7 @@ def test_rope64_deterministic():
     a = s.rollout_vjp(_t(q0, 4), _t(U, 4))
     b = s.rollout_vjp(_t(q0, 4), _t(U, 4))
     for x, y in zip(a, b):
-        assert torch.equal(x, y)
+        assert torch.equal(x.isnan(), y.isnan()) and torch.equal(x.nan_to_num(), y.nan_to_num())
 
 
 # ------------------------------------------------------------------------------------------
@@ -303,3 +307,22 @@ def test_argument_errors_and_empty_batch():
         s.rollout(_t(scenes.batch_q0(sc, 1), 4), _t(np.zeros((1, 6, 6)), 4))   # H > max_horizon
     traj, qH, st = s.rollout(_t(np.zeros((0, s.nq)), 4), _t(np.zeros((0, 5, 6)), 4))
     assert qH.shape == (0, s.nq)
+
+
+@pytest.mark.parametrize("rb", [4, 8])
+def test_saddle_root_flagged_like_the_oracle(rb):
+    """A straight chain compressed past Euler buckling (stage-1 root = saddle): the adjoint has
+    no defined step Jacobian; both sides flag CS_ST_NOTPD (the GPU's L is NaN, gradients 0)."""
+    p = scenes.default_params("rope")
+    L0 = 0.4
+    X0 = np.array([[0.0, 0.0, 1.0], [L0, 0.0, 1.0], [2 * L0, 0.0, 1.0]])
+    p.update(n_nodes=3, node_mass=1e-3, k_stretch=500.0, k_bend=0.0, gravity=(0, 0, 0),
+             obstacles=[], grasp_nodes=(0, 2), grad_mode="consistent", fwd_mode="smooth")
+    sc = dict(params=p, rest_x=X0)
+    q0 = np.concatenate([X0.ravel(), X0[0], X0[2]])[None]
+    u = np.array([[[0.02, 0.0, 0.0, -0.02, 0.0, 0.0]]])
+    ref = ograd.rollout_vjp(_oscene(sc), q0[0], u[0], "consistent")
+    s = _sim(sc, rb, 1, 1)
+    Lv, dU, _, st = s.rollout_vjp(_t(q0, rb), _t(u, rb))
+    assert ref["status"] & osim.ST_NOTPD and int(st[0]) & osim.ST_NOTPD
+    assert np.isnan(float(Lv[0])) and float(dU.abs().max()) == 0.0

@@ -572,3 +572,27 @@ def test_infeasible_cone_set_is_flagged():
     qp, st = sim.step(sc, q, np.zeros(6), sim.HARD, info=info)
     assert st & sim.ST_CONTACT
     assert info["ipm_it"] < 60
+
+
+def test_saddle_root_has_no_defined_step_jacobian():
+    """Three nodes on a line, the end nodes held, no gravity, the grippers pushed towards each
+    other: by symmetry stage 1 returns the straight, compressed chain, whose transverse stiffness
+    w + 2 k (1 - L/l) is negative once the compression is large enough (Euler buckling): the root
+    is a saddle of the potential, dF/dq* is indefinite and the step's Jacobian is reported as
+    undefined (ST_NOTPD), never as numbers."""
+    L0, k, m, dt = 0.4, 500.0, 1e-3, 0.01
+    X0 = np.array([[0.0, 0.0, 1.0], [L0, 0.0, 1.0], [2 * L0, 0.0, 1.0]])
+    sc, q = rope(3, X0, k_s=k, k_b=0.0, m=m, dt=dt, gravity=(0, 0, 0))
+    delta = 0.02
+    u = np.array([delta, 0.0, 0.0, -delta, 0.0, 0.0])
+    jac = grad.SmoothStepJacobian(sc, q, u)
+    x, _ = sim.split_q(sc, jac.q_next)
+    assert np.allclose(x[:, 1:], X0[:, 1:], atol=1e-12)             # still straight
+    l = x[1, 0] - x[0, 0]
+    assert l < L0 and sc.w + 2 * k * (1 - L0 / l) < 0                 # transverse saddle
+    assert not jac.defined and (jac.status & sim.ST_NOTPD)
+    r = grad.rollout_vjp(sc, q, u[None, :], "consistent")
+    assert (r["status"] & sim.ST_NOTPD) and np.isnan(r["L"])
+    # a small push keeps the chain stable: defined Jacobian
+    jac2 = grad.SmoothStepJacobian(sc, q, u * 1e-3)
+    assert jac2.defined and jac2.status == 0
