@@ -199,12 +199,8 @@ def time_device(fn, steps, flush, stream):
 
 
 def max_over_ranks(t, world):
-    if world > 1:
-        import torch
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt)
-    return t
+    from paper_2606_14188_b300.shard import max_over_ranks as mor
+    return mor(t, "cuda") if world > 1 else t
 
 
 def measured_hbm_peak():
@@ -351,7 +347,8 @@ def run_ours(args):
     from paper_2606_14188_b300.sim import Sim
     from paper_2606_14188_b300 import _lib
 
-    w = scenes.workload(2, B=args.rollouts)
+    # every rank simulates its own share of world x 1024 rollouts (different controls per rank)
+    w = scenes.workload(2, B=args.rollouts, shard=rank)
     sc, B, H = w["scene"], w["B"], w["H"]
     nv = sc["params"]["n_nodes"]
     k = sc["params"]["checkpoint_every"]
@@ -385,10 +382,7 @@ def run_ours(args):
     launches = int(_lib.lib().cs_launch_count())
     per = [a.elapsed_time(b) * 1e-3 for a, b in zip(starts, ends)]
     t = sum(per)
-    if world > 1:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt)
+    t = max_over_ranks(t, world)
     status = st.cpu().numpy()
 
     # end to end through the public call from pinned host buffers
@@ -411,10 +405,7 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     te = e0.elapsed_time(e1) * 1e-3
-    if world > 1:
-        tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        te = float(tt)
+    te = max_over_ranks(te, world)
 
     # forward alone (the same rollouts, nonsmooth forward, trajectory written)
     t_fwd = max_over_ranks(sum(time_device(lambda: s.rollout(q0, U), args.steps, flush, stream)),

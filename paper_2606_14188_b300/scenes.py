@@ -224,31 +224,33 @@ def batch_q0(scene: dict, B: int) -> np.ndarray:
 # precision.  `small=True` shrinks the batch so the oracle can finish in seconds.
 # ------------------------------------------------------------------------------------------
 
-def workload(i: int, B: int | None = None, H: int | None = None) -> dict:
+def workload(i: int, B: int | None = None, H: int | None = None, shard: int = 0) -> dict:
+    """Workload i (1..4).  shard > 0 draws other controls for the same scene (the share of one
+    rank of a multi-GPU run)."""
     seed = BASE_SEED + i
     if i == 1:    # one 20-node rope, FP64, horizon 10, one sphere, uniform controls
         sc = rope_scene(20, n_spheres=1, n_boxes=0, seed=seed)
         B = B or 1; H = H or 10
-        U = controls_uniform(B, H, seed=seed)
+        U = controls_uniform(B, H, seed=seed + 1000003 * shard)
         real = 8
         ck = 1
     elif i == 2:  # 1024 rollouts x 64-node rope, FP32, horizon 50, 2 spheres + 2 boxes
         sc = rope_scene(64, n_spheres=2, n_boxes=2, seed=seed,
                         sphere_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)))
         B = B or 1024; H = H or 50
-        U = controls_normal_clear(sc, B, H, seed=seed)
+        U = controls_normal_clear(sc, B, H, seed=seed + 1000003 * shard)
         real = 4
         ck = 7
     elif i == 3:  # 512 rollouts of a 32x32 cloth, FP32, horizon 30, table + 2 spheres
         sc = cloth_scene(32, 32, n_spheres=2, seed=seed)
         B = B or 512; H = H or 30
-        U = controls_normal_clear(sc, B, H, seed=seed)
+        U = controls_normal_clear(sc, B, H, seed=seed + 1000003 * shard)
         real = 4
         ck = 5
     elif i == 4:  # 256 nominal trajectories of a 40-node rope, horizon 20 (linearisation)
         sc = rope_scene(40, n_spheres=1, n_boxes=0, seed=seed)
         B = B or 256; H = H or 20
-        U = controls_normal_clear(sc, B, H, seed=seed)
+        U = controls_normal_clear(sc, B, H, seed=seed + 1000003 * shard)
         real = 4
         ck = 1
     else:
