@@ -154,7 +154,8 @@ cs_status sim_rollout_vjp(cs_sim* sim, int B, int H, const void* q0, const void*
 
 /* Per-step linearisation of the smooth step about a nominal trajectory (Sec. 4.2: A(z,v),
  * B(z,v)), by forward-mode tangents of the implicit two-stage solve.
- *   z  [B][H+1][n_q] nominal states (only z_0..z_{H-1} are read)
+ *   z  [B][H+1][n_q] nominal states; the stage-1 Newton iteration of step t starts at the node
+ *                     positions of z_{t+1} (the root next to the nominal trajectory)
  *   v  [B][H][6]     nominal controls
  *   A  [B][H][n_q][n_q]  A_t[i][j] = d q_{t+1,i} / d q_{t,j}
  *   Bm [B][H][n_q][6]    B_t[i][j] = d q_{t+1,i} / d u_{t,j}

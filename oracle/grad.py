@@ -243,12 +243,14 @@ def rollout_vjp(sc: sim.Scene, q0, U, grad_mode="surrogate", dL_dtraj=None, tol=
 
 def linearize(sc: sim.Scene, Z, V, tol=sim.TOL_X):
     """A_t = dq_{t+1}/dq_t and B_t = dq_{t+1}/du_t of the smooth step at each nominal (z_t, v_t)
-    (the linearisation A(z, v), B(z, v) consumed by the SLS tube synthesis of Sec. 4.2)."""
+    (the linearisation A(z, v), B(z, v) consumed by the SLS tube synthesis of Sec. 4.2).  The
+    stage-1 Newton iteration of step t starts at the nominal next state z_{t+1}, so the step is
+    linearised at the root next to the nominal trajectory."""
     H = V.shape[0]
     A = np.zeros((H, sc.nq, sc.nq))
     Bm = np.zeros((H, sc.nq, 6))
     for t in range(H):
-        jac = SmoothStepJacobian(sc, Z[t], V[t], tol)
+        jac = SmoothStepJacobian(sc, Z[t], V[t], tol, x_start=np.asarray(Z[t + 1])[: sc.n].reshape(sc.nv, 3))
         if jac.defined:
             A[t], Bm[t] = jac.jacobians()
         else:

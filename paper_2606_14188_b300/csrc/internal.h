@@ -93,7 +93,7 @@ inline size_t smem_bytes(const cs_sim* s, int H, bool lin) {
   const size_t rb = (size_t)s->real_bytes;
   const int NP = s->npair <= 32 ? 32 : 64;
   size_t n = cs::ws_size(NP, s->P.n_obstacles, lin ? 1 : H, lin);
-  if (lin) n += (size_t)2 * 6 * NP * 32;
+  if (lin) n += (size_t)2 * 6 * s->npair * 32 + (size_t)27 * s->nv;
   return n * rb;
 }
 

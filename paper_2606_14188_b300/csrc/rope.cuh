@@ -1354,8 +1354,11 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
   const int NP = 32 * PPL;
   WS<R> w = ws_carve<R>(reinterpret_cast<R*>(cs_smem), NP, S.nobs, 1, true);
   // per-lane tangent vectors in element-major pair layout, interleaved by lane
+  // per-lane tangents, element a of pair row p at ((a * N + p) * 32 + lane), N = npair rows
   R* tv1 = w.Dn + 6 * (size_t)NP;
-  R* tv2 = tv1 + (size_t)6 * NP * 32;
+  R* tv2 = tv1 + (size_t)6 * N * 32;
+  R* Kc = tv2 + (size_t)6 * N * 32;         // [nv nodes][9]
+  R* Ks = Kc + (size_t)9 * nv;              // [nv nodes][2 springs][9]
   Lane<R, PPL> L;
   zero_lane(L);
   load_rest(S, L, lane);
@@ -1365,9 +1368,17 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
     const R* z = Z + ((size_t)b * (H + 1) + t) * nq;
     load_q(S, L, w, z, lane);
     if (lane < 6) w.misc[M_U + lane] = Vc[((size_t)b * H + t) * 6 + lane];
+    // the stage-1 Newton iteration starts at the nominal next state z_{t+1}
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      const int p = lane + 32 * k;
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+        L.dx[k][e] = (2 * p + e / 3 < nv) ? z[nq + 6 * p + e] - z[6 * p + e] : R(0);
+    }
     __syncwarp();
     int ni, ii;
-    int st = sim_step(S, L, w, lane, true, &ni, &ii);
+    int st = sim_step(S, L, w, lane, true, &ni, &ii, true);
     // keep H2's factorisation; factorise H1 at x* into the first slot
     for (int i = lane; i < CR_LDT * NP; i += 32) w.T2[i] = w.T[i];
     for (int i = lane; i < CR_LDM * NP; i += 32) { w.B2[i] = w.B[i]; w.V2[i] = w.V[i]; }
@@ -1391,8 +1402,66 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
     const R* gd = w.misc + M_GD;
     auto node_dx = [&](int j, int i) -> R { return w.xs[(3 * (j & 1) + i) * NP + (j >> 1)]; };
     auto node_D = [&](int j, int i) -> R { return w.Dn[(3 * (j & 1) + i) * NP + (j >> 1)]; };
-    auto T1 = [&](int j, int i) -> R& { return tv1[((size_t)(3 * (j & 1) + i) * NP + (j >> 1)) * 32 + lane]; };
-    auto T2v = [&](int j, int i) -> R& { return tv2[((size_t)(3 * (j & 1) + i) * NP + (j >> 1)) * 32 + lane]; };
+    auto T1 = [&](int j, int i) -> R& { return tv1[((size_t)(3 * (j & 1) + i) * N + (j >> 1)) * 32 + lane]; };
+    auto T2v = [&](int j, int i) -> R& { return tv2[((size_t)(3 * (j & 1) + i) * N + (j >> 1)) * 32 + lane]; };
+    // dR/dx* (direction independent): per node the contact block Kc = sum_o [-W (n n^T + phi N)
+    // + (d lam / d n) N] and per spring (j, j+o) the third-derivative block Ks with
+    // t = Ks (v_b - v_a); each direction then needs only these 3x3 products
+    for (int j = lane; j < nv; j += 32) {
+      R X[3], Dj[3];
+      for (int i = 0; i < 3; ++i) { X[i] = z[3 * j + i] + node_dx(j, i); Dj[i] = node_D(j, i); }
+      R K[9];
+      for (int i = 0; i < 9; ++i) K[i] = R(0);
+      for (int o = 0; o < S.nobs; ++o) {
+        R ph, n[3], Nm[9];
+        obstacle_eval(S.ob_type[o], S.ob[o], X, S.rad, ph, n, Nm);
+        R sg[3];
+        for (int i = 0; i < 3; ++i) sg[i] = Dj[i] + ph * n[i];
+        R lam[3], W[9];
+        cone_force_jac(sg, n, S.kc, S.mu, lam, W);
+        // d lam / d n = c1 (n sg^T + sn I) - c2 a sg^T (as cone_force_dn)
+        const R mu2 = S.mu * S.mu, sn = dot3(n, sg);
+        const R g = (R(1) + mu2) * sn * sn - mu2 * dot3(sg, sg);
+        const R c1 = S.kc * (R(1) + mu2) / g, c2 = R(2) * S.kc * (R(1) + mu2) * sn / (g * g);
+        R Gn[9], Ds[9];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            const R aa = (R(1) + mu2) * sn * n[a] - mu2 * sg[a];
+            Gn[a * 3 + b] = c1 * (n[a] * sg[b] + (a == b ? sn : R(0))) - c2 * aa * sg[b];
+            Ds[a * 3 + b] = n[a] * n[b] + ph * Nm[a * 3 + b];
+          }
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            R t = R(0);
+            for (int e = 0; e < 3; ++e) t += -W[a * 3 + e] * Ds[e * 3 + b] + Gn[a * 3 + e] * Nm[e * 3 + b];
+            K[a * 3 + b] += t;
+          }
+      }
+      for (int i = 0; i < 9; ++i) Kc[9 * j + i] = K[i];
+      for (int o = 1; o <= 2; ++o) {
+        const int b2 = j + o;
+        R Sm[9];
+        for (int i = 0; i < 9; ++i) Sm[i] = R(0);
+        if (b2 < nv) {
+          const R kk = o == 1 ? S.k1 : S.k2;
+          const R Lr = o == 1 ? S.L1[j] : S.L2[j];
+          R dv[3], dl[3];
+          for (int i = 0; i < 3; ++i) {
+            dv[i] = (z[3 * b2 + i] - z[3 * j + i]) + (node_dx(b2, i) - node_dx(j, i));
+            dl[i] = node_D(b2, i) - Dj[i];
+          }
+          // spring_d3 as a matrix on mt: c (u dl^T + (u.dl) I + dl u^T - 3 (u.dl) u u^T)
+          const R l = sqrt(dot3(dv, dv)), inv = R(1) / l;
+          const R uu[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+          const R cc2 = kk * Lr * inv * inv, ud = dot3(uu, dl);
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+              Sm[a * 3 + b] = cc2 * (uu[a] * dl[b] + (a == b ? ud : R(0)) + dl[a] * uu[b] - R(3) * ud * uu[a] * uu[b]);
+        }
+        for (int i = 0; i < 9; ++i) Ks[(2 * j + o - 1) * 9 + i] = Sm[i];
+      }
+    }
+    __syncwarp();
     for (int d0 = 0; d0 < ndir; d0 += 32) {
       const int dir = d0 + lane;
       const bool act = dir < ndir;
@@ -1400,7 +1469,7 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
       if (dir < 3 * nv) { kind = 0; jn = dir / 3; cc = dir % 3; }
       else if (dir < nq) { kind = 1; gi = (dir - 3 * nv) / 3; cc = (dir - 3 * nv) % 3; }
       else { kind = 2; gi = (dir - nq) / 3; cc = (dir - nq) % 3; if (gi > 1) gi = 1; }
-      for (int r = 0; r < 6 * NP; ++r) { tv1[(size_t)r * 32 + lane] = R(0); tv2[(size_t)r * 32 + lane] = R(0); }
+      for (int r = 0; r < 6 * N; ++r) { tv1[(size_t)r * 32 + lane] = R(0); tv2[(size_t)r * 32 + lane] = R(0); }
       // rhs1 = -(dF/dtheta) e_dir ; dx* = H1^{-1} rhs1
       if (act) {
         if (kind == 0) {
@@ -1417,40 +1486,22 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
             for (int i = 0; i < 3; ++i) T1(a, i) -= (node_dx(a, i) - (c[3 * gi + i] + u[3 * gi + i])) * gd[3 * gi + cc];
         }
       }
-      cr_solve_serial(w.T, w.B, w.V, tv1 + lane, 32, N, NP);
+      cr_solve_serial(w.T, w.B, w.V, tv1 + lane, 32, N, N);
       // rhs2 = -(Rx dx* + Rq theta)
       for (int j = 0; j < nv; ++j) {
-        R X[3];
-        for (int i = 0; i < 3; ++i) X[i] = z[3 * j + i] + node_dx(j, i);
-        R v[3] = {T1(j, 0), T1(j, 1), T1(j, 2)};
-        for (int o = 0; o < S.nobs; ++o) {
-          R ph, n[3], Nm[9];
-          obstacle_eval(S.ob_type[o], S.ob[o], X, S.rad, ph, n, Nm);
-          R sg[3];
-          for (int i = 0; i < 3; ++i) sg[i] = node_D(j, i) + ph * n[i];
-          R lam[3], W[9];
-          cone_force_jac(sg, n, S.kc, S.mu, lam, W);
-          R Nv[3], dsg[3], Wd[3], Ld[3];
-          for (int i = 0; i < 3; ++i) Nv[i] = Nm[i * 3] * v[0] + Nm[i * 3 + 1] * v[1] + Nm[i * 3 + 2] * v[2];
-          const R nv_ = dot3(n, v);
-          for (int i = 0; i < 3; ++i) dsg[i] = n[i] * nv_ + ph * Nv[i];
-          for (int i = 0; i < 3; ++i) Wd[i] = W[i * 3] * dsg[0] + W[i * 3 + 1] * dsg[1] + W[i * 3 + 2] * dsg[2];
-          cone_force_dn(sg, n, S.kc, S.mu, Nv, Ld);
-          for (int i = 0; i < 3; ++i) T2v(j, i) -= (-Wd[i] + Ld[i]);
-        }
+        const R v[3] = {T1(j, 0), T1(j, 1), T1(j, 2)};
+        const R* K = Kc + 9 * j;
+        for (int i = 0; i < 3; ++i) T2v(j, i) -= K[i * 3] * v[0] + K[i * 3 + 1] * v[1] + K[i * 3 + 2] * v[2];
         for (int o = 1; o <= 2; ++o) {
-          const int a = j, b2 = j + o;
+          const int b2 = j + o;
           if (b2 >= nv) continue;
-          const R kk = o == 1 ? S.k1 : S.k2;
-          const R Lr = o == 1 ? S.L1[a] : S.L2[a];
-          R dv[3], mt[3], dl[3], t3[3];
+          const R* Sm = Ks + (2 * j + o - 1) * 9;
+          const R mt[3] = {T1(b2, 0) - v[0], T1(b2, 1) - v[1], T1(b2, 2) - v[2]};
           for (int i = 0; i < 3; ++i) {
-            dv[i] = (z[3 * b2 + i] - z[3 * a + i]) + (node_dx(b2, i) - node_dx(a, i));
-            mt[i] = T1(b2, i) - T1(a, i);
-            dl[i] = node_D(b2, i) - node_D(a, i);
+            const R t3 = Sm[i * 3] * mt[0] + Sm[i * 3 + 1] * mt[1] + Sm[i * 3 + 2] * mt[2];
+            T2v(b2, i) += t3;
+            T2v(j, i) -= t3;
           }
-          spring_d3(dv, kk, Lr, mt, dl, t3);
-          for (int i = 0; i < 3; ++i) { T2v(b2, i) += t3[i]; T2v(a, i) -= t3[i]; }
         }
       }
       if (act && kind != 2) {
@@ -1464,7 +1515,7 @@ __global__ void __launch_bounds__(32) rope_linearize_kernel(Scene<R> S, int B, i
       }
       for (int j = 0; j < nv; ++j)
         for (int i = 0; i < 3; ++i) T2v(j, i) = -T2v(j, i);
-      cr_solve_serial(w.T2, w.B2, w.V2, tv2 + lane, 32, N, NP);
+      cr_solve_serial(w.T2, w.B2, w.V2, tv2 + lane, 32, N, N);
       if (act) {
         R* out;
         size_t ld;

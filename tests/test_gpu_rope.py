@@ -210,7 +210,8 @@ def test_rope40_linearize_full_size_sampled():
     assert np.count_nonzero(st) == 0
     for b in picks:
         for t in (0, 7, H - 1):
-            Ar, Br = ograd.SmoothStepJacobian(osc, Z[b, t], V[b, t]).jacobians()
+            xs0 = Z[b, t + 1][: osc.n].reshape(osc.nv, 3)
+            Ar, Br = ograd.SmoothStepJacobian(osc, Z[b, t], V[b, t], x_start=xs0).jacobians()
             Ag, Bg = A[b, t].cpu().numpy(), Bm[b, t].cpu().numpy()
             assert np.linalg.norm(Ag - Ar) <= 1e-3 * np.linalg.norm(Ar), (b, t)
             assert np.linalg.norm(Bg - Br) <= 1e-3 * np.linalg.norm(Br), (b, t)
