@@ -241,26 +241,21 @@ __device__ __forceinline__ void nt_scaling(const R s[3], const R z[3], R W[9], R
   for (int i = 0; i < 3; ++i) lam[i] = W[i * 3] * z[0] + W[i * 3 + 1] * z[1] + W[i * 3 + 2] * z[2];
 }
 
-// largest alpha with x + alpha dx in Q (1e30 when unbounded)
+// largest alpha with x + alpha dx in Q (1e30 when unbounded), x in int Q.  Computed in the frame
+// where x is the cone's centre: with g = sqrt(det x) and xh = x / g, the hyperbolic rotation that
+// takes xh to e = (1, 0, 0) takes dx / g to y with y0 = (xh0 dx0 - xh1.dx1) / g and
+// y1 = dx1 / g - (y0 + dx0 / g) / (xh0 + 1) xh1; the step to the boundary is 1 / (|y1| - y0) when
+// that is positive (an eigenvalue y0 - |y1| of y reaches -1).  Well conditioned near the boundary,
+// unlike the roots of the quadratic det(x + alpha dx) = 0.
 template <typename R>
 __device__ __forceinline__ R soc_max_step(const R x[3], const R dx[3]) {
-  const R a = soc_det(dx);
-  const R b = R(2) * (x[0] * dx[0] - x[1] * dx[1] - x[2] * dx[2]);
-  const R c = soc_det(x);
-  R out = R(1e30);
-  const R disc = b * b - R(4) * a * c;
-  if (a != R(0)) {
-    if (disc >= R(0)) {
-      const R sq = sqrt(disc);
-      const R r1 = (-b - sq) / (R(2) * a), r2 = (-b + sq) / (R(2) * a);
-      if (r1 > R(0)) out = fmin(out, r1);
-      if (r2 > R(0)) out = fmin(out, r2);
-    }
-  } else if (b < R(0)) {
-    out = fmin(out, -c / b);
-  }
-  if (dx[0] < R(0)) out = fmin(out, -x[0] / dx[0]);
-  return out;
+  const R ig = rsq(soc_det(x));
+  const R xh[3] = {x[0] * ig, x[1] * ig, x[2] * ig};
+  const R y0 = (xh[0] * dx[0] - xh[1] * dx[1] - xh[2] * dx[2]) * ig;
+  const R f = (y0 + dx[0] * ig) / (xh[0] + R(1));
+  const R y1 = dx[1] * ig - f * xh[1], y2 = dx[2] * ig - f * xh[2];
+  const R t = sqrt(y1 * y1 + y2 * y2) - y0;
+  return t > R(0) ? R(1) / t : R(1e30);
 }
 
 // ---- spring k/2 (|d| - L)^2 with d = x_b - x_a: force on b (f = dE/dx_b), and the Hessian
