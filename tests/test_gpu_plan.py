@@ -139,3 +139,25 @@ def test_plan_session_warm_start():
         nxt = srv.poll(srv.submit(sc, sc["q0"], H, 1, 1, seed=4, session_id=77))
     shifted = np.concatenate([first["u"][1:], first["u"][-1:]])
     np.testing.assert_array_equal(nxt["u"], shifted)
+
+
+def test_plan_autotuner_writes_and_reuses_its_cache(tmp_path):
+    """The autotuner times the packed launch at 1, 2 and 4 warps per CTA, writes its choice per
+    (device, real type, pairs per lane) to the cache file, and a second server reads it back;
+    plans do not depend on the launch shape."""
+    cache = str(tmp_path / "tuning.txt")
+    reqs = _mix()[:3]
+    with _server(real_bytes=4, autotune=True, tuner_cache=cache) as srv:
+        tuned = _run(srv, reqs)
+    lines = [l.split() for l in open(cache).read().splitlines() if l.strip()]
+    assert len(lines) == 2
+    for key, warps in lines:
+        assert key.split("|")[1] == "4" and key.split("|")[2] in ("1", "2")
+        assert warps in ("1", "2", "4")
+    with _server(real_bytes=4, autotune=True, tuner_cache=cache) as srv:
+        again = _run(srv, reqs)
+    with _server(real_bytes=4) as srv:
+        plain = _run(srv, reqs)
+    for a, b, c in zip(tuned, again, plain):
+        _same(a, b)
+        _same(a, c)
