@@ -58,10 +58,10 @@ def _blocks_to_sparse(rows, cols, blocks, shape):
 class SmoothStepJacobian:
     """Everything needed to apply the smooth step's Jacobian at (q, u), both ways."""
 
-    def __init__(self, sc: sim.Scene, q, u, tol=sim.TOL_X, x_start=None):
+    def __init__(self, sc: sim.Scene, q, u, tol=sim.TOL_X, x_start=None, Delta_start=None):
         self.sc = sc
         info = {}
-        qp, st = sim.step(sc, q, u, SMOOTH, tol, info, x_start=x_start)
+        qp, st = sim.step(sc, q, u, SMOOTH, tol, info, x_start=x_start, Delta_start=Delta_start)
         self.q_next = qp
         self.counts = (info["newton_it"], info["ipm_it"])
         self.status = st
@@ -228,7 +228,9 @@ def rollout_vjp(sc: sim.Scene, q0, U, grad_mode="surrogate", dL_dtraj=None, tol=
     smooth_counts = []
     for t in range(H - 1, -1, -1):
         # the smooth re-solve starts its Newton iteration at the forward step's stage-1 solution
-        jac = SmoothStepJacobian(sc, traj[t], U[t], tol, x_start=xs_fwd[t])
+        # and its interior point at the forward step's stage-2 displacement
+        D_fwd = traj[t + 1][: sc.n].reshape(sc.nv, 3) - xs_fwd[t]
+        jac = SmoothStepJacobian(sc, traj[t], U[t], tol, x_start=xs_fwd[t], Delta_start=D_fwd)
         status |= jac.status
         smooth_counts.append(jac.counts)
         if not jac.defined:          # no gradient through a step without a defined Jacobian

@@ -467,7 +467,8 @@ def max_step(x, dx):
     return np.minimum(out, t0)
 
 
-def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IPM_MAX):
+def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IPM_MAX,
+               Delta_start=None):
     """Primal-dual interior point with Nesterov-Todd scaling (the cone QP method of Vandenberghe
     2010) for
         min 1/2 Delta^T P Delta  s.t.  s_i = A_i Delta_j + phi_i e1 in Q,
@@ -497,6 +498,8 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
     Pd = np.einsum("joa,jab,job->jo", n, stage1_hessian_vec_diag(sc, xs, d), n)
     push = 0.5 * (-phi + np.sqrt(phi * phi + 4.0 * kappa / Pd))
     Delta = np.einsum("jo,joa->ja", np.where(phi < 0.0, push, 0.0), n)
+    if Delta_start is not None:         # warm start (the central point reached does not depend on it)
+        Delta = np.asarray(Delta_start, dtype=np.float64).reshape(nv, 3).copy()
     s = np.einsum("joab,jb->joa", A, Delta) + phi[..., None] * e1
     ok = (s[..., 0] > 0.0) & (soc_det(s) > 0.25 * s[..., 0] ** 2)
     s = np.where(ok[..., None], s, np.maximum(phi, sc.p["sigma0"])[..., None] * e1)
@@ -582,10 +585,10 @@ def stage1_hessian_vec_diag(sc: Scene, X, d):
     return D
 
 
-def stage2_smooth(sc: Scene, xs, d, tol=TOL_X):
+def stage2_smooth(sc: Scene, xs, d, tol=TOL_X, Delta_start=None):
     """Smoothed stage 2: the central point at kappa_c (relaxed complementarity s^T lam = kappa_c)."""
     phi, n = contact_geometry(sc, xs)
-    Delta, sig, it, st = stage2_ipm(sc, xs, d, phi, n, sc.p["kappa_c"], None, tol)
+    Delta, sig, it, st = stage2_ipm(sc, xs, d, phi, n, sc.p["kappa_c"], None, tol, Delta_start=Delta_start)
     return Delta, sig, phi, n, it, st
 
 
@@ -612,7 +615,7 @@ def join_q(x, g):
     return np.concatenate([x.ravel(), g.ravel()])
 
 
-def step(sc: Scene, q, u, mode, tol=TOL_X, info=None, x_start=None):
+def step(sc: Scene, q, u, mode, tol=TOL_X, info=None, x_start=None, Delta_start=None):
     """(q, u) -> q+ : stage 1 then stage 2 (Sec. 4.1, "Simulation Solver").  x_start: optional
     start of the stage-1 Newton iteration (the root it converges to is the same)."""
     x, g = split_q(sc, q)
@@ -622,7 +625,7 @@ def step(sc: Scene, q, u, mode, tol=TOL_X, info=None, x_start=None):
     if mode == HARD:
         Delta, sig, phi, n, it2, st2 = stage2_hard(sc, xs, d, tol)
     else:
-        Delta, sig, phi, n, it2, st2 = stage2_smooth(sc, xs, d, tol)
+        Delta, sig, phi, n, it2, st2 = stage2_smooth(sc, xs, d, tol, Delta_start)
     if info is not None:
         info.update(xs=xs, Delta=Delta, sig=sig, phi=phi, n=n, d=d, gstar=gstar,
                     newton_it=it1, ipm_it=it2, status=st1 | st2)

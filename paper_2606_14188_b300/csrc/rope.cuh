@@ -582,7 +582,7 @@ __device__ __forceinline__ void diag_block(const Scene<R>& S, const Lane<R, PPL>
 // point of kfinal.  On exit (T, B, V) hold the factorisation of the last H2 = P + sum A^T W^-2 A.
 template <typename R, int PPL>
 __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, R kappa, R kfinal,
-                          int lane, int* iters) {
+                          int lane, int* iters, bool warm = false) {
   const int nobs = S.nobs;
   const R mm = R(S.nv * nobs);
   const int NP = w.NP;
@@ -598,6 +598,9 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
       R D[9];
       diag_block(S, L, dxm, dxp, w.misc, k, p, h, D);
       R Dj[3] = {0, 0, 0};
+      if (warm) {                    // given start (L.Dl); the central point does not depend on it
+        for (int i = 0; i < 3; ++i) Dj[i] = L.Dl[k][3 * h + i];
+      } else
       for (int o = 0; o < nobs; ++o) {
         const R ph = w.phi[cs1(o, h, p, NP)];
         if (ph < R(0)) {
@@ -847,12 +850,13 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
 }
 
 // ------------------------------------------------------------------------------------------
-// one step: inputs x0 (registers + neighbours), misc g, u, c.  Outputs dx, Dl, contact data,
+// one step: inputs x0 (registers + neighbours), misc g, u, c; with warm, the stage-1 start dx; with
+// warm2, the stage-2 start Dl.  Outputs dx, Dl, contact data,
 // misc d, gd.  smooth = the smooth grasp and the smooth (kappa_c) contact solve.
 // ------------------------------------------------------------------------------------------
 template <typename R, int PPL>
 __device__ __forceinline__ int sim_step(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, int lane, bool smooth,
-                        int* nit, int* iit, bool warm = false) {
+                        int* nit, int* iit, bool warm = false, bool warm2 = false) {
   R* d = w.misc + M_D;
   R* gd = w.misc + M_GD;
   const R* c = w.misc + M_C;
@@ -871,14 +875,14 @@ __device__ __forceinline__ int sim_step(const Scene<R>& S, Lane<R, PPL>& L, WS<R
     d[lane] = dd;
   }
   __syncwarp();
-  zero6<R, PPL>(L.Dl);
+  if (!warm2) zero6<R, PPL>(L.Dl);
   int st = stage1_newton(S, L, w, lane, nit, warm);
   *iit = 0;
   if (S.nobs == 0) return st;
   const R pmin = contact_geometry(S, L, w, lane);
   __syncwarp();
   if (!smooth && pmin >= R(0)) return st;
-  st |= stage2_ipm(S, L, w, S.kc, smooth ? R(-1) : S.khard, lane, iit);
+  st |= stage2_ipm(S, L, w, S.kc, smooth ? R(-1) : S.khard, lane, iit, warm2);
   return st;
 }
 
@@ -1113,6 +1117,19 @@ __device__ __forceinline__ void load_rec_dx(const Scene<R>& S, Lane<R, PPL>& L, 
   }
 }
 
+// the forward step's stage-2 displacement Delta = x_{t+1} - (x_t + dx) from the record r of
+// q_{t+1} (after load_rec of q_t and load_rec_dx of r): the smooth re-solve's stage-2 start
+template <typename R, int PPL>
+__device__ __forceinline__ void load_rec_delta(const Scene<R>& S, Lane<R, PPL>& L, const R* r, int lane) {
+#pragma unroll
+  for (int k = 0; k < PPL; ++k) {
+    const int p = lane + 32 * k;
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+      L.Dl[k][e] = (2 * p + e / 3 < S.nv) ? (r[6 * p + e] - L.x0[k][e]) - L.dx[k][e] : R(0);
+  }
+}
+
 template <typename R, int PPL>
 __device__ __forceinline__ void load_rec(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, const R* r, int lane) {
   load_nodes(S, L, r, lane);
@@ -1216,13 +1233,16 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
   while (true) {
     if (kind == BACK) {
       load_rec(S, L, w, seg + (size_t)(t - t0) * rl, lane);
-      // start the smooth re-solve at the forward step's stage-1 solution (record of q_{t+1})
-      load_rec_dx(S, L, t + 1 < t1 ? seg + (size_t)(t + 1 - t0) * rl : ck + (size_t)(sgi + 1) * rl, lane);
+      // start the smooth re-solve at the forward step's stage-1 solution and stage-2 displacement
+      // (record of q_{t+1})
+      const R* rn = t + 1 < t1 ? seg + (size_t)(t + 1 - t0) * rl : ck + (size_t)(sgi + 1) * rl;
+      load_rec_dx(S, L, rn, lane);
+      load_rec_delta(S, L, rn, lane);
     }
     if (lane < 6) w.misc[M_U + lane] = w.u[6 * t + lane];
     __syncwarp();
     int ni, ii;
-    st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK);
+    st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK, kind == BACK);
     if (st) break;                 // a failed step: the rollout's loss and gradient are undefined
     if (kind != BACK) {
       advance_state(S, L, w, lane);
