@@ -179,7 +179,7 @@ cs_status sim_linearize(cs_sim* sim, int B, int H, const void* z, const void* v,
  *     (different streams, or different host threads on one device) race on it.
  *   - Errors: CS_ERR_INVALID_ARG when the checkpoint records of B rollouts of H steps do not fit
  *     in CS_NOALLOC_SCRATCH_BYTES, plus the errors of sim_create and sim_rollout_vjp. */
-#define CS_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define CS_NOALLOC_SCRATCH_BYTES (48u << 20)
 cs_status sim_rollout_vjp_noalloc(const cs_params* params, const double* rest_x, int B, int H,
                                   const void* q0, const void* u, const void* dL_dtraj,
                                   const cs_loss* loss, void* L, void* dL_du, void* dL_dq0,

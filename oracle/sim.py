@@ -592,13 +592,14 @@ def stage2_smooth(sc: Scene, xs, d, tol=TOL_X, Delta_start=None):
     return Delta, sig, phi, n, it, st
 
 
-def stage2_hard(sc: Scene, xs, d, tol=TOL_X):
+def stage2_hard(sc: Scene, xs, d, tol=TOL_X, Delta_start=None):
     """The nonsmooth contact SOCP of eq. (dynamics-second-stage).  Delta = 0 when no pair
     penetrates; otherwise the primal-dual path is followed from kappa_c down to kappa_hard."""
     phi, n = contact_geometry(sc, xs)
     if np.all(phi >= 0.0):
         return np.zeros((sc.nv, 3)), None, phi, n, 0, 0
-    Delta, sig, it, st = stage2_ipm(sc, xs, d, phi, n, sc.p["kappa_c"], sc.p["kappa_hard"], tol)
+    Delta, sig, it, st = stage2_ipm(sc, xs, d, phi, n, sc.p["kappa_c"], sc.p["kappa_hard"], tol,
+                                    Delta_start=Delta_start)
     return Delta, sig, phi, n, it, st
 
 
@@ -623,7 +624,7 @@ def step(sc: Scene, q, u, mode, tol=TOL_X, info=None, x_start=None, Delta_start=
     d = grasp_stiffness(sc, x, g, mode)
     xs, it1, st1 = stage1_solve(sc, x, gstar, d, tol, x_start=x_start)
     if mode == HARD:
-        Delta, sig, phi, n, it2, st2 = stage2_hard(sc, xs, d, tol)
+        Delta, sig, phi, n, it2, st2 = stage2_hard(sc, xs, d, tol, Delta_start)
     else:
         Delta, sig, phi, n, it2, st2 = stage2_smooth(sc, xs, d, tol, Delta_start)
     if info is not None:
@@ -634,15 +635,19 @@ def step(sc: Scene, q, u, mode, tol=TOL_X, info=None, x_start=None, Delta_start=
 
 def rollout(sc: Scene, q0, U, mode, tol=TOL_X, xs_out=None):
     """q_0 .. q_H for controls U[H, 6].  Returns (traj[H+1, nq], status, newton/ipm counts);
-    xs_out, if a list, receives each step's stage-1 solution q*."""
+    xs_out, if a list, receives each step's stage-1 solution q*.  Stage 2 of a step starts its
+    interior point at the previous step's Delta when that step ran stage 2 (the point it
+    converges to does not depend on the start)."""
     H = U.shape[0]
     traj = np.zeros((H + 1, sc.nq))
     traj[0] = q0
     status = 0
     counts = []
+    D_prev = None
     for t in range(H):
         info = {}
-        traj[t + 1], st = step(sc, traj[t], U[t], mode, tol, info)
+        traj[t + 1], st = step(sc, traj[t], U[t], mode, tol, info, Delta_start=D_prev)
+        D_prev = info["Delta"] if np.any(info["Delta"] != 0.0) else None
         status |= st
         counts.append((info["newton_it"], info["ipm_it"]))
         if xs_out is not None:

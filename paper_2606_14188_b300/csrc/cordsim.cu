@@ -114,8 +114,9 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   }
   const int k = P->checkpoint_every;
   const int nseg = (P->max_horizon + k - 1) / k;
-  // checkpoint records: state, grasp offsets, stage-1 offset of the producing step
-  s->ws_stride = (size_t)(nseg + 1 + k) * (s->nq + 6 + 3 * nv);
+  // checkpoint records: state, grasp offsets, stage-1 offset and stage-2 displacement of the
+  // producing step
+  s->ws_stride = (size_t)(nseg + 1 + k) * cs::rec_len(nv);
   e = cudaMalloc(&s->d_ws, s->ws_stride * (size_t)P->max_batch * rb);
   if (e != cudaSuccess) {
     sim_destroy(s);

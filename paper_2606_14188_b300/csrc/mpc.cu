@@ -102,7 +102,7 @@ Layout make_layout(int nv, int H, int Rc, int ck, int rb) {
   l.L = take((size_t)Rc * rb);
   l.status = take((size_t)Rc * 4);
   const int nseg = (H + ck - 1) / ck;
-  l.ws_stride = (size_t)(nseg + 1 + ck) * (nq + 6 + 3 * nv);
+  l.ws_stride = (size_t)(nseg + 1 + ck) * cs::rec_len(nv);
   l.ws = take((size_t)Rc * l.ws_stride * rb);
   const size_t bu = ((size_t)H * 6 * rb + 15) & ~(size_t)15;
   l.best_bytes = bu + sizeof(cs::PlanState);

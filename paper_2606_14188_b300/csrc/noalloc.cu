@@ -91,7 +91,7 @@ extern "C" cs_status sim_rollout_vjp_noalloc(const cs_params* P, const double* r
   s.real_bytes = P->real_bytes;
   const int k = P->checkpoint_every;
   const int nseg = (H + k - 1) / k;
-  s.ws_stride = (size_t)(nseg + 1 + k) * (s.nq + 6 + 3 * nv);
+  s.ws_stride = (size_t)(nseg + 1 + k) * cs::rec_len(nv);
   const size_t need = 2 * kRestBytes + s.ws_stride * (size_t)B * (size_t)s.real_bytes;
   if (need > CS_NOALLOC_SCRATCH_BYTES)
     return cs_fail(CS_ERR_INVALID_ARG,

@@ -78,6 +78,10 @@ __device__ __forceinline__ WS<R> ws_carve(R* base, int NP, int nobs, int H, bool
   return w;
 }
 
+// checkpoint record of a state: q [n_q] | c [6] | dx [3 nv] | Delta [3 nv] (grasp offsets, and
+// the stage-1 offset and stage-2 displacement of the step that produced the state)
+__host__ __device__ inline int rec_len(int nv) { return 3 * nv + 6 + 6 + 6 * nv; }
+
 // contact-pair element addresses
 __device__ __forceinline__ int cv(int o, int h, int c, int p, int NP) { return ((o * 2 + h) * 3 + c) * NP + p; }
 __device__ __forceinline__ int cs1(int o, int h, int p, int NP) { return (o * 2 + h) * NP + p; }
@@ -878,10 +882,10 @@ __device__ __forceinline__ int sim_step(const Scene<R>& S, Lane<R, PPL>& L, WS<R
   if (!warm2) zero6<R, PPL>(L.Dl);
   int st = stage1_newton(S, L, w, lane, nit, warm);
   *iit = 0;
-  if (S.nobs == 0) return st;
+  if (S.nobs == 0) { zero6<R, PPL>(L.Dl); return st; }
   const R pmin = contact_geometry(S, L, w, lane);
   __syncwarp();
-  if (!smooth && pmin >= R(0)) return st;
+  if (!smooth && pmin >= R(0)) { zero6<R, PPL>(L.Dl); return st; }   // Delta = 0 is optimal
   st |= stage2_ipm(S, L, w, S.kc, smooth ? R(-1) : S.khard, lane, iit, warm2);
   return st;
 }
@@ -1097,12 +1101,13 @@ __device__ __forceinline__ void store_rec(const Scene<R>& S, const Lane<R, PPL>&
   store_q(S, L, w, r, lane);
   if (lane < 6) r[3 * S.nv + 6 + lane] = w.misc[M_C + lane];
   R* rd = r + 3 * S.nv + 12;
+  R* rD = rd + 3 * S.nv;
 #pragma unroll
   for (int k = 0; k < PPL; ++k) {
     const int p = lane + 32 * k;
 #pragma unroll
     for (int e = 0; e < 6; ++e)
-      if (2 * p + e / 3 < S.nv) rd[6 * p + e] = L.dx[k][e];
+      if (2 * p + e / 3 < S.nv) { rd[6 * p + e] = L.dx[k][e]; rD[6 * p + e] = L.Dl[k][e]; }
   }
 }
 
@@ -1117,17 +1122,27 @@ __device__ __forceinline__ void load_rec_dx(const Scene<R>& S, Lane<R, PPL>& L, 
   }
 }
 
-// the forward step's stage-2 displacement Delta = x_{t+1} - (x_t + dx) from the record r of
-// q_{t+1} (after load_rec of q_t and load_rec_dx of r): the smooth re-solve's stage-2 start
+// the stage-2 displacement Delta of the step that produced the state of record r
 template <typename R, int PPL>
 __device__ __forceinline__ void load_rec_delta(const Scene<R>& S, Lane<R, PPL>& L, const R* r, int lane) {
+  const R* rD = r + 6 * S.nv + 12;
 #pragma unroll
   for (int k = 0; k < PPL; ++k) {
     const int p = lane + 32 * k;
 #pragma unroll
-    for (int e = 0; e < 6; ++e)
-      L.Dl[k][e] = (2 * p + e / 3 < S.nv) ? (r[6 * p + e] - L.x0[k][e]) - L.dx[k][e] : R(0);
+    for (int e = 0; e < 6; ++e) L.Dl[k][e] = (2 * p + e / 3 < S.nv) ? rD[6 * p + e] : R(0);
   }
+}
+
+// true on every lane when some node has a nonzero Delta (the previous step ran stage 2)
+template <typename R, int PPL>
+__device__ __forceinline__ bool any_delta(const Lane<R, PPL>& L) {
+  bool nz = false;
+#pragma unroll
+  for (int k = 0; k < PPL; ++k)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) nz = nz || L.Dl[k][e] != R(0);
+  return __any_sync(FULL, nz);
 }
 
 template <typename R, int PPL>
@@ -1180,6 +1195,7 @@ __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int
   const bool smooth = S.fwd_mode == CS_SMOOTH;
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     load_q(S, L, w, q0 + (size_t)b * nq, lane);
+    zero6<R, PPL>(L.Dl);
     load_controls(w.u, U + (size_t)b * H * 6, 6 * H, lane);
     __syncwarp();
     if (traj) store_q(S, L, w, traj + (size_t)b * (H + 1) * nq, lane);
@@ -1188,7 +1204,9 @@ __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int
       if (lane < 6) w.misc[M_U + lane] = w.u[6 * t + lane];
       __syncwarp();
       int ni, ii;
-      const int s1 = sim_step(S, L, w, lane, smooth, &ni, &ii);
+      // stage 2 starts from the previous step's Delta when that step ran stage 2
+      const bool w2 = any_delta(L);
+      const int s1 = sim_step(S, L, w, lane, smooth, &ni, &ii, false, w2);
       st |= s1;
       if (counters && lane == 0) {
         int32_t* c = counters + ((size_t)b * H + t) * 3;
@@ -1214,13 +1232,14 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
                                             const R* q0, const R* U, const R* dLdtraj, R* Lout, R* dLdu,
                                             R* dLdq0, int32_t* status, R* ck) {
   const int nq = 3 * S.nv + 6;
-  const int rl = nq + 6 + 3 * S.nv;
+  const int rl = rec_len(S.nv);
   const int k = S.ckpt;
   const int nseg = (H + k - 1) / k;
   const bool fwd_smooth = S.grad_mode == CS_CONSISTENT;
   enum { FWD = 0, RECOMP = 1, BACK = 2 };
   R* seg = ck + (size_t)(nseg + 1) * rl;     // segment records [k][rl]
   load_q(S, L, w, q0, lane);
+  zero6<R, PPL>(L.Dl);
   load_controls(w.u, U, 6 * H, lane);
   __syncwarp();
   store_rec(S, L, w, ck, lane);
@@ -1242,7 +1261,10 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
     if (lane < 6) w.misc[M_U + lane] = w.u[6 * t + lane];
     __syncwarp();
     int ni, ii;
-    st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK, kind == BACK);
+    // stage-2 start: in the backward the forward step's Delta; forward and recompute start from
+    // the previous step's Delta when it ran stage 2
+    const bool w2 = kind == BACK || any_delta(L);
+    st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK, w2);
     if (st) break;                 // a failed step: the rollout's loss and gradient are undefined
     if (kind != BACK) {
       advance_state(S, L, w, lane);
@@ -1314,6 +1336,7 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
       t0 = sgi * k;
       t1 = min(t0 + k, H);
       load_rec(S, L, w, ck + (size_t)sgi * rl, lane);
+      load_rec_delta(S, L, ck + (size_t)sgi * rl, lane);
       store_rec(S, L, w, seg, lane);
       if (t1 - t0 > 1) { kind = RECOMP; t = t0; } else { kind = BACK; t = t0; }
     }
