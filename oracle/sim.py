@@ -618,9 +618,15 @@ def join_q(x, g):
 
 def step(sc: Scene, q, u, mode, tol=TOL_X, info=None, x_start=None, Delta_start=None):
     """(q, u) -> q+ : stage 1 then stage 2 (Sec. 4.1, "Simulation Solver").  x_start: optional
-    start of the stage-1 Newton iteration (the root it converges to is the same)."""
+    start of the stage-1 Newton iteration (default: q with the grasped nodes moved with their
+    grippers)."""
     x, g = split_q(sc, q)
     gstar = g + np.asarray(u, dtype=np.float64).reshape(2, 3)
+    if x_start is None:
+        # stage 1 starts at q with each grasped node moved with its gripper
+        x_start = x.copy()
+        for i in range(2):
+            x_start[sc.grasp[i]] += gstar[i] - g[i]
     d = grasp_stiffness(sc, x, g, mode)
     xs, it1, st1 = stage1_solve(sc, x, gstar, d, tol, x_start=x_start)
     if mode == HARD:

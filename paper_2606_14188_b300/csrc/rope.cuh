@@ -409,7 +409,19 @@ __device__ __forceinline__ void assemble_P(const Scene<R>& S, Lane<R, PPL>& L, W
 template <typename R, int PPL>
 __device__ __forceinline__ int stage1_newton(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, int lane, int* iters,
                                              bool warm) {
-  if (!warm) zero6<R, PPL>(L.dx);
+  if (!warm) {
+    // start at the step's initial state with each grasped node moved with its gripper
+    zero6<R, PPL>(L.dx);
+#pragma unroll
+    for (int k = 0; k < PPL; ++k)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi)
+          if (S.grasp[gi] == 2 * (lane + 32 * k) + h)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) L.dx[k][3 * h + i] = w.misc[M_U + 3 * gi + i];
+  }
   R dxm[PPL][6], dxp[PPL][6];
   for (int it = 0; it < S.newton_max; ++it) {
     nbr<R, PPL>(L.dx, dxm, dxp, lane);
