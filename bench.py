@@ -85,16 +85,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
+def load_traffic(kernel: str, workload: str = WORKLOAD):
     """dram bytes per launch from a committed ncu summary, if it was taken on this exact kernel
-    source; else None."""
+    source and workload; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     try:
         d = json.load(open(path))
         e = d.get(kernel)
-        if e and e.get("source_hash") == kernel_source_hash() and e.get("workload") == WORKLOAD:
+        if e and e.get("source_hash") == kernel_source_hash() and e.get("workload") == workload:
             return float(e["dram_bytes_per_launch"])
     except Exception:
         return None
@@ -236,7 +236,8 @@ def linearize_leg(args, flush, stream, world):
                 ms_per_step=1e3 * avg, bytes_per_launch=out_bytes + in_bytes,
                 status_nonzero=int(torch.count_nonzero(st).item()),
                 roofline=dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=gbs / peak,
-                              traffic=None, peak_source=f"{src} HBM copy bandwidth"))
+                              traffic=load_traffic("rope_linearize_kernel", f"rope{nv}_b{B}_h{H}"),
+                              peak_source=f"{src} HBM copy bandwidth"))
 
 
 def served_stream(n, seed):
@@ -258,7 +259,8 @@ def served_stream(n, seed):
 def serve_stream(reqs, gaps, batched):
     """Submit reqs with the given inter-arrival gaps [s]; returns (results, makespan [s])."""
     from paper_2606_14188_b300.serve import PlanServer
-    srv = PlanServer(real_bytes=4, mem_budget_bytes=8 << 30, batched=batched, use_graphs=True)
+    srv = PlanServer(real_bytes=4, mem_budget_bytes=8 << 30, batched=batched, use_graphs=True,
+                     autotune=batched)
     try:
         t0 = time.perf_counter()
         due = t0
