@@ -327,3 +327,25 @@ def test_saddle_root_flagged_like_the_oracle(rb):
     Lv, dU, _, st = s.rollout_vjp(_t(q0, rb), _t(u, rb))
     assert ref["status"] & osim.ST_NOTPD and int(st[0]) & osim.ST_NOTPD
     assert np.isnan(float(Lv[0])) and float(dU.abs().max()) == 0.0
+
+
+def test_rope100_fp32_two_pairs_per_lane_vs_oracle():
+    """FP32 with two node pairs per lane (100 nodes): rollout and adjoint against the oracle."""
+    sc = scenes.rope_scene(100, n_spheres=1, n_boxes=1, seed=17,
+                           sphere_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)))
+    sc["params"]["checkpoint_every"] = 3
+    B, H = 3, 10
+    U = scenes.controls_normal_clear(sc, B, H, seed=17)
+    q0 = scenes.batch_q0(sc, B)
+    osc = _oscene(sc)
+    s = _sim(sc, 4, B, H)
+    traj, _, st = s.rollout(_t(q0, 4), _t(U, 4))
+    Lv, dU, _, st2 = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    for b in range(B):
+        ref, ost, _ = osim.rollout(osc, q0[b], U[b], "hard")
+        g = ograd.rollout_vjp(osc, q0[b], U[b], "surrogate")
+        assert (ost != 0) == (int(st[b]) != 0) and (g["status"] != 0) == (int(st2[b]) != 0)
+        if ost == 0 and g["status"] == 0:
+            assert rel_state(traj[b].cpu().numpy(), ref) <= TOL_STATE32, b
+            assert abs(float(Lv[b]) - g["L"]) <= TOL_STATE32 * abs(g["L"])
+            check_grad(dU[b].cpu().numpy(), g["dL_du"], TOL_GRAD32, COS32)
