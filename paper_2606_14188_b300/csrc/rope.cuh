@@ -703,7 +703,10 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
             rhs[0] = rhs[1] = rhs[2] = R(0);
           }
 #pragma unroll
-          for (int i = 0; i < 3; ++i) w.r[cr_v(p, 3 * h + i)] = rhs[i];
+          for (int i = 0; i < 3; ++i) {
+            w.r[cr_v(p, 3 * h + i)] = rhs[i];
+            L.F[k][3 * h + i] = rhs[i];       // kept for the corrector's right-hand side
+          }
         }
         put_rows(w, p, T, Bc);
       }
@@ -742,26 +745,40 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
       target = fmax(kfinal, om * om * om * gap / mm);
       centring = target == kfinal;
       // combined right-hand side: d_s = lam^-1 o (target e - lam o lam - (W^-1 ds_a) o (W dz_a)),
-      // the second-order term dropped once the target is kfinal; same factorisation
+      // the second-order term dropped once the target is kfinal; same factorisation.  Only g
+      // changes from the affine system: rhs = rhs_aff + sum A^T M (g - g_aff).
 #pragma unroll
       for (int k = 0; k < PPL; ++k) {
         const int p = lane + 32 * k;
         if (p >= S.npair) continue;
-        R PD[6];
-        hessvec(S, L, dxm, dxp, L.Dl, Dlm, Dlp, w.misc, k, p, proj, PD);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          R rhs[3] = {-PD[3 * h], -PD[3 * h + 1], -PD[3 * h + 2]};
+          R rhs[3] = {L.F[k][3 * h], L.F[k][3 * h + 1], L.F[k][3 * h + 2]};
           if (2 * p + h < S.nv) {
             const R dD[3] = {L.pv[k][3 * h], L.pv[k][3 * h + 1], L.pv[k][3 * h + 2]};
             for (int o = 0; o < nobs; ++o) {
-              R dsa[3], dza[3], sv[3], zv[3], A[9], W[9], Wi[9], lam[3];
-              pair_step(S, w, o, h, p, dD, dsa, dza);
+              R A[9], W[9], Wi[9], lam[3], sv[3], zv[3], ga[3], rz[3];
               pair_frame(w, o, h, p, S.mu, A);
-              for (int a = 0; a < 3; ++a) { sv[a] = w.s[cv(o, h, a, p, NP)]; zv[a] = w.z[cv(o, h, a, p, NP)]; }
+              const R m6[6] = {w.pm[cm6(o, h, 0, p, NP)], w.pm[cm6(o, h, 1, p, NP)], w.pm[cm6(o, h, 2, p, NP)],
+                               w.pm[cm6(o, h, 3, p, NP)], w.pm[cm6(o, h, 4, p, NP)], w.pm[cm6(o, h, 5, p, NP)]};
+              const R M[9] = {m6[0], m6[1], m6[2], m6[1], m6[3], m6[4], m6[2], m6[4], m6[5]};
+              for (int a = 0; a < 3; ++a) {
+                sv[a] = w.s[cv(o, h, a, p, NP)];
+                zv[a] = w.z[cv(o, h, a, p, NP)];
+                ga[a] = w.pg[cv(o, h, a, p, NP)];
+                rz[a] = w.prz[cv(o, h, a, p, NP)];
+              }
               nt_scaling(sv, zv, W, Wi, lam);
               R c3[3] = {R(0), R(0), R(0)};
               if (!centring) {
+                // affine directions ds_a = A dD - r_z, dz_a = M (g_aff - A dD)
+                R ADd[3], dsa[3], gm[3], dza[3];
+                for (int a = 0; a < 3; ++a) {
+                  ADd[a] = A[a * 3] * dD[0] + A[a * 3 + 1] * dD[1] + A[a * 3 + 2] * dD[2];
+                  dsa[a] = ADd[a] - rz[a];
+                  gm[a] = ga[a] - ADd[a];
+                }
+                for (int a = 0; a < 3; ++a) dza[a] = M[a * 3] * gm[0] + M[a * 3 + 1] * gm[1] + M[a * 3 + 2] * gm[2];
                 R a1[3], a2[3];
                 for (int a = 0; a < 3; ++a) {
                   a1[a] = Wi[a * 3] * dsa[0] + Wi[a * 3 + 1] * dsa[1] + Wi[a * 3 + 2] * dsa[2];
@@ -775,17 +792,15 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
                                R(-2) * lam[0] * lam[1] - c3[1], R(-2) * lam[0] * lam[2] - c3[2]};
               R ds[3];
               jordan_solve(lam, r3, ds);
-              R g[3], zg[3];
-              const R m6[6] = {w.pm[cm6(o, h, 0, p, NP)], w.pm[cm6(o, h, 1, p, NP)], w.pm[cm6(o, h, 2, p, NP)],
-                               w.pm[cm6(o, h, 3, p, NP)], w.pm[cm6(o, h, 4, p, NP)], w.pm[cm6(o, h, 5, p, NP)]};
-              const R M[9] = {m6[0], m6[1], m6[2], m6[1], m6[3], m6[4], m6[2], m6[4], m6[5]};
-              for (int a = 0; a < 3; ++a)
-                g[a] = w.prz[cv(o, h, a, p, NP)] + W[a * 3] * ds[0] + W[a * 3 + 1] * ds[1] + W[a * 3 + 2] * ds[2];
+              R dg[3];
               for (int a = 0; a < 3; ++a) {
-                w.pg[cv(o, h, a, p, NP)] = g[a];
-                zg[a] = zv[a] + M[a * 3] * g[0] + M[a * 3 + 1] * g[1] + M[a * 3 + 2] * g[2];
+                const R g = rz[a] + W[a * 3] * ds[0] + W[a * 3 + 1] * ds[1] + W[a * 3 + 2] * ds[2];
+                w.pg[cv(o, h, a, p, NP)] = g;
+                dg[a] = g - ga[a];
               }
-              for (int i = 0; i < 3; ++i) rhs[i] += A[i] * zg[0] + A[3 + i] * zg[1] + A[6 + i] * zg[2];
+              R Mdg[3];
+              for (int a = 0; a < 3; ++a) Mdg[a] = M[a * 3] * dg[0] + M[a * 3 + 1] * dg[1] + M[a * 3 + 2] * dg[2];
+              for (int i = 0; i < 3; ++i) rhs[i] += A[i] * Mdg[0] + A[3 + i] * Mdg[1] + A[6 + i] * Mdg[2];
             }
           } else {
             rhs[0] = rhs[1] = rhs[2] = R(0);
@@ -808,7 +823,6 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (2 * p + h >= S.nv) continue;
-        const R D[3] = {L.Dl[k][3 * h], L.Dl[k][3 * h + 1], L.Dl[k][3 * h + 2]};
         const R dD[3] = {L.pv[k][3 * h], L.pv[k][3 * h + 1], L.pv[k][3 * h + 2]};
         for (int i = 0; i < 3; ++i) {
           dmax = fmax(dmax, fabs(dD[i]));
@@ -822,6 +836,8 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
             bad = bad || !(fabs(dz[a]) <= R(1e30)) || !(fabs(dsv[a]) <= R(1e30));
             sv[a] = w.s[cv(o, h, a, p, NP)];
             zv[a] = w.z[cv(o, h, a, p, NP)];
+            w.prz[cv(o, h, a, p, NP)] = dsv[a];     // the directions, for the update below
+            w.pg[cv(o, h, a, p, NP)] = dz[a];
           }
           amin = fmin(amin, soc_max_step(sv, dsv));
           amin = fmin(amin, soc_max_step(zv, dz));
@@ -841,14 +857,11 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (2 * p + h >= S.nv) continue;
-        const R D[3] = {L.Dl[k][3 * h], L.Dl[k][3 * h + 1], L.Dl[k][3 * h + 2]};
-        const R dD[3] = {L.pv[k][3 * h], L.pv[k][3 * h + 1], L.pv[k][3 * h + 2]};
         for (int o = 0; o < nobs; ++o) {
-          R dsv[3], dz[3], sv[3], zv[3];
-          pair_step(S, w, o, h, p, dD, dsv, dz);
+          R sv[3], zv[3];
           for (int a = 0; a < 3; ++a) {
-            sv[a] = w.s[cv(o, h, a, p, NP)] + alpha * dsv[a];
-            zv[a] = w.z[cv(o, h, a, p, NP)] + alpha * dz[a];
+            sv[a] = w.s[cv(o, h, a, p, NP)] + alpha * w.prz[cv(o, h, a, p, NP)];
+            zv[a] = w.z[cv(o, h, a, p, NP)] + alpha * w.pg[cv(o, h, a, p, NP)];
             w.s[cv(o, h, a, p, NP)] = sv[a];
             w.z[cv(o, h, a, p, NP)] = zv[a];
           }
