@@ -34,9 +34,10 @@ Readings taken where the paper is silent (the same readings drive the CUDA path)
   cone QP method).  Its central path at kappa is exactly the smoothed model (s o z = kappa e,
   s^T lam = kappa); the nonsmooth SOCP is the end of the path, declared reached at kappa_hard.
   When every phi_i(q*) >= 0, Delta = 0 is the exact nonsmooth optimum and is returned as is.
-* Newton directions use the exact Hessian when it is positive definite, else the Hessian with
-  each spring's transverse factor (1 - L/l) clamped at 0; a backtracking Armijo search on the
-  stage-1 potential Psi (whose gradient is F) globalises it.
+* Newton directions use the exact Hessian when it is positive definite, else (rope) the Hessian
+  with each spring's transverse factor (1 - L/l) clamped at 0 or (cloth) the exact Hessian plus
+  a multiple of the identity; a backtracking Armijo search on the stage-1 potential Psi (whose
+  gradient is F) globalises it.
 """
 from __future__ import annotations
 
@@ -267,21 +268,58 @@ def band_solve_cols(cb, R):
     return cho_solve_banded((cb, True), R)
 
 
+def shift_floor(sc: Scene):
+    """Smallest nonzero diagonal shift of the cloth's stage-1 Newton: a quarter of the proximal
+    stiffness m/dt^2 of one node."""
+    return 0.25 * sc.w
+
+
+def shifted_factor(sc: Scene, X, d, tau_prev):
+    """Cholesky factor of dF/dq* + tau I with the smallest tau of the sequence 0 or tau_prev/2,
+    then doubling (at least shift_floor) that is positive definite -- Cholesky with an added
+    multiple of the identity (Nocedal & Wright, Numerical Optimization, 2nd ed., Alg. 3.3), its
+    first trial taken from the previous iteration's shift.  Returns (factor, tau) or (None, tau)."""
+    ab = stage1_hessian_band(sc, X, d)
+    beta = shift_floor(sc)
+    tau = 0.5 * tau_prev if 0.5 * tau_prev >= beta else 0.0
+    for _ in range(64):
+        a2 = ab.copy()
+        a2[0] += tau
+        try:
+            return band_factor(a2), tau
+        except LinAlgError:
+            tau = max(2.0 * tau, beta)
+    return None, tau
+
+
 def stage1_solve(sc: Scene, x, gstar, d, tol=TOL_X, maxit=NEWTON_MAX, x_start=None):
     """Damped Newton for the root q* of F, started at q (Sec. 4.1, "solved using Newton's
     method") or at x_start when given.  Stops when the Newton step is below `tol` in every
-    coordinate (the step is then taken).  Returns (q*, iterations, status)."""
+    coordinate (the step is then taken).  Returns (q*, iterations, status).
+
+    The direction: for a rope, the exact Hessian, or the projected one where the exact one is
+    not positive definite.  For a cloth, the exact Hessian plus the shift of `shifted_factor`, and
+    the iteration only stops on an unshifted step, so the root is a local minimiser of Psi: a
+    slack cloth has many wrinkle modes of nearly zero stiffness, along which the projected
+    Hessian (which drops their negative curvature) gives only linear convergence."""
     X = x.copy() if x_start is None else np.array(x_start, dtype=np.float64)
+    cloth = sc.kind == "cloth"
+    tau = 0.0
     for it in range(maxit):
         F = stage1_residual(sc, X, x, gstar, d)
         if not np.all(np.isfinite(F)):
             return X, it, ST_NONFINITE
-        try:
-            cb = band_factor(stage1_hessian_band(sc, X, d))
-        except LinAlgError:
-            cb = band_factor(stage1_hessian_band(sc, X, d, project=True))
+        if cloth:
+            cb, tau = shifted_factor(sc, X, d, tau)
+            if cb is None:
+                return X, it + 1, ST_NONFINITE
+        else:
+            try:
+                cb = band_factor(stage1_hessian_band(sc, X, d))
+            except LinAlgError:
+                cb = band_factor(stage1_hessian_band(sc, X, d, project=True))
         p = -band_solve(cb, F)
-        if np.max(np.abs(p)) <= tol:
+        if np.max(np.abs(p)) <= tol and tau == 0.0:
             return X + p, it + 1, 0
         slope = float(np.sum(F * p))
         alpha = 1.0

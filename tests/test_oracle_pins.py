@@ -596,3 +596,107 @@ def test_saddle_root_has_no_defined_step_jacobian():
     # a small push keeps the chain stable: defined Jacobian
     jac2 = grad.SmoothStepJacobian(sc, q, u * 1e-3)
     assert jac2.defined and jac2.status == 0
+
+
+# ------------------------------------------------------------------------------------------
+# cloth stage 1
+# ------------------------------------------------------------------------------------------
+
+def _cloth_params(rows, cols, **kw):
+    p = scenes.default_params("cloth")
+    p.update(rows=rows, cols=cols, n_nodes=rows * cols, obstacles=[])
+    p.update(kw)
+    return p
+
+
+def test_one_row_cloth_is_a_rope():
+    """A cloth of one row has exactly the rope's springs (structural along the row = stretch,
+    distance-2 along the row = bend); on a well-posed step (both roots minimisers) the cloth's
+    shifted Newton and the rope's Newton reach the same root."""
+    n = 9
+    X0 = np.stack([np.linspace(0.0, 0.4, n), np.zeros(n), np.full(n, 0.3)], axis=1)
+    prm = dict(node_mass=0.01, dt=0.01, k_stretch=500.0, k_bend=25.0, D_max=1e4,
+               grasp_nodes=(0, n - 1), gravity=(0, 0, -9.81))
+    pr = scenes.default_params("rope"); pr.update(n_nodes=n, obstacles=[], **prm)
+    pc = _cloth_params(1, n, **prm)
+    sr, sc = sim.Scene(pr, X0), sim.Scene(pc, X0)
+    assert sorted(zip(sr.a, sr.b, sr.k)) == sorted(zip(sc.a, sc.b, sc.k))
+    q0 = sim.join_q(X0, X0[[0, n - 1]])
+    U = np.tile([0.01, 0.0, 0.0, -0.01, 0.0, 0.0], (4, 1))      # pull the ends apart: taut
+    tr, st_r, _ = sim.rollout(sr, q0, U, sim.HARD)
+    tc, st_c, _ = sim.rollout(sc, q0, U, sim.HARD)
+    assert st_r == 0 and st_c == 0
+    np.testing.assert_allclose(tc, tr, rtol=0, atol=1e-12)
+
+
+def test_cloth_linear_springs_equilibrium_is_a_linear_solve():
+    """Zero rest lengths make every spring linear, E = sum k/2 |x_b - x_a|^2, so stage 1 is the
+    linear system (w I + K + D_g) x* = w x + m g + D_g g*, with K the spring-weighted graph
+    Laplacian of the grid.  The test enumerates the grid's springs itself (4-neighbour
+    structural, both diagonals of every cell shear, distance-2 along rows and columns bend)."""
+    R, C = 4, 5
+    n = R * C
+    rng = np.random.default_rng(3)
+    X0 = rng.normal(0.0, 0.05, size=(n, 3)) + np.array([0.0, 0.0, 0.3])
+    rest = np.zeros((n, 3))                     # every rest length 0
+    ks, ksh, kb, m, dt, D = 40.0, 20.0, 5.0, 0.01, 0.01, 300.0
+    p = _cloth_params(R, C, node_mass=m, dt=dt, k_stretch=ks, k_shear=ksh, k_bend=kb, D_max=D,
+                      grasp_nodes=(0, C - 1), gravity=(0, 0, -9.81))
+    sc = sim.Scene(p, rest)
+    g = X0[[0, C - 1]]
+    u = np.array([0.01, 0.02, -0.01, -0.02, 0.0, 0.01])
+    q1, st = sim.step(sc, sim.join_q(X0, g), u, sim.HARD)
+    assert st == 0
+    Kl = np.zeros((n, n))
+    def spring(i, j, k):
+        Kl[i, i] += k; Kl[j, j] += k; Kl[i, j] -= k; Kl[j, i] -= k
+    idx = lambda r, c: r * C + c
+    for r in range(R):
+        for c in range(C):
+            if c + 1 < C: spring(idx(r, c), idx(r, c + 1), ks)
+            if r + 1 < R: spring(idx(r, c), idx(r + 1, c), ks)
+            if r + 1 < R and c + 1 < C:
+                spring(idx(r, c), idx(r + 1, c + 1), ksh); spring(idx(r, c + 1), idx(r + 1, c), ksh)
+            if c + 2 < C: spring(idx(r, c), idx(r, c + 2), kb)
+            if r + 2 < R: spring(idx(r, c), idx(r + 2, c), kb)
+    w = m / dt ** 2
+    A = w * np.eye(n) + Kl
+    rhs = w * X0 + m * np.array([0.0, 0.0, -9.81])
+    gs = g + u.reshape(2, 3)
+    for i, j in enumerate((0, C - 1)):          # both grippers grasp (|c| = 0 <= r_grasp)
+        A[j, j] += D
+        rhs[j] += D * gs[i]
+    x_ref = np.linalg.solve(A, rhs)
+    x1, g1 = sim.split_q(sc, q1)
+    np.testing.assert_allclose(x1, x_ref, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(g1, gs, rtol=0, atol=0)
+
+
+def test_cloth_root_is_a_local_minimiser():
+    """On a slack 16 x 16 cloth the shifted Newton ends at a point where F = 0 and dF/dq* is positive definite (it stops only on an unshifted step):
+    a local minimiser of Psi, i.e. a stable quasi-static equilibrium."""
+    sc_ = scenes.cloth_scene(16, 16, n_spheres=0, seed=5)
+    sc = sim.Scene(sc_["params"], sc_["rest_x"])
+    u = scenes.controls_normal_clear(sc_, 1, 1, seed=9)[0, 0]
+    x, g = sim.split_q(sc, sc_["q0"])
+    d = sim.grasp_stiffness(sc, x, g, sim.HARD)
+    gs = g + u.reshape(2, 3)
+    X0 = x.copy()
+    for i in range(2):
+        X0[sc.grasp[i]] += u[3 * i:3 * i + 3]
+    xs, it, st = sim.stage1_solve(sc, x, gs, d, x_start=X0)
+    assert st == 0 and it > 1
+    F = sim.stage1_residual(sc, xs, x, gs, d)
+    assert np.abs(F).max() <= 1e-9 * np.abs(sim.stage1_residual(sc, X0, x, gs, d)).max()
+    ev = np.linalg.eigvalsh(_dense_from_band(sim.stage1_hessian_band(sc, xs, d)))
+    assert ev.min() > 0.0
+
+
+def _dense_from_band(ab):
+    bw, n = ab.shape[0] - 1, ab.shape[1]
+    A = np.zeros((n, n))
+    for k in range(bw + 1):
+        i = np.arange(n - k)
+        A[i + k, i] = ab[k, : n - k]
+        A[i, i + k] = ab[k, : n - k]
+    return A
