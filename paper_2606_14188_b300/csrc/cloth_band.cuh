@@ -1,0 +1,396 @@
+// Cloth topology and the CTA-wide banded Cholesky of the cloth path.
+//
+// A cloth of R x C nodes (node (r, c) = r C + c, row-major) has six spring families: structural
+// along rows (r, c)-(r, c+1) and columns (r, c)-(r+1, c), shear along both diagonals of every cell,
+// and bend at distance two along rows and columns.  Every node-coupled matrix of the method
+// (dF/dq*, the stage-2 Newton matrix H2 = P + sum A^T M A) is symmetric and banded with scalar half
+// bandwidth bw = 3 span + 2, span = the largest node-index difference of a spring (2 C).
+//
+// Factorisation: one CTA, right-looking and blocked by panels of CL_KB columns over a window of
+// the band held in shared memory.  Columns are assembled straight into the window as they enter it
+// (spring Hessian blocks computed there, diagonal blocks from a node array), the panel is factored
+// by one warp while the rank-CL_KB update of the trailing triangle is shared by all threads, and the
+// finished panel is written to global memory (column-major band, stride LDB) for the backward
+// solve.  The forward substitution of one right-hand side is fused into the panel step.
+#pragma once
+#include "common.cuh"
+
+namespace cs {
+
+constexpr int CL_NT = 256;              // threads per CTA
+constexpr int CL_NW = CL_NT / 32;
+constexpr int CL_KB = 12;               // panel width (four nodes)
+
+struct ClothDims {
+  int R, C, nv, N;       // grid, nodes, unknowns (3 nv)
+  int bw;                // scalar half bandwidth
+  int LDW, WC;           // window: column stride, columns held (multiple of 3)
+  int LDB;               // global factor column stride (multiple of 4)
+  int PL;                // panel buffer row length
+  int nspr;              // springs
+  int off[7];            // first spring of each family (off[6] = nspr)
+};
+
+__host__ __device__ inline int cl_rup(int x, int m) { return (x + m - 1) / m * m; }
+
+__host__ __device__ inline ClothDims cloth_dims(int R, int C) {
+  ClothDims d;
+  d.R = R; d.C = C; d.nv = R * C; d.N = 3 * d.nv;
+  int span = 0;
+  if (C >= 2) span = 1;
+  if (C >= 3) span = 2;
+  if (R >= 2 && C > span) span = C;
+  if (R >= 2 && C >= 2 && C + 1 > span) span = C + 1;
+  if (R >= 3 && 2 * C > span) span = 2 * C;
+  d.bw = 3 * span + 2;
+  d.LDW = d.bw + 1;
+  d.WC = cl_rup(d.bw + CL_KB, 3);
+  d.LDB = cl_rup(d.bw + 1, 4);
+  d.PL = cl_rup(d.bw + CL_KB + 3, 4);
+  const int nh = R * (C - 1), nvt = (R - 1) * C, nd = (R - 1) * (C - 1);
+  const int nbh = C >= 3 ? R * (C - 2) : 0, nbv = R >= 3 ? (R - 2) * C : 0;
+  d.off[0] = 0;
+  d.off[1] = d.off[0] + (C >= 2 ? nh : 0);
+  d.off[2] = d.off[1] + (R >= 2 ? nvt : 0);
+  d.off[3] = d.off[2] + (R >= 2 && C >= 2 ? nd : 0);
+  d.off[4] = d.off[3] + (R >= 2 && C >= 2 ? nd : 0);
+  d.off[5] = d.off[4] + nbh;
+  d.off[6] = d.off[5] + nbv;
+  d.nspr = d.off[6];
+  return d;
+}
+
+// shared memory of one CTA (elements of the real type): window (or the two staging panels of a
+// solve), panel buffer, right-hand side, panel partial sums, reductions, step scalars
+__host__ __device__ inline size_t cloth_smem_elems(const ClothDims& d) {
+  const size_t win = (size_t)d.WC * d.LDW;
+  const size_t stg = (size_t)2 * CL_KB * d.LDB;
+  return (win > stg ? win : stg) + (size_t)CL_KB * d.PL + (size_t)d.N + CL_KB + 64 + 64;
+}
+
+// elements of one CTA's workspace slot in global memory: eight node vectors [N], the diagonal
+// blocks [nv][6], the contact pairs (s, z, n, g, r_z [3], phi [1], M [6] per pair) and the band
+// factor [N][LDB], each array padded to a multiple of 4 elements
+__host__ __device__ inline size_t cloth_ws_elems(const ClothDims& D, int nobs) {
+  const size_t N = (size_t)D.N, np = (size_t)nobs * D.nv;
+  auto r4 = [](size_t x) { return (x + 3) & ~(size_t)3; };
+  return 8 * r4(N) + r4(6 * (size_t)D.nv) + 5 * r4(3 * np) + r4(np) + r4(6 * np) + r4(N * D.LDB);
+}
+
+// spring s -> nodes a < b and family (0, 1 structural; 2, 3 shear; 4, 5 bend)
+__device__ __forceinline__ void cl_spring(const ClothDims& D, int s, int& a, int& b, int& fam) {
+  fam = 0;
+  while (s >= D.off[fam + 1]) ++fam;
+  const int i = s - D.off[fam], C = D.C;
+  int r, c;
+  switch (fam) {
+    case 0: r = i / (C - 1); c = i - r * (C - 1); a = r * C + c; b = a + 1; break;
+    case 1: r = i / C; c = i - r * C; a = r * C + c; b = a + C; break;
+    case 2: r = i / (C - 1); c = i - r * (C - 1); a = r * C + c; b = a + C + 1; break;
+    case 3: r = i / (C - 1); c = i - r * (C - 1); a = r * C + c + 1; b = (r + 1) * C + c; break;
+    case 4: r = i / (C - 2); c = i - r * (C - 2); a = r * C + c; b = a + 2; break;
+    default: r = i / C; c = i - r * C; a = r * C + c; b = a + 2 * C; break;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R cl_stiff(const Scene<R>& S, int fam) {
+  return fam < 2 ? S.k1 : (fam < 4 ? S.k3 : S.k2);
+}
+
+// incident spring t (0..11) of node v = (r, c): returns its index (or -1) and the other node u;
+// even t: v is the lower node (d = x_u - x_v), odd t: v is the upper node (d = x_v - x_u)
+__device__ __forceinline__ int cl_incident(const ClothDims& D, int v, int t, int& u, int& fam) {
+  const int C = D.C, Rr = D.R;
+  const int r = v / C, c = v - r * C;
+  fam = t >> 1;
+  switch (t) {
+    case 0: if (c + 1 < C) { u = v + 1; return D.off[0] + r * (C - 1) + c; } break;
+    case 1: if (c >= 1) { u = v - 1; return D.off[0] + r * (C - 1) + c - 1; } break;
+    case 2: if (r + 1 < Rr) { u = v + C; return D.off[1] + r * C + c; } break;
+    case 3: if (r >= 1) { u = v - C; return D.off[1] + (r - 1) * C + c; } break;
+    case 4: if (r + 1 < Rr && c + 1 < C) { u = v + C + 1; return D.off[2] + r * (C - 1) + c; } break;
+    case 5: if (r >= 1 && c >= 1) { u = v - C - 1; return D.off[2] + (r - 1) * (C - 1) + c - 1; } break;
+    case 6: if (r + 1 < Rr && c >= 1) { u = v + C - 1; return D.off[3] + r * (C - 1) + c - 1; } break;
+    case 7: if (r >= 1 && c + 1 < C) { u = v - C + 1; return D.off[3] + (r - 1) * (C - 1) + c; } break;
+    case 8: if (c + 2 < C) { u = v + 2; return D.off[4] + r * (C - 2) + c; } break;
+    case 9: if (c >= 2) { u = v - 2; return D.off[4] + r * (C - 2) + c - 2; } break;
+    case 10: if (r + 2 < Rr) { u = v + 2 * C; return D.off[5] + r * C + c; } break;
+    default: if (r >= 2) { u = v - 2 * C; return D.off[5] + (r - 2) * C + c; } break;
+  }
+  return -1;
+}
+
+// ---- CTA reductions (every thread gets the same value, summed in the same order)
+template <typename R>
+__device__ __forceinline__ R cl_sum(R v, R* red) {
+  v = wsum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R t = R(0);
+#pragma unroll
+  for (int i = 0; i < CL_NW; ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+template <typename R>
+__device__ __forceinline__ R cl_max(R v, R* red) {
+  v = wmax(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  R t = red[0];
+#pragma unroll
+  for (int i = 1; i < CL_NW; ++i) t = red[i] > t ? red[i] : t;
+  __syncthreads();
+  return t;
+}
+
+// symmetric 3x3 block as 6 numbers: (0,0) (1,0) (1,1) (2,0) (2,1) (2,2)
+__device__ __forceinline__ int sym3(int a, int b) { return a >= b ? a * (a + 1) / 2 + b : b * (b + 1) / 2 + a; }
+
+// The matrix being factored: diagonal 3x3 blocks Dg[v] (already holding everything node-local)
+// and, for every spring (v, u > v), the off-diagonal block -H_s at the positions x0 + dx.
+template <typename R>
+struct BandSrc {
+  const R* x0;
+  const R* dx;
+  const R* Dg;       // [nv][6]
+  bool proj;         // projected spring Hessians (transverse factor clamped at 0)
+};
+
+// spring Hessian block of spring s between v (lower) and u at the positions x0 + dx
+template <typename R>
+__device__ __forceinline__ void cl_spring_hess(const Scene<R>& S, const R* x0, const R* dx, int v, int u,
+                                               int s, int fam, bool proj, R f[3], R H[9]) {
+  R d[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) d[i] = (x0[3 * u + i] - x0[3 * v + i]) + (dx[3 * u + i] - dx[3 * v + i]);
+  spring_eval(d, cl_stiff(S, fam), S.L1[s], proj, f, H);
+}
+
+// assemble the columns of nodes [v0, v1) into their window slots
+template <typename R>
+__device__ __forceinline__ void cl_load_cols(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M,
+                                             R* Wn, int v0, int v1) {
+  const int ncol = 3 * (v1 - v0);
+  for (int idx = threadIdx.x; idx < ncol * D.LDW; idx += CL_NT) {
+    const int col = 3 * v0 + idx / D.LDW;
+    Wn[(col % D.WC) * D.LDW + idx % D.LDW] = R(0);
+  }
+  __syncthreads();
+  for (int task = threadIdx.x; task < 7 * (v1 - v0); task += CL_NT) {
+    const int v = v0 + task / 7, t = task % 7;
+    if (t == 0) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = b; a < 3; ++a) Wn[((3 * v + b) % D.WC) * D.LDW + (a - b)] = M.Dg[6 * v + sym3(a, b)];
+    } else {
+      int u, fam;
+      const int s = cl_incident(D, v, 2 * (t - 1), u, fam);
+      if (s < 0) continue;
+      R f[3], H[9];
+      cl_spring_hess(S, M.x0, M.dx, v, u, s, fam, M.proj, f, H);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          Wn[((3 * v + b) % D.WC) * D.LDW + (3 * (u - v) + a - b)] = -H[a * 3 + b];
+    }
+  }
+  __syncthreads();
+}
+
+// Cholesky factorisation L L^T of the band matrix M into Lg [N][LDB] (column c: rows c .. c+bw),
+// with the forward substitution L y = vb fused (vb in shared memory becomes y).  Returns false,
+// uniformly over the CTA, when a pivot is not positive (the matrix is not positive definite).
+template <typename R>
+__device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M, R* Lg, R* sm) {
+  R* Wn = sm;
+  const size_t win = (size_t)D.WC * D.LDW, stg = (size_t)2 * CL_KB * D.LDB;
+  R* Pb = sm + (win > stg ? win : stg);
+  R* vb = Pb + (size_t)CL_KB * D.PL;
+  R* flag = vb + D.N + CL_KB + 63;         // last slot of the reduction area: failure flag
+  const int N = D.N, bw = D.bw, WC = D.WC, LDW = D.LDW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) flag[0] = R(0);
+  cl_load_cols(S, D, M, Wn, 0, min(WC, N) / 3);
+  for (int j = 0; j < N; j += CL_KB) {
+    const int jn = min(j + CL_KB, N), kbp = jn - j;
+    if (warp == 0) {
+      bool bad = false;
+      for (int c = j; c < jn; ++c) {
+        R* col = Wn + (c % WC) * LDW;
+        const R dg = col[0];
+        if (!(dg > R(0)) || !(dg < R(1e300))) { bad = true; break; }
+        const R l = sqrt(dg), il = R(1) / l;
+        const R y = vb[c] * il;
+        __syncwarp();
+        if (lane == 0) { col[0] = l; vb[c] = y; }
+        const int rmax = min(bw, N - 1 - c);
+        for (int r = 1 + lane; r <= rmax; r += 32) {
+          const R lv = col[r] * il;
+          col[r] = lv;
+          vb[c + r] -= lv * y;
+        }
+        __syncwarp();
+        const int imax = min(c + bw, N - 1);
+        for (int c2 = c + 1; c2 < jn && c2 - c <= bw; ++c2) {
+          const R f = col[c2 - c];
+          R* dst = Wn + (c2 % WC) * LDW;
+          for (int i = c2 + lane; i <= imax; i += 32) dst[i - c2] -= col[i - c] * f;
+        }
+        __syncwarp();
+      }
+      if (bad && lane == 0) flag[0] = R(1);
+    }
+    __syncthreads();
+    if (flag[0] != R(0)) return false;
+    // panel -> dense buffer (zero outside the band) and -> global factor
+    for (int idx = threadIdx.x; idx < CL_KB * D.PL; idx += CL_NT) {
+      const int cc = idx / D.PL, ii = idx - cc * D.PL;
+      const int c = j + cc, i = j + ii;
+      R val = R(0);
+      if (cc < kbp && i >= c && i - c <= bw && i < N) val = Wn[(c % WC) * LDW + (i - c)];
+      Pb[idx] = val;
+    }
+    for (int idx = threadIdx.x; idx < kbp * LDW; idx += CL_NT) {
+      const int cc = idx / LDW, r = idx - cc * LDW;
+      Lg[(size_t)(j + cc) * D.LDB + r] = Wn[((j + cc) % WC) * LDW + r];
+    }
+    __syncthreads();
+    // rank-kbp update of the trailing triangle [jn, jn + T)
+    const int T = min(bw, N - jn);
+    const int nt = (T + 3) >> 2, ntiles = nt * (nt + 1) / 2;
+    for (int id = threadIdx.x; id < ntiles; id += CL_NT) {
+      int a = (int)((sqrtf(8.0f * (float)id + 1.0f) - 1.0f) * 0.5f);
+      while (a * (a + 1) / 2 > id) --a;
+      while ((a + 1) * (a + 2) / 2 <= id) ++a;
+      const int b = id - a * (a + 1) / 2;
+      R acc[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = R(0);
+      const R* pr = Pb + kbp + 4 * a;
+      const R* pc = Pb + kbp + 4 * b;
+      for (int cc = 0; cc < kbp; ++cc) {
+        R ra[4], cb[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) { ra[x] = pr[cc * D.PL + x]; cb[x] = pc[cc * D.PL + x]; }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] += ra[x] * cb[y];
+      }
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int k = jn + 4 * b + y;
+        if (k >= jn + T) continue;
+        R* dst = Wn + (k % WC) * LDW;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const int i = jn + 4 * a + x;
+          if (i < jn + T && i >= k) dst[i - k] -= acc[x][y];
+        }
+      }
+    }
+    __syncthreads();
+    const int c0 = j + WC, c1 = min(j + WC + kbp, N);
+    if (c0 < c1) cl_load_cols(S, D, M, Wn, c0 / 3, c1 / 3);
+  }
+  return true;
+}
+
+// stage the factor's panel [j, j + kbp) (contiguous in Lg) into a shared buffer
+template <typename R>
+__device__ __forceinline__ void cl_stage(const ClothDims& D, const R* Lg, int j, int kbp, R* buf) {
+  const R* src = Lg + (size_t)j * D.LDB;
+  for (int idx = threadIdx.x; idx < kbp * D.LDB; idx += CL_NT) buf[idx] = src[idx];
+}
+
+// backward substitution L^T x = vb in place (vb in shared memory), panels from the last
+template <typename R>
+__device__ __noinline__ void cl_back(const ClothDims& D, const R* Lg, R* sm) {
+  const size_t win = (size_t)D.WC * D.LDW, stg = (size_t)2 * CL_KB * D.LDB;
+  R* vb = sm + (win > stg ? win : stg) + (size_t)CL_KB * D.PL;
+  R* tc = vb + D.N;
+  const int N = D.N, bw = D.bw, LDB = D.LDB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int jlast = ((N - 1) / CL_KB) * CL_KB;
+  int buf = 0;
+  cl_stage(D, Lg, jlast, N - jlast, sm);
+  __syncthreads();
+  for (int j = jlast; j >= 0; j -= CL_KB) {
+    const int jn = min(j + CL_KB, N), kbp = jn - j;
+    const R* Lb = sm + (size_t)buf * CL_KB * LDB;
+    if (j > 0) cl_stage(D, Lg, j - CL_KB, CL_KB, sm + (size_t)(buf ^ 1) * CL_KB * LDB);
+    for (int cc = warp; cc < kbp; cc += CL_NW) {
+      const int c = j + cc;
+      const R* col = Lb + cc * LDB;
+      const int imax = min(c + bw, N - 1);
+      R acc = R(0);
+      for (int i = jn + lane; i <= imax; i += 32) acc += col[i - c] * vb[i];
+      acc = wsum(acc);
+      if (lane == 0) tc[cc] = acc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int c = jn - 1; c >= j; --c) {
+        const R* col = Lb + (c - j) * LDB;
+        const int i = c + 1 + lane;
+        R acc = (i < jn && i - c <= bw) ? col[i - c] * vb[i] : R(0);
+        acc = wsum(acc);
+        __syncwarp();
+        if (lane == 0) vb[c] = (vb[c] - tc[c - j] - acc) / col[0];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+}
+
+// forward substitution L y = vb in place
+template <typename R>
+__device__ __noinline__ void cl_fwd(const ClothDims& D, const R* Lg, R* sm) {
+  const size_t win = (size_t)D.WC * D.LDW, stg = (size_t)2 * CL_KB * D.LDB;
+  R* vb = sm + (win > stg ? win : stg) + (size_t)CL_KB * D.PL;
+  const int N = D.N, bw = D.bw, LDB = D.LDB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int buf = 0;
+  cl_stage(D, Lg, 0, min(CL_KB, N), sm);
+  __syncthreads();
+  for (int j = 0; j < N; j += CL_KB) {
+    const int jn = min(j + CL_KB, N), kbp = jn - j;
+    const R* Lb = sm + (size_t)buf * CL_KB * LDB;
+    if (jn < N) cl_stage(D, Lg, jn, min(CL_KB, N - jn), sm + (size_t)(buf ^ 1) * CL_KB * LDB);
+    if (warp == 0) {
+      for (int c = j; c < jn; ++c) {
+        const R* col = Lb + (c - j) * LDB;
+        const R y = vb[c] / col[0];
+        __syncwarp();
+        if (lane == 0) vb[c] = y;
+        const int i = c + 1 + lane;
+        if (i < jn && i - c <= bw) vb[i] -= col[i - c] * y;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // rows below the panel
+    const int imax = min(jn - 1 + bw, N - 1);
+    for (int i = jn + threadIdx.x; i <= imax; i += CL_NT) {
+      R acc = R(0);
+      for (int cc = 0; cc < kbp; ++cc) {
+        const int c = j + cc;
+        if (i - c <= bw) acc += Lb[cc * LDB + (i - c)] * vb[c];
+      }
+      vb[i] -= acc;
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+}
+
+}  // namespace cs

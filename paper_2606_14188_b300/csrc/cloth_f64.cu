@@ -1,0 +1,8 @@
+// cloth kernels, double instantiation.
+#include "launch_cloth.cuh"
+
+namespace csi {
+template cs_status launch_cloth_rollout<double>(cs_sim*, int, int, const void*, const void*, void*, void*, int32_t*, int32_t*, cudaStream_t);
+template cs_status launch_cloth_vjp<double>(cs_sim*, int, int, const void*, const void*, const void*, const cs_loss*, void*, void*, void*, int32_t*, cudaStream_t);
+template int cloth_ctas_per_sm<double>(const cs_sim*);
+}  // namespace csi

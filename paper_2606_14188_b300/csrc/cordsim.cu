@@ -47,9 +47,12 @@ extern "C" {
 cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   if (!P || !rest_x || !out) return cs_fail(CS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
-  if (P->kind != CS_ROPE) return cs_fail(CS_ERR_UNSUPPORTED, "only kind = CS_ROPE is built");
+  if (P->kind != CS_ROPE && P->kind != CS_CLOTH) return cs_fail(CS_ERR_INVALID_ARG, "unknown kind");
+  const bool cloth = P->kind == CS_CLOTH;
   const int nv = P->n_nodes;
-  if (nv < 2 || nv > 128) return cs_fail(CS_ERR_INVALID_ARG, "rope n_nodes must be in [2, 128]");
+  if (!cloth && (nv < 2 || nv > 128)) return cs_fail(CS_ERR_INVALID_ARG, "rope n_nodes must be in [2, 128]");
+  if (cloth && (P->rows < 1 || P->cols < 2 || P->rows > 256 || P->cols > 256 || nv != P->rows * P->cols))
+    return cs_fail(CS_ERR_INVALID_ARG, "cloth needs rows >= 1, cols >= 2 and n_nodes = rows * cols");
   for (int i = 0; i < 2; ++i)
     if (P->grasp_node[i] < 0 || P->grasp_node[i] >= nv)
       return cs_fail(CS_ERR_INVALID_ARG, "grasp_node out of range");
@@ -86,20 +89,41 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   s->sms = v;
   cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   s->smem_optin = (size_t)v;
-  if (smem_bytes(s, 1, false) > s->smem_optin) {
-    delete s;
-    return cs_fail(CS_ERR_INVALID_ARG, "scene too large for one warp's shared memory");
-  }
-
-  // rest lengths in the kernels' real type
-  std::vector<double> L1(nv - 1), L2(nv > 2 ? nv - 2 : 1, 0.0);
   auto dist = [&](int a, int b) {
     double d0 = rest_x[3 * b] - rest_x[3 * a], d1 = rest_x[3 * b + 1] - rest_x[3 * a + 1],
            d2 = rest_x[3 * b + 2] - rest_x[3 * a + 2];
     return std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
   };
-  for (int j = 0; j + 1 < nv; ++j) L1[j] = dist(j, j + 1);
-  for (int j = 0; j + 2 < nv; ++j) L2[j] = dist(j, j + 2);
+  // rest lengths in the kernels' real type (cloth: every spring, family by family)
+  std::vector<double> L1, L2(1, 0.0);
+  if (cloth) {
+    s->cd = cs::cloth_dims(P->rows, P->cols);
+    if (cs::cloth_smem_elems(s->cd) * (size_t)P->real_bytes > s->smem_optin) {
+      delete s;
+      return cs_fail(CS_ERR_INVALID_ARG, "cloth too wide for the band window in shared memory");
+    }
+    const int R = P->rows, C = P->cols;
+    auto id = [&](int r, int c) { return r * C + c; };
+    for (int r = 0; r < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c), id(r, c + 1)));
+    for (int r = 0; r + 1 < R; ++r) for (int c = 0; c < C; ++c) L1.push_back(dist(id(r, c), id(r + 1, c)));
+    for (int r = 0; r + 1 < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c), id(r + 1, c + 1)));
+    for (int r = 0; r + 1 < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c + 1), id(r + 1, c)));
+    for (int r = 0; r < R; ++r) for (int c = 0; c + 2 < C; ++c) L1.push_back(dist(id(r, c), id(r, c + 2)));
+    for (int r = 0; r + 2 < R; ++r) for (int c = 0; c < C; ++c) L1.push_back(dist(id(r, c), id(r + 2, c)));
+    if ((int)L1.size() != s->cd.nspr) {
+      delete s;
+      return cs_fail(CS_ERR_INVALID_ARG, "cloth spring count mismatch");
+    }
+  } else {
+    if (smem_bytes(s, 1, false) > s->smem_optin) {
+      delete s;
+      return cs_fail(CS_ERR_INVALID_ARG, "scene too large for one warp's shared memory");
+    }
+    L1.assign(nv - 1, 0.0);
+    L2.assign(nv > 2 ? nv - 2 : 1, 0.0);
+    for (int j = 0; j + 1 < nv; ++j) L1[j] = dist(j, j + 1);
+    for (int j = 0; j + 2 < nv; ++j) L2[j] = dist(j, j + 2);
+  }
   const size_t rb = (size_t)s->real_bytes;
   auto upload = [&](const std::vector<double>& h, void** d) -> cudaError_t {
     cudaError_t er = cudaMalloc(d, h.size() * rb);
@@ -122,6 +146,18 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
     sim_destroy(s);
     return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "adjoint workspace") : cs_cuda_fail(e, "cudaMalloc");
   }
+  if (cloth) {
+    // one workspace slot per CTA the device holds at once (the kernels' grid never exceeds it)
+    const int per_sm = rb == 4 ? cloth_ctas_per_sm<float>(s) : cloth_ctas_per_sm<double>(s);
+    const int resident = per_sm * s->sms;
+    s->nslots = P->max_batch < resident ? P->max_batch : resident;
+    s->slot_stride = cs::cloth_ws_elems(s->cd, P->n_obstacles);
+    e = cudaMalloc(&s->d_slots, s->slot_stride * (size_t)s->nslots * rb);
+    if (e != cudaSuccess) {
+      sim_destroy(s);
+      return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "cloth workspace") : cs_cuda_fail(e, "cudaMalloc");
+    }
+  }
   *out = s;
   g_err.clear();
   return CS_OK;
@@ -133,6 +169,7 @@ cs_status sim_destroy(cs_sim* s) {
   if (s->d_L1) cudaFree(s->d_L1);
   if (s->d_L2) cudaFree(s->d_L2);
   if (s->d_ws) cudaFree(s->d_ws);
+  if (s->d_slots) cudaFree(s->d_slots);
   delete s;
   return CS_OK;
 }
@@ -149,6 +186,9 @@ cs_status sim_rollout_counters(cs_sim* s, int B, int H, const void* q0, const vo
   if (B == 0) return CS_OK;
   if (!q0 || !u) return cs_fail(CS_ERR_INVALID_ARG, "q0 and u are required");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (s->P.kind == CS_CLOTH)
+    return s->real_bytes == 4 ? launch_cloth_rollout<float>(s, B, H, q0, u, traj, qH, status, counters, st)
+                              : launch_cloth_rollout<double>(s, B, H, q0, u, traj, qH, status, counters, st);
   return s->real_bytes == 4 ? launch_rollout<float>(s, B, H, q0, u, traj, qH, status, counters, st)
                             : launch_rollout<double>(s, B, H, q0, u, traj, qH, status, counters, st);
 }
@@ -168,6 +208,10 @@ cs_status sim_rollout_vjp(cs_sim* s, int B, int H, const void* q0, const void* u
   }
   if (B == 0) return CS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (s->P.kind == CS_CLOTH)
+    return s->real_bytes == 4
+               ? launch_cloth_vjp<float>(s, B, H, q0, u, dL_dtraj, loss, L, dL_du, dL_dq0, status, st)
+               : launch_cloth_vjp<double>(s, B, H, q0, u, dL_dtraj, loss, L, dL_du, dL_dq0, status, st);
   return s->real_bytes == 4
              ? launch_vjp<float>(s, B, H, q0, u, dL_dtraj, loss, L, dL_du, dL_dq0, status, st)
              : launch_vjp<double>(s, B, H, q0, u, dL_dtraj, loss, L, dL_du, dL_dq0, status, st);
@@ -179,6 +223,7 @@ cs_status sim_linearize(cs_sim* s, int B, int H, const void* z, const void* v, v
   if (r) return r;
   if (B == 0) return CS_OK;
   if (!z || !v || !A || !Bm) return cs_fail(CS_ERR_INVALID_ARG, "z, v, A and Bm are required");
+  if (s->P.kind == CS_CLOTH) return cs_fail(CS_ERR_UNSUPPORTED, "sim_linearize is built for ropes only");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   return s->real_bytes == 4 ? launch_linearize<float>(s, B, H, z, v, A, Bm, status, st)
                             : launch_linearize<double>(s, B, H, z, v, A, Bm, status, st);

@@ -6,6 +6,7 @@
 #include <string>
 
 #include "cordsim.h"
+#include "cloth_band.cuh"
 #include "common.cuh"
 #include "rope.cuh"
 
@@ -23,6 +24,11 @@ struct cs_sim {
   size_t ws_stride = 0;   // elements per rollout
   int sms = 0;
   size_t smem_optin = 0;
+  // cloth only: band geometry and the per-CTA workspace slots of the cloth kernels
+  cs::ClothDims cd{};
+  void* d_slots = nullptr;
+  size_t slot_stride = 0;  // elements per slot
+  int nslots = 0;
 };
 
 namespace csi {
@@ -121,6 +127,15 @@ template <typename R>
 cs_status launch_vjp(cs_sim* s, int B, int H, const void* q0, const void* u, const void* dLdtraj,
                      const cs_loss* loss, void* L, void* dLdu, void* dLdq0, int32_t* status,
                      cudaStream_t st);
+template <typename R>
+cs_status launch_cloth_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj, void* qH,
+                               int32_t* status, int32_t* counters, cudaStream_t st);
+template <typename R>
+cs_status launch_cloth_vjp(cs_sim* s, int B, int H, const void* q0, const void* u, const void* dLdtraj,
+                           const cs_loss* loss, void* L, void* dLdu, void* dLdq0, int32_t* status,
+                           cudaStream_t st);
+template <typename R>
+int cloth_ctas_per_sm(const cs_sim* s);
 template <typename R>
 cs_status launch_linearize(cs_sim* s, int B, int H, const void* z, const void* v, void* A,
                            void* Bm, int32_t* status, cudaStream_t st);

@@ -1,0 +1,53 @@
+// Kernel launchers of the cloth path (instantiated per real type in cloth_*.cu).  One CTA per
+// rollout at a time over a grid of at most s->nslots CTAs, each with its own workspace slot.
+#pragma once
+#include "cloth.cuh"
+#include "internal.h"
+
+namespace csi {
+
+inline size_t cloth_smem_bytes(const cs_sim* s) { return cs::cloth_smem_elems(s->cd) * (size_t)s->real_bytes; }
+
+template <typename R>
+cs_status launch_cloth_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj, void* qH,
+                               int32_t* status, int32_t* counters, cudaStream_t st) {
+  cs::Scene<R> S = make_scene<R>(s, nullptr);
+  const size_t smem = cloth_smem_bytes(s);
+  cs_status r = prep_kernel(cs::cloth_rollout_kernel<R>, smem);
+  if (r) return r;
+  const int grid = B < s->nslots ? B : s->nslots;
+  cs::cloth_rollout_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, s->cd, B, H, (const R*)q0, (const R*)u, (R*)traj,
+                                                            (R*)qH, status, counters, (R*)s->d_slots,
+                                                            s->slot_stride);
+  return check_launch("cloth_rollout_kernel");
+}
+
+template <typename R>
+cs_status launch_cloth_vjp(cs_sim* s, int B, int H, const void* q0, const void* u, const void* dLdtraj,
+                           const cs_loss* loss, void* L, void* dLdu, void* dLdq0, int32_t* status,
+                           cudaStream_t st) {
+  cs::Scene<R> S = make_scene<R>(s, loss);
+  const size_t smem = cloth_smem_bytes(s);
+  cs_status r = prep_kernel(cs::cloth_vjp_kernel<R>, smem);
+  if (r) return r;
+  const int grid = B < s->nslots ? B : s->nslots;
+  cs::cloth_vjp_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, s->cd, B, H, (const R*)q0, (const R*)u,
+                                                        (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0, status,
+                                                        (R*)s->d_slots, s->slot_stride, (R*)s->d_ws,
+                                                        s->ws_stride);
+  return check_launch("cloth_vjp_kernel");
+}
+
+// resident CTAs per SM of the cloth kernels at their shared-memory size (at least 1)
+template <typename R>
+int cloth_ctas_per_sm(const cs_sim* s) {
+  const size_t smem = cloth_smem_bytes(s);
+  int a = 0, b = 0;
+  if (prep_kernel(cs::cloth_rollout_kernel<R>, smem) || prep_kernel(cs::cloth_vjp_kernel<R>, smem)) return 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cs::cloth_rollout_kernel<R>, cs::CL_NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cs::cloth_vjp_kernel<R>, cs::CL_NT, smem);
+  const int m = a > b ? a : b;
+  return m > 0 ? m : 1;
+}
+
+}  // namespace csi

@@ -104,20 +104,24 @@ def rope_scene(n_nodes: int, n_spheres: int = 1, n_boxes: int = 0, seed: int = B
     obs = [plane((0, 0, 1), 0.0)]
     clear = p["node_radius"] + 0.01
     for _ in range(n_spheres):
-        while True:
+        for _try in range(100000):
             c = [rng.uniform(*sphere_box[k]) for k in range(3)]
             r = rng.uniform(*sphere_r)
             ob = sphere(c, r)
             if _point_clear(rest, ob, clear):
                 break
+        else:
+            raise ValueError("no obstacle placement clear of the rest shape")
         obs.append(ob)
     for _ in range(n_boxes):
-        while True:
+        for _try in range(100000):
             c = [rng.uniform(*box_box[k]) for k in range(3)]
             h = [rng.uniform(*box_half) for _ in range(3)]
             ob = box(c, h)
             if _point_clear(rest, ob, clear):
                 break
+        else:
+            raise ValueError("no obstacle placement clear of the rest shape")
         obs.append(ob)
     p["obstacles"] = obs
     goal_nodes = (0, n_nodes - 1)
@@ -143,18 +147,20 @@ def cloth_scene(rows: int, cols: int, n_spheres: int = 2, seed: int = BASE_SEED,
     p["node_radius"] = 0.002
     p["k_stretch"], p["k_shear"], p["k_bend"] = 500.0, 250.0, 25.0
     r_idx, c_idx = np.meshgrid(np.arange(rows), np.arange(cols), indexing="ij")
-    rest = np.stack([r_idx.ravel() * side / (rows - 1), c_idx.ravel() * side / (cols - 1),
+    rest = np.stack([r_idx.ravel() * side / max(rows - 1, 1), c_idx.ravel() * side / max(cols - 1, 1),
                      np.full(n, height)], axis=1)
     obs = [plane((0, 0, 1), 0.0)]
     clear = p["node_radius"] + 0.01
     for _ in range(n_spheres):
-        while True:
+        for _try in range(100000):
             c = [rng.uniform(-0.1, side + 0.1), rng.uniform(-0.1, side + 0.1),
                  rng.uniform(-0.1, 0.0)]
             r = rng.uniform(0.05, 0.15)
             ob = sphere(c, r)
             if _point_clear(rest, ob, clear):
                 break
+        else:
+            raise ValueError("no obstacle placement clear of the rest shape")
         obs.append(ob)
     p["obstacles"] = obs
     goal_nodes = tuple(range(cols))
