@@ -20,7 +20,7 @@ namespace cs {
 
 template <typename R>
 struct ClothWS {
-  R *x0, *dx, *Dl, *pv, *F, *xb, *mu, *rA;    // [N] node vectors
+  R *x0, *dx, *Dl, *pv, *F, *xb, *mu, *rA;    // [N] node vectors (x0, dx in shared memory)
   R *Dg;                                      // [nv][6] diagonal blocks of the matrix to factor
   R *s, *z, *nrm, *pg, *prz;                  // [nobs nv][3] contact pairs
   R *phi;                                     // [nobs nv]
@@ -35,7 +35,10 @@ __device__ __forceinline__ ClothWS<R> cloth_carve(R* base, const ClothDims& D, i
   const size_t N = (size_t)D.N, np = (size_t)nobs * D.nv;
   R* p = base;
   auto take = [&](size_t n) { R* q = p; p += (n + 3) & ~(size_t)3; return q; };
-  w.x0 = take(N); w.dx = take(N); w.Dl = take(N); w.pv = take(N);
+  // the state x0 and the stage-1 offset dx live in shared memory, after the step scalars
+  w.x0 = reinterpret_cast<R*>(cs_smem) + cloth_smem_elems(D) - 2 * (size_t)D.N;
+  w.dx = w.x0 + D.N;
+  w.Dl = take(N); w.pv = take(N);
   w.F = take(N); w.xb = take(N); w.mu = take(N); w.rA = take(N);
   w.Dg = take(6 * (size_t)D.nv);
   w.s = take(3 * np); w.z = take(3 * np); w.nrm = take(3 * np); w.pg = take(3 * np); w.prz = take(3 * np);
@@ -58,8 +61,7 @@ template <typename R>
 __device__ __forceinline__ ClothSm<R> cloth_sm(const ClothDims& D) {
   ClothSm<R> c;
   c.sm = reinterpret_cast<R*>(cs_smem);
-  const size_t win = (size_t)D.WC * D.LDW, stg = (size_t)2 * CL_KB * D.LDB;
-  c.vb = c.sm + (win > stg ? win : stg) + (size_t)CL_KB * D.PL;
+  c.vb = c.sm + cloth_win_elems(D) + (size_t)CL_KB * D.PL;
   c.red = c.vb + D.N + CL_KB;
   c.misc = c.red + 64;
   return c;

@@ -17,7 +17,7 @@
 
 namespace cs {
 
-constexpr int CL_NT = 256;              // threads per CTA
+constexpr int CL_NT = 512;              // threads per CTA
 constexpr int CL_NW = CL_NT / 32;
 constexpr int CL_KB = 12;               // panel width (four nodes)
 
@@ -62,19 +62,32 @@ __host__ __device__ inline ClothDims cloth_dims(int R, int C) {
 
 // shared memory of one CTA (elements of the real type): window (or the two staging panels of a
 // solve), panel buffer, right-hand side, panel partial sums, reductions, step scalars
-__host__ __device__ inline size_t cloth_smem_elems(const ClothDims& d) {
+__host__ __device__ inline size_t cloth_win_elems(const ClothDims& d) {
   const size_t win = (size_t)d.WC * d.LDW;
   const size_t stg = (size_t)2 * CL_KB * d.LDB;
-  return (win > stg ? win : stg) + (size_t)CL_KB * d.PL + (size_t)d.N + CL_KB + 64 + 64;
+  return ((win > stg ? win : stg) + 3) & ~(size_t)3;       // keeps the panel buffer 16-byte aligned
 }
 
-// elements of one CTA's workspace slot in global memory: eight node vectors [N], the diagonal
+__host__ __device__ inline size_t cloth_smem_elems(const ClothDims& d) {
+  return cloth_win_elems(d) + (size_t)CL_KB * d.PL + (size_t)d.N + CL_KB + 64 + 64 + 2 * (size_t)d.N;
+}
+
+// four consecutive elements (16-byte aligned for float)
+template <typename R>
+__device__ __forceinline__ void ld4(const R* p, R o[4]) { o[0] = p[0]; o[1] = p[1]; o[2] = p[2]; o[3] = p[3]; }
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float o[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+
+// elements of one CTA's workspace slot in global memory: six node vectors [N], the diagonal
 // blocks [nv][6], the contact pairs (s, z, n, g, r_z [3], phi [1], M [6] per pair) and the band
 // factor [N][LDB], each array padded to a multiple of 4 elements
 __host__ __device__ inline size_t cloth_ws_elems(const ClothDims& D, int nobs) {
   const size_t N = (size_t)D.N, np = (size_t)nobs * D.nv;
   auto r4 = [](size_t x) { return (x + 3) & ~(size_t)3; };
-  return 8 * r4(N) + r4(6 * (size_t)D.nv) + 5 * r4(3 * np) + r4(np) + r4(6 * np) + r4(N * D.LDB);
+  return 6 * r4(N) + r4(6 * (size_t)D.nv) + 5 * r4(3 * np) + r4(np) + r4(6 * np) + r4(N * D.LDB);
 }
 
 // spring s -> nodes a < b and family (0, 1 structural; 2, 3 shear; 4, 5 bend)
@@ -169,23 +182,31 @@ __device__ __forceinline__ void cl_spring_hess(const Scene<R>& S, const R* x0, c
   spring_eval(d, cl_stiff(S, fam), S.L1[s], proj, f, H);
 }
 
-// assemble the columns of nodes [v0, v1) into their window slots
+// assemble the columns of nodes [v0, v1) into their window slots; slot0 = (3 v0) mod WC
 template <typename R>
 __device__ __forceinline__ void cl_load_cols(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M,
-                                             R* Wn, int v0, int v1) {
+                                             R* Wn, int v0, int v1, int slot0) {
   const int ncol = 3 * (v1 - v0);
-  for (int idx = threadIdx.x; idx < ncol * D.LDW; idx += CL_NT) {
-    const int col = 3 * v0 + idx / D.LDW;
-    Wn[(col % D.WC) * D.LDW + idx % D.LDW] = R(0);
+  for (int cl = 0; cl < ncol; ++cl) {
+    int sl = slot0 + cl;
+    while (sl >= D.WC) sl -= D.WC;
+    R* col = Wn + sl * D.LDW;
+    for (int r = threadIdx.x; r < D.LDW; r += CL_NT) col[r] = R(0);
   }
   __syncthreads();
   for (int task = threadIdx.x; task < 7 * (v1 - v0); task += CL_NT) {
-    const int v = v0 + task / 7, t = task % 7;
+    const int vl = task / 7, t = task - 7 * vl, v = v0 + vl;
+    int sl[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      sl[b] = slot0 + 3 * vl + b;
+      while (sl[b] >= D.WC) sl[b] -= D.WC;
+    }
     if (t == 0) {
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = b; a < 3; ++a) Wn[((3 * v + b) % D.WC) * D.LDW + (a - b)] = M.Dg[6 * v + sym3(a, b)];
+        for (int a = b; a < 3; ++a) Wn[sl[b] * D.LDW + (a - b)] = M.Dg[6 * v + sym3(a, b)];
     } else {
       int u, fam;
       const int s = cl_incident(D, v, 2 * (t - 1), u, fam);
@@ -195,8 +216,7 @@ __device__ __forceinline__ void cl_load_cols(const Scene<R>& S, const ClothDims&
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-          Wn[((3 * v + b) % D.WC) * D.LDW + (3 * (u - v) + a - b)] = -H[a * 3 + b];
+        for (int a = 0; a < 3; ++a) Wn[sl[b] * D.LDW + (3 * (u - v) + a - b)] = -H[a * 3 + b];
     }
   }
   __syncthreads();
@@ -208,61 +228,101 @@ __device__ __forceinline__ void cl_load_cols(const Scene<R>& S, const ClothDims&
 template <typename R>
 __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M, R* Lg, R* sm) {
   R* Wn = sm;
-  const size_t win = (size_t)D.WC * D.LDW, stg = (size_t)2 * CL_KB * D.LDB;
-  R* Pb = sm + (win > stg ? win : stg);
+  R* Pb = sm + cloth_win_elems(D);
   R* vb = Pb + (size_t)CL_KB * D.PL;
+  R* ild = vb + D.N;                       // reciprocal pivots of the current panel [CL_KB]
   R* flag = vb + D.N + CL_KB + 63;         // last slot of the reduction area: failure flag
   const int N = D.N, bw = D.bw, WC = D.WC, LDW = D.LDW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) flag[0] = R(0);
-  cl_load_cols(S, D, M, Wn, 0, min(WC, N) / 3);
+  cl_load_cols(S, D, M, Wn, 0, min(WC, N) / 3, 0);
+  int slot0 = 0;                           // window slot of column j
   for (int j = 0; j < N; j += CL_KB) {
     const int jn = min(j + CL_KB, N), kbp = jn - j;
-    if (warp == 0) {
-      bool bad = false;
-      for (int c = j; c < jn; ++c) {
-        R* col = Wn + (c % WC) * LDW;
-        const R dg = col[0];
-        if (!(dg > R(0)) || !(dg < R(1e300))) { bad = true; break; }
-        const R l = sqrt(dg), il = R(1) / l;
-        const R y = vb[c] * il;
-        __syncwarp();
-        if (lane == 0) { col[0] = l; vb[c] = y; }
-        const int rmax = min(bw, N - 1 - c);
-        for (int r = 1 + lane; r <= rmax; r += 32) {
-          const R lv = col[r] * il;
-          col[r] = lv;
-          vb[c + r] -= lv * y;
-        }
-        __syncwarp();
-        const int imax = min(c + bw, N - 1);
-        for (int c2 = c + 1; c2 < jn && c2 - c <= bw; ++c2) {
-          const R f = col[c2 - c];
-          R* dst = Wn + (c2 % WC) * LDW;
-          for (int i = c2 + lane; i <= imax; i += 32) dst[i - c2] -= col[i - c] * f;
-        }
-        __syncwarp();
+    int cb[CL_KB];                         // window offsets of the panel's columns
+    {
+      int sl = slot0;
+#pragma unroll
+      for (int cc = 0; cc < CL_KB; ++cc) {
+        cb[cc] = sl * LDW;
+        if (++sl == WC) sl = 0;
       }
-      if (bad && lane == 0) flag[0] = R(1);
+    }
+    // (a) diagonal block [j, jn): lane l holds row j + l in registers; right-looking with
+    //     shuffles, the forward substitution of the block rows alongside
+    if (warp == 0) {
+      R row[CL_KB];
+      const int l = lane;
+#pragma unroll
+      for (int cc = 0; cc < CL_KB; ++cc)
+        row[cc] = (cc < kbp && l < kbp && cc <= l && l - cc <= bw) ? Wn[cb[cc] + (l - cc)] : R(0);
+      R yv = l < kbp ? vb[j + l] : R(0);
+      bool bad = false;
+#pragma unroll
+      for (int cc = 0; cc < CL_KB; ++cc) {
+        if (cc >= kbp) break;
+        const R piv = __shfl_sync(FULL, row[cc], cc);
+        bad = bad || !(piv > R(0)) || !(piv < R(1e300));
+        const R lp = sqrt(piv), il = R(1) / lp;
+        const R ycc = __shfl_sync(FULL, yv, cc) * il;
+        if (l == cc) { row[cc] = lp; yv = ycc; }
+        else if (l > cc) { row[cc] *= il; yv -= row[cc] * ycc; }
+#pragma unroll
+        for (int c2 = cc + 1; c2 < CL_KB; ++c2) {
+          const R lc2 = __shfl_sync(FULL, row[cc], c2);
+          if (l >= c2) row[c2] -= row[cc] * lc2;
+        }
+        if (l == 0) ild[cc] = il;
+      }
+      if (l < kbp) {
+#pragma unroll
+        for (int cc = 0; cc < CL_KB; ++cc)
+          if (cc <= l && l - cc <= bw) Wn[cb[cc] + (l - cc)] = row[cc];
+        vb[j + l] = yv;
+      }
+      if (bad && l == 0) flag[0] = R(1);
     }
     __syncthreads();
     if (flag[0] != R(0)) return false;
-    // panel -> dense buffer (zero outside the band) and -> global factor
-    for (int idx = threadIdx.x; idx < CL_KB * D.PL; idx += CL_NT) {
-      const int cc = idx / D.PL, ii = idx - cc * D.PL;
-      const int c = j + cc, i = j + ii;
-      R val = R(0);
-      if (cc < kbp && i >= c && i - c <= bw && i < N) val = Wn[(c % WC) * LDW + (i - c)];
-      Pb[idx] = val;
+    // (b) rows below the block: L21 = A21 L11^-T, one row per thread, and the fused forward
+    //     substitution vb_i -= L21_i . y_panel; the rows also go to the panel buffer
+    const int imax = min(j + kbp - 1 + bw, N - 1);
+    for (int i = jn + threadIdx.x; i <= imax; i += CL_NT) {
+      R a[CL_KB];
+#pragma unroll
+      for (int cc = 0; cc < CL_KB; ++cc) a[cc] = (cc < kbp && i - j - cc <= bw) ? Wn[cb[cc] + (i - j - cc)] : R(0);
+      R acc = R(0);
+#pragma unroll
+      for (int cc = 0; cc < CL_KB; ++cc) {
+        if (cc >= kbp) break;
+        R sv = a[cc];
+#pragma unroll
+        for (int cp = 0; cp < cc; ++cp)           // L11[cc][cp]: column j + cp, offset cc - cp
+          if (cc - cp <= bw) sv -= a[cp] * Wn[cb[cp] + (cc - cp)];
+        sv *= ild[cc];
+        a[cc] = sv;
+        acc += sv * vb[j + cc];
+      }
+      vb[i] -= acc;
+#pragma unroll
+      for (int cc = 0; cc < CL_KB; ++cc) {
+        if (cc >= kbp) break;
+        if (i - j - cc <= bw) Wn[cb[cc] + (i - j - cc)] = a[cc];
+        Pb[cc * D.PL + CL_KB + (i - jn)] = a[cc];
+      }
     }
-    for (int idx = threadIdx.x; idx < kbp * LDW; idx += CL_NT) {
-      const int cc = idx / LDW, r = idx - cc * LDW;
-      Lg[(size_t)(j + cc) * D.LDB + r] = Wn[((j + cc) % WC) * LDW + r];
-    }
+    // panel buffer: row i >= jn of column j + cc at [cc][CL_KB + i - jn]; everything outside
+    // [jn, imax] is zero (band tail, tile padding, unused columns of a short last panel)
+    for (int cc = 0; cc < CL_KB; ++cc)
+      for (int ii = threadIdx.x; ii < D.PL; ii += CL_NT)
+        if (cc >= kbp || ii < CL_KB || jn + ii - CL_KB > imax) Pb[cc * D.PL + ii] = R(0);
     __syncthreads();
+    for (int cc = 0; cc < kbp; ++cc)
+      for (int r = threadIdx.x; r < LDW; r += CL_NT) Lg[(size_t)(j + cc) * D.LDB + r] = Wn[cb[cc] + r];
     // rank-kbp update of the trailing triangle [jn, jn + T)
     const int T = min(bw, N - jn);
     const int nt = (T + 3) >> 2, ntiles = nt * (nt + 1) / 2;
+    const int tslot = slot0 + kbp;           // window slot of column jn (before wrapping)
     for (int id = threadIdx.x; id < ntiles; id += CL_NT) {
       int a = (int)((sqrtf(8.0f * (float)id + 1.0f) - 1.0f) * 0.5f);
       while (a * (a + 1) / 2 > id) --a;
@@ -273,32 +333,36 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) acc[x][y] = R(0);
-      const R* pr = Pb + kbp + 4 * a;
-      const R* pc = Pb + kbp + 4 * b;
+      const R* pr = Pb + CL_KB + 4 * a;
+      const R* pc = Pb + CL_KB + 4 * b;
       for (int cc = 0; cc < kbp; ++cc) {
-        R ra[4], cb[4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x) { ra[x] = pr[cc * D.PL + x]; cb[x] = pc[cc * D.PL + x]; }
+        R ra[4], cbv[4];
+        ld4(pr + cc * D.PL, ra);
+        ld4(pc + cc * D.PL, cbv);
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] += ra[x] * cb[y];
+          for (int y = 0; y < 4; ++y) acc[x][y] += ra[x] * cbv[y];
       }
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
-        const int k = jn + 4 * b + y;
-        if (k >= jn + T) continue;
-        R* dst = Wn + (k % WC) * LDW;
+        const int kk = 4 * b + y;
+        if (kk >= T) continue;
+        int sl = tslot + kk;
+        while (sl >= WC) sl -= WC;
+        R* dst = Wn + sl * LDW;
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
-          const int i = jn + 4 * a + x;
-          if (i < jn + T && i >= k) dst[i - k] -= acc[x][y];
+          const int ii = 4 * a + x;
+          if (ii < T && ii >= kk) dst[ii - kk] -= acc[x][y];
         }
       }
     }
     __syncthreads();
     const int c0 = j + WC, c1 = min(j + WC + kbp, N);
-    if (c0 < c1) cl_load_cols(S, D, M, Wn, c0 / 3, c1 / 3);
+    if (c0 < c1) cl_load_cols(S, D, M, Wn, c0 / 3, c1 / 3, slot0);   // the panel's freed slots
+    slot0 += CL_KB;
+    if (slot0 >= WC) slot0 -= WC;
   }
   return true;
 }
@@ -313,8 +377,7 @@ __device__ __forceinline__ void cl_stage(const ClothDims& D, const R* Lg, int j,
 // backward substitution L^T x = vb in place (vb in shared memory), panels from the last
 template <typename R>
 __device__ __noinline__ void cl_back(const ClothDims& D, const R* Lg, R* sm) {
-  const size_t win = (size_t)D.WC * D.LDW, stg = (size_t)2 * CL_KB * D.LDB;
-  R* vb = sm + (win > stg ? win : stg) + (size_t)CL_KB * D.PL;
+  R* vb = sm + cloth_win_elems(D) + (size_t)CL_KB * D.PL;
   R* tc = vb + D.N;
   const int N = D.N, bw = D.bw, LDB = D.LDB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -355,8 +418,7 @@ __device__ __noinline__ void cl_back(const ClothDims& D, const R* Lg, R* sm) {
 // forward substitution L y = vb in place
 template <typename R>
 __device__ __noinline__ void cl_fwd(const ClothDims& D, const R* Lg, R* sm) {
-  const size_t win = (size_t)D.WC * D.LDW, stg = (size_t)2 * CL_KB * D.LDB;
-  R* vb = sm + (win > stg ? win : stg) + (size_t)CL_KB * D.PL;
+  R* vb = sm + cloth_win_elems(D) + (size_t)CL_KB * D.PL;
   const int N = D.N, bw = D.bw, LDB = D.LDB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int buf = 0;
