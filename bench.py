@@ -244,6 +244,73 @@ def linearize_leg(args, flush, stream, world):
                               peak_source=f"{src} HBM copy bandwidth"))
 
 
+def cloth_oracle_sample(steps=2):
+    """The oracle's forward + adjoint of one rollout of the cloth workload over `steps` steps (CPU,
+    one process): node-steps/s and the sample described."""
+    from oracle import grad as ograd, sim as osim
+    w = scenes.workload(3, B=1, H=steps)
+    sc = w["scene"]
+    osc = osim.Scene(sc["params"], sc["rest_x"])
+    t0 = time.perf_counter()
+    ograd.rollout_vjp(osc, w["q0"][0], w["U"][0], "surrogate")
+    dt = time.perf_counter() - t0
+    nv = sc["params"]["n_nodes"]
+    return dict(value=nv * steps / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"1 rollout x {steps} steps of the 32x32 cloth, forward + adjoint, {dt:.1f} s")
+
+
+def cloth_leg(args, flush, stream, world, cpu):
+    """sim_rollout_vjp on the batched cloth workload (32 x 32 cloth, FP32, table + 2 spheres,
+    checkpoint every 5): a bounded sample of one rollout per SM (one wave of the 512) over the
+    first `cloth_horizon` steps.  Iteration counts for the flop model from the forward rollout's
+    counters on the same inputs (untimed)."""
+    import torch
+    from paper_2606_14188_b300.sim import Sim
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    B = args.cloth_rollouts or props.multi_processor_count
+    H = args.cloth_horizon
+    w = scenes.workload(3, B=B, H=H)
+    sc = w["scene"]
+    p = sc["params"]
+    R, C, nv = p["rows"], p["cols"], p["n_nodes"]
+    k = p["checkpoint_every"]
+    nobs = len(p["obstacles"])
+    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H, newton_max=100)
+    q0 = torch.tensor(w["q0"], dtype=torch.float32, device="cuda")
+    U = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
+    _, _, st_f, cnt = s.rollout_counters(q0, U)
+    c = cnt.cpu().numpy().reshape(B, H, 3)
+    counts = dict(fwd_newton=float(c[..., 0].mean()), fwd_ipm=float(c[..., 1].mean()))
+    s.rollout_vjp(q0, U, want_dq0=False)
+    per = time_device(lambda: s.rollout_vjp(q0, U, want_dq0=False), args.cloth_steps, flush, stream)
+    t = max_over_ranks(sum(per), world)
+    avg = t / args.cloth_steps
+    _, dU, _, st = s.rollout_vjp(q0, U, want_dq0=False)
+    status = st.cpu().numpy()
+    node_steps = B * nv * H
+    clean_steps = int(np.count_nonzero(status == 0)) * nv * H
+    pband = flops.cloth_band(C)
+    spn = flops.cloth_springs_per_node(R, C)
+    f_ns = flops.cloth_rollout_vjp_flops_per_node_step(counts, pband, spn, nobs, k)
+    sm_mhz = 2032.0
+    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    # a flagged rollout stops at its failed step: only the clean rollouts' work is counted
+    achieved = f_ns * clean_steps / avg / 1e12
+    wl = f"cloth{R}x{C}_b{B}_h{H}"
+    return dict(workload=wl, what=f"sample of the 512-rollout, horizon-30 cloth workload: {B} rollouts "
+                                  f"(one per SM), first {H} steps", value=world * node_steps / avg,
+                unit=UNIT, ms_per_step=1e3 * avg, rollouts=B, horizon=H, checkpoint_every=k,
+                value_clean_rollouts_only=world * clean_steps / avg,
+                status_flagged=int(np.count_nonzero(status)),
+                status_newton_cap=int(np.count_nonzero(status & 1)),
+                grads_finite=bool(torch.isfinite(dU).all().item()),
+                roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                              traffic=load_traffic("cloth_vjp_kernel", wl),
+                              peak_source="FP32 FMA at the max SM clock", flops_per_node_step=f_ns,
+                              band_half_width=pband, iterations_per_step=counts),
+                cpu_baseline=cpu)
+
+
 def served_stream(n, seed):
     """The served workload: n plan solves with rope sizes U{16..128}, horizons U{20..60}, candidates
     log-uniform in {64, ..., 1024}, 10 evaluations each, Poisson arrival order (times set later)."""
@@ -345,6 +412,7 @@ def run_ours(args):
                    one_core_value=per_core)
         cres, _ = oracle_sample([0, 341, 682, 1023], 1e-5, 4)
         counts = counts_mean(cres)
+    cloth_cpu = cloth_oracle_sample() if rank == 0 and not args.no_cpu and args.cloth_horizon > 0 else None
 
     import torch
     if world > 1:
@@ -421,6 +489,7 @@ def run_ours(args):
     # linearisation workload: 256 nominal trajectories of a 40-node rope, horizon 20
     lin = linearize_leg(args, flush, stream, world)
     served = served_leg(args) if args.served_requests > 0 else None
+    cloth = cloth_leg(args, flush, stream, world, cloth_cpu) if args.cloth_horizon > 0 else None
 
     if rank == 0:
         node_steps = B * nv * H
@@ -455,7 +524,7 @@ def run_ours(args):
                     forward=dict(value=world * args.steps * node_steps / t_fwd, unit=UNIT,
                                  ms_per_step=1e3 * t_fwd / args.steps,
                                  what="sim_rollout alone on the same rollouts"),
-                    linearize=lin, served=served,
+                    linearize=lin, served=served, cloth=cloth,
                     gpu_launches=launches, clocks=clocks,
                     status_nonzero=int(np.count_nonzero(status)),
                     per_step_ms=[round(x * 1e3, 4) for x in per])
@@ -475,6 +544,11 @@ def main():
                     help="plan solves in the served stream (0: skip the served leg)")
     ap.add_argument("--rollouts", type=int, default=None,
                     help="rollouts per GPU (default 1024; smaller only for profiling captures)")
+    ap.add_argument("--cloth-horizon", type=int, default=10,
+                    help="steps of the cloth leg's sample (0: skip the cloth leg)")
+    ap.add_argument("--cloth-rollouts", type=int, default=None,
+                    help="rollouts of the cloth leg's sample (default: one per SM)")
+    ap.add_argument("--cloth-steps", type=int, default=1, help="timed calls of the cloth leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -64,3 +64,47 @@ def rollout_vjp_flops_per_node_step(counts: dict, nobs: int, k: int) -> float:
     back = counts["sm_newton"] * newton_iter_per_node() + counts["sm_ipm"] * barrier_iter_per_node(nobs) \
         + adjoint_per_node(nobs)
     return fwd + recompute + back
+
+
+# ---- cloth: the node-coupled matrices are banded with scalar half bandwidth p = 3 span + 2
+#      (span = 2 C for C columns); a cloth node has about 5.7 springs (structural, shear, bend)
+
+def cloth_band(cols: int) -> int:
+    return 3 * 2 * cols + 2
+
+
+def cloth_springs_per_node(rows: int, cols: int) -> float:
+    n = rows * cols
+    s = rows * (cols - 1) + (rows - 1) * cols + 2 * (rows - 1) * (cols - 1) + rows * max(cols - 2, 0) \
+        + max(rows - 2, 0) * cols
+    return s / n
+
+
+def band_factor_per_node(p: int) -> float:
+    return 3 * (p * p + 3 * p)
+
+
+def band_solve_per_node(p: int) -> float:
+    return 3 * (4 * p + 1)
+
+
+def cloth_newton_iter_per_node(p: int, spn: float) -> float:
+    return spn * (40 + 36) + 10 + band_factor_per_node(p) + band_solve_per_node(p) + 1.5 * (spn * 24 + 12)
+
+
+def cloth_pc_barrier_iter_per_node(p: int, spn: float, nobs: int) -> float:
+    return spn * (40 + 36 + 24) + 10 + nobs * (60 + 90) + band_factor_per_node(p) + \
+        2 * band_solve_per_node(p) + 1.5 * (spn * 24 + nobs * 25)
+
+
+def cloth_rollout_vjp_flops_per_node_step(counts: dict, p: int, spn: float, nobs: int, k: int) -> float:
+    """counts: mean Newton and barrier iterations per step of the forward (fwd_newton, fwd_ipm).
+    Forward, the recompute of k-1 of every k steps, and a backward step counted at its minimum:
+    one Newton iteration of the smooth re-solve, the two adjoint factorisations and solves, and the
+    VJP products (spring third derivatives, contact terms).  Shift retries of the stage-1
+    factorisation are not counted."""
+    fwd = counts["fwd_newton"] * cloth_newton_iter_per_node(p, spn) + \
+        counts["fwd_ipm"] * cloth_pc_barrier_iter_per_node(p, spn, nobs)
+    back = cloth_newton_iter_per_node(p, spn) + 2 * (band_factor_per_node(p) + band_solve_per_node(p)) + \
+        spn * 30 + nobs * 70 + 12
+    return fwd + fwd * (k - 1) / k + back

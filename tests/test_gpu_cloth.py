@@ -116,3 +116,92 @@ def test_cloth8_fp32_rollout_and_vjp():
             assert abs(float(Lv[b]) - ref["L"]) <= TOL_STATE32 * abs(ref["L"])
             check_grad(dU[b].cpu().numpy(), ref["dL_du"], TOL_GRAD32, COS32)
     assert clean >= B // 2
+
+
+def _grid_springs(R, C, ks, ksh, kb):
+    """(a, b, k) of every spring of an R x C grid, enumerated here independently of both paths."""
+    out = []
+    idx = lambda r, c: r * C + c
+    for r in range(R):
+        for c in range(C):
+            if c + 1 < C: out.append((idx(r, c), idx(r, c + 1), ks))
+            if r + 1 < R: out.append((idx(r, c), idx(r + 1, c), ks))
+            if r + 1 < R and c + 1 < C:
+                out.append((idx(r, c), idx(r + 1, c + 1), ksh))
+                out.append((idx(r, c + 1), idx(r + 1, c), ksh))
+            if c + 2 < C: out.append((idx(r, c), idx(r, c + 2), kb))
+            if r + 2 < R: out.append((idx(r, c), idx(r + 2, c), kb))
+    return np.array(out)
+
+
+def _force_balance(p, rest, x, xs, gs, d):
+    """w (x* - x) + grad E(x*) - m g + sum_i d_i (x*_a(i) - g*_i): zero at a stage-1 root."""
+    R, C = p["rows"], p["cols"]
+    S = _grid_springs(R, C, p["k_stretch"], p["k_shear"], p["k_bend"])
+    a, b, k = S[:, 0].astype(int), S[:, 1].astype(int), S[:, 2]
+    L = np.linalg.norm(rest[b] - rest[a], axis=1)
+    w = p["node_mass"] / p["dt"] ** 2
+    F = w * (xs - x) - p["node_mass"] * np.asarray(p["gravity"])[None, :]
+    dv = xs[b] - xs[a]
+    l = np.linalg.norm(dv, axis=1)
+    f = (k * (l - L) / l)[:, None] * dv
+    np.add.at(F, b, f)
+    np.add.at(F, a, -f)
+    for i, j in enumerate(p["grasp_nodes"]):
+        F[j] += d[i] * (xs[j] - gs[i])
+    return F
+
+
+def _min_clearance(p, X):
+    """smallest distance of a node sphere to the table plane or an obstacle sphere"""
+    r = p["node_radius"]
+    out = np.inf
+    for ob in p["obstacles"]:
+        if ob["type"] == "plane":
+            out = min(out, float((X @ np.asarray(ob["normal"]) - ob["offset"] - r).min()))
+        elif ob["type"] == "sphere":
+            out = min(out, float((np.linalg.norm(X - np.asarray(ob["center"]), axis=1) - ob["radius"] - r).min()))
+    return out
+
+
+def test_cloth32_fp32_full_size_properties():
+    """The batched workload's 32 x 32 cloth, FP32: each contact-free step ends at a stage-1 root
+    (force balance below 1e-4 of the step's initial imbalance); flags are the status bits only;
+    gradients finite, zero exactly on flagged rollouts, NaN loss exactly there."""
+    B, H = 3, 2
+    w = scenes.workload(3, B=B, H=H)
+    sc, q0, U = w["scene"], w["q0"], w["U"]
+    p = sc["params"]
+    s = _sim(sc, 4, B, H, newton_max=100)
+    traj, qH, st = s.rollout(_t(q0, 4), _t(U, 4))
+    traj = traj.cpu().numpy().astype(np.float64)
+    st = st.cpu().numpy()
+    assert np.all((st & ~15) == 0)
+    n = 3 * p["n_nodes"]
+    checked = 0
+    for b in range(B):
+        for t in range(H):
+            if st[b] & 1:
+                break
+            x, g = traj[b, t, :n].reshape(-1, 3), traj[b, t, n:].reshape(2, 3)
+            xs, g1 = traj[b, t + 1, :n].reshape(-1, 3), traj[b, t + 1, n:].reshape(2, 3)
+            np.testing.assert_allclose(g1, g + U[b, t].reshape(2, 3), rtol=0, atol=1e-6)
+            if _min_clearance(p, xs) <= 1e-4:
+                continue                                  # contact active: q+ = q* + Delta
+            c = g - x[list(p["grasp_nodes"])]
+            d = np.where(np.linalg.norm(c, axis=1) <= p["r_grasp"], p["D_max"], 0.0)
+            x0 = x.copy()
+            for i, j in enumerate(p["grasp_nodes"]):
+                x0[j] += U[b, t, 3 * i:3 * i + 3]
+            F1 = _force_balance(p, sc["rest_x"], x, xs, g1, d)
+            F0 = _force_balance(p, sc["rest_x"], x, x0, g1, d)
+            assert np.abs(F1).max() <= 1e-4 * np.abs(F0).max(), (b, t, np.abs(F1).max(), np.abs(F0).max())
+            checked += 1
+    assert checked >= 2
+    Lv, dU, dq0, st2 = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    Lv, dU, st2 = Lv.cpu().numpy(), dU.cpu().numpy(), st2.cpu().numpy()
+    for b in range(B):
+        if st2[b]:
+            assert np.isnan(Lv[b]) and np.all(dU[b] == 0)
+        else:
+            assert np.isfinite(Lv[b]) and np.all(np.isfinite(dU[b])) and np.abs(dU[b]).max() > 0
