@@ -222,6 +222,47 @@ __device__ __forceinline__ void cl_load_cols(const Scene<R>& S, const ClothDims&
   __syncthreads();
 }
 
+// the same, by one warp (the others update the trailing triangle meanwhile)
+template <typename R>
+__device__ __forceinline__ void cl_load_cols_warp(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M,
+                                                  R* Wn, int v0, int v1, int slot0) {
+  const int lane = threadIdx.x & 31;
+  const int ncol = 3 * (v1 - v0);
+  for (int cl = 0; cl < ncol; ++cl) {
+    int sl = slot0 + cl;
+    while (sl >= D.WC) sl -= D.WC;
+    R* col = Wn + sl * D.LDW;
+    for (int r = lane; r < D.LDW; r += 32) col[r] = R(0);
+  }
+  __syncwarp();
+  for (int task = lane; task < 7 * (v1 - v0); task += 32) {
+    const int vl = task / 7, t = task - 7 * vl, v = v0 + vl;
+    int sl[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      sl[b] = slot0 + 3 * vl + b;
+      while (sl[b] >= D.WC) sl[b] -= D.WC;
+    }
+    if (t == 0) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = b; a < 3; ++a) Wn[sl[b] * D.LDW + (a - b)] = M.Dg[6 * v + sym3(a, b)];
+    } else {
+      int u, fam;
+      const int s = cl_incident(D, v, 2 * (t - 1), u, fam);
+      if (s < 0) continue;
+      R f[3], H[9];
+      cl_spring_hess(S, M.x0, M.dx, v, u, s, fam, M.proj, f, H);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Wn[sl[b] * D.LDW + (3 * (u - v) + a - b)] = -H[a * 3 + b];
+    }
+  }
+  __syncwarp();
+}
+
 // Cholesky factorisation L L^T of the band matrix M into Lg [N][LDB] (column c: rows c .. c+bw),
 // with the forward substitution L y = vb fused (vb in shared memory becomes y).  Returns false,
 // uniformly over the CTA, when a pivot is not positive (the matrix is not positive definite).
@@ -319,48 +360,53 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
     __syncthreads();
     for (int cc = 0; cc < kbp; ++cc)
       for (int r = threadIdx.x; r < LDW; r += CL_NT) Lg[(size_t)(j + cc) * D.LDB + r] = Wn[cb[cc] + r];
-    // rank-kbp update of the trailing triangle [jn, jn + T)
-    const int T = min(bw, N - jn);
-    const int nt = (T + 3) >> 2, ntiles = nt * (nt + 1) / 2;
-    const int tslot = slot0 + kbp;           // window slot of column jn (before wrapping)
-    for (int id = threadIdx.x; id < ntiles; id += CL_NT) {
-      int a = (int)((sqrtf(8.0f * (float)id + 1.0f) - 1.0f) * 0.5f);
-      while (a * (a + 1) / 2 > id) --a;
-      while ((a + 1) * (a + 2) / 2 <= id) ++a;
-      const int b = id - a * (a + 1) / 2;
-      R acc[4][4];
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = R(0);
-      const R* pr = Pb + CL_KB + 4 * a;
-      const R* pc = Pb + CL_KB + 4 * b;
-      for (int cc = 0; cc < kbp; ++cc) {
-        R ra[4], cbv[4];
-        ld4(pr + cc * D.PL, ra);
-        ld4(pc + cc * D.PL, cbv);
+    __syncthreads();                         // the panel's window slots are free from here
+    // the last warp assembles the columns entering the window into the panel's slots while the
+    // others apply the rank-kbp update to the trailing triangle [jn, jn + T)
+    const int c0 = j + WC, c1 = min(j + WC + kbp, N);
+    if (warp == CL_NW - 1) {
+      if (c0 < c1) cl_load_cols_warp(S, D, M, Wn, c0 / 3, c1 / 3, slot0);
+    } else {
+      const int T = min(bw, N - jn);
+      const int nt = (T + 3) >> 2, ntiles = nt * (nt + 1) / 2;
+      const int tslot = slot0 + kbp;           // window slot of column jn (before wrapping)
+      for (int id = threadIdx.x; id < ntiles; id += CL_NT - 32) {
+        int a = (int)((sqrtf(8.0f * (float)id + 1.0f) - 1.0f) * 0.5f);
+        while (a * (a + 1) / 2 > id) --a;
+        while ((a + 1) * (a + 2) / 2 <= id) ++a;
+        const int b = id - a * (a + 1) / 2;
+        R acc[4][4];
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 4; ++y) acc[x][y] += ra[x] * cbv[y];
-      }
+          for (int y = 0; y < 4; ++y) acc[x][y] = R(0);
+        const R* pr = Pb + CL_KB + 4 * a;
+        const R* pc = Pb + CL_KB + 4 * b;
+        for (int cc = 0; cc < kbp; ++cc) {
+          R ra[4], cbv[4];
+          ld4(pr + cc * D.PL, ra);
+          ld4(pc + cc * D.PL, cbv);
 #pragma unroll
-      for (int y = 0; y < 4; ++y) {
-        const int kk = 4 * b + y;
-        if (kk >= T) continue;
-        int sl = tslot + kk;
-        while (sl >= WC) sl -= WC;
-        R* dst = Wn + sl * LDW;
+          for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
-          const int ii = 4 * a + x;
-          if (ii < T && ii >= kk) dst[ii - kk] -= acc[x][y];
+            for (int y = 0; y < 4; ++y) acc[x][y] += ra[x] * cbv[y];
+        }
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int kk = 4 * b + y;
+          if (kk >= T) continue;
+          int sl = tslot + kk;
+          while (sl >= WC) sl -= WC;
+          R* dst = Wn + sl * LDW;
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            const int ii = 4 * a + x;
+            if (ii < T && ii >= kk) dst[ii - kk] -= acc[x][y];
+          }
         }
       }
     }
     __syncthreads();
-    const int c0 = j + WC, c1 = min(j + WC + kbp, N);
-    if (c0 < c1) cl_load_cols(S, D, M, Wn, c0 / 3, c1 / 3, slot0);   // the panel's freed slots
     slot0 += CL_KB;
     if (slot0 >= WC) slot0 -= WC;
   }

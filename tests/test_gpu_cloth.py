@@ -165,23 +165,25 @@ def _min_clearance(p, X):
 
 
 def test_cloth32_fp32_full_size_properties():
-    """The batched workload's 32 x 32 cloth, FP32: each contact-free step ends at a stage-1 root
-    (force balance below 1e-4 of the step's initial imbalance); flags are the status bits only;
-    gradients finite, zero exactly on flagged rollouts, NaN loss exactly there."""
+    """The batched workload's 32 x 32 cloth, FP32 (Newton cap raised so that the hard first steps
+    converge): each contact-free step ends at a stage-1 root (force balance below 1e-4 of the
+    step's initial imbalance); the rollout status is the OR of the step flags; gradients finite,
+    zero exactly on flagged rollouts, NaN loss exactly there."""
     B, H = 3, 2
     w = scenes.workload(3, B=B, H=H)
     sc, q0, U = w["scene"], w["q0"], w["U"]
     p = sc["params"]
-    s = _sim(sc, 4, B, H, newton_max=100)
-    traj, qH, st = s.rollout(_t(q0, 4), _t(U, 4))
+    s = _sim(sc, 4, B, H, newton_max=400)
+    traj, qH, st, cnt = s.rollout_counters(_t(q0, 4), _t(U, 4))
     traj = traj.cpu().numpy().astype(np.float64)
-    st = st.cpu().numpy()
+    st, cnt = st.cpu().numpy(), cnt.cpu().numpy()
     assert np.all((st & ~15) == 0)
+    assert np.all(st == np.bitwise_or.reduce(cnt[..., 2], axis=1))
     n = 3 * p["n_nodes"]
     checked = 0
     for b in range(B):
         for t in range(H):
-            if st[b] & 1:
+            if cnt[b, t, 2] != 0:
                 break
             x, g = traj[b, t, :n].reshape(-1, 3), traj[b, t, n:].reshape(2, 3)
             xs, g1 = traj[b, t + 1, :n].reshape(-1, 3), traj[b, t + 1, n:].reshape(2, 3)
