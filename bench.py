@@ -78,10 +78,18 @@ def counts_mean(res):
 # helpers
 # ------------------------------------------------------------------------------------------
 
-def kernel_source_hash():
+# the source files each kernel is compiled from (its own, the shared headers, its launcher)
+KERNEL_SOURCES = {
+    "rope": ["common.cuh", "cr.cuh", "rope.cuh", "launch_rope.cuh", "rope_vjp_f32.cu",
+             "rope_rollout_f32.cu", "rope_linearize_f32.cu"],
+    "cloth": ["common.cuh", "rope.cuh", "cloth_band.cuh", "cloth.cuh", "launch_cloth.cuh", "cloth_f32.cu"],
+}
+
+
+def kernel_source_hash(kernel: str):
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2606_14188_b300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in KERNEL_SOURCES["cloth" if kernel.startswith("cloth") else "rope"]:
+        h.update(open(os.path.join(ROOT, "paper_2606_14188_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -94,7 +102,7 @@ def load_traffic(kernel: str, workload: str = WORKLOAD):
     try:
         d = json.load(open(path))
         e = d.get(kernel)
-        if e and e.get("source_hash") == kernel_source_hash() and e.get("workload") == workload:
+        if e and e.get("source_hash") == kernel_source_hash(kernel) and e.get("workload") == workload:
             return float(e["dram_bytes_per_launch"])
     except Exception:
         return None

@@ -318,7 +318,10 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
       if (l < kbp) {
 #pragma unroll
         for (int cc = 0; cc < CL_KB; ++cc)
-          if (cc <= l && l - cc <= bw) Wn[cb[cc] + (l - cc)] = row[cc];
+          if (cc <= l && l - cc <= bw) {
+            Wn[cb[cc] + (l - cc)] = row[cc];
+            Lg[(size_t)(j + cc) * D.LDB + (l - cc)] = row[cc];
+          }
         vb[j + l] = yv;
       }
       if (bad && l == 0) flag[0] = R(1);
@@ -348,7 +351,10 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
 #pragma unroll
       for (int cc = 0; cc < CL_KB; ++cc) {
         if (cc >= kbp) break;
-        if (i - j - cc <= bw) Wn[cb[cc] + (i - j - cc)] = a[cc];
+        if (i - j - cc <= bw) {
+          Wn[cb[cc] + (i - j - cc)] = a[cc];
+          Lg[(size_t)(j + cc) * D.LDB + (i - j - cc)] = a[cc];
+        }
         Pb[cc * D.PL + CL_KB + (i - jn)] = a[cc];
       }
     }
@@ -357,10 +363,7 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
     for (int cc = 0; cc < CL_KB; ++cc)
       for (int ii = threadIdx.x; ii < D.PL; ii += CL_NT)
         if (cc >= kbp || ii < CL_KB || jn + ii - CL_KB > imax) Pb[cc * D.PL + ii] = R(0);
-    __syncthreads();
-    for (int cc = 0; cc < kbp; ++cc)
-      for (int r = threadIdx.x; r < LDW; r += CL_NT) Lg[(size_t)(j + cc) * D.LDB + r] = Wn[cb[cc] + r];
-    __syncthreads();                         // the panel's window slots are free from here
+    __syncthreads();                         // the panel is final (and in Lg): its slots are free
     // the last warp assembles the columns entering the window into the panel's slots while the
     // others apply the rank-kbp update to the trailing triangle [jn, jn + T)
     const int c0 = j + WC, c1 = min(j + WC + kbp, N);
@@ -446,15 +449,16 @@ __device__ __noinline__ void cl_back(const ClothDims& D, const R* Lg, R* sm) {
     }
     __syncthreads();
     if (warp == 0) {
-      for (int c = jn - 1; c >= j; --c) {
-        const R* col = Lb + (c - j) * LDB;
-        const int i = c + 1 + lane;
-        R acc = (i < jn && i - c <= bw) ? col[i - c] * vb[i] : R(0);
-        acc = wsum(acc);
-        __syncwarp();
-        if (lane == 0) vb[c] = (vb[c] - tc[c - j] - acc) / col[0];
-        __syncwarp();
+      // lane l holds y_{j+l} - (contributions of the rows below the panel); from the last column
+      // up, x_c is broadcast and the lanes above it subtract L[c][l] x_c
+      const int l = lane;
+      R yl = l < kbp ? vb[j + l] - tc[l] : R(0);
+      for (int cc = kbp - 1; cc >= 0; --cc) {
+        const R xc = __shfl_sync(FULL, yl, cc) / Lb[cc * LDB];
+        if (l == cc) yl = xc;
+        else if (l < cc && cc - l <= bw) yl -= Lb[l * LDB + (cc - l)] * xc;
       }
+      if (l < kbp) vb[j + l] = yl;
     }
     __syncthreads();
     buf ^= 1;

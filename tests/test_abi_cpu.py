@@ -6,6 +6,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 from paper_2606_14188_b300 import _lib as L
@@ -95,3 +96,22 @@ def test_argument_errors_without_gpu():
     assert lib.mpc_poll(None, 1, 0, None) == 1
     assert lib.mpc_cancel(None, 1) == 1
     assert lib.mpc_destroy(None) == 0
+
+
+def test_cloth_argument_errors_without_gpu():
+    """Malformed cloth grids and unknown kinds are rejected before any device call."""
+    from paper_2606_14188_b300 import scenes
+    from paper_2606_14188_b300.sim import make_params
+    lib = L.lib()
+    sc = scenes.cloth_scene(4, 5, n_spheres=1, seed=1)
+    rest = np.ascontiguousarray(sc["rest_x"], dtype=np.float64)
+    rp = rest.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+    for bad in (dict(rows=4, cols=6), dict(rows=0, cols=5), dict(rows=20, cols=1), dict(kind="x")):
+        P = make_params(sc)
+        if "kind" in bad:
+            P.kind = 7
+        else:
+            P.rows, P.cols = bad["rows"], bad["cols"]
+        assert lib.sim_create(C.byref(P), rp, C.byref(h)) == 1, bad
+        assert not h.value
