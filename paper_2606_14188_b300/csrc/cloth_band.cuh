@@ -7,7 +7,8 @@
 // bandwidth bw = 3 span + 2, span = the largest node-index difference of a spring (2 C).
 //
 // Factorisation: one CTA, right-looking and blocked by panels of CL_KB columns over a window of
-// the band held in shared memory.  Columns are assembled straight into the window as they enter it
+// the band held in shared memory: column c in slot c mod WC, its row i at offset i - (c & ~3), so
+// that every 4-row segment starting at a multiple of 4 is 16-byte aligned.  Columns are assembled straight into the window as they enter it
 // (spring Hessian blocks computed there, diagonal blocks from a node array), the panel is factored
 // by one warp while the rank-CL_KB update of the trailing triangle is shared by all threads, and the
 // finished panel is written to global memory (column-major band, stride LDB) for the backward
@@ -24,7 +25,7 @@ constexpr int CL_KB = 12;               // panel width (four nodes)
 struct ClothDims {
   int R, C, nv, N;       // grid, nodes, unknowns (3 nv)
   int bw;                // scalar half bandwidth
-  int LDW, WC;           // window: column stride, columns held (multiple of 3)
+  int LDW, WC;           // window: column stride (multiple of 4), columns held (multiple of 3)
   int LDB;               // global factor column stride (multiple of 4)
   int PL;                // panel buffer row length
   int nspr;              // springs
@@ -43,7 +44,7 @@ __host__ __device__ inline ClothDims cloth_dims(int R, int C) {
   if (R >= 2 && C >= 2 && C + 1 > span) span = C + 1;
   if (R >= 3 && 2 * C > span) span = 2 * C;
   d.bw = 3 * span + 2;
-  d.LDW = d.bw + 1;
+  d.LDW = cl_rup(d.bw + 4, 4);
   d.WC = cl_rup(d.bw + CL_KB, 3);
   d.LDB = cl_rup(d.bw + 1, 4);
   d.PL = cl_rup(d.bw + CL_KB + 3, 4);
@@ -79,6 +80,12 @@ template <>
 __device__ __forceinline__ void ld4<float>(const float* p, float o[4]) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <typename R>
+__device__ __forceinline__ void st4(R* p, const R v[4]) { p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = v[3]; }
+template <>
+__device__ __forceinline__ void st4<float>(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // elements of one CTA's workspace slot in global memory: six node vectors [N], the diagonal
@@ -206,7 +213,7 @@ __device__ __forceinline__ void cl_load_cols(const Scene<R>& S, const ClothDims&
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = b; a < 3; ++a) Wn[sl[b] * D.LDW + (a - b)] = M.Dg[6 * v + sym3(a, b)];
+        for (int a = b; a < 3; ++a) Wn[sl[b] * D.LDW + (a - b) + ((3 * v + b) & 3)] = M.Dg[6 * v + sym3(a, b)];
     } else {
       int u, fam;
       const int s = cl_incident(D, v, 2 * (t - 1), u, fam);
@@ -216,7 +223,8 @@ __device__ __forceinline__ void cl_load_cols(const Scene<R>& S, const ClothDims&
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) Wn[sl[b] * D.LDW + (3 * (u - v) + a - b)] = -H[a * 3 + b];
+        for (int a = 0; a < 3; ++a)
+          Wn[sl[b] * D.LDW + (3 * (u - v) + a - b) + ((3 * v + b) & 3)] = -H[a * 3 + b];
     }
   }
   __syncthreads();
@@ -247,7 +255,7 @@ __device__ __forceinline__ void cl_load_cols_warp(const Scene<R>& S, const Cloth
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = b; a < 3; ++a) Wn[sl[b] * D.LDW + (a - b)] = M.Dg[6 * v + sym3(a, b)];
+        for (int a = b; a < 3; ++a) Wn[sl[b] * D.LDW + (a - b) + ((3 * v + b) & 3)] = M.Dg[6 * v + sym3(a, b)];
     } else {
       int u, fam;
       const int s = cl_incident(D, v, 2 * (t - 1), u, fam);
@@ -257,7 +265,8 @@ __device__ __forceinline__ void cl_load_cols_warp(const Scene<R>& S, const Cloth
 #pragma unroll
       for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) Wn[sl[b] * D.LDW + (3 * (u - v) + a - b)] = -H[a * 3 + b];
+        for (int a = 0; a < 3; ++a)
+          Wn[sl[b] * D.LDW + (3 * (u - v) + a - b) + ((3 * v + b) & 3)] = -H[a * 3 + b];
     }
   }
   __syncwarp();
@@ -285,7 +294,7 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
       int sl = slot0;
 #pragma unroll
       for (int cc = 0; cc < CL_KB; ++cc) {
-        cb[cc] = sl * LDW;
+        cb[cc] = sl * LDW + (cc & 3);        // row i of column j + cc at cb[cc] + (i - j - cc)
         if (++sl == WC) sl = 0;
       }
     }
@@ -397,15 +406,17 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
           const int kk = 4 * b + y;
-          if (kk >= T) continue;
+          if (kk >= T) continue;                // (such a slot may be refilled meanwhile)
           int sl = tslot + kk;
           while (sl >= WC) sl -= WC;
-          R* dst = Wn + sl * LDW;
+          // rows jn + 4a .. jn + 4a + 3 of column jn + kk: offset 4 (a - b), aligned; rows past the
+          // triangle get zero updates, rows above the diagonal land in the column's padding
+          R* dst = Wn + sl * LDW + 4 * (a - b);
+          R d4[4];
+          ld4(dst, d4);
 #pragma unroll
-          for (int x = 0; x < 4; ++x) {
-            const int ii = 4 * a + x;
-            if (ii < T && ii >= kk) dst[ii - kk] -= acc[x][y];
-          }
+          for (int x = 0; x < 4; ++x) d4[x] -= acc[x][y];
+          st4(dst, d4);
         }
       }
     }
