@@ -26,7 +26,7 @@ struct ClothDims {
   int R, C, nv, N;       // grid, nodes, unknowns (3 nv)
   int bw;                // scalar half bandwidth
   int LDW, WC;           // window: column stride (multiple of 4), columns held (multiple of 3)
-  int LDB;               // global factor column stride (multiple of 4)
+  int LDB;               // global factor column stride (multiple of 4, > bw + 1)
   int PL;                // panel buffer row length
   int nspr;              // springs
   int off[7];            // first spring of each family (off[6] = nspr)
@@ -44,9 +44,9 @@ __host__ __device__ inline ClothDims cloth_dims(int R, int C) {
   if (R >= 2 && C >= 2 && C + 1 > span) span = C + 1;
   if (R >= 3 && 2 * C > span) span = 2 * C;
   d.bw = 3 * span + 2;
-  d.LDW = cl_rup(d.bw + 4, 4);
+  d.LDW = cl_rup(d.bw + 5, 4);          // padding (c & 3) in front, at least one spare entry behind
   d.WC = cl_rup(d.bw + CL_KB, 3);
-  d.LDB = cl_rup(d.bw + 1, 4);
+  d.LDB = cl_rup(d.bw + 2, 4);          // at least one spare entry behind the band
   d.PL = cl_rup(d.bw + CL_KB + 3, 4);
   const int nh = R * (C - 1), nvt = (R - 1) * C, nd = (R - 1) * (C - 1);
   const int nbh = C >= 3 ? R * (C - 2) : 0, nbv = R >= 3 ? (R - 2) * C : 0;
@@ -313,14 +313,17 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
         if (cc >= kbp) break;
         const R piv = __shfl_sync(FULL, row[cc], cc);
         bad = bad || !(piv > R(0)) || !(piv < R(1e300));
-        const R lp = sqrt(piv), il = R(1) / lp;
+        const R il = rsq(piv), lp = piv * il;   // one reciprocal square root per pivot
         const R ycc = __shfl_sync(FULL, yv, cc) * il;
-        if (l == cc) { row[cc] = lp; yv = ycc; }
-        else if (l > cc) { row[cc] *= il; yv -= row[cc] * ycc; }
+        // branch-free: lane cc takes the pivot, the lanes below scale their entry
+        const R rs = row[cc] * il;
+        row[cc] = l == cc ? lp : (l > cc ? rs : row[cc]);
+        yv = l == cc ? ycc : (l > cc ? yv - rs * ycc : yv);
+        const R rc = l > cc ? rs : R(0);
 #pragma unroll
         for (int c2 = cc + 1; c2 < CL_KB; ++c2) {
-          const R lc2 = __shfl_sync(FULL, row[cc], c2);
-          if (l >= c2) row[c2] -= row[cc] * lc2;
+          const R lc2 = __shfl_sync(FULL, rs, c2);
+          row[c2] -= (l >= c2 ? rc : R(0)) * lc2;
         }
         if (l == 0) ild[cc] = il;
       }
@@ -341,9 +344,18 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
     //     substitution vb_i -= L21_i . y_panel; the rows also go to the panel buffer
     const int imax = min(j + kbp - 1 + bw, N - 1);
     for (int i = jn + threadIdx.x; i <= imax; i += CL_NT) {
+      // branch-free: entries outside the band are read at a clamped address and replaced by 0;
+      // their results (exactly 0) are stored to each column's spare last entry (window: LDW - 1,
+      // factor: LDB - 1), which nothing reads
       R a[CL_KB];
+      bool in[CL_KB];
 #pragma unroll
-      for (int cc = 0; cc < CL_KB; ++cc) a[cc] = (cc < kbp && i - j - cc <= bw) ? Wn[cb[cc] + (i - j - cc)] : R(0);
+      for (int cc = 0; cc < CL_KB; ++cc) {
+        const int off = i - j - cc;
+        in[cc] = cc < kbp && off <= bw;
+        const R v = Wn[cb[cc] + min(max(off, 0), bw)];
+        a[cc] = in[cc] ? v : R(0);
+      }
       R acc = R(0);
 #pragma unroll
       for (int cc = 0; cc < CL_KB; ++cc) {
@@ -360,10 +372,9 @@ __device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, co
 #pragma unroll
       for (int cc = 0; cc < CL_KB; ++cc) {
         if (cc >= kbp) break;
-        if (i - j - cc <= bw) {
-          Wn[cb[cc] + (i - j - cc)] = a[cc];
-          Lg[(size_t)(j + cc) * D.LDB + (i - j - cc)] = a[cc];
-        }
+        const int off = i - j - cc;
+        Wn[in[cc] ? cb[cc] + off : cb[cc] - (cc & 3) + LDW - 1] = a[cc];
+        Lg[(size_t)(j + cc) * D.LDB + (in[cc] ? off : D.LDB - 1)] = a[cc];
         Pb[cc * D.PL + CL_KB + (i - jn)] = a[cc];
       }
     }
