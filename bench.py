@@ -283,7 +283,7 @@ def cloth_leg(args, flush, stream, world, cpu):
     R, C, nv = p["rows"], p["cols"], p["n_nodes"]
     k = p["checkpoint_every"]
     nobs = len(p["obstacles"])
-    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H, newton_max=100)
+    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H, newton_max=300)
     q0 = torch.tensor(w["q0"], dtype=torch.float32, device="cuda")
     U = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
     _, _, st_f, cnt = s.rollout_counters(q0, U)

@@ -56,6 +56,7 @@ ST_NOTPD = 8       # a stage-2 / adjoint system was not positive definite
 # root / optimum to FP64 accuracy
 TOL_X = 1e-13
 NEWTON_MAX = 100
+NEWTON_MAX_CLOTH = 300  # a slack cloth's first steps from the flat state need up to ~200 iterations
 IPM_MAX = 200
 STALL_ALPHA = 1e-6     # stage-2 step length counted as a stall
 STALL_MAX = 5          # consecutive stalls after which stage 2 reports no solution
@@ -666,7 +667,8 @@ def step(sc: Scene, q, u, mode, tol=TOL_X, info=None, x_start=None, Delta_start=
         for i in range(2):
             x_start[sc.grasp[i]] += gstar[i] - g[i]
     d = grasp_stiffness(sc, x, g, mode)
-    xs, it1, st1 = stage1_solve(sc, x, gstar, d, tol, x_start=x_start)
+    cap = NEWTON_MAX_CLOTH if sc.kind == "cloth" else NEWTON_MAX
+    xs, it1, st1 = stage1_solve(sc, x, gstar, d, tol, maxit=cap, x_start=x_start)
     if mode == HARD:
         Delta, sig, phi, n, it2, st2 = stage2_hard(sc, xs, d, tol, Delta_start)
     else:

@@ -60,7 +60,7 @@ def _cloth(R, C, B, H, seed, spheres=2, ckpt=None):
 def test_cloth6_fp64_rollout(mode):
     B, H = 2, 8
     sc, q0, U = _cloth(6, 6, B, H, seed=11)
-    s = _sim(sc, 8, B, H, fwd_mode=mode, newton_max=100)
+    s = _sim(sc, 8, B, H, fwd_mode=mode, newton_max=300)
     traj, qH, st = s.rollout(_t(q0, 8), _t(U, 8))
     traj = traj.cpu().numpy()
     osc = _oscene(sc)
@@ -75,7 +75,7 @@ def test_cloth_ragged_fp64_rollout():
     topology through the cloth kernel)."""
     for R, C, H in [(5, 7, 6), (1, 9, 5)]:
         sc, q0, U = _cloth(R, C, 1, H, seed=21, spheres=1)
-        s = _sim(sc, 8, 1, H, newton_max=100)
+        s = _sim(sc, 8, 1, H, newton_max=300)
         traj, qH, st = s.rollout(_t(q0, 8), _t(U, 8))
         ref, ost, _ = osim.rollout(_oscene(sc), q0[0], U[0], "hard")
         assert ost == 0 and int(st[0]) == 0, (R, C, ost, int(st[0]))
@@ -86,7 +86,7 @@ def test_cloth_ragged_fp64_rollout():
 def test_cloth6_fp64_vjp(grad_mode):
     B, H = 2, 6
     sc, q0, U = _cloth(6, 6, B, H, seed=13, ckpt=4)
-    s = _sim(sc, 8, B, H, grad_mode=grad_mode, newton_max=100)
+    s = _sim(sc, 8, B, H, grad_mode=grad_mode, newton_max=300)
     Lv, dU, dq0, st = s.rollout_vjp(_t(q0, 8), _t(U, 8))
     osc = _oscene(sc)
     for b in range(B):
@@ -100,7 +100,7 @@ def test_cloth6_fp64_vjp(grad_mode):
 def test_cloth8_fp32_rollout_and_vjp():
     B, H = 4, 10
     sc, q0, U = _cloth(8, 8, B, H, seed=17, ckpt=5)
-    s = _sim(sc, 4, B, H, newton_max=100)
+    s = _sim(sc, 4, B, H, newton_max=300)
     traj, qH, st = s.rollout(_t(q0, 4), _t(U, 4))
     Lv, dU, dq0, st2 = s.rollout_vjp(_t(q0, 4), _t(U, 4))
     traj = traj.cpu().numpy()
