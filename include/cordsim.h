@@ -108,8 +108,11 @@ typedef struct cs_sim cs_sim;
 
 /* Create a simulator for one scene.  rest_x: HOST array [n_v][3] of rest node positions (the
  * spring rest lengths are taken from it).  Allocates the handle's device workspace for
- * max_batch rollouts of up to max_horizon steps.  Errors: CS_ERR_INVALID_ARG (bad sizes,
- * n_v beyond the kernel's limit, unknown obstacle), CS_ERR_OOM, CS_ERR_CUDA. */
+ * max_batch rollouts of up to max_horizon steps.  A rope (CS_ROPE) has 2..128 nodes; a cloth
+ * (CS_CLOTH) rows x cols nodes, row-major, with cols limited by the band window in shared memory
+ * (33 in FP32, 22 in FP64: the node-coupled matrices have half bandwidth 6 cols + 2).
+ * Errors: CS_ERR_INVALID_ARG (bad sizes, a rope or cloth beyond those limits, unknown kind or
+ * obstacle), CS_ERR_OOM, CS_ERR_CUDA. */
 cs_status sim_create(const cs_params* params, const double* rest_x, cs_sim** out);
 
 /* Release the handle and its workspace (synchronises the device first).  NULL is accepted. */
@@ -160,7 +163,7 @@ cs_status sim_rollout_vjp(cs_sim* sim, int B, int H, const void* q0, const void*
  *   A  [B][H][n_q][n_q]  A_t[i][j] = d q_{t+1,i} / d q_{t,j}
  *   Bm [B][H][n_q][6]    B_t[i][j] = d q_{t+1,i} / d u_{t,j}
  *   status [B] (OR over the steps)
- * Errors: as sim_rollout. */
+ * Errors: as sim_rollout; CS_ERR_UNSUPPORTED for a cloth (built for ropes). */
 cs_status sim_linearize(cs_sim* sim, int B, int H, const void* z, const void* v, void* A,
                         void* Bm, int32_t* status, void* stream);
 
@@ -244,9 +247,9 @@ typedef struct {
 
 /* Create a server on the current device.  Errors: CS_ERR_INVALID_ARG, CS_ERR_OOM, CS_ERR_CUDA. */
 cs_status mpc_create(const cs_mpc_config* config, cs_mpc** out);
-/* Queue a plan solve; the request and its host arrays are copied before the call returns.
- * Errors: CS_ERR_INVALID_ARG (sizes, unsupported scene, a request larger than the memory
- * budget). */
+/* Queue a plan solve of a rope or a cloth; the request and its host arrays are copied before the
+ * call returns.  Errors: CS_ERR_INVALID_ARG (sizes, a rope or cloth beyond the limits of
+ * sim_create, a request larger than the memory budget). */
 cs_status mpc_submit(cs_mpc* mpc, const cs_mpc_request* req, uint64_t* ticket);
 /* Wait up to timeout_ms (0: do not wait, < 0: no limit) for a result.  CS_OK fills `out` and
  * forgets the ticket; CS_ERR_PENDING if it is not done yet; CS_ERR_CANCELLED; CS_ERR_INVALID_ARG

@@ -102,14 +102,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
       delete s;
       return cs_fail(CS_ERR_INVALID_ARG, "cloth too wide for the band window in shared memory");
     }
-    const int R = P->rows, C = P->cols;
-    auto id = [&](int r, int c) { return r * C + c; };
-    for (int r = 0; r < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c), id(r, c + 1)));
-    for (int r = 0; r + 1 < R; ++r) for (int c = 0; c < C; ++c) L1.push_back(dist(id(r, c), id(r + 1, c)));
-    for (int r = 0; r + 1 < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c), id(r + 1, c + 1)));
-    for (int r = 0; r + 1 < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c + 1), id(r + 1, c)));
-    for (int r = 0; r < R; ++r) for (int c = 0; c + 2 < C; ++c) L1.push_back(dist(id(r, c), id(r, c + 2)));
-    for (int r = 0; r + 2 < R; ++r) for (int c = 0; c < C; ++c) L1.push_back(dist(id(r, c), id(r + 2, c)));
+    cloth_rest_lengths(P->rows, P->cols, rest_x, L1);
     if ((int)L1.size() != s->cd.nspr) {
       delete s;
       return cs_fail(CS_ERR_INVALID_ARG, "cloth spring count mismatch");

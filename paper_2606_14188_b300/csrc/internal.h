@@ -2,8 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "cordsim.h"
 #include "cloth_band.cuh"
@@ -136,6 +138,29 @@ cs_status launch_cloth_vjp(cs_sim* s, int B, int H, const void* q0, const void* 
                            cudaStream_t st);
 template <typename R>
 int cloth_ctas_per_sm(const cs_sim* s);
+template <typename R>
+cs_status launch_cloth_plan(const cs::Scene<R>& S, const cs::ClothDims& D, const void* job, int Rc, void* slots,
+                            size_t slot_stride, int nslots, cudaStream_t st);
+template <typename R>
+cs_status cloth_plan_prepare(const cs::ClothDims& D, int* ctas_per_sm);
+
+// rest lengths of a cloth's springs in the cloth kernels' order (family by family: structural along
+// rows, along columns, the two shear diagonals, bend along rows, along columns)
+inline void cloth_rest_lengths(int R, int C, const double* rest, std::vector<double>& L1) {
+  auto dist = [&](int a, int b) {
+    const double d0 = rest[3 * b] - rest[3 * a], d1 = rest[3 * b + 1] - rest[3 * a + 1],
+                 d2 = rest[3 * b + 2] - rest[3 * a + 2];
+    return std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  };
+  auto id = [&](int r, int c) { return r * C + c; };
+  L1.clear();
+  for (int r = 0; r < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c), id(r, c + 1)));
+  for (int r = 0; r + 1 < R; ++r) for (int c = 0; c < C; ++c) L1.push_back(dist(id(r, c), id(r + 1, c)));
+  for (int r = 0; r + 1 < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c), id(r + 1, c + 1)));
+  for (int r = 0; r + 1 < R; ++r) for (int c = 0; c + 1 < C; ++c) L1.push_back(dist(id(r, c + 1), id(r + 1, c)));
+  for (int r = 0; r < R; ++r) for (int c = 0; c + 2 < C; ++c) L1.push_back(dist(id(r, c), id(r, c + 2)));
+  for (int r = 0; r + 2 < R; ++r) for (int c = 0; c < C; ++c) L1.push_back(dist(id(r, c), id(r + 2, c)));
+}
 template <typename R>
 cs_status launch_linearize(cs_sim* s, int B, int H, const void* z, const void* v, void* A,
                            void* Bm, int32_t* status, cudaStream_t st);

@@ -1,7 +1,7 @@
 // Kernel launchers of the cloth path (instantiated per real type in cloth_*.cu).  One CTA per
 // rollout at a time over a grid of at most s->nslots CTAs, each with its own workspace slot.
 #pragma once
-#include "cloth.cuh"
+#include "cloth_plan.cuh"
 #include "internal.h"
 
 namespace csi {
@@ -36,6 +36,31 @@ cs_status launch_cloth_vjp(cs_sim* s, int B, int H, const void* q0, const void* 
                                                         (R*)s->d_slots, s->slot_stride, (R*)s->d_ws,
                                                         s->ws_stride);
   return check_launch("cloth_vjp_kernel");
+}
+
+// plan solves: every candidate of one request (job: its PlanJob in device memory; S: the same
+// scene, from the host copy of the job table), over at most nslots CTAs
+template <typename R>
+cs_status launch_cloth_plan(const cs::Scene<R>& S, const cs::ClothDims& D, const void* job, int Rc, void* slots,
+                            size_t slot_stride, int nslots, cudaStream_t st) {
+  const size_t smem = cs::cloth_smem_elems(D) * sizeof(R);
+  const int grid = Rc < nslots ? Rc : nslots;
+  cs::cloth_vjp_plan_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, D, static_cast<const cs::PlanJob<R>*>(job),
+                                                             static_cast<R*>(slots), slot_stride);
+  return check_launch("cloth_vjp_plan_kernel");
+}
+
+// raise the plan kernel's shared-memory limit (not a stream operation: before a capture) and
+// report its resident CTAs per SM
+template <typename R>
+cs_status cloth_plan_prepare(const cs::ClothDims& D, int* ctas_per_sm) {
+  const size_t smem = cs::cloth_smem_elems(D) * sizeof(R);
+  cs_status r = prep_kernel(cs::cloth_vjp_plan_kernel<R>, smem);
+  if (r) return r;
+  int a = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cs::cloth_vjp_plan_kernel<R>, cs::CL_NT, smem);
+  *ctas_per_sm = a > 0 ? a : 1;
+  return CS_OK;
 }
 
 // resident CTAs per SM of the cloth kernels at their shared-memory size (at least 1)

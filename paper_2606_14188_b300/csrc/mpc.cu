@@ -79,18 +79,20 @@ class Arena {
 // device layout of one request (offsets from its arena block)
 struct Layout {
   size_t L1, L2, q0, warm, U, M, V, dU, L, status, ws, best, st, total;
+  size_t l1_n;           // rest lengths in the L1 region (rope: 128 slots; cloth: every spring)
   size_t ws_stride;      // elements per candidate
   size_t best_bytes;     // best_u (padded) + PlanState: one D2H copy
   // pinned host staging: uploads then the result
   size_t h_L1, h_L2, h_q0, h_warm, h_res, h_total;
 };
 
-Layout make_layout(int nv, int H, int Rc, int ck, int rb) {
+Layout make_layout(int nv, int H, int Rc, int ck, int rb, size_t l1_n) {
   Layout l{};
   const int nq = 3 * nv + 6;
   size_t o = 0;
   auto take = [&](size_t n) { const size_t at = o; o += al(n); return at; };
-  l.L1 = take(128 * (size_t)rb);
+  l.l1_n = l1_n;
+  l.L1 = take(l1_n * (size_t)rb);
   l.L2 = take(128 * (size_t)rb);
   l.q0 = take((size_t)nq * rb);
   l.warm = take((size_t)H * 6 * rb);
@@ -110,7 +112,7 @@ Layout make_layout(int nv, int H, int Rc, int ck, int rb) {
   l.st = l.best + bu;
   l.total = o;
   o = 0;
-  l.h_L1 = take(128 * (size_t)rb);
+  l.h_L1 = take(l1_n * (size_t)rb);
   l.h_L2 = take(128 * (size_t)rb);
   l.h_q0 = take((size_t)nq * rb);
   l.h_warm = take((size_t)H * 6 * rb);
@@ -123,7 +125,9 @@ struct Req {
   uint64_t ticket = 0;
   cs_mpc_request r{};
   std::vector<double> rest, q0, warm;
-  int nv = 0, nq = 0, ppl = 1;
+  int nv = 0, nq = 0, ppl = 1;   // ppl: rope pairs per lane; 3 for a cloth
+  bool cloth = false;
+  cs::ClothDims cd{};
   Layout lay{};
   size_t off = 0, poff = 0;
   unsigned char* dev = nullptr;    // device block
@@ -186,6 +190,10 @@ struct cs_mpc {
   bool set_dirty = false;     // the running set lost members since the last tick
   std::atomic<int64_t> ticks{0}, graph_launches{0}, kernel_launches{0}, graphs_built{0};
   int warps[3] = {1, 1, 1};   // tuned warps per CTA of the packed launch, by pairs per lane
+  // cloth candidates: CTA workspace slots shared by the cloth launches of a tick (one stream)
+  void* cloth_pool = nullptr;
+  size_t cloth_pool_bytes = 0, cloth_stride = 0;
+  int cloth_nslots = 0;
 };
 
 namespace {
@@ -197,8 +205,11 @@ cs_status cuda_err(cudaError_t e, const char* what) { return cs_cuda_fail(e, wha
 cs_status check_request(const cs_mpc* m, const cs_mpc_request* q) {
   const cs_params& P = q->params;
   if (!q->rest_x || !q->q0) return cs_fail(CS_ERR_INVALID_ARG, "rest_x and q0 are required");
-  if (P.kind != CS_ROPE) return cs_fail(CS_ERR_UNSUPPORTED, "only kind = CS_ROPE is built");
-  if (P.n_nodes < 2 || P.n_nodes > 128) return cs_fail(CS_ERR_INVALID_ARG, "rope n_nodes must be in [2, 128]");
+  const bool cloth = P.kind == CS_CLOTH;
+  if (P.kind != CS_ROPE && !cloth) return cs_fail(CS_ERR_INVALID_ARG, "unknown kind");
+  if (!cloth && (P.n_nodes < 2 || P.n_nodes > 128)) return cs_fail(CS_ERR_INVALID_ARG, "rope n_nodes must be in [2, 128]");
+  if (cloth && (P.rows < 1 || P.cols < 2 || P.rows > 256 || P.cols > 256 || P.n_nodes != P.rows * P.cols))
+    return cs_fail(CS_ERR_INVALID_ARG, "cloth needs rows >= 1, cols >= 2 and n_nodes = rows * cols");
   for (int i = 0; i < 2; ++i)
     if (P.grasp_node[i] < 0 || P.grasp_node[i] >= P.n_nodes) return cs_fail(CS_ERR_INVALID_ARG, "grasp_node out of range");
   if (P.grasp_node[0] == P.grasp_node[1]) return cs_fail(CS_ERR_INVALID_ARG, "the two grippers must hold different nodes");
@@ -219,6 +230,11 @@ cs_status check_request(const cs_mpc* m, const cs_mpc_request* q) {
     if (q->loss.goal_nodes[g] < 0 || q->loss.goal_nodes[g] >= P.n_nodes)
       return cs_fail(CS_ERR_INVALID_ARG, "goal node out of range");
   if (!(q->u_max > 0) || !(q->sigma >= 0) || !(q->lr >= 0)) return cs_fail(CS_ERR_INVALID_ARG, "need u_max > 0, sigma >= 0, lr >= 0");
+  if (cloth) {
+    if (cs::cloth_smem_elems(cs::cloth_dims(P.rows, P.cols)) * (size_t)m->rb > m->smem_optin)
+      return cs_fail(CS_ERR_INVALID_ARG, "cloth too wide for the band window in shared memory");
+    return CS_OK;
+  }
   const int ppl = (P.n_nodes + 1) / 2 <= 32 ? 1 : 2;
   const size_t ws = m->rb == 4 ? csi::plan_warp_smem<float>(ppl, P.n_obstacles, q->H)
                                : csi::plan_warp_smem<double>(ppl, P.n_obstacles, q->H);
@@ -240,13 +256,17 @@ void stage_uploads(cs_mpc* m, Req& q) {
     const double d0 = x[3 * b] - x[3 * a], d1 = x[3 * b + 1] - x[3 * a + 1], d2 = x[3 * b + 2] - x[3 * a + 2];
     return std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
   };
-  for (int j = 0; j + 1 < nv; ++j) L1[j] = dist(j, j + 1);
-  for (int j = 0; j + 2 < nv; ++j) L2[j] = dist(j, j + 2);
+  if (q.cloth) {
+    csi::cloth_rest_lengths(q.r.params.rows, q.r.params.cols, q.rest.data(), L1);
+  } else {
+    for (int j = 0; j + 1 < nv; ++j) L1[j] = dist(j, j + 1);
+    for (int j = 0; j + 2 < nv; ++j) L2[j] = dist(j, j + 2);
+  }
   auto put = [&](size_t off, const double* src, size_t n) {
     if (m->rb == 4) put_real<float>(q.host + off, src, n);
     else put_real<double>(q.host + off, src, n);
   };
-  put(q.lay.h_L1, L1.data(), 128);
+  put(q.lay.h_L1, L1.data(), q.lay.l1_n);
   put(q.lay.h_L2, L2.data(), 128);
   put(q.lay.h_q0, q.q0.data(), q.q0.size());
   if (!q.warm.empty()) put(q.lay.h_warm, q.warm.data(), q.warm.size());
@@ -255,7 +275,7 @@ void stage_uploads(cs_mpc* m, Req& q) {
 cs_status enqueue_uploads(cs_mpc* m, Req& q) {
   const Layout& l = q.lay;
   const size_t rb = (size_t)m->rb;
-  struct C { size_t d, h, n; } cps[4] = {{l.L1, l.h_L1, 128 * rb}, {l.L2, l.h_L2, 128 * rb},
+  struct C { size_t d, h, n; } cps[4] = {{l.L1, l.h_L1, l.l1_n * rb}, {l.L2, l.h_L2, 128 * rb},
                                          {l.q0, l.h_q0, (size_t)q.nq * rb},
                                          {l.warm, l.h_warm, q.warm.empty() ? 0 : (size_t)q.r.H * 6 * rb}};
   for (const C& c : cps) {
@@ -305,7 +325,8 @@ struct Group {
 };
 
 template <typename R>
-cs_status enqueue_tick(cs_mpc* m, const Group g[3], int njobs, int max_elems, bool count) {
+cs_status enqueue_tick(cs_mpc* m, const Group g[3], const std::vector<int>& cloth_jobs, int njobs, int max_elems,
+                       bool count) {
   cs_status r;
   for (int ppl = 1; ppl <= 2; ++ppl) {
     const Group& G = g[ppl];
@@ -316,6 +337,14 @@ cs_status enqueue_tick(cs_mpc* m, const Group g[3], int njobs, int max_elems, bo
     const int grid = (G.total + warps - 1) / warps;
     r = csi::launch_plan_vjp<R>(m->d_jobs + (size_t)G.j0 * m->job_bytes, m->d_first + (ppl == 1 ? 0 : g[1].n + 1),
                                 G.n, G.total, ppl, warps, ws, grid, m->stream);
+    if (r) return r;
+    if (count) ++m->kernel_launches;
+  }
+  // cloth requests: one launch each over its candidates (scene from the host job table)
+  for (int j : cloth_jobs) {
+    const auto* hj = reinterpret_cast<const cs::PlanJob<R>*>(m->h_jobs + (size_t)j * m->job_bytes);
+    r = csi::launch_cloth_plan<R>(hj->S, m->running[j]->cd, m->d_jobs + (size_t)j * m->job_bytes, hj->Rc,
+                                  m->cloth_pool, m->cloth_stride, m->cloth_nslots, m->stream);
     if (r) return r;
     if (count) ++m->kernel_launches;
   }
@@ -335,6 +364,38 @@ cs_status prepare_groups(cs_mpc* m, const Group g[3]) {
     cs_status r = csi::plan_prepare<R>(ppl, ws * warps);
     if (r) return r;
   }
+  return CS_OK;
+}
+
+// the cloth plan kernel's shared-memory limit (the widest running cloth) and a workspace pool of
+// one slot per resident CTA, grown (after the stream drains) when a wider cloth joins
+template <typename R>
+cs_status prepare_cloth(cs_mpc* m, const std::vector<int>& cloth_jobs) {
+  if (cloth_jobs.empty()) return CS_OK;
+  const Req* widest = nullptr;
+  size_t stride = 0;
+  for (int j : cloth_jobs) {
+    const Req& q = *m->running[j];
+    if (!widest || cs::cloth_smem_elems(q.cd) > cs::cloth_smem_elems(widest->cd)) widest = &q;
+    stride = std::max(stride, cs::cloth_ws_elems(q.cd, q.r.params.n_obstacles));
+  }
+  int per_sm = 1;
+  cs_status r = csi::cloth_plan_prepare<R>(widest->cd, &per_sm);
+  if (r) return r;
+  const int nslots = per_sm * m->sms;
+  const size_t bytes = stride * (size_t)nslots * sizeof(R);
+  if (bytes > m->cloth_pool_bytes) {
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_err(e, "cudaStreamSynchronize");
+    if (m->cloth_pool) cudaFree(m->cloth_pool);
+    m->cloth_pool = nullptr;
+    m->cloth_pool_bytes = 0;
+    e = cudaMalloc(&m->cloth_pool, bytes);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "cloth workspace") : cuda_err(e, "cudaMalloc");
+    m->cloth_pool_bytes = bytes;
+  }
+  m->cloth_stride = stride;
+  m->cloth_nslots = nslots;
   return CS_OK;
 }
 
@@ -361,8 +422,15 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
     if (e != cudaSuccess) return cuda_err(e, "cudaStreamSynchronize");
   }
   int first1 = 0, first2 = 0;
+  std::vector<int> cloth_jobs;
   for (int j = 0; j < n; ++j) {
     const Req& q = *run[j];
+    if (q.cloth) {
+      cloth_jobs.push_back(j);
+      max_elems = std::max(max_elems, q.r.R * q.r.H * 6);
+      if (changed) csi::plan_fill_job<R>(m->h_jobs + (size_t)j * m->job_bytes, make_spec(m, q));
+      continue;
+    }
     Group& G = g[q.ppl];
     if (!G.n) G.j0 = j;
     ++G.n;
@@ -392,6 +460,7 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
       ++m->kernel_launches;
     }
     if ((r = prepare_groups<R>(m, g))) return r;
+    if ((r = prepare_cloth<R>(m, cloth_jobs))) return r;
     m->graph_valid = false;
   }
   // at most two ticks in flight
@@ -405,7 +474,7 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
       cudaGraph_t graph = nullptr;
       e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_err(e, "cudaStreamBeginCapture");
-      r = enqueue_tick<R>(m, g, n, max_elems, false);
+      r = enqueue_tick<R>(m, g, cloth_jobs, n, max_elems, false);
       e = cudaStreamEndCapture(m->stream, &graph);
       if (r) return r;
       if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
@@ -418,9 +487,9 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
     e = cudaGraphLaunch(m->gexec, m->stream);
     if (e != cudaSuccess) return cuda_err(e, "cudaGraphLaunch");
     ++m->graph_launches;
-    m->kernel_launches += (g[1].n ? 1 : 0) + (g[2].n ? 1 : 0) + 2;
+    m->kernel_launches += (g[1].n ? 1 : 0) + (g[2].n ? 1 : 0) + (int64_t)cloth_jobs.size() + 2;
   } else {
-    if ((r = enqueue_tick<R>(m, g, n, max_elems, true))) return r;
+    if ((r = enqueue_tick<R>(m, g, cloth_jobs, n, max_elems, true))) return r;
   }
   e = cudaEventRecord(ev, m->stream);
   if (e != cudaSuccess) return cuda_err(e, "cudaEventRecord");
@@ -663,7 +732,7 @@ cs_status tune(cs_mpc* m) {
     q.r.G = 1;
     q.r.u_max = 0.05;
     q.r.sigma = 0.02;
-    q.lay = make_layout(nv, H, Rc, P.checkpoint_every, m->rb);
+    q.lay = make_layout(nv, H, Rc, P.checkpoint_every, m->rb, 128);
     q.rest.resize(3 * nv);
     q.q0.resize(q.nq);
     for (int j = 0; j < nv; ++j) {
@@ -738,6 +807,7 @@ void destroy_resources(cs_mpc* m) {
   if (m->pinned) cudaFreeHost(m->pinned);
   if (m->h_jobs) cudaFreeHost(m->h_jobs);
   if (m->h_first) cudaFreeHost(m->h_first);
+  if (m->cloth_pool) cudaFree(m->cloth_pool);
   if (m->stream) cudaStreamDestroy(m->stream);
 }
 
@@ -812,11 +882,18 @@ cs_status mpc_submit(cs_mpc* m, const cs_mpc_request* req, uint64_t* ticket) {
   q->nv = req->params.n_nodes;
   q->nq = 3 * q->nv + 6;
   q->ppl = (q->nv + 1) / 2 <= 32 ? 1 : 2;
+  size_t l1_n = 128;
+  if (req->params.kind == CS_CLOTH) {
+    q->cloth = true;
+    q->ppl = 3;                      // after the rope groups in the running set
+    q->cd = cs::cloth_dims(req->params.rows, req->params.cols);
+    l1_n = (size_t)q->cd.nspr;
+  }
   q->rest.assign(req->rest_x, req->rest_x + 3 * q->nv);
   q->q0.assign(req->q0, req->q0 + q->nq);
   if (req->warm) q->warm.assign(req->warm, req->warm + 6 * (size_t)req->H);
   q->r.rest_x = q->r.q0 = q->r.warm = nullptr;
-  q->lay = make_layout(q->nv, req->H, req->R, req->params.checkpoint_every, m->rb);
+  q->lay = make_layout(q->nv, req->H, req->R, req->params.checkpoint_every, m->rb, l1_n);
   if (q->lay.total > m->arena_bytes) return cs_fail(CS_ERR_INVALID_ARG, "request larger than the memory budget");
   if (q->lay.h_total > m->pinned_bytes) return cs_fail(CS_ERR_INVALID_ARG, "request larger than the staging memory");
   q->t_submit = now_ns();

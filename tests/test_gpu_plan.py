@@ -73,7 +73,8 @@ def _mix():
 
 
 def _run(srv, reqs):
-    ts = [srv.submit(r["scene"], r["q0"], r["H"], r["R"], r["G"], seed=r["seed"]) for r in reqs]
+    ts = [srv.submit(r["scene"], r["q0"], r["H"], r["R"], r["G"], seed=r["seed"], **r.get("kw", {}))
+          for r in reqs]
     return [srv.poll(t) for t in ts]
 
 
@@ -161,3 +162,34 @@ def test_plan_autotuner_writes_and_reuses_its_cache(tmp_path):
     for a, b, c in zip(tuned, again, plain):
         _same(a, b)
         _same(a, c)
+
+
+def test_plan_cloth_fp64_matches_oracle():
+    """A cloth request (one CTA per candidate, banded Cholesky) gives the oracle planner's plan."""
+    sc = scenes.cloth_scene(4, 5, n_spheres=1, seed=3)
+    H, R, G = 3, 3, 3
+    ref = oplan.plan_solve(_oscene(sc), sc["q0"], np.zeros((H, 6)), R, G, lr=0.01, seed=5)
+    with _server(real_bytes=8) as srv:
+        out = srv.poll(srv.submit(sc, sc["q0"], H, R, G, lr=0.01, seed=5, newton_max=300))
+    assert out["status"] == 0
+    assert (out["best_iter"], out["best_candidate"]) == (ref["it"], ref["r"])
+    assert abs(out["L"] - ref["L"]) <= 1e-8 * abs(ref["L"])
+    np.testing.assert_allclose(out["u"], ref["u"], rtol=0, atol=1e-9)
+
+
+def test_plan_rope_and_cloth_mixed_bit_identical():
+    """Cloth and rope requests served together (packed rope launch, one launch per cloth request,
+    graphs) give the results each gives alone."""
+    reqs = _mix()[:3]
+    for i, (R_, C_) in enumerate([(6, 6), (8, 8)]):
+        sc = scenes.cloth_scene(R_, C_, n_spheres=1, seed=300 + i)
+        reqs.append(dict(scene=sc, q0=sc["q0"], H=4, R=6, G=2, seed=2000 + i, kw=dict(newton_max=300)))
+    with _server(real_bytes=4, batched=False) as srv:
+        alone = [_run(srv, [r])[0] for r in reqs]
+    with _server(real_bytes=4, batched=True, use_graphs=True) as srv:
+        mixed = _run(srv, reqs)
+        st = srv.stats()
+    for a, b in zip(alone, mixed):
+        _same(a, b)
+    assert all(m["status"] == 0 for m in mixed[3:])
+    assert st["graph_launches"] >= 1
