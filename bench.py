@@ -87,9 +87,14 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_hash(kernel: str):
+    """hash of the kernel family's sources with // comments and blank lines removed (editing a
+    comment does not invalidate a measured figure)"""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES["cloth" if kernel.startswith("cloth") else "rope"]:
-        h.update(open(os.path.join(ROOT, "paper_2606_14188_b300", "csrc", f), "rb").read())
+        for line in open(os.path.join(ROOT, "paper_2606_14188_b300", "csrc", f)).read().splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -593,9 +593,11 @@ __device__ __forceinline__ void diag_block(const Scene<R>& S, const Lane<R, PPL>
 // Primal-dual interior point with Nesterov-Todd scaling (Vandenberghe, "The CVXOPT linear and
 // quadratic cone program solvers", 2010) for
 //   min 1/2 D^T P D  s.t.  s_i = A_i D_j + phi_i e1 in Q,  z_i in Q  (forces lam_i = A_i^T z_i),
-// centering s_i o z_i = kappa e.  kfinal < 0: fixed target kappa (smooth model); else the target
-// falls each iteration to max(kfinal, min(kappa, 0.1 <s,z>/m)) and the solve ends at the central
-// point of kfinal.  On exit (T, B, V) hold the factorisation of the last H2 = P + sum A^T W^-2 A.
+// centering s_i o z_i = kappa e.  kfinal < 0: fixed target kappa (smooth model).  Else each
+// iteration is a Mehrotra predictor-corrector step: the affine direction (target 0) and its step
+// length alpha_a give the target max(kfinal, (1 - alpha_a)^3 <s,z>/m), and the combined direction
+// adds the second-order term (W^-1 ds_a) o (W dz_a); once the target is kfinal, centring steps at
+// kfinal end the solve.  On exit (T, B, V) hold the factorisation of the last H2 = P + sum A^T W^-2 A.
 template <typename R, int PPL>
 __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS<R>& w, R kappa, R kfinal,
                           int lane, int* iters, bool warm = false) {
