@@ -207,3 +207,44 @@ def test_cloth32_fp32_full_size_properties():
             assert np.isnan(Lv[b]) and np.all(dU[b] == 0)
         else:
             assert np.isfinite(Lv[b]) and np.all(np.isfinite(dU[b])) and np.abs(dU[b]).max() > 0
+
+
+def test_cloth_box_obstacle_fp64():
+    """A 5 x 5 cloth dropping onto a box and the table: stage 2 against box faces, edges and the
+    plane, FP64 against the oracle."""
+    sc = scenes.cloth_scene(5, 5, n_spheres=0, seed=7, height=0.015)
+    sc["params"]["obstacles"].append(scenes.box((0.19, 0.19, 0.0), (0.08, 0.08, 0.012)))
+    H = 6
+    U = np.zeros((1, H, 6))
+    q0 = np.tile(sc["q0"], (1, 1))
+    s = _sim(sc, 8, 1, H, newton_max=300)
+    traj, qH, st = s.rollout(_t(q0, 8), _t(U, 8))
+    ref, ost, counts = osim.rollout(_oscene(sc), q0[0], U[0], "hard")
+    assert ost == 0 and int(st[0]) == 0, (ost, int(st[0]))
+    assert max(c[1] for c in counts) > 0                     # stage 2 ran
+    assert rel_state(traj[0].cpu().numpy(), ref) <= TOL64
+
+
+def test_cloth8_fp32_consistent_gradient():
+    """Smooth forward with its exact gradient (the mode finite differences can check), FP32."""
+    B, H = 3, 6
+    sc, q0, U = _cloth(8, 8, B, H, seed=23, ckpt=3)
+    s = _sim(sc, 4, B, H, grad_mode="consistent", newton_max=300)
+    Lv, dU, dq0, st = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    osc = _oscene(sc)
+    for b in range(B):
+        ref = ograd.rollout_vjp(osc, q0[b], U[b], "consistent")
+        assert ref["status"] == 0 and int(st[b]) == 0
+        assert abs(float(Lv[b]) - ref["L"]) <= TOL_STATE32 * abs(ref["L"])
+        check_grad(dU[b].cpu().numpy(), ref["dL_du"], TOL_GRAD32, COS32)
+
+
+def test_cloth_deterministic():
+    """Repeated launches give bit-identical states, losses and gradients."""
+    B, H = 4, 5
+    sc, q0, U = _cloth(6, 7, B, H, seed=29, ckpt=2)
+    s = _sim(sc, 4, B, H, newton_max=300)
+    a = [x.cpu().numpy() for x in s.rollout_vjp(_t(q0, 4), _t(U, 4))]
+    b = [x.cpu().numpy() for x in s.rollout_vjp(_t(q0, 4), _t(U, 4))]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y, equal_nan=True)
