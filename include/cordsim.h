@@ -109,8 +109,10 @@ typedef struct cs_sim cs_sim;
 /* Create a simulator for one scene.  rest_x: HOST array [n_v][3] of rest node positions (the
  * spring rest lengths are taken from it).  Allocates the handle's device workspace for
  * max_batch rollouts of up to max_horizon steps.  A rope (CS_ROPE) has 2..128 nodes; a cloth
- * (CS_CLOTH) rows x cols nodes, row-major, with cols limited by the band window in shared memory
- * (33 in FP32, 22 in FP64: the node-coupled matrices have half bandwidth 6 cols + 2).
+ * (CS_CLOTH) rows x cols nodes, row-major (its node-coupled matrices have half bandwidth
+ * 6 cols + 2): the band window sits in shared memory up to 33 columns in FP32 (22 in FP64) and in
+ * the handle's global workspace beyond; the other per-rollout arrays in shared memory limit a
+ * square cloth to about 66 x 66 in FP32 (46 x 46 in FP64).
  * Errors: CS_ERR_INVALID_ARG (bad sizes, a rope or cloth beyond those limits, unknown kind or
  * obstacle), CS_ERR_OOM, CS_ERR_CUDA. */
 cs_status sim_create(const cs_params* params, const double* rest_x, cs_sim** out);

@@ -26,6 +26,7 @@ struct ClothWS {
   R *phi;                                     // [nobs nv]
   R *pm;                                      // [nobs nv][6]
   R *Lg;                                      // [N][LDB] band factor
+  R *Wg;                                      // band window, when it is in global memory
 };
 
 // layout of one workspace slot (elements, each array padded to a multiple of 4): see cloth_ws_elems
@@ -45,6 +46,7 @@ __device__ __forceinline__ ClothWS<R> cloth_carve(R* base, const ClothDims& D, i
   w.phi = take(np);
   w.pm = take(6 * np);
   w.Lg = take(N * D.LDB);
+  w.Wg = D.win_global ? take(cloth_gwin_elems(D)) : nullptr;
   return w;
 }
 
@@ -65,6 +67,13 @@ __device__ __forceinline__ ClothSm<R> cloth_sm(const ClothDims& D) {
   c.red = c.vb + D.N + CL_KB;
   c.misc = c.red + 64;
   return c;
+}
+
+// the factorisation with the band window where this cloth keeps it
+template <typename R>
+__device__ __forceinline__ bool cl_factor_w(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M,
+                                            const ClothWS<R>& w, R* sm) {
+  return D.win_global ? cl_factor<R, true>(S, D, M, w.Lg, sm, w.Wg) : cl_factor<R, false>(S, D, M, w.Lg, sm, w.Wg);
 }
 
 template <typename R>
@@ -220,7 +229,7 @@ __device__ int cl_stage1(const Scene<R>& S, const ClothDims& D, const ClothWS<R>
       cl_diag(S, D, w, c.misc, false, t);
       for (int i = threadIdx.x; i < N; i += CL_NT) c.vb[i] = -w.F[i];
       __syncthreads();
-      ok = cl_factor(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, false}, w.Lg, c.sm);
+      ok = cl_factor_w(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, false}, w, c.sm);
       if (ok) break;
       t = fmax(R(2) * t, beta);
     }
@@ -388,7 +397,7 @@ __device__ int cl_stage2(const Scene<R>& S, const ClothDims& D, const ClothWS<R>
         for (int i = 0; i < 3; ++i) { c.vb[3 * v + i] = rhs[i]; w.rA[3 * v + i] = rhs[i]; }
       }
       __syncthreads();
-      ok = cl_factor(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, proj}, w.Lg, c.sm);
+      ok = cl_factor_w(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, proj}, w, c.sm);
       if (!ok) {
         // H2 not positive definite with the exact P: the projected spring Hessian for the rest
         // of this solve
@@ -702,7 +711,7 @@ __device__ int cl_adjoint(const Scene<R>& S, const ClothDims& D, const ClothWS<R
     for (int i = 0; i < 3; ++i) c.vb[3 * v + i] = w.xb[3 * v + i];
   }
   __syncthreads();
-  if (!cl_factor(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, false}, w.Lg, c.sm)) return ST_NOTPD;
+  if (!cl_factor_w(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, false}, w, c.sm)) return ST_NOTPD;
   cl_back(D, w.Lg, c.sm);
   for (int i = threadIdx.x; i < N; i += CL_NT) w.mu[i] = c.vb[i];
   __syncthreads();
@@ -749,7 +758,7 @@ __device__ int cl_adjoint(const Scene<R>& S, const ClothDims& D, const ClothWS<R
   // the step's Jacobian is undefined
   cl_diag(S, D, w, misc, false, R(0));
   __syncthreads();
-  if (!cl_factor(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, false}, w.Lg, c.sm)) return ST_NOTPD;
+  if (!cl_factor_w(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, false}, w, c.sm)) return ST_NOTPD;
   cl_back(D, w.Lg, c.sm);
   for (int i = threadIdx.x; i < N; i += CL_NT) w.xb[i] = S.w * c.vb[i];
   __syncthreads();

@@ -30,6 +30,8 @@ struct ClothDims {
   int PL;                // panel buffer row length
   int nspr;              // springs
   int off[7];            // first spring of each family (off[6] = nspr)
+  int win_global;        // the band window lives in the CTA's global workspace slot (too wide
+                         // for shared memory) instead of shared memory
 };
 
 __host__ __device__ inline int cl_rup(int x, int m) { return (x + m - 1) / m * m; }
@@ -58,19 +60,34 @@ __host__ __device__ inline ClothDims cloth_dims(int R, int C) {
   d.off[5] = d.off[4] + nbh;
   d.off[6] = d.off[5] + nbv;
   d.nspr = d.off[6];
+  d.win_global = 0;
   return d;
 }
 
 // shared memory of one CTA (elements of the real type): window (or the two staging panels of a
 // solve), panel buffer, right-hand side, panel partial sums, reductions, step scalars
 __host__ __device__ inline size_t cloth_win_elems(const ClothDims& d) {
-  const size_t win = (size_t)d.WC * d.LDW;
+  const size_t win = d.win_global ? 0 : (size_t)d.WC * d.LDW;
   const size_t stg = (size_t)2 * CL_KB * d.LDB;
   return ((win > stg ? win : stg) + 3) & ~(size_t)3;       // keeps the panel buffer 16-byte aligned
 }
 
+// the band window in global memory, when it is there
+__host__ __device__ inline size_t cloth_gwin_elems(const ClothDims& d) {
+  return d.win_global ? (((size_t)d.WC * d.LDW + 3) & ~(size_t)3) : 0;
+}
+
 __host__ __device__ inline size_t cloth_smem_elems(const ClothDims& d) {
   return cloth_win_elems(d) + (size_t)CL_KB * d.PL + (size_t)d.N + CL_KB + 64 + 64 + 2 * (size_t)d.N;
+}
+
+// place the band window (shared memory when it fits, else the global workspace slot); false when
+// even the rest does not fit in shared memory
+inline bool cloth_fit(ClothDims& d, size_t real_bytes, size_t smem_optin) {
+  d.win_global = 0;
+  if (cloth_smem_elems(d) * real_bytes <= smem_optin) return true;
+  d.win_global = 1;
+  return cloth_smem_elems(d) * real_bytes <= smem_optin;
 }
 
 // four consecutive elements (16-byte aligned for float)
@@ -89,12 +106,14 @@ __device__ __forceinline__ void st4<float>(float* p, const float v[4]) {
 }
 
 // elements of one CTA's workspace slot in global memory: six node vectors [N], the diagonal
-// blocks [nv][6], the contact pairs (s, z, n, g, r_z [3], phi [1], M [6] per pair) and the band
-// factor [N][LDB], each array padded to a multiple of 4 elements
+// blocks [nv][6], the contact pairs (s, z, n, g, r_z [3], phi [1], M [6] per pair), the band
+// factor [N][LDB] and, for a cloth too wide for shared memory, the band window; each array padded
+// to a multiple of 4 elements
 __host__ __device__ inline size_t cloth_ws_elems(const ClothDims& D, int nobs) {
   const size_t N = (size_t)D.N, np = (size_t)nobs * D.nv;
   auto r4 = [](size_t x) { return (x + 3) & ~(size_t)3; };
-  return 6 * r4(N) + r4(6 * (size_t)D.nv) + 5 * r4(3 * np) + r4(np) + r4(6 * np) + r4(N * D.LDB);
+  return 6 * r4(N) + r4(6 * (size_t)D.nv) + 5 * r4(3 * np) + r4(np) + r4(6 * np) + r4(N * D.LDB) +
+         cloth_gwin_elems(D);
 }
 
 // spring s -> nodes a < b and family (0, 1 structural; 2, 3 shear; 4, 5 bend)
@@ -275,9 +294,12 @@ __device__ __forceinline__ void cl_load_cols_warp(const Scene<R>& S, const Cloth
 // Cholesky factorisation L L^T of the band matrix M into Lg [N][LDB] (column c: rows c .. c+bw),
 // with the forward substitution L y = vb fused (vb in shared memory becomes y).  Returns false,
 // uniformly over the CTA, when a pivot is not positive (the matrix is not positive definite).
-template <typename R>
-__device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M, R* Lg, R* sm) {
-  R* Wn = sm;
+// GW: the band window is Wg in global memory (a cloth too wide for shared memory), else it is the
+// start of shared memory.
+template <typename R, bool GW>
+__device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M, R* Lg, R* sm,
+                                       R* Wg) {
+  R* Wn = GW ? Wg : sm;                    // the band window: global workspace or shared memory
   R* Pb = sm + cloth_win_elems(D);
   R* vb = Pb + (size_t)CL_KB * D.PL;
   R* ild = vb + D.N;                       // reciprocal pivots of the current panel [CL_KB]

@@ -98,9 +98,9 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   std::vector<double> L1, L2(1, 0.0);
   if (cloth) {
     s->cd = cs::cloth_dims(P->rows, P->cols);
-    if (cs::cloth_smem_elems(s->cd) * (size_t)P->real_bytes > s->smem_optin) {
+    if (!cs::cloth_fit(s->cd, (size_t)P->real_bytes, s->smem_optin)) {
       delete s;
-      return cs_fail(CS_ERR_INVALID_ARG, "cloth too wide for the band window in shared memory");
+      return cs_fail(CS_ERR_INVALID_ARG, "cloth too large for one CTA's shared memory");
     }
     cloth_rest_lengths(P->rows, P->cols, rest_x, L1);
     if ((int)L1.size() != s->cd.nspr) {

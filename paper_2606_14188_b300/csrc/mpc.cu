@@ -231,8 +231,9 @@ cs_status check_request(const cs_mpc* m, const cs_mpc_request* q) {
       return cs_fail(CS_ERR_INVALID_ARG, "goal node out of range");
   if (!(q->u_max > 0) || !(q->sigma >= 0) || !(q->lr >= 0)) return cs_fail(CS_ERR_INVALID_ARG, "need u_max > 0, sigma >= 0, lr >= 0");
   if (cloth) {
-    if (cs::cloth_smem_elems(cs::cloth_dims(P.rows, P.cols)) * (size_t)m->rb > m->smem_optin)
-      return cs_fail(CS_ERR_INVALID_ARG, "cloth too wide for the band window in shared memory");
+    cs::ClothDims d = cs::cloth_dims(P.rows, P.cols);
+    if (!cs::cloth_fit(d, (size_t)m->rb, m->smem_optin))
+      return cs_fail(CS_ERR_INVALID_ARG, "cloth too large for one CTA's shared memory");
     return CS_OK;
   }
   const int ppl = (P.n_nodes + 1) / 2 <= 32 ? 1 : 2;
@@ -887,6 +888,7 @@ cs_status mpc_submit(cs_mpc* m, const cs_mpc_request* req, uint64_t* ticket) {
     q->cloth = true;
     q->ppl = 3;                      // after the rope groups in the running set
     q->cd = cs::cloth_dims(req->params.rows, req->params.cols);
+    cs::cloth_fit(q->cd, (size_t)m->rb, m->smem_optin);
     l1_n = (size_t)q->cd.nspr;
   }
   q->rest.assign(req->rest_x, req->rest_x + 3 * q->nv);

@@ -248,3 +248,46 @@ def test_cloth_deterministic():
     b = [x.cpu().numpy() for x in s.rollout_vjp(_t(q0, 4), _t(U, 4))]
     for x, y in zip(a, b):
         assert np.array_equal(x, y, equal_nan=True)
+
+
+def test_cloth_band_window_in_global_memory_fp64():
+    """A 3 x 26 cloth in FP64: its band window (half bandwidth 158) does not fit in shared memory
+    and lives in the CTA's global workspace; rollout and adjoint still equal the oracle's."""
+    B, H = 1, 4
+    sc, q0, U = _cloth(3, 26, B, H, seed=31, spheres=1, ckpt=2)
+    s = _sim(sc, 8, B, H, newton_max=300)
+    traj, qH, st = s.rollout(_t(q0, 8), _t(U, 8))
+    Lv, dU, dq0, st2 = s.rollout_vjp(_t(q0, 8), _t(U, 8))
+    osc = _oscene(sc)
+    ref = ograd.rollout_vjp(osc, q0[0], U[0], "surrogate")
+    assert ref["status"] == 0 and int(st[0]) == 0 and int(st2[0]) == 0
+    assert rel_state(traj[0].cpu().numpy(), ref["traj"]) <= TOL64
+    assert abs(float(Lv[0]) - ref["L"]) <= TOL64 * abs(ref["L"])
+    check_grad(dU[0].cpu().numpy(), ref["dL_du"], TOL64, 1 - 1e-12)
+
+
+def test_cloth48_fp32_wide_runs():
+    """The widest cloth of the served stream (48 x 48, FP32, band window in global memory): one
+    step ends at a stage-1 root (force balance) with a finite gradient."""
+    sc = scenes.cloth_scene(48, 48, n_spheres=2, seed=37)
+    p = sc["params"]
+    U = scenes.controls_normal_clear(sc, 1, 1, seed=38)
+    q0 = np.tile(sc["q0"], (1, 1))
+    s = _sim(sc, 4, 1, 1, newton_max=400)
+    traj, qH, st = s.rollout(_t(q0, 4), _t(U, 4))
+    assert int(st[0]) == 0
+    traj = traj.cpu().numpy().astype(np.float64)
+    n = 3 * p["n_nodes"]
+    x, g = traj[0, 0, :n].reshape(-1, 3), traj[0, 0, n:].reshape(2, 3)
+    xs, g1 = traj[0, 1, :n].reshape(-1, 3), traj[0, 1, n:].reshape(2, 3)
+    assert _min_clearance(p, xs) > 1e-4
+    c = g - x[list(p["grasp_nodes"])]
+    d = np.where(np.linalg.norm(c, axis=1) <= p["r_grasp"], p["D_max"], 0.0)
+    x0 = x.copy()
+    for i, j in enumerate(p["grasp_nodes"]):
+        x0[j] += U[0, 0, 3 * i:3 * i + 3]
+    F1 = _force_balance(p, sc["rest_x"], x, xs, g1, d)
+    F0 = _force_balance(p, sc["rest_x"], x, x0, g1, d)
+    assert np.abs(F1).max() <= 1e-4 * np.abs(F0).max()
+    Lv, dU, _, st2 = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    assert int(st2[0]) == 0 and bool(torch.isfinite(dU).all())
