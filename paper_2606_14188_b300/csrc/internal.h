@@ -139,10 +139,10 @@ cs_status launch_cloth_vjp(cs_sim* s, int B, int H, const void* q0, const void* 
 template <typename R>
 int cloth_ctas_per_sm(const cs_sim* s);
 template <typename R>
-cs_status launch_cloth_plan(const cs::Scene<R>& S, const cs::ClothDims& D, const void* job, int Rc, void* slots,
-                            size_t slot_stride, int nslots, cudaStream_t st);
+cs_status launch_cloth_packed(const void* jobs, const int* first, int njobs, int total, void* slots,
+                              size_t slot_stride, int nslots, size_t smem, size_t scene_off, cudaStream_t st);
 template <typename R>
-cs_status cloth_plan_prepare(const cs::ClothDims& D, int* ctas_per_sm);
+cs_status cloth_packed_prepare(size_t smem, int* ctas_per_sm);
 
 // rest lengths of a cloth's springs in the cloth kernels' order (family by family: structural along
 // rows, along columns, the two shear diagonals, bend along rows, along columns)

@@ -38,27 +38,26 @@ cs_status launch_cloth_vjp(cs_sim* s, int B, int H, const void* q0, const void* 
   return check_launch("cloth_vjp_kernel");
 }
 
-// plan solves: every candidate of one request (job: its PlanJob in device memory; S: the same
-// scene, from the host copy of the job table), over at most nslots CTAs
+// plan solves: every candidate of the njobs cloth jobs (device job table `jobs`, candidate offsets
+// `first`), over at most nslots CTAs of smem bytes (scene copy at scene_off)
 template <typename R>
-cs_status launch_cloth_plan(const cs::Scene<R>& S, const cs::ClothDims& D, const void* job, int Rc, void* slots,
-                            size_t slot_stride, int nslots, cudaStream_t st) {
-  const size_t smem = cs::cloth_smem_elems(D) * sizeof(R);
-  const int grid = Rc < nslots ? Rc : nslots;
-  cs::cloth_vjp_plan_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, D, static_cast<const cs::PlanJob<R>*>(job),
-                                                             static_cast<R*>(slots), slot_stride);
-  return check_launch("cloth_vjp_plan_kernel");
+cs_status launch_cloth_packed(const void* jobs, const int* first, int njobs, int total, void* slots,
+                              size_t slot_stride, int nslots, size_t smem, size_t scene_off, cudaStream_t st) {
+  const int grid = total < nslots ? total : nslots;
+  cs::cloth_vjp_packed_kernel<R><<<grid, cs::CL_NT, smem, st>>>(static_cast<const cs::PlanJob<R>*>(jobs), first,
+                                                               njobs, total, static_cast<R*>(slots), slot_stride,
+                                                               scene_off);
+  return check_launch("cloth_vjp_packed_kernel");
 }
 
-// raise the plan kernel's shared-memory limit (not a stream operation: before a capture) and
+// raise the packed kernel's shared-memory limit (not a stream operation: before a capture) and
 // report its resident CTAs per SM
 template <typename R>
-cs_status cloth_plan_prepare(const cs::ClothDims& D, int* ctas_per_sm) {
-  const size_t smem = cs::cloth_smem_elems(D) * sizeof(R);
-  cs_status r = prep_kernel(cs::cloth_vjp_plan_kernel<R>, smem);
+cs_status cloth_packed_prepare(size_t smem, int* ctas_per_sm) {
+  cs_status r = prep_kernel(cs::cloth_vjp_packed_kernel<R>, smem);
   if (r) return r;
   int a = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cs::cloth_vjp_plan_kernel<R>, cs::CL_NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cs::cloth_vjp_packed_kernel<R>, cs::CL_NT, smem);
   *ctas_per_sm = a > 0 ? a : 1;
   return CS_OK;
 }

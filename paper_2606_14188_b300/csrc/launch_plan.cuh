@@ -17,11 +17,15 @@ struct PlanSpec {
   size_t ws_stride;
   unsigned long long seed;
   int H, Rc, G, warm_H, warm_shift;
+  int cloth_wg;
   double lr, sigma, u_max;
 };
 
 template <typename R>
-inline size_t plan_job_bytes() { return sizeof(cs::PlanJob<R>); }
+inline size_t plan_job_bytes() {
+  static_assert(sizeof(cs::PlanJob<R>) % 16 == 0, "the job table's stride must be sizeof(PlanJob)");
+  return sizeof(cs::PlanJob<R>);
+}
 
 template <typename R>
 inline void plan_fill_job(void* out, const PlanSpec& p) {
@@ -46,6 +50,7 @@ inline void plan_fill_job(void* out, const PlanSpec& p) {
   J.G = p.G;
   J.warm_H = p.warm_H;
   J.warm_shift = p.warm_shift;
+  J.cloth_wg = p.cloth_wg;
   J.lr = (R)p.lr;
   J.sigma = (R)p.sigma;
   J.u_max = (R)p.u_max;

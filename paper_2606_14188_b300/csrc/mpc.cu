@@ -194,6 +194,7 @@ struct cs_mpc {
   void* cloth_pool = nullptr;
   size_t cloth_pool_bytes = 0, cloth_stride = 0;
   int cloth_nslots = 0;
+  size_t cloth_smem = 0, cloth_scene_off = 0;   // packed cloth launch: shared memory, scene copy
 };
 
 namespace {
@@ -312,6 +313,7 @@ csi::PlanSpec make_spec(const cs_mpc* m, const Req& q) {
   p.G = q.r.G;
   p.warm_H = q.warm_H;
   p.warm_shift = q.warm_shift;
+  p.cloth_wg = q.cloth ? q.cd.win_global : 0;
   p.lr = q.r.lr;
   p.sigma = q.r.sigma;
   p.u_max = q.r.u_max;
@@ -325,9 +327,11 @@ struct Group {
   int j0 = 0, n = 0, total = 0, nobs = 0, H = 0;
 };
 
+// offset of the cloth group's candidate offsets in the first[] table (after the two rope groups)
+inline int cloth_first_base(const Group g[3]) { return g[1].n + 1 + g[2].n + 1; }
+
 template <typename R>
-cs_status enqueue_tick(cs_mpc* m, const Group g[3], const std::vector<int>& cloth_jobs, int njobs, int max_elems,
-                       bool count) {
+cs_status enqueue_tick(cs_mpc* m, const Group g[3], const Group& cg, int njobs, int max_elems, bool count) {
   cs_status r;
   for (int ppl = 1; ppl <= 2; ++ppl) {
     const Group& G = g[ppl];
@@ -341,11 +345,11 @@ cs_status enqueue_tick(cs_mpc* m, const Group g[3], const std::vector<int>& clot
     if (r) return r;
     if (count) ++m->kernel_launches;
   }
-  // cloth requests: one launch each over its candidates (scene from the host job table)
-  for (int j : cloth_jobs) {
-    const auto* hj = reinterpret_cast<const cs::PlanJob<R>*>(m->h_jobs + (size_t)j * m->job_bytes);
-    r = csi::launch_cloth_plan<R>(hj->S, m->running[j]->cd, m->d_jobs + (size_t)j * m->job_bytes, hj->Rc,
-                                  m->cloth_pool, m->cloth_stride, m->cloth_nslots, m->stream);
+  // cloth requests: one packed launch over the candidates of all of them
+  if (cg.n) {
+    r = csi::launch_cloth_packed<R>(m->d_jobs + (size_t)cg.j0 * m->job_bytes, m->d_first + cloth_first_base(g), cg.n,
+                                    cg.total, m->cloth_pool, m->cloth_stride, m->cloth_nslots, m->cloth_smem,
+                                    m->cloth_scene_off, m->stream);
     if (r) return r;
     if (count) ++m->kernel_launches;
   }
@@ -368,20 +372,23 @@ cs_status prepare_groups(cs_mpc* m, const Group g[3]) {
   return CS_OK;
 }
 
-// the cloth plan kernel's shared-memory limit (the widest running cloth) and a workspace pool of
-// one slot per resident CTA, grown (after the stream drains) when a wider cloth joins
+// the packed cloth kernel's shared memory (the widest running cloth's layout, then the scene copy)
+// and a workspace pool of one slot per resident CTA, grown (after the stream drains) when a wider
+// cloth joins
 template <typename R>
-cs_status prepare_cloth(cs_mpc* m, const std::vector<int>& cloth_jobs) {
-  if (cloth_jobs.empty()) return CS_OK;
-  const Req* widest = nullptr;
-  size_t stride = 0;
-  for (int j : cloth_jobs) {
+cs_status prepare_cloth(cs_mpc* m, const Group& cg) {
+  if (!cg.n) return CS_OK;
+  size_t lay = 0, stride = 0;
+  for (int j = cg.j0; j < cg.j0 + cg.n; ++j) {
     const Req& q = *m->running[j];
-    if (!widest || cs::cloth_smem_elems(q.cd) > cs::cloth_smem_elems(widest->cd)) widest = &q;
+    lay = std::max(lay, cs::cloth_smem_elems(q.cd) * sizeof(R));
     stride = std::max(stride, cs::cloth_ws_elems(q.cd, q.r.params.n_obstacles));
   }
+  const size_t scene_off = (lay + 15) & ~(size_t)15;
+  const size_t smem = scene_off + cs::plan_scene_bytes<R>();
+  if (smem > m->smem_optin) return cs_fail(CS_ERR_INVALID_ARG, "cloth too large for the packed launch");
   int per_sm = 1;
-  cs_status r = csi::cloth_plan_prepare<R>(widest->cd, &per_sm);
+  cs_status r = csi::cloth_packed_prepare<R>(smem, &per_sm);
   if (r) return r;
   const int nslots = per_sm * m->sms;
   const size_t bytes = stride * (size_t)nslots * sizeof(R);
@@ -397,6 +404,8 @@ cs_status prepare_cloth(cs_mpc* m, const std::vector<int>& cloth_jobs) {
   }
   m->cloth_stride = stride;
   m->cloth_nslots = nslots;
+  m->cloth_smem = smem;
+  m->cloth_scene_off = scene_off;
   return CS_OK;
 }
 
@@ -423,11 +432,13 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
     if (e != cudaSuccess) return cuda_err(e, "cudaStreamSynchronize");
   }
   int first1 = 0, first2 = 0;
-  std::vector<int> cloth_jobs;
+  Group cg;                              // cloth requests (last in the sorted running set)
   for (int j = 0; j < n; ++j) {
     const Req& q = *run[j];
     if (q.cloth) {
-      cloth_jobs.push_back(j);
+      if (!cg.n) cg.j0 = j;
+      ++cg.n;
+      cg.total += q.r.R;
       max_elems = std::max(max_elems, q.r.R * q.r.H * 6);
       if (changed) csi::plan_fill_job<R>(m->h_jobs + (size_t)j * m->job_bytes, make_spec(m, q));
       continue;
@@ -449,10 +460,17 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
   if (changed) {
     m->h_first[g[1].n] = first1;
     m->h_first[g[1].n + 1 + g[2].n] = first2;
+    const int cb = cloth_first_base(g);
+    int first3 = 0;
+    for (int k = 0; k < cg.n; ++k) {
+      m->h_first[cb + k] = first3;
+      first3 += run[cg.j0 + k]->r.R;
+    }
+    m->h_first[cb + cg.n] = first3;
     cudaError_t e = cudaMemcpyAsync(m->d_jobs, m->h_jobs, (size_t)n * m->job_bytes, cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(m->d_first, m->h_first, sizeof(int) * (size_t)(g[1].n + g[2].n + 2),
-                          cudaMemcpyHostToDevice, m->stream);
+      e = cudaMemcpyAsync(m->d_first, m->h_first, sizeof(int) * (size_t)(cb + cg.n + 1), cudaMemcpyHostToDevice,
+                          m->stream);
     if (e != cudaSuccess) return cuda_err(e, "cudaMemcpyAsync");
     for (const auto& q : admitted) {
       int j = 0;
@@ -461,7 +479,7 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
       ++m->kernel_launches;
     }
     if ((r = prepare_groups<R>(m, g))) return r;
-    if ((r = prepare_cloth<R>(m, cloth_jobs))) return r;
+    if ((r = prepare_cloth<R>(m, cg))) return r;
     m->graph_valid = false;
   }
   // at most two ticks in flight
@@ -475,7 +493,7 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
       cudaGraph_t graph = nullptr;
       e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_err(e, "cudaStreamBeginCapture");
-      r = enqueue_tick<R>(m, g, cloth_jobs, n, max_elems, false);
+      r = enqueue_tick<R>(m, g, cg, n, max_elems, false);
       e = cudaStreamEndCapture(m->stream, &graph);
       if (r) return r;
       if (e != cudaSuccess) return cuda_err(e, "cudaStreamEndCapture");
@@ -488,9 +506,9 @@ cs_status run_tick(cs_mpc* m, const std::vector<std::shared_ptr<Req>>& admitted,
     e = cudaGraphLaunch(m->gexec, m->stream);
     if (e != cudaSuccess) return cuda_err(e, "cudaGraphLaunch");
     ++m->graph_launches;
-    m->kernel_launches += (g[1].n ? 1 : 0) + (g[2].n ? 1 : 0) + (int64_t)cloth_jobs.size() + 2;
+    m->kernel_launches += (g[1].n ? 1 : 0) + (g[2].n ? 1 : 0) + (cg.n ? 1 : 0) + 2;
   } else {
-    if ((r = enqueue_tick<R>(m, g, cloth_jobs, n, max_elems, true))) return r;
+    if ((r = enqueue_tick<R>(m, g, cg, n, max_elems, true))) return r;
   }
   e = cudaEventRecord(ev, m->stream);
   if (e != cudaSuccess) return cuda_err(e, "cudaEventRecord");
@@ -854,10 +872,10 @@ cs_status mpc_create(const cs_mpc_config* cfg, cs_mpc** out) {
   m->session_bytes = (size_t)16 << 20;
   if ((e = cudaMalloc(&m->session_dev, m->session_bytes)) != cudaSuccess) return fail(e, "session plans");
   if ((e = cudaMalloc(&m->d_jobs, m->job_bytes * m->max_slots)) != cudaSuccess) return fail(e, "job table");
-  if ((e = cudaMalloc(&m->d_first, sizeof(int) * (m->max_slots + 2))) != cudaSuccess) return fail(e, "job table");
+  if ((e = cudaMalloc(&m->d_first, sizeof(int) * (m->max_slots + 3))) != cudaSuccess) return fail(e, "job table");
   if ((e = cudaHostAlloc(&m->pinned, m->pinned_bytes, cudaHostAllocDefault)) != cudaSuccess) return fail(e, "pinned staging");
   if ((e = cudaHostAlloc(&m->h_jobs, m->job_bytes * m->max_slots, cudaHostAllocDefault)) != cudaSuccess) return fail(e, "pinned job table");
-  if ((e = cudaHostAlloc(&m->h_first, sizeof(int) * (m->max_slots + 2), cudaHostAllocDefault)) != cudaSuccess) return fail(e, "pinned job table");
+  if ((e = cudaHostAlloc(&m->h_first, sizeof(int) * (m->max_slots + 3), cudaHostAllocDefault)) != cudaSuccess) return fail(e, "pinned job table");
   m->arena.init(m->arena_bytes);
   m->pinned_arena.init(m->pinned_bytes);
   m->session_arena.init(m->session_bytes);

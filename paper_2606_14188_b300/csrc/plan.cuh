@@ -23,9 +23,10 @@ struct PlanState {
   int n_ok;        // candidates that succeeded at the last evaluation
 };
 
-// one request as the kernels see it (an array of these lives in device memory)
+// one request as the kernels see it (an array of these lives in device memory; 16-byte aligned so
+// that the array's stride, sizeof(PlanJob), is also the host table's stride)
 template <typename R>
-struct PlanJob {
+struct alignas(16) PlanJob {
   Scene<R> S;            // scene and planning loss; S.L1/S.L2 point at the request's rest lengths
   const R* q0;           // [n_q]
   const R* warm;         // [warm_H][6] or null (zeros)
@@ -41,6 +42,7 @@ struct PlanJob {
   size_t ws_stride;
   unsigned long long seed;
   int H, Rc, G, warm_H, warm_shift;
+  int cloth_wg;          // cloth: its band window lives in global memory (too wide for shared)
   R lr, sigma, u_max;
 };
 
