@@ -324,12 +324,24 @@ def cloth_leg(args, flush, stream, world, cpu):
                 cpu_baseline=cpu)
 
 
-def served_stream(n, seed):
+def served_stream(n, seed, cloth_frac=0.0):
     """The served workload: n plan solves with rope sizes U{16..128}, horizons U{20..60}, candidates
-    log-uniform in {64, ..., 1024}, 10 evaluations each, Poisson arrival order (times set later)."""
+    log-uniform in {64, ..., 1024}, 10 evaluations each, Poisson arrival order (times set later).
+    With cloth_frac > 0 that fraction of the requests are cloths of side U{8..16}, horizon
+    U{10..20}, candidates log-uniform in {32, 64, 128}."""
     rng = np.random.default_rng(seed)
+    crng = np.random.default_rng(seed + 17)
     reqs = []
     for i in range(n):
+        if cloth_frac > 0 and crng.random() < cloth_frac:
+            side = int(crng.integers(8, 17))
+            H = int(crng.integers(10, 21))
+            R = int(2 ** crng.integers(5, 8))
+            sc = scenes.cloth_scene(side, side, n_spheres=2, seed=seed + 1 + i)
+            sc["params"]["checkpoint_every"] = max(1, int(round(H ** 0.5)))
+            reqs.append(dict(scene=sc, q0=sc["q0"], H=H, R=R, G=10, seed=seed + 7919 * i, nv=side * side,
+                             kw=dict(newton_max=300)))
+            continue
         nv = int(rng.integers(16, 129))
         H = int(rng.integers(20, 61))
         R = int(2 ** rng.integers(6, 11))
@@ -356,7 +368,7 @@ def serve_stream(reqs, gaps, batched):
                 if now >= due:
                     break
                 time.sleep(min(due - now, 0.002))
-            tickets.append(srv.submit(r["scene"], r["q0"], r["H"], r["R"], r["G"], seed=r["seed"]))
+            tickets.append(srv.submit(r["scene"], r["q0"], r["H"], r["R"], r["G"], seed=r["seed"], **r.get("kw", {})))
         out = [srv.poll(t, -1) for t in tickets]
         makespan = (max(o["t_done_ns"] for o in out) - min(o["t_submit_ns"] for o in out)) * 1e-9
         stats = srv.stats()
@@ -370,13 +382,17 @@ def served_leg(args):
     same stream arriving as a Poisson process at 70 % and 95 % of that capacity, served batched and
     one request at a time (one launch per kernel per evaluation, no graphs)."""
     n = args.served_requests
-    reqs = served_stream(n, BASE_SERVED_SEED)
+    reqs = served_stream(n, BASE_SERVED_SEED, args.served_cloth_fraction)
+    ncloth = sum(1 for r in reqs if "kw" in r)
     node_steps = sum(r["R"] * r["H"] * r["nv"] * r["G"] for r in reqs)
     out_cap, t_cap, _ = serve_stream(reqs, [0.0] * n, True)
     cap = n / t_cap
     rng = np.random.default_rng(BASE_SERVED_SEED + 1)
-    res = dict(workload=f"{n} rope plan solves, nodes U{{16..128}}, horizon U{{20..60}}, "
-                        "candidates log-U{64..1024}, 10 evaluations each, FP32",
+    what = f"{n} plan solves: {n - ncloth} ropes (nodes U{{16..128}}, horizon U{{20..60}}, candidates " \
+           f"log-U{{64..1024}})"
+    if ncloth:
+        what += f", {ncloth} cloths (side U{{8..16}}, horizon U{{10..20}}, candidates log-U{{32..128}})"
+    res = dict(workload=what + ", 10 evaluations each, FP32",
                requests=n, node_steps=node_steps, capacity_solves_per_s=cap,
                capacity_node_steps_per_s=node_steps / t_cap)
 
@@ -562,6 +578,8 @@ def main():
     ap.add_argument("--cloth-rollouts", type=int, default=None,
                     help="rollouts of the cloth leg's sample (default: one per SM)")
     ap.add_argument("--cloth-steps", type=int, default=1, help="timed calls of the cloth leg")
+    ap.add_argument("--served-cloth-fraction", type=float, default=0.0,
+                    help="fraction of the served requests that are cloths (default 0: ropes only)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
