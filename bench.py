@@ -82,16 +82,30 @@ def counts_mean(res):
 KERNEL_SOURCES = {
     "rope": ["common.cuh", "cr.cuh", "rope.cuh", "launch_rope.cuh", "rope_vjp_f32.cu",
              "rope_rollout_f32.cu", "rope_linearize_f32.cu"],
-    "cloth": ["common.cuh", "rope.cuh", "cloth_band.cuh", "cloth.cuh", "launch_cloth.cuh", "cloth_f32.cu"],
+    # the cloth VJP kernel's device code and its own launcher (the packed serving kernel, built
+    # from the same headers, has a launcher of its own in the same file)
+    "cloth": ["common.cuh", "rope.cuh", "cloth_band.cuh", "cloth.cuh", ("launch_cloth.cuh", "launch_cloth_vjp")],
 }
+
+
+def _source_lines(entry):
+    """a whole file, or (file, function): that function's definition, from the line naming it to
+    the first closing brace in column 0"""
+    name, fn = (entry, None) if isinstance(entry, str) else entry
+    lines = open(os.path.join(ROOT, "paper_2606_14188_b300", "csrc", name)).read().splitlines()
+    if fn is None:
+        return lines
+    start = next(i for i, l in enumerate(lines) if f" {fn}(" in l and not l.lstrip().startswith("//"))
+    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
+    return lines[start:end + 1]
 
 
 def kernel_source_hash(kernel: str):
     """hash of the kernel family's sources with // comments and blank lines removed (editing a
     comment does not invalidate a measured figure)"""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES["cloth" if kernel.startswith("cloth") else "rope"]:
-        for line in open(os.path.join(ROOT, "paper_2606_14188_b300", "csrc", f)).read().splitlines():
+    for entry in KERNEL_SOURCES["cloth" if kernel.startswith("cloth") else "rope"]:
+        for line in _source_lines(entry):
             code = line.split("//", 1)[0].rstrip()
             if code:
                 h.update(code.encode() + b"\n")
