@@ -130,11 +130,10 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
     return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "rest lengths") : cs_cuda_fail(e, "upload");
   }
   const int k = P->checkpoint_every;
-  const int nseg = (P->max_horizon + k - 1) / k;
-  // checkpoint records: state, grasp offsets, stage-1 offset and stage-2 displacement of the
-  // producing step
-  s->ws_stride = (size_t)(nseg + 1 + k) * cs::rec_len(nv);
-  e = cudaMalloc(&s->d_ws, s->ws_stride * (size_t)P->max_batch * rb);
+  // checkpoint records (state, grasp offsets, stage-1 offset and stage-2 displacement of the
+  // producing step) and the carry of the two-part launch
+  s->ws_stride = cs::vjp_ws_elems(nv, P->max_horizon, k);
+  e = cudaMalloc(&s->d_ws, vjp_ws_bytes(s->ws_stride, P->max_batch, rb));
   if (e != cudaSuccess) {
     sim_destroy(s);
     return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "adjoint workspace") : cs_cuda_fail(e, "cudaMalloc");

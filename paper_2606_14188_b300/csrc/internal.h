@@ -22,7 +22,8 @@ struct cs_sim {
   int real_bytes;
   void* d_L1 = nullptr;   // rest lengths (stretch)
   void* d_L2 = nullptr;   // rest lengths (bend)
-  void* d_ws = nullptr;   // adjoint workspace: checkpoints + segment states per rollout
+  void* d_ws = nullptr;   // adjoint workspace: ws_stride elements per rollout (checkpoint and
+                          // segment records, carry), then the cost and order arrays (vjp_ord_offset)
   size_t ws_stride = 0;   // elements per rollout
   int sms = 0;
   size_t smem_optin = 0;
@@ -110,6 +111,15 @@ cs_status prep_kernel(Kern k, size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cs_cuda_fail(e, "cudaFuncSetAttribute");
   return CS_OK;
+}
+
+// the adjoint workspace: max_batch blocks of ws_stride elements, then (256-byte aligned) the
+// int32 cost [max_batch] and order [max_batch] arrays of the two-part launch
+inline size_t vjp_ord_offset(size_t ws_stride, int max_batch, size_t rb) {
+  return (ws_stride * (size_t)max_batch * rb + 255) & ~(size_t)255;
+}
+inline size_t vjp_ws_bytes(size_t ws_stride, int max_batch, size_t rb) {
+  return vjp_ord_offset(ws_stride, max_batch, rb) + 2 * sizeof(int32_t) * (size_t)max_batch;
 }
 
 inline cs_status check_launch(const char* what) {

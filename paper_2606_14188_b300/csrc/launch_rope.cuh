@@ -39,6 +39,28 @@ cs_status vjp_ppl(cs_sim* s, int B, int H, const void* q0, const void* u, const 
   const size_t smem = smem_bytes(s, H, false);
   cs_status r = launch_prep(cs::rope_vjp_kernel<R, PPL>, smem, s);
   if (r) return r;
+  // More rollouts than the device holds at once: the late starters decide when the launch ends,
+  // so the forward parts run first (each measuring its cost), then the backward parts, costliest
+  // first, leaving the cheap ones to start late.
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cs::rope_vjp_kernel<R, PPL>, 32, smem);
+  if ((long long)per_sm * s->sms < B && B <= cs::CS_ORDER_MAX) {
+    if ((r = launch_prep(cs::rope_vjp_fwd_kernel<R, PPL>, smem, s))) return r;
+    if ((r = launch_prep(cs::rope_vjp_bwd_kernel<R, PPL>, smem, s))) return r;
+    int32_t* cost = reinterpret_cast<int32_t*>(static_cast<char*>(s->d_ws) +
+                                               vjp_ord_offset(s->ws_stride, s->P.max_batch, s->real_bytes));
+    int32_t* order = cost + B;
+    cs::rope_vjp_fwd_kernel<R, PPL><<<B, 32, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
+                                                          (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
+                                                          status, (R*)s->d_ws, s->ws_stride, cost);
+    if ((r = check_launch("rope_vjp_fwd_kernel"))) return r;
+    cs::rope_order_kernel<cs::CS_ORDER_NT><<<1, cs::CS_ORDER_NT, 0, st>>>(cost, B, order);
+    if ((r = check_launch("rope_order_kernel"))) return r;
+    cs::rope_vjp_bwd_kernel<R, PPL><<<B, 32, smem, st>>>(S, B, H, (const R*)u, (const R*)dLdtraj, (R*)L,
+                                                          (R*)dLdu, (R*)dLdq0, status, (R*)s->d_ws,
+                                                          s->ws_stride, cost, order);
+    return check_launch("rope_vjp_bwd_kernel");
+  }
   cs::rope_vjp_kernel<R, PPL><<<B, 32, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
                                                     (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
                                                     status, (R*)s->d_ws, s->ws_stride);

@@ -18,7 +18,8 @@
 
 namespace {
 
-// scratch layout: [L1 rest lengths | L2 rest lengths | checkpoint records], 256-byte aligned parts
+// scratch layout: [L1 rest lengths | L2 rest lengths | adjoint workspace (checkpoint records and
+// carry per rollout, then the cost and order arrays)], 256-byte aligned parts
 constexpr size_t kRestBytes = 256 * sizeof(double);   // room for 128 nodes of either real type
 static __device__ __align__(256) unsigned char g_noalloc_scratch[CS_NOALLOC_SCRATCH_BYTES];
 
@@ -90,9 +91,8 @@ extern "C" cs_status sim_rollout_vjp_noalloc(const cs_params* P, const double* r
   s.nq = 3 * nv + 6;
   s.real_bytes = P->real_bytes;
   const int k = P->checkpoint_every;
-  const int nseg = (H + k - 1) / k;
-  s.ws_stride = (size_t)(nseg + 1 + k) * cs::rec_len(nv);
-  const size_t need = 2 * kRestBytes + s.ws_stride * (size_t)B * (size_t)s.real_bytes;
+  s.ws_stride = cs::vjp_ws_elems(nv, H, k);
+  const size_t need = 2 * kRestBytes + csi::vjp_ws_bytes(s.ws_stride, B, (size_t)s.real_bytes);
   if (need > CS_NOALLOC_SCRATCH_BYTES)
     return cs_fail(CS_ERR_INVALID_ARG,
                    "B x horizon exceed the allocation-free scratch (CS_NOALLOC_SCRATCH_BYTES)");

@@ -1248,16 +1248,33 @@ __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int
   }
 }
 
+// The parts of vjp_rollout a launch runs: both (one kernel), or the forward steps and the
+// backward segments as two kernels with the rollouts of the second ordered by the cost the first
+// measured (longest first).
+enum { VJP_FWD = 1, VJP_BWD = 2, VJP_ALL = 3 };
+
+// what the forward part hands to the backward part, per rollout, after its records: the adjoint
+// seeds of q_H [6][32 PPL] (lane-major) and of the grippers [6]
+__host__ __device__ constexpr int vjp_carry_elems(int PPL) { return 6 * 32 * PPL + 8; }
+
+// elements of one rollout's adjoint workspace: checkpoint records, segment records, carry
+__host__ __device__ inline size_t vjp_ws_elems(int nv, int H, int k) {
+  const int nseg = (H + k - 1) / k;
+  return ((size_t)(nseg + 1 + k) * rec_len(nv) + 3) / 4 * 4 + vjp_carry_elems(2);
+}
+
 // Forward rollout + checkpointed adjoint of one rollout by one warp.  Pointers are this
 // rollout's: q0 [n_q], U [H][6], dLdtraj [H+1][n_q] (or null), Lout (or null), dLdu [H][6],
-// dLdq0 [n_q] (or null), status (or null), ck: its workspace of checkpoint records.
+// dLdq0 [n_q] (or null), status (or null), ck: its workspace (records, then the carry).
 // The steps run through one loop over a schedule -- the H forward steps, then for each segment
 // (last to first) the recomputed steps and the backward steps -- so that the step and its
-// adjoint are each inlined once.
-template <typename R, int PPL>
+// adjoint are each inlined once.  PH = VJP_FWD stops after the forward steps: L and the carry are
+// written, and *cost gets the forward's Newton and interior-point work (-1: the rollout failed and
+// its outputs are final).  PH = VJP_BWD resumes from the carry at the last segment.
+template <typename R, int PPL, int PH = VJP_ALL>
 __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R, PPL>& L, int lane, int H,
                                             const R* q0, const R* U, const R* dLdtraj, R* Lout, R* dLdu,
-                                            R* dLdq0, int32_t* status, R* ck) {
+                                            R* dLdq0, int32_t* status, R* ck, int32_t* cost = nullptr) {
   const int nq = 3 * S.nv + 6;
   const int rl = rec_len(S.nv);
   const int k = S.ckpt;
@@ -1265,17 +1282,40 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
   const bool fwd_smooth = S.grad_mode == CS_CONSISTENT;
   enum { FWD = 0, RECOMP = 1, BACK = 2 };
   R* seg = ck + (size_t)(nseg + 1) * rl;     // segment records [k][rl]
-  load_q(S, L, w, q0, lane);
-  zero6<R, PPL>(L.Dl);
-  load_controls(w.u, U, 6 * H, lane);
-  __syncwarp();
-  store_rec(S, L, w, ck, lane);
+  R* carry = ck + (vjp_ws_elems(S.nv, H, k) - vjp_carry_elems(2));
   int st = 0;
   R Lacc = R(0);
   R xb[PPL][6];
   zero6<R, PPL>(xb);
+  int work = 0;
   // schedule state
   int kind = FWD, t = 0, sgi = nseg - 1, t0 = 0, t1 = 0;
+  // the first step of the segment sgi: its start state from the checkpoint, recomputed steps
+  // (if it has more than one) then its backward steps
+  auto begin_segment = [&]() {
+    t0 = sgi * k;
+    t1 = min(t0 + k, H);
+    load_rec(S, L, w, ck + (size_t)sgi * rl, lane);
+    load_rec_delta(S, L, ck + (size_t)sgi * rl, lane);
+    store_rec(S, L, w, seg, lane);
+    if (t1 - t0 > 1) { kind = RECOMP; t = t0; } else { kind = BACK; t = t0; }
+  };
+  if constexpr ((PH & VJP_FWD) != 0) {
+    load_q(S, L, w, q0, lane);
+    zero6<R, PPL>(L.Dl);
+    load_controls(w.u, U, 6 * H, lane);
+    __syncwarp();
+    store_rec(S, L, w, ck, lane);
+  } else {
+    load_controls(w.u, U, 6 * H, lane);
+#pragma unroll
+    for (int kk = 0; kk < PPL; ++kk)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) xb[kk][e] = carry[(kk * 6 + e) * 32 + lane];
+    if (lane < 6) w.misc[M_GB + lane] = carry[6 * 32 * PPL + lane];
+    __syncwarp();
+    begin_segment();
+  }
   while (true) {
     if (kind == BACK) {
       load_rec(S, L, w, seg + (size_t)(t - t0) * rl, lane);
@@ -1293,6 +1333,7 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
     const bool w2 = kind == BACK || any_delta(L);
     st |= sim_step(S, L, w, lane, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK, w2);
     if (st) break;                 // a failed step: the rollout's loss and gradient are undefined
+    if (kind == FWD) work = min(work + 2 * ni + 5 * ii, 1 << 30);
     if (kind != BACK) {
       advance_state(S, L, w, lane);
       if (kind == FWD) {
@@ -1353,22 +1394,36 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
     // next schedule entry
     bool start_seg = false;
     if (kind == FWD) {
-      if (++t == H) start_seg = true;
+      if (++t == H) {
+        if constexpr (PH == VJP_FWD) break;
+        start_seg = true;
+      }
     } else if (kind == RECOMP) {
       if (++t == t1 - 1) { kind = BACK; t = t1 - 1; }
     } else {
       if (--t < t0) { if (--sgi < 0) break; start_seg = true; }
     }
-    if (start_seg) {
-      t0 = sgi * k;
-      t1 = min(t0 + k, H);
-      load_rec(S, L, w, ck + (size_t)sgi * rl, lane);
-      load_rec_delta(S, L, ck + (size_t)sgi * rl, lane);
-      store_rec(S, L, w, seg, lane);
-      if (t1 - t0 > 1) { kind = RECOMP; t = t0; } else { kind = BACK; t = t0; }
-    }
+    if (start_seg) begin_segment();
   }
   __syncwarp();
+  if constexpr (PH == VJP_FWD) {
+    if (!st) {                     // hand the seeds over; L is final
+#pragma unroll
+      for (int kk = 0; kk < PPL; ++kk)
+#pragma unroll
+        for (int e = 0; e < 6; ++e) carry[(kk * 6 + e) * 32 + lane] = xb[kk][e];
+      if (lane < 6) carry[6 * 32 * PPL + lane] = w.misc[M_GB + lane];
+      Lacc = wsum(Lacc);
+      if (lane == 0) {
+        if (Lout) *Lout = Lacc;
+        if (status) *status = 0;
+        *cost = work;
+      }
+      __syncwarp();
+      return;
+    }
+    if (lane == 0) *cost = -1;
+  }
   if (st) {                        // failed rollout: L = NaN, gradients zero
     for (int i = lane; i < 6 * H; i += 32) w.ub[i] = R(0);
     zero6<R, PPL>(xb);
@@ -1389,27 +1444,94 @@ __device__ __forceinline__ void vjp_rollout(const Scene<R>& S, WS<R>& w, Lane<R,
   }
   Lacc = wsum(Lacc);
   if (lane == 0) {
-    if (Lout) *Lout = Lacc;
+    // the backward part leaves the forward's L unless the rollout failed
+    if (Lout && (PH != VJP_BWD || st)) *Lout = Lacc;
     if (status) *status = st;
   }
   __syncwarp();
 }
 
-template <typename R, int PPL>
-__global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, const R* q0,
-                                                     const R* U, const R* dLdtraj, R* Lout, R* dLdu,
-                                                     R* dLdq0, int32_t* status, R* ws, size_t ws_stride) {
+// the rollouts i = blockIdx.x, blockIdx.x + gridDim.x, ... (through order[i] when given); the
+// backward part skips a rollout whose forward failed (cost -1: its outputs are written)
+template <typename R, int PPL, int PH>
+__device__ __forceinline__ void vjp_rollouts(const Scene<R>& S, int B, int H, const R* q0, const R* U,
+                                             const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0, int32_t* status,
+                                             R* ws, size_t ws_stride, int32_t* cost, const int32_t* order) {
   const int lane = threadIdx.x;
   const int nq = 3 * S.nv + 6;
   WS<R> w = ws_carve<R>(reinterpret_cast<R*>(cs_smem), 32 * PPL, S.nobs, H, false);
   Lane<R, PPL> L;
   zero_lane(L);
   load_rest(S, L, lane);
-  for (int b = blockIdx.x; b < B; b += gridDim.x)
-    vjp_rollout<R, PPL>(S, w, L, lane, H, q0 + (size_t)b * nq, U + (size_t)b * H * 6,
-                        dLdtraj ? dLdtraj + (size_t)b * (H + 1) * nq : nullptr, Lout ? Lout + b : nullptr,
-                        dLdu + (size_t)b * H * 6, dLdq0 ? dLdq0 + (size_t)b * nq : nullptr,
-                        status ? status + b : nullptr, ws + (size_t)b * ws_stride);
+  for (int i = blockIdx.x; i < B; i += gridDim.x) {
+    const int b = order ? order[i] : i;
+    if (PH == VJP_BWD && cost[b] < 0) continue;
+    vjp_rollout<R, PPL, PH>(S, w, L, lane, H, q0 + (size_t)b * nq, U + (size_t)b * H * 6,
+                            dLdtraj ? dLdtraj + (size_t)b * (H + 1) * nq : nullptr, Lout ? Lout + b : nullptr,
+                            dLdu + (size_t)b * H * 6, dLdq0 ? dLdq0 + (size_t)b * nq : nullptr,
+                            status ? status + b : nullptr, ws + (size_t)b * ws_stride, cost ? cost + b : nullptr);
+  }
+}
+
+// forward + adjoint in one launch
+template <typename R, int PPL>
+__global__ void __launch_bounds__(32) rope_vjp_kernel(Scene<R> S, int B, int H, const R* q0,
+                                                     const R* U, const R* dLdtraj, R* Lout, R* dLdu,
+                                                     R* dLdq0, int32_t* status, R* ws, size_t ws_stride) {
+  vjp_rollouts<R, PPL, VJP_ALL>(S, B, H, q0, U, dLdtraj, Lout, dLdu, dLdq0, status, ws, ws_stride, nullptr,
+                                nullptr);
+}
+
+// the forward part of every rollout: records, L, the carry and the cost of each
+template <typename R, int PPL>
+__global__ void __launch_bounds__(32) rope_vjp_fwd_kernel(Scene<R> S, int B, int H, const R* q0,
+                                                         const R* U, const R* dLdtraj, R* Lout, R* dLdu,
+                                                         R* dLdq0, int32_t* status, R* ws, size_t ws_stride,
+                                                         int32_t* cost) {
+  vjp_rollouts<R, PPL, VJP_FWD>(S, B, H, q0, U, dLdtraj, Lout, dLdu, dLdq0, status, ws, ws_stride, cost,
+                                nullptr);
+}
+
+// the backward part, rollout order[i] in CTA i (the block scheduler starts CTAs in index order,
+// so the costliest start first)
+template <typename R, int PPL>
+__global__ void __launch_bounds__(32) rope_vjp_bwd_kernel(Scene<R> S, int B, int H, const R* U,
+                                                         const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
+                                                         int32_t* status, R* ws, size_t ws_stride,
+                                                         int32_t* cost, const int32_t* order) {
+  vjp_rollouts<R, PPL, VJP_BWD>(S, B, H, nullptr, U, dLdtraj, Lout, dLdu, dLdq0, status, ws, ws_stride, cost,
+                                order);
+}
+
+// order[0..B) = the rollouts by decreasing cost, equal costs by increasing index (a bitonic sort
+// of (cost, index) keys in shared memory by one CTA; B <= CS_ORDER_MAX)
+constexpr int CS_ORDER_MAX = 4096;
+constexpr int CS_ORDER_NT = 1024;
+
+template <int NT>
+__global__ void __launch_bounds__(NT) rope_order_kernel(const int32_t* cost, int B, int32_t* order) {
+  __shared__ unsigned long long key[CS_ORDER_MAX];
+  int n = 1;
+  while (n < B) n <<= 1;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const long long c = i < B ? (long long)cost[i] : 0;
+    // 0x7fffffff - cost in the high word: the costliest first; a failed rollout (-1) last but one
+    // ahead of the padding
+    key[i] = i < B ? ((unsigned long long)(0x7fffffffLL - c) << 32) | (unsigned)i : ~0ull;
+  }
+  for (int size = 2; size <= n; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += NT) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const unsigned long long a = key[i], b = key[j];
+          if ((a > b) == ((i & size) == 0)) { key[i] = b; key[j] = a; }
+        }
+      }
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < B; i += NT) order[i] = (int32_t)(key[i] & 0xffffffffull);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -141,6 +141,22 @@ def test_rope64_full_batch_sampled():
             check_grad(dU[b].cpu().numpy(), ref["dL_du"], TOL_GRAD32, COS32)
 
 
+def test_rope64_two_part_launch_equals_one_launch():
+    """1024 rollouts are more than the device holds at once, so the call runs the forward parts,
+    orders the rollouts by their measured cost and runs the backward parts costliest first; 128
+    of them (fewer than the device holds) run as one launch.  Each rollout's outputs must be
+    bit-identical."""
+    w = scenes.workload(2)
+    sc = w["scene"]
+    B, H = w["B"], w["H"]
+    idx = np.r_[0:64, B - 64:B]
+    big = _sim(sc, 4, B, H).rollout_vjp(_t(w["q0"], 4), _t(w["U"], 4))
+    small = _sim(sc, 4, len(idx), H).rollout_vjp(_t(w["q0"][idx], 4), _t(w["U"][idx], 4))
+    for a, b in zip(big, small):
+        a = a[torch.as_tensor(idx, device=a.device)]
+        assert torch.equal(a.isnan(), b.isnan()) and torch.equal(a.nan_to_num(), b.nan_to_num())
+
+
 def test_rope64_deterministic():
     B = 32
     w, sc, q0, U = _rope64(B)
