@@ -549,7 +549,10 @@ def run_ours(args):
             f_ns = flops.rollout_vjp_flops_per_node_step(counts, nobs, k)
             achieved = f_ns * node_steps / avg_launch / 1e12
             roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
-                        frac=achieved / peak, traffic=load_traffic("rope_vjp_kernel"),
+                        frac=achieved / peak, traffic=load_traffic("rope_vjp_call"),
+                        kernels="one sim_rollout_vjp call: rope_vjp_fwd_kernel, rope_order_kernel, "
+                                "rope_vjp_bwd_kernel (more rollouts than the device holds at once); "
+                                "achieved = the call's flops / the call's event time",
                         peak_source=f"FP32 FMA: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
                                     "(recipe unit counts and the max SM clock)",
                         flops_per_node_step=f_ns, oracle_iterations_per_step=counts)
