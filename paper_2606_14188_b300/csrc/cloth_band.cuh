@@ -295,9 +295,11 @@ __device__ __forceinline__ void cl_load_cols_warp(const Scene<R>& S, const Cloth
 // with the forward substitution L y = vb fused (vb in shared memory becomes y).  Returns false,
 // uniformly over the CTA, when a pivot is not positive (the matrix is not positive definite).
 // GW: the band window is Wg in global memory (a cloth too wide for shared memory), else it is the
-// start of shared memory.
+// start of shared memory.  Inlined at every call: as a called function under the 128-register
+// budget of a 512-thread CTA it spilled registers with no stack frame of its own (ptxas -v), and
+// with the window in global memory its results were nondeterministic.
 template <typename R, bool GW>
-__device__ __noinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M, R* Lg, R* sm,
+__device__ __forceinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D, const BandSrc<R>& M, R* Lg, R* sm,
                                        R* Wg) {
   R* Wn = GW ? Wg : sm;                    // the band window: global workspace or shared memory
   R* Pb = sm + cloth_win_elems(D);
