@@ -63,7 +63,7 @@ template <typename R>
 __device__ __forceinline__ ClothSm<R> cloth_sm(const ClothDims& D) {
   ClothSm<R> c;
   c.sm = reinterpret_cast<R*>(cs_smem);
-  c.vb = c.sm + cloth_win_elems(D) + (size_t)CL_KB * D.PL;
+  c.vb = c.sm + cloth_vb_off(D);
   c.red = c.vb + D.N + CL_KB;
   c.misc = c.red + 64;
   return c;

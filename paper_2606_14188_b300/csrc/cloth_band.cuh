@@ -65,7 +65,8 @@ __host__ __device__ inline ClothDims cloth_dims(int R, int C) {
 }
 
 // shared memory of one CTA (elements of the real type): window (or the two staging panels of a
-// solve), panel buffer, right-hand side, panel partial sums, reductions, step scalars
+// solve), panel buffer, solve barriers, right-hand side, panel partial sums, reductions, step
+// scalars, state and stage-1 offset
 __host__ __device__ inline size_t cloth_win_elems(const ClothDims& d) {
   const size_t win = d.win_global ? 0 : (size_t)d.WC * d.LDW;
   const size_t stg = (size_t)2 * CL_KB * d.LDB;
@@ -77,8 +78,15 @@ __host__ __device__ inline size_t cloth_gwin_elems(const ClothDims& d) {
   return d.win_global ? (((size_t)d.WC * d.LDW + 3) & ~(size_t)3) : 0;
 }
 
+// after the panel buffer: the solves' two mbarriers and a failure flag (32 bytes or more,
+// 16-byte aligned), then the right-hand side
+__host__ __device__ inline size_t cloth_mbar_off(const ClothDims& d) {
+  return cloth_win_elems(d) + (size_t)CL_KB * d.PL;
+}
+__host__ __device__ inline size_t cloth_vb_off(const ClothDims& d) { return cloth_mbar_off(d) + 8; }
+
 __host__ __device__ inline size_t cloth_smem_elems(const ClothDims& d) {
-  return cloth_win_elems(d) + (size_t)CL_KB * d.PL + (size_t)d.N + CL_KB + 64 + 64 + 2 * (size_t)d.N;
+  return cloth_vb_off(d) + (size_t)d.N + CL_KB + 64 + 64 + 2 * (size_t)d.N;
 }
 
 // place the band window (shared memory when it fits, else the global workspace slot); false when
@@ -303,7 +311,7 @@ __device__ __forceinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D,
                                        R* Wg) {
   R* Wn = GW ? Wg : sm;                    // the band window: global workspace or shared memory
   R* Pb = sm + cloth_win_elems(D);
-  R* vb = Pb + (size_t)CL_KB * D.PL;
+  R* vb = sm + cloth_vb_off(D);
   R* ild = vb + D.N;                       // reciprocal pivots of the current panel [CL_KB]
   R* flag = vb + D.N + CL_KB + 63;         // last slot of the reduction area: failure flag
   const int N = D.N, bw = D.bw, WC = D.WC, LDW = D.LDW;
@@ -462,28 +470,123 @@ __device__ __forceinline__ bool cl_factor(const Scene<R>& S, const ClothDims& D,
   return true;
 }
 
-// stage the factor's panel [j, j + kbp) (contiguous in Lg) into a shared buffer
+// The two substitutions stream the factor from global memory panel by panel.  A panel (kbp
+// columns of LDB elements) is contiguous in Lg, so it reaches shared memory as ONE bulk copy of the
+// TMA engine (cp.async.bulk, global -> shared), completed on an mbarrier; two buffers alternate so
+// that the copy of the next panel overlaps the work on the current one.  Alignment: Lg, the panel
+// start j LDB (j a multiple of CL_KB, LDB a multiple of 4) and both buffers sit on 16-byte
+// boundaries, and kbp LDB sizeof(R) is a multiple of 16 bytes.
+//
+// Every wait is bounded.  A thread whose wait runs out records it and carries on (the loop's
+// indices do not depend on the data, so nothing goes out of bounds); after the loop the CTA waits
+// once more, bounded, for copies still in flight and sets the solution to NaN, so that the step
+// fails as non-finite instead of hanging.
+constexpr unsigned CL_WAIT_LIMIT = 1u << 22;
+
+struct ClBar {
+  unsigned long long b[2];   // one mbarrier per staging buffer
+  int fail;                  // a wait ran out
+};
+static_assert(sizeof(ClBar) <= 8 * sizeof(float), "barrier slot of the cloth shared-memory layout");
+
+__device__ __forceinline__ unsigned cl_saddr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
 template <typename R>
-__device__ __forceinline__ void cl_stage(const ClothDims& D, const R* Lg, int j, int kbp, R* buf) {
-  const R* src = Lg + (size_t)j * D.LDB;
-  for (int idx = threadIdx.x; idx < kbp * D.LDB; idx += CL_NT) buf[idx] = src[idx];
+__device__ __forceinline__ ClBar* cl_bar(const ClothDims& D, R* sm) {
+  return reinterpret_cast<ClBar*>(sm + cloth_mbar_off(D));
+}
+
+// both barriers expect one arrival per phase; every thread orders its earlier generic accesses of
+// the factor (written in global memory by the factorisation) and of the staging buffers (the
+// window, before) before the copies of the async proxy.  The caller synchronises afterwards.
+__device__ __forceinline__ void cl_bar_init(ClBar* B) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cl_saddr(&B->b[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cl_saddr(&B->b[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    B->fail = 0;
+  }
+  asm volatile("fence.proxy.async;" ::: "memory");
+}
+
+// thread 0: copy panel [j, j + kbp) of the factor into buf, completing on barrier bar
+template <typename R>
+__device__ __forceinline__ void cl_bulk(const ClothDims& D, const R* Lg, int j, int kbp, R* buf,
+                                        unsigned long long* bar) {
+  const unsigned bytes = (unsigned)((size_t)kbp * D.LDB * sizeof(R));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cl_saddr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(cl_saddr(buf)), "l"(Lg + (size_t)j * D.LDB), "r"(bytes), "r"(cl_saddr(bar))
+               : "memory");
+}
+
+// poll the barrier until the phase of the given parity has completed, at most CL_WAIT_LIMIT times
+__device__ __forceinline__ bool cl_bar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = cl_saddr(bar);
+  for (unsigned it = 0; it < CL_WAIT_LIMIT; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool cl_bar_failed(ClBar* B) { return *reinterpret_cast<volatile int*>(&B->fail) != 0; }
+
+// wait for buffer b's copy (phase parity in bit b of ph, flipped afterwards); a wait that runs out
+// is recorded in B->fail, and once one has, no thread waits again
+__device__ __forceinline__ void cl_bar_take(ClBar* B, int b, unsigned& ph) {
+  if (!cl_bar_failed(B) && !cl_bar_wait(&B->b[b], (ph >> b) & 1u)) B->fail = 1;
+  ph ^= 1u << b;
+}
+
+// after the loop (all threads past a barrier): on a recorded failure wait once more, bounded, for
+// the last phase taken on each buffer (the copy that may still be in flight) and poison the
+// solution; then release the barriers
+template <typename R>
+__device__ __forceinline__ void cl_bar_finish(ClBar* B, R* vb, int N, unsigned ph) {
+  if (B->fail) {
+    cl_bar_wait(&B->b[0], (ph & 1u) ^ 1u);
+    cl_bar_wait(&B->b[1], ((ph >> 1) & 1u) ^ 1u);
+    const R q = sizeof(R) == 4 ? R(nanf("")) : R(nan(""));
+    for (int i = threadIdx.x; i < N; i += CL_NT) vb[i] = q;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(cl_saddr(&B->b[0])) : "memory");
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(cl_saddr(&B->b[1])) : "memory");
+  }
 }
 
 // backward substitution L^T x = vb in place (vb in shared memory), panels from the last
 template <typename R>
 __device__ __noinline__ void cl_back(const ClothDims& D, const R* Lg, R* sm) {
-  R* vb = sm + cloth_win_elems(D) + (size_t)CL_KB * D.PL;
+  R* vb = sm + cloth_vb_off(D);
   R* tc = vb + D.N;
+  ClBar* B = cl_bar(D, sm);
   const int N = D.N, bw = D.bw, LDB = D.LDB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int jlast = ((N - 1) / CL_KB) * CL_KB;
-  int buf = 0;
-  cl_stage(D, Lg, jlast, N - jlast, sm);
+  cl_bar_init(B);
   __syncthreads();
+  if (threadIdx.x == 0) cl_bulk(D, Lg, jlast, N - jlast, sm, &B->b[0]);
+  unsigned ph = 0;
+  int buf = 0;
   for (int j = jlast; j >= 0; j -= CL_KB) {
     const int jn = min(j + CL_KB, N), kbp = jn - j;
     const R* Lb = sm + (size_t)buf * CL_KB * LDB;
-    if (j > 0) cl_stage(D, Lg, j - CL_KB, CL_KB, sm + (size_t)(buf ^ 1) * CL_KB * LDB);
+    cl_bar_take(B, buf, ph);
+    // the other buffer was last read before the previous iteration's closing barrier
+    if (j > 0 && threadIdx.x == 0 && !cl_bar_failed(B))
+      cl_bulk(D, Lg, j - CL_KB, CL_KB, sm + (size_t)(buf ^ 1) * CL_KB * LDB, &B->b[buf ^ 1]);
     for (int cc = warp; cc < kbp; cc += CL_NW) {
       const int c = j + cc;
       const R* col = Lb + cc * LDB;
@@ -509,21 +612,27 @@ __device__ __noinline__ void cl_back(const ClothDims& D, const R* Lg, R* sm) {
     __syncthreads();
     buf ^= 1;
   }
+  cl_bar_finish(B, vb, N, ph);
 }
 
 // forward substitution L y = vb in place
 template <typename R>
 __device__ __noinline__ void cl_fwd(const ClothDims& D, const R* Lg, R* sm) {
-  R* vb = sm + cloth_win_elems(D) + (size_t)CL_KB * D.PL;
+  R* vb = sm + cloth_vb_off(D);
+  ClBar* B = cl_bar(D, sm);
   const int N = D.N, bw = D.bw, LDB = D.LDB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int buf = 0;
-  cl_stage(D, Lg, 0, min(CL_KB, N), sm);
+  cl_bar_init(B);
   __syncthreads();
+  if (threadIdx.x == 0) cl_bulk(D, Lg, 0, min(CL_KB, N), sm, &B->b[0]);
+  unsigned ph = 0;
+  int buf = 0;
   for (int j = 0; j < N; j += CL_KB) {
     const int jn = min(j + CL_KB, N), kbp = jn - j;
     const R* Lb = sm + (size_t)buf * CL_KB * LDB;
-    if (jn < N) cl_stage(D, Lg, jn, min(CL_KB, N - jn), sm + (size_t)(buf ^ 1) * CL_KB * LDB);
+    cl_bar_take(B, buf, ph);
+    if (jn < N && threadIdx.x == 0 && !cl_bar_failed(B))
+      cl_bulk(D, Lg, jn, min(CL_KB, N - jn), sm + (size_t)(buf ^ 1) * CL_KB * LDB, &B->b[buf ^ 1]);
     if (warp == 0) {
       for (int c = j; c < jn; ++c) {
         const R* col = Lb + (c - j) * LDB;
@@ -549,6 +658,7 @@ __device__ __noinline__ void cl_fwd(const ClothDims& D, const R* Lg, R* sm) {
     __syncthreads();
     buf ^= 1;
   }
+  cl_bar_finish(B, vb, N, ph);
 }
 
 }  // namespace cs
