@@ -781,15 +781,31 @@ __device__ int cl_adjoint(const Scene<R>& S, const ClothDims& D, const ClothWS<R
 }
 
 // ---- kernels: one CTA per rollout at a time (grid <= workspace slots)
+
+// the rollout a CTA takes after rollout b: with more rollouts than CTAs, the next unstarted one,
+// claimed from a counter zeroed before the launch (the first wave is b = blockIdx.x), so that a
+// CTA whose rollouts were cheap takes more of them; without a counter, b + gridDim.x.  Every
+// thread gets the same value.
+__device__ __forceinline__ int cl_next_rollout(int b, int B, int* claim) {
+  __shared__ int next;
+  if (!claim) return b + (int)gridDim.x;
+  if (B <= (int)gridDim.x) return B;
+  __syncthreads();
+  if (threadIdx.x == 0) next = (int)gridDim.x + atomicAdd(claim, 1);
+  __syncthreads();
+  return next;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(CL_NT) cloth_rollout_kernel(Scene<R> S, ClothDims D, int B, int H, const R* q0,
                                                              const R* U, R* traj, R* qH, int32_t* status,
-                                                             int32_t* counters, R* slots, size_t slot_stride) {
+                                                             int32_t* counters, R* slots, size_t slot_stride,
+                                                             int* claim) {
   const ClothSm<R> c = cloth_sm<R>(D);
   const ClothWS<R> w = cloth_carve<R>(slots + blockIdx.x * slot_stride, D, S.nobs);
   const int nq = D.N + 6;
   const bool smooth = S.fwd_mode == CS_SMOOTH;
-  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+  for (int b = blockIdx.x; b < B; b = cl_next_rollout(b, B, claim)) {
     cl_load_q(S, D, w, c.misc, q0 + (size_t)b * nq);
     for (int i = threadIdx.x; i < D.N; i += CL_NT) w.Dl[i] = R(0);
     __syncthreads();
@@ -936,11 +952,11 @@ template <typename R>
 __global__ void __launch_bounds__(CL_NT) cloth_vjp_kernel(Scene<R> S, ClothDims D, int B, int H, const R* q0,
                                                          const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
                                                          int32_t* status, R* slots, size_t slot_stride, R* ck,
-                                                         size_t ck_stride) {
+                                                         size_t ck_stride, int* claim) {
   const ClothSm<R> c = cloth_sm<R>(D);
   const ClothWS<R> w = cloth_carve<R>(slots + blockIdx.x * slot_stride, D, S.nobs);
   const int nq = D.N + 6;
-  for (int b = blockIdx.x; b < B; b += gridDim.x)
+  for (int b = blockIdx.x; b < B; b = cl_next_rollout(b, B, claim))
     cl_vjp_rollout<R>(S, D, w, c, H, q0 + (size_t)b * nq, U + (size_t)b * H * 6,
                       dLdtraj ? dLdtraj + (size_t)b * (H + 1) * nq : nullptr, Lout ? Lout + b : nullptr,
                       dLdu + (size_t)b * H * 6, dLdq0 ? dLdq0 + (size_t)b * nq : nullptr,

@@ -145,6 +145,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
     s->nslots = P->max_batch < resident ? P->max_batch : resident;
     s->slot_stride = cs::cloth_ws_elems(s->cd, P->n_obstacles);
     e = cudaMalloc(&s->d_slots, s->slot_stride * (size_t)s->nslots * rb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_claim, sizeof(int));
     if (e != cudaSuccess) {
       sim_destroy(s);
       return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "cloth workspace") : cs_cuda_fail(e, "cudaMalloc");
@@ -162,6 +163,7 @@ cs_status sim_destroy(cs_sim* s) {
   if (s->d_L2) cudaFree(s->d_L2);
   if (s->d_ws) cudaFree(s->d_ws);
   if (s->d_slots) cudaFree(s->d_slots);
+  if (s->d_claim) cudaFree(s->d_claim);
   delete s;
   return CS_OK;
 }

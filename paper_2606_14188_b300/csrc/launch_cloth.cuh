@@ -8,6 +8,13 @@ namespace csi {
 
 inline size_t cloth_smem_bytes(const cs_sim* s) { return cs::cloth_smem_elems(s->cd) * (size_t)s->real_bytes; }
 
+// a launch with more rollouts than CTAs hands out the rest through a counter: zero it first
+inline cs_status zero_claim(cs_sim* s, int B, int grid, cudaStream_t st) {
+  if (B <= grid) return CS_OK;
+  const cudaError_t e = cudaMemsetAsync(s->d_claim, 0, sizeof(int), st);
+  return e == cudaSuccess ? CS_OK : cs_cuda_fail(e, "cudaMemsetAsync");
+}
+
 template <typename R>
 cs_status launch_cloth_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj, void* qH,
                                int32_t* status, int32_t* counters, cudaStream_t st) {
@@ -16,9 +23,10 @@ cs_status launch_cloth_rollout(cs_sim* s, int B, int H, const void* q0, const vo
   cs_status r = prep_kernel(cs::cloth_rollout_kernel<R>, smem);
   if (r) return r;
   const int grid = B < s->nslots ? B : s->nslots;
+  if ((r = zero_claim(s, B, grid, st))) return r;
   cs::cloth_rollout_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, s->cd, B, H, (const R*)q0, (const R*)u, (R*)traj,
                                                             (R*)qH, status, counters, (R*)s->d_slots,
-                                                            s->slot_stride);
+                                                            s->slot_stride, (int*)s->d_claim);
   return check_launch("cloth_rollout_kernel");
 }
 
@@ -31,10 +39,11 @@ cs_status launch_cloth_vjp(cs_sim* s, int B, int H, const void* q0, const void* 
   cs_status r = prep_kernel(cs::cloth_vjp_kernel<R>, smem);
   if (r) return r;
   const int grid = B < s->nslots ? B : s->nslots;
+  if ((r = zero_claim(s, B, grid, st))) return r;
   cs::cloth_vjp_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, s->cd, B, H, (const R*)q0, (const R*)u,
                                                         (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0, status,
                                                         (R*)s->d_slots, s->slot_stride, (R*)s->d_ws,
-                                                        s->ws_stride);
+                                                        s->ws_stride, (int*)s->d_claim);
   return check_launch("cloth_vjp_kernel");
 }
 

@@ -307,3 +307,23 @@ def test_cloth34_fp32_global_window_repeatable():
         assert torch.equal(a, b)
     for a, b in zip(runs[0], runs[2]):
         assert torch.equal(a, b)
+
+
+def test_cloth32_more_rollouts_than_ctas():
+    """152 rollouts of the 32 x 32 FP32 cloth on a device that holds one such CTA per SM: the
+    rollouts past the first wave are handed out through a counter; each one's outputs equal the
+    same rollout run alone, bit for bit (forward and adjoint)."""
+    B, H = 152, 1
+    w = scenes.workload(3, B=B, H=H)
+    sc, q0, U = w["scene"], w["q0"], w["U"]
+    s = _sim(sc, 4, B, H, newton_max=400)
+    traj, qH, st = s.rollout(_t(q0, 4), _t(U, 4))
+    vjp = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    idx = [0, 147, 148, 151]
+    a = _sim(sc, 4, len(idx), H, newton_max=400)
+    traj1, qH1, st1 = a.rollout(_t(q0[idx], 4), _t(U[idx], 4))
+    vjp1 = a.rollout_vjp(_t(q0[idx], 4), _t(U[idx], 4))
+    sel = torch.as_tensor(idx, device="cuda")
+    for x, y in zip((traj, qH, st) + tuple(vjp), (traj1, qH1, st1) + tuple(vjp1)):
+        x = x[sel]
+        assert torch.equal(x.isnan(), y.isnan()) and torch.equal(x.nan_to_num(), y.nan_to_num())
