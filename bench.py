@@ -15,6 +15,7 @@ bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import copy
 import csv
 import hashlib
 import glob
@@ -529,6 +530,14 @@ def run_ours(args):
     # forward alone (the same rollouts, nonsmooth forward, trajectory written)
     t_fwd = max_over_ranks(sum(time_device(lambda: s.rollout(q0, U), args.steps, flush, stream)),
                            world)
+    # the same adjoint with a record at every step (k = 1: 51 records of 588 numbers per rollout,
+    # 123 MB for 1024 rollouts) instead of recomputing each segment from its checkpoint
+    sc1 = copy.deepcopy(sc)
+    sc1["params"]["checkpoint_every"] = 1
+    s1 = Sim(sc1, real_bytes=4, max_batch=B, max_horizon=H)
+    t_k1 = max_over_ranks(sum(time_device(lambda: s1.rollout_vjp(q0, U, want_dq0=False), args.steps,
+                                          flush, stream)), world)
+    del s1
     # linearisation workload: 256 nominal trajectories of a 40-node rope, horizon 20
     lin = linearize_leg(args, flush, stream, world)
     served = served_leg(args) if args.served_requests > 0 else None
@@ -570,6 +579,12 @@ def run_ours(args):
                     forward=dict(value=world * args.steps * node_steps / t_fwd, unit=UNIT,
                                  ms_per_step=1e3 * t_fwd / args.steps,
                                  what="sim_rollout alone on the same rollouts"),
+                    adjoint_every_step_recorded=dict(
+                        value=world * args.steps * node_steps / t_k1, unit=UNIT,
+                        ms_per_step=1e3 * t_k1 / args.steps,
+                        what="sim_rollout_vjp on the same rollouts with checkpoint_every = 1 (every "
+                             "step's record stored, no segment recompute); not the headline, whose "
+                             "workload checkpoints every 7 steps"),
                     linearize=lin, served=served, cloth=cloth,
                     gpu_launches=launches, clocks=clocks,
                     status_nonzero=int(np.count_nonzero(status)),

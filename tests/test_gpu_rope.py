@@ -157,6 +157,21 @@ def test_rope64_two_part_launch_equals_one_launch():
         assert torch.equal(a.isnan(), b.isnan()) and torch.equal(a.nan_to_num(), b.nan_to_num())
 
 
+def test_rope64_checkpoint_interval_does_not_change_the_adjoint():
+    """The recomputed segment steps reproduce the forward's steps exactly, so the adjoint with a
+    record at every step (k = 1, no recompute) equals the one with k = 7, bit for bit."""
+    import copy
+    B = 8
+    w, sc, q0, U = _rope64(B)
+    sc1 = copy.deepcopy(sc)
+    sc1["params"]["checkpoint_every"] = 1
+    a = _sim(sc, 4, B, 50).rollout_vjp(_t(q0, 4), _t(U, 4))
+    b = _sim(sc1, 4, B, 50).rollout_vjp(_t(q0, 4), _t(U, 4))
+    assert sc["params"]["checkpoint_every"] == 7
+    for x, y in zip(a, b):
+        assert torch.equal(x.isnan(), y.isnan()) and torch.equal(x.nan_to_num(), y.nan_to_num())
+
+
 def test_rope64_deterministic():
     B = 32
     w, sc, q0, U = _rope64(B)
