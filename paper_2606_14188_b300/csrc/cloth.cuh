@@ -831,10 +831,15 @@ __global__ void __launch_bounds__(CL_NT) cloth_rollout_kernel(Scene<R> S, ClothD
   }
 }
 
-template <typename R>
+// Forward rollout + checkpointed adjoint of one cloth rollout by one CTA (the schedule of
+// vjp_rollout for ropes).  PH = VJP_FWD stops after the forward steps: L and the carry are
+// written and *cost gets the forward's work (2 x Newton + 5 x interior-point iterations; -1: the
+// rollout failed and its outputs are final); PH = VJP_BWD resumes from the carry at the last
+// segment.
+template <typename R, int PH = VJP_ALL>
 __device__ void cl_vjp_rollout(const Scene<R>& S, const ClothDims& D, const ClothWS<R>& w, const ClothSm<R>& c,
                                int H, const R* q0, const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
-                               int32_t* status, R* ck) {
+                               int32_t* status, R* ck, int32_t* cost = nullptr) {
   const int N = D.N, nq = N + 6;
   const int rl = rec_len(D.nv);
   const int k = S.ckpt;
@@ -843,13 +848,32 @@ __device__ void cl_vjp_rollout(const Scene<R>& S, const ClothDims& D, const Clot
   R* misc = c.misc;
   enum { FWD = 0, RECOMP = 1, BACK = 2 };
   R* seg = ck + (size_t)(nseg + 1) * rl;
-  cl_load_q(S, D, w, misc, q0);
-  for (int i = threadIdx.x; i < N; i += CL_NT) { w.Dl[i] = R(0); w.dx[i] = R(0); w.xb[i] = R(0); }
-  __syncthreads();
-  cl_store_rec(D, w, misc, ck);
+  R* carry = ck + cloth_vjp_rec_elems(D.nv, H, k);
   int st = 0;
   R Lacc = R(0);
+  int work = 0;
   int kind = FWD, t = 0, sgi = nseg - 1, t0 = 0, t1 = 0;
+  auto begin_segment = [&]() {
+    t0 = sgi * k;
+    t1 = min(t0 + k, H);
+    cl_load_rec(D, w, misc, ck + (size_t)sgi * rl);
+    cl_load_rec_delta(D, w, ck + (size_t)sgi * rl);
+    __syncthreads();
+    cl_store_rec(D, w, misc, seg);
+    if (t1 - t0 > 1) { kind = RECOMP; t = t0; } else { kind = BACK; t = t0; }
+  };
+  if constexpr ((PH & VJP_FWD) != 0) {
+    cl_load_q(S, D, w, misc, q0);
+    for (int i = threadIdx.x; i < N; i += CL_NT) { w.Dl[i] = R(0); w.dx[i] = R(0); w.xb[i] = R(0); }
+    __syncthreads();
+    cl_store_rec(D, w, misc, ck);
+  } else {
+    for (int i = threadIdx.x; i < N; i += CL_NT) { w.dx[i] = R(0); w.xb[i] = carry[i]; }
+    if (threadIdx.x < 6) misc[M_GB + threadIdx.x] = carry[N + threadIdx.x];
+    __syncthreads();
+    begin_segment();
+    __syncthreads();
+  }
   while (true) {
     if (kind == BACK) {
       cl_load_rec(D, w, misc, seg + (size_t)(t - t0) * rl);
@@ -865,6 +889,7 @@ __device__ void cl_vjp_rollout(const Scene<R>& S, const ClothDims& D, const Clot
     const bool w2 = kind == BACK || cl_any_delta(D, w);
     st |= cl_step(S, D, w, c, kind == BACK || fwd_smooth, &ni, &ii, kind == BACK, w2);
     if (st) break;                 // a failed step: the rollout's loss and gradient are undefined
+    if (kind == FWD) work = min(work + 2 * ni + 5 * ii, 1 << 30);
     if (kind != BACK) {
       cl_advance(S, D, w, misc);
       if (kind == FWD) {
@@ -911,25 +936,34 @@ __device__ void cl_vjp_rollout(const Scene<R>& S, const ClothDims& D, const Clot
     }
     bool start_seg = false;
     if (kind == FWD) {
-      if (++t == H) start_seg = true;
+      if (++t == H) {
+        if constexpr (PH == VJP_FWD) break;
+        start_seg = true;
+      }
     } else if (kind == RECOMP) {
       if (++t == t1 - 1) { kind = BACK; t = t1 - 1; }
     } else {
       if (--t < t0) { if (--sgi < 0) break; start_seg = true; }
     }
-    if (start_seg) {
-      t0 = sgi * k;
-      t1 = min(t0 + k, H);
-      cl_load_rec(D, w, misc, ck + (size_t)sgi * rl);
-      cl_load_rec_delta(D, w, ck + (size_t)sgi * rl);
-      __syncthreads();
-      cl_store_rec(D, w, misc, seg);
-      if (t1 - t0 > 1) { kind = RECOMP; t = t0; } else { kind = BACK; t = t0; }
-    }
+    if (start_seg) begin_segment();
     __syncthreads();
   }
   __syncthreads();
   Lacc = cl_sum(Lacc, c.red);
+  if constexpr (PH == VJP_FWD) {
+    if (!st) {                     // hand the seeds over; L is final
+      for (int i = threadIdx.x; i < N; i += CL_NT) carry[i] = w.xb[i];
+      if (threadIdx.x < 6) carry[N + threadIdx.x] = misc[M_GB + threadIdx.x];
+      if (threadIdx.x == 0) {
+        if (Lout) *Lout = Lacc;
+        if (status) *status = 0;
+        *cost = work;
+      }
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0) *cost = -1;
+  }
   if (st) {                        // failed rollout: L = NaN, gradients zero
     for (int i = threadIdx.x; i < 6 * H; i += CL_NT) dLdu[i] = R(0);
     for (int i = threadIdx.x; i < N; i += CL_NT) w.xb[i] = R(0);
@@ -942,10 +976,32 @@ __device__ void cl_vjp_rollout(const Scene<R>& S, const ClothDims& D, const Clot
     if (threadIdx.x < 6) dLdq0[N + threadIdx.x] = misc[M_GB + threadIdx.x];
   }
   if (threadIdx.x == 0) {
-    if (Lout) *Lout = Lacc;
+    // the backward part leaves the forward's L unless the rollout failed
+    if (Lout && (PH != VJP_BWD || st)) *Lout = Lacc;
     if (status) *status = st;
   }
   __syncthreads();
+}
+
+// the rollouts of one CTA (order[i] when given): the first wave by blockIdx.x, then handed out
+// by the counter; the backward part skips a rollout whose forward failed (cost -1)
+template <typename R, int PH>
+__device__ __forceinline__ void cl_vjp_rollouts(const Scene<R>& S, const ClothDims& D, int B, int H, const R* q0,
+                                                const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
+                                                int32_t* status, R* slots, size_t slot_stride, R* ck,
+                                                size_t ck_stride, int* claim, int32_t* cost,
+                                                const int32_t* order) {
+  const ClothSm<R> c = cloth_sm<R>(D);
+  const ClothWS<R> w = cloth_carve<R>(slots + blockIdx.x * slot_stride, D, S.nobs);
+  const int nq = D.N + 6;
+  for (int i = blockIdx.x; i < B; i = cl_next_rollout(i, B, claim)) {
+    const int b = order ? order[i] : i;
+    if (PH == VJP_BWD && cost[b] < 0) continue;
+    cl_vjp_rollout<R, PH>(S, D, w, c, H, q0 + (size_t)b * nq, U + (size_t)b * H * 6,
+                          dLdtraj ? dLdtraj + (size_t)b * (H + 1) * nq : nullptr, Lout ? Lout + b : nullptr,
+                          dLdu + (size_t)b * H * 6, dLdq0 ? dLdq0 + (size_t)b * nq : nullptr,
+                          status ? status + b : nullptr, ck + (size_t)b * ck_stride, cost ? cost + b : nullptr);
+  }
 }
 
 template <typename R>
@@ -953,14 +1009,30 @@ __global__ void __launch_bounds__(CL_NT) cloth_vjp_kernel(Scene<R> S, ClothDims 
                                                          const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
                                                          int32_t* status, R* slots, size_t slot_stride, R* ck,
                                                          size_t ck_stride, int* claim) {
-  const ClothSm<R> c = cloth_sm<R>(D);
-  const ClothWS<R> w = cloth_carve<R>(slots + blockIdx.x * slot_stride, D, S.nobs);
-  const int nq = D.N + 6;
-  for (int b = blockIdx.x; b < B; b = cl_next_rollout(b, B, claim))
-    cl_vjp_rollout<R>(S, D, w, c, H, q0 + (size_t)b * nq, U + (size_t)b * H * 6,
-                      dLdtraj ? dLdtraj + (size_t)b * (H + 1) * nq : nullptr, Lout ? Lout + b : nullptr,
-                      dLdu + (size_t)b * H * 6, dLdq0 ? dLdq0 + (size_t)b * nq : nullptr,
-                      status ? status + b : nullptr, ck + (size_t)b * ck_stride);
+  cl_vjp_rollouts<R, VJP_ALL>(S, D, B, H, q0, U, dLdtraj, Lout, dLdu, dLdq0, status, slots, slot_stride, ck,
+                              ck_stride, claim, nullptr, nullptr);
+}
+
+// the forward parts of a two-part launch (more rollouts than CTAs): records, L, the carry and the
+// cost of each rollout
+template <typename R>
+__global__ void __launch_bounds__(CL_NT) cloth_vjp_fwd_kernel(Scene<R> S, ClothDims D, int B, int H, const R* q0,
+                                                             const R* U, const R* dLdtraj, R* Lout, R* dLdu,
+                                                             R* dLdq0, int32_t* status, R* slots, size_t slot_stride,
+                                                             R* ck, size_t ck_stride, int* claim, int32_t* cost) {
+  cl_vjp_rollouts<R, VJP_FWD>(S, D, B, H, q0, U, dLdtraj, Lout, dLdu, dLdq0, status, slots, slot_stride, ck,
+                              ck_stride, claim, cost, nullptr);
+}
+
+// the backward parts, rollout order[i] as the i-th one handed out (costliest first)
+template <typename R>
+__global__ void __launch_bounds__(CL_NT) cloth_vjp_bwd_kernel(Scene<R> S, ClothDims D, int B, int H, const R* U,
+                                                             const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
+                                                             int32_t* status, R* slots, size_t slot_stride, R* ck,
+                                                             size_t ck_stride, int* claim, int32_t* cost,
+                                                             const int32_t* order) {
+  cl_vjp_rollouts<R, VJP_BWD>(S, D, B, H, nullptr, U, dLdtraj, Lout, dLdu, dLdq0, status, slots, slot_stride, ck,
+                              ck_stride, claim, cost, order);
 }
 
 }  // namespace cs

@@ -92,10 +92,11 @@ __host__ __device__ inline size_t cloth_smem_elems(const ClothDims& d) {
 // place the band window (shared memory when it fits, else the global workspace slot); false when
 // even the rest does not fit in shared memory
 inline bool cloth_fit(ClothDims& d, size_t real_bytes, size_t smem_optin) {
+  const size_t avail = smem_optin - 256;   // the kernels' static shared variables come on top
   d.win_global = 0;
-  if (cloth_smem_elems(d) * real_bytes <= smem_optin) return true;
+  if (cloth_smem_elems(d) * real_bytes <= avail) return true;
   d.win_global = 1;
-  return cloth_smem_elems(d) * real_bytes <= smem_optin;
+  return cloth_smem_elems(d) * real_bytes <= avail;
 }
 
 // four consecutive elements (16-byte aligned for float)

@@ -132,7 +132,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   const int k = P->checkpoint_every;
   // checkpoint records (state, grasp offsets, stage-1 offset and stage-2 displacement of the
   // producing step) and the carry of the two-part launch
-  s->ws_stride = cs::vjp_ws_elems(nv, P->max_horizon, k);
+  s->ws_stride = cloth ? cs::cloth_vjp_ws_elems(nv, P->max_horizon, k) : cs::vjp_ws_elems(nv, P->max_horizon, k);
   e = cudaMalloc(&s->d_ws, vjp_ws_bytes(s->ws_stride, P->max_batch, rb));
   if (e != cudaSuccess) {
     sim_destroy(s);
@@ -145,7 +145,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
     s->nslots = P->max_batch < resident ? P->max_batch : resident;
     s->slot_stride = cs::cloth_ws_elems(s->cd, P->n_obstacles);
     e = cudaMalloc(&s->d_slots, s->slot_stride * (size_t)s->nslots * rb);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_claim, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_claim, 2 * sizeof(int));
     if (e != cudaSuccess) {
       sim_destroy(s);
       return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "cloth workspace") : cs_cuda_fail(e, "cudaMalloc");

@@ -30,7 +30,8 @@ struct cs_sim {
   // cloth only: band geometry and the per-CTA workspace slots of the cloth kernels
   cs::ClothDims cd{};
   void* d_slots = nullptr;
-  void* d_claim = nullptr;  // int: next rollout to hand out, for launches with more rollouts than CTAs
+  void* d_claim = nullptr;  // int[2]: next rollout to hand out, for launches with more rollouts than
+                            // CTAs (the second for the backward part of a two-part launch)
   size_t slot_stride = 0;  // elements per slot
   int nslots = 0;
 };

@@ -8,10 +8,10 @@ namespace csi {
 
 inline size_t cloth_smem_bytes(const cs_sim* s) { return cs::cloth_smem_elems(s->cd) * (size_t)s->real_bytes; }
 
-// a launch with more rollouts than CTAs hands out the rest through a counter: zero it first
+// a launch with more rollouts than CTAs hands out the rest through a counter: zero both first
 inline cs_status zero_claim(cs_sim* s, int B, int grid, cudaStream_t st) {
   if (B <= grid) return CS_OK;
-  const cudaError_t e = cudaMemsetAsync(s->d_claim, 0, sizeof(int), st);
+  const cudaError_t e = cudaMemsetAsync(s->d_claim, 0, 2 * sizeof(int), st);
   return e == cudaSuccess ? CS_OK : cs_cuda_fail(e, "cudaMemsetAsync");
 }
 
@@ -40,6 +40,28 @@ cs_status launch_cloth_vjp(cs_sim* s, int B, int H, const void* q0, const void* 
   if (r) return r;
   const int grid = B < s->nslots ? B : s->nslots;
   if ((r = zero_claim(s, B, grid, st))) return r;
+  // more rollouts than CTAs: the forward parts first (each measuring its Newton and interior-point
+  // work), then the backward parts handed out costliest first, so that the late ones are cheap
+  if (B > grid && B <= cs::CS_ORDER_MAX) {
+    if ((r = prep_kernel(cs::cloth_vjp_fwd_kernel<R>, smem))) return r;
+    if ((r = prep_kernel(cs::cloth_vjp_bwd_kernel<R>, smem))) return r;
+    int32_t* cost = reinterpret_cast<int32_t*>(static_cast<char*>(s->d_ws) +
+                                               vjp_ord_offset(s->ws_stride, s->P.max_batch, s->real_bytes));
+    int32_t* order = cost + B;
+    int* claim = static_cast<int*>(s->d_claim);
+    cs::cloth_vjp_fwd_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, s->cd, B, H, (const R*)q0, (const R*)u,
+                                                              (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0, status,
+                                                              (R*)s->d_slots, s->slot_stride, (R*)s->d_ws,
+                                                              s->ws_stride, claim, cost);
+    if ((r = check_launch("cloth_vjp_fwd_kernel"))) return r;
+    cs::rope_order_kernel<cs::CS_ORDER_NT><<<1, cs::CS_ORDER_NT, 0, st>>>(cost, B, order);
+    if ((r = check_launch("rope_order_kernel"))) return r;
+    cs::cloth_vjp_bwd_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, s->cd, B, H, (const R*)u, (const R*)dLdtraj,
+                                                              (R*)L, (R*)dLdu, (R*)dLdq0, status, (R*)s->d_slots,
+                                                              s->slot_stride, (R*)s->d_ws, s->ws_stride, claim + 1,
+                                                              cost, order);
+    return check_launch("cloth_vjp_bwd_kernel");
+  }
   cs::cloth_vjp_kernel<R><<<grid, cs::CL_NT, smem, st>>>(S, s->cd, B, H, (const R*)q0, (const R*)u,
                                                         (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0, status,
                                                         (R*)s->d_slots, s->slot_stride, (R*)s->d_ws,

@@ -1263,6 +1263,16 @@ __host__ __device__ inline size_t vjp_ws_elems(int nv, int H, int k) {
   return ((size_t)(nseg + 1 + k) * rec_len(nv) + 3) / 4 * 4 + vjp_carry_elems(2);
 }
 
+// the same for a cloth (one CTA per rollout): records, then a carry of the adjoint seeds of q_H
+// [3 nv + 6]
+__host__ __device__ inline size_t cloth_vjp_rec_elems(int nv, int H, int k) {
+  const int nseg = (H + k - 1) / k;
+  return ((size_t)(nseg + 1 + k) * rec_len(nv) + 3) / 4 * 4;
+}
+__host__ __device__ inline size_t cloth_vjp_ws_elems(int nv, int H, int k) {
+  return cloth_vjp_rec_elems(nv, H, k) + ((size_t)3 * nv + 6 + 3) / 4 * 4;
+}
+
 // Forward rollout + checkpointed adjoint of one rollout by one warp.  Pointers are this
 // rollout's: q0 [n_q], U [H][6], dLdtraj [H+1][n_q] (or null), Lout (or null), dLdu [H][6],
 // dLdq0 [n_q] (or null), status (or null), ck: its workspace (records, then the carry).
