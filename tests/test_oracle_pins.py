@@ -393,7 +393,7 @@ def test_contact_force_is_barrier_gradient_and_W_its_jacobian():
 # gradients
 # ------------------------------------------------------------------------------------------
 
-def _cfg1_state(t=9):
+def _rope20_state(t=9):
     w = scenes.workload(1)
     sc = sim.Scene(w["scene"]["params"], w["scene"]["rest_x"])
     traj, _, _ = sim.rollout(sc, w["q0"][0], w["U"][0, :t], sim.HARD)
@@ -403,7 +403,7 @@ def _cfg1_state(t=9):
 def test_step_jacobian_vs_central_differences():
     """Implicit differentiation (eq. diff-sim, with the total derivative) against central
     differences of the smooth step, at a state with an active contact."""
-    sc, q, u, _ = _cfg1_state()
+    sc, q, u, _ = _rope20_state()
     J = grad.SmoothStepJacobian(sc, q, u)
     A, B = J.jacobians()
     h = 1e-6
@@ -418,7 +418,7 @@ def test_step_jacobian_vs_central_differences():
 
 
 def test_adjoint_dot_product():
-    sc, q, u, _ = _cfg1_state(6)
+    sc, q, u, _ = _rope20_state(6)
     J = grad.SmoothStepJacobian(sc, q, u)
     rng = np.random.default_rng(5)
     for _ in range(3):
