@@ -327,3 +327,23 @@ def test_cloth32_more_rollouts_than_ctas():
     for x, y in zip((traj, qH, st) + tuple(vjp), (traj1, qH1, st1) + tuple(vjp1)):
         x = x[sel]
         assert torch.equal(x.isnan(), y.isnan()) and torch.equal(x.nan_to_num(), y.nan_to_num())
+
+
+def test_cloth20_fp64_more_rollouts_than_ctas():
+    """150 rollouts of a 20 x 20 FP64 cloth (one CTA per SM): the two-part adjoint and the claimed
+    forward rollouts equal the same rollouts run alone, bit for bit."""
+    B, H = 150, 1
+    sc = scenes.cloth_scene(20, 20, n_spheres=2, seed=41)
+    U = scenes.controls_normal_clear(sc, B, H, seed=42)
+    q0 = np.tile(sc["q0"], (B, 1))
+    s = _sim(sc, 8, B, H, newton_max=300)
+    fwd = s.rollout(_t(q0, 8), _t(U, 8))
+    vjp = s.rollout_vjp(_t(q0, 8), _t(U, 8))
+    idx = [0, 147, 148, 149]
+    a = _sim(sc, 8, len(idx), H, newton_max=300)
+    fwd1 = a.rollout(_t(q0[idx], 8), _t(U[idx], 8))
+    vjp1 = a.rollout_vjp(_t(q0[idx], 8), _t(U[idx], 8))
+    sel = torch.as_tensor(idx, device="cuda")
+    for x, y in zip(tuple(fwd) + tuple(vjp), tuple(fwd1) + tuple(vjp1)):
+        x = x[sel]
+        assert torch.equal(x.isnan(), y.isnan()) and torch.equal(x.nan_to_num(), y.nan_to_num())

@@ -380,3 +380,18 @@ def test_rope100_fp32_two_pairs_per_lane_vs_oracle():
             assert rel_state(traj[b].cpu().numpy(), ref) <= TOL_STATE32, b
             assert abs(float(Lv[b]) - g["L"]) <= TOL_STATE32 * abs(g["L"])
             check_grad(dU[b].cpu().numpy(), g["dL_du"], TOL_GRAD32, COS32)
+
+
+def test_rope64_fp64_two_part_launch_equals_one_launch():
+    """FP64 (about two one-warp CTAs per SM): 320 rollouts take the two-part launch; rollouts
+    from both ends equal the same rollouts run alone, bit for bit."""
+    w = scenes.workload(2)
+    sc = w["scene"]
+    B, H = 320, 12
+    idx = np.r_[0:4, B - 4:B]
+    q0, U = w["q0"][:B], w["U"][:B, :H]
+    big = _sim(sc, 8, B, H).rollout_vjp(_t(q0, 8), _t(U, 8))
+    small = _sim(sc, 8, len(idx), H).rollout_vjp(_t(q0[idx], 8), _t(U[idx], 8))
+    for a, b in zip(big, small):
+        a = a[torch.as_tensor(idx, device=a.device)]
+        assert torch.equal(a.isnan(), b.isnan()) and torch.equal(a.nan_to_num(), b.nan_to_num())
