@@ -353,7 +353,7 @@ def served_stream(n, seed, cloth_frac=0.0):
             H = int(crng.integers(10, 21))
             R = int(2 ** crng.integers(5, 8))
             sc = scenes.cloth_scene(side, side, n_spheres=2, seed=seed + 1 + i)
-            sc["params"]["checkpoint_every"] = max(1, int(round(H ** 0.5)))
+            sc["params"]["checkpoint_every"] = 0      # the server picks it by memory
             reqs.append(dict(scene=sc, q0=sc["q0"], H=H, R=R, G=10, seed=seed + 7919 * i, nv=side * side,
                              kw=dict(newton_max=300)))
             continue
@@ -362,7 +362,7 @@ def served_stream(n, seed, cloth_frac=0.0):
         R = int(2 ** rng.integers(6, 11))
         sc = scenes.rope_scene(nv, n_spheres=int(rng.integers(1, 3)), n_boxes=int(rng.integers(0, 2)),
                                seed=seed + 1 + i, sphere_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)))
-        sc["params"]["checkpoint_every"] = max(1, int(round(H ** 0.5)))
+        sc["params"]["checkpoint_every"] = 0          # the server picks it by memory
         reqs.append(dict(scene=sc, q0=sc["q0"], H=H, R=R, G=10, seed=seed + 7919 * i, nv=nv))
     return reqs
 

@@ -223,7 +223,10 @@ typedef struct {
 } cs_mpc_config;
 
 typedef struct {
-  cs_params params;         /* scene and solver settings (real_bytes, max_* are ignored)      */
+  cs_params params;         /* scene and solver settings (real_bytes, max_* are ignored;
+                               checkpoint_every = 0: the server picks the smallest interval
+                               whose candidates' records fit in an eighth of its memory
+                               budget, at most about sqrt(H))                                 */
   const double* rest_x;     /* HOST [n_nodes][3] rest positions                               */
   const double* q0;         /* HOST [n_q] state to plan from                                  */
   const double* warm;       /* HOST [H][6] warm start, or NULL: the session's previous plan

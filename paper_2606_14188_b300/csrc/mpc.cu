@@ -220,8 +220,8 @@ cs_status check_request(const cs_mpc* m, const cs_mpc_request* q) {
     if (t != CS_PLANE && t != CS_SPHERE && t != CS_BOX) return cs_fail(CS_ERR_INVALID_ARG, "unknown obstacle type");
   }
   if (!(P.dt > 0) || !(P.node_mass > 0)) return cs_fail(CS_ERR_INVALID_ARG, "dt and node_mass must be > 0");
-  if (P.checkpoint_every < 1 || P.newton_max < 1 || P.ipm_max < 1)
-    return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every and iteration caps must be >= 1");
+  if (P.checkpoint_every < 0 || P.newton_max < 1 || P.ipm_max < 1)
+    return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every must be >= 0 and iteration caps >= 1");
   if (!(P.kappa_decay > 0 && P.kappa_decay < 1)) return cs_fail(CS_ERR_INVALID_ARG, "kappa_decay must be in (0,1)");
   if (!(P.kappa_c > 0) || !(P.kappa_hard > 0) || P.kappa_hard > P.kappa_c)
     return cs_fail(CS_ERR_INVALID_ARG, "need 0 < kappa_hard <= kappa_c");
@@ -913,7 +913,16 @@ cs_status mpc_submit(cs_mpc* m, const cs_mpc_request* req, uint64_t* ticket) {
   q->q0.assign(req->q0, req->q0 + q->nq);
   if (req->warm) q->warm.assign(req->warm, req->warm + 6 * (size_t)req->H);
   q->r.rest_x = q->r.q0 = q->r.warm = nullptr;
-  q->lay = make_layout(q->nv, req->H, req->R, req->params.checkpoint_every, m->rb, l1_n);
+  if (q->r.params.checkpoint_every == 0) {
+    // automatic: the smallest interval whose candidates' records fit in an eighth of the memory
+    // budget, at most about sqrt(H); the result is the same for every interval, only the
+    // recomputed steps and the memory differ
+    const int kmax = std::max(1, (int)std::lround(std::sqrt((double)req->H)));
+    int k = 1;
+    while (k < kmax && make_layout(q->nv, req->H, req->R, k, m->rb, l1_n).total > m->arena_bytes / 8) ++k;
+    q->r.params.checkpoint_every = k;
+  }
+  q->lay = make_layout(q->nv, req->H, req->R, q->r.params.checkpoint_every, m->rb, l1_n);
   if (q->lay.total > m->arena_bytes) return cs_fail(CS_ERR_INVALID_ARG, "request larger than the memory budget");
   if (q->lay.h_total > m->pinned_bytes) return cs_fail(CS_ERR_INVALID_ARG, "request larger than the staging memory");
   q->t_submit = now_ns();
