@@ -193,3 +193,22 @@ def test_plan_rope_and_cloth_mixed_bit_identical():
         _same(a, b)
     assert all(m["status"] == 0 for m in mixed[3:])
     assert st["graph_launches"] >= 1
+
+
+def test_plan_server_picked_checkpoint_interval_gives_the_same_plan():
+    """A request that leaves the checkpoint interval to the server (checkpoint_every = 0; with
+    room, every step is recorded) returns the plan of the same request checkpointing every 4
+    steps, bit for bit."""
+    import copy
+    sc = scenes.rope_scene(24, n_spheres=1, n_boxes=1, seed=71)
+    H, R, G = 16, 64, 3
+    outs = []
+    for k in (4, 0):
+        s2 = copy.deepcopy(sc)
+        s2["params"]["checkpoint_every"] = k
+        with _server(real_bytes=4) as srv:
+            outs.append(srv.poll(srv.submit(s2, s2["q0"], H, R, G, seed=5)))
+    a, b = outs
+    assert a["status"] == b["status"] and a["best_iter"] == b["best_iter"]
+    assert a["best_candidate"] == b["best_candidate"] and a["L"] == b["L"]
+    assert np.array_equal(a["u"], b["u"])
