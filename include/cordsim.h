@@ -88,7 +88,11 @@ typedef struct {
   int newton_max, ipm_max;  /* iteration caps                                                */
   double newton_tol;        /* stage-1 stop: max |Newton step| <= newton_tol [m]             */
   double ipm_tol;           /* stage-2 stop: max |Newton step| <= ipm_tol [m]                */
-  int checkpoint_every;     /* adjoint checkpoint interval k (>= 1)                          */
+  int checkpoint_every;     /* adjoint checkpoint interval k (>= 1; 0 in sim_create: the
+                               smallest interval whose adjoint workspace fits in a quarter of
+                               the free device memory, at most about sqrt(max_horizon); 0 in
+                               an mpc request: see cs_mpc_request; sim_rollout_vjp_noalloc
+                               needs k >= 1)                                                  */
   int real_bytes;           /* 4 = FP32, 8 = FP64                                            */
   int max_batch, max_horizon; /* size the handle's workspace                                 */
 } cs_params;

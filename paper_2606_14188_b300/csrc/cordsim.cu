@@ -2,6 +2,7 @@
 // Every entry point is declared (with its contract) in include/cordsim.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -68,7 +69,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
       return cs_fail(CS_ERR_INVALID_ARG, "unknown obstacle type");
   }
   if (!(P->dt > 0) || !(P->node_mass > 0)) return cs_fail(CS_ERR_INVALID_ARG, "dt and node_mass must be > 0");
-  if (P->checkpoint_every < 1) return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every must be >= 1");
+  if (P->checkpoint_every < 0) return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every must be >= 0");
   if (P->max_batch < 1 || P->max_horizon < 1) return cs_fail(CS_ERR_INVALID_ARG, "max_batch/max_horizon must be >= 1");
   if (P->newton_max < 1 || P->ipm_max < 1) return cs_fail(CS_ERR_INVALID_ARG, "iteration caps must be >= 1");
   if (!(P->kappa_decay > 0 && P->kappa_decay < 1)) return cs_fail(CS_ERR_INVALID_ARG, "kappa_decay must be in (0,1)");
@@ -129,10 +130,24 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
     sim_destroy(s);
     return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "rest lengths") : cs_cuda_fail(e, "upload");
   }
-  const int k = P->checkpoint_every;
+  auto ws_elems = [&](int kk) {
+    return cloth ? cs::cloth_vjp_ws_elems(nv, P->max_horizon, kk) : cs::vjp_ws_elems(nv, P->max_horizon, kk);
+  };
+  if (s->P.checkpoint_every == 0) {
+    // automatic: the smallest interval whose adjoint workspace fits in a quarter of the free
+    // device memory, at most about sqrt(max_horizon) (the adjoint is the same for every
+    // interval; a shorter one recomputes fewer steps)
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const int kmax = std::max(1, (int)std::lround(std::sqrt((double)P->max_horizon)));
+    int kk = 1;
+    while (kk < kmax && vjp_ws_bytes(ws_elems(kk), P->max_batch, rb) > free_b / 4) ++kk;
+    s->P.checkpoint_every = kk;
+  }
+  const int k = s->P.checkpoint_every;
   // checkpoint records (state, grasp offsets, stage-1 offset and stage-2 displacement of the
   // producing step) and the carry of the two-part launch
-  s->ws_stride = cloth ? cs::cloth_vjp_ws_elems(nv, P->max_horizon, k) : cs::vjp_ws_elems(nv, P->max_horizon, k);
+  s->ws_stride = ws_elems(k);
   e = cudaMalloc(&s->d_ws, vjp_ws_bytes(s->ws_stride, P->max_batch, rb));
   if (e != cudaSuccess) {
     sim_destroy(s);

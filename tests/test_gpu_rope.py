@@ -159,17 +159,22 @@ def test_rope64_two_part_launch_equals_one_launch():
 
 def test_rope64_checkpoint_interval_does_not_change_the_adjoint():
     """The recomputed segment steps reproduce the forward's steps exactly, so the adjoint with a
-    record at every step (k = 1, no recompute) equals the one with k = 7, bit for bit."""
+    record at every step (k = 1, no recompute) and with the interval sim_create picks (k = 0)
+    equals the one with k = 7, bit for bit."""
     import copy
     B = 8
     w, sc, q0, U = _rope64(B)
     sc1 = copy.deepcopy(sc)
     sc1["params"]["checkpoint_every"] = 1
+    sc0 = copy.deepcopy(sc)
+    sc0["params"]["checkpoint_every"] = 0          # picked by sim_create from the free memory
     a = _sim(sc, 4, B, 50).rollout_vjp(_t(q0, 4), _t(U, 4))
     b = _sim(sc1, 4, B, 50).rollout_vjp(_t(q0, 4), _t(U, 4))
+    c = _sim(sc0, 4, B, 50).rollout_vjp(_t(q0, 4), _t(U, 4))
     assert sc["params"]["checkpoint_every"] == 7
-    for x, y in zip(a, b):
+    for x, y, z in zip(a, b, c):
         assert torch.equal(x.isnan(), y.isnan()) and torch.equal(x.nan_to_num(), y.nan_to_num())
+        assert torch.equal(x.isnan(), z.isnan()) and torch.equal(x.nan_to_num(), z.nan_to_num())
 
 
 def test_rope64_deterministic():
