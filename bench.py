@@ -407,7 +407,9 @@ def served_leg(args):
            f"log-U{{64..1024}})"
     if ncloth:
         what += f", {ncloth} cloths (side U{{8..16}}, horizon U{{10..20}}, candidates log-U{{32..128}})"
-    res = dict(workload=what + ", 10 evaluations each, FP32",
+    res = dict(workload=what + ", 10 evaluations each, FP32, checkpoint interval picked by the server "
+                                "(checkpoint_every = 0: the shortest whose records fit in an eighth of "
+                                "its memory budget)",
                requests=n, node_steps=node_steps, capacity_solves_per_s=cap,
                capacity_node_steps_per_s=node_steps / t_cap)
 
