@@ -91,7 +91,11 @@ def _stream():
 
 
 class Sim:
-    """One scene on the GPU: sim_create / sim_rollout / sim_rollout_vjp / sim_linearize."""
+    """One scene on the GPU: sim_create / sim_rollout / sim_rollout_vjp / sim_linearize.
+
+    The adjoint's checkpoint interval is the scene's params["checkpoint_every"] (1 when absent:
+    every step recorded, nothing recomputed; 0: the library picks the shortest interval whose
+    workspace fits in a quarter of the free device memory).  The gradients do not depend on it."""
 
     def __init__(self, scene: dict, real_bytes: int = 4, max_batch: int = 1, max_horizon: int = 1,
                  **overrides):
