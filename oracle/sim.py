@@ -530,7 +530,6 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
         return Delta, np.zeros((nv, 0, 3)), 0, 0
     A = cone_frames(n, mu)
     P_ab = stage1_hessian_band(sc, xs, d)
-    projected = False       # P falls back to the projected spring Hessian if H2 is not PD
     e1 = np.zeros((nv, no, 3)); e1[..., 0] = 1.0
     # interior start: the per-node closed form along each penetrating normal, then s from it
     # where it lies well inside Q, else (max(phi, sigma0), 0, 0); z central for that s
@@ -548,7 +547,7 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
     centring = False        # the target has reached kappa_final
     for it in range(maxit):
         lam_w = np.einsum("joab,joa->job", A, z)
-        r_d = stage1_hessian_vec(sc, xs, d, Delta, projected) - lam_w.sum(axis=1)
+        r_d = stage1_hessian_vec(sc, xs, d, Delta) - lam_w.sum(axis=1)
         r_z = s - np.einsum("joab,jb->joa", A, Delta) - phi[..., None] * e1
         W, Winv, lam = nt_scaling(s, z)
         M = Winv @ Winv
@@ -558,19 +557,10 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
         try:
             cb = band_factor(ab)
         except LinAlgError:
-            if projected:
-                return Delta, None, it, ST_NOTPD
-            # stage 1 ended where d^2E is indefinite: use the Hessian with each spring's
-            # transverse factor clamped at 0 (as stage 1 does), for the rest of this solve
-            projected = True
-            P_ab = stage1_hessian_band(sc, xs, d, project=True)
-            r_d = r_d - stage1_hessian_vec(sc, xs, d, Delta) + stage1_hessian_vec(sc, xs, d, Delta, True)
-            ab = P_ab.copy()
-            band_add_node_blocks(sc, ab, np.arange(nv), AMA.sum(axis=1))
-            try:
-                cb = band_factor(ab)
-            except LinAlgError:
-                return Delta, None, it, ST_NOTPD
+            # H2 = P + sum A^T M A is not positive definite, so neither is P: the stage-1 root is
+            # not a minimiser of its potential and the QP of eq. (dynamics-second-stage) is not
+            # convex; the step has no defined contact solution
+            return Delta, None, it, ST_NOTPD
 
         def direction(d_s):
             # W^{-1} ds + W dz = d_s, ds = A dDelta - r_z, P dDelta - sum A^T dz = -r_d

@@ -344,13 +344,13 @@ __device__ int cl_stage2(const Scene<R>& S, const ClothDims& D, const ClothWS<R>
   }
   __syncthreads();
   int stalls = 0;
-  bool proj = false, centring = false;
+  const bool proj = false;    // stage 2 uses the exact P
+  bool centring = false;
   for (int it = 0; it < S.ipm_max; ++it) {
     const bool pc = kfinal >= R(0) && !centring;
     R target = kfinal < R(0) ? kappa : kfinal;
     // assemble H2 = P + sum A^T M A and -P D + sum A^T (z + M g), g = r_z + W d_s (affine when pc)
-    bool ok = false;
-    for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+    {
       for (int v = threadIdx.x; v < nv; v += CL_NT) {
         R Dv[9], PD[3];
         cl_node_P(S, D, w, c.misc, v, proj, Dv, w.Dl, PD);
@@ -397,13 +397,9 @@ __device__ int cl_stage2(const Scene<R>& S, const ClothDims& D, const ClothWS<R>
         for (int i = 0; i < 3; ++i) { c.vb[3 * v + i] = rhs[i]; w.rA[3 * v + i] = rhs[i]; }
       }
       __syncthreads();
-      ok = cl_factor_w(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, proj}, w, c.sm);
-      if (!ok) {
-        // H2 not positive definite with the exact P: the projected spring Hessian for the rest
-        // of this solve
-        if (proj) { *iters = it + 1; return ST_NOTPD; }
-        proj = true;
-      }
+      // H2 not positive definite means P is not either (the stage-1 root is not a minimiser of
+      // its potential, and the QP of eq. dynamics-second-stage is not convex): no contact solution
+      if (!cl_factor_w(S, D, BandSrc<R>{w.x0, w.dx, w.Dg, proj}, w, c.sm)) { *iters = it + 1; return ST_NOTPD; }
     }
     cl_back(D, w.Lg, c.sm);
     for (int i = threadIdx.x; i < N; i += CL_NT) w.pv[i] = c.vb[i];

@@ -648,7 +648,7 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
     }
   }
   int stalls = 0;
-  bool proj = false;
+  const bool proj = false;    // stage 2 uses the exact P
   bool centring = false;      // the target has reached kfinal: plain centring steps from now on
   for (int it = 0; it < S.ipm_max; ++it) {
     // predictor-corrector iteration (towards kfinal, not yet centring): assemble with the affine
@@ -657,10 +657,10 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
     R target = kfinal < R(0) ? kappa : kfinal;
     R Dlm[PPL][6], Dlp[PPL][6];
     nbr<R, PPL>(L.Dl, Dlm, Dlp, lane);
-    // assemble H2 and the right-hand side -P D + sum A^T (z + M g), g = r_z + W d_s.  If H2 is
-    // not positive definite with the exact P (stage 1 ended where d^2E is indefinite), P becomes
-    // the projected spring Hessian for the rest of this solve.
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    // assemble H2 and the right-hand side -P D + sum A^T (z + M g), g = r_z + W d_s.  H2 not
+    // positive definite means P is not either (the stage-1 root is not a minimiser of its
+    // potential, and the QP of eq. dynamics-second-stage is not convex): no contact solution.
+    {
 #pragma unroll
       for (int k = 0; k < PPL; ++k) {
         const int p = lane + 32 * k;
@@ -713,9 +713,7 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
         put_rows(w, p, T, Bc);
       }
       __syncwarp();
-      if (cr_factor(w.T, w.B, w.V, S.npair, lane)) break;
-      if (proj) { *iters = it + 1; return ST_NOTPD; }
-      proj = true;
+      if (!cr_factor(w.T, w.B, w.V, S.npair, lane)) { *iters = it + 1; return ST_NOTPD; }
     }
     cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
     get_rhs<R, PPL>(S, w, L.pv, lane);            // dDelta (affine when pc)

@@ -700,3 +700,203 @@ def _dense_from_band(ab):
         A[i + k, i] = ab[k, : n - k]
         A[i, i + k] = ab[k, : n - k]
     return A
+
+
+# ------------------------------------------------------------------------------------------
+# grasp stiffness values, the planning loss value, the surrogate composition, the stage-1 start
+# ------------------------------------------------------------------------------------------
+
+def test_grasp_stiffness_values():
+    """Sec. 4.1 Contact Smoothing: the smooth grasp stiffness D_max exp(-|c|/kappa) and the
+    indicator-like nonsmooth one D_max 1[|c| <= r_grasp], at hand-chosen offsets (D_max 1e4 N/m,
+    kappa_h 0.01 m, r_grasp 0.01 m): |c| = 0.005 m gives 1e4 e^(-1/2) = 6065.306597126334,
+    |c| = 0.01 m gives 1e4 e^(-1) = 3678.7944117144234 and |c| = 0.0101 m 1e4 e^(-1.01) =
+    3642.1897957152332 (a grasp smoothed with kappa_c = 1e-4, or with |c|^2, gives other values)."""
+    p = scenes.default_params("rope")
+    p.update(n_nodes=2, node_mass=0.01, grasp_nodes=(0, 1), D_max=1e4, kappa_h=0.01, r_grasp=0.01)
+    sc = sim.Scene(p, np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]]))
+    c = np.array([[0.003, 0.004, 0.0], [0.0, 0.006, 0.008], [0.0, 0.0, 0.0101]])
+    np.testing.assert_allclose(sim.grasp_stiffness_of_c(sc, c, sim.SMOOTH),
+                               [6065.306597126334, 3678.7944117144234, 3642.1897957152332], rtol=1e-14)
+    np.testing.assert_array_equal(sim.grasp_stiffness_of_c(sc, c, sim.HARD), [1e4, 1e4, 0.0])
+
+
+def test_smooth_grasp_spring_closed_form():
+    """The smooth stiffness enters stage 1 at the old state (eq. dynamics-first-stage uses c_i(q)):
+    one free node, gripper offset c = (0.003, 0.004, 0) (|c| = 0.005 m), D_max = 300 N/m,
+    kappa_h = 0.01 m, so d = 300 e^(-1/2); then x+ = (w x + d (g + u) + m grav)/(w + d) =
+    (0.0025813550224302265, 0.00387203253364534, 0.49771606105242844) for w = 100."""
+    m, dt, D = 0.01, 0.01, 300.0
+    X0 = np.array([[0.0, 0.0, 0.5], [1.0, 0.0, 0.5]])
+    g0 = np.array([[0.003, 0.004, 0.5], [9.0, 9.0, 9.0]])
+    sc, q = rope(2, X0, k_s=0.0, k_b=0.0, D=D, m=m, dt=dt, grippers=g0)
+    sc.p["kappa_h"] = 0.01
+    u = np.array([0.001, 0.002, -0.003, 0.0, 0.0, 0.0])
+    qp, st = sim.step(sc.__class__({**sc.p, "obstacles": []}, X0), q, u, sim.SMOOTH)
+    x, _ = sim.split_q(sc, qp)
+    np.testing.assert_allclose(x[0], [0.0025813550224302265, 0.00387203253364534, 0.49771606105242844],
+                               rtol=0, atol=1e-15)
+
+
+def _loss_scene():
+    """Three nodes, a table plane z = 0 and a sphere (centre 0, radius 0.1 m); node radius 5 mm,
+    margin 0.02 m, w_pen 100, goal node 2 at (0.5, 0, 0.3) with w_goal 1, w_u 0.01."""
+    X0 = np.array([[0.0, 0.0, 1.0], [0.3, 0.0, 1.0], [0.6, 0.0, 1.0]])
+    sc, _ = rope(3, X0, obstacles=[scenes.plane(), scenes.sphere((0.0, 0.0, 0.0), 0.1)])
+    sc.p["loss"] = dict(goal_nodes=(2,), goal_pos=np.array([[0.5, 0.0, 0.3]]), w_goal=1.0,
+                        w_pen=100.0, pen_margin=0.02, w_u=0.01)
+    g = np.zeros(6)
+    traj = np.array([
+        np.concatenate([[0.105, 0, 0], [1, 0, 1], [2, 0, 1], g]),         # t = 0: not penalised
+        np.concatenate([[0, 0.11, 0], [0, 0, -0.12], [1, 1, 1], g]),      # t = 1: node 1 below the table
+        np.concatenate([[1, 0, 1], [0.3, 0, 0.4], [0.5, 0.1, 0.2], g]),   # t = 2 = H: goal error
+    ], dtype=np.float64)
+    U = np.array([[0.01, 0, 0, 0, 0.02, 0], [0, 0, 0, 0, 0, 0.03]], dtype=np.float64)
+    return sc, traj, U
+
+
+def test_loss_value_by_hand():
+    """The planning loss on a 3-node, 2-step trajectory computed by hand:
+      t = 1 node 0: phi_sphere = 0.11 - 0.1 - 0.005 = 0.005, 100 (0.02 - 0.005)^2 = 0.0225;
+      t = 1 node 1: phi_sphere = 0.12 - 0.105 = 0.015, 100 (0.02 - 0.015)^2 = 0.0025
+                    (its plane term, 100 (0.02 + 0.125)^2 = 2.1025, is excluded);
+      t = 0 node 0 touches the sphere (0.04 if t = 0 were penalised): excluded;
+      goal: |(0.5, 0.1, 0.2) - (0.5, 0, 0.3)|^2 = 0.02;  effort: 0.01 (1e-4 + 4e-4 + 9e-4) = 1.4e-5.
+    L = 0.045014; seeds dL/dx_0(1) = -2 100 0.015 (0, 1, 0), dL/dx_1(1) = -2 100 0.005 (0, 0, -1),
+    dL/dx_2(2) = 2 (0, 0.1, -0.1), dL/du = 0.02 u."""
+    sc, traj, U = _loss_scene()
+    L, seeds, dU = grad.loss_and_seeds(sc, traj, U)
+    assert abs(L - 0.045014) < 1e-15
+    expect = np.zeros_like(traj)
+    expect[1, 0:3] = [0.0, -3.0, 0.0]
+    expect[1, 3:6] = [0.0, 0.0, 1.0]
+    expect[2, 6:9] = [0.0, 0.2, -0.2]
+    np.testing.assert_allclose(seeds, expect, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(dU, 0.02 * U, rtol=0, atol=0)
+
+
+def _contact_rope6():
+    """Six nodes along x at z = 0.3 m, ends held, resting on a sphere (centre (0.125, 0, 0.2),
+    radius 0.1 m) that the middle nodes penetrate by about 2 mm: a contact step from t = 0."""
+    X0 = np.stack([np.linspace(0.0, 0.25, 6), np.zeros(6), np.full(6, 0.3)], axis=1)
+    sc, q = rope(6, X0, m=0.1 / 6, obstacles=[scenes.plane(), scenes.sphere((0.125, 0.0, 0.2), 0.1)])
+    sc.p["loss"] = dict(goal_nodes=(2, 3), goal_pos=X0[[2, 3]] + [0.0, 0.0, 0.05], w_goal=1.0,
+                        w_pen=100.0, pen_margin=0.02, w_u=0.01)
+    U = np.array([[0.002, 0, 0.003, -0.001, 0, 0.002],
+                  [0.001, 0.001, 0.002, 0, -0.001, 0.003],
+                  [0, 0.002, 0.001, 0.001, 0, 0.002]], dtype=np.float64)
+    return sc, q, U
+
+
+def test_surrogate_gradient_is_the_smooth_step_chain_at_the_hard_states():
+    """The surrogate gradient (Sec. 4.1 Contact Smoothing): the nonsmooth rollout's loss,
+    differentiated with the SMOOTH step's Jacobians evaluated at the NONSMOOTH trajectory's
+    states.  Here those Jacobians come from central differences of the smooth step map at each
+    (q_t, u_t) of the nonsmooth rollout (no implicit differentiation), chained by hand:
+      lam_H = dL/dq_H;  dL/du_t = B_t^T lam_{t+1} + dL_u/du_t;  lam_t = A_t^T lam_{t+1} + dL/dq_t.
+    The consistent gradient (smooth forward) differs from it by far more than the tolerance, so
+    evaluating the Jacobians on the smooth trajectory, or one step off, fails."""
+    sc, q0, U = _contact_rope6()
+    H = U.shape[0]
+    r = grad.rollout_vjp(sc, q0, U, "surrogate")
+    traj, st, _ = sim.rollout(sc, q0, U, sim.HARD)
+    assert st == 0 and r["status"] == 0
+    phi, _ = sim.contact_geometry(sc, sim.split_q(sc, traj[1])[0])
+    assert np.min(phi) < 0.05 * sc.p["node_radius"]          # the rollout is in contact
+    L, seeds, dU = grad.loss_and_seeds(sc, traj, U)
+    assert abs(L - r["L"]) < 1e-14
+    h = 1e-6
+    lam = seeds[H].copy()
+    g_u = np.zeros_like(U)
+    for t in range(H - 1, -1, -1):
+        info = {}
+        sim.step(sc, traj[t], U[t], sim.SMOOTH, info=info)
+        xs0 = info["xs"]
+
+        def f(qq, uu):
+            return sim.step(sc, qq, uu, sim.SMOOTH, x_start=xs0)[0]
+
+        A = np.zeros((sc.nq, sc.nq))
+        for k in range(sc.nq):
+            e = np.zeros(sc.nq); e[k] = h
+            A[:, k] = (f(traj[t] + e, U[t]) - f(traj[t] - e, U[t])) / (2 * h)
+        Bm = np.zeros((sc.nq, 6))
+        for k in range(6):
+            e = np.zeros(6); e[k] = h
+            Bm[:, k] = (f(traj[t], U[t] + e) - f(traj[t], U[t] - e)) / (2 * h)
+        g_u[t] = Bm.T @ lam + dU[t]
+        lam = A.T @ lam + seeds[t]
+    scale = np.max(np.abs(g_u))
+    assert np.max(np.abs(g_u - r["dL_du"])) < 2e-6 * scale, (g_u, r["dL_du"])
+    rc = grad.rollout_vjp(sc, q0, U, "consistent")
+    assert np.max(np.abs(rc["dL_du"] - r["dL_du"])) > 1e-3 * scale
+
+
+def test_surrogate_equals_consistent_without_contact_in_the_grasp_limit():
+    """No obstacles and the grasp held (|c| stays far below r_grasp): with kappa_h large the
+    smooth grasp stiffness equals D_max to 1e-9 and its slope is negligible, so the smooth and
+    nonsmooth models coincide and the surrogate gradient must equal the consistent (exact)
+    gradient of the same rollout."""
+    X0 = np.stack([np.linspace(0.0, 0.3, 6), np.zeros(6), np.full(6, 0.3)], axis=1)
+    sc, q0 = rope(6, X0, m=0.1 / 6)
+    sc.p["kappa_h"] = 1e6
+    sc.p["loss"] = dict(goal_nodes=(2, 3), goal_pos=X0[[2, 3]] + [0.0, 0.0, 0.05], w_goal=1.0,
+                        w_pen=100.0, pen_margin=0.02, w_u=0.01)
+    U = scenes.controls_normal(1, 5, sigma=0.005, seed=7)[0]
+    rs = grad.rollout_vjp(sc, q0, U, "surrogate")
+    rc = grad.rollout_vjp(sc, q0, U, "consistent")
+    assert rs["status"] == 0 and rc["status"] == 0
+    for t in range(U.shape[0] + 1):
+        c = sim.grasp_offsets(sc, *sim.split_q(sc, rs["traj"][t]))
+        assert np.max(np.linalg.norm(c, axis=1)) < 0.1 * sc.p["r_grasp"]
+    assert abs(rs["L"] - rc["L"]) < 1e-12
+    scale = np.max(np.abs(rc["dL_du"]))
+    assert np.max(np.abs(rs["dL_du"] - rc["dL_du"])) < 1e-8 * scale
+    np.testing.assert_allclose(rs["dL_dq0"], rc["dL_dq0"], rtol=0, atol=1e-8 * np.max(np.abs(rc["dL_dq0"])))
+
+
+def _stage1_from(sc, q, u, moved):
+    x, g = sim.split_q(sc, q)
+    gstar = g + np.asarray(u).reshape(2, 3)
+    d = sim.grasp_stiffness(sc, x, g, sim.HARD)
+    xs0 = x.copy()
+    if moved:
+        for i in range(2):
+            xs0[sc.grasp[i]] += gstar[i] - g[i]
+    xs, _, st = sim.stage1_solve(sc, x, gstar, d, maxit=2000, x_start=xs0)
+    try:
+        sim.band_factor(sim.stage1_hessian_band(sc, xs, d))
+        pd = True
+    except Exception:
+        pd = False
+    return xs, st, pd
+
+
+def test_stage1_start_reaches_the_minimising_root():
+    """Which root stage 1 returns (Sec. 4.1: "solved using Newton's method", start unstated).
+    The start is q with each grasped node moved with its gripper: the start at which the grasp
+    offsets c_i are those of q, i.e. the linearised holonomic constraint J_i (q* - q) + c_i(q) =
+    c_i(q) holds.  On the 1024 x 64-node rope workload, Newton from q itself ends at the first step
+    of rollouts 267, 384 and 727 at a saddle of the stage-1 potential (dF/dq* indefinite: the
+    chain compressed between a moved gripper and its unmoved node), where the QP of eq.
+    dynamics-second-stage is not convex and eq. diff-sim is not defined; from the moved start it
+    reaches a root with dF/dq* positive definite.  On sampled rollouts, wherever the start at q
+    reaches a minimising root, both starts reach the same root to 1e-10 (all 50 steps)."""
+    wl = scenes.workload(2)
+    sc = sim.Scene(wl["scene"]["params"], wl["scene"]["rest_x"])
+    U, q0 = wl["U"], wl["q0"]
+    for b in (267, 384, 727):
+        xa, sa, pda = _stage1_from(sc, q0[b], U[b, 0], moved=False)
+        xb, sb, pdb = _stage1_from(sc, q0[b], U[b, 0], moved=True)
+        assert sa == 0 and sb == 0
+        assert not pda and pdb, b
+        assert np.max(np.abs(xa - xb)) > 1e-4
+    for b in (0, 100, 521):
+        q = q0[b]
+        for t in range(U.shape[1]):
+            xa, sa, pda = _stage1_from(sc, q, U[b, t], moved=False)
+            xb, sb, pdb = _stage1_from(sc, q, U[b, t], moved=True)
+            assert sb == 0 and pdb
+            if pda:
+                assert np.max(np.abs(xa - xb)) < 1e-10, (b, t)
+            q, _ = sim.step(sc, q, U[b, t], sim.HARD)
