@@ -186,8 +186,12 @@ cs_status sim_linearize(cs_sim* sim, int B, int H, const void* z, const void* v,
  *   - All calls share the array and it keeps the last call's contents; nothing in it needs to
  *     start at zero (each call writes every element it reads).  Calls that overlap on the GPU
  *     (different streams, or different host threads on one device) race on it.
+ *   - The rest lengths reach the device through a small kernel launched on `stream` that carries
+ *     them in its argument; no host-to-device copy is issued.
  *   - Errors: CS_ERR_INVALID_ARG when the checkpoint records of B rollouts of H steps do not fit
- *     in CS_NOALLOC_SCRATCH_BYTES, plus the errors of sim_create and sim_rollout_vjp. */
+ *     in CS_NOALLOC_SCRATCH_BYTES, checkpoint_every < 1, and the argument errors of sim_create
+ *     (parameters) and sim_rollout_vjp (loss, sizes, pointers), checked before any device call;
+ *     CS_ERR_UNSUPPORTED for a cloth. */
 #define CS_NOALLOC_SCRATCH_BYTES (48u << 20)
 cs_status sim_rollout_vjp_noalloc(const cs_params* params, const double* rest_x, int B, int H,
                                   const void* q0, const void* u, const void* dL_dtraj,
@@ -241,6 +245,10 @@ typedef struct {
   uint64_t seed;
   uint64_t session_id;      /* nonzero: keep this plan on the device for the session's next
                                request                                                        */
+  int deadline_ms;          /* 0: none.  > 0: a request still queued or running this long after
+                               mpc_submit leaves at the next tick boundary (its device work
+                               stops there, nothing waits on the device) and mpc_poll returns
+                               CS_ERR_TIMEOUT for it                                          */
 } cs_mpc_request;
 
 typedef struct {
@@ -261,8 +269,9 @@ cs_status mpc_create(const cs_mpc_config* config, cs_mpc** out);
  * sim_create, a request larger than the memory budget). */
 cs_status mpc_submit(cs_mpc* mpc, const cs_mpc_request* req, uint64_t* ticket);
 /* Wait up to timeout_ms (0: do not wait, < 0: no limit) for a result.  CS_OK fills `out` and
- * forgets the ticket; CS_ERR_PENDING if it is not done yet; CS_ERR_CANCELLED; CS_ERR_INVALID_ARG
- * for an unknown ticket; CS_ERR_CUDA if the server's stream failed. */
+ * forgets the ticket; CS_ERR_PENDING if it is not done yet; CS_ERR_CANCELLED; CS_ERR_TIMEOUT when
+ * the request's deadline_ms passed before it finished (the ticket is then forgotten);
+ * CS_ERR_INVALID_ARG for an unknown ticket; CS_ERR_CUDA if the server's stream failed. */
 cs_status mpc_poll(cs_mpc* mpc, uint64_t ticket, int timeout_ms, cs_mpc_result* out);
 /* Cancel a queued or running solve (a running one stops at the next tick boundary). */
 cs_status mpc_cancel(cs_mpc* mpc, uint64_t ticket);

@@ -63,7 +63,7 @@ class cs_mpc_request(C.Structure):
                 ("q0", C.POINTER(C.c_double)), ("warm", C.POINTER(C.c_double)), ("loss", cs_loss),
                 ("H", C.c_int), ("R", C.c_int), ("G", C.c_int),
                 ("lr", C.c_double), ("sigma", C.c_double), ("u_max", C.c_double),
-                ("seed", C.c_uint64), ("session_id", C.c_uint64)]
+                ("seed", C.c_uint64), ("session_id", C.c_uint64), ("deadline_ms", C.c_int)]
 
 
 class cs_mpc_result(C.Structure):

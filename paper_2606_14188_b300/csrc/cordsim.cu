@@ -43,11 +43,8 @@ static cs_status check_common(cs_sim* s, int B, int H) {
 }
 
 
-extern "C" {
-
-cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
-  if (!P || !rest_x || !out) return cs_fail(CS_ERR_INVALID_ARG, "null argument");
-  *out = nullptr;
+cs_status cs_validate_params(const cs_params* P) {
+  if (!P) return cs_fail(CS_ERR_INVALID_ARG, "null params");
   if (P->kind != CS_ROPE && P->kind != CS_CLOTH) return cs_fail(CS_ERR_INVALID_ARG, "unknown kind");
   const bool cloth = P->kind == CS_CLOTH;
   const int nv = P->n_nodes;
@@ -69,12 +66,33 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
       return cs_fail(CS_ERR_INVALID_ARG, "unknown obstacle type");
   }
   if (!(P->dt > 0) || !(P->node_mass > 0)) return cs_fail(CS_ERR_INVALID_ARG, "dt and node_mass must be > 0");
-  if (P->checkpoint_every < 0) return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every must be >= 0");
-  if (P->max_batch < 1 || P->max_horizon < 1) return cs_fail(CS_ERR_INVALID_ARG, "max_batch/max_horizon must be >= 1");
   if (P->newton_max < 1 || P->ipm_max < 1) return cs_fail(CS_ERR_INVALID_ARG, "iteration caps must be >= 1");
   if (!(P->kappa_decay > 0 && P->kappa_decay < 1)) return cs_fail(CS_ERR_INVALID_ARG, "kappa_decay must be in (0,1)");
   if (!(P->kappa_c > 0) || !(P->kappa_hard > 0) || P->kappa_hard > P->kappa_c)
     return cs_fail(CS_ERR_INVALID_ARG, "need 0 < kappa_hard <= kappa_c");
+  return CS_OK;
+}
+
+cs_status cs_validate_loss(const cs_loss* loss, int nv) {
+  if (!loss) return CS_OK;
+  if (loss->n_goal < 0 || loss->n_goal > CS_MAX_GOAL) return cs_fail(CS_ERR_INVALID_ARG, "n_goal out of range");
+  for (int g = 0; g < loss->n_goal; ++g)
+    if (loss->goal_nodes[g] < 0 || loss->goal_nodes[g] >= nv)
+      return cs_fail(CS_ERR_INVALID_ARG, "goal node out of range");
+  return CS_OK;
+}
+
+extern "C" {
+
+cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
+  if (!P || !rest_x || !out) return cs_fail(CS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  cs_status vr = cs_validate_params(P);
+  if (vr) return vr;
+  const bool cloth = P->kind == CS_CLOTH;
+  const int nv = P->n_nodes;
+  if (P->checkpoint_every < 0) return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every must be >= 0");
+  if (P->max_batch < 1 || P->max_horizon < 1) return cs_fail(CS_ERR_INVALID_ARG, "max_batch/max_horizon must be >= 1");
 
   cs_sim* s = new cs_sim();
   s->P = *P;
@@ -209,12 +227,7 @@ cs_status sim_rollout_vjp(cs_sim* s, int B, int H, const void* q0, const void* u
   if (r) return r;
   if (!dL_dtraj && !loss) return cs_fail(CS_ERR_INVALID_ARG, "give dL_dtraj or a loss");
   if (B > 0 && (!q0 || !u || !dL_du)) return cs_fail(CS_ERR_INVALID_ARG, "q0, u and dL_du are required");
-  if (loss) {
-    if (loss->n_goal < 0 || loss->n_goal > CS_MAX_GOAL) return cs_fail(CS_ERR_INVALID_ARG, "n_goal out of range");
-    for (int g = 0; g < loss->n_goal; ++g)
-      if (loss->goal_nodes[g] < 0 || loss->goal_nodes[g] >= s->nv)
-        return cs_fail(CS_ERR_INVALID_ARG, "goal node out of range");
-  }
+  if (loss && (r = cs_validate_loss(loss, s->nv))) return r;
   if (B == 0) return CS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (s->P.kind == CS_CLOTH)

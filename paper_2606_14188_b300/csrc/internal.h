@@ -16,6 +16,14 @@ cs_status cs_fail(cs_status s, const std::string& msg);
 cs_status cs_cuda_fail(cudaError_t e, const char* where);
 void cs_count_launch();
 
+// Argument checks shared by the entry points that take a cs_params or a cs_loss (sim_create,
+// sim_rollout_vjp, sim_rollout_vjp_noalloc): kind and sizes, grasp nodes (in range, distinct),
+// real type, obstacles, dt and node mass, iteration caps, barrier parameters.  The workspace
+// sizes (max_batch, max_horizon) and the checkpoint interval are checked by each caller.
+cs_status cs_validate_params(const cs_params* P);
+// n_goal within [0, CS_MAX_GOAL] and every goal node within [0, nv)
+cs_status cs_validate_loss(const cs_loss* loss, int nv);
+
 struct cs_sim {
   cs_params P;
   int nv, npair, nq;

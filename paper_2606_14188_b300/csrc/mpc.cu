@@ -136,9 +136,16 @@ struct Req {
   int warm_H = 0, warm_shift = 0;
   int ticks = 0;
   bool admitted = false, cancelled = false, done = false, released = false;
+  bool timed_out = false;          // left because its deadline passed (then cancelled too)
   cs_status err = CS_OK;
   int64_t t_submit = 0, t_start = 0, t_done = 0;
+  int64_t deadline_ns = 0;         // steady-clock time after which it leaves; 0: none
 };
+
+// a request whose deadline has passed at time `now` (steady clock, ns)
+inline bool deadline_passed(const Req& q, int64_t now) {
+  return q.deadline_ns > 0 && !q.cancelled && !q.done && now >= q.deadline_ns;
+}
 
 struct Session {
   size_t off = 0, bytes = 0;
@@ -599,6 +606,17 @@ void scheduler(cs_mpc* m) {
       std::unique_lock<std::mutex> lk(m->mu);
       m->cv.wait(lk, [&] { return m->stop || !m->pending.empty() || !m->running.empty(); });
       if (m->stop) break;
+      // deadlines: a queued or running request past its deadline leaves like a cancelled one
+      // (at this tick boundary) and its poll reports CS_ERR_TIMEOUT
+      {
+        const int64_t now = now_ns();
+        bool expired = false;
+        for (auto& q : m->running)
+          if (deadline_passed(*q, now)) { q->cancelled = q->timed_out = true; expired = true; }
+        for (auto& q : m->pending)
+          if (deadline_passed(*q, now)) { q->cancelled = q->timed_out = true; expired = true; }
+        if (expired) m->cv.notify_all();
+      }
       for (auto it = m->running.begin(); it != m->running.end();) {
         if ((*it)->cancelled) {
           dropped.push_back(*it);
@@ -925,7 +943,9 @@ cs_status mpc_submit(cs_mpc* m, const cs_mpc_request* req, uint64_t* ticket) {
   q->lay = make_layout(q->nv, req->H, req->R, q->r.params.checkpoint_every, m->rb, l1_n);
   if (q->lay.total > m->arena_bytes) return cs_fail(CS_ERR_INVALID_ARG, "request larger than the memory budget");
   if (q->lay.h_total > m->pinned_bytes) return cs_fail(CS_ERR_INVALID_ARG, "request larger than the staging memory");
+  if (req->deadline_ms < 0) return cs_fail(CS_ERR_INVALID_ARG, "deadline_ms must be >= 0");
   q->t_submit = now_ns();
+  if (req->deadline_ms > 0) q->deadline_ns = q->t_submit + (int64_t)req->deadline_ms * 1000000;
   {
     std::unique_lock<std::mutex> lk(m->mu);
     if (m->fatal) return cs_fail(m->fatal, "server failed: " + m->fatal_msg);
@@ -965,7 +985,9 @@ cs_status mpc_poll(cs_mpc* m, uint64_t ticket, int timeout_ms, cs_mpc_result* ou
   if (q->cancelled && !q->done) {
     if (!ready()) return cs_fail(CS_ERR_PENDING, "cancellation in progress");
     m->pinned_arena.release(q->poff, q->lay.h_total);
+    const bool timed_out = q->timed_out;
     m->tickets.erase(it);
+    if (timed_out) return cs_fail(CS_ERR_TIMEOUT, "deadline passed before the plan finished");
     return cs_fail(CS_ERR_CANCELLED, "cancelled");
   }
   if (!q->done) return cs_fail(CS_ERR_PENDING, "not done");

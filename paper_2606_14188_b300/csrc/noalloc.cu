@@ -44,21 +44,35 @@ cs_status scratch_address(void** out) {
   return CS_OK;
 }
 
+// the rest lengths travel in the kernel's argument (by value): no host buffer has to outlive the
+// call and no host-to-device copy is issued
+template <typename R>
+struct RestLengths {
+  R L1[128];   // stretch (j, j+1)
+  R L2[128];   // bend (j, j+2)
+};
+
+template <typename R>
+__global__ void noalloc_rest_kernel(RestLengths<R> a, R* dst1, R* dst2) {
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+    dst1[i] = a.L1[i];
+    dst2[i] = a.L2[i];
+  }
+}
+
 template <typename R>
 cs_status upload_rest(const double* rest_x, int nv, R* dst1, R* dst2, cudaStream_t st) {
-  R h[256];                                   // fixed host buffer: no host allocation either
-  for (int i = 0; i < 256; ++i) h[i] = R(0);
-  auto dist = [&](int a, int b) {
-    const double d0 = rest_x[3 * b] - rest_x[3 * a], d1 = rest_x[3 * b + 1] - rest_x[3 * a + 1],
-                 d2 = rest_x[3 * b + 2] - rest_x[3 * a + 2];
+  RestLengths<R> a;
+  for (int i = 0; i < 128; ++i) a.L1[i] = a.L2[i] = R(0);
+  auto dist = [&](int i, int j) {
+    const double d0 = rest_x[3 * j] - rest_x[3 * i], d1 = rest_x[3 * j + 1] - rest_x[3 * i + 1],
+                 d2 = rest_x[3 * j + 2] - rest_x[3 * i + 2];
     return std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
   };
-  for (int j = 0; j + 1 < nv; ++j) h[j] = (R)dist(j, j + 1);
-  for (int j = 0; j + 2 < nv; ++j) h[128 + j] = (R)dist(j, j + 2);
-  // pageable source: the copy has consumed h when cudaMemcpyAsync returns
-  cudaError_t e = cudaMemcpyAsync(dst1, h, 128 * sizeof(R), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dst2, h + 128, 128 * sizeof(R), cudaMemcpyHostToDevice, st);
-  return e == cudaSuccess ? CS_OK : cs_cuda_fail(e, "cudaMemcpyAsync");
+  for (int j = 0; j + 1 < nv; ++j) a.L1[j] = (R)dist(j, j + 1);
+  for (int j = 0; j + 2 < nv; ++j) a.L2[j] = (R)dist(j, j + 2);
+  noalloc_rest_kernel<R><<<1, 128, 0, st>>>(a, dst1, dst2);
+  return csi::check_launch("noalloc_rest_kernel");
 }
 
 }  // namespace
@@ -68,16 +82,14 @@ extern "C" cs_status sim_rollout_vjp_noalloc(const cs_params* P, const double* r
                                              const cs_loss* loss, void* L, void* dL_du, void* dL_dq0,
                                              int32_t* status, void* stream) {
   if (!P || !rest_x) return cs_fail(CS_ERR_INVALID_ARG, "null params or rest_x");
+  cs_status r = cs_validate_params(P);
+  if (r) return r;
   if (P->kind != CS_ROPE) return cs_fail(CS_ERR_UNSUPPORTED, "only kind = CS_ROPE is built");
   const int nv = P->n_nodes;
-  if (nv < 2 || nv > 128) return cs_fail(CS_ERR_INVALID_ARG, "rope n_nodes must be in [2, 128]");
-  if (P->real_bytes != 4 && P->real_bytes != 8) return cs_fail(CS_ERR_INVALID_ARG, "real_bytes must be 4 or 8");
   if (P->checkpoint_every < 1) return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every must be >= 1");
-  if (P->n_obstacles < 0 || P->n_obstacles > CS_MAX_OBSTACLES) return cs_fail(CS_ERR_INVALID_ARG, "n_obstacles out of range");
-  for (int i = 0; i < 2; ++i)
-    if (P->grasp_node[i] < 0 || P->grasp_node[i] >= nv) return cs_fail(CS_ERR_INVALID_ARG, "grasp_node out of range");
   if (B < 0 || H < 1) return cs_fail(CS_ERR_INVALID_ARG, "B must be >= 0 and H >= 1");
   if (!dL_dtraj && !loss) return cs_fail(CS_ERR_INVALID_ARG, "give dL_dtraj or a loss");
+  if (loss && (r = cs_validate_loss(loss, nv))) return r;
   if (B == 0) return CS_OK;
   if (!q0 || !u || !dL_du) return cs_fail(CS_ERR_INVALID_ARG, "q0, u and dL_du are required");
 
@@ -97,8 +109,7 @@ extern "C" cs_status sim_rollout_vjp_noalloc(const cs_params* P, const double* r
     return cs_fail(CS_ERR_INVALID_ARG,
                    "B x horizon exceed the allocation-free scratch (CS_NOALLOC_SCRATCH_BYTES)");
   void* base = nullptr;
-  cs_status r = scratch_address(&base);
-  if (r) return r;
+  if ((r = scratch_address(&base))) return r;
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);

@@ -10,7 +10,7 @@ import numpy as np
 from . import _lib as L
 from .sim import make_loss, make_params
 
-CS_ERR_PENDING, CS_ERR_CANCELLED = 6, 8
+CS_ERR_TIMEOUT, CS_ERR_PENDING, CS_ERR_CANCELLED = 5, 6, 8
 
 
 class PlanServer:
@@ -38,7 +38,7 @@ class PlanServer:
 
     def submit(self, scene: dict, q0, H: int, R: int, G: int, lr: float = 0.005,
                sigma: float = 0.02, u_max: float = 0.05, seed: int = 0, warm=None,
-               session_id: int = 0, **param_overrides) -> int:
+               session_id: int = 0, deadline_ms: int = 0, **param_overrides) -> int:
         req = L.cs_mpc_request()
         req.params = make_params(scene, real_bytes=self.real_bytes, **param_overrides)
         rest = np.ascontiguousarray(scene["rest_x"], dtype=np.float64).ravel()
@@ -52,13 +52,15 @@ class PlanServer:
         req.H, req.R, req.G = int(H), int(R), int(G)
         req.lr, req.sigma, req.u_max = float(lr), float(sigma), float(u_max)
         req.seed, req.session_id = int(seed), int(session_id)
+        req.deadline_ms = int(deadline_ms)
         t = C.c_uint64()
         L.check(L.lib().mpc_submit(self._h, C.byref(req), C.byref(t)), "mpc_submit")
         self._horizon[t.value] = int(H)
         return t.value
 
     def poll(self, ticket: int, timeout_ms: int = -1):
-        """The result dict, or None while it is pending; raises for a cancelled or failed solve."""
+        """The result dict, or None while it is pending; raises for a cancelled, timed-out
+        (deadline passed) or failed solve."""
         H = self._horizon[ticket]
         u = np.zeros((H, 6))
         res = L.cs_mpc_result()

@@ -63,9 +63,10 @@ def test_mpc_struct_layout_matches_c():
     #include <stddef.h>
     #include "cordsim.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cs_mpc_config), sizeof(cs_mpc_request),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cs_mpc_config), sizeof(cs_mpc_request),
              sizeof(cs_mpc_result), offsetof(cs_mpc_config, tuner_cache), offsetof(cs_mpc_request, loss),
              offsetof(cs_mpc_request, H), offsetof(cs_mpc_request, session_id),
+             offsetof(cs_mpc_request, deadline_ms),
              offsetof(cs_mpc_result, best_candidate), offsetof(cs_mpc_result, t_done_ns));
       return 0;
     }
@@ -80,7 +81,8 @@ def test_mpc_struct_layout_matches_c():
     assert vals == [C.sizeof(L.cs_mpc_config), C.sizeof(L.cs_mpc_request), C.sizeof(L.cs_mpc_result),
                     L.cs_mpc_config.tuner_cache.offset, L.cs_mpc_request.loss.offset,
                     L.cs_mpc_request.H.offset, L.cs_mpc_request.session_id.offset,
-                    L.cs_mpc_result.best_candidate.offset, L.cs_mpc_result.t_done_ns.offset]
+                    L.cs_mpc_request.deadline_ms.offset, L.cs_mpc_result.best_candidate.offset,
+                    L.cs_mpc_result.t_done_ns.offset]
 
 
 def test_argument_errors_without_gpu():
@@ -115,3 +117,49 @@ def test_cloth_argument_errors_without_gpu():
             P.rows, P.cols = bad["rows"], bad["cols"]
         assert lib.sim_create(C.byref(P), rp, C.byref(h)) == 1, bad
         assert not h.value
+
+
+def test_noalloc_argument_errors_without_gpu():
+    """The allocation-free entry point checks its parameters and loss as sim_create and
+    sim_rollout_vjp do, before any device call: a goal list longer than CS_MAX_GOAL, a goal node
+    past the chain, both grippers on one node, an unknown obstacle type, a non-positive time step
+    or node mass, zero iteration caps and barrier parameters out of order all fail with
+    CS_ERR_INVALID_ARG (the device pointers below are never dereferenced)."""
+    from paper_2606_14188_b300 import scenes
+    from paper_2606_14188_b300.sim import make_params, make_loss
+    lib = L.lib()
+    w = scenes.workload(2, B=2)
+    sc = w["scene"]
+    rest = np.ascontiguousarray(sc["rest_x"], dtype=np.float64)
+    rp = rest.ctypes.data_as(C.POINTER(C.c_double))
+    fake = C.c_void_p(256)            # a device address, never touched by a failing call
+
+    def call(P, loss):
+        return lib.sim_rollout_vjp_noalloc(C.byref(P), rp, 2, 5, fake, fake, None,
+                                           C.byref(loss) if loss is not None else None,
+                                           fake, fake, fake, fake, None)
+
+    loss = make_loss(sc)
+    loss.n_goal = L.CS_MAX_GOAL + 1
+    assert call(make_params(sc, 4, 2, 5), loss) == 1
+    assert b"n_goal" in lib.cs_last_error()
+    loss = make_loss(sc)
+    loss.goal_nodes[0] = sc["params"]["n_nodes"]
+    assert call(make_params(sc, 4, 2, 5), loss) == 1
+    assert b"goal node" in lib.cs_last_error()
+
+    def bad(**kw):
+        P = make_params(sc, 4, 2, 5)
+        for k, v in kw.items():
+            if k == "grasp":
+                P.grasp_node[0], P.grasp_node[1] = v
+            elif k == "ob_type":
+                P.obstacles[0].type = v
+            else:
+                setattr(P, k, v)
+        return P
+
+    for P in (bad(grasp=(3, 3)), bad(ob_type=9), bad(dt=0.0), bad(node_mass=-1.0),
+              bad(newton_max=0), bad(ipm_max=0), bad(kappa_decay=1.0), bad(kappa_hard=1.0),
+              bad(real_bytes=2), bad(n_nodes=129), bad(checkpoint_every=0)):
+        assert call(P, make_loss(sc)) == 1, lib.cs_last_error()

@@ -130,6 +130,32 @@ def test_plan_cancel_and_pending():
         assert out["status"] == 0
 
 
+def test_plan_deadline_expires_running_and_queued_requests():
+    """Per-request deadline (failure detection on the host): a running request whose deadline
+    passes leaves at the next tick boundary and its poll reports CS_ERR_TIMEOUT, as does a request
+    still queued behind it; nothing on the device waits.  A request with a generous deadline, and
+    the requests after the expired ones, finish with the result they give without a deadline."""
+    from paper_2606_14188_b300._lib import CordsimError
+    reqs = _mix()
+    r0, r1, r2 = reqs[3], reqs[1], reqs[0]
+    with _server(real_bytes=4, batched=False) as srv:
+        ref = _run(srv, [r2])[0]
+    with _server(real_bytes=4, batched=True, max_slots=1) as srv:
+        t0 = srv.submit(r0["scene"], r0["q0"], r0["H"], r0["R"], 100000, seed=1, deadline_ms=300)
+        t1 = srv.submit(r1["scene"], r1["q0"], r1["H"], r1["R"], r1["G"], seed=2, deadline_ms=100)
+        t2 = srv.submit(r2["scene"], r2["q0"], r2["H"], r2["R"], r2["G"], seed=r2["seed"],
+                        deadline_ms=600000)
+        for t in (t1, t0):
+            with pytest.raises(CordsimError) as e:
+                srv.poll(t)
+            assert e.value.code == 5
+        _same(srv.poll(t2), ref)
+        st = srv.stats()
+        assert st["ticks"] < 100000
+        t3 = srv.submit(r2["scene"], r2["q0"], r2["H"], r2["R"], r2["G"], seed=r2["seed"])
+        _same(srv.poll(t3), ref)
+
+
 def test_plan_session_warm_start():
     """A session's next request starts from its previous plan shifted by one step."""
     sc = scenes.rope_scene(16, n_spheres=0, seed=5)

@@ -2,10 +2,12 @@
 
 sim_rollout_vjp_noalloc serves callers that cannot allocate device memory (a real-time control
 loop that must not block on a driver allocation, or a process whose device memory is owned by
-another allocator): it keeps its scratch in a fixed device array inside the library.  Two calls
-in a row, through the C ABI, must give the results of the handle-based entry point.  This file is
-collected last so that a run stopping at the first failure has already run every other test.
+another allocator): it keeps its scratch in a fixed device array inside the library.  Calls in a
+row, through the C ABI, must give the results of the handle-based entry point, whatever the
+previous call left in the shared scratch.  This file is collected last so that a run stopping at
+the first failure has already run every other test.
 """
+import copy
 import ctypes as C
 
 import numpy as np
@@ -15,13 +17,18 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-TOL_STATE32, TOL_GRAD32 = 1e-4, 1e-3
+TOL = {4: (1e-4, 1e-3), 8: (1e-8, 1e-8)}     # (loss / states, gradients) relative
 
 
-def _call_noalloc(lib, params, rest, q0, U, loss, stream):
+def _dtype(rb):
+    return torch.float32 if rb == 4 else torch.float64
+
+
+def _call_noalloc(lib, params, rest, q0, U, loss, stream, rb):
     B, H = U.shape[0], U.shape[1]
-    Lv = torch.empty(B, dtype=torch.float32, device="cuda")
-    dU = torch.empty(B, H, 6, dtype=torch.float32, device="cuda")
+    dt = _dtype(rb)
+    Lv = torch.empty(B, dtype=dt, device="cuda")
+    dU = torch.empty(B, H, 6, dtype=dt, device="cuda")
     dq0 = torch.empty_like(q0)
     st = torch.zeros(B, dtype=torch.int32, device="cuda")
     p = lambda t: C.c_void_p(t.data_ptr())
@@ -31,32 +38,71 @@ def _call_noalloc(lib, params, rest, q0, U, loss, stream):
     return code, Lv, dU, dq0, st
 
 
-def test_noalloc_matches_handle_entry_point_twice():
-    from paper_2606_14188_b300 import scenes, _lib
+def _case(nodes, B, H, rb, seed):
+    """A rope of `nodes` nodes shaped like the 64-node workload (2 spheres, 2 boxes, both ends
+    held), B rollouts of H steps, checkpoint every 7 steps."""
+    from paper_2606_14188_b300 import scenes
+    if nodes == 64:
+        w = scenes.workload(2, B=B, H=H)
+        sc, U = w["scene"], w["U"]
+    else:
+        sc = scenes.rope_scene(nodes, n_spheres=2, n_boxes=2, seed=seed,
+                               sphere_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)))
+        U = scenes.controls_normal_clear(sc, B, H, seed=seed + 1)
+    sc = copy.deepcopy(sc)
+    sc["params"]["checkpoint_every"] = 7
+    dt = _dtype(rb)
+    q0 = torch.tensor(scenes.batch_q0(sc, B), dtype=dt, device="cuda")
+    Ut = torch.tensor(U, dtype=dt, device="cuda")
+    return sc, q0, Ut
+
+
+def _check_against_handle(lib, sc, q0, U, rb, stream, calls=1):
     from paper_2606_14188_b300.sim import Sim, make_params, make_loss
-    lib = _lib.lib()
-    w = scenes.workload(2, B=96)
-    sc = w["scene"]
-    B, H = w["B"], w["H"]
-    q0 = torch.tensor(w["q0"], dtype=torch.float32, device="cuda")
-    U = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
-    ref = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H)
+    B, H = U.shape[0], U.shape[1]
+    ref = Sim(sc, real_bytes=rb, max_batch=B, max_horizon=H)
     Lr, dUr, dqr, str_ = ref.rollout_vjp(q0, U)
-    params = make_params(sc, 4, B, H)
+    params = make_params(sc, rb, B, H)
     loss = make_loss(sc)
     rest = np.ascontiguousarray(sc["rest_x"], dtype=np.float64)
-    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for _ in range(2):
-        code, Lv, dU, dq0, st = _call_noalloc(lib, params, rest, q0, U, loss, stream)
+    tol_s, tol_g = TOL[rb]
+    for _ in range(calls):
+        code, Lv, dU, dq0, st = _call_noalloc(lib, params, rest, q0, U, loss, stream, rb)
         torch.cuda.synchronize()
         assert code == 0, lib.cs_last_error()
         assert torch.equal(st, str_)
-        ok = (st == 0)
+        ok = st == 0
+        assert int(ok.sum()) > 0
         rel = (Lv[ok] - Lr[ok]).abs().max() / Lr[ok].abs().max()
-        assert float(rel) <= TOL_STATE32
+        assert float(rel) <= tol_s
         g, gr = dU[ok].reshape(-1), dUr[ok].reshape(-1)
-        assert float((g - gr).norm() / gr.norm()) <= TOL_GRAD32
-        assert float((dq0[ok] - dqr[ok]).norm() / dqr[ok].norm()) <= TOL_GRAD32
+        assert float((g - gr).norm() / gr.norm()) <= tol_g
+        assert float((dq0[ok] - dqr[ok]).norm() / dqr[ok].norm()) <= tol_g
+        # failed rollouts: L is NaN and the gradients zero, on both sides
+        assert bool(Lv[~ok].isnan().all()) and bool((dU[~ok] == 0).all())
+
+
+@pytest.mark.parametrize("rb,nodes,B,H", [(4, 64, 96, 50), (8, 64, 12, 16), (4, 100, 32, 20),
+                                          (8, 100, 6, 10)])
+def test_noalloc_matches_handle_entry_point_twice(rb, nodes, B, H):
+    """FP32 and FP64, one pair per lane (64 nodes) and two (100 nodes): two calls in a row."""
+    from paper_2606_14188_b300 import _lib
+    lib = _lib.lib()
+    sc, q0, U = _case(nodes, B, H, rb, seed=2606 + nodes)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check_against_handle(lib, sc, q0, U, rb, stream, calls=2)
+
+
+def test_noalloc_large_call_then_small_calls_of_other_shapes():
+    """The benchmark's 1024 x 64-node x 50-step call fills most of the shared scratch; the calls
+    after it (a 30-node rope of 8 rollouts x 9 steps, then a 100-node rope in FP64) must not see
+    anything it left there."""
+    from paper_2606_14188_b300 import _lib
+    lib = _lib.lib()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for nodes, B, H, rb in ((64, 1024, 50, 4), (30, 8, 9, 4), (100, 4, 11, 8), (30, 8, 9, 4)):
+        sc, q0, U = _case(nodes, B, H, rb, seed=77 + nodes)
+        _check_against_handle(lib, sc, q0, U, rb, stream)
 
 
 def test_noalloc_rejects_oversized_batches():
@@ -94,7 +140,7 @@ def test_noalloc_benchmark_batch_two_part_launch():
     loss = make_loss(sc)
     rest = np.ascontiguousarray(sc["rest_x"], dtype=np.float64)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    code, Lv, dU, dq0, st = _call_noalloc(lib, params, rest, q0, U, loss, stream)
+    code, Lv, dU, dq0, st = _call_noalloc(lib, params, rest, q0, U, loss, stream, 4)
     torch.cuda.synchronize()
     assert code == 0, lib.cs_last_error()
     for a, b in zip((Lv, dU, dq0, st), ref):
