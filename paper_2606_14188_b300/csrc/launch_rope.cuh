@@ -1,8 +1,11 @@
-// Kernel launchers for the rope kernels (instantiated per real type in rope_*.cu).  The pairs
-// per lane (PPL) template argument follows the chain length: 1 up to 64 nodes, 2 up to 128.
+// Kernel launchers for the rope kernels (instantiated per real type in rope_*.cu).  Rollouts and
+// adjoints run one 64-thread CTA per rollout (rope_cta.cuh; nodes per thread NPT = 1 up to 64
+// nodes, 2 up to 128); the linearisation runs one warp per (trajectory, step) (rope.cuh; pairs per
+// lane PPL = 1 up to 64 nodes, 2 up to 128).
 #pragma once
 #include "internal.h"
 #include "rope.cuh"
+#include "rope_cta.cuh"
 
 namespace csi {
 
@@ -12,67 +15,68 @@ inline cs_status launch_prep(Kern k, size_t smem, const cs_sim* s) {
   return prep_kernel(k, smem);
 }
 
-template <typename R, int PPL>
-cs_status rollout_ppl(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj,
+template <typename R, int NPT>
+cs_status rollout_cta(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj,
                       void* qH, int32_t* status, int32_t* counters, cudaStream_t st) {
   cs::Scene<R> S = make_scene<R>(s, nullptr);
-  const size_t smem = smem_bytes(s, H, false);
-  cs_status r = launch_prep(cs::rope_rollout_kernel<R, PPL>, smem, s);
+  const size_t smem = cs::rc::sm_elems(NPT, s->P.n_obstacles) * sizeof(R);
+  cs_status r = launch_prep(cs::rc::rope_cta_rollout_kernel<R, NPT>, smem, s);
   if (r) return r;
-  cs::rope_rollout_kernel<R, PPL><<<B, 32, smem, st>>>(S, B, H, (const R*)q0, (const R*)u, (R*)traj,
-                                                        (R*)qH, status, counters);
-  return check_launch("rope_rollout_kernel");
+  cs::rc::rope_cta_rollout_kernel<R, NPT><<<B, cs::rc::NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
+                                                                       (R*)traj, (R*)qH, status, counters);
+  return check_launch("rope_cta_rollout_kernel");
 }
 
 template <typename R>
 cs_status launch_rollout(cs_sim* s, int B, int H, const void* q0, const void* u, void* traj,
                          void* qH, int32_t* status, int32_t* counters, cudaStream_t st) {
-  return s->npair <= 32 ? rollout_ppl<R, 1>(s, B, H, q0, u, traj, qH, status, counters, st)
-                        : rollout_ppl<R, 2>(s, B, H, q0, u, traj, qH, status, counters, st);
+  return s->nv <= 64 ? rollout_cta<R, 1>(s, B, H, q0, u, traj, qH, status, counters, st)
+                     : rollout_cta<R, 2>(s, B, H, q0, u, traj, qH, status, counters, st);
 }
 
-template <typename R, int PPL>
-cs_status vjp_ppl(cs_sim* s, int B, int H, const void* q0, const void* u, const void* dLdtraj,
+template <typename R, int NPT>
+cs_status vjp_cta(cs_sim* s, int B, int H, const void* q0, const void* u, const void* dLdtraj,
                   const cs_loss* loss, void* L, void* dLdu, void* dLdq0, int32_t* status,
                   cudaStream_t st) {
   cs::Scene<R> S = make_scene<R>(s, loss);
-  const size_t smem = smem_bytes(s, H, false);
-  cs_status r = launch_prep(cs::rope_vjp_kernel<R, PPL>, smem, s);
+  const size_t smem = cs::rc::sm_elems(NPT, s->P.n_obstacles) * sizeof(R);
+  cs_status r = launch_prep(cs::rc::rope_cta_vjp_kernel<R, NPT>, smem, s);
   if (r) return r;
+  const int NT = cs::rc::NT;
   // More rollouts than the device holds at once: the late starters decide when the launch ends,
   // so the forward parts run first (each measuring its cost), then the backward parts, costliest
   // first, leaving the cheap ones to start late.
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cs::rope_vjp_kernel<R, PPL>, 32, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cs::rc::rope_cta_vjp_kernel<R, NPT>, NT, smem);
   if ((long long)per_sm * s->sms < B && B <= cs::CS_ORDER_MAX) {
-    if ((r = launch_prep(cs::rope_vjp_fwd_kernel<R, PPL>, smem, s))) return r;
-    if ((r = launch_prep(cs::rope_vjp_bwd_kernel<R, PPL>, smem, s))) return r;
+    if ((r = launch_prep(cs::rc::rope_cta_vjp_fwd_kernel<R, NPT>, smem, s))) return r;
+    if ((r = launch_prep(cs::rc::rope_cta_vjp_bwd_kernel<R, NPT>, smem, s))) return r;
     int32_t* cost = reinterpret_cast<int32_t*>(static_cast<char*>(s->d_ws) +
                                                vjp_ord_offset(s->ws_stride, s->P.max_batch, s->real_bytes));
     int32_t* order = cost + B;
-    cs::rope_vjp_fwd_kernel<R, PPL><<<B, 32, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
-                                                          (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
-                                                          status, (R*)s->d_ws, s->ws_stride, cost);
-    if ((r = check_launch("rope_vjp_fwd_kernel"))) return r;
+    cs::rc::rope_cta_vjp_fwd_kernel<R, NPT><<<B, NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
+                                                                 (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
+                                                                 status, (R*)s->d_ws, s->ws_stride, cost);
+    if ((r = check_launch("rope_cta_vjp_fwd_kernel"))) return r;
     cs::rope_order_kernel<cs::CS_ORDER_NT><<<1, cs::CS_ORDER_NT, 0, st>>>(cost, B, order);
     if ((r = check_launch("rope_order_kernel"))) return r;
-    cs::rope_vjp_bwd_kernel<R, PPL><<<B, 32, smem, st>>>(S, B, H, (const R*)u, (const R*)dLdtraj, (R*)L,
-                                                          (R*)dLdu, (R*)dLdq0, status, (R*)s->d_ws,
-                                                          s->ws_stride, cost, order);
-    return check_launch("rope_vjp_bwd_kernel");
+    cs::rc::rope_cta_vjp_bwd_kernel<R, NPT><<<B, NT, smem, st>>>(S, B, H, (const R*)u, (const R*)dLdtraj, (R*)L,
+                                                                 (R*)dLdu, (R*)dLdq0, status, (R*)s->d_ws,
+                                                                 s->ws_stride, cost, order);
+    return check_launch("rope_cta_vjp_bwd_kernel");
   }
-  cs::rope_vjp_kernel<R, PPL><<<B, 32, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
-                                                    (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
-                                                    status, (R*)s->d_ws, s->ws_stride);
-  return check_launch("rope_vjp_kernel");
+  cs::rc::rope_cta_vjp_kernel<R, NPT><<<B, NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
+                                                           (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
+                                                           status, (R*)s->d_ws, s->ws_stride);
+  return check_launch("rope_cta_vjp_kernel");
 }
 
 template <typename R>
 cs_status launch_vjp(cs_sim* s, int B, int H, const void* q0, const void* u, const void* dLdtraj,
                      const cs_loss* loss, void* L, void* dLdu, void* dLdq0, int32_t* status,
                      cudaStream_t st) {
-  return s->npair <= 32 ? vjp_ppl<R, 1>(s, B, H, q0, u, dLdtraj, loss, L, dLdu, dLdq0, status, st)
-                        : vjp_ppl<R, 2>(s, B, H, q0, u, dLdtraj, loss, L, dLdu, dLdq0, status, st);
+  return s->nv <= 64 ? vjp_cta<R, 1>(s, B, H, q0, u, dLdtraj, loss, L, dLdu, dLdq0, status, st)
+                     : vjp_cta<R, 2>(s, B, H, q0, u, dLdtraj, loss, L, dLdu, dLdq0, status, st);
 }
 
 template <typename R, int PPL>
