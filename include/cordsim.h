@@ -47,6 +47,7 @@ typedef enum {
 #define CS_ST_CONTACT 2    /* stage-2 interior point reached ipm_max / found no interior    */
 #define CS_ST_NONFINITE 4  /* a non-finite value appeared                                   */
 #define CS_ST_NOTPD 8      /* a stage-2 or adjoint system was not positive definite         */
+#define CS_ST_TIMEOUT 16   /* a bounded device-side wait of the adjoint ran out (no result)  */
 
 #define CS_MAX_OBSTACLES 8
 #define CS_MAX_GOAL 64

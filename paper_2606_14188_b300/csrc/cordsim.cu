@@ -171,6 +171,24 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
     sim_destroy(s);
     return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "adjoint workspace") : cs_cuda_fail(e, "cudaMalloc");
   }
+  if (!cloth) {
+    // the work-queue adjoint's per-step records; without room for them the adjoint runs as the
+    // one-launch or two-part form instead (same results)
+    const int NPT = nv <= 64 ? 1 : 2;
+    const int nseg = (P->max_horizon + k - 1) / k;
+    s->fac_stride = (size_t)P->max_horizon * cs::rc::fac_step_elems(NPT, nv);
+    const size_t fac_bytes = s->fac_stride * (size_t)P->max_batch * rb;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    if (fac_bytes <= free_b / 2) {
+      if (cudaMalloc(&s->d_fac, fac_bytes) != cudaSuccess ||
+          cudaMalloc(&s->d_queue, cs::rc::queue_ints(P->max_batch, nseg) * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();          // clear the allocation failure: the handle works without the queue
+        if (s->d_fac) cudaFree(s->d_fac);
+        s->d_fac = s->d_queue = nullptr;
+      }
+    }
+  }
   if (cloth) {
     // one workspace slot per CTA the device holds at once (the kernels' grid never exceeds it)
     const int per_sm = rb == 4 ? cloth_ctas_per_sm<float>(s) : cloth_ctas_per_sm<double>(s);
@@ -197,6 +215,8 @@ cs_status sim_destroy(cs_sim* s) {
   if (s->d_ws) cudaFree(s->d_ws);
   if (s->d_slots) cudaFree(s->d_slots);
   if (s->d_claim) cudaFree(s->d_claim);
+  if (s->d_fac) cudaFree(s->d_fac);
+  if (s->d_queue) cudaFree(s->d_queue);
   delete s;
   return CS_OK;
 }

@@ -11,6 +11,7 @@
 #include "cloth_band.cuh"
 #include "common.cuh"
 #include "rope.cuh"
+#include "rope_cta.cuh"
 
 cs_status cs_fail(cs_status s, const std::string& msg);
 cs_status cs_cuda_fail(cudaError_t e, const char* where);
@@ -33,6 +34,12 @@ struct cs_sim {
   void* d_ws = nullptr;   // adjoint workspace: ws_stride elements per rollout (checkpoint and
                           // segment records, carry), then the cost and order arrays (vjp_ord_offset)
   size_t ws_stride = 0;   // elements per rollout
+  // rope adjoint by the work queue: per rollout max_horizon per-step records (factorisations of the
+  // step's adjoint and its smooth solution, fac_stride elements), and the queue state (int32);
+  // null when the memory was not available (then the adjoint runs without the queue)
+  void* d_fac = nullptr;
+  size_t fac_stride = 0;
+  void* d_queue = nullptr;
   int sms = 0;
   size_t smem_optin = 0;
   // cloth only: band geometry and the per-CTA workspace slots of the cloth kernels

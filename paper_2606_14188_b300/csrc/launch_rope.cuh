@@ -3,6 +3,7 @@
 // nodes, 2 up to 128); the linearisation runs one warp per (trajectory, step) (rope.cuh; pairs per
 // lane PPL = 1 up to 64 nodes, 2 up to 128).
 #pragma once
+#include <algorithm>
 #include "internal.h"
 #include "rope.cuh"
 #include "rope_cta.cuh"
@@ -43,6 +44,26 @@ cs_status vjp_cta(cs_sim* s, int B, int H, const void* q0, const void* u, const 
   cs_status r = launch_prep(cs::rc::rope_cta_vjp_kernel<R, NPT>, smem, s);
   if (r) return r;
   const int NT = cs::rc::NT;
+  if (s->d_fac && s->d_queue) {
+    // work queue: forward jobs, then (rollout, segment) jobs, each rollout's adjoint chain in the
+    // CTA that finishes its last segment; a persistent grid of the CTAs the device holds at once
+    auto kq = cs::rc::rope_cta_vjp_queue_kernel<R, NPT>;
+    if ((r = launch_prep(kq, smem, s))) return r;
+    const int nseg = (H + s->P.checkpoint_every - 1) / s->P.checkpoint_every;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kq, NT, smem);
+    if (per_sm < 1) return cs_fail(CS_ERR_INVALID_ARG, "scene too large for shared memory");
+    const long long jobs = (long long)B * (1 + nseg);
+    const int grid = (int)std::min<long long>((long long)per_sm * s->sms, jobs);
+    cudaError_t e = cudaMemsetAsync(s->d_queue, 0, cs::rc::queue_ints(B, nseg) * sizeof(int), st);
+    if (e != cudaSuccess) return cs_cuda_fail(e, "cudaMemsetAsync");
+    int* q = static_cast<int*>(s->d_queue);
+    kq<<<grid, NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u, (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
+                              status, (R*)s->d_ws, s->ws_stride, (R*)s->d_fac, s->fac_stride, q);
+    if ((r = check_launch("rope_cta_vjp_queue_kernel"))) return r;
+    cs::rc::rope_queue_finish_kernel<R><<<(B + 127) / 128, 128, 0, st>>>(B, H, nseg, q, (R*)L, (R*)dLdu, status);
+    return check_launch("rope_queue_finish_kernel");
+  }
   // More rollouts than the device holds at once: the late starters decide when the launch ends,
   // so the forward parts run first (each measuring its cost), then the backward parts, costliest
   // first, leaving the cheap ones to start late.

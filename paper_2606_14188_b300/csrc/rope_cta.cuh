@@ -24,6 +24,17 @@ namespace cs {
 namespace rc {
 
 constexpr int NT = 64;   // threads per rollout
+constexpr int LDT = 21;  // row stride of a packed lower triangle (odd: a thread per row touches 32 banks)
+
+__device__ __forceinline__ int rt(int p, int i, int j) { return p * LDT + i * (i + 1) / 2 + j; }
+
+template <typename R>
+__device__ __forceinline__ void ld_low(const R* T, int row, R* a) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int k = 0; k <= i; ++k) a[i * 6 + k] = T[rt(row, i, k)];
+}
 
 __host__ __device__ constexpr int pow2ceil(int x) {
   int p = 1;
@@ -37,20 +48,21 @@ __host__ __device__ constexpr int pow2ceil(int x) {
 template <typename R>
 struct Sm {
   int NVP;                      // node slots: 64 NPT
-  R *T, *B, *V, *r;             // block cyclic reduction: rows of stride CR_LDT, CR_LDM, CR_LDM, CR_LDV
-  R *x0, *dx, *v1, *v2;         // node exchange: element c of node j at [c * NVP + j]
+  R *T, *B, *V, *r;             // block cyclic reduction: rows of stride LDT, CR_LDM, CR_LDM, CR_LDV
+  R *x0, *dx, *v1;              // node exchange: element c of node j at [c * NVP + j]
   R *s, *z, *g;                 // contact pairs (obstacle o, node j): element c at [(o * 3 + c) * NVP + j]
-  R *M;                         // W^-2 of a pair (6, symmetric): element c at [(o * 6 + c) * NVP + j]
+  R *wp;                        // Nesterov-Todd scaling of a pair: (v1, v2, beta) at [(o * 3 + c) * NVP + j]
   R *misc;                      // [64]: grippers, controls, grasp offsets and stiffness (M_* slots)
   R *red;                       // [4]: block reductions (two buffers of one value per warp)
 };
 
 // The signed distances and normals of the contact pairs are recomputed from x* where needed (they
-// are fixed during a stage-2 solve), and the controls are read from global memory, which keeps a
-// 64-node rope with 5 obstacles at 6 CTAs per SM.
+// are fixed during a stage-2 solve), a pair's scaling W = beta (2 v v^T - J) is kept as (v1, v2,
+// beta) (v0 = sqrt(1 + v1^2 + v2^2) on the unit hyperboloid), and the controls are read from global
+// memory: a 64-node rope with 5 obstacles takes 31 KB, 7 CTAs per SM.
 __host__ __device__ inline size_t sm_elems(int NPT, int nobs) {
   const size_t NVP = 64 * (size_t)NPT, N = 32 * (size_t)NPT;
-  return N * (CR_LDT + 2 * CR_LDM + CR_LDV) + 4 * 3 * NVP + (size_t)nobs * 15 * NVP + 64 + 4;
+  return N * (LDT + 2 * CR_LDM + CR_LDV) + 3 * 3 * NVP + (size_t)nobs * 12 * NVP + 64 + 4;
 }
 
 template <typename R>
@@ -60,17 +72,16 @@ __device__ __forceinline__ Sm<R> sm_carve(R* base, int NPT, int nobs) {
   w.NVP = (int)NVP;
   R* p = base;
   auto take = [&](size_t n) { R* q = p; p += n; return q; };
-  w.T = take(CR_LDT * N); w.B = take(CR_LDM * N); w.V = take(CR_LDM * N); w.r = take(CR_LDV * N);
-  w.x0 = take(3 * NVP); w.dx = take(3 * NVP); w.v1 = take(3 * NVP); w.v2 = take(3 * NVP);
+  w.T = take(LDT * N); w.B = take(CR_LDM * N); w.V = take(CR_LDM * N); w.r = take(CR_LDV * N);
+  w.x0 = take(3 * NVP); w.dx = take(3 * NVP); w.v1 = take(3 * NVP);
   w.s = take((size_t)nobs * 3 * NVP); w.z = take((size_t)nobs * 3 * NVP);
-  w.g = take((size_t)nobs * 3 * NVP); w.M = take((size_t)nobs * 6 * NVP);
+  w.g = take((size_t)nobs * 3 * NVP); w.wp = take((size_t)nobs * 3 * NVP);
   w.misc = take(64);
   w.red = take(4);
   return w;
 }
 
 __device__ __forceinline__ int pv_(int o, int c, int j, int NVP) { return (o * 3 + c) * NVP + j; }
-__device__ __forceinline__ int pm_(int o, int c, int j, int NVP) { return (o * 6 + c) * NVP + j; }
 
 // ------------------------------------------------------------------------------------------
 // block reductions (every thread calls them; the result is the same on every thread)
@@ -127,7 +138,7 @@ __device__ __noinline__ bool crb_factor(R* T, R* B, R* V, int N) {
       if (act) {
         const int k = s + 2 * s * idx;
         R L[36];
-        ld_lower(T, k, L);
+        ld_low(T, k, L);
         __syncwarp(m);                        // the group has read T_k before it is overwritten
         ok = chol6(L) && ok;
         int e = 0;
@@ -135,7 +146,7 @@ __device__ __noinline__ bool crb_factor(R* T, R* B, R* V, int N) {
         for (int a = 0; a < 6; ++a)
 #pragma unroll
           for (int b = 0; b <= a; ++b, ++e)
-            if ((e & (G - 1)) == g) T[cr_t(k, a, b)] = L[a * 6 + b];
+            if ((e & (G - 1)) == g) T[rt(k, a, b)] = L[a * 6 + b];
         // column c of U_k = L_k^-1 B_k (c < 6) or of V_k = L_k^-1 B_{k+s}^T (c >= 6): the same
         // instructions on every lane, the operands chosen by address
         const int ncol = k + s < N ? 12 : 6;
@@ -171,7 +182,7 @@ __device__ __noinline__ bool crb_factor(R* T, R* B, R* V, int N) {
         for (int e = g; e < 21; e += G2) {
           const int a = (e >= 1) + (e >= 3) + (e >= 6) + (e >= 10) + (e >= 15);
           const int b = e - a * (a + 1) / 2;
-          R t = T[cr_t(i, a, b)];
+          R t = T[rt(i, a, b)];
           if (hr) {
 #pragma unroll
             for (int q = 0; q < 6; ++q) t -= Ur[q * 6 + a] * Ur[q * 6 + b];
@@ -180,7 +191,7 @@ __device__ __noinline__ bool crb_factor(R* T, R* B, R* V, int N) {
 #pragma unroll
             for (int q = 0; q < 6; ++q) t -= Vl[q * 6 + a] * Vl[q * 6 + b];
           }
-          T[cr_t(i, a, b)] = t;
+          T[rt(i, a, b)] = t;
         }
         if (hl) {
           for (int e = g; e < 36; e += G2) {
@@ -197,9 +208,12 @@ __device__ __noinline__ bool crb_factor(R* T, R* B, R* V, int N) {
   }
   if (tid == 0) {
     R L[36];
-    ld_lower(T, 0, L);
+    ld_low(T, 0, L);
     ok = chol6(L) && ok;
-    st_lower(T, 0, L);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int q = 0; q <= i; ++q) T[rt(0, i, q)] = L[i * 6 + q];
   }
   return __syncthreads_and(ok);
 }
@@ -216,7 +230,7 @@ __device__ __noinline__ void crb_solve(const R* T, const R* B, const R* V, R* r,
   for (int s = 1; s < N; s <<= 1) {
     if (row && (t & (2 * s - 1)) == s) {
       R L[36], y[6];
-      ld_lower(T, t, L);
+      ld_low(T, t, L);
 #pragma unroll
       for (int a = 0; a < 6; ++a) y[a] = r[cr_v(t, a)];
       lsolve6(L, y, 1);
@@ -250,7 +264,7 @@ __device__ __noinline__ void crb_solve(const R* T, const R* B, const R* V, R* r,
   }
   if (t == 0) {
     R L[36], y[6];
-    ld_lower(T, 0, L);
+    ld_low(T, 0, L);
 #pragma unroll
     for (int a = 0; a < 6; ++a) y[a] = r[cr_v(0, a)];
     lsolve6(L, y, 1);
@@ -278,7 +292,7 @@ __device__ __noinline__ void crb_solve(const R* T, const R* B, const R* V, R* r,
           for (int q = 0; q < 6; ++q) y[a] -= V[cr_m(t, a * 6 + q)] * xr[q];
       }
       R L[36];
-      ld_lower(T, t, L);
+      ld_low(T, t, L);
       ltsolve6(L, y, 1);
 #pragma unroll
       for (int a = 0; a < 6; ++a) r[cr_v(t, a)] = y[a];
@@ -411,7 +425,7 @@ __device__ __forceinline__ void put_node_rows(const Sm<R>& w, int j, const R D[9
     const int row = 3 * h + i;
     if (h == 0) {
 #pragma unroll
-      for (int q = 0; q <= i; ++q) w.T[cr_t(p, row, q)] = D[i * 3 + q];
+      for (int q = 0; q <= i; ++q) w.T[rt(p, row, q)] = D[i * 3 + q];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         w.B[cr_m(p, row * 6 + q)] = C2[i * 3 + q];
@@ -419,9 +433,9 @@ __device__ __forceinline__ void put_node_rows(const Sm<R>& w, int j, const R D[9
       }
     } else {
 #pragma unroll
-      for (int q = 0; q < 3; ++q) w.T[cr_t(p, row, q)] = C1[i * 3 + q];
+      for (int q = 0; q < 3; ++q) w.T[rt(p, row, q)] = C1[i * 3 + q];
 #pragma unroll
-      for (int q = 0; q <= i; ++q) w.T[cr_t(p, row, 3 + q)] = D[i * 3 + q];
+      for (int q = 0; q <= i; ++q) w.T[rt(p, row, 3 + q)] = D[i * 3 + q];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         w.B[cr_m(p, row * 6 + q)] = R(0);
@@ -657,14 +671,48 @@ __device__ __forceinline__ void pair_sz(const Sm<R>& w, int o, int j, R sv[3], R
   for (int a = 0; a < 3; ++a) { sv[a] = w.s[pv_(o, a, j, w.NVP)]; zv[a] = w.z[pv_(o, a, j, w.NVP)]; }
 }
 
+// M = W^-2 of a pair from its stored scaling (v1, v2, beta): with u = J v = (v0, -v1, -v2),
+// W^-1 = (2 u u^T - J) / beta, so M = (4 (u.u) u u^T - 2 (u v^T + v u^T) + I) / beta^2
 template <typename R>
 __device__ __forceinline__ void pair_M(const Sm<R>& w, int o, int j, R M[9]) {
-  R m6[6];
+  const R v1 = w.wp[pv_(o, 0, j, w.NVP)], v2 = w.wp[pv_(o, 1, j, w.NVP)], be = w.wp[pv_(o, 2, j, w.NVP)];
+  const R v0 = sqrt(R(1) + v1 * v1 + v2 * v2);
+  const R v[3] = {v0, v1, v2}, u[3] = {v0, -v1, -v2};
+  const R uu = v0 * v0 + v1 * v1 + v2 * v2;
+  const R ib2 = R(1) / (be * be);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) m6[c] = w.M[pm_(o, c, j, w.NVP)];
-  M[0] = m6[0]; M[1] = m6[1]; M[2] = m6[2];
-  M[3] = m6[1]; M[4] = m6[3]; M[5] = m6[4];
-  M[6] = m6[2]; M[7] = m6[4]; M[8] = m6[5];
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      M[a * 3 + b] = (R(4) * uu * u[a] * u[b] - R(2) * (u[a] * v[b] + v[a] * u[b]) + (a == b ? R(1) : R(0))) * ib2;
+}
+
+// the scaling W, W^-1 and lam = W z of a pair (Vandenberghe 2010, second-order cone), and its
+// compact form (v1, v2, beta) for pair_M
+template <typename R>
+__device__ __forceinline__ void nt_scaling_v(const R s[3], const R z[3], R W[9], R Wi[9], R lam[3], R wp[3]) {
+  const R ds = soc_det(s), dz = soc_det(z);
+  const R rs = R(1) / sqrt(ds), rz = R(1) / sqrt(dz);
+  const R sb[3] = {s[0] * rs, s[1] * rs, s[2] * rs};
+  const R zb[3] = {z[0] * rz, z[1] * rz, z[2] * rz};
+  const R gam = sqrt(R(0.5) * (R(1) + sb[0] * zb[0] + sb[1] * zb[1] + sb[2] * zb[2]));
+  const R ig = R(1) / (R(2) * gam);
+  const R wb[3] = {(sb[0] + zb[0]) * ig, (sb[1] - zb[1]) * ig, (sb[2] - zb[2]) * ig};
+  const R iv = R(1) / sqrt(R(2) * (wb[0] + R(1)));
+  const R v[3] = {(wb[0] + R(1)) * iv, wb[1] * iv, wb[2] * iv};
+  const R beta = sqrt(sqrt(ds / dz));
+  const R Jv[3] = {v[0], -v[1], -v[2]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const R J = i == k ? (i == 0 ? R(1) : R(-1)) : R(0);
+      W[i * 3 + k] = beta * (R(2) * v[i] * v[k] - J);
+      Wi[i * 3 + k] = (R(2) * Jv[i] * Jv[k] - J) / beta;
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) lam[i] = W[i * 3] * z[0] + W[i * 3 + 1] * z[1] + W[i * 3 + 2] * z[2];
+  wp[0] = v[1]; wp[1] = v[2]; wp[2] = beta;
 }
 
 // residual of the slack r_z = s - A D - phi e1
@@ -820,7 +868,8 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, cons
         cone_frame(n, S.mu, A);
         pair_sz(w, o, j, sv, zv);
         pair_rz(A, sv, Dn, ph, rz);
-        nt_scaling(sv, zv, W, Wi, lam);
+        R wpv[3];
+        nt_scaling_v(sv, zv, W, Wi, lam, wpv);
         const R tg = pc ? R(0) : target;
         const R r3[3] = {tg - (lam[0] * lam[0] + lam[1] * lam[1] + lam[2] * lam[2]), R(-2) * lam[0] * lam[1],
                          R(-2) * lam[0] * lam[2]};
@@ -831,8 +880,8 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, cons
 #pragma unroll
           for (int b = 0; b < 3; ++b)
             M[a * 3 + b] = Wi[a * 3] * Wi[b] + Wi[a * 3 + 1] * Wi[3 + b] + Wi[a * 3 + 2] * Wi[6 + b];
-        w.M[pm_(o, 0, j, NVP)] = M[0]; w.M[pm_(o, 1, j, NVP)] = M[1]; w.M[pm_(o, 2, j, NVP)] = M[2];
-        w.M[pm_(o, 3, j, NVP)] = M[4]; w.M[pm_(o, 4, j, NVP)] = M[5]; w.M[pm_(o, 5, j, NVP)] = M[8];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) w.wp[pv_(o, a, j, NVP)] = wpv[a];
         R g[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -964,8 +1013,8 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, cons
           bad = bad || !(fabs(dz[a]) <= R(1e30)) || !(fabs(dsv[a]) <= R(1e30));
         }
         amin = fmin(amin, fmin(soc_max_step(sv, dsv), soc_max_step(zv, dz)));
-        // g and M are not needed after this: they keep the directions for the update
-        for (int a = 0; a < 3; ++a) { w.g[pv_(o, a, j, NVP)] = dsv[a]; w.M[pm_(o, a, j, NVP)] = dz[a]; }
+        // g and the scaling are not needed after this: they keep the directions for the update
+        for (int a = 0; a < 3; ++a) { w.g[pv_(o, a, j, NVP)] = dsv[a]; w.wp[pv_(o, a, j, NVP)] = dz[a]; }
       }
     }
     if (__syncthreads_or(bad)) { *iters = it + 1; return ST_NONFINITE; }
@@ -985,7 +1034,7 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, cons
         pair_sz(w, o, j, sv, zv);
         for (int a = 0; a < 3; ++a) {
           sv[a] += alpha * w.g[pv_(o, a, j, NVP)];
-          zv[a] += alpha * w.M[pm_(o, a, j, NVP)];
+          zv[a] += alpha * w.wp[pv_(o, a, j, NVP)];
           w.s[pv_(o, a, j, NVP)] = sv[a];
           w.z[pv_(o, a, j, NVP)] = zv[a];
         }
@@ -1066,8 +1115,13 @@ __device__ __forceinline__ void advance_state(const Scene<R>& S, Nd<R, NPT>& N, 
 //        the factorisation of H2 in (T, B, V); x0 and dx published
 //   out: xb = xbar (adjoint of x), misc GB = gbar, misc UB = ubar
 // ------------------------------------------------------------------------------------------
+// the first half of the adjoint of one smooth step (eq. diff-sim with the total derivative):
+//   in : xb = xbar+, the smooth solution in the node state, x0 and dx published, the factorisation of
+//        H2 in (T, B, V)
+//   out: mu = H2^-1 xbar+, xs = xbar* = xbar+ - (dR/dx*)^T mu
 template <typename R, int NPT>
-__device__ __forceinline__ int adjoint_step(const Scene<R>& S, Nd<R, NPT>& N, const Sm<R>& w, R xb[NPT][3]) {
+__device__ __forceinline__ void adjoint_xs(const Scene<R>& S, const Nd<R, NPT>& N, const Sm<R>& w,
+                                           const R xb[NPT][3], R mu[NPT][3], R xs[NPT][3]) {
   const R kappa = S.kc;
   const R* d = w.misc + M_D;
   const R* c = w.misc + M_C;
@@ -1075,16 +1129,15 @@ __device__ __forceinline__ int adjoint_step(const Scene<R>& S, Nd<R, NPT>& N, co
   const R* gd = w.misc + M_GD;
   const int NVP = w.NVP;
   // mu = H2^{-1} xbar+
-  R mu[NPT][3];
   put_rhs<R, NPT>(S, w, xb, R(1));
   __syncthreads();
   crb_solve(w.T, w.B, w.V, w.r, S.npair);
   get_rhs<R, NPT>(S, w, mu);
+  __syncthreads();                             // every thread has its mu before r is reused
   publish<R, NPT>(w.v1, mu, NVP);
-  publish<R, NPT>(w.v2, N.Dl, NVP);
+  put_rhs<R, NPT>(S, w, N.Dl, R(1));           // Delta of the neighbours, through r (free until nu)
   __syncthreads();
   // xbar* = xbar+ - (dR/dx*)^T mu
-  R xs[NPT][3];
 #pragma unroll
   for (int k = 0; k < NPT; ++k) {
     const int j = node_of(k);
@@ -1120,7 +1173,7 @@ __device__ __forceinline__ int adjoint_step(const Scene<R>& S, Nd<R, NPT>& N, co
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         mt[i] = w.v1[i * NVP + jo] - mu[k][i];
-        dl[i] = w.v2[i * NVP + jo] - N.Dl[k][i];
+        dl[i] = w.r[cr_v(jo >> 1, 3 * (jo & 1) + i)] - N.Dl[k][i];
       }
       // third-derivative contraction of the spring energy (odd in the spring vector: the same
       // expression at either end of the spring)
@@ -1129,12 +1182,20 @@ __device__ __forceinline__ int adjoint_step(const Scene<R>& S, Nd<R, NPT>& N, co
       for (int i = 0; i < 3; ++i) xs[k][i] += t3[i];
     }
   }
-  // nu = H1^{-1} xbar*  (dF/dq* at x*): not positive definite means the stage-1 root is a saddle of
-  // the potential (a buckled, unstable equilibrium); the step's Jacobian is reported as undefined
-  assemble_P(S, N, w, false, false);
+  __syncthreads();                             // the neighbours' Delta are read before r is overwritten
+}
+
+// the second half of the adjoint of one smooth step: nu = H1^-1 xbar*, then xbar, gbar, ubar
+template <typename R, int NPT>
+__device__ __forceinline__ void adjoint_nu(const Scene<R>& S, const Nd<R, NPT>& N, const Sm<R>& w,
+                                           const R mu[NPT][3], const R xs[NPT][3], R xb[NPT][3]) {
+  const R* d = w.misc + M_D;
+  const R* c = w.misc + M_C;
+  const R* u = w.misc + M_U;
+  const R* gd = w.misc + M_GD;
+  // nu = H1^{-1} xbar*, the factorisation of H1 = dF/dq* at x* in (T, B, V)
   put_rhs<R, NPT>(S, w, xs, R(1));
   __syncthreads();
-  if (!crb_factor(w.T, w.B, w.V, S.npair)) return ST_NOTPD;
   crb_solve(w.T, w.B, w.V, w.r, S.npair);
   R nu[NPT][3];
   get_rhs<R, NPT>(S, w, nu);
@@ -1162,8 +1223,27 @@ __device__ __forceinline__ int adjoint_step(const Scene<R>& S, Nd<R, NPT>& N, co
       }
   }
   __syncthreads();
+}
+
+
+// adjoint of one smooth step with the factorisation of H2 in (T, B, V): H1 is assembled and
+// factorised here; not positive definite means the stage-1 root is a saddle of the potential (a
+// buckled, unstable equilibrium) and the step's Jacobian is reported as undefined
+template <typename R, int NPT>
+__device__ __forceinline__ int adjoint_step(const Scene<R>& S, Nd<R, NPT>& N, const Sm<R>& w, R xb[NPT][3]) {
+  R mu[NPT][3], xs[NPT][3];
+  adjoint_xs(S, N, w, xb, mu, xs);
+  assemble_P(S, N, w, false, false);
+  __syncthreads();
+  if (!crb_factor(w.T, w.B, w.V, S.npair)) return ST_NOTPD;
+  adjoint_nu(S, N, w, mu, xs, xb);
   return 0;
 }
+
+// the same with both factorisations stored: H2 in (T, B, V), H1 at h1 (global)
+template <typename R, int NPT>
+__device__ __forceinline__ int adjoint_step_stored(const Scene<R>& S, Nd<R, NPT>& N, const Sm<R>& w, R xb[NPT][3],
+                                                   const R* h1);
 
 // penalty part of the planning loss at the state x0: this thread's share of the value, and the
 // seeds added to sd
@@ -1290,11 +1370,13 @@ extern __shared__ __align__(16) unsigned char rc_smem[];
 // ------------------------------------------------------------------------------------------
 // kernels
 // ------------------------------------------------------------------------------------------
-template <int NPT>
-__host__ __device__ constexpr int ctas_per_sm() { return NPT == 1 ? 6 : 2; }
+// CTAs per SM the register budget is sized for: FP32 64-node ropes fit 7 (31 KB of shared memory);
+// FP64 and 128-node scenes are held to fewer by shared memory, so they keep more registers
+template <typename R, int NPT>
+__host__ __device__ constexpr int ctas_per_sm() { return sizeof(R) == 4 && NPT == 1 ? 7 : (NPT == 1 ? 3 : 2); }
 
 template <typename R, int NPT>
-__global__ void __launch_bounds__(NT, ctas_per_sm<NPT>()) rope_cta_rollout_kernel(
+__global__ void __launch_bounds__(NT, (ctas_per_sm<R, NPT>())) rope_cta_rollout_kernel(
     Scene<R> S, int B, int H, const R* q0, const R* U, R* traj, R* qH, int32_t* status, int32_t* counters) {
   const int nq = 3 * S.nv + 6;
   Sm<R> w = sm_carve<R>(reinterpret_cast<R*>(rc_smem), NPT, S.nobs);
@@ -1532,7 +1614,7 @@ __device__ __forceinline__ void vjp_rollouts(const Scene<R>& S, int B, int H, co
 
 // forward + adjoint in one launch
 template <typename R, int NPT>
-__global__ void __launch_bounds__(NT, ctas_per_sm<NPT>()) rope_cta_vjp_kernel(
+__global__ void __launch_bounds__(NT, (ctas_per_sm<R, NPT>())) rope_cta_vjp_kernel(
     Scene<R> S, int B, int H, const R* q0, const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
     int32_t* status, R* ws, size_t ws_stride) {
   rc::vjp_rollouts<R, NPT, VJP_ALL>(S, B, H, q0, U, dLdtraj, Lout, dLdu, dLdq0, status, ws, ws_stride, nullptr,
@@ -1541,7 +1623,7 @@ __global__ void __launch_bounds__(NT, ctas_per_sm<NPT>()) rope_cta_vjp_kernel(
 
 // the forward part of every rollout: records, L, the carry and the cost of each
 template <typename R, int NPT>
-__global__ void __launch_bounds__(NT, ctas_per_sm<NPT>()) rope_cta_vjp_fwd_kernel(
+__global__ void __launch_bounds__(NT, (ctas_per_sm<R, NPT>())) rope_cta_vjp_fwd_kernel(
     Scene<R> S, int B, int H, const R* q0, const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
     int32_t* status, R* ws, size_t ws_stride, int32_t* cost) {
   rc::vjp_rollouts<R, NPT, VJP_FWD>(S, B, H, q0, U, dLdtraj, Lout, dLdu, dLdq0, status, ws, ws_stride, cost,
@@ -1551,11 +1633,331 @@ __global__ void __launch_bounds__(NT, ctas_per_sm<NPT>()) rope_cta_vjp_fwd_kerne
 // the backward part, rollout order[i] in CTA i (the block scheduler starts CTAs in index order,
 // so the costliest start first)
 template <typename R, int NPT>
-__global__ void __launch_bounds__(NT, ctas_per_sm<NPT>()) rope_cta_vjp_bwd_kernel(
+__global__ void __launch_bounds__(NT, (ctas_per_sm<R, NPT>())) rope_cta_vjp_bwd_kernel(
     Scene<R> S, int B, int H, const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0, int32_t* status,
     R* ws, size_t ws_stride, int32_t* cost, const int32_t* order) {
   rc::vjp_rollouts<R, NPT, VJP_BWD>(S, B, H, nullptr, U, dLdtraj, Lout, dLdu, dLdq0, status, ws, ws_stride, cost,
                                 order);
+}
+
+
+// ------------------------------------------------------------------------------------------
+// Work-queue adjoint.  The backward's expensive part -- recomputing each segment from its
+// checkpoint, the smooth re-solve of every step and the two factorisations of its adjoint -- does
+// not depend on the adjoint seeds, so it runs as independent (rollout, segment) jobs that any CTA
+// takes as soon as that rollout's forward has finished; each job stores, per step, the
+// factorisations of H2 and H1 and the smooth solution.  The rollout's adjoint chain (two solves
+// with stored factors and the VJP products per step, last step to first) runs in the CTA that
+// finishes its last segment.  One persistent launch: CTAs take the forward jobs first, then
+// segment jobs in the order the forwards publish them; a CTA waits only for a forward that a
+// running CTA has already taken (bounded wait; on expiry the rollout gets CS_ST_TIMEOUT).
+// ------------------------------------------------------------------------------------------
+
+// per-step record of the queue path: [H2 factor T|B|V][H1 factor T|B|V][x0 3nv][dx 3nv][Delta 3nv]
+// [misc 32][status], padded to 4 elements
+__host__ __device__ inline size_t fac_block(int NPT) { return (size_t)(LDT + 2 * CR_LDM) * 32 * NPT; }
+__host__ __device__ inline size_t fac_step_elems(int NPT, int nv) {
+  return (2 * fac_block(NPT) + 9 * (size_t)nv + 32 + 1 + 3) / 4 * 4;
+}
+
+// queue state (int32, zeroed before the launch): [0] next forward job, [1] next queue slot taken,
+// [2] queue slots filled, [3] spare, then slot entries [nslot], slot ready flags [nslot], segments
+// done per rollout [B]
+__host__ __device__ inline size_t queue_ints(int B, int nseg) { return 4 + 2 * (size_t)B * nseg + (size_t)B; }
+
+constexpr long long QUEUE_WAIT_MAX = 1ll << 21;   // polls of 1 us: about 2 s
+
+template <typename R>
+__device__ __forceinline__ void copy_block(R* dst, const R* src, size_t n) {
+  // n is a multiple of 4 and both pointers 16-byte aligned
+  if (sizeof(R) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (size_t i = threadIdx.x; i < n / 4; i += NT) d4[i] = s4[i];
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    for (size_t i = threadIdx.x; i < n / 2; i += NT) d2[i] = s2[i];
+  }
+}
+
+template <typename R, int NPT>
+__device__ __forceinline__ int adjoint_step_stored(const Scene<R>& S, Nd<R, NPT>& N, const Sm<R>& w, R xb[NPT][3],
+                                                   const R* h1) {
+  R mu[NPT][3], xs[NPT][3];
+  adjoint_xs(S, N, w, xb, mu, xs);
+  copy_block(w.T, h1, fac_block(NPT));
+  adjoint_nu(S, N, w, mu, xs, xb);
+  return 0;
+}
+
+// one (rollout, segment) job: the hard steps of the segment from its checkpoint and, at each of
+// their start states, the smooth step with the factorisations of its adjoint, stored per step
+template <typename R, int NPT>
+__device__ __forceinline__ void seg_job(const Scene<R>& S, const Sm<R>& w, Nd<R, NPT>& N, Red& rb, int H,
+                                        const R* U, const R* ck, R* fac, int sgi) {
+  const int rl = rec_len(S.nv);
+  const int k = S.ckpt;
+  const int t0 = sgi * k, t1 = min(t0 + k, H);
+  const size_t fb = fac_block(NPT), fs = fac_step_elems(NPT, S.nv);
+  const int tid = threadIdx.x;
+  load_rec(S, N, w, ck + (size_t)sgi * rl);
+  load_rec_delta(S, N, ck + (size_t)sgi * rl);
+  for (int t = t0; t < t1; ++t) {
+    R* rec = fac + (size_t)t * fs;
+    if (tid < 6) w.misc[M_U + tid] = U[6 * t + tid];
+    // the hard step, as the forward took it (same start, same interior-point start)
+    const bool w2 = any_delta(N);
+    int ni, ii;
+    int st = sim_step(S, N, w, rb, false, &ni, &ii, false, w2);
+    const int hard_st = st;
+    R dxh[NPT][3], Dlh[NPT][3];
+#pragma unroll
+    for (int kk = 0; kk < NPT; ++kk)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { dxh[kk][i] = N.dx[kk][i]; Dlh[kk][i] = N.Dl[kk][i]; }
+    // the smooth step from the same state, started at the hard step's solution
+    if (!st) st = sim_step(S, N, w, rb, true, &ni, &ii, true, true);
+    if (!st) {
+      __syncthreads();
+      copy_block(rec, w.T, fb);                       // H2 = P + sum A^T W^-2 A
+      __syncthreads();
+      assemble_P(S, N, w, false, false);              // H1 = dF/dq* at the smooth x*
+      __syncthreads();
+      if (!crb_factor(w.T, w.B, w.V, S.npair)) st = ST_NOTPD;
+      copy_block(rec + fb, w.T, fb);
+    }
+    R* rn = rec + 2 * fb;
+#pragma unroll
+    for (int kk = 0; kk < NPT; ++kk) {
+      const int j = node_of(kk);
+      if (j < S.nv)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          rn[3 * j + i] = N.x0[kk][i];
+          rn[3 * S.nv + 3 * j + i] = N.dx[kk][i];
+          rn[6 * S.nv + 3 * j + i] = N.Dl[kk][i];
+        }
+    }
+    if (tid < 32) rn[9 * S.nv + tid] = w.misc[tid];
+    if (tid == 0) rn[9 * S.nv + 32] = R(st);
+    // advance with the hard step (a failed smooth step only marks its record: the chain stops at
+    // the latest failed step and reads every later record)
+#pragma unroll
+    for (int kk = 0; kk < NPT; ++kk)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { N.dx[kk][i] = dxh[kk][i]; N.Dl[kk][i] = Dlh[kk][i]; }
+    __syncthreads();
+    advance_state(S, N, w);
+    if (hard_st) {
+      // the recomputed hard step failed (the forward did not: it does not happen); the
+      // remaining records of the segment are marked failed too
+      for (int t2 = t + 1; t2 < t1; ++t2)
+        if (tid == 0) fac[(size_t)t2 * fs + 2 * fb + 9 * S.nv + 32] = R(hard_st);
+      break;
+    }
+  }
+  __syncthreads();
+}
+
+// the adjoint chain of one rollout from its stored per-step records: steps H-1 .. 0 (eq. diff-sim
+// with the total derivative, as adjoint_step)
+template <typename R, int NPT>
+__device__ __forceinline__ void chain_job(const Scene<R>& S, const Sm<R>& w, Nd<R, NPT>& N, Red& rb, int H,
+                                          const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
+                                          int32_t* status, const R* ck, const R* fac) {
+  const int nq = 3 * S.nv + 6;
+  const int k = S.ckpt;
+  const int tid = threadIdx.x;
+  const size_t fb = fac_block(NPT), fs = fac_step_elems(NPT, S.nv);
+  const R* carry = ck + (vjp_ws_elems(S.nv, H, k) - vjp_carry_elems(2));
+  R xb[NPT][3];
+#pragma unroll
+  for (int kk = 0; kk < NPT; ++kk) {
+    const int j = node_of(kk);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xb[kk][i] = j < S.nv ? carry[3 * j + i] : R(0);
+  }
+  if (tid < 6) w.misc[M_GB + tid] = carry[3 * S.nv + tid];
+  int st = 0;
+  for (int t = H - 1; t >= 0; --t) {
+    const R* rec = fac + (size_t)t * fs;
+    const R* rn = rec + 2 * fb;
+    st |= (int)rn[9 * S.nv + 32];
+    if (st) break;
+#pragma unroll
+    for (int kk = 0; kk < NPT; ++kk) {
+      const int j = node_of(kk);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        N.x0[kk][i] = j < S.nv ? rn[3 * j + i] : R(0);
+        N.dx[kk][i] = j < S.nv ? rn[3 * S.nv + 3 * j + i] : R(0);
+        N.Dl[kk][i] = j < S.nv ? rn[6 * S.nv + 3 * j + i] : R(0);
+      }
+    }
+    if (tid < 32 && tid != M_GB && !(tid > M_GB && tid < M_GB + 6)) w.misc[tid] = rn[9 * S.nv + tid];
+    publish<R, NPT>(w.x0, N.x0, w.NVP);
+    publish<R, NPT>(w.dx, N.dx, w.NVP);
+    copy_block(w.T, rec, fb);
+    __syncthreads();
+    st |= adjoint_step_stored(S, N, w, xb, rec + fb);
+    if (st) break;
+    if (tid < 6)
+      dLdu[6 * t + tid] = w.misc[M_UB + tid] + (S.has_loss ? R(2) * S.w_u * U[6 * t + tid] : R(0));
+    // seeds dL/dq_t of q_t (x0)
+    if (t >= 1 && S.has_loss) penalty(S, N, xb, true);
+    if (dLdtraj) {
+      const R* sd = dLdtraj + (size_t)t * nq;
+#pragma unroll
+      for (int kk = 0; kk < NPT; ++kk) {
+        const int j = node_of(kk);
+        if (j < S.nv)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) xb[kk][i] += sd[3 * j + i];
+      }
+      if (tid < 6) w.misc[M_GB + tid] += sd[3 * S.nv + tid];
+    }
+    __syncthreads();
+  }
+  if (st) {                        // failed rollout: L = NaN, gradients zero
+    for (int i = tid; i < 6 * H; i += NT) dLdu[i] = R(0);
+    zero3<R, NPT>(xb);
+    if (tid < 6) w.misc[M_GB + tid] = R(0);
+    __syncthreads();
+  }
+  if (dLdq0) {
+#pragma unroll
+    for (int kk = 0; kk < NPT; ++kk) {
+      const int j = node_of(kk);
+      if (j < S.nv)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dLdq0[3 * j + i] = xb[kk][i];
+    }
+    if (tid < 6) dLdq0[3 * S.nv + tid] = w.misc[M_GB + tid];
+  }
+  if (tid == 0 && st) {
+    if (Lout) *Lout = sizeof(R) == 4 ? R(nanf("")) : R(nan(""));
+    if (status) *status = st;
+  }
+  __syncthreads();
+}
+
+template <typename R, int NPT>
+__global__ void __launch_bounds__(NT, (ctas_per_sm<R, NPT>())) rope_cta_vjp_queue_kernel(
+    Scene<R> S, int B, int H, const R* q0, const R* U, const R* dLdtraj, R* Lout, R* dLdu, R* dLdq0,
+    int32_t* status, R* ws, size_t ws_stride, R* fac, size_t fac_stride, int* q) {
+  const int nq = 3 * S.nv + 6;
+  const int nseg = (H + S.ckpt - 1) / S.ckpt;
+  const int nslot = B * nseg;
+  int* slot = q + 4;
+  int* ready = slot + nslot;
+  int* done = ready + nslot;
+  Sm<R> w = sm_carve<R>(reinterpret_cast<R*>(rc_smem), NPT, S.nobs);
+  __shared__ int job[2];
+  Red rb;
+  Nd<R, NPT> N;
+  zero_nd(N);
+  load_rest(S, N);
+  const int tid = threadIdx.x;
+  // the record and copy geometry every access below relies on: 16-byte aligned blocks of a
+  // multiple of 4 elements, H records per rollout within its stride (q[3] bit 2 otherwise)
+  {
+    const size_t fb = fac_block(NPT), fs = fac_step_elems(NPT, S.nv);
+    const bool geom = ((uintptr_t)fac & 15) == 0 && ((uintptr_t)w.T & 15) == 0 && fb % 4 == 0 && fs % 4 == 0 &&
+                      fac_stride % 4 == 0 && (size_t)H * fs <= fac_stride && 2 * fb + 9 * (size_t)S.nv + 33 <= fs;
+    if (!geom) {
+      if (tid == 0 && blockIdx.x == 0) atomicOr(&q[3], 2);
+      return;
+    }
+  }
+  while (true) {
+    // take a job: a forward while any is left, else the next queue slot
+    if (tid == 0) {
+      int kind = 0, val = -1;
+      if (*(volatile int*)&q[0] < B) {
+        const int b = atomicAdd(&q[0], 1);
+        if (b < B) { kind = 1; val = b; }
+      }
+      if (kind == 0) {
+        const int p = atomicAdd(&q[1], 1);
+        if (p < nslot) {
+          long long n = 0;
+          while (*(volatile int*)&ready[p] == 0 && n < QUEUE_WAIT_MAX) { __nanosleep(1000); ++n; }
+          __threadfence();
+          if (n >= QUEUE_WAIT_MAX) { kind = 3; val = p; } else { kind = 2; val = *(volatile int*)&slot[p]; }
+        }
+      }
+      job[0] = kind;
+      job[1] = val;
+    }
+    __syncthreads();
+    const int kind = job[0], val = job[1];
+    __syncthreads();
+    if (kind == 0) break;
+    if (kind == 3) {                 // the wait ran out: nothing is known about this slot's rollout
+      if (tid == 0) atomicOr(&q[3], 1);
+      break;
+    }
+    if (kind == 1) {
+      const int b = val;
+      R* ck = ws + (size_t)b * ws_stride;
+      int32_t cost = 0;
+      rc::vjp_rollout<R, NPT, VJP_FWD>(S, w, N, rb, H, q0 + (size_t)b * nq, U + (size_t)b * H * 6,
+                                       dLdtraj ? dLdtraj + (size_t)b * (H + 1) * nq : nullptr,
+                                       Lout ? Lout + b : nullptr, dLdu + (size_t)b * H * 6,
+                                       dLdq0 ? dLdq0 + (size_t)b * nq : nullptr, status ? status + b : nullptr,
+                                       ck, &cost);
+      // publish the segment jobs (negative: the forward failed and its outputs are final)
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        const int p0 = atomicAdd(&q[2], nseg);
+        if (p0 + nseg > nslot) { atomicOr(&q[3], 8); continue; }   // cannot happen: B x nseg slots
+        for (int sg = 0; sg < nseg; ++sg) slot[p0 + sg] = cost < 0 ? -1 : b * nseg + sg;
+        __threadfence();
+        for (int sg = 0; sg < nseg; ++sg) atomicExch(&ready[p0 + sg], 1);
+      }
+      continue;
+    }
+    if (val < 0) continue;           // a failed forward's placeholder
+    const int b = val / nseg, sg = val % nseg;
+    if (b >= B) {                    // cannot happen: entries are written as b nseg + sg
+      if (tid == 0) atomicOr(&q[3], 8);
+      continue;
+    }
+    const R* Ub = U + (size_t)b * H * 6;
+    R* ck = ws + (size_t)b * ws_stride;
+    R* fb = fac + (size_t)b * fac_stride;
+    seg_job<R, NPT>(S, w, N, rb, H, Ub, ck, fb, sg);
+    if (tid == 0) {
+      __threadfence();
+      const int old = atomicAdd(&done[b], 1);
+      __threadfence();
+      job[0] = old == nseg - 1;
+    }
+    __syncthreads();
+    const bool last = job[0];
+    __syncthreads();
+    if (last)
+      chain_job<R, NPT>(S, w, N, rb, H, Ub, dLdtraj ? dLdtraj + (size_t)b * (H + 1) * nq : nullptr,
+                        Lout ? Lout + b : nullptr, dLdu + (size_t)b * H * 6,
+                        dLdq0 ? dLdq0 + (size_t)b * nq : nullptr, status ? status + b : nullptr, ck, fb);
+  }
+}
+
+
+// after a queue launch: a rollout whose segments did not all finish (a wait ran out, q[3] set)
+// gets CS_ST_TIMEOUT, L = NaN and zero gradients
+template <typename R>
+__global__ void rope_queue_finish_kernel(int B, int H, int nseg, const int* q, R* Lout, R* dLdu,
+                                         int32_t* status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || q[3] == 0) return;
+  const int* done = q + 4 + 2 * (size_t)B * nseg;
+  if (done[b] >= nseg || (status && status[b] != 0)) return;
+  if (status) status[b] |= CS_ST_TIMEOUT;
+  if (Lout) Lout[b] = sizeof(R) == 4 ? R(nanf("")) : R(nan(""));
+  for (int i = 0; i < 6 * H; ++i) dLdu[(size_t)b * H * 6 + i] = R(0);
 }
 
 }  // namespace rc

@@ -123,10 +123,12 @@ def test_noalloc_rejects_oversized_batches():
     assert b"CS_NOALLOC_SCRATCH_BYTES" in lib.cs_last_error()
 
 
-def test_noalloc_benchmark_batch_two_part_launch():
-    """The benchmark's 1024 rollouts (more than the device holds at once: forward parts, cost
-    order and backward parts, the order arrays inside the fixed scratch) equal the handle-based
-    call, bit for bit."""
+def test_noalloc_benchmark_batch_without_the_work_queue():
+    """The benchmark's 1024 rollouts: the allocation-free call runs the adjoint without the work
+    queue (it has no room for per-step records: one launch, each rollout's forward and backward in
+    one CTA), the handle-based call through it; same flags, results within the FP32 tolerances
+    (the two kernels inline the same device code in different contexts, so the compiler may round
+    a contraction differently)."""
     from paper_2606_14188_b300 import scenes, _lib
     from paper_2606_14188_b300.sim import Sim, make_params, make_loss
     lib = _lib.lib()
@@ -135,7 +137,7 @@ def test_noalloc_benchmark_batch_two_part_launch():
     B, H = w["B"], w["H"]
     q0 = torch.tensor(w["q0"], dtype=torch.float32, device="cuda")
     U = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
-    ref = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H).rollout_vjp(q0, U)
+    Lr, dUr, dqr, str_ = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H).rollout_vjp(q0, U)
     params = make_params(sc, 4, B, H)
     loss = make_loss(sc)
     rest = np.ascontiguousarray(sc["rest_x"], dtype=np.float64)
@@ -143,5 +145,10 @@ def test_noalloc_benchmark_batch_two_part_launch():
     code, Lv, dU, dq0, st = _call_noalloc(lib, params, rest, q0, U, loss, stream, 4)
     torch.cuda.synchronize()
     assert code == 0, lib.cs_last_error()
-    for a, b in zip((Lv, dU, dq0, st), ref):
-        assert torch.equal(a.isnan(), b.isnan()) and torch.equal(a.nan_to_num(), b.nan_to_num())
+    assert torch.equal(st, str_)
+    ok = st == 0
+    tol_s, tol_g = TOL[4]
+    assert float((Lv[ok] - Lr[ok]).abs().max() / Lr[ok].abs().max()) <= tol_s
+    for a, b in ((dU[ok], dUr[ok]), (dq0[ok], dqr[ok])):
+        assert float((a - b).norm() / b.norm()) <= tol_g
+    assert bool(Lv[~ok].isnan().all()) and bool((dU[~ok] == 0).all())
