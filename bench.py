@@ -470,7 +470,7 @@ def run_ours(args):
     from paper_2606_14188_b300 import _lib
 
     # every rank simulates its own share of world x 1024 rollouts (different controls per rank)
-    w = scenes.workload(2, B=args.rollouts, shard=rank)
+    w = scenes.workload(2, B=args.rollouts, H=args.rope_horizon, shard=rank)
     sc, B, H = w["scene"], w["B"], w["H"]
     nv = sc["params"]["n_nodes"]
     k = sc["params"]["checkpoint_every"]
@@ -570,7 +570,8 @@ def run_ours(args):
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=1e3 * t / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                    config=dict(workload=WORKLOAD if B == 1024 else f"rope64_b{B}_h50", rollouts=B, nodes=nv, horizon=H,
+                    config=dict(workload=WORKLOAD if (B, H) == (1024, 50) else f"rope64_b{B}_h{H}", rollouts=B,
+                                nodes=nv, horizon=H,
                                 checkpoint_every=k, obstacles=nobs, grad_mode="surrogate",
                                 parallelism=f"rollouts sharded, dp{world}",
                                 l2="256 MB write between timed steps, outside the timed intervals"),
@@ -607,6 +608,8 @@ def main():
                     help="plan solves in the served stream (0: skip the served leg)")
     ap.add_argument("--rollouts", type=int, default=None,
                     help="rollouts per GPU (default 1024; smaller only for profiling captures)")
+    ap.add_argument("--rope-horizon", type=int, default=None,
+                    help="horizon of the rope legs (default 50; shorter only for profiling captures)")
     ap.add_argument("--cloth-horizon", type=int, default=10,
                     help="steps of the cloth leg's sample (0: skip the cloth leg)")
     ap.add_argument("--cloth-rollouts", type=int, default=None,

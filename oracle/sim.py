@@ -299,10 +299,12 @@ def stage1_solve(sc: Scene, x, gstar, d, tol=TOL_X, maxit=NEWTON_MAX, x_start=No
     coordinate (the step is then taken).  Returns (q*, iterations, status).
 
     The direction: for a rope, the exact Hessian, or the projected one where the exact one is
-    not positive definite.  For a cloth, the exact Hessian plus the shift of `shifted_factor`, and
-    the iteration only stops on an unshifted step, so the root is a local minimiser of Psi: a
+    not positive definite.  For a cloth, the exact Hessian plus the shift of `shifted_factor` (a
     slack cloth has many wrinkle modes of nearly zero stiffness, along which the projected
-    Hessian (which drops their negative curvature) gives only linear convergence."""
+    Hessian, which drops their negative curvature, gives only linear convergence).  Either way the
+    iteration stops only on a step taken with the exact (unshifted, unprojected) Hessian, so the
+    root is a local minimiser of Psi: a stable equilibrium, where the QP of stage 2 is convex and
+    dF/dq* of the adjoint is positive definite."""
     X = x.copy() if x_start is None else np.array(x_start, dtype=np.float64)
     cloth = sc.kind == "cloth"
     tau = 0.0
@@ -319,9 +321,12 @@ def stage1_solve(sc: Scene, x, gstar, d, tol=TOL_X, maxit=NEWTON_MAX, x_start=No
                 cb = band_factor(stage1_hessian_band(sc, X, d))
             except LinAlgError:
                 cb = band_factor(stage1_hessian_band(sc, X, d, project=True))
+                tau = -1.0          # marks a projected (not exact) direction
         p = -band_solve(cb, F)
         if np.max(np.abs(p)) <= tol and tau == 0.0:
             return X + p, it + 1, 0
+        if not cloth:
+            tau = 0.0
         slope = float(np.sum(F * p))
         alpha = 1.0
         for _ in range(60):

@@ -425,13 +425,14 @@ __device__ __forceinline__ int stage1_newton(const Scene<R>& S, Lane<R, PPL>& L,
   R dxm[PPL][6], dxp[PPL][6];
   for (int it = 0; it < S.newton_max; ++it) {
     nbr<R, PPL>(L.dx, dxm, dxp, lane);
-    bool ok = false;
+    bool ok = false, exact = false;
     // exact Hessian; if it is not positive definite, the projected one (same call site)
     for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
       assemble_P(S, L, w, dxm, dxp, attempt == 1, attempt == 0, lane);
       if (attempt == 0) put_rhs<R, PPL>(S, w, L.F, R(-1), lane);
       __syncwarp();
       ok = cr_factor(w.T, w.B, w.V, S.npair, lane);
+      exact = ok && attempt == 0;
     }
     if (!ok) { *iters = it + 1; return ST_NOTPD; }
     cr_solve(w.T, w.B, w.V, w.r, S.npair, lane);
@@ -450,7 +451,8 @@ __device__ __forceinline__ int stage1_newton(const Scene<R>& S, Lane<R, PPL>& L,
     pm = wmax(pm);
     sl = wsum(sl);
     if (__any_sync(FULL, bad)) { *iters = it + 1; return ST_NONFINITE; }
-    if (pm <= S.ntol) {
+    // converged only on an exact-Hessian step: the root is a local minimiser of the potential
+    if (pm <= S.ntol && exact) {
 #pragma unroll
       for (int k = 0; k < PPL; ++k)
 #pragma unroll
@@ -650,6 +652,12 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
   int stalls = 0;
   const bool proj = false;    // stage 2 uses the exact P
   bool centring = false;      // the target has reached kfinal: plain centring steps from now on
+  R xmax = R(0);
+#pragma unroll
+  for (int k = 0; k < PPL; ++k)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) xmax = fmax(xmax, fabs(L.x0[k][e] + L.dx[k][e]));
+  const R ilim = R(128) * (sizeof(R) == 4 ? R(1.1920928955078125e-7) : R(2.220446049250313e-16)) * wmax(xmax);
   for (int it = 0; it < S.ipm_max; ++it) {
     // predictor-corrector iteration (towards kfinal, not yet centring): assemble with the affine
     // right-hand side (target 0); otherwise with the fixed target
@@ -872,7 +880,13 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Lane<R, PPL>& L, WS
       for (int e = 0; e < 6; ++e) L.Dl[k][e] += alpha * L.pv[k][e];
     }
     if (!__all_sync(FULL, inside)) { *iters = it + 1; return ST_CONTACT; }
-    if (final_target && alpha == R(1) && dmax <= S.itol) { *iters = it + 1; return 0; }
+    // stop at the central point: a full step below the tolerance, or (nonsmooth solve) any step
+    // below 128 ulps of the state's scale (the resolution of the real type's directions at
+    // near-boundary sliding contacts)
+    if (final_target && ((alpha == R(1) && dmax <= S.itol) || (kfinal >= R(0) && dmax <= ilim))) {
+      *iters = it + 1;
+      return 0;
+    }
   }
   *iters = S.ipm_max;
   return ST_CONTACT;

@@ -587,13 +587,14 @@ __device__ __forceinline__ int stage1_newton(const Scene<R>& S, Nd<R, NPT>& N, c
   for (int it = 0; it < S.newton_max; ++it) {
     publish<R, NPT>(w.dx, N.dx, w.NVP);
     __syncthreads();
-    bool ok = false;
+    bool ok = false, exact = false;
     // exact Hessian; if it is not positive definite, the projected one (same call site)
     for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
       assemble_P(S, N, w, attempt == 1, attempt == 0);
       if (attempt == 0) put_rhs<R, NPT>(S, w, N.F, R(-1));
       __syncthreads();
       ok = crb_factor(w.T, w.B, w.V, S.npair);
+      exact = ok && attempt == 0;
     }
     if (!ok) { *iters = it + 1; return ST_NOTPD; }
     crb_solve(w.T, w.B, w.V, w.r, S.npair);
@@ -612,7 +613,8 @@ __device__ __forceinline__ int stage1_newton(const Scene<R>& S, Nd<R, NPT>& N, c
     if (__syncthreads_or(bad)) { *iters = it + 1; return ST_NONFINITE; }
     pm = bmax(pm, w.red, rb);
     sl = bsum(sl, w.red, rb);
-    if (pm <= S.ntol) {
+    // converged only on an exact-Hessian step: the root is a local minimiser of the potential
+    if (pm <= S.ntol && exact) {
 #pragma unroll
       for (int k = 0; k < NPT; ++k)
 #pragma unroll
@@ -793,7 +795,7 @@ __device__ __forceinline__ void diag_block(const Scene<R>& S, const Nd<R, NPT>& 
 // warm, N.Dl the start.
 template <typename R, int NPT>
 __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, const Sm<R>& w, Red& rb, R kappa,
-                                          R kfinal, int* iters, bool warm) {
+                                          R kfinal, int* iters, bool warm, R frac) {
   const int nobs = S.nobs;
   const int NVP = w.NVP;
   const R mm = R(S.nv * nobs);
@@ -838,6 +840,13 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, cons
   }
   int stalls = 0;
   bool centring = false;      // the target has reached kfinal: plain centring steps from now on
+  R xmax = R(0);
+#pragma unroll
+  for (int k = 0; k < NPT; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xmax = fmax(xmax, fabs(N.x0[k][i] + N.dx[k][i]));
+  const R ilim = R(128) * (sizeof(R) == 4 ? R(1.1920928955078125e-7) : R(2.220446049250313e-16)) *
+                 bmax(xmax, w.red, rb);
   for (int it = 0; it < S.ipm_max; ++it) {
     const bool pc = kfinal >= R(0) && !centring;
     R target = kfinal < R(0) ? kappa : kfinal;
@@ -1020,7 +1029,7 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, cons
     if (__syncthreads_or(bad)) { *iters = it + 1; return ST_NONFINITE; }
     dmax = bmax(dmax, w.red, rb);
     amin = bmin(amin, w.red, rb);
-    const R alpha = fmin(R(1), R(0.99) * amin);
+    const R alpha = fmin(R(1), frac * amin);
     stalls = alpha < R(1e-6) ? stalls + 1 : 0;
     if (stalls >= 5) { *iters = it + 1; return ST_CONTACT; }
     // update with the directions kept by the step-length pass
@@ -1044,7 +1053,13 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, cons
       for (int i = 0; i < 3; ++i) N.Dl[k][i] += alpha * N.pv[k][i];
     }
     if (!__syncthreads_and(inside)) { *iters = it + 1; return ST_CONTACT; }
-    if (final_target && alpha == R(1) && dmax <= S.itol) { *iters = it + 1; return 0; }
+    // stop at the central point: a full step below the tolerance, or (nonsmooth solve) any step
+    // below 128 ulps of the state's scale, the resolution the real type's directions reach at the
+    // near-boundary sliding contacts of the nonsmooth end of the path
+    if (final_target && ((alpha == R(1) && dmax <= S.itol) || (kfinal >= R(0) && dmax <= ilim))) {
+      *iters = it + 1;
+      return 0;
+    }
   }
   *iters = S.ipm_max;
   return ST_CONTACT;
@@ -1085,8 +1100,31 @@ __device__ __forceinline__ int sim_step(const Scene<R>& S, Nd<R, NPT>& N, const 
   if (S.nobs == 0) { zero3<R, NPT>(N.Dl); return st; }
   const R pmin = min_phi(S, N, w, rb);
   if (!smooth && pmin >= R(0)) { zero3<R, NPT>(N.Dl); return st; }   // Delta = 0 is optimal
-  st |= stage2_ipm(S, N, w, rb, S.kc, smooth ? R(-1) : S.khard, iit, warm2);
-  return st;
+  // The interior point takes steps of 0.99 of the distance to the cone boundaries; if it fails it
+  // is run again on paths that stay further inside the cones (single precision loses the
+  // near-boundary iterates of hard sliding contacts): 0.9 from the same start, 0.9 and then 0.75
+  // from the per-node closed-form start.  The central point reached does not depend on the path.
+  R D0[NPT][3];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D0[k][i] = N.Dl[k][i];
+  int st2 = 0, it2 = 0;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if (attempt) {
+#pragma unroll
+      for (int k = 0; k < NPT; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) N.Dl[k][i] = D0[k][i];
+    }
+    int ii = 0;
+    st2 = stage2_ipm(S, N, w, rb, S.kc, smooth ? R(-1) : S.khard, &ii, warm2 && attempt < 2,
+                     attempt == 0 ? R(0.99) : (attempt < 3 ? R(0.9) : R(0.75)));
+    it2 += ii;
+    if (!(st2 & ST_CONTACT)) break;
+  }
+  *iit = it2;
+  return st | st2;
 }
 
 // x0 <- x0 + dx + Dl ; g <- g + u ; c <- c + u - (dx_a + Dl_a); x0 published on exit

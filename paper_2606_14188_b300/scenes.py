@@ -263,4 +263,10 @@ def workload(i: int, B: int | None = None, H: int | None = None, shard: int = 0)
         raise ValueError(f"unknown workload {i}")
     sc = copy.deepcopy(sc)
     sc["params"]["checkpoint_every"] = ck
+    if real == 4:
+        # the nonsmooth contact problem is declared solved at the central point of kappa_hard,
+        # whose contact slacks are O(kappa_hard / lam_n): at 1e-6 N m and the 1-2 N sliding
+        # contacts of these scenes they are below what single precision resolves at the state's
+        # metre scale, at 1e-5 (10 um of slack at 1 N, under the FP32 state tolerance) they are not
+        sc["params"]["kappa_hard"] = 1.0e-5
     return dict(scene=sc, B=B, H=H, U=U, q0=batch_q0(sc, B), real_bytes=real, seed=seed)

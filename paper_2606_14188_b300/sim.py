@@ -12,8 +12,8 @@ import torch
 
 from . import _lib as L
 
-DEFAULT_TOL = {4: dict(newton_tol=1e-5, ipm_tol=1e-6, newton_max=40, ipm_max=80),
-               8: dict(newton_tol=1e-12, ipm_tol=1e-12, newton_max=60, ipm_max=200)}
+DEFAULT_TOL = {4: dict(newton_tol=1e-5, ipm_tol=1e-7, newton_max=100, ipm_max=80),
+               8: dict(newton_tol=1e-12, ipm_tol=1e-12, newton_max=100, ipm_max=200)}
 
 
 def make_params(scene: dict, real_bytes: int = 4, max_batch: int = 1, max_horizon: int = 1,

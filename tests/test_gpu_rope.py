@@ -118,27 +118,40 @@ def test_rope64_fp32_vjp_vs_oracle():
     assert clean >= B // 2
 
 
-def test_rope64_full_batch_sampled():
-    """The launch the benchmark times (1024 rollouts x 50 steps): sampled rollouts against the
-    oracle.  The FP32 interior point may give up (CS_ST_CONTACT) on hard contact steps that the
-    FP64 oracle still solves; that fraction is bounded here and reported by the benchmark."""
+def test_rope64_full_batch_flags_and_values_match_the_oracle():
+    """The launch the benchmark times (1024 rollouts x 50 steps, FP32): on 256 of its rollouts
+    (every fourth) the status flags equal the oracle's, rollout for rollout, and every rollout the
+    oracle completes is within 1e-4 on its nonsmooth trajectory, within 1e-4 on L and within 1e-3
+    with cosine >= 0.999 on dL/du.  A flagged rollout stops at its failing step: L NaN, gradient 0."""
+    import multiprocessing as mp
+    import os
+    from tests import oracle_jobs
     w = scenes.workload(2)
     sc = w["scene"]
     B, H = w["B"], w["H"]
     s = _sim(sc, 4, B, H)
-    Lv, dU, _, st = s.rollout_vjp(_t(w["q0"], 4), _t(w["U"], 4), want_dq0=False)
-    st = st.cpu().numpy()
-    assert np.count_nonzero(st) <= B // 16, np.unique(st, return_counts=True)
-    # a failed rollout stops at its failing step: L is NaN, the gradient zero
+    q0, U = _t(w["q0"], 4), _t(w["U"], 4)
+    traj, _, st_f = s.rollout(q0, U)
+    Lv, dU, _, st = s.rollout_vjp(q0, U, want_dq0=False)
+    traj, st_f, st = traj.cpu().numpy(), st_f.cpu().numpy(), st.cpu().numpy()
+    Lv, dU = Lv.cpu().numpy(), dU.cpu().numpy()
     fl = st != 0
-    assert np.all(np.isnan(Lv.cpu().numpy()[fl])) and np.all(dU.cpu().numpy()[fl] == 0)
-    assert np.all(np.isfinite(Lv.cpu().numpy()[~fl])) and np.all(np.isfinite(dU.cpu().numpy()[~fl]))
-    osc = _oscene(sc)
-    for b in (0, 517, 777, B - 1):
-        ref = ograd.rollout_vjp(osc, w["q0"][b], w["U"][b], "surrogate")
-        if int(st[b]) == 0 and ref["status"] == 0:
-            assert abs(float(Lv[b]) - ref["L"]) <= TOL_STATE32 * abs(ref["L"])
-            check_grad(dU[b].cpu().numpy(), ref["dL_du"], TOL_GRAD32, COS32)
+    assert np.all(np.isnan(Lv[fl])) and np.all(dU[fl] == 0)
+    assert np.all(np.isfinite(Lv[~fl])) and np.all(np.isfinite(dU[~fl]))
+    idx = list(range(0, B, 4))
+    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 32))) as pool:
+        refs = pool.map(oracle_jobs.rope64_rollout, idx)
+    clean = 0
+    for r in refs:
+        b = r["b"]
+        assert (int(st[b]) != 0) == (r["status"] != 0), (b, int(st[b]), r["status"])
+        assert (int(st_f[b]) != 0) == (r["status_fwd"] != 0), (b, int(st_f[b]), r["status_fwd"])
+        if r["status"] == 0:
+            clean += 1
+            assert rel_state(traj[b], r["traj"]) <= TOL_STATE32, b
+            assert abs(float(Lv[b]) - r["L"]) <= TOL_STATE32 * abs(r["L"]), b
+            check_grad(dU[b], r["dL_du"], TOL_GRAD32, COS32)
+    assert clean >= len(idx) * 9 // 10
 
 
 def test_rope64_two_part_launch_equals_one_launch():
@@ -348,8 +361,11 @@ def test_argument_errors_and_empty_batch():
 
 @pytest.mark.parametrize("rb", [4, 8])
 def test_saddle_root_flagged_like_the_oracle(rb):
-    """A straight chain compressed past Euler buckling (stage-1 root = saddle): the adjoint has
-    no defined step Jacobian; both sides flag CS_ST_NOTPD (the GPU's L is NaN, gradients 0)."""
+    """A straight chain compressed past Euler buckling, symmetric about its axis: the only root
+    stage 1 can reach is a saddle of the potential, which the iteration does not accept (it
+    accepts only exact-Hessian steps, i.e. minimisers), so both sides flag the step's stage 1
+    (CS_ST_NEWTON at the cap; the oracle's adjoint adds CS_ST_NOTPD for the undefined step
+    Jacobian) and the GPU's L is NaN, its gradients 0."""
     p = scenes.default_params("rope")
     L0 = 0.4
     X0 = np.array([[0.0, 0.0, 1.0], [L0, 0.0, 1.0], [2 * L0, 0.0, 1.0]])
@@ -361,7 +377,8 @@ def test_saddle_root_flagged_like_the_oracle(rb):
     ref = ograd.rollout_vjp(_oscene(sc), q0[0], u[0], "consistent")
     s = _sim(sc, rb, 1, 1)
     Lv, dU, _, st = s.rollout_vjp(_t(q0, rb), _t(u, rb))
-    assert ref["status"] & osim.ST_NOTPD and int(st[0]) & osim.ST_NOTPD
+    assert ref["status"] & osim.ST_NEWTON and int(st[0]) & osim.ST_NEWTON
+    assert ref["status"] & osim.ST_NOTPD
     assert np.isnan(float(Lv[0])) and float(dU.abs().max()) == 0.0
 
 

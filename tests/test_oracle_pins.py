@@ -855,7 +855,7 @@ def test_surrogate_equals_consistent_without_contact_in_the_grasp_limit():
     np.testing.assert_allclose(rs["dL_dq0"], rc["dL_dq0"], rtol=0, atol=1e-8 * np.max(np.abs(rc["dL_dq0"])))
 
 
-def _stage1_from(sc, q, u, moved):
+def _stage1_from(sc, q, u, moved, maxit=100):
     x, g = sim.split_q(sc, q)
     gstar = g + np.asarray(u).reshape(2, 3)
     d = sim.grasp_stiffness(sc, x, g, sim.HARD)
@@ -863,7 +863,7 @@ def _stage1_from(sc, q, u, moved):
     if moved:
         for i in range(2):
             xs0[sc.grasp[i]] += gstar[i] - g[i]
-    xs, _, st = sim.stage1_solve(sc, x, gstar, d, maxit=2000, x_start=xs0)
+    xs, _, st = sim.stage1_solve(sc, x, gstar, d, maxit=maxit, x_start=xs0)
     try:
         sim.band_factor(sim.stage1_hessian_band(sc, xs, d))
         pd = True
@@ -874,29 +874,33 @@ def _stage1_from(sc, q, u, moved):
 
 def test_stage1_start_reaches_the_minimising_root():
     """Which root stage 1 returns (Sec. 4.1: "solved using Newton's method", start unstated).
-    The start is q with each grasped node moved with its gripper: the start at which the grasp
-    offsets c_i are those of q, i.e. the linearised holonomic constraint J_i (q* - q) + c_i(q) =
-    c_i(q) holds.  On the 1024 x 64-node rope workload, Newton from q itself ends at the first step
-    of rollouts 267, 384 and 727 at a saddle of the stage-1 potential (dF/dq* indefinite: the
-    chain compressed between a moved gripper and its unmoved node), where the QP of eq.
-    dynamics-second-stage is not convex and eq. diff-sim is not defined; from the moved start it
-    reaches a root with dF/dq* positive definite.  On sampled rollouts, wherever the start at q
-    reaches a minimising root, both starts reach the same root to 1e-10 (all 50 steps)."""
+    The iteration accepts a root only on a step taken with the exact Hessian, so the root is a
+    local minimiser of the stage-1 potential (a stable equilibrium: stage 2's QP is convex there
+    and dF/dq* of the adjoint positive definite).  The start is q with each grasped node moved
+    with its gripper: the start at which the grasp offsets c_i are those of q, i.e. the linearised
+    holonomic constraint J_i (q* - q) + c_i(q) = c_i(q) holds.  On the 1024 x 64-node rope
+    workload, Newton from q itself does not converge within the cap of 100 iterations at the first
+    step of rollouts 267, 384 and 727 (it wanders near saddles of the potential: the chain
+    compressed between a moved gripper and its unmoved node), and where it converges given 2000
+    iterations (rollout 384, after 385) it reaches the root of the moved start, which converges
+    in 19-25.  On sampled rollouts both starts reach the same root to 1e-10 (all 50 steps)."""
     wl = scenes.workload(2)
     sc = sim.Scene(wl["scene"]["params"], wl["scene"]["rest_x"])
     U, q0 = wl["U"], wl["q0"]
     for b in (267, 384, 727):
         xa, sa, pda = _stage1_from(sc, q0[b], U[b, 0], moved=False)
         xb, sb, pdb = _stage1_from(sc, q0[b], U[b, 0], moved=True)
-        assert sa == 0 and sb == 0
-        assert not pda and pdb, b
-        assert np.max(np.abs(xa - xb)) > 1e-4
+        assert sa == sim.ST_NEWTON and not pda, b
+        assert sb == 0 and pdb, b
+    xa, sa, pda = _stage1_from(sc, q0[384], U[384, 0], moved=False, maxit=2000)
+    xb, sb, pdb = _stage1_from(sc, q0[384], U[384, 0], moved=True)
+    assert sa == 0 and pda and np.max(np.abs(xa - xb)) < 1e-10
     for b in (0, 100, 521):
         q = q0[b]
         for t in range(U.shape[1]):
             xa, sa, pda = _stage1_from(sc, q, U[b, t], moved=False)
             xb, sb, pdb = _stage1_from(sc, q, U[b, t], moved=True)
             assert sb == 0 and pdb
-            if pda:
+            if sa == 0:
                 assert np.max(np.abs(xa - xb)) < 1e-10, (b, t)
             q, _ = sim.step(sc, q, U[b, t], sim.HARD)
