@@ -48,6 +48,22 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 # oracle work (CPU baseline, reference arm, iteration counts for the flop model)
 # ------------------------------------------------------------------------------------------
 
+def _one_thread():
+    """pool initializer: the oracle's linear algebra on one thread per process (a process per core;
+    multithreaded BLAS in every process would oversubscribe the cores)"""
+    from threadpoolctl import threadpool_limits
+    global _LIMITS
+    _LIMITS = threadpool_limits(1)
+
+
+def _pool(procs):
+    return mp.get_context("spawn").Pool(procs, initializer=_one_thread)
+
+
+def _leg(name, t0):
+    print(f"bench: {name} {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+
+
 def _oracle_vjp(args):
     b, tol = args
     from oracle import sim as osim, grad as ograd
@@ -63,9 +79,8 @@ def _oracle_vjp(args):
 
 
 def oracle_sample(rollouts, tol, procs):
-    ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
-    with ctx.Pool(procs) as pool:
+    with _pool(procs) as pool:
         res = pool.map(_oracle_vjp, [(b, tol) for b in rollouts])
     wall = time.perf_counter() - t0
     return res, wall
@@ -190,8 +205,7 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     procs = max(1, min(cores, 16))
     per_step = 2 * procs                      # rollouts per step (two per process)
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(procs) as pool:             # one pool for the run: start-up is not timed
+    with _pool(procs) as pool:                # one pool for the run: start-up is not timed
         for s in range(args.warmup):
             pool.map(_oracle_vjp, [(b, None) for b in range(s * per_step, (s + 1) * per_step)])
         t = 0.0
@@ -279,23 +293,39 @@ def cloth_oracle_sample(steps=2):
     w = scenes.workload(3, B=1, H=steps)
     sc = w["scene"]
     osc = osim.Scene(sc["params"], sc["rest_x"])
-    t0 = time.perf_counter()
-    ograd.rollout_vjp(osc, w["q0"][0], w["U"][0], "surrogate")
-    dt = time.perf_counter() - t0
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(1):                # one core, as reported
+        t0 = time.perf_counter()
+        ograd.rollout_vjp(osc, w["q0"][0], w["U"][0], "surrogate")
+        dt = time.perf_counter() - t0
     nv = sc["params"]["n_nodes"]
     return dict(value=nv * steps / dt, unit=UNIT, cores=1, kind="oracle",
                 sample=f"1 rollout x {steps} steps of the 32x32 cloth, forward + adjoint, {dt:.1f} s")
 
 
+def _cloth_oracle_counts(args):
+    """The oracle's iterations on one step of the cloth workload from a state the GPU reached:
+    its nonsmooth step from q (the defined stage-1 start) and the smooth re-solve of the backward
+    (started at the GPU's next node positions, the root next to the GPU's)."""
+    scene, q, u, xn = args
+    from oracle import grad as ograd, sim as osim
+    sc = osim.Scene(scene["params"], scene["rest_x"])
+    info = {}
+    osim.step(sc, q, u, osim.HARD, info=info)
+    jac = ograd.SmoothStepJacobian(sc, q, u, x_start=np.asarray(xn).reshape(sc.nv, 3))
+    return dict(fwd_newton=info["newton_it"], fwd_ipm=info["ipm_it"], sm_newton=jac.counts[0],
+                sm_ipm=jac.counts[1])
+
+
 def cloth_leg(args, flush, stream, world, cpu):
-    """sim_rollout_vjp on the batched cloth workload (32 x 32 cloth, FP32, table + 2 spheres,
-    checkpoint every 5): a bounded sample of one rollout per SM (one wave of the 512) over the
-    first `cloth_horizon` steps.  Iteration counts for the flop model from the forward rollout's
-    counters on the same inputs (untimed)."""
+    """sim_rollout_vjp on the batched cloth workload: 512 rollouts of a 32 x 32 cloth, FP32, horizon
+    30, table + 2 spheres, checkpoint every 5 (flags --cloth-rollouts / --cloth-horizon shrink it
+    for profiling captures only).  The flop count uses the FP64 oracle's iterations per step on a
+    sample of (rollout, step) states the GPU's forward reached (untimed)."""
     import torch
     from paper_2606_14188_b300.sim import Sim
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    B = args.cloth_rollouts or props.multi_processor_count
+    B = args.cloth_rollouts or 512
     H = args.cloth_horizon
     w = scenes.workload(3, B=B, H=H)
     sc = w["scene"]
@@ -303,40 +333,61 @@ def cloth_leg(args, flush, stream, world, cpu):
     R, C, nv = p["rows"], p["cols"], p["n_nodes"]
     k = p["checkpoint_every"]
     nobs = len(p["obstacles"])
+    n = 3 * nv
     s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H, newton_max=300)
     q0 = torch.tensor(w["q0"], dtype=torch.float32, device="cuda")
     U = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
-    _, _, st_f, cnt = s.rollout_counters(q0, U)
+    # untimed: the forward's trajectory and counters, and the oracle's iterations at sampled states
+    traj, _, st_f, cnt = s.rollout_counters(q0, U)
     c = cnt.cpu().numpy().reshape(B, H, 3)
-    counts = dict(fwd_newton=float(c[..., 0].mean()), fwd_ipm=float(c[..., 1].mean()))
-    s.rollout_vjp(q0, U, want_dq0=False)
-    per = time_device(lambda: s.rollout_vjp(q0, U, want_dq0=False), args.cloth_steps, flush, stream)
+    gpu_counts = dict(fwd_newton=float(c[..., 0].mean()), fwd_ipm=float(c[..., 1].mean()))
+    samp_b = [int(x) for x in np.linspace(0, B - 1, 4).round()]
+    samp_t = sorted({int(x) for x in np.linspace(0, H - 1, 5).round()})
+    jobs = []
+    tr = traj.cpu().numpy().astype(np.float64)
+    for b in samp_b:
+        for t in samp_t:
+            if not np.any(c[b, :t + 1, 2]):
+                jobs.append((sc, tr[b, t], w["U"][b, t], tr[b, t + 1, :n]))
+    del traj, tr
+    counts = None
+    if jobs and not args.no_cpu:
+        with _pool(max(1, min(os.cpu_count() or 1, 16))) as pool:
+            res = pool.map(_cloth_oracle_counts, jobs)
+        counts = {key: float(np.mean([r[key] for r in res])) for key in res[0]}
+    outs = []          # the timer's untimed first call is the warm-up; the last timed call's outputs
+    per = time_device(lambda: outs.append(s.rollout_vjp(q0, U, want_dq0=False)), args.cloth_steps, flush, stream)
     t = max_over_ranks(sum(per), world)
     avg = t / args.cloth_steps
-    _, dU, _, st = s.rollout_vjp(q0, U, want_dq0=False)
+    _, dU, _, st = outs[-1]
     status = st.cpu().numpy()
     node_steps = B * nv * H
     clean_steps = int(np.count_nonzero(status == 0)) * nv * H
     pband = flops.cloth_band(C)
     spn = flops.cloth_springs_per_node(R, C)
-    f_ns = flops.cloth_rollout_vjp_flops_per_node_step(counts, pband, spn, nobs, k)
     sm_mhz = 2032.0
     peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    # a flagged rollout stops at its failed step: only the clean rollouts' work is counted
-    achieved = f_ns * clean_steps / avg / 1e12
     wl = f"cloth{R}x{C}_b{B}_h{H}"
-    return dict(workload=wl, what=f"sample of the 512-rollout, horizon-30 cloth workload: {B} rollouts "
-                                  f"(one per SM), first {H} steps", value=world * node_steps / avg,
-                unit=UNIT, ms_per_step=1e3 * avg, rollouts=B, horizon=H, checkpoint_every=k,
-                value_clean_rollouts_only=world * clean_steps / avg,
+    roof = None
+    if counts is not None:
+        f_ns = flops.cloth_rollout_vjp_flops_per_node_step(counts, pband, spn, nobs, k)
+        # a flagged rollout stops at its failed step: only the clean rollouts' work is counted
+        achieved = f_ns * clean_steps / avg / 1e12
+        roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                    traffic=load_traffic("cloth_vjp_kernel", wl),
+                    peak_source="FP32 FMA at the max SM clock", flops_per_node_step=f_ns,
+                    band_half_width=pband,
+                    oracle_iterations_per_step=counts,
+                    oracle_sample=f"{len(jobs)} (rollout, step) states of the GPU's forward: rollouts "
+                                  f"{samp_b}, steps {samp_t}")
+    return dict(workload=wl, what="the batched cloth workload: 512 rollouts x 32x32 cloth x 30 steps, "
+                                  "checkpoint every 5" if (B, H) == (512, 30) else "reduced cloth case",
+                value=world * node_steps / avg, unit=UNIT, ms_per_step=1e3 * avg, rollouts=B, horizon=H,
+                checkpoint_every=k, value_clean_rollouts_only=world * clean_steps / avg,
                 status_flagged=int(np.count_nonzero(status)),
                 status_newton_cap=int(np.count_nonzero(status & 1)),
                 grads_finite=bool(torch.isfinite(dU).all().item()),
-                roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                              traffic=load_traffic("cloth_vjp_kernel", wl),
-                              peak_source="FP32 FMA at the max SM clock", flops_per_node_step=f_ns,
-                              band_half_width=pband, iterations_per_step=counts),
-                cpu_baseline=cpu)
+                gpu_iterations_per_step=gpu_counts, roofline=roof, cpu_baseline=cpu)
 
 
 def served_stream(n, seed, cloth_frac=0.0):
@@ -458,7 +509,9 @@ def run_ours(args):
                    one_core_value=per_core)
         cres, _ = oracle_sample([0, 341, 682, 1023], 1e-5, 4)
         counts = counts_mean(cres)
+    t_leg = time.perf_counter()
     cloth_cpu = cloth_oracle_sample() if rank == 0 and not args.no_cpu and args.cloth_horizon > 0 else None
+    _leg("cloth CPU baseline", t_leg)
 
     import torch
     if world > 1:
@@ -481,6 +534,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    t_leg = time.perf_counter()
     for _ in range(args.warmup):
         s.rollout_vjp(q0, U, want_dq0=False)
     torch.cuda.synchronize()
@@ -529,6 +583,8 @@ def run_ours(args):
     te = e0.elapsed_time(e1) * 1e-3
     te = max_over_ranks(te, world)
 
+    _leg("rope forward + adjoint and end-to-end", t_leg)
+    t_leg = time.perf_counter()
     # forward alone (the same rollouts, nonsmooth forward, trajectory written)
     t_fwd = max_over_ranks(sum(time_device(lambda: s.rollout(q0, U), args.steps, flush, stream)),
                            world)
@@ -540,10 +596,17 @@ def run_ours(args):
     t_k1 = max_over_ranks(sum(time_device(lambda: s1.rollout_vjp(q0, U, want_dq0=False), args.steps,
                                           flush, stream)), world)
     del s1
+    _leg("rope forward alone and every-step records", t_leg)
     # linearisation workload: 256 nominal trajectories of a 40-node rope, horizon 20
+    t_leg = time.perf_counter()
     lin = linearize_leg(args, flush, stream, world)
+    _leg("linearisation", t_leg)
+    t_leg = time.perf_counter()
     served = served_leg(args) if args.served_requests > 0 else None
+    _leg("served", t_leg)
+    t_leg = time.perf_counter()
     cloth = cloth_leg(args, flush, stream, world, cloth_cpu) if args.cloth_horizon > 0 else None
+    _leg("cloth", t_leg)
 
     if rank == 0:
         node_steps = B * nv * H
@@ -610,10 +673,10 @@ def main():
                     help="rollouts per GPU (default 1024; smaller only for profiling captures)")
     ap.add_argument("--rope-horizon", type=int, default=None,
                     help="horizon of the rope legs (default 50; shorter only for profiling captures)")
-    ap.add_argument("--cloth-horizon", type=int, default=10,
-                    help="steps of the cloth leg's sample (0: skip the cloth leg)")
+    ap.add_argument("--cloth-horizon", type=int, default=30,
+                    help="horizon of the cloth leg (default 30, the workload's; 0: skip the cloth leg)")
     ap.add_argument("--cloth-rollouts", type=int, default=None,
-                    help="rollouts of the cloth leg's sample (default: one per SM)")
+                    help="rollouts of the cloth leg (default 512, the workload's)")
     ap.add_argument("--cloth-steps", type=int, default=1, help="timed calls of the cloth leg")
     ap.add_argument("--served-cloth-fraction", type=float, default=0.0,
                     help="fraction of the served requests that are cloths (default 0: ropes only)")

@@ -97,14 +97,25 @@ def cloth_pc_barrier_iter_per_node(p: int, spn: float, nobs: int) -> float:
         2 * band_solve_per_node(p) + 1.5 * (spn * 24 + nobs * 25)
 
 
+def cloth_barrier_iter_per_node(p: int, spn: float, nobs: int) -> float:
+    """barrier iteration of the smooth stage 2 (fixed target, one solve)"""
+    return spn * (40 + 36 + 24) + 10 + nobs * 60 + band_factor_per_node(p) + band_solve_per_node(p) + \
+        1.5 * (spn * 24 + nobs * 25)
+
+
 def cloth_rollout_vjp_flops_per_node_step(counts: dict, p: int, spn: float, nobs: int, k: int) -> float:
-    """counts: mean Newton and barrier iterations per step of the forward (fwd_newton, fwd_ipm).
-    Forward, the recompute of k-1 of every k steps, and a backward step counted at its minimum:
-    one Newton iteration of the smooth re-solve, the two adjoint factorisations and solves, and the
-    VJP products (spring third derivatives, contact terms).  Shift retries of the stage-1
-    factorisation are not counted."""
+    """counts: mean iterations per step: fwd_newton, fwd_ipm (nonsmooth forward) and, when given,
+    sm_newton, sm_ipm (the smooth re-solve of the backward).  Forward, the recompute of k-1 of
+    every k steps, and a backward step: the smooth re-solve (at its minimum, one Newton iteration,
+    without its counts), the factorisation of the adjoint's dF/dq*, two solves and the VJP products
+    (spring third derivatives, contact terms).  Shift retries of the stage-1 factorisation are not
+    counted."""
     fwd = counts["fwd_newton"] * cloth_newton_iter_per_node(p, spn) + \
         counts["fwd_ipm"] * cloth_pc_barrier_iter_per_node(p, spn, nobs)
-    back = cloth_newton_iter_per_node(p, spn) + 2 * (band_factor_per_node(p) + band_solve_per_node(p)) + \
-        spn * 30 + nobs * 70 + 12
+    if "sm_newton" in counts:
+        resolve = counts["sm_newton"] * cloth_newton_iter_per_node(p, spn) + \
+            counts["sm_ipm"] * cloth_barrier_iter_per_node(p, spn, nobs)
+    else:
+        resolve = cloth_newton_iter_per_node(p, spn)
+    back = resolve + band_factor_per_node(p) + 2 * band_solve_per_node(p) + spn * 30 + nobs * 70 + 12
     return fwd + fwd * (k - 1) / k + back

@@ -14,3 +14,42 @@ def rope64_rollout(b):
     traj, st_f, _ = osim.rollout(sc, w["q0"][b], w["U"][b], osim.HARD)
     r = ograd.rollout_vjp(sc, w["q0"][b], w["U"][b], "surrogate")
     return dict(b=b, traj=traj, status_fwd=int(st_f), L=float(r["L"]), dL_du=r["dL_du"], status=int(r["status"]))
+
+
+def cloth_chain(args):
+    """The surrogate gradient of one cloth rollout chained through the oracle's smooth-step
+    Jacobians at the GPU's own states: traj [H+1][n_q] (the GPU's nonsmooth forward), controls
+    U [H][6].  Each step's smooth Newton starts at the GPU's next node positions (its stage-1
+    solution plus the stage-2 displacement), which lands on the root next to the GPU's.
+    Returns dL/du [H][6] and L."""
+    scene, traj, U = args
+    sc = osim.Scene(scene["params"], scene["rest_x"])
+    H = U.shape[0]
+    L, seeds, dU = ograd.loss_and_seeds(sc, traj, U)
+    lam = seeds[H].copy()
+    g = np.zeros_like(U)
+    for t in range(H - 1, -1, -1):
+        xn = np.asarray(traj[t + 1][: sc.n]).reshape(sc.nv, 3)
+        jac = ograd.SmoothStepJacobian(sc, traj[t], U[t], x_start=xn)
+        if not jac.defined:
+            return dict(L=L, dL_du=None, status=int(jac.status))
+        qb, ub = jac.vjp(lam)
+        g[t] = ub + dU[t]
+        lam = qb + seeds[t]
+    return dict(L=L, dL_du=g, status=0)
+
+
+def cloth_stage2(args):
+    """Stage 2 of one nonsmooth cloth step from the GPU's state q (the oracle's stage-1 root next
+    to the GPU's next node positions xn): returns the oracle's q+ and its status."""
+    scene, q, u, xn = args
+    sc = osim.Scene(scene["params"], scene["rest_x"])
+    qp, st = osim.step(sc, q, u, osim.HARD, x_start=np.asarray(xn).reshape(sc.nv, 3))
+    return dict(q_next=qp, status=int(st))
+
+
+def one_thread():
+    """pool initializer: one BLAS thread per process (a process per core)"""
+    from threadpoolctl import threadpool_limits
+    global _LIMITS
+    _LIMITS = threadpool_limits(1)

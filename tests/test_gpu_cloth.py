@@ -209,6 +209,50 @@ def test_cloth32_fp32_full_size_properties():
             assert np.isfinite(Lv[b]) and np.all(np.isfinite(dU[b])) and np.abs(dU[b]).max() > 0
 
 
+def test_cloth32_fp32_gradient_and_contact_steps_against_the_oracle_at_the_gpu_states():
+    """The batched workload's 32 x 32 cloth, FP32: several stage-1 roots per step make element-
+    wise trajectory parity ill-posed, but the step map and its adjoint are checkable at the GPU's
+    own states.  (1) The whole-rollout dL/du of the GPU equals the surrogate gradient chained
+    through the oracle's smooth-step Jacobians built at the GPU's states (each smooth Newton
+    started at the GPU's next node positions, so that it converges to the root next to the GPU's)
+    within 1e-3 with cosine >= 0.999.  (2) At contact steps (the GPU's interior point ran), the
+    GPU's next state equals the oracle's nonsmooth step from the same state, stage 1 started at the
+    GPU's next node positions, within 1e-4 of max |q|."""
+    import multiprocessing as mp
+    import os
+    from tests import oracle_jobs
+    B, H = 3, 5
+    w = scenes.workload(3, B=B, H=H)
+    sc, q0, U = w["scene"], w["q0"], w["U"]
+    s = _sim(sc, 4, B, H, newton_max=300)
+    traj, _, st_f, cnt = s.rollout_counters(_t(q0, 4), _t(U, 4))
+    Lv, dU, _, st = s.rollout_vjp(_t(q0, 4), _t(U, 4))
+    traj = traj.cpu().numpy().astype(np.float64)
+    cnt, st, Lv, dU = cnt.cpu().numpy(), st.cpu().numpy(), Lv.cpu().numpy(), dU.cpu().numpy()
+    clean = [b for b in range(B) if st[b] == 0]
+    assert len(clean) >= 2
+    # contact steps over a longer horizon of more rollouts (forward only)
+    B2, H2 = 16, 10
+    w2 = scenes.workload(3, B=B2, H=H2)
+    s2 = _sim(w2["scene"], 4, B2, H2, newton_max=300)
+    traj2, _, _, cnt2 = s2.rollout_counters(_t(w2["q0"], 4), _t(w2["U"], 4))
+    traj2, cnt2 = traj2.cpu().numpy().astype(np.float64), cnt2.cpu().numpy()
+    contact = [(b, t) for b in range(B2) for t in range(H2) if cnt2[b, t, 1] > 0 and cnt2[b, t, 2] == 0
+               and not np.any(cnt2[b, :t, 2])][:4]
+    n = 3 * sc["params"]["n_nodes"]
+    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 16)), initializer=oracle_jobs.one_thread) as pool:
+        chains = pool.map(oracle_jobs.cloth_chain, [(sc, traj[b], U[b]) for b in clean])
+        steps = pool.map(oracle_jobs.cloth_stage2, [(w2["scene"], traj2[b, t], w2["U"][b, t], traj2[b, t + 1, :n])
+                                                    for b, t in contact])
+    for b, r in zip(clean, chains):
+        assert r["status"] == 0 and r["dL_du"] is not None, b
+        assert abs(float(Lv[b]) - r["L"]) <= TOL_STATE32 * abs(r["L"]), b
+        check_grad(dU[b], r["dL_du"], TOL_GRAD32, COS32)
+    for (b, t), r in zip(contact, steps):
+        assert r["status"] == 0, (b, t)
+        assert rel_state(traj2[b, t + 1], r["q_next"]) <= TOL_STATE32, (b, t)
+
+
 def test_cloth_box_obstacle_fp64():
     """A 5 x 5 cloth dropping onto a box and the table: stage 2 against box faces, edges and the
     plane, FP64 against the oracle."""

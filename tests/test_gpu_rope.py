@@ -139,7 +139,7 @@ def test_rope64_full_batch_flags_and_values_match_the_oracle():
     assert np.all(np.isnan(Lv[fl])) and np.all(dU[fl] == 0)
     assert np.all(np.isfinite(Lv[~fl])) and np.all(np.isfinite(dU[~fl]))
     idx = list(range(0, B, 4))
-    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 32))) as pool:
+    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 32)), initializer=oracle_jobs.one_thread) as pool:
         refs = pool.map(oracle_jobs.rope64_rollout, idx)
     clean = 0
     for r in refs:
