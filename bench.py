@@ -48,16 +48,24 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 # oracle work (CPU baseline, reference arm, iteration counts for the flop model)
 # ------------------------------------------------------------------------------------------
 
-def _one_thread():
-    """pool initializer: the oracle's linear algebra on one thread per process (a process per core;
-    multithreaded BLAS in every process would oversubscribe the cores)"""
-    from threadpoolctl import threadpool_limits
-    global _LIMITS
-    _LIMITS = threadpool_limits(1)
+_BLAS_ENV = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
 
 
 def _pool(procs):
-    return mp.get_context("spawn").Pool(procs, initializer=_one_thread)
+    """A spawned pool whose workers run the oracle's linear algebra on one thread each (a process
+    per core; multithreaded BLAS in every process would oversubscribe the cores).  A worker reads
+    the BLAS thread count from its environment when it loads numpy, so the variables are set
+    while the workers start."""
+    saved = {k: os.environ.get(k) for k in _BLAS_ENV}
+    os.environ.update({k: "1" for k in _BLAS_ENV})
+    try:
+        return mp.get_context("spawn").Pool(procs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def _leg(name, t0):
@@ -286,19 +294,21 @@ def linearize_leg(args, flush, stream, world):
                               peak_source=f"{src} HBM copy bandwidth"))
 
 
-def cloth_oracle_sample(steps=2):
-    """The oracle's forward + adjoint of one rollout of the cloth workload over `steps` steps (CPU,
-    one process): node-steps/s and the sample described."""
+def _cloth_sample_job(steps):
     from oracle import grad as ograd, sim as osim
     w = scenes.workload(3, B=1, H=steps)
     sc = w["scene"]
     osc = osim.Scene(sc["params"], sc["rest_x"])
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(1):                # one core, as reported
-        t0 = time.perf_counter()
-        ograd.rollout_vjp(osc, w["q0"][0], w["U"][0], "surrogate")
-        dt = time.perf_counter() - t0
-    nv = sc["params"]["n_nodes"]
+    t0 = time.perf_counter()
+    ograd.rollout_vjp(osc, w["q0"][0], w["U"][0], "surrogate")
+    return time.perf_counter() - t0, sc["params"]["n_nodes"]
+
+
+def cloth_oracle_sample(steps=2):
+    """The oracle's forward + adjoint of one rollout of the cloth workload over `steps` steps (CPU,
+    one process on one thread): node-steps/s and the sample described."""
+    with _pool(1) as pool:
+        dt, nv = pool.apply(_cloth_sample_job, (steps,))
     return dict(value=nv * steps / dt, unit=UNIT, cores=1, kind="oracle",
                 sample=f"1 rollout x {steps} steps of the 32x32 cloth, forward + adjoint, {dt:.1f} s")
 
@@ -499,7 +509,9 @@ def run_ours(args):
         cores = os.cpu_count() or 1
         procs = max(1, min(cores, 16))
         nroll = 16 * procs
+        t_leg = time.perf_counter()
         res, wall = oracle_sample(list(range(nroll)), None, procs)
+        _leg("rope CPU baseline", t_leg)
         w0 = scenes.workload(2)
         ns = nroll * w0["scene"]["params"]["n_nodes"] * w0["H"]
         per_core = float(np.mean([ns / nroll / r["seconds"] for r in res]))
@@ -507,8 +519,10 @@ def run_ours(args):
                    sample=f"{nroll} of the 1024 rollouts (full horizon 50, forward + adjoint) on "
                           f"{procs} processes; {wall:.1f} s wall",
                    one_core_value=per_core)
+        t_leg = time.perf_counter()
         cres, _ = oracle_sample([0, 341, 682, 1023], 1e-5, 4)
         counts = counts_mean(cres)
+        _leg("rope oracle iteration counts", t_leg)
     t_leg = time.perf_counter()
     cloth_cpu = cloth_oracle_sample() if rank == 0 and not args.no_cpu and args.cloth_horizon > 0 else None
     _leg("cloth CPU baseline", t_leg)

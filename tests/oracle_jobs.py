@@ -48,8 +48,21 @@ def cloth_stage2(args):
     return dict(q_next=qp, status=int(st))
 
 
-def one_thread():
-    """pool initializer: one BLAS thread per process (a process per core)"""
-    from threadpoolctl import threadpool_limits
-    global _LIMITS
-    _LIMITS = threadpool_limits(1)
+_BLAS_ENV = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def pool(procs):
+    """A spawned pool whose workers run the oracle on one BLAS thread each (a process per core):
+    the thread count is read from the environment when a worker loads numpy."""
+    import multiprocessing as mp
+    import os
+    saved = {k: os.environ.get(k) for k in _BLAS_ENV}
+    os.environ.update({k: "1" for k in _BLAS_ENV})
+    try:
+        return mp.get_context("spawn").Pool(procs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v

@@ -240,7 +240,7 @@ def test_cloth32_fp32_gradient_and_contact_steps_against_the_oracle_at_the_gpu_s
     contact = [(b, t) for b in range(B2) for t in range(H2) if cnt2[b, t, 1] > 0 and cnt2[b, t, 2] == 0
                and not np.any(cnt2[b, :t, 2])][:4]
     n = 3 * sc["params"]["n_nodes"]
-    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 16)), initializer=oracle_jobs.one_thread) as pool:
+    with oracle_jobs.pool(max(1, min(os.cpu_count() or 1, 16))) as pool:
         chains = pool.map(oracle_jobs.cloth_chain, [(sc, traj[b], U[b]) for b in clean])
         steps = pool.map(oracle_jobs.cloth_stage2, [(w2["scene"], traj2[b, t], w2["U"][b, t], traj2[b, t + 1, :n])
                                                     for b, t in contact])

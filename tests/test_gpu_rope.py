@@ -139,7 +139,7 @@ def test_rope64_full_batch_flags_and_values_match_the_oracle():
     assert np.all(np.isnan(Lv[fl])) and np.all(dU[fl] == 0)
     assert np.all(np.isfinite(Lv[~fl])) and np.all(np.isfinite(dU[~fl]))
     idx = list(range(0, B, 4))
-    with mp.get_context("spawn").Pool(max(1, min(os.cpu_count() or 1, 32)), initializer=oracle_jobs.one_thread) as pool:
+    with oracle_jobs.pool(max(1, min(os.cpu_count() or 1, 32))) as pool:
         refs = pool.map(oracle_jobs.rope64_rollout, idx)
     clean = 0
     for r in refs:
@@ -278,6 +278,30 @@ def test_rope20_fp64_linearize_vs_oracle():
     assert int(st[0]) == 0
     assert np.max(np.abs(A[0].cpu().numpy() - Ar)) <= TOL64 * np.max(np.abs(Ar))
     assert np.max(np.abs(Bm[0].cpu().numpy() - Br)) <= TOL64 * np.max(np.abs(Br))
+
+
+@pytest.mark.parametrize("nv", [3, 21, 64, 100])
+def test_linearize_odd_and_long_chains_fp64(nv):
+    """A_t, B_t in FP64 against the oracle's forward-mode Jacobians: a three-node chain, an odd chain
+    (a padded pair), one node per thread and two (several passes of the tangent directions), with
+    the nominal lowered onto the obstacles so that some steps have active contacts."""
+    sc = scenes.rope_scene(nv, n_spheres=2, n_boxes=1, seed=29 + nv,
+                           sphere_box=((0.0, 1.0), (-0.2, 0.2), (0.0, 0.3)))
+    H = 5
+    U = scenes.controls_uniform(2, H, seed=nv + 1)
+    U[..., 2] = -0.03                              # both grippers move down
+    U[..., 5] = -0.03
+    q0 = scenes.batch_q0(sc, 2)
+    osc = _oscene(sc)
+    Z = np.stack([osim.rollout(osc, q0[b], U[b], "hard")[0] for b in range(2)])
+    s = _sim(sc, 8, 2, H)
+    A, Bm, st = s.linearize(_t(Z, 8), _t(U, 8))
+    assert np.all(st.cpu().numpy() == 0)
+    for b in range(2):
+        Ar, Br = ograd.linearize(osc, Z[b], U[b])
+        Ag, Bg = A[b].cpu().numpy(), Bm[b].cpu().numpy()
+        assert np.max(np.abs(Ag - Ar)) <= TOL64 * np.max(np.abs(Ar)), b
+        assert np.max(np.abs(Bg - Br)) <= TOL64 * np.max(np.abs(Br)), b
 
 
 # ------------------------------------------------------------------------------------------
