@@ -1,12 +1,14 @@
 // Kernel launchers for the rope kernels (instantiated per real type in rope_*.cu).  Rollouts and
 // adjoints run one 64-thread CTA per rollout (rope_cta.cuh; nodes per thread NPT = 1 up to 64
-// nodes, 2 up to 128); the linearisation runs one warp per (trajectory, step) (rope.cuh; pairs per
-// lane PPL = 1 up to 64 nodes, 2 up to 128).
+// nodes, 2 up to 128); the linearisation runs a CTA per (trajectory, step) in two launches
+// (rope_lin.cuh) with the handle's per-step records, else one warp per (trajectory, step)
+// (rope.cuh; pairs per lane PPL = 1 up to 64 nodes, 2 up to 128).
 #pragma once
 #include <algorithm>
 #include "internal.h"
 #include "rope.cuh"
 #include "rope_cta.cuh"
+#include "rope_lin.cuh"
 
 namespace csi {
 
@@ -100,6 +102,50 @@ cs_status launch_vjp(cs_sim* s, int B, int H, const void* q0, const void* u, con
                      : vjp_cta<R, 2>(s, B, H, q0, u, dLdtraj, loss, L, dLdu, dLdq0, status, st);
 }
 
+// The linearisation in two launches (rope_lin.cuh) when the handle holds per-step records: the
+// smooth step of every (trajectory, step) job with its record, then every tangent direction of a
+// job in one pass of a CTA.
+template <typename R, int NPT>
+cs_status linearize_cta(cs_sim* s, int B, int H, const void* z, const void* v, void* A, void* Bm,
+                        int32_t* status, cudaStream_t st) {
+  cs::Scene<R> S = make_scene<R>(s, nullptr);
+  const size_t smem1 = cs::rc::sm_elems(NPT, s->P.n_obstacles) * sizeof(R);
+  auto k1 = cs::rc::rope_cta_lin_step_kernel<R, NPT>;
+  auto k2 = cs::rc::rope_lin_tangent_kernel<R>;
+  cs_status r = launch_prep(k1, smem1, s);
+  if (r) return r;
+  const int nv = s->nv, N = s->npair, ndir = 3 * nv + 12;
+  const size_t rb = sizeof(R);
+  const size_t fixed = (cs::rc::lin_fixed_elems(N, nv) + 3) / 4 * 4 * rb, per = 6 * (size_t)N * rb;
+  // directions per pass: what fits three CTAs on an SM, else two
+  size_t budget = 76000;
+  long long dpr = fixed < budget ? (long long)((budget - fixed) / per) : 0;
+  if (dpr < 32) {
+    budget = std::min<size_t>(s->smem_optin, 2 * budget);
+    dpr = fixed < budget ? (long long)((budget - fixed) / per) : 0;
+  }
+  dpr = std::min<long long>(std::min<long long>(dpr, ndir), 160);
+  if (dpr < 1) return cs_fail(CS_ERR_INVALID_ARG, "scene too large for shared memory");
+  const int threads = (int)((dpr + 31) / 32 * 32);
+  const size_t smem2 = cs::rc::lin_smem_elems(N, nv, (int)dpr) * rb;
+  if ((r = launch_prep(k2, smem2, s))) return r;
+  if (status) {
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, st);
+    if (e != cudaSuccess) return cs_cuda_fail(e, "cudaMemsetAsync");
+  }
+  const long long jobs = (long long)B * H;
+  int per1 = 0, per2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k1, cs::rc::NT, smem1);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, threads, smem2);
+  if (per1 < 1 || per2 < 1) return cs_fail(CS_ERR_INVALID_ARG, "scene too large for shared memory");
+  const int g1 = (int)std::min<long long>((long long)per1 * s->sms, jobs);
+  const int g2 = (int)std::min<long long>((long long)per2 * s->sms, jobs);
+  k1<<<g1, cs::rc::NT, smem1, st>>>(S, B, H, (const R*)z, (const R*)v, (R*)s->d_fac, s->fac_stride, status);
+  if ((r = check_launch("rope_cta_lin_step_kernel"))) return r;
+  k2<<<g2, threads, smem2, st>>>(S, B, H, 32 * NPT, (const R*)s->d_fac, s->fac_stride, (int)dpr, (R*)A, (R*)Bm);
+  return check_launch("rope_lin_tangent_kernel");
+}
+
 template <typename R, int PPL>
 cs_status linearize_ppl(cs_sim* s, int B, int H, const void* z, const void* v, void* A, void* Bm,
                         int32_t* status, cudaStream_t st) {
@@ -121,6 +167,9 @@ cs_status linearize_ppl(cs_sim* s, int B, int H, const void* z, const void* v, v
 template <typename R>
 cs_status launch_linearize(cs_sim* s, int B, int H, const void* z, const void* v, void* A,
                            void* Bm, int32_t* status, cudaStream_t st) {
+  if (s->d_fac)
+    return s->nv <= 64 ? linearize_cta<R, 1>(s, B, H, z, v, A, Bm, status, st)
+                       : linearize_cta<R, 2>(s, B, H, z, v, A, Bm, status, st);
   return s->npair <= 32 ? linearize_ppl<R, 1>(s, B, H, z, v, A, Bm, status, st)
                         : linearize_ppl<R, 2>(s, B, H, z, v, A, Bm, status, st);
 }

@@ -1065,6 +1065,47 @@ __device__ __forceinline__ int stage2_ipm(const Scene<R>& S, Nd<R, NPT>& N, cons
   return ST_CONTACT;
 }
 
+// H2 = P + sum A^T W^-2 A assembled at the final iterate of a smooth stage 2 (the scaling from the
+// stored s, z; with no obstacle H2 = P) into (T, B, V), unfactorised: the interior point leaves the
+// factorisation of its last Newton matrix, taken one step before the solution, where a pressed
+// contact's W^-2 (of order z/s) still differs by that step relative to s.  Entry: x0, dx published.
+template <typename R, int NPT>
+__device__ __forceinline__ void assemble_h2(const Scene<R>& S, const Nd<R, NPT>& N, const Sm<R>& w) {
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) {
+    const int j = node_of(k);
+    if (j >= S.nv) {
+      if (j < 2 * S.npair) put_pad_rows(w, j);
+      continue;
+    }
+    R D[9], C1[9], C2[9], F[3];
+    node_rows(S, N, w, k, false, D, C1, C2, F);
+    for (int o = 0; o < S.nobs; ++o) {
+      R ph, n[3], A[9], sv[3], zv[3], W[9], Wi[9], lam[3], wpv[3], M[9];
+      pair_geom(S, N, k, o, ph, n);
+      cone_frame(n, S.mu, A);
+      pair_sz(w, o, j, sv, zv);
+      nt_scaling_v(sv, zv, W, Wi, lam, wpv);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          M[a * 3 + b] = Wi[a * 3] * Wi[b] + Wi[a * 3 + 1] * Wi[3 + b] + Wi[a * 3 + 2] * Wi[6 + b];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int c = 0; c <= i; ++c) {
+          R t = R(0);
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            t += A[a * 3 + i] * (M[a * 3] * A[c] + M[a * 3 + 1] * A[3 + c] + M[a * 3 + 2] * A[6 + c]);
+          D[i * 3 + c] += t;
+        }
+    }
+    put_node_rows(w, j, D, C1, C2);     // takes the lower triangle of D
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // one step: x0 (registers, published), misc g, u, c; with warm the stage-1 start dx, with warm2 the
 // stage-2 start Dl.  Outputs dx, Dl (dx published on exit), misc d, gd.  smooth = the smooth grasp
@@ -1264,12 +1305,16 @@ __device__ __forceinline__ void adjoint_nu(const Scene<R>& S, const Nd<R, NPT>& 
 }
 
 
-// adjoint of one smooth step with the factorisation of H2 in (T, B, V): H1 is assembled and
-// factorised here; not positive definite means the stage-1 root is a saddle of the potential (a
-// buckled, unstable equilibrium) and the step's Jacobian is reported as undefined
+// adjoint of one smooth step at its solution: H2 and H1 are assembled and factorised here; not
+// positive definite means the stage-1 root is a saddle of the potential (a buckled, unstable
+// equilibrium) and the step's Jacobian is reported as undefined
 template <typename R, int NPT>
 __device__ __forceinline__ int adjoint_step(const Scene<R>& S, Nd<R, NPT>& N, const Sm<R>& w, R xb[NPT][3]) {
   R mu[NPT][3], xs[NPT][3];
+  __syncthreads();
+  assemble_h2(S, N, w);
+  __syncthreads();
+  if (!crb_factor(w.T, w.B, w.V, S.npair)) return ST_NOTPD;
   adjoint_xs(S, N, w, xb, mu, xs);
   assemble_P(S, N, w, false, false);
   __syncthreads();
@@ -1758,7 +1803,10 @@ __device__ __forceinline__ void seg_job(const Scene<R>& S, const Sm<R>& w, Nd<R,
     if (!st) st = sim_step(S, N, w, rb, true, &ni, &ii, true, true);
     if (!st) {
       __syncthreads();
-      copy_block(rec, w.T, fb);                       // H2 = P + sum A^T W^-2 A
+      assemble_h2(S, N, w);                           // H2 = P + sum A^T W^-2 A at the solution
+      __syncthreads();
+      if (!crb_factor(w.T, w.B, w.V, S.npair)) st = ST_NOTPD;
+      copy_block(rec, w.T, fb);
       __syncthreads();
       assemble_P(S, N, w, false, false);              // H1 = dF/dq* at the smooth x*
       __syncthreads();
