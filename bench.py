@@ -454,44 +454,75 @@ def serve_stream(reqs, gaps, batched):
 
 
 def served_leg(args):
-    """Served MPC plan solves: capacity of the batched server on the whole stream at once, then the
-    same stream arriving as a Poisson process at 70 % and 95 % of that capacity, served batched and
-    one request at a time (one launch per kernel per evaluation, no graphs)."""
+    """Served MPC plan solves, batched (continuous batching, graph replay) against one request at a
+    time (one launch per kernel per evaluation, no graphs), on the same stream: each server's
+    capacity with the whole stream submitted at once, then the stream arriving as a Poisson process
+    at 70 % and 95 % of the batched capacity (of the first repeat), served both ways.  With
+    --served-repeats R every measurement is taken R times (arrival gaps drawn afresh each time) and
+    reported as the median with its [min, max] spread."""
     n = args.served_requests
+    reps = max(1, args.served_repeats)
     reqs = served_stream(n, BASE_SERVED_SEED, args.served_cloth_fraction)
     ncloth = sum(1 for r in reqs if "kw" in r)
     node_steps = sum(r["R"] * r["H"] * r["nv"] * r["G"] for r in reqs)
-    out_cap, t_cap, _ = serve_stream(reqs, [0.0] * n, True)
-    cap = n / t_cap
-    rng = np.random.default_rng(BASE_SERVED_SEED + 1)
     what = f"{n} plan solves: {n - ncloth} ropes (nodes U{{16..128}}, horizon U{{20..60}}, candidates " \
            f"log-U{{64..1024}})"
     if ncloth:
         what += f", {ncloth} cloths (side U{{8..16}}, horizon U{{10..20}}, candidates log-U{{32..128}})"
+
+    def lat(out, t):
+        ms = np.array([(o["t_done_ns"] - o["t_submit_ns"]) * 1e-6 for o in out])
+        return dict(p50_ms=float(np.percentile(ms, 50)), p99_ms=float(np.percentile(ms, 99)),
+                    throughput_solves_per_s=n / t)
+
+    same = True
+
+    def check(x, y):
+        nonlocal same
+        for a2, b2 in zip(x, y):
+            same = same and a2["L"] == b2["L"] and np.array_equal(a2["u"], b2["u"])
+
+    runs = []
+    rate0 = None
+    for rep in range(reps):
+        run = {}
+        ob, tb, sb = serve_stream(reqs, [0.0] * n, True)
+        op, tp, _ = serve_stream(reqs, [0.0] * n, False)
+        check(ob, op)
+        run["capacity"] = dict(batched=n / tb, per_request=n / tp)
+        if rate0 is None:
+            rate0 = n / tb
+        rng = np.random.default_rng(BASE_SERVED_SEED + 1 + rep)
+        for load in (0.7, 0.95):
+            gaps = rng.exponential(1.0 / (load * rate0), n)
+            gaps[0] = 0.0
+            ob, tb, sb = serve_stream(reqs, gaps, True)
+            op, tp, sp = serve_stream(reqs, gaps, False)
+            check(ob, op)
+            run[f"load_{int(load * 100)}"] = dict(batched=dict(**lat(ob, tb), ticks=sb["ticks"],
+                                                               graph_launches=sb["graph_launches"]),
+                                                  per_request=dict(**lat(op, tp), ticks=sp["ticks"]))
+        runs.append(run)
+
+    def summ(vals):
+        v = np.array(vals, dtype=float)
+        return dict(median=float(np.median(v)), spread=[float(v.min()), float(v.max())])
+
     res = dict(workload=what + ", 10 evaluations each, FP32, checkpoint interval picked by the server "
                                 "(checkpoint_every = 0: the shortest whose records fit in an eighth of "
                                 "its memory budget)",
-               requests=n, node_steps=node_steps, capacity_solves_per_s=cap,
-               capacity_node_steps_per_s=node_steps / t_cap)
-
-    def lat(out):
-        ms = np.array([(o["t_done_ns"] - o["t_submit_ns"]) * 1e-6 for o in out])
-        return dict(p50_ms=float(np.percentile(ms, 50)), p99_ms=float(np.percentile(ms, 99)))
-
-    same = True
-    for load in (0.7, 0.95):
-        gaps = rng.exponential(1.0 / (load * cap), n)
-        gaps[0] = 0.0
-        ob, tb, sb = serve_stream(reqs, gaps, True)
-        entry = dict(rate_solves_per_s=load * cap,
-                     batched=dict(**lat(ob), throughput_solves_per_s=n / tb, ticks=sb["ticks"],
-                                  graph_launches=sb["graph_launches"]))
-        if load == 0.7:
-            op, tp, sp = serve_stream(reqs, gaps, False)
-            entry["per_request"] = dict(**lat(op), throughput_solves_per_s=n / tp, ticks=sp["ticks"])
-            for a, b in zip(ob, op):
-                same = same and a["L"] == b["L"] and np.array_equal(a["u"], b["u"])
-        res[f"load_{int(load * 100)}"] = entry
+               requests=n, repeats=reps, node_steps=node_steps,
+               capacity_solves_per_s=summ([r["capacity"]["batched"] for r in runs]),
+               capacity_per_request_solves_per_s=summ([r["capacity"]["per_request"] for r in runs]))
+    res["capacity_node_steps_per_s"] = node_steps * res["capacity_solves_per_s"]["median"] / n
+    for load in (70, 95):
+        key = f"load_{load}"
+        ent = dict(rate_solves_per_s=load / 100 * rate0)
+        for mode in ("batched", "per_request"):
+            ent[mode] = {m: summ([r[key][mode][m] for r in runs])
+                         for m in ("p50_ms", "p99_ms", "throughput_solves_per_s")}
+        ent["batched"]["graph_launches"] = int(np.median([r[key]["batched"]["graph_launches"] for r in runs]))
+        res[key] = ent
     res["results_identical_batched_vs_per_request"] = bool(same)
     return res
 
@@ -692,6 +723,8 @@ def main():
     ap.add_argument("--cloth-rollouts", type=int, default=None,
                     help="rollouts of the cloth leg (default 512, the workload's)")
     ap.add_argument("--cloth-steps", type=int, default=1, help="timed calls of the cloth leg")
+    ap.add_argument("--served-repeats", type=int, default=1,
+                    help="repeats of every served measurement (median and spread reported)")
     ap.add_argument("--served-cloth-fraction", type=float, default=0.0,
                     help="fraction of the served requests that are cloths (default 0: ropes only)")
     args = ap.parse_args()

@@ -512,7 +512,7 @@ def max_step(x, dx):
 
 
 def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IPM_MAX,
-               Delta_start=None):
+               Delta_start=None, extra=None):
     """Primal-dual interior point with Nesterov-Todd scaling (the cone QP method of Vandenberghe
     2010) for
         min 1/2 Delta^T P Delta  s.t.  s_i = A_i Delta_j + phi_i e1 in Q,
@@ -527,7 +527,9 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
     central point follow (no predictor, no correction), and the solve ends there.  Each direction solves
     H2 dDelta = rhs with the banded SPD matrix H2 = P + sum_i E_j A_i^T W_i^{-2} A_i E_j^T (one
     factorisation per iteration); steps keep s, z strictly inside Q (fraction to the boundary
-    0.99).  Returns (Delta, sigma_world, iterations, status)."""
+    0.99).  `extra` (the second-order variant's damping, oracle/second_order.py) adds a constant
+    symmetric term to P: its band `extra.band`, its node diagonal blocks `extra.diag` and its
+    product `extra.vec(V)`.  Returns (Delta, sigma_world, iterations, status)."""
     mu = sc.p["mu"]
     nv, no = phi.shape
     Delta = np.zeros((nv, 3))
@@ -535,10 +537,15 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
         return Delta, np.zeros((nv, 0, 3)), 0, 0
     A = cone_frames(n, mu)
     P_ab = stage1_hessian_band(sc, xs, d)
+    if extra is not None:
+        P_ab = P_ab + extra.band
     e1 = np.zeros((nv, no, 3)); e1[..., 0] = 1.0
     # interior start: the per-node closed form along each penetrating normal, then s from it
     # where it lies well inside Q, else (max(phi, sigma0), 0, 0); z central for that s
-    Pd = np.einsum("joa,jab,job->jo", n, stage1_hessian_vec_diag(sc, xs, d), n)
+    Pdiag = stage1_hessian_vec_diag(sc, xs, d)
+    if extra is not None:
+        Pdiag = Pdiag + extra.diag
+    Pd = np.einsum("joa,jab,job->jo", n, Pdiag, n)
     push = 0.5 * (-phi + np.sqrt(phi * phi + 4.0 * kappa / Pd))
     Delta = np.einsum("jo,joa->ja", np.where(phi < 0.0, push, 0.0), n)
     if Delta_start is not None:         # warm start (the central point reached does not depend on it)
@@ -553,6 +560,8 @@ def stage2_ipm(sc: Scene, xs, d, phi, n, kappa, kappa_final, tol=TOL_X, maxit=IP
     for it in range(maxit):
         lam_w = np.einsum("joab,joa->job", A, z)
         r_d = stage1_hessian_vec(sc, xs, d, Delta) - lam_w.sum(axis=1)
+        if extra is not None:
+            r_d = r_d + extra.vec(Delta)
         r_z = s - np.einsum("joab,jb->joa", A, Delta) - phi[..., None] * e1
         W, Winv, lam = nt_scaling(s, z)
         M = Winv @ Winv
