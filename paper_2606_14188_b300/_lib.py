@@ -42,6 +42,7 @@ class cs_params(C.Structure):
         ("newton_tol", C.c_double), ("ipm_tol", C.c_double),
         ("checkpoint_every", C.c_int), ("real_bytes", C.c_int),
         ("max_batch", C.c_int), ("max_horizon", C.c_int),
+        ("second_order", C.c_int), ("damp_alpha", C.c_double), ("damp_beta", C.c_double),
     ]
 
 

@@ -29,6 +29,8 @@ struct Scene {
   R grav[3];
   R Dmax, kh, kc, khard, kdecay, mu, rgrasp, rad, sig0, ntol, itol;
   R k1, k2, k3;     // rope: stretch (j,j+1), bend (j,j+2); cloth: stretch, shear, bend
+  int so, nq;       // inertial variant (state [x, v, g]); state length
+  R dt, cm, cb;     // time step; damp_alpha m / dt; damp_beta / dt
   int ob_type[MAX_OBS];
   R ob[MAX_OBS][6];
   const R* L1;      // rest lengths (rope: stretch [nv-1], bend [nv-2])

@@ -70,6 +70,9 @@ cs_status cs_validate_params(const cs_params* P) {
   if (!(P->kappa_decay > 0 && P->kappa_decay < 1)) return cs_fail(CS_ERR_INVALID_ARG, "kappa_decay must be in (0,1)");
   if (!(P->kappa_c > 0) || !(P->kappa_hard > 0) || P->kappa_hard > P->kappa_c)
     return cs_fail(CS_ERR_INVALID_ARG, "need 0 < kappa_hard <= kappa_c");
+  if (P->second_order && cloth) return cs_fail(CS_ERR_UNSUPPORTED, "the inertial variant is built for ropes only");
+  if (P->second_order && !(P->damp_alpha >= 0 && P->damp_beta >= 0 && P->damp_alpha < 1e30 && P->damp_beta < 1e30))
+    return cs_fail(CS_ERR_INVALID_ARG, "damp_alpha and damp_beta must be finite and >= 0");
   return CS_OK;
 }
 
@@ -98,7 +101,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
   s->P = *P;
   s->nv = nv;
   s->npair = (nv + 1) / 2;
-  s->nq = 3 * nv + 6;
+  s->nq = (P->second_order ? 6 : 3) * nv + 6;
   s->real_bytes = P->real_bytes;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -248,6 +251,7 @@ cs_status sim_rollout_vjp(cs_sim* s, int B, int H, const void* q0, const void* u
   if (!dL_dtraj && !loss) return cs_fail(CS_ERR_INVALID_ARG, "give dL_dtraj or a loss");
   if (B > 0 && (!q0 || !u || !dL_du)) return cs_fail(CS_ERR_INVALID_ARG, "q0, u and dL_du are required");
   if (loss && (r = cs_validate_loss(loss, s->nv))) return r;
+  if (s->P.second_order) return cs_fail(CS_ERR_UNSUPPORTED, "sim_rollout_vjp is built for the quasi-static step");
   if (B == 0) return CS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (s->P.kind == CS_CLOTH)

@@ -86,6 +86,11 @@ cs::Scene<R> make_scene_from(const cs_params& P, const void* d_L1, const void* d
   S.sig0 = (R)P.sigma0;
   S.ntol = (R)P.newton_tol;
   S.itol = (R)P.ipm_tol;
+  S.so = P.second_order ? 1 : 0;
+  S.nq = (S.so ? 6 : 3) * P.n_nodes + 6;
+  S.dt = (R)P.dt;
+  S.cm = (R)(S.so ? P.damp_alpha * P.node_mass / P.dt : 0.0);
+  S.cb = (R)(S.so ? P.damp_beta / P.dt : 0.0);
   S.k1 = (R)P.k_stretch;
   S.k2 = (R)P.k_bend;
   S.k3 = (R)P.k_shear;

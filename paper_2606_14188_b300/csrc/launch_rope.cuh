@@ -114,7 +114,7 @@ cs_status linearize_cta(cs_sim* s, int B, int H, const void* z, const void* v, v
   auto k2 = cs::rc::rope_lin_tangent_kernel<R>;
   cs_status r = launch_prep(k1, smem1, s);
   if (r) return r;
-  const int nv = s->nv, N = s->npair, ndir = 3 * nv + 12;
+  const int nv = s->nv, N = s->npair, ndir = s->nq + 6;
   const size_t rb = sizeof(R);
   const size_t fixed = (cs::rc::lin_fixed_elems(N, nv) + 3) / 4 * 4 * rb, per = 6 * (size_t)N * rb;
   // directions per pass: what fits three CTAs on an SM, else two
@@ -170,6 +170,8 @@ cs_status launch_linearize(cs_sim* s, int B, int H, const void* z, const void* v
   if (s->d_fac)
     return s->nv <= 64 ? linearize_cta<R, 1>(s, B, H, z, v, A, Bm, status, st)
                        : linearize_cta<R, 2>(s, B, H, z, v, A, Bm, status, st);
+  if (s->P.second_order)
+    return cs_fail(CS_ERR_UNSUPPORTED, "the inertial linearisation needs the handle's per-step records");
   return s->npair <= 32 ? linearize_ppl<R, 1>(s, B, H, z, v, A, Bm, status, st)
                         : linearize_ppl<R, 2>(s, B, H, z, v, A, Bm, status, st);
 }

@@ -211,6 +211,7 @@ cs_status cuda_err(cudaError_t e, const char* what) { return cs_cuda_fail(e, wha
 // ---- request validation and copies ---------------------------------------------------------
 
 cs_status check_request(const cs_mpc* m, const cs_mpc_request* q) {
+  if (q->params.second_order) return cs_fail(CS_ERR_UNSUPPORTED, "plan solves use the quasi-static step");
   const cs_params& P = q->params;
   if (!q->rest_x || !q->q0) return cs_fail(CS_ERR_INVALID_ARG, "rest_x and q0 are required");
   const bool cloth = P.kind == CS_CLOTH;

@@ -85,6 +85,7 @@ extern "C" cs_status sim_rollout_vjp_noalloc(const cs_params* P, const double* r
   cs_status r = cs_validate_params(P);
   if (r) return r;
   if (P->kind != CS_ROPE) return cs_fail(CS_ERR_UNSUPPORTED, "only kind = CS_ROPE is built");
+  if (P->second_order) return cs_fail(CS_ERR_UNSUPPORTED, "built for the quasi-static step");
   const int nv = P->n_nodes;
   if (P->checkpoint_every < 1) return cs_fail(CS_ERR_INVALID_ARG, "checkpoint_every must be >= 1");
   if (B < 0 || H < 1) return cs_fail(CS_ERR_INVALID_ARG, "B must be >= 0 and H >= 1");

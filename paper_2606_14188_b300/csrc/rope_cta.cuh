@@ -313,6 +313,7 @@ struct Nd {
   R pv[NPT][3];               // step / work vector
   R F[NPT][3];                // residual
   R Ls[NPT][4];               // rest lengths of the springs to j-2, j-1, j+1, j+2 (1 where absent)
+  R v[NPT][3];                // velocity at the step start (inertial variant)
 };
 
 __device__ __forceinline__ int node_of(int k) { return threadIdx.x + NT * k; }
@@ -331,6 +332,7 @@ __device__ __forceinline__ void zero3(R v[NPT][3]) {
 template <typename R, int NPT>
 __device__ __forceinline__ void zero_nd(Nd<R, NPT>& N) {
   zero3<R, NPT>(N.x0); zero3<R, NPT>(N.dx); zero3<R, NPT>(N.Dl); zero3<R, NPT>(N.pv); zero3<R, NPT>(N.F);
+  zero3<R, NPT>(N.v);
 }
 
 template <typename R, int NPT>
@@ -364,6 +366,19 @@ __device__ __forceinline__ void spring_vec(const Nd<R, NPT>& N, const Sm<R>& w, 
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     e[c] = (w.x0[c * w.NVP + jo] - N.x0[k][c]) + (w.dx[c * w.NVP + jo] - N.dx[k][c]);
+}
+
+// Inertial variant: the Rayleigh damping term of the spring (j, jo) is c u u^T with u the unit
+// spring vector at the step start x0 and c = (damp_beta / dt) k; returns c and sets u.
+template <typename R, int NPT>
+__device__ __forceinline__ R damp_axis(const Scene<R>& S, const Nd<R, NPT>& N, const Sm<R>& w, int k, int si, R u[3]) {
+  const int jo = node_of(k) + spr_off(si);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) u[c] = w.x0[c * w.NVP + jo] - N.x0[k][c];
+  const R il = R(1) / sqrt(dot3(u, u));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) u[c] *= il;
+  return S.cb * ((si == 1 || si == 2) ? S.k1 : S.k2);
 }
 
 // Stage-1 rows of node j (slot k) at x0 + dx: the diagonal 3x3 block D of P = dF/dq*, its couplings
@@ -400,6 +415,20 @@ __device__ __forceinline__ void node_rows(const Scene<R>& S, const Nd<R, NPT>& N
     R e[3], f[3], H[9];
     spring_vec(N, w, k, jo, e);
     spring_eval(e, (si == 1 || si == 2) ? S.k1 : S.k2, N.Ls[k][si], proj, f, H);
+    if (S.so) {
+      // damping: F += c u u^T (dx_j - dx_jo), the block c u u^T with + and the coupling with -
+      R ua[3];
+      const R cs = damp_axis(S, N, w, k, si, ua);
+      R dd = R(0);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dd += ua[i] * (N.dx[k][i] - w.dx[i * w.NVP + jo]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        f[i] -= cs * dd * ua[i];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) H[i * 3 + q] += cs * ua[i] * ua[q];
+      }
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) F[i] -= f[i];
 #pragma unroll
@@ -410,6 +439,14 @@ __device__ __forceinline__ void node_rows(const Scene<R>& S, const Nd<R, NPT>& N
     } else if (si == 0) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) C2[i] = -H[i];
+    }
+  }
+  if (S.so) {
+    // inertia about x0 + dt v and the mass-proportional damping: F += -w dt v + cm dx, D += cm I
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      F[i] += S.cm * N.dx[k][i] - S.w * S.dt * N.v[k][i];
+      D[i * 4] += S.cm;
     }
   }
 }
@@ -498,7 +535,16 @@ __device__ __forceinline__ void hessvec(const Scene<R>& S, const Nd<R, NPT>& N, 
     for (int i = 0; i < 3; ++i) dd[i] = v[k][i] - vx[i * w.NVP + jo];
 #pragma unroll
     for (int i = 0; i < 3; ++i) y[i] += H[i * 3] * dd[0] + H[i * 3 + 1] * dd[1] + H[i * 3 + 2] * dd[2];
+    if (S.so) {
+      R ua[3];
+      const R cs = damp_axis(S, N, w, k, si, ua) * dot3(ua, dd);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) y[i] += cs * ua[i];
+    }
   }
+  if (S.so)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] += S.cm * v[k][i];
 }
 
 // this thread's share of Psi(x* + alpha pv) - Psi(x*) (stage-1 potential, gradient F), in difference
@@ -517,6 +563,7 @@ __device__ __forceinline__ R psi_diff(const Scene<R>& S, const Nd<R, NPT>& N, co
     for (int i = 0; i < 3; ++i) {
       const R D = alpha * N.pv[k][i];
       val += R(0.5) * S.w * D * (R(2) * N.dx[k][i] + D) - S.m * S.grav[i] * D;
+      if (S.so) val += D * (S.cm * (N.dx[k][i] + R(0.5) * D) - S.w * S.dt * N.v[k][i]);
     }
 #pragma unroll
     for (int gi = 0; gi < 2; ++gi)
@@ -541,6 +588,14 @@ __device__ __forceinline__ R psi_diff(const Scene<R>& S, const Nd<R, NPT>& N, co
       const R dl = (dD[0] * (R(2) * dX[0] + dD[0]) + dD[1] * (R(2) * dX[1] + dD[1]) +
                     dD[2] * (R(2) * dX[2] + dD[2])) / (lY + lX);
       val += R(0.5) * (si == 2 ? S.k1 : S.k2) * dl * (lY + lX - R(2) * N.Ls[k][si]);
+      if (S.so) {
+        // damping potential (y_jo - y_j)^T c u u^T (y_jo - y_j)/2 of the displacement y = dx
+        R ua[3], yd[3];
+        const R cs = damp_axis(S, N, w, k, si, ua);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) yd[i] = w.dx[i * w.NVP + jo] - N.dx[k][i] + R(0.5) * dD[i];
+        val += cs * dot3(ua, dD) * dot3(ua, yd);
+      }
     }
   }
   return val;
@@ -575,7 +630,11 @@ template <typename R, int NPT>
 __device__ __forceinline__ int stage1_newton(const Scene<R>& S, Nd<R, NPT>& N, const Sm<R>& w, Red& rb,
                                              int* iters, bool warm) {
   if (!warm) {
-    zero3<R, NPT>(N.dx);
+    // the inertial variant starts at the predictor x0 + dt v
+#pragma unroll
+    for (int k = 0; k < NPT; ++k)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) N.dx[k][i] = S.so ? S.dt * N.v[k][i] : R(0);
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
 #pragma unroll
@@ -779,7 +838,18 @@ __device__ __forceinline__ void diag_block(const Scene<R>& S, const Nd<R, NPT>& 
     spring_eval(e, (si == 1 || si == 2) ? S.k1 : S.k2, N.Ls[k][si], false, f, H);
 #pragma unroll
     for (int i = 0; i < 9; ++i) D[i] += H[i];
+    if (S.so) {
+      R ua[3];
+      const R cs = damp_axis(S, N, w, k, si, ua);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) D[i * 3 + q] += cs * ua[i] * ua[q];
+    }
   }
+  if (S.so)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D[i * 4] += S.cm;
 }
 
 // Primal-dual interior point with Nesterov-Todd scaling (Vandenberghe, "The CVXOPT linear and
@@ -1181,7 +1251,10 @@ __device__ __forceinline__ void advance_state(const Scene<R>& S, Nd<R, NPT>& N, 
         for (int i = 0; i < 3; ++i)
           w.misc[M_C + 3 * gi + i] += w.misc[M_U + 3 * gi + i] - (N.dx[k][i] + N.Dl[k][i]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) N.x0[k][i] += N.dx[k][i] + N.Dl[k][i];
+    for (int i = 0; i < 3; ++i) {
+      N.x0[k][i] += N.dx[k][i] + N.Dl[k][i];
+      if (S.so) N.v[k][i] = (N.dx[k][i] + N.Dl[k][i]) / S.dt;
+    }
   }
   if (threadIdx.x < 6) w.misc[M_G + threadIdx.x] += w.misc[M_U + threadIdx.x];
   publish<R, NPT>(w.x0, N.x0, w.NVP);
@@ -1359,11 +1432,14 @@ __device__ __forceinline__ void load_q(const Scene<R>& S, Nd<R, NPT>& N, const S
   for (int k = 0; k < NPT; ++k) {
     const int j = node_of(k);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) N.x0[k][i] = j < S.nv ? q[3 * j + i] : R(0);
+    for (int i = 0; i < 3; ++i) {
+      N.x0[k][i] = j < S.nv ? q[3 * j + i] : R(0);
+      N.v[k][i] = (S.so && j < S.nv) ? q[3 * S.nv + 3 * j + i] : R(0);
+    }
   }
   const int t = threadIdx.x;
   if (t < 6) {
-    const R g = q[3 * S.nv + t];
+    const R g = q[S.nq - 6 + t];
     w.misc[M_G + t] = g;
     w.misc[M_C + t] = g - q[3 * S.grasp[t / 3] + t % 3];
   }
@@ -1378,9 +1454,12 @@ __device__ __forceinline__ void store_q(const Scene<R>& S, const Nd<R, NPT>& N, 
     const int j = node_of(k);
     if (j < S.nv)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) q[3 * j + i] = N.x0[k][i];
+      for (int i = 0; i < 3; ++i) {
+        q[3 * j + i] = N.x0[k][i];
+        if (S.so) q[3 * S.nv + 3 * j + i] = N.v[k][i];
+      }
   }
-  if (threadIdx.x < 6) q[3 * S.nv + threadIdx.x] = w.misc[M_G + threadIdx.x];
+  if (threadIdx.x < 6) q[S.nq - 6 + threadIdx.x] = w.misc[M_G + threadIdx.x];
 }
 
 template <typename R, int NPT>
@@ -1461,7 +1540,7 @@ __host__ __device__ constexpr int ctas_per_sm() { return sizeof(R) == 4 && NPT =
 template <typename R, int NPT>
 __global__ void __launch_bounds__(NT, (ctas_per_sm<R, NPT>())) rope_cta_rollout_kernel(
     Scene<R> S, int B, int H, const R* q0, const R* U, R* traj, R* qH, int32_t* status, int32_t* counters) {
-  const int nq = 3 * S.nv + 6;
+  const int nq = S.nq;
   Sm<R> w = sm_carve<R>(reinterpret_cast<R*>(rc_smem), NPT, S.nobs);
   Red rb;
   Nd<R, NPT> N;

@@ -31,7 +31,7 @@ __device__ __forceinline__ bool block_chol_pairs(R* T, R* B, int N);
 template <typename R, int NPT>
 __global__ void __launch_bounds__(NT, (ctas_per_sm<R, NPT>())) rope_cta_lin_step_kernel(
     Scene<R> S, int B, int H, const R* Z, const R* Vc, R* fac, size_t fac_stride, int32_t* status) {
-  const int nq = 3 * S.nv + 6;
+  const int nq = S.nq;
   Sm<R> w = sm_carve<R>(reinterpret_cast<R*>(rc_smem), NPT, S.nobs);
   Red rb;
   Nd<R, NPT> N;
@@ -226,6 +226,53 @@ __device__ __forceinline__ void block_solve_col(const R* F, R* r, int ld, int N)
   }
 }
 
+// Inertial variant, direction e of node jn's coordinate cc.  With rhs1: adds (D/dt) e - G e to
+// the column, G = d/dx [(D/dt) y] at y = x* - x; else (rhs2) adds -G e at y = Delta.  For the
+// spring (jn, jo), u the unit vector from jn to jo at the step start, c = (damp_beta/dt) k and
+// yd = y_jo - y_jn, the damping force on jo is f = c u (u.yd) (on jn -f) and
+// df/d(x_jo - x_jn) = (c/l) [(u.yd)(I - u u^T) + u (yd - u (u.yd))^T].  yofs: y in the record
+// (3 nv: dx, 6 nv: Delta).
+template <typename R, typename Col>
+__device__ __forceinline__ void damp_tangent(const Scene<R>& S, const R* rn, int jn, int cc, int yofs, Col E,
+                                             bool with_D) {
+  const int nv = S.nv;
+  if (with_D) E(jn, cc) += S.cm;
+#pragma unroll
+  for (int si = 0; si < 4; ++si) {
+    const int o = si == 0 ? -2 : (si == 1 ? -1 : (si == 2 ? 1 : 2));
+    const int jo = jn + o;
+    if (jo < 0 || jo >= nv) continue;
+    const int a = o < 0 ? jo : jn;
+    (void)a;
+    R ua[3], yd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      ua[i] = rn[3 * jo + i] - rn[3 * jn + i];
+      yd[i] = rn[yofs + 3 * jo + i] - rn[yofs + 3 * jn + i];
+    }
+    const R l = sqrt(dot3(ua, ua)), il = R(1) / l;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ua[i] *= il;
+    const R cs = S.cb * ((si == 1 || si == 2) ? S.k1 : S.k2);
+    const R uy = dot3(ua, yd);
+    // G e at jo (e = e_cc at jn, d/dx_jn of (x_jo - x_jn) = -I): -J e; at jn: +J e
+    R Je[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      Je[i] = cs * il * (uy * ((i == cc ? R(1) : R(0)) - ua[i] * ua[cc]) + ua[i] * (yd[cc] - ua[cc] * uy));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      E(jn, i) -= Je[i];
+      E(jo, i) += Je[i];
+      if (with_D) {
+        const R t = cs * ua[i] * ua[cc];
+        E(jn, i) += t;
+        E(jo, i) -= t;
+      }
+    }
+  }
+}
+
 // dR/dx* blocks of a job from its record's node state: per node Kc = sum_o [-W (n n^T + phi N) +
 // (d lam / d n) N], per spring (j, j+o) the third-derivative block Ks with t = Ks (v_b - v_a)
 template <typename R>
@@ -309,7 +356,7 @@ template <typename R>
 __global__ void __launch_bounds__(160, 3) rope_lin_tangent_kernel(Scene<R> S, int B, int H, int NP,
                                                                  const R* fac, size_t fac_stride, int dpr,
                                                                  R* A, R* Bm) {
-  const int nv = S.nv, nq = 3 * nv + 6, N = S.npair, ndir = nq + 6;
+  const int nv = S.nv, nq = S.nq, N = S.npair, ndir = nq + 6;
   const size_t fb = (size_t)(LDT + 2 * CR_LDM) * NP;
   const size_t fs = (2 * fb + 9 * (size_t)nv + 32 + 1 + 3) / 4 * 4;
   R* sm = reinterpret_cast<R*>(rc_smem);
@@ -350,9 +397,11 @@ __global__ void __launch_bounds__(160, 3) rope_lin_tangent_kernel(Scene<R> S, in
       __syncthreads();
       const int dir = rd * dpr + tid;
       const bool act = tid < dpr && dir < ndir;
+      // kind 0: node position, 3: node velocity (inertial variant), 1: gripper, 2: control
       int kind = 0, jn = 0, cc = 0, gi = 0;
       if (dir < 3 * nv) { kind = 0; jn = dir / 3; cc = dir % 3; }
-      else if (dir < nq) { kind = 1; gi = (dir - 3 * nv) / 3; cc = (dir - 3 * nv) % 3; }
+      else if (dir < nq - 6) { kind = 3; jn = (dir - 3 * nv) / 3; cc = (dir - 3 * nv) % 3; }
+      else if (dir < nq) { kind = 1; gi = (dir - (nq - 6)) / 3; cc = (dir - (nq - 6)) % 3; }
       else { kind = 2; gi = (dir - nq) / 3; cc = (dir - nq) % 3; if (gi > 1) gi = 1; }
       R* col = tv + (tid < dpr ? tid : 0);
       auto E = [&](int j, int i) -> R& { return col[(size_t)(3 * j + i) * dpr]; };
@@ -369,6 +418,9 @@ __global__ void __launch_bounds__(160, 3) rope_lin_tangent_kernel(Scene<R> S, in
               const R dd = -gd[3 * g2 + cc];
               for (int i = 0; i < 3; ++i) E(jn, i) -= (ga[6 * g2 + i] - (c[3 * g2 + i] + u[3 * g2 + i])) * dd;
             }
+          if (S.so) damp_tangent(S, rn, jn, cc, 3 * nv, E, true);   // (D/dt) e - d/dx[(D/dt)(x* - x)] e
+        } else if (kind == 3) {
+          E(jn, cc) += S.w * S.dt;                                  // -dF/dv = M/dt
         } else {
           const int a = S.grasp[gi];
           E(a, cc) += d[gi];
@@ -379,7 +431,7 @@ __global__ void __launch_bounds__(160, 3) rope_lin_tangent_kernel(Scene<R> S, in
         for (int j = 0; j < nv; ++j)
           for (int i = 0; i < 3; ++i) out[(size_t)(3 * j + i) * ld + oc] = E(j, i);
         for (int r = 0; r < 6; ++r)
-          out[(size_t)(3 * nv + r) * ld + oc] = (kind >= 1 && r == 3 * gi + cc) ? R(1) : R(0);
+          out[(size_t)(nq - 6 + r) * ld + oc] = ((kind == 1 || kind == 2) && r == 3 * gi + cc) ? R(1) : R(0);
       }
       __syncthreads();                                // F1 read by every direction
       dR_blocks(S, rn, Kc, Ks);
@@ -434,8 +486,11 @@ __global__ void __launch_bounds__(160, 3) rope_lin_tangent_kernel(Scene<R> S, in
             c2[i] = j + 3 < nv ? E(j + 3, i) : R(0);
           }
         }
+        // inertial variant: P's damping depends on the step start, -d/dx[(D/dt) Delta] e
+        if (S.so && kind == 0) damp_tangent(S, rn, jn, cc, 6 * nv, E, false);
         block_solve_col(F2, col, dpr, N);             // dDelta
-        // dq+/dtheta = dx* (written above) + dDelta, read back a pair of nodes at a time
+        // dq+/dtheta = dx* (written above) + dDelta, read back a pair of nodes at a time; the
+        // inertial variant's velocity rows (dx+/dtheta - dx/dtheta)/dt
         for (int j0 = 0; j0 < nv; j0 += 2) {
           const int nn = j0 + 1 < nv ? 6 : 3;
           R o6[6];
@@ -444,7 +499,14 @@ __global__ void __launch_bounds__(160, 3) rope_lin_tangent_kernel(Scene<R> S, in
             if (e < nn) o6[e] = out[(size_t)(3 * j0 + e) * ld + oc];
 #pragma unroll
           for (int e = 0; e < 6; ++e)
-            if (e < nn) out[(size_t)(3 * j0 + e) * ld + oc] = o6[e] + col[(size_t)(3 * j0 + e) * dpr];
+            if (e < nn) {
+              const R xp = o6[e] + col[(size_t)(3 * j0 + e) * dpr];
+              out[(size_t)(3 * j0 + e) * ld + oc] = xp;
+              if (S.so) {
+                const R ex = (kind == 0 && 3 * j0 + e == 3 * jn + cc) ? R(1) : R(0);
+                out[(size_t)(3 * nv + 3 * j0 + e) * ld + oc] = (xp - ex) / S.dt;
+              }
+            }
         }
       }
       __syncthreads();                                // F1 / Kc, Ks free for the next pass

@@ -54,6 +54,8 @@ def make_params(scene: dict, real_bytes: int = 4, max_batch: int = 1, max_horizo
             P.obstacles[o].p[i] = float(v)
     P.fwd_mode = L.CS_HARD if p["fwd_mode"] == "hard" else L.CS_SMOOTH
     P.grad_mode = L.CS_SURROGATE if p["grad_mode"] == "surrogate" else L.CS_CONSISTENT
+    P.second_order = int(bool(p.get("second_order", False)))
+    P.damp_alpha, P.damp_beta = float(p.get("damp_alpha", 0.0)), float(p.get("damp_beta", 0.0))
     tol = DEFAULT_TOL[real_bytes]
     P.newton_max = int(overrides.get("newton_max", tol["newton_max"]))
     P.ipm_max = int(overrides.get("ipm_max", tol["ipm_max"]))
@@ -105,7 +107,8 @@ class Sim:
         self.params = make_params(scene, real_bytes, max_batch, max_horizon, **overrides)
         self.loss = make_loss(scene)
         self.nv = int(self.params.n_nodes)
-        self.nq = 3 * self.nv + 6
+        # state [x, g] (quasi-static), [x, v, g] (inertial variant)
+        self.nq = (6 if self.params.second_order else 3) * self.nv + 6
         rest = np.ascontiguousarray(scene["rest_x"], dtype=np.float64)
         h = C.c_void_p()
         L.check(L.lib().sim_create(C.byref(self.params),

@@ -39,9 +39,9 @@ def test_struct_layout_matches_c():
     #include <stddef.h>
     #include "cordsim.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(cs_params), sizeof(cs_loss), sizeof(cs_obstacle),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(cs_params), sizeof(cs_loss), sizeof(cs_obstacle),
              offsetof(cs_params, obstacles), offsetof(cs_params, max_horizon),
-             offsetof(cs_loss, goal_pos), offsetof(cs_params, newton_tol));
+             offsetof(cs_loss, goal_pos), offsetof(cs_params, newton_tol), offsetof(cs_params, damp_beta));
       return 0;
     }
     """
@@ -54,7 +54,7 @@ def test_struct_layout_matches_c():
     vals = [int(v) for v in out]
     assert vals == [C.sizeof(L.cs_params), C.sizeof(L.cs_loss), C.sizeof(L.cs_obstacle),
                     L.cs_params.obstacles.offset, L.cs_params.max_horizon.offset,
-                    L.cs_loss.goal_pos.offset, L.cs_params.newton_tol.offset]
+                    L.cs_loss.goal_pos.offset, L.cs_params.newton_tol.offset, L.cs_params.damp_beta.offset]
 
 
 def test_mpc_struct_layout_matches_c():
