@@ -104,8 +104,9 @@ def counts_mean(res):
 
 # the source files each kernel is compiled from (its own, the shared headers, its launcher)
 KERNEL_SOURCES = {
-    "rope": ["common.cuh", "cr.cuh", "rope.cuh", "launch_rope.cuh", "rope_vjp_f32.cu",
-             "rope_rollout_f32.cu", "rope_linearize_f32.cu"],
+    "rope": ["common.cuh", "cr.cuh", "rope.cuh", "rope_cta.cuh", "rope_cta_body.cuh", "rope_lin.cuh",
+             "rope_lin_body.cuh", "launch_rope.cuh", "rope_vjp_f32.cu", "rope_rollout_f32.cu",
+             "rope_linearize_f32.cu"],
     # the cloth VJP kernel's device code and its own launcher (the packed serving kernel, built
     # from the same headers, has a launcher of its own in the same file)
     "cloth": ["common.cuh", "rope.cuh", "cloth_band.cuh", "cloth.cuh", ("launch_cloth.cuh", "launch_cloth_vjp")],

@@ -96,7 +96,7 @@ typedef struct {
                                needs k >= 1)                                                  */
   int real_bytes;           /* 4 = FP32, 8 = FP64                                            */
   int max_batch, max_horizon; /* size the handle's workspace                                 */
-  /* Inertial variant (ropes; sim_rollout and sim_linearize only): the state is
+  /* Inertial variant (ropes; sim_rollout, sim_rollout_vjp, sim_linearize): the state is
    * q = [x (3 n_v), v (3 n_v), g (6)], n_q = 6 n_v + 6, and a step solves
    * M (x+ - x - dt v)/dt^2 + D (x+ - x)/dt + dE/dx(x+) = tau + sum J^T lam, v+ = (x+ - x)/dt, with
    * Rayleigh damping D = damp_alpha M + damp_beta sum_s k_s u_s u_s^T (the springs' axial

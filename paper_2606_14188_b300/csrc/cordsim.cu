@@ -152,7 +152,7 @@ cs_status sim_create(const cs_params* P, const double* rest_x, cs_sim** out) {
     return e == cudaErrorMemoryAllocation ? cs_fail(CS_ERR_OOM, "rest lengths") : cs_cuda_fail(e, "upload");
   }
   auto ws_elems = [&](int kk) {
-    return cloth ? cs::cloth_vjp_ws_elems(nv, P->max_horizon, kk) : cs::vjp_ws_elems(nv, P->max_horizon, kk);
+    return cloth ? cs::cloth_vjp_ws_elems(nv, P->max_horizon, kk) : cs::vjp_ws_elems(nv, P->max_horizon, kk, P->second_order ? 1 : 0);
   };
   if (s->P.checkpoint_every == 0) {
     // automatic: the smallest interval whose adjoint workspace fits in a quarter of the free
@@ -251,7 +251,6 @@ cs_status sim_rollout_vjp(cs_sim* s, int B, int H, const void* q0, const void* u
   if (!dL_dtraj && !loss) return cs_fail(CS_ERR_INVALID_ARG, "give dL_dtraj or a loss");
   if (B > 0 && (!q0 || !u || !dL_du)) return cs_fail(CS_ERR_INVALID_ARG, "q0, u and dL_du are required");
   if (loss && (r = cs_validate_loss(loss, s->nv))) return r;
-  if (s->P.second_order) return cs_fail(CS_ERR_UNSUPPORTED, "sim_rollout_vjp is built for the quasi-static step");
   if (B == 0) return CS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (s->P.kind == CS_CLOTH)

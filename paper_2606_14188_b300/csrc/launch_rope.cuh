@@ -23,9 +23,11 @@ cs_status rollout_cta(cs_sim* s, int B, int H, const void* q0, const void* u, vo
                       void* qH, int32_t* status, int32_t* counters, cudaStream_t st) {
   cs::Scene<R> S = make_scene<R>(s, nullptr);
   const size_t smem = cs::rc::sm_elems(NPT, s->P.n_obstacles) * sizeof(R);
-  cs_status r = launch_prep(cs::rc::rope_cta_rollout_kernel<R, NPT>, smem, s);
+  const bool so = s->P.second_order != 0;    // the inertial variant's copy of the kernels
+  auto kr = so ? cs::rci::rope_cta_rollout_kernel<R, NPT> : cs::rc::rope_cta_rollout_kernel<R, NPT>;
+  cs_status r = launch_prep(kr, smem, s);
   if (r) return r;
-  cs::rc::rope_cta_rollout_kernel<R, NPT><<<B, cs::rc::NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
+  kr<<<B, cs::rc::NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
                                                                        (R*)traj, (R*)qH, status, counters);
   return check_launch("rope_cta_rollout_kernel");
 }
@@ -43,13 +45,17 @@ cs_status vjp_cta(cs_sim* s, int B, int H, const void* q0, const void* u, const 
                   cudaStream_t st) {
   cs::Scene<R> S = make_scene<R>(s, loss);
   const size_t smem = cs::rc::sm_elems(NPT, s->P.n_obstacles) * sizeof(R);
-  cs_status r = launch_prep(cs::rc::rope_cta_vjp_kernel<R, NPT>, smem, s);
+  const bool so = s->P.second_order != 0;    // the inertial variant's copy of the kernels
+  auto k_all = so ? cs::rci::rope_cta_vjp_kernel<R, NPT> : cs::rc::rope_cta_vjp_kernel<R, NPT>;
+  auto k_fwd = so ? cs::rci::rope_cta_vjp_fwd_kernel<R, NPT> : cs::rc::rope_cta_vjp_fwd_kernel<R, NPT>;
+  auto k_bwd = so ? cs::rci::rope_cta_vjp_bwd_kernel<R, NPT> : cs::rc::rope_cta_vjp_bwd_kernel<R, NPT>;
+  cs_status r = launch_prep(k_all, smem, s);
   if (r) return r;
   const int NT = cs::rc::NT;
   if (s->d_fac && s->d_queue) {
     // work queue: forward jobs, then (rollout, segment) jobs, each rollout's adjoint chain in the
     // CTA that finishes its last segment; a persistent grid of the CTAs the device holds at once
-    auto kq = cs::rc::rope_cta_vjp_queue_kernel<R, NPT>;
+    auto kq = so ? cs::rci::rope_cta_vjp_queue_kernel<R, NPT> : cs::rc::rope_cta_vjp_queue_kernel<R, NPT>;
     if ((r = launch_prep(kq, smem, s))) return r;
     const int nseg = (H + s->P.checkpoint_every - 1) / s->P.checkpoint_every;
     int per_sm = 0;
@@ -70,25 +76,25 @@ cs_status vjp_cta(cs_sim* s, int B, int H, const void* q0, const void* u, const 
   // so the forward parts run first (each measuring its cost), then the backward parts, costliest
   // first, leaving the cheap ones to start late.
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cs::rc::rope_cta_vjp_kernel<R, NPT>, NT, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_all, NT, smem);
   if ((long long)per_sm * s->sms < B && B <= cs::CS_ORDER_MAX) {
-    if ((r = launch_prep(cs::rc::rope_cta_vjp_fwd_kernel<R, NPT>, smem, s))) return r;
-    if ((r = launch_prep(cs::rc::rope_cta_vjp_bwd_kernel<R, NPT>, smem, s))) return r;
+    if ((r = launch_prep(k_fwd, smem, s))) return r;
+    if ((r = launch_prep(k_bwd, smem, s))) return r;
     int32_t* cost = reinterpret_cast<int32_t*>(static_cast<char*>(s->d_ws) +
                                                vjp_ord_offset(s->ws_stride, s->P.max_batch, s->real_bytes));
     int32_t* order = cost + B;
-    cs::rc::rope_cta_vjp_fwd_kernel<R, NPT><<<B, NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
+    k_fwd<<<B, NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
                                                                  (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
                                                                  status, (R*)s->d_ws, s->ws_stride, cost);
     if ((r = check_launch("rope_cta_vjp_fwd_kernel"))) return r;
     cs::rope_order_kernel<cs::CS_ORDER_NT><<<1, cs::CS_ORDER_NT, 0, st>>>(cost, B, order);
     if ((r = check_launch("rope_order_kernel"))) return r;
-    cs::rc::rope_cta_vjp_bwd_kernel<R, NPT><<<B, NT, smem, st>>>(S, B, H, (const R*)u, (const R*)dLdtraj, (R*)L,
+    k_bwd<<<B, NT, smem, st>>>(S, B, H, (const R*)u, (const R*)dLdtraj, (R*)L,
                                                                  (R*)dLdu, (R*)dLdq0, status, (R*)s->d_ws,
                                                                  s->ws_stride, cost, order);
     return check_launch("rope_cta_vjp_bwd_kernel");
   }
-  cs::rc::rope_cta_vjp_kernel<R, NPT><<<B, NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
+  k_all<<<B, NT, smem, st>>>(S, B, H, (const R*)q0, (const R*)u,
                                                            (const R*)dLdtraj, (R*)L, (R*)dLdu, (R*)dLdq0,
                                                            status, (R*)s->d_ws, s->ws_stride);
   return check_launch("rope_cta_vjp_kernel");
@@ -110,8 +116,9 @@ cs_status linearize_cta(cs_sim* s, int B, int H, const void* z, const void* v, v
                         int32_t* status, cudaStream_t st) {
   cs::Scene<R> S = make_scene<R>(s, nullptr);
   const size_t smem1 = cs::rc::sm_elems(NPT, s->P.n_obstacles) * sizeof(R);
-  auto k1 = cs::rc::rope_cta_lin_step_kernel<R, NPT>;
-  auto k2 = cs::rc::rope_lin_tangent_kernel<R>;
+  const bool so = s->P.second_order != 0;    // the inertial variant's copy of the kernels
+  auto k1 = so ? cs::rci::rope_cta_lin_step_kernel<R, NPT> : cs::rc::rope_cta_lin_step_kernel<R, NPT>;
+  auto k2 = so ? cs::rci::rope_lin_tangent_kernel<R> : cs::rc::rope_lin_tangent_kernel<R>;
   cs_status r = launch_prep(k1, smem1, s);
   if (r) return r;
   const int nv = s->nv, N = s->npair, ndir = s->nq + 6;

@@ -81,6 +81,9 @@ __device__ __forceinline__ WS<R> ws_carve(R* base, int NP, int nobs, int H, bool
 // checkpoint record of a state: q [n_q] | c [6] | dx [3 nv] | Delta [3 nv] (grasp offsets, and
 // the stage-1 offset and stage-2 displacement of the step that produced the state)
 __host__ __device__ inline int rec_len(int nv) { return 3 * nv + 6 + 6 + 6 * nv; }
+// the record of the CTA kernels (rope_cta.cuh): the same, then (inertial variant) the velocities
+// [3 nv]
+__host__ __device__ inline int rec_len_rc(int nv, int so) { return rec_len(nv) + (so ? 3 * nv : 0); }
 
 // contact-pair element addresses
 __device__ __forceinline__ int cv(int o, int h, int c, int p, int NP) { return ((o * 2 + h) * 3 + c) * NP + p; }
@@ -1266,13 +1269,14 @@ __global__ void __launch_bounds__(32) rope_rollout_kernel(Scene<R> S, int B, int
 enum { VJP_FWD = 1, VJP_BWD = 2, VJP_ALL = 3 };
 
 // what the forward part hands to the backward part, per rollout, after its records: the adjoint
-// seeds of q_H [6][32 PPL] (lane-major) and of the grippers [6]
-__host__ __device__ constexpr int vjp_carry_elems(int PPL) { return 6 * 32 * PPL + 8; }
+// seeds of q_H [6][32 PPL] (lane-major) and of the grippers [6]; with so (the inertial variant of
+// the CTA kernels) room for the velocity seeds
+__host__ __device__ constexpr int vjp_carry_elems(int PPL, int so = 0) { return (so ? 12 : 6) * 32 * PPL + 8; }
 
 // elements of one rollout's adjoint workspace: checkpoint records, segment records, carry
-__host__ __device__ inline size_t vjp_ws_elems(int nv, int H, int k) {
+__host__ __device__ inline size_t vjp_ws_elems(int nv, int H, int k, int so = 0) {
   const int nseg = (H + k - 1) / k;
-  return ((size_t)(nseg + 1 + k) * rec_len(nv) + 3) / 4 * 4 + vjp_carry_elems(2);
+  return ((size_t)(nseg + 1 + k) * rec_len_rc(nv, so) + 3) / 4 * 4 + vjp_carry_elems(2, so);
 }
 
 // the same for a cloth (one CTA per rollout): records, then a carry of the adjoint seeds of q_H

@@ -1,6 +1,7 @@
 """The inertial variant (state [x, v, g], implicit Euler inertia, axial Rayleigh damping) on the GPU
-against its FP64 oracle, oracle/second_order.py: the rope rollout of the 20-node workload and the
-linearisation A_t, B_t of the 40-node workload (a 240 + 6 dimensional state)."""
+against its FP64 oracle, oracle/second_order.py: the rope rollout and the rollout gradient of the
+20-node workload, and the linearisation A_t, B_t of the 40-node workload (a 240 + 6 dimensional
+state)."""
 import copy
 
 import numpy as np
@@ -109,12 +110,24 @@ def test_inertial_rope40_linearize_full_size_fp32_sampled():
             assert np.linalg.norm(Bg - Br) <= 1e-3 * np.linalg.norm(Br), (b, t)
 
 
-def test_inertial_adjoint_is_refused():
-    from paper_2606_14188_b300 import _lib
-    w = scenes.workload(1, B=1)
+@pytest.mark.parametrize("rb,tol_s,tol_g,cos", [(8, 1e-8, 1e-7, 1 - 1e-12), (4, 1e-4, 1e-3, 0.999)])
+def test_inertial_rope20_gradient_matches_the_oracle(rb, tol_s, tol_g, cos):
+    """Forward + checkpointed adjoint of the planning loss in the inertial variant (surrogate:
+    nonsmooth forward, smooth step Jacobians along it), checkpoint every 3 steps (ragged last
+    segment), against the oracle's rollout adjoint; also dL/dq0 (positions, velocities, grippers)."""
+    w = scenes.workload(1, B=3)
     sc = _inertial(w["scene"])
-    s = _sim(sc, 8, 1, 4)
-    q = torch.zeros(1, s.nq, dtype=torch.float64, device="cuda")
-    U = torch.zeros(1, 4, 6, dtype=torch.float64, device="cuda")
-    with pytest.raises(_lib.CordsimError):
-        s.rollout_vjp(q, U)
+    sc["params"]["checkpoint_every"] = 3
+    osc = osim.Scene(sc["params"], sc["rest_x"])
+    B, H = 3, w["H"]
+    Q0 = np.stack([_start(osc, w["q0"][b], 21 + b) for b in range(B)])
+    s = _sim(sc, rb, B, H)
+    Lv, dU, dq0, st = s.rollout_vjp(_t(Q0, rb), _t(w["U"][:B], rb))
+    for b in range(B):
+        ref = so.rollout_vjp2(osc, Q0[b], w["U"][b], "surrogate")
+        assert ref["status"] == 0 and int(st[b]) == 0
+        assert abs(float(Lv[b]) - ref["L"]) <= tol_s * abs(ref["L"])
+        for g, r in ((dU[b].cpu().numpy().ravel(), ref["dL_du"].ravel()),
+                     (dq0[b].cpu().numpy(), ref["dL_dq0"])):
+            assert np.linalg.norm(g - r) <= tol_g * np.linalg.norm(r), b
+            assert g @ r >= cos * np.linalg.norm(g) * np.linalg.norm(r), b
