@@ -655,7 +655,9 @@ def run_ours(args):
     _leg("cloth", t_leg)
 
     if rank == 0:
-        node_steps = B * nv * H
+        # only the node-steps of the rollouts that completed count (a flagged rollout stops at
+        # its failing step); every rank's shard has the same make-up in expectation
+        node_steps = int(np.count_nonzero(status == 0)) * nv * H
         value = world * args.steps * node_steps / t
         e2e_value = world * args.steps * node_steps / te
         avg_launch = t / args.steps
@@ -670,9 +672,10 @@ def run_ours(args):
             achieved = f_ns * node_steps / avg_launch / 1e12
             roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s",
                         frac=achieved / peak, traffic=load_traffic("rope_vjp_call"),
-                        kernels="one sim_rollout_vjp call: rope_vjp_fwd_kernel, rope_order_kernel, "
-                                "rope_vjp_bwd_kernel (more rollouts than the device holds at once); "
-                                "achieved = the call's flops / the call's event time",
+                        kernels="one sim_rollout_vjp call: rope_cta_vjp_queue_kernel (forward jobs, "
+                                "(rollout, segment) jobs, per-rollout adjoint chains) and "
+                                "rope_queue_finish_kernel; achieved = the completed rollouts' flops / "
+                                "the call's event time",
                         peak_source=f"FP32 FMA: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
                                     "(recipe unit counts and the max SM clock)",
                         flops_per_node_step=f_ns, oracle_iterations_per_step=counts)
@@ -700,6 +703,8 @@ def run_ours(args):
                     linearize=lin, served=served, cloth=cloth,
                     gpu_launches=launches, clocks=clocks,
                     status_nonzero=int(np.count_nonzero(status)),
+                    node_steps_counted=f"{int(np.count_nonzero(status == 0))} of {B} rollouts "
+                                       f"(the flagged ones excluded) x {nv} nodes x {H} steps",
                     per_step_ms=[round(x * 1e3, 4) for x in per])
         print(json.dumps(line), flush=True)
     if world > 1:
