@@ -291,7 +291,7 @@ def linearize_leg(args, flush, stream, world):
                 ms_per_step=1e3 * avg, bytes_per_launch=out_bytes + in_bytes,
                 status_nonzero=int(torch.count_nonzero(st).item()),
                 roofline=dict(bound="hbm", achieved=gbs, peak=peak, unit="GB/s", frac=gbs / peak,
-                              traffic=load_traffic("rope_linearize_kernel", f"rope{nv}_b{B}_h{H}"),
+                              traffic=load_traffic("rope_linearize_call", f"rope{nv}_b{B}_h{H}"),
                               peak_source=f"{src} HBM copy bandwidth"))
 
 
