@@ -265,6 +265,52 @@ def measured_hbm_peak():
         return 6400.0, "fallback"
 
 
+def inertial_leg(args, flush, stream, world):
+    """The inertial step variant (state [x, v, g], implicit Euler inertia, Rayleigh damping
+    alpha = 0.5 /s, beta = 0.02 s): forward + adjoint on the headline's 1024 rollouts of the
+    64-node rope (at rest at t = 0) and the linearisation of the 256 x 20 40-node workload in the
+    246-dimensional state, FP32."""
+    import copy
+    import torch
+    from paper_2606_14188_b300.sim import Sim
+    out = {}
+    w = scenes.workload(2, B=args.rollouts, H=args.rope_horizon)
+    sc = copy.deepcopy(w["scene"])
+    sc["params"].update(second_order=True, damp_alpha=0.5, damp_beta=0.02)
+    B, H, nv = w["B"], w["H"], sc["params"]["n_nodes"]
+    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H)
+    q = np.zeros((B, s.nq), dtype=np.float32)
+    q[:, :3 * nv] = w["q0"][:, :3 * nv]
+    q[:, 6 * nv:] = w["q0"][:, 3 * nv:]
+    q0 = torch.tensor(q, device="cuda")
+    U = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
+    res = []
+    per = time_device(lambda: res.append(s.rollout_vjp(q0, U, want_dq0=False)), args.steps, flush, stream)
+    t = max_over_ranks(sum(per), world) / args.steps
+    st = res[-1][3].cpu().numpy()
+    out["rollout_vjp"] = dict(workload=f"rope{nv}_b{B}_h{H}, inertial", ms_per_step=1e3 * t,
+                              value=world * int(np.count_nonzero(st == 0)) * nv * H / t, unit=UNIT,
+                              status_nonzero=int(np.count_nonzero(st)))
+    del s, res
+    w = scenes.workload(4)
+    sc = copy.deepcopy(w["scene"])
+    sc["params"].update(second_order=True, damp_alpha=0.5, damp_beta=0.02)
+    B, H, nv = w["B"], w["H"], sc["params"]["n_nodes"]
+    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H)
+    q = np.zeros((B, s.nq), dtype=np.float32)
+    q[:, :3 * nv] = w["q0"][:, :3 * nv]
+    q[:, 6 * nv:] = w["q0"][:, 3 * nv:]
+    V = torch.tensor(w["U"], dtype=torch.float32, device="cuda")
+    Z, _, _ = s.rollout(torch.tensor(q, device="cuda"), V)
+    A, Bm, st = s.linearize(Z, V)
+    per = time_device(lambda: s.linearize(Z, V), args.steps, flush, stream)
+    t = max_over_ranks(sum(per), world) / args.steps
+    out["linearize"] = dict(workload=f"rope{nv}_b{B}_h{H}, inertial (n_q = {s.nq})", ms_per_step=1e3 * t,
+                            value=world * B * H / t, unit="step Jacobians/s",
+                            status_nonzero=int(torch.count_nonzero(st).item()))
+    return out
+
+
 def linearize_leg(args, flush, stream, world):
     """sim_linearize on 256 nominal trajectories of a 40-node rope (horizon 20): every A_t, B_t of
     the smooth step written to HBM.  Bound: HBM writes of A and B."""
@@ -648,6 +694,9 @@ def run_ours(args):
     lin = linearize_leg(args, flush, stream, world)
     _leg("linearisation", t_leg)
     t_leg = time.perf_counter()
+    inertial = inertial_leg(args, flush, stream, world)
+    _leg("inertial variant", t_leg)
+    t_leg = time.perf_counter()
     served = served_leg(args) if args.served_requests > 0 else None
     _leg("served", t_leg)
     t_leg = time.perf_counter()
@@ -700,7 +749,7 @@ def run_ours(args):
                         what="sim_rollout_vjp on the same rollouts with checkpoint_every = 1 (every "
                              "step's record stored, no segment recompute); not the headline, whose "
                              "workload checkpoints every 7 steps"),
-                    linearize=lin, served=served, cloth=cloth,
+                    linearize=lin, inertial_variant=inertial, served=served, cloth=cloth,
                     gpu_launches=launches, clocks=clocks,
                     status_nonzero=int(np.count_nonzero(status)),
                     node_steps_counted=f"{int(np.count_nonzero(status == 0))} of {B} rollouts "
