@@ -177,8 +177,13 @@ cs_status sim_rollout_vjp(cs_sim* sim, int B, int H, const void* q0, const void*
  *   v  [B][H][6]     nominal controls
  *   A  [B][H][n_q][n_q]  A_t[i][j] = d q_{t+1,i} / d q_{t,j}
  *   Bm [B][H][n_q][6]    B_t[i][j] = d q_{t+1,i} / d u_{t,j}
- *   status [B] (OR over the steps)
- * Errors: as sim_rollout; CS_ERR_UNSUPPORTED for a cloth (built for ropes). */
+ *   status [B] (OR over the steps; a step whose smooth solve fails or whose H1 or H2 is not
+ *               positive definite gets NaN Jacobians)
+ * With the handle's per-step records (allocated by sim_create when they fit in half the free
+ * device memory) it runs as two launches: the smooth steps with their factorisations, then every
+ * tangent direction of a step in one CTA; otherwise one warp per (trajectory, step).
+ * Errors: as sim_rollout; CS_ERR_UNSUPPORTED for a cloth (built for ropes), and for the inertial
+ * variant without the per-step records. */
 cs_status sim_linearize(cs_sim* sim, int B, int H, const void* z, const void* v, void* A,
                         void* Bm, int32_t* status, void* stream);
 
