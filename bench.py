@@ -341,6 +341,64 @@ def linearize_leg(args, flush, stream, world):
                               peak_source=f"{src} HBM copy bandwidth"))
 
 
+def sls_leg(args, flush, stream, world):
+    """The output-feedback SLS observer stage about the linearisation workload's nominal
+    trajectories (the 40-node rope, 256 x 20 steps, state 126, the 120 node coordinates observed,
+    FP32): sls_observer (Kalman recursion and observer responses) and sls_closed_loop (the four
+    closed-loop maps) on the A_t, B_t that sim_linearize writes, the state-feedback responses from
+    seeded gains.  Bound: FP32 FMA (dense products of 120-126 wide blocks)."""
+    import torch
+    from paper_2606_14188_b300 import sls as gsls
+    from paper_2606_14188_b300.sim import Sim
+    w = scenes.workload(4)
+    sc, H = w["scene"], w["H"]
+    B = min(w["B"], args.sls_trajectories)
+    nv = sc["params"]["n_nodes"]
+    n, m, p = 3 * nv + 6, 6, 3 * nv
+    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H)
+    V = torch.tensor(w["U"][:B], dtype=torch.float32, device="cuda")
+    Z, _, _ = s.rollout(torch.tensor(w["q0"][:B], dtype=torch.float32, device="cuda"), V)
+    A, Bm, st = s.linearize(Z, V)
+    lin_flagged = int(torch.count_nonzero(st).item())
+    del s
+    obs = scenes.sls_observation_model(B, H, nv)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    Cm, E, F, Xi = (torch.tensor(obs[k], **f32) for k in ("C", "E", "F", "Xi"))
+    A = torch.nan_to_num(A).contiguous()          # a flagged linearisation step (NaN) stands as 0
+    Kg = torch.tensor(scenes.sls_feedback_gains(B, H, m, n), **f32)
+    PBX = gsls.response((A + torch.nan_to_num(Bm) @ Kg[:, :H]).contiguous())
+    kidx = torch.tensor([k for k in range(H + 1) for _ in range(k + 1)], device="cuda")
+    PBU = (Kg[:, kidx] @ PBX).contiguous()
+    for _ in range(max(1, args.warmup)):
+        out = gsls.observer(A, Cm, E, F, Xi)
+    flagged = int(torch.count_nonzero(out[4]).item())
+    PX, PY = out[2], out[3]
+    del out
+    for _ in range(max(1, args.warmup)):
+        maps = gsls.closed_loop(A, PBX, PBU, PX, PY)
+    del maps
+    t_obs = max_over_ranks(sum(time_device(lambda: gsls.observer(A, Cm, E, F, Xi), args.steps, flush,
+                                           stream)), world) / args.steps
+    t_cl = max_over_ranks(sum(time_device(lambda: gsls.closed_loop(A, PBX, PBU, PX, PY), args.steps,
+                                          flush, stream)), world) / args.steps
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2 * 2032e6 / 1e12
+    f_obs = flops.sls_observer_flops(H, n, p, n, p, n) * B
+    f_cl = flops.sls_closed_loop_flops(H, n, m, p) * B
+
+    def roof(f, t):
+        a = f / t / 1e12
+        return dict(bound="alu", achieved=a, peak=peak, unit="TFLOP/s", frac=a / peak, traffic=None,
+                    flops_per_call=f, peak_source=f"FP32 FMA: {sms} SMs x 128 lanes x 2 x 2032 MHz")
+
+    return dict(workload=f"rope{nv}_b{B}_h{H} observer stage (n {n}, p {p}, m {m})",
+                observer=dict(ms_per_step=1e3 * t_obs, value=world * B / t_obs, unit="trajectories/s",
+                              roofline=roof(f_obs, t_obs)),
+                closed_loop=dict(ms_per_step=1e3 * t_cl, value=world * B / t_cl, unit="trajectories/s",
+                                 roofline=roof(f_cl, t_cl)),
+                status_nonzero=flagged, linearize_status_nonzero=lin_flagged)
+
+
 def _cloth_sample_job(steps):
     from oracle import grad as ograd, sim as osim
     w = scenes.workload(3, B=1, H=steps)
@@ -694,6 +752,9 @@ def run_ours(args):
     lin = linearize_leg(args, flush, stream, world)
     _leg("linearisation", t_leg)
     t_leg = time.perf_counter()
+    sls_out = sls_leg(args, flush, stream, world) if args.sls_trajectories > 0 else None
+    _leg("observer stage", t_leg)
+    t_leg = time.perf_counter()
     inertial = inertial_leg(args, flush, stream, world)
     _leg("inertial variant", t_leg)
     t_leg = time.perf_counter()
@@ -749,7 +810,7 @@ def run_ours(args):
                         what="sim_rollout_vjp on the same rollouts with checkpoint_every = 1 (every "
                              "step's record stored, no segment recompute); not the headline, whose "
                              "workload checkpoints every 7 steps"),
-                    linearize=lin, inertial_variant=inertial, served=served, cloth=cloth,
+                    linearize=lin, sls_observer_stage=sls_out, inertial_variant=inertial, served=served, cloth=cloth,
                     gpu_launches=launches, clocks=clocks,
                     status_nonzero=int(np.count_nonzero(status)),
                     node_steps_counted=f"{int(np.count_nonzero(status == 0))} of {B} rollouts "
@@ -778,6 +839,8 @@ def main():
     ap.add_argument("--cloth-rollouts", type=int, default=None,
                     help="rollouts of the cloth leg (default 512, the workload's)")
     ap.add_argument("--cloth-steps", type=int, default=1, help="timed calls of the cloth leg")
+    ap.add_argument("--sls-trajectories", type=int, default=256,
+                    help="nominal trajectories of the observer-stage leg (default 256; 0: skip)")
     ap.add_argument("--served-repeats", type=int, default=1,
                     help="repeats of every served measurement (median and spread reported)")
     ap.add_argument("--served-cloth-fraction", type=float, default=0.0,

@@ -23,6 +23,7 @@
 #ifndef CORDSIM_H
 #define CORDSIM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -294,6 +295,67 @@ cs_status mpc_destroy(cs_mpc* mpc);
 /* Counters of a server: ticks run, graph launches, kernel launches, graphs captured. */
 cs_status mpc_stats(cs_mpc* mpc, int64_t* ticks, int64_t* graph_launches, int64_t* kernel_launches,
                     int64_t* graphs_built);
+
+/* ------------------------------------------------------------------------------------------
+ * Output-feedback SLS observer stage (Sec. 4.2): the Kalman recursion, the observer's closed-loop
+ * responses and the closed-loop maps, about B nominal trajectories at once (the consumer of
+ * sim_linearize's A_t).  Per trajectory, times 0..N, state dimension n, observation p, control m:
+ *   A  [B][N][n][n]   A_j, the dynamics linearisation (sim_linearize's A)
+ *   C  [B][N][p][n]   C_j, the observation model's linearisation
+ *   E  [B][N][n][nw]  E_j, process disturbance scaling
+ *   F  [B][N][p][ne]  F_j, observation disturbance scaling (F_j F_j^T positive definite)
+ *   Xi [B][n][n0]     initial state uncertainty
+ * A block lower-triangular operator over times 0..N is stored packed: block (k, j),
+ * 0 <= j <= k <= N, at index k (k + 1) / 2 + j of T = (N + 1)(N + 2) / 2 blocks, each row-major.
+ * Arrays are caller-owned DEVICE pointers in the real type real_bytes names (4 float, 8 double).
+ * `workspace` is caller-owned device memory of at least the size the matching *_workspace call
+ * returns; these calls allocate nothing.  Calls are asynchronous on `stream`; sizes and pointers
+ * are checked before any launch.  Errors: CS_ERR_INVALID_ARG (B < 0, a dimension < 1 or > 4096,
+ * real_bytes not 4 or 8, a NULL pointer while B > 0, a workspace too small), CS_ERR_CUDA. */
+
+/* Device bytes of scratch sls_observer needs (0 for invalid sizes). */
+size_t sls_observer_workspace(int B, int N, int n, int p, int real_bytes);
+
+/* Kalman recursion (Sec. 4.2 eq. kalman_recursions) and observer responses (eq.
+ * backward_propagations):
+ *   Pi   [B][N+1][n][n]  Pi_0 = Xi Xi^T,
+ *                        Pi_{j+1} = E_j E_j^T + A_j Pi_j A_j^T + A_j Pi_j C_j^T L_{j+1}
+ *   L    [B][N][p][n]    L[j] = L_{j+1} = -(F_j F_j^T + C_j Pi_j C_j^T)^{-1} C_j Pi_j A_j^T
+ *   PhiX [B][T][n][n]    Phihat^x_{k,k} = I, Phihat^x_{k,j} = Phihat^x_{k,j+1} (A_j + L_{j+1}^T C_j)
+ *   PhiY [B][T][n][p]    Phihat^y_{k,j} = Phihat^x_{k,j} L_j^T (j >= 1), Phihat^y_{k,0} = 0
+ *   status [B]           CS_ST_NOTPD when an innovation matrix F_j F_j^T + C_j Pi_j C_j^T was not
+ *                        positive definite: that step's gain and what follows it are NaN (may be
+ *                        NULL)
+ * The gain computed from (Pi_j, A_j, C_j) carries the label j+1 and is the one the propagation
+ * through A_j uses; Pi and L are the same for every injection time k.  p is limited by the gain
+ * solve's shared memory (p^2 + 2p reals within 200 KB: p <= 225 in FP32, 159 in FP64). */
+cs_status sls_observer(int B, int N, int n, int p, int nw, int ne, int n0, int real_bytes,
+                       const void* A, const void* C, const void* E, const void* F, const void* Xi,
+                       void* Pi, void* L, void* PhiX, void* PhiY, int32_t* status,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* Closed-loop response of x_{k+1} = Acl_k x_k + delta_{k+1}, the products that eq.
+ * backward_propagations forms, for given closed-loop matrices:
+ *   Acl [B][N][n][n];  Phi [B][T][n][n], Phi_{k,k} = I, Phi_{k,j} = Phi_{k,j+1} Acl_j.
+ * With Acl_j = A_j + B_j K_j it is the state-feedback response (I - Z (A + B K))^{-1}. */
+cs_status sls_response(int B, int N, int n, int real_bytes, const void* Acl, void* Phi,
+                       void* stream);
+
+/* Device bytes of scratch sls_closed_loop needs (0 for invalid sizes). */
+size_t sls_closed_loop_workspace(int B, int N, int n, int p, int real_bytes);
+
+/* Closed-loop maps (Sec. 4.2) from the state-feedback responses Phibar (the stage before this
+ * one; an input) and the observer's, with M = I - Z A (Z the block downshift):
+ *   PhiXW [B][T][n][n] = Phibar^x + Phihat^x - Phibar^x M Phihat^x
+ *   PhiUW [B][T][m][n] = Phibar^u (I - M Phihat^x)
+ *   PhiXE [B][T][n][p] = Phihat^y - Phibar^x M Phihat^y
+ *   PhiUE [B][T][m][p] = -Phibar^u M Phihat^y
+ * from A [B][N][n][n], PhiBarX [B][T][n][n], PhiBarU [B][T][m][n] and PhiX, PhiY as sls_observer
+ * writes them. */
+cs_status sls_closed_loop(int B, int N, int n, int m, int p, int real_bytes, const void* A,
+                          const void* PhiBarX, const void* PhiBarU, const void* PhiX,
+                          const void* PhiY, void* PhiXW, void* PhiUW, void* PhiXE, void* PhiUE,
+                          void* workspace, size_t workspace_bytes, void* stream);
 
 /* Number of kernel launches the library made on the calling thread since the last call
  * (instrumentation for benchmarks). */

@@ -97,6 +97,11 @@ SIGNATURES = {
     "mpc_destroy": (C.c_int, [C.c_void_p]),
     "mpc_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                             C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "sls_observer_workspace": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "sls_observer": (C.c_int, [C.c_int] * 8 + [C.c_void_p] * 10 + [C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sls_response": (C.c_int, [C.c_int] * 4 + [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sls_closed_loop_workspace": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "sls_closed_loop": (C.c_int, [C.c_int] * 6 + [C.c_void_p] * 9 + [C.c_void_p, C.c_size_t, C.c_void_p]),
     "cs_launch_count": (C.c_int64, []),
     "cs_last_error": (C.c_char_p, []),
 }

@@ -1,0 +1,648 @@
+// Output-feedback SLS observer stage (arxiv 2606.14188, Sec. 4.2): the Kalman recursion
+// (eq. kalman_recursions), the observer's closed-loop responses (eq. backward_propagations) and the
+// assembly of the closed-loop maps Phi^xw, Phi^uw, Phi^xe, Phi^ue, batched over nominal
+// trajectories.
+//
+// Every stage is a batch of dense products of small matrices (n, p ~ 100-250), computed by one
+// tile routine: a 64 x 64 output tile per 256-thread CTA, 4 x 4 outputs per thread, the operand
+// panels staged through shared memory 16 deep.  The trajectories, the blocks of a block-triangular
+// operator and the output tiles are the grid; the horizon is the sequential direction:
+//   Kalman   per step j, five batched products and one gain solve (a CTA per trajectory:
+//            Cholesky factor of the innovation matrix in shared memory, a thread per gain column);
+//   Phihat^x one launch per block diagonal d = k - j: Phihat^x_{k,j} = Phihat^x_{k,j+1} Abar_j for
+//            all (trajectory, k) at once, the products the paper's propagation forms, in N launches;
+//   assembly block lower-triangular products sum_i X_{k,i} Y_{i,j}, a CTA per output block tile.
+// The paper forms the horizon direction by associative scans to reach logarithmic depth for one
+// trajectory; with hundreds of trajectories in one call the batch already fills the GPU, and the
+// step-by-step recursion does several times fewer flops than a scan over the same elements.
+//
+// Packed block storage: block (k, j), 0 <= j <= k <= N, of a block lower-triangular operator over
+// times 0..N at index k (k + 1) / 2 + j of T = (N + 1)(N + 2) / 2 blocks, each row-major.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+
+#include "cordsim.h"
+
+cs_status cs_fail(cs_status s, const std::string& msg);
+cs_status cs_cuda_fail(cudaError_t e, const char* where);
+void cs_count_launch();
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16, NTH = 256, PADS = 4;
+constexpr size_t kGainSmemBudget = 200 * 1024;   // shared memory of the gain kernel
+
+template <typename R>
+struct Tile {
+  R a[TK][TM + PADS];   // op(A) panel, k-major
+  R b[TK][TN + PADS];   // op(B) panel, k-major
+};
+
+// acc += alpha op(A)[r0.., 0..K) op(B)[0..K, c0..] for this thread's 4 x 4 outputs (rows
+// r0 + 4 ty + u, columns c0 + 4 tx + v).  op(X)(i, k) = X[i ld + k] (t = 0) or X[k ld + i]
+// (t = 1); entries outside M x K and K x N read as zero.
+template <typename R>
+__device__ __forceinline__ void tile_mma(R (&acc)[4][4], const R* __restrict__ ap, int lda, int ta,
+                                         R alpha, const R* __restrict__ bp, int ldb, int tb, int M,
+                                         int N, int K, int r0, int c0, Tile<R>& sm) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+    for (int s = 0; s < TM * TK / NTH; ++s) {
+      const int e = tid + s * NTH;
+      int i, k;
+      if (ta) { i = e % TM; k = e / TM; } else { k = e % TK; i = e / TK; }
+      const int gi = r0 + i, gk = k0 + k;
+      R v = R(0);
+      if (gi < M && gk < K) v = alpha * (ta ? ap[(size_t)gk * lda + gi] : ap[(size_t)gi * lda + gk]);
+      sm.a[k][i] = v;
+    }
+#pragma unroll
+    for (int s = 0; s < TK * TN / NTH; ++s) {
+      const int e = tid + s * NTH;
+      int k, j;
+      if (tb) { k = e % TK; j = e / TK; } else { j = e % TN; k = e / TN; }
+      const int gk = k0 + k, gj = c0 + j;
+      R v = R(0);
+      if (gk < K && gj < N) v = tb ? bp[(size_t)gj * ldb + gk] : bp[(size_t)gk * ldb + gj];
+      sm.b[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      R av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        av[u] = sm.a[kk][4 * ty + u];
+        bv[u] = sm.b[kk][4 * tx + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+}
+
+// out = acc (+ d1) (+ d2) on the tile, within M x N (all three row-major with their own ld)
+template <typename R>
+__device__ __forceinline__ void tile_store(const R (&acc)[4][4], R* __restrict__ out, int ldo,
+                                           const R* d1, int ld1, const R* d2, int ld2, int M, int N,
+                                           int r0, int c0) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = r0 + 4 * ty + u;
+    if (i >= M) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = c0 + 4 * tx + v;
+      if (j >= N) continue;
+      R x = acc[u][v];
+      if (d1) x += d1[(size_t)i * ld1 + j];
+      if (d2) x += d2[(size_t)i * ld2 + j];
+      out[(size_t)i * ldo + j] = x;
+    }
+  }
+}
+
+__device__ __forceinline__ void unpack_block(long long t, int& k, int& j) {
+  int kk = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((long long)kk * (kk + 1) / 2 > t) --kk;
+  while ((long long)(kk + 1) * (kk + 2) / 2 <= t) ++kk;
+  k = kk;
+  j = (int)(t - (long long)kk * (kk + 1) / 2);
+}
+
+__host__ __device__ __forceinline__ long long tri_index(int k, int j) { return (long long)k * (k + 1) / 2 + j; }
+
+// ---------------------------------------------------------------------------------------------
+// batched C = sum_q alpha_q op(A_q) op(B_q) (+ D), batch item z = blockIdx.z + zoff
+// ---------------------------------------------------------------------------------------------
+
+template <typename R>
+struct Prod {
+  const R* a;
+  long long sa;
+  int lda, ta;
+  R alpha;
+  const R* b;
+  long long sb;
+  int ldb, tb;
+  int K;
+};
+
+template <typename R>
+struct Gemm {
+  int M, N, np;
+  Prod<R> pr[3];
+  const R* d;
+  long long sd;
+  int ldd;
+  R* c;
+  long long sc;
+  int ldc;
+  long long zoff;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(NTH) sls_gemm_kernel(Gemm<R> g) {
+  __shared__ __align__(16) Tile<R> sm;
+  const long long z = blockIdx.z + g.zoff;
+  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
+  R acc[4][4] = {};
+  for (int q = 0; q < g.np; ++q) {
+    const Prod<R> P = g.pr[q];
+    tile_mma(acc, P.a + z * P.sa, P.lda, P.ta, P.alpha, P.b + z * P.sb, P.ldb, P.tb, g.M, g.N, P.K,
+             r0, c0, sm);
+  }
+  tile_store(acc, g.c + z * g.sc, g.ldc, g.d ? g.d + z * g.sd : nullptr, g.ldd, (const R*)nullptr,
+             0, g.M, g.N, r0, c0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kalman gain of one step for every trajectory (a CTA each):
+//   L = -S^{-1} W^T,  S = F F^T + C Pi C^T  (p x p, SPD),  W = A Pi C^T  (n x p)
+// S is factorised S = G G^T in shared memory, right-looking, one barrier per column: phase c
+// subtracts column c's outer product (scaled by 1/S_cc) from the trailing block and scales column
+// c - 1 into G; then each thread solves G G^T x = w for one column of W^T.
+// ---------------------------------------------------------------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(NTH) sls_gain_kernel(int p, int n, int cw, const R* __restrict__ S,
+                                                       const R* __restrict__ W, R* __restrict__ L,
+                                                       long long sL, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char sls_smem[];
+  R* s = reinterpret_cast<R*>(sls_smem);   // p x p, row stride p
+  R* dg = s + (size_t)p * p;               // p pivots S_cc
+  R* x = dg + p;                           // p x cw right-hand sides, row stride cw
+  __shared__ int bad;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const R* Sb = S + (size_t)b * p * p;
+  for (int e = tid; e < p * p; e += NTH) s[e] = Sb[e];
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int c = 0; c < p; ++c) {
+    R d = s[(size_t)c * p + c];
+    if (!(d > R(0))) {        // not positive definite (or NaN): continue on 1 and flag
+      if (tid == 0) bad = 1;
+      d = R(1);
+    }
+    if (tid == 0) dg[c] = d;
+    const R rd = R(1) / d;
+    const int m = p - c - 1;
+    for (int e = tid; e < m * m; e += NTH) {
+      const int i = c + 1 + e / m, j = c + 1 + e % m;
+      if (j <= i) s[(size_t)i * p + j] -= s[(size_t)i * p + c] * s[(size_t)j * p + c] * rd;
+    }
+    if (c > 0) {
+      const R rs = R(1) / sqrt(dg[c - 1]);
+      for (int i = c + tid; i < p; i += NTH) s[(size_t)i * p + c - 1] *= rs;
+    }
+    __syncthreads();
+  }
+  for (int c = tid; c < p; c += NTH) s[(size_t)c * p + c] = sqrt(dg[c]);
+  __syncthreads();
+
+  const R* Wb = W + (size_t)b * n * p;
+  R* Lb = L + (size_t)b * sL;
+  const R nan = R(NAN);
+  for (int c0 = 0; c0 < n; c0 += cw) {
+    const int cn = min(cw, n - c0);
+    for (int e = tid; e < p * cn; e += NTH) {
+      const int i = e / cn, t = e % cn;
+      x[(size_t)i * cw + t] = Wb[(size_t)(c0 + t) * p + i];
+    }
+    __syncthreads();
+    if (tid < cn) {
+      R* xc = x + tid;
+      for (int i = 0; i < p; ++i) {          // G y = w
+        const R* gi = s + (size_t)i * p;
+        R a0 = xc[(size_t)i * cw], a1 = 0, a2 = 0, a3 = 0;
+        int k = 0;
+        for (; k + 4 <= i; k += 4) {
+          a0 -= gi[k] * xc[(size_t)k * cw];
+          a1 -= gi[k + 1] * xc[(size_t)(k + 1) * cw];
+          a2 -= gi[k + 2] * xc[(size_t)(k + 2) * cw];
+          a3 -= gi[k + 3] * xc[(size_t)(k + 3) * cw];
+        }
+        for (; k < i; ++k) a0 -= gi[k] * xc[(size_t)k * cw];
+        xc[(size_t)i * cw] = ((a0 + a1) + (a2 + a3)) / gi[i];
+      }
+      for (int i = p - 1; i >= 0; --i) {     // G^T z = y
+        R a0 = xc[(size_t)i * cw], a1 = 0, a2 = 0, a3 = 0;
+        int k = i + 1;
+        for (; k + 4 <= p; k += 4) {
+          a0 -= s[(size_t)k * p + i] * xc[(size_t)k * cw];
+          a1 -= s[(size_t)(k + 1) * p + i] * xc[(size_t)(k + 1) * cw];
+          a2 -= s[(size_t)(k + 2) * p + i] * xc[(size_t)(k + 2) * cw];
+          a3 -= s[(size_t)(k + 3) * p + i] * xc[(size_t)(k + 3) * cw];
+        }
+        for (; k < p; ++k) a0 -= s[(size_t)k * p + i] * xc[(size_t)k * cw];
+        xc[(size_t)i * cw] = ((a0 + a1) + (a2 + a3)) / s[(size_t)i * p + i];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < p * cn; e += NTH) {
+      const int i = e / cn, t = e % cn;
+      Lb[(size_t)i * n + c0 + t] = bad ? nan : -x[(size_t)i * cw + t];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && bad && status) atomicOr(status + b, CS_ST_NOTPD);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block-triangular operators (packed storage; item z = blockIdx.z + zoff over (trajectory, block))
+// ---------------------------------------------------------------------------------------------
+
+// identity diagonal blocks Phi_{k,k} = I of every trajectory
+template <typename R>
+__global__ void sls_identity_kernel(long long nb, int N, int n, R* Phi) {
+  const long long T = (long long)(N + 1) * (N + 2) / 2;
+  const long long total = nb * (N + 1) * n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long blk = e / ((long long)n * n);
+    const int r = (int)(e % ((long long)n * n));
+    const long long b = blk / (N + 1);
+    const int k = (int)(blk % (N + 1));
+    Phi[(b * T + tri_index(k, k)) * n * n + r] = (r / n == r % n) ? R(1) : R(0);
+  }
+}
+
+// diagonal d >= 1: Phi_{k,k-d} = Phi_{k,k-d+1} Acl_{k-d}, items (b, k), k = d..N
+template <typename R>
+__global__ void __launch_bounds__(NTH) sls_level_kernel(int N, int n, int d, const R* __restrict__ Acl,
+                                                        R* Phi, long long zoff) {
+  __shared__ __align__(16) Tile<R> sm;
+  const long long z = blockIdx.z + zoff;
+  const int per = N - d + 1;
+  const long long b = z / per;
+  const int k = d + (int)(z % per), j = k - d;
+  const long long T = (long long)(N + 1) * (N + 2) / 2;
+  R* base = Phi + b * T * n * n;
+  const R* X = base + tri_index(k, j + 1) * n * n;
+  const R* Y = Acl + (b * N + j) * n * n;
+  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
+  R acc[4][4] = {};
+  tile_mma(acc, X, n, 0, R(1), Y, n, 0, n, n, n, r0, c0, sm);
+  tile_store(acc, base + tri_index(k, j) * n * n, n, (const R*)nullptr, 0, (const R*)nullptr, 0, n, n,
+             r0, c0);
+}
+
+// Phihat^y_{k,j} = Phihat^x_{k,j} L_j^T (L_j = Lg[j - 1], p x n), zero for j = 0
+template <typename R>
+__global__ void __launch_bounds__(NTH) sls_phiy_kernel(int N, int n, int p, const R* __restrict__ PX,
+                                                       const R* __restrict__ Lg, R* PY, long long zoff) {
+  __shared__ __align__(16) Tile<R> sm;
+  const long long z = blockIdx.z + zoff;
+  const long long T = (long long)(N + 1) * (N + 2) / 2;
+  const long long b = z / T, t = z % T;
+  int k, j;
+  unpack_block(t, k, j);
+  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
+  R acc[4][4] = {};
+  if (j > 0)
+    tile_mma(acc, PX + (b * T + t) * n * n, n, 0, R(1), Lg + (b * N + j - 1) * p * n, n, 1, n, p, n, r0,
+             c0, sm);
+  tile_store(acc, PY + (b * T + t) * n * p, p, (const R*)nullptr, 0, (const R*)nullptr, 0, n, p, r0, c0);
+}
+
+// (M X)_{k,j} = X_{k,j} - A_{k-1} X_{k-1,j} (j < k), X_{k,k} (j = k); M = I - Z A, X blocks n x c
+template <typename R>
+__global__ void __launch_bounds__(NTH) sls_shift_kernel(int N, int n, int c, const R* __restrict__ A,
+                                                        const R* __restrict__ X, R* out, long long zoff) {
+  __shared__ __align__(16) Tile<R> sm;
+  const long long z = blockIdx.z + zoff;
+  const long long T = (long long)(N + 1) * (N + 2) / 2;
+  const long long b = z / T, t = z % T;
+  int k, j;
+  unpack_block(t, k, j);
+  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
+  R acc[4][4] = {};
+  if (j < k)
+    tile_mma(acc, A + (b * N + k - 1) * n * n, n, 0, R(-1), X + (b * T + tri_index(k - 1, j)) * n * c, c,
+             0, n, c, n, r0, c0, sm);
+  tile_store(acc, out + (b * T + t) * n * c, c, X + (b * T + t) * n * c, c, (const R*)nullptr, 0, n, c,
+             r0, c0);
+}
+
+// out_{k,j} = alpha sum_{i=j..k} X_{k,i} Y_{i,j} (+ d1_{k,j}) (+ d2_{k,j});
+// X blocks r x n, Y blocks n x c, out / d1 / d2 blocks r x c
+template <typename R>
+__global__ void __launch_bounds__(NTH) sls_tri_kernel(int N, int r, int n, int c, R alpha,
+                                                      const R* __restrict__ X, const R* __restrict__ Y,
+                                                      const R* d1, const R* d2, R* out, long long zoff) {
+  __shared__ __align__(16) Tile<R> sm;
+  const long long z = blockIdx.z + zoff;
+  const long long T = (long long)(N + 1) * (N + 2) / 2;
+  const long long b = z / T, t = z % T;
+  int k, j;
+  unpack_block(t, k, j);
+  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
+  R acc[4][4] = {};
+  for (int i = j; i <= k; ++i)
+    tile_mma(acc, X + (b * T + tri_index(k, i)) * r * n, n, 0, alpha, Y + (b * T + tri_index(i, j)) * n * c,
+             c, 0, r, c, n, r0, c0, sm);
+  const long long o = (b * T + t) * r * c;
+  tile_store(acc, out + o, c, d1 ? d1 + o : nullptr, c, d2 ? d2 + o : nullptr, c, r, c, r0, c0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+
+constexpr long long kMaxZ = 65535;
+
+inline cs_status launched(const char* what) {
+  cs_count_launch();
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CS_OK : cs_cuda_fail(e, what);
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+inline dim3 tiles(int M, int N, long long z) {
+  return dim3((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM), (unsigned)z);
+}
+
+template <typename R>
+cs_status gemm(Gemm<R> g, long long batch, cudaStream_t st) {
+  for (long long z0 = 0; z0 < batch; z0 += kMaxZ) {
+    g.zoff = z0;
+    sls_gemm_kernel<R><<<tiles(g.M, g.N, std::min(kMaxZ, batch - z0)), NTH, 0, st>>>(g);
+    cs_status r = launched("sls_gemm_kernel");
+    if (r) return r;
+  }
+  return CS_OK;
+}
+
+template <typename R>
+Prod<R> prod(const R* a, long long sa, int lda, int ta, const R* b, long long sb, int ldb, int tb, int K,
+             R alpha = R(1)) {
+  Prod<R> P;
+  P.a = a; P.sa = sa; P.lda = lda; P.ta = ta; P.alpha = alpha;
+  P.b = b; P.sb = sb; P.ldb = ldb; P.tb = tb; P.K = K;
+  return P;
+}
+
+template <typename R>
+Gemm<R> gemm_desc(int M, int N, R* c, long long sc, int ldc) {
+  Gemm<R> g{};
+  g.M = M; g.N = N; g.np = 0; g.c = c; g.sc = sc; g.ldc = ldc; g.d = nullptr; g.sd = 0; g.ldd = 0;
+  return g;
+}
+
+// gain kernel: right-hand-side columns per pass that fit the shared-memory budget
+inline int gain_cols(int n, int p, size_t rb) {
+  const long long room = (long long)(kGainSmemBudget / rb) - (long long)p * p - p;
+  long long cw = room > 0 ? room / p : 0;
+  cw = std::min<long long>(std::min<long long>(cw, NTH), n);
+  return (int)cw;
+}
+
+inline size_t gain_smem(int p, int cw, size_t rb) { return ((size_t)p * p + p + (size_t)p * cw) * rb; }
+
+struct ObsWs {
+  size_t t1, s, w, t2, abar, total;
+};
+
+inline ObsWs observer_ws(long long B, int N, int n, int p, size_t rb) {
+  ObsWs o;
+  size_t off = 0;
+  o.t1 = off; off = align256(off + (size_t)B * n * p * rb);
+  o.s = off; off = align256(off + (size_t)B * p * p * rb);
+  o.w = off; off = align256(off + (size_t)B * n * p * rb);
+  o.t2 = off; off = align256(off + (size_t)B * n * n * rb);
+  o.abar = off; off = align256(off + (size_t)B * N * n * n * rb);
+  o.total = off;
+  return o;
+}
+
+template <typename R>
+cs_status response_levels(int B, int N, int n, const R* Acl, R* Phi, cudaStream_t st) {
+  {
+    const long long total = (long long)B * (N + 1) * n * n;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 148LL * 16);
+    sls_identity_kernel<R><<<grid, 256, 0, st>>>(B, N, n, Phi);
+    cs_status r = launched("sls_identity_kernel");
+    if (r) return r;
+  }
+  for (int d = 1; d <= N; ++d) {
+    const long long items = (long long)B * (N - d + 1);
+    for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+      sls_level_kernel<R><<<tiles(n, n, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, n, d, Acl, Phi, z0);
+      cs_status r = launched("sls_level_kernel");
+      if (r) return r;
+    }
+  }
+  return CS_OK;
+}
+
+template <typename R>
+cs_status observer(int B, int N, int n, int p, int nw, int ne, int n0, const R* A, const R* Cm,
+                   const R* E, const R* F, const R* Xi, R* Pi, R* L, R* PX, R* PY, int32_t* status,
+                   unsigned char* ws, cudaStream_t st) {
+  const ObsWs o = observer_ws(B, N, n, p, sizeof(R));
+  R* T1 = reinterpret_cast<R*>(ws + o.t1);
+  R* S = reinterpret_cast<R*>(ws + o.s);
+  R* W = reinterpret_cast<R*>(ws + o.w);
+  R* T2 = reinterpret_cast<R*>(ws + o.t2);
+  R* Abar = reinterpret_cast<R*>(ws + o.abar);
+  const long long nn = (long long)n * n, np_ = (long long)n * p, sPi = (N + 1) * nn;
+  cs_status r;
+  if (status) {
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, st);
+    if (e != cudaSuccess) return cs_cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (B == 0) return CS_OK;
+  {  // Pi_0 = Xi Xi^T
+    Gemm<R> g = gemm_desc<R>(n, n, Pi, sPi, n);
+    g.pr[g.np++] = prod<R>(Xi, (long long)n * n0, n0, 0, Xi, (long long)n * n0, n0, 1, n0);
+    if ((r = gemm(g, B, st))) return r;
+  }
+  const int cw = gain_cols(n, p, sizeof(R));
+  const size_t gsm = gain_smem(p, cw, sizeof(R));
+  {
+    cudaError_t e = cudaFuncSetAttribute(sls_gain_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gsm);
+    if (e != cudaSuccess) return cs_cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  for (int j = 0; j < N; ++j) {
+    const R* Pj = Pi + j * nn;
+    const R* Aj = A + j * nn;
+    const R* Cj = Cm + (long long)j * p * n;
+    const R* Ej = E + (long long)j * n * nw;
+    const R* Fj = F + (long long)j * p * ne;
+    const long long sA = N * nn, sC = (long long)N * p * n, sE = (long long)N * n * nw,
+                    sF = (long long)N * p * ne;
+    R* Lj = L + (long long)j * p * n;
+    {  // T1 = Pi_j C_j^T (n x p)
+      Gemm<R> g = gemm_desc<R>(n, p, T1, np_, p);
+      g.pr[g.np++] = prod<R>(Pj, sPi, n, 0, Cj, sC, n, 1, n);
+      if ((r = gemm(g, B, st))) return r;
+    }
+    {  // S = C_j T1 + F_j F_j^T (p x p)
+      Gemm<R> g = gemm_desc<R>(p, p, S, (long long)p * p, p);
+      g.pr[g.np++] = prod<R>(Cj, sC, n, 0, T1, np_, p, 0, n);
+      g.pr[g.np++] = prod<R>(Fj, sF, ne, 0, Fj, sF, ne, 1, ne);
+      if ((r = gemm(g, B, st))) return r;
+    }
+    {  // W = A_j T1 = A_j Pi_j C_j^T (n x p)
+      Gemm<R> g = gemm_desc<R>(n, p, W, np_, p);
+      g.pr[g.np++] = prod<R>(Aj, sA, n, 0, T1, np_, p, 0, n);
+      if ((r = gemm(g, B, st))) return r;
+    }
+    {  // T2 = A_j Pi_j (n x n)
+      Gemm<R> g = gemm_desc<R>(n, n, T2, nn, n);
+      g.pr[g.np++] = prod<R>(Aj, sA, n, 0, Pj, sPi, n, 0, n);
+      if ((r = gemm(g, B, st))) return r;
+    }
+    // L_{j+1} = -S^{-1} W^T (p x n)
+    sls_gain_kernel<R><<<B, NTH, gsm, st>>>(p, n, cw, S, W, Lj, (long long)N * p * n, status);
+    if ((r = launched("sls_gain_kernel"))) return r;
+    {  // Pi_{j+1} = T2 A_j^T + E_j E_j^T + W L_{j+1}
+      Gemm<R> g = gemm_desc<R>(n, n, Pi + (j + 1) * nn, sPi, n);
+      g.pr[g.np++] = prod<R>(T2, nn, n, 0, Aj, sA, n, 1, n);
+      g.pr[g.np++] = prod<R>(Ej, sE, nw, 0, Ej, sE, nw, 1, nw);
+      g.pr[g.np++] = prod<R>(W, np_, p, 0, Lj, (long long)N * p * n, n, 0, p);
+      if ((r = gemm(g, B, st))) return r;
+    }
+  }
+  {  // Abar_j = A_j + L_{j+1}^T C_j for every (trajectory, step)
+    Gemm<R> g = gemm_desc<R>(n, n, Abar, nn, n);
+    g.pr[g.np++] = prod<R>(L, (long long)p * n, n, 1, Cm, (long long)p * n, n, 0, p);
+    g.d = A; g.sd = nn; g.ldd = n;
+    if ((r = gemm(g, (long long)B * N, st))) return r;
+  }
+  if ((r = response_levels<R>(B, N, n, Abar, PX, st))) return r;
+  const long long T = (long long)(N + 1) * (N + 2) / 2, items = (long long)B * T;
+  for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+    sls_phiy_kernel<R><<<tiles(n, p, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, n, p, PX, L, PY, z0);
+    if ((r = launched("sls_phiy_kernel"))) return r;
+  }
+  return CS_OK;
+}
+
+template <typename R>
+cs_status closed_loop(int B, int N, int n, int m, int p, const R* A, const R* PBX, const R* PBU,
+                      const R* PX, const R* PY, R* XW, R* UW, R* XE, R* UE, unsigned char* ws,
+                      cudaStream_t st) {
+  const long long T = (long long)(N + 1) * (N + 2) / 2, items = (long long)B * T;
+  R* MX = reinterpret_cast<R*>(ws);
+  R* MY = reinterpret_cast<R*>(ws + align256((size_t)B * T * n * n * sizeof(R)));
+  cs_status r;
+  for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+    const long long zc = std::min(kMaxZ, items - z0);
+    sls_shift_kernel<R><<<tiles(n, n, zc), NTH, 0, st>>>(N, n, n, A, PX, MX, z0);
+    if ((r = launched("sls_shift_kernel"))) return r;
+    sls_shift_kernel<R><<<tiles(n, p, zc), NTH, 0, st>>>(N, n, p, A, PY, MY, z0);
+    if ((r = launched("sls_shift_kernel"))) return r;
+  }
+  for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+    const long long zc = std::min(kMaxZ, items - z0);
+    // Phi^xw = Phibar^x + Phihat^x - Phibar^x (M Phihat^x)
+    sls_tri_kernel<R><<<tiles(n, n, zc), NTH, 0, st>>>(N, n, n, n, R(-1), PBX, MX, PBX, PX, XW, z0);
+    if ((r = launched("sls_tri_kernel"))) return r;
+    // Phi^uw = Phibar^u - Phibar^u (M Phihat^x)
+    sls_tri_kernel<R><<<tiles(m, n, zc), NTH, 0, st>>>(N, m, n, n, R(-1), PBU, MX, PBU, nullptr, UW, z0);
+    if ((r = launched("sls_tri_kernel"))) return r;
+    // Phi^xe = Phihat^y - Phibar^x (M Phihat^y)
+    sls_tri_kernel<R><<<tiles(n, p, zc), NTH, 0, st>>>(N, n, n, p, R(-1), PBX, MY, PY, nullptr, XE, z0);
+    if ((r = launched("sls_tri_kernel"))) return r;
+    // Phi^ue = -Phibar^u (M Phihat^y)
+    sls_tri_kernel<R><<<tiles(m, p, zc), NTH, 0, st>>>(N, m, n, p, R(-1), PBU, MY, nullptr, nullptr, UE, z0);
+    if ((r = launched("sls_tri_kernel"))) return r;
+  }
+  return CS_OK;
+}
+
+cs_status check_sizes(int B, int N, int n, int real_bytes) {
+  if (B < 0) return cs_fail(CS_ERR_INVALID_ARG, "B must be >= 0");
+  if (N < 1 || n < 1) return cs_fail(CS_ERR_INVALID_ARG, "N and n must be >= 1");
+  if (real_bytes != 4 && real_bytes != 8) return cs_fail(CS_ERR_INVALID_ARG, "real_bytes must be 4 or 8");
+  if (N > 4096 || n > 4096) return cs_fail(CS_ERR_INVALID_ARG, "N and n must be <= 4096");
+  return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sls_observer_workspace(int B, int N, int n, int p, int real_bytes) {
+  if (B < 0 || N < 1 || n < 1 || p < 1 || (real_bytes != 4 && real_bytes != 8)) return 0;
+  return observer_ws(B, N, n, p, (size_t)real_bytes).total;
+}
+
+cs_status sls_observer(int B, int N, int n, int p, int nw, int ne, int n0, int real_bytes, const void* A,
+                       const void* C, const void* E, const void* F, const void* Xi, void* Pi, void* L,
+                       void* PhiX, void* PhiY, int32_t* status, void* workspace, size_t workspace_bytes,
+                       void* stream) {
+  cs_status r = check_sizes(B, N, n, real_bytes);
+  if (r) return r;
+  if (p < 1 || nw < 1 || ne < 1 || n0 < 1 || p > 4096 || nw > 4096 || ne > 4096 || n0 > 4096)
+    return cs_fail(CS_ERR_INVALID_ARG, "p, nw, ne and n0 must be in [1, 4096]");
+  if (gain_cols(n, p, (size_t)real_bytes) < 1)
+    return cs_fail(CS_ERR_INVALID_ARG, "p too large for the gain kernel's shared memory");
+  if (B > 0 && (!A || !C || !E || !F || !Xi || !Pi || !L || !PhiX || !PhiY || !workspace))
+    return cs_fail(CS_ERR_INVALID_ARG, "null pointer");
+  if (workspace_bytes < sls_observer_workspace(B, N, n, p, real_bytes))
+    return cs_fail(CS_ERR_INVALID_ARG, "workspace smaller than sls_observer_workspace()");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* ws = (unsigned char*)workspace;
+  if (real_bytes == 4)
+    return observer<float>(B, N, n, p, nw, ne, n0, (const float*)A, (const float*)C, (const float*)E,
+                           (const float*)F, (const float*)Xi, (float*)Pi, (float*)L, (float*)PhiX,
+                           (float*)PhiY, status, ws, st);
+  return observer<double>(B, N, n, p, nw, ne, n0, (const double*)A, (const double*)C, (const double*)E,
+                          (const double*)F, (const double*)Xi, (double*)Pi, (double*)L, (double*)PhiX,
+                          (double*)PhiY, status, ws, st);
+}
+
+cs_status sls_response(int B, int N, int n, int real_bytes, const void* Acl, void* Phi, void* stream) {
+  cs_status r = check_sizes(B, N, n, real_bytes);
+  if (r) return r;
+  if (B > 0 && (!Acl || !Phi)) return cs_fail(CS_ERR_INVALID_ARG, "null pointer");
+  if (B == 0) return CS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (real_bytes == 4) return response_levels<float>(B, N, n, (const float*)Acl, (float*)Phi, st);
+  return response_levels<double>(B, N, n, (const double*)Acl, (double*)Phi, st);
+}
+
+size_t sls_closed_loop_workspace(int B, int N, int n, int p, int real_bytes) {
+  if (B < 0 || N < 1 || n < 1 || p < 1 || (real_bytes != 4 && real_bytes != 8)) return 0;
+  const size_t T = (size_t)(N + 1) * (N + 2) / 2;
+  return align256((size_t)B * T * n * n * real_bytes) + align256((size_t)B * T * n * p * real_bytes);
+}
+
+cs_status sls_closed_loop(int B, int N, int n, int m, int p, int real_bytes, const void* A,
+                          const void* PhiBarX, const void* PhiBarU, const void* PhiX, const void* PhiY,
+                          void* PhiXW, void* PhiUW, void* PhiXE, void* PhiUE, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  cs_status r = check_sizes(B, N, n, real_bytes);
+  if (r) return r;
+  if (m < 1 || p < 1 || m > 4096 || p > 4096) return cs_fail(CS_ERR_INVALID_ARG, "m and p must be in [1, 4096]");
+  if (B > 0 && (!A || !PhiBarX || !PhiBarU || !PhiX || !PhiY || !PhiXW || !PhiUW || !PhiXE || !PhiUE ||
+                !workspace))
+    return cs_fail(CS_ERR_INVALID_ARG, "null pointer");
+  if (workspace_bytes < sls_closed_loop_workspace(B, N, n, p, real_bytes))
+    return cs_fail(CS_ERR_INVALID_ARG, "workspace smaller than sls_closed_loop_workspace()");
+  if (B == 0) return CS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* ws = (unsigned char*)workspace;
+  if (real_bytes == 4)
+    return closed_loop<float>(B, N, n, m, p, (const float*)A, (const float*)PhiBarX, (const float*)PhiBarU,
+                              (const float*)PhiX, (const float*)PhiY, (float*)PhiXW, (float*)PhiUW,
+                              (float*)PhiXE, (float*)PhiUE, ws, st);
+  return closed_loop<double>(B, N, n, m, p, (const double*)A, (const double*)PhiBarX,
+                             (const double*)PhiBarU, (const double*)PhiX, (const double*)PhiY,
+                             (double*)PhiXW, (double*)PhiUW, (double*)PhiXE, (double*)PhiUE, ws, st);
+}
+
+}  // extern "C"

@@ -119,3 +119,34 @@ def cloth_rollout_vjp_flops_per_node_step(counts: dict, p: int, spn: float, nobs
         resolve = cloth_newton_iter_per_node(p, spn)
     back = resolve + band_factor_per_node(p) + 2 * band_solve_per_node(p) + spn * 30 + nobs * 70 + 12
     return fwd + fwd * (k - 1) / k + back
+
+
+# ------------------------------------------------------------------------------------------
+# output-feedback SLS observer stage (Sec. 4.2): dense products of the formulas as written,
+# 2 r c k flops for an (r x k)(k x c) product; a Cholesky factorisation of a p x p matrix p^3 / 3,
+# its two triangular solves with c right-hand sides 2 p^2 c
+# ------------------------------------------------------------------------------------------
+
+def _mm(r, c, k):
+    return 2.0 * r * c * k
+
+
+def sls_observer_flops(N: int, n: int, p: int, nw: int, ne: int, n0: int) -> float:
+    """One trajectory of sls_observer: eq. kalman_recursions step by step (Pi C^T, C Pi C^T,
+    F F^T, A Pi C^T, A Pi A^T, E E^T, the gain solve, A Pi C^T L), the closed-loop matrices
+    A + L^T C, the N (N + 1) / 2 products of eq. backward_propagations and Phihat^y = Phihat^x L^T."""
+    per_step = (_mm(n, p, n) + _mm(p, p, n) + _mm(p, p, ne) + _mm(n, p, n) + 2 * _mm(n, n, n)
+                + _mm(n, n, nw) + p ** 3 / 3.0 + 2.0 * p * p * n + _mm(n, n, p) + _mm(n, n, p))
+    tri = N * (N + 1) / 2.0
+    return _mm(n, n, n0) + N * per_step + tri * _mm(n, n, n) + tri * _mm(n, p, n)
+
+
+def sls_closed_loop_flops(N: int, n: int, m: int, p: int) -> float:
+    """One trajectory of sls_closed_loop: M Phihat^x and M Phihat^y (one block product per block
+    below the diagonal), then the block lower-triangular products Phibar^x (M Phihat^x),
+    Phibar^u (M Phihat^x), Phibar^x (M Phihat^y), Phibar^u (M Phihat^y), block (k, j) summing
+    k - j + 1 block products."""
+    tri = N * (N + 1) / 2.0
+    s3 = sum((N + 1 - d) * (d + 1) for d in range(N + 1))
+    return (tri * (_mm(n, n, n) + _mm(n, p, n))
+            + s3 * (_mm(n, n, n) + _mm(m, n, n) + _mm(n, p, n) + _mm(m, p, n)))

@@ -270,3 +270,58 @@ def workload(i: int, B: int | None = None, H: int | None = None, shard: int = 0)
         # metre scale, at 1e-5 (10 um of slack at 1 N, under the FP32 state tolerance) they are not
         sc["params"]["kappa_hard"] = 1.0e-5
     return dict(scene=sc, B=B, H=H, U=U, q0=batch_q0(sc, B), real_bytes=real, seed=seed)
+
+
+# ------------------------------------------------------------------------------------------
+# output-feedback SLS stage inputs (Sec. 4.2)
+# ------------------------------------------------------------------------------------------
+
+def sls_observation_model(B: int, H: int, nv: int, seed: int = BASE_SEED + 500,
+                          sigma_w: float = 0.005, sigma_e: float = 0.01, sigma_0: float = 0.02,
+                          jitter: float = 0.05) -> dict:
+    """Seeded observation model and disturbance scalings about B nominal rope trajectories of H
+    steps (state q = [x, g], n = 3 nv + 6), the inputs of the observer stage besides A_t:
+      C  [B][H][3 nv][n]  the node positions (what the vision front end measures), each entry
+                          perturbed by N(0, jitter^2) (a perception model linearised along the
+                          trajectory differs from step to step);
+      E  [B][H][n][n]     diagonal process-disturbance scaling: sigma_w per node coordinate,
+                          sigma_w / 10 on the gripper coordinates, each times U[0.5, 1.5];
+      F  [B][H][3 nv][3 nv]  diagonal observation-noise scaling sigma_e U[0.5, 1.5];
+      Xi [B][n][n]        diagonal initial uncertainty sigma_0 U[0.5, 1.5]."""
+    rng = np.random.default_rng(seed)
+    n, p = 3 * nv + 6, 3 * nv
+    C = np.zeros((B, H, p, n))
+    C[:, :, np.arange(p), np.arange(p)] = 1.0
+    C += jitter * rng.normal(size=C.shape)
+    ew = np.full(n, sigma_w)
+    ew[3 * nv:] = sigma_w / 10
+    E = np.zeros((B, H, n, n))
+    E[:, :, np.arange(n), np.arange(n)] = ew * rng.uniform(0.5, 1.5, size=(B, H, n))
+    F = np.zeros((B, H, p, p))
+    F[:, :, np.arange(p), np.arange(p)] = sigma_e * rng.uniform(0.5, 1.5, size=(B, H, p))
+    Xi = np.zeros((B, n, n))
+    Xi[:, np.arange(n), np.arange(n)] = sigma_0 * rng.uniform(0.5, 1.5, size=(B, n))
+    return dict(C=C, E=E, F=F, Xi=Xi)
+
+
+def sls_random_system(B: int, N: int, n: int, p: int, nw: int, ne: int, n0: int,
+                      seed: int = BASE_SEED + 501, rho: float = 0.9) -> dict:
+    """Seeded dense time-varying systems of any size (every matrix differs at every step):
+    A_j = rho Q_j + 0.1 G_j / sqrt(n) (Q_j orthogonal, G_j Gaussian), C_j, E_j, F_j, Xi Gaussian
+    with F_j = 0.3 [I 0] + 0.1 G so that F_j F_j^T is positive definite."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.normal(size=(B, N, n, n)))
+    A = rho * Q + 0.1 * rng.normal(size=(B, N, n, n)) / np.sqrt(n)
+    C = rng.normal(size=(B, N, p, n)) / np.sqrt(n)
+    E = 0.3 * rng.normal(size=(B, N, n, nw)) / np.sqrt(nw)
+    F = 0.3 * np.eye(p, ne)[None, None] + 0.1 * rng.normal(size=(B, N, p, ne)) / np.sqrt(ne)
+    Xi = 0.5 * rng.normal(size=(B, n, n0)) / np.sqrt(n0)
+    return dict(A=A, C=C, E=E, F=F, Xi=Xi)
+
+
+def sls_feedback_gains(B: int, N: int, m: int, n: int, scale: float = 0.05,
+                       seed: int = BASE_SEED + 502) -> np.ndarray:
+    """Seeded state-feedback gains K_k [B][N+1][m][n] ~ N(0, (scale / sqrt(n))^2): the input from
+    which the tests and the benchmark form the state-feedback responses Phibar."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.normal(size=(B, N + 1, m, n)) / np.sqrt(n)

@@ -163,3 +163,33 @@ def test_noalloc_argument_errors_without_gpu():
               bad(newton_max=0), bad(ipm_max=0), bad(kappa_decay=1.0), bad(kappa_hard=1.0),
               bad(real_bytes=2), bad(n_nodes=129), bad(checkpoint_every=0)):
         assert call(P, make_loss(sc)) == 1, lib.cs_last_error()
+
+
+def test_sls_argument_errors_without_gpu():
+    """The SLS observer-stage calls check sizes, pointers and the workspace before any device call
+    (the device pointers below are never dereferenced); an empty batch without a status array
+    makes no device call at all."""
+    lib = L.lib()
+    f = C.c_void_p(256)
+    ws = lib.sls_observer_workspace(2, 3, 10, 4, 4)
+    assert ws > 0 and lib.sls_observer_workspace(2, 3, 0, 4, 4) == 0
+
+    def obs(B=2, N=3, n=10, p=4, rb=4, ptr=f, wsb=ws):
+        return lib.sls_observer(B, N, n, p, n, p, n, rb, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr, ptr,
+                                None, ptr, wsb, None)
+
+    assert obs(n=0) == 1
+    assert obs(N=0) == 1
+    assert obs(B=-1) == 1
+    assert obs(rb=2) == 1
+    assert obs(p=400) == 1 and b"shared memory" in lib.cs_last_error()
+    assert obs(ptr=None) == 1 and b"null" in lib.cs_last_error()
+    assert obs(wsb=ws - 1) == 1 and b"workspace" in lib.cs_last_error()
+    assert obs(B=0, ptr=None, wsb=0) == 0
+    assert lib.sls_response(1, 3, 0, 4, f, f, None) == 1
+    assert lib.sls_response(1, 3, 4, 4, None, f, None) == 1
+    cw = lib.sls_closed_loop_workspace(2, 3, 10, 4, 8)
+    assert cw > 0
+    assert lib.sls_closed_loop(2, 3, 10, 0, 4, 8, *([f] * 9), f, cw, None) == 1
+    assert lib.sls_closed_loop(2, 3, 10, 6, 4, 8, *([f] * 9), f, cw - 1, None) == 1
+    assert lib.sls_closed_loop(0, 3, 10, 6, 4, 8, *([None] * 9), None, 0, None) == 0
