@@ -328,7 +328,7 @@ size_t sls_observer_workspace(int B, int N, int n, int p, int real_bytes);
  *                        NULL)
  * The gain computed from (Pi_j, A_j, C_j) carries the label j+1 and is the one the propagation
  * through A_j uses; Pi and L are the same for every injection time k.  p is limited by the gain
- * solve's shared memory (p^2 + 2p reals within 200 KB: p <= 225 in FP32, 159 in FP64). */
+ * solve's shared memory (p^2 + 10 p reals within 200 KB: p <= 221 in FP32, 155 in FP64). */
 cs_status sls_observer(int B, int N, int n, int p, int nw, int ne, int n0, int real_bytes,
                        const void* A, const void* C, const void* E, const void* F, const void* Xi,
                        void* Pi, void* L, void* PhiX, void* PhiY, int32_t* status,

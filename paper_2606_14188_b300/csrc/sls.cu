@@ -4,14 +4,18 @@
 // trajectories.
 //
 // Every stage is a batch of dense products of small matrices (n, p ~ 100-250), computed by one
-// tile routine: a 64 x 64 output tile per 256-thread CTA, 4 x 4 outputs per thread, the operand
-// panels staged through shared memory 16 deep.  The trajectories, the blocks of a block-triangular
+// tile routine on 256-thread CTAs: in FP32 a 128 x 128 output tile, 8 x 8 outputs per thread
+// (two 4 x 4 quads 64 apart, so that a quarter warp's vector reads of a panel row are contiguous);
+// in FP64 64 x 64, 4 x 4 per thread; for products with few rows (the m = 6 control rows)
+// 16 x 128, 1 x 8 per thread.  The operand panels are staged through shared memory 16 deep, the
+// next panel's global loads issued before the current panel's products.  The trajectories, the blocks of a block-triangular
 // operator and the output tiles are the grid; the horizon is the sequential direction:
 //   Kalman   per step j, five batched products and one gain solve (a CTA per trajectory:
 //            Cholesky factor of the innovation matrix in shared memory, a thread per gain column);
 //   Phihat^x one launch per block diagonal d = k - j: Phihat^x_{k,j} = Phihat^x_{k,j+1} Abar_j for
 //            all (trajectory, k) at once, the products the paper's propagation forms, in N launches;
-//   assembly block lower-triangular products sum_i X_{k,i} Y_{i,j}, a CTA per output block tile.
+//   assembly block lower-triangular products sum_i X_{k,i} Y_{i,j}, a CTA per output block tile
+//            (blocks of at most 8 rows: split over the warps along K instead).
 // The paper forms the horizon direction by associative scans to reach logarithmic depth for one
 // trajectory; with hundreds of trajectories in one call the batch already fills the GPU, and the
 // step-by-step recursion does several times fewer flops than a scan over the same elements.
@@ -33,75 +37,118 @@ void cs_count_launch();
 
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 16, NTH = 256, PADS = 4;
+constexpr int TK = 16, NTH = 256, PADS = 4;
 constexpr size_t kGainSmemBudget = 200 * 1024;   // shared memory of the gain kernel
 
-template <typename R>
+// tile geometries: BM x BN outputs per CTA, RM x RN per thread (16 x 16 threads)
+struct GBig { static constexpr int BM = 128, BN = 128, RM = 8, RN = 8; };
+struct GMid { static constexpr int BM = 64, BN = 64, RM = 4, RN = 4; };
+struct GShort { static constexpr int BM = 16, BN = 128, RM = 1, RN = 8; };
+
+template <typename R, class G>
 struct Tile {
-  R a[TK][TM + PADS];   // op(A) panel, k-major
-  R b[TK][TN + PADS];   // op(B) panel, k-major
+  R a[TK][G::BM + PADS];   // op(A) panel, k-major
+  R b[TK][G::BN + PADS];   // op(B) panel, k-major
 };
 
-// acc += alpha op(A)[r0.., 0..K) op(B)[0..K, c0..] for this thread's 4 x 4 outputs (rows
-// r0 + 4 ty + u, columns c0 + 4 tx + v).  op(X)(i, k) = X[i ld + k] (t = 0) or X[k ld + i]
-// (t = 1); entries outside M x K and K x N read as zero.
-template <typename R>
-__device__ __forceinline__ void tile_mma(R (&acc)[4][4], const R* __restrict__ ap, int lda, int ta,
-                                         R alpha, const R* __restrict__ bp, int ldb, int tb, int M,
-                                         int N, int K, int r0, int c0, Tile<R>& sm) {
+// the tile row of this thread's r-th output row (quads of 4 rows, BM / (RM / 4) apart), likewise
+// for columns
+template <class G>
+__device__ __forceinline__ int row_of(int ty, int r) {
+  if constexpr (G::RM >= 4) return (r >> 2) * (G::BM / (G::RM / 4)) + 4 * ty + (r & 3);
+  else return ty * G::RM + r;
+}
+template <class G>
+__device__ __forceinline__ int col_of(int tx, int c) {
+  if constexpr (G::RN >= 4) return (c >> 2) * (G::BN / (G::RN / 4)) + 4 * tx + (c & 3);
+  else return tx * G::RN + c;
+}
+
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// acc += alpha op(A)[r0.., 0..K) op(B)[0..K, c0..] for this thread's outputs.  op(X)(i, k) =
+// X[i ld + k] (t = 0) or X[k ld + i] (t = 1); entries outside M x K and K x N read as zero.
+template <typename R, class G>
+__device__ __forceinline__ void tile_mma(R (&acc)[G::RM][G::RN], const R* __restrict__ ap, int lda,
+                                         int ta, R alpha, const R* __restrict__ bp, int ldb, int tb,
+                                         int M, int N, int K, int r0, int c0, Tile<R, G>& sm) {
+  constexpr int LA = G::BM * TK / NTH, LB = TK * G::BN / NTH;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int k0 = 0; k0 < K; k0 += TK) {
+  R ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
 #pragma unroll
-    for (int s = 0; s < TM * TK / NTH; ++s) {
+    for (int s = 0; s < LA; ++s) {
       const int e = tid + s * NTH;
       int i, k;
-      if (ta) { i = e % TM; k = e / TM; } else { k = e % TK; i = e / TK; }
+      if (ta) { i = e % G::BM; k = e / G::BM; } else { k = e % TK; i = e / TK; }
       const int gi = r0 + i, gk = k0 + k;
-      R v = R(0);
-      if (gi < M && gk < K) v = alpha * (ta ? ap[(size_t)gk * lda + gi] : ap[(size_t)gi * lda + gk]);
-      sm.a[k][i] = v;
+      ra[s] = (gi < M && gk < K) ? alpha * (ta ? ap[(size_t)gk * lda + gi] : ap[(size_t)gi * lda + gk])
+                                 : R(0);
     }
 #pragma unroll
-    for (int s = 0; s < TK * TN / NTH; ++s) {
+    for (int s = 0; s < LB; ++s) {
       const int e = tid + s * NTH;
       int k, j;
-      if (tb) { k = e % TK; j = e / TK; } else { j = e % TN; k = e / TN; }
+      if (tb) { k = e % TK; j = e / TK; } else { j = e % G::BN; k = e / G::BN; }
       const int gk = k0 + k, gj = c0 + j;
-      R v = R(0);
-      if (gk < K && gj < N) v = tb ? bp[(size_t)gj * ldb + gk] : bp[(size_t)gk * ldb + gj];
-      sm.b[k][j] = v;
+      rb[s] = (gk < K && gj < N) ? (tb ? bp[(size_t)gj * ldb + gk] : bp[(size_t)gk * ldb + gj]) : R(0);
+    }
+  };
+  fetch(0);
+  for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+    for (int s = 0; s < LA; ++s) {
+      const int e = tid + s * NTH;
+      if (ta) sm.a[e / G::BM][e % G::BM] = ra[s]; else sm.a[e % TK][e / TK] = ra[s];
+    }
+#pragma unroll
+    for (int s = 0; s < LB; ++s) {
+      const int e = tid + s * NTH;
+      if (tb) sm.b[e % TK][e / TK] = rb[s]; else sm.b[e / G::BN][e % G::BN] = rb[s];
     }
     __syncthreads();
+    if (k0 + TK < K) fetch(k0 + TK);
 #pragma unroll
     for (int kk = 0; kk < TK; ++kk) {
-      R av[4], bv[4];
+      R av[G::RM], bv[G::RN];
+      if constexpr (G::RM >= 4) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        av[u] = sm.a[kk][4 * ty + u];
-        bv[u] = sm.b[kk][4 * tx + u];
+        for (int q = 0; q < G::RM / 4; ++q) ld4(&sm.a[kk][row_of<G>(ty, 4 * q)], av + 4 * q);
+      } else {
+#pragma unroll
+        for (int r = 0; r < G::RM; ++r) av[r] = sm.a[kk][row_of<G>(ty, r)];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int q = 0; q < G::RN / 4; ++q) ld4(&sm.b[kk][col_of<G>(tx, 4 * q)], bv + 4 * q);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+      for (int r = 0; r < G::RM; ++r)
+#pragma unroll
+        for (int c = 0; c < G::RN; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
     }
     __syncthreads();
   }
 }
 
 // out = acc (+ d1) (+ d2) on the tile, within M x N (all three row-major with their own ld)
-template <typename R>
-__device__ __forceinline__ void tile_store(const R (&acc)[4][4], R* __restrict__ out, int ldo,
+template <typename R, class G>
+__device__ __forceinline__ void tile_store(const R (&acc)[G::RM][G::RN], R* __restrict__ out, int ldo,
                                            const R* d1, int ld1, const R* d2, int ld2, int M, int N,
                                            int r0, int c0) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int i = r0 + 4 * ty + u;
+  for (int u = 0; u < G::RM; ++u) {
+    const int i = r0 + row_of<G>(ty, u);
     if (i >= M) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int j = c0 + 4 * tx + v;
+    for (int v = 0; v < G::RN; ++v) {
+      const int j = c0 + col_of<G>(tx, v);
       if (j >= N) continue;
       R x = acc[u][v];
       if (d1) x += d1[(size_t)i * ld1 + j];
@@ -150,18 +197,18 @@ struct Gemm {
   long long zoff;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(NTH) sls_gemm_kernel(Gemm<R> g) {
-  __shared__ __align__(16) Tile<R> sm;
+template <typename R, class G>
+__global__ void __launch_bounds__(NTH, 2) sls_gemm_kernel(Gemm<R> g) {
+  __shared__ __align__(16) Tile<R, G> sm;
   const long long z = blockIdx.z + g.zoff;
-  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
-  R acc[4][4] = {};
+  const int r0 = blockIdx.y * G::BM, c0 = blockIdx.x * G::BN;
+  R acc[G::RM][G::RN] = {};
   for (int q = 0; q < g.np; ++q) {
     const Prod<R> P = g.pr[q];
-    tile_mma(acc, P.a + z * P.sa, P.lda, P.ta, P.alpha, P.b + z * P.sb, P.ldb, P.tb, g.M, g.N, P.K,
+    tile_mma<R, G>(acc, P.a + z * P.sa, P.lda, P.ta, P.alpha, P.b + z * P.sb, P.ldb, P.tb, g.M, g.N, P.K,
              r0, c0, sm);
   }
-  tile_store(acc, g.c + z * g.sc, g.ldc, g.d ? g.d + z * g.sd : nullptr, g.ldd, (const R*)nullptr,
+  tile_store<R, G>(acc, g.c + z * g.sc, g.ldc, g.d ? g.d + z * g.sd : nullptr, g.ldd, (const R*)nullptr,
              0, g.M, g.N, r0, c0);
 }
 
@@ -170,7 +217,9 @@ __global__ void __launch_bounds__(NTH) sls_gemm_kernel(Gemm<R> g) {
 //   L = -S^{-1} W^T,  S = F F^T + C Pi C^T  (p x p, SPD),  W = A Pi C^T  (n x p)
 // S is factorised S = G G^T in shared memory, right-looking, one barrier per column: phase c
 // subtracts column c's outer product (scaled by 1/S_cc) from the trailing block and scales column
-// c - 1 into G; then each thread solves G G^T x = w for one column of W^T.
+// c - 1 into G; then four threads solve G G^T x = w for each column of W^T.  Up to 64 columns
+// per pass keep a 120-wide innovation matrix and its right-hand sides within 93 KB (FP32), two
+// CTAs per SM.
 // ---------------------------------------------------------------------------------------------
 
 template <typename R>
@@ -180,7 +229,7 @@ __global__ void __launch_bounds__(NTH) sls_gain_kernel(int p, int n, int cw, con
   extern __shared__ __align__(16) unsigned char sls_smem[];
   R* s = reinterpret_cast<R*>(sls_smem);   // p x p, row stride p
   R* dg = s + (size_t)p * p;               // p pivots S_cc
-  R* x = dg + p;                           // p x cw right-hand sides, row stride cw
+  R* x = dg + p;                           // p x cw right-hand sides, row stride cw + 8
   __shared__ int bad;
   const int b = blockIdx.x, tid = threadIdx.x;
   const R* Sb = S + (size_t)b * p * p;
@@ -195,10 +244,10 @@ __global__ void __launch_bounds__(NTH) sls_gain_kernel(int p, int n, int cw, con
     }
     if (tid == 0) dg[c] = d;
     const R rd = R(1) / d;
-    const int m = p - c - 1;
-    for (int e = tid; e < m * m; e += NTH) {
-      const int i = c + 1 + e / m, j = c + 1 + e % m;
-      if (j <= i) s[(size_t)i * p + j] -= s[(size_t)i * p + c] * s[(size_t)j * p + c] * rd;
+    // trailing update of the lower triangle: rows c+1+(tid/16)+16r, columns c+1+(tid%16)+16q <= row
+    for (int i = c + 1 + (tid >> 4); i < p; i += 16) {
+      const R lic = s[(size_t)i * p + c] * rd;
+      for (int j = c + 1 + (tid & 15); j <= i; j += 16) s[(size_t)i * p + j] -= lic * s[(size_t)j * p + c];
     }
     if (c > 0) {
       const R rs = R(1) / sqrt(dg[c - 1]);
@@ -209,48 +258,45 @@ __global__ void __launch_bounds__(NTH) sls_gain_kernel(int p, int n, int cw, con
   for (int c = tid; c < p; c += NTH) s[(size_t)c * p + c] = sqrt(dg[c]);
   __syncthreads();
 
+  // the right-hand sides, cw columns per pass, four threads per column: thread part q sums the
+  // terms k = q mod 4 of each row's dot product and the four partial sums meet by shuffles; every
+  // x_k is written and read by the one thread with q = k mod 4 (row stride cw + 8: the four parts
+  // and eight columns of a warp fall in distinct banks)
+  const int xs = cw + 8;
   const R* Wb = W + (size_t)b * n * p;
   R* Lb = L + (size_t)b * sL;
   const R nan = R(NAN);
+  const int col = tid >> 2, part = tid & 3;
   for (int c0 = 0; c0 < n; c0 += cw) {
     const int cn = min(cw, n - c0);
     for (int e = tid; e < p * cn; e += NTH) {
       const int i = e / cn, t = e % cn;
-      x[(size_t)i * cw + t] = Wb[(size_t)(c0 + t) * p + i];
+      x[(size_t)i * xs + t] = Wb[(size_t)(c0 + t) * p + i];
     }
     __syncthreads();
-    if (tid < cn) {
-      R* xc = x + tid;
-      for (int i = 0; i < p; ++i) {          // G y = w
-        const R* gi = s + (size_t)i * p;
-        R a0 = xc[(size_t)i * cw], a1 = 0, a2 = 0, a3 = 0;
-        int k = 0;
-        for (; k + 4 <= i; k += 4) {
-          a0 -= gi[k] * xc[(size_t)k * cw];
-          a1 -= gi[k + 1] * xc[(size_t)(k + 1) * cw];
-          a2 -= gi[k + 2] * xc[(size_t)(k + 2) * cw];
-          a3 -= gi[k + 3] * xc[(size_t)(k + 3) * cw];
-        }
-        for (; k < i; ++k) a0 -= gi[k] * xc[(size_t)k * cw];
-        xc[(size_t)i * cw] = ((a0 + a1) + (a2 + a3)) / gi[i];
-      }
-      for (int i = p - 1; i >= 0; --i) {     // G^T z = y
-        R a0 = xc[(size_t)i * cw], a1 = 0, a2 = 0, a3 = 0;
-        int k = i + 1;
-        for (; k + 4 <= p; k += 4) {
-          a0 -= s[(size_t)k * p + i] * xc[(size_t)k * cw];
-          a1 -= s[(size_t)(k + 1) * p + i] * xc[(size_t)(k + 1) * cw];
-          a2 -= s[(size_t)(k + 2) * p + i] * xc[(size_t)(k + 2) * cw];
-          a3 -= s[(size_t)(k + 3) * p + i] * xc[(size_t)(k + 3) * cw];
-        }
-        for (; k < p; ++k) a0 -= s[(size_t)k * p + i] * xc[(size_t)k * cw];
-        xc[(size_t)i * cw] = ((a0 + a1) + (a2 + a3)) / s[(size_t)i * p + i];
-      }
+    const bool act = col < cn;
+    R* xc = x + col;
+    for (int i = 0; i < p; ++i) {            // G y = w
+      const R* gi = s + (size_t)i * p;
+      R a = R(0);
+      if (act)
+        for (int k = part; k < i; k += 4) a -= gi[k] * xc[(size_t)k * xs];
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      a += __shfl_xor_sync(0xffffffffu, a, 2);
+      if (act && part == (i & 3)) xc[(size_t)i * xs] = (xc[(size_t)i * xs] + a) / gi[i];
+    }
+    for (int i = p - 1; i >= 0; --i) {       // G^T z = y
+      R a = R(0);
+      if (act)
+        for (int k = i + 1 + ((part - i - 1) & 3); k < p; k += 4) a -= s[(size_t)k * p + i] * xc[(size_t)k * xs];
+      a += __shfl_xor_sync(0xffffffffu, a, 1);
+      a += __shfl_xor_sync(0xffffffffu, a, 2);
+      if (act && part == (i & 3)) xc[(size_t)i * xs] = (xc[(size_t)i * xs] + a) / s[(size_t)i * p + i];
     }
     __syncthreads();
     for (int e = tid; e < p * cn; e += NTH) {
       const int i = e / cn, t = e % cn;
-      Lb[(size_t)i * n + c0 + t] = bad ? nan : -x[(size_t)i * cw + t];
+      Lb[(size_t)i * n + c0 + t] = bad ? nan : -x[(size_t)i * xs + t];
     }
     __syncthreads();
   }
@@ -277,10 +323,10 @@ __global__ void sls_identity_kernel(long long nb, int N, int n, R* Phi) {
 }
 
 // diagonal d >= 1: Phi_{k,k-d} = Phi_{k,k-d+1} Acl_{k-d}, items (b, k), k = d..N
-template <typename R>
-__global__ void __launch_bounds__(NTH) sls_level_kernel(int N, int n, int d, const R* __restrict__ Acl,
+template <typename R, class G>
+__global__ void __launch_bounds__(NTH, 2) sls_level_kernel(int N, int n, int d, const R* __restrict__ Acl,
                                                         R* Phi, long long zoff) {
-  __shared__ __align__(16) Tile<R> sm;
+  __shared__ __align__(16) Tile<R, G> sm;
   const long long z = blockIdx.z + zoff;
   const int per = N - d + 1;
   const long long b = z / per;
@@ -289,69 +335,137 @@ __global__ void __launch_bounds__(NTH) sls_level_kernel(int N, int n, int d, con
   R* base = Phi + b * T * n * n;
   const R* X = base + tri_index(k, j + 1) * n * n;
   const R* Y = Acl + (b * N + j) * n * n;
-  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
-  R acc[4][4] = {};
-  tile_mma(acc, X, n, 0, R(1), Y, n, 0, n, n, n, r0, c0, sm);
-  tile_store(acc, base + tri_index(k, j) * n * n, n, (const R*)nullptr, 0, (const R*)nullptr, 0, n, n,
+  const int r0 = blockIdx.y * G::BM, c0 = blockIdx.x * G::BN;
+  R acc[G::RM][G::RN] = {};
+  tile_mma<R, G>(acc, X, n, 0, R(1), Y, n, 0, n, n, n, r0, c0, sm);
+  tile_store<R, G>(acc, base + tri_index(k, j) * n * n, n, (const R*)nullptr, 0, (const R*)nullptr, 0, n, n,
              r0, c0);
 }
 
 // Phihat^y_{k,j} = Phihat^x_{k,j} L_j^T (L_j = Lg[j - 1], p x n), zero for j = 0
-template <typename R>
-__global__ void __launch_bounds__(NTH) sls_phiy_kernel(int N, int n, int p, const R* __restrict__ PX,
+template <typename R, class G>
+__global__ void __launch_bounds__(NTH, 2) sls_phiy_kernel(int N, int n, int p, const R* __restrict__ PX,
                                                        const R* __restrict__ Lg, R* PY, long long zoff) {
-  __shared__ __align__(16) Tile<R> sm;
+  __shared__ __align__(16) Tile<R, G> sm;
   const long long z = blockIdx.z + zoff;
   const long long T = (long long)(N + 1) * (N + 2) / 2;
   const long long b = z / T, t = z % T;
   int k, j;
   unpack_block(t, k, j);
-  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
-  R acc[4][4] = {};
+  const int r0 = blockIdx.y * G::BM, c0 = blockIdx.x * G::BN;
+  R acc[G::RM][G::RN] = {};
   if (j > 0)
-    tile_mma(acc, PX + (b * T + t) * n * n, n, 0, R(1), Lg + (b * N + j - 1) * p * n, n, 1, n, p, n, r0,
+    tile_mma<R, G>(acc, PX + (b * T + t) * n * n, n, 0, R(1), Lg + (b * N + j - 1) * p * n, n, 1, n, p, n, r0,
              c0, sm);
-  tile_store(acc, PY + (b * T + t) * n * p, p, (const R*)nullptr, 0, (const R*)nullptr, 0, n, p, r0, c0);
+  tile_store<R, G>(acc, PY + (b * T + t) * n * p, p, (const R*)nullptr, 0, (const R*)nullptr, 0, n, p, r0, c0);
 }
 
 // (M X)_{k,j} = X_{k,j} - A_{k-1} X_{k-1,j} (j < k), X_{k,k} (j = k); M = I - Z A, X blocks n x c
-template <typename R>
-__global__ void __launch_bounds__(NTH) sls_shift_kernel(int N, int n, int c, const R* __restrict__ A,
+template <typename R, class G>
+__global__ void __launch_bounds__(NTH, 2) sls_shift_kernel(int N, int n, int c, const R* __restrict__ A,
                                                         const R* __restrict__ X, R* out, long long zoff) {
-  __shared__ __align__(16) Tile<R> sm;
+  __shared__ __align__(16) Tile<R, G> sm;
   const long long z = blockIdx.z + zoff;
   const long long T = (long long)(N + 1) * (N + 2) / 2;
   const long long b = z / T, t = z % T;
   int k, j;
   unpack_block(t, k, j);
-  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
-  R acc[4][4] = {};
+  const int r0 = blockIdx.y * G::BM, c0 = blockIdx.x * G::BN;
+  R acc[G::RM][G::RN] = {};
   if (j < k)
-    tile_mma(acc, A + (b * N + k - 1) * n * n, n, 0, R(-1), X + (b * T + tri_index(k - 1, j)) * n * c, c,
+    tile_mma<R, G>(acc, A + (b * N + k - 1) * n * n, n, 0, R(-1), X + (b * T + tri_index(k - 1, j)) * n * c, c,
              0, n, c, n, r0, c0, sm);
-  tile_store(acc, out + (b * T + t) * n * c, c, X + (b * T + t) * n * c, c, (const R*)nullptr, 0, n, c,
+  tile_store<R, G>(acc, out + (b * T + t) * n * c, c, X + (b * T + t) * n * c, c, (const R*)nullptr, 0, n, c,
              r0, c0);
 }
 
 // out_{k,j} = alpha sum_{i=j..k} X_{k,i} Y_{i,j} (+ d1_{k,j}) (+ d2_{k,j});
 // X blocks r x n, Y blocks n x c, out / d1 / d2 blocks r x c
-template <typename R>
-__global__ void __launch_bounds__(NTH) sls_tri_kernel(int N, int r, int n, int c, R alpha,
+template <typename R, class G>
+__global__ void __launch_bounds__(NTH, 2) sls_tri_kernel(int N, int r, int n, int c, R alpha,
                                                       const R* __restrict__ X, const R* __restrict__ Y,
                                                       const R* d1, const R* d2, R* out, long long zoff) {
-  __shared__ __align__(16) Tile<R> sm;
+  __shared__ __align__(16) Tile<R, G> sm;
   const long long z = blockIdx.z + zoff;
   const long long T = (long long)(N + 1) * (N + 2) / 2;
   const long long b = z / T, t = z % T;
   int k, j;
   unpack_block(t, k, j);
-  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
-  R acc[4][4] = {};
+  const int r0 = blockIdx.y * G::BM, c0 = blockIdx.x * G::BN;
+  R acc[G::RM][G::RN] = {};
   for (int i = j; i <= k; ++i)
-    tile_mma(acc, X + (b * T + tri_index(k, i)) * r * n, n, 0, alpha, Y + (b * T + tri_index(i, j)) * n * c,
+    tile_mma<R, G>(acc, X + (b * T + tri_index(k, i)) * r * n, n, 0, alpha, Y + (b * T + tri_index(i, j)) * n * c,
              c, 0, r, c, n, r0, c0, sm);
   const long long o = (b * T + t) * r * c;
-  tile_store(acc, out + o, c, d1 ? d1 + o : nullptr, c, d2 ? d2 + o : nullptr, c, r, c, r0, c0);
+  tile_store<R, G>(acc, out + o, c, d1 ? d1 + o : nullptr, c, d2 ? d2 + o : nullptr, c, r, c, r0, c0);
+}
+
+// the same for blocks of r <= 8 rows (the control rows): each warp takes every eighth k of every
+// product (split K), each lane VPL adjacent columns of Y's rows; a product's X block is staged in
+// shared memory 128 columns at a time, transposed and padded to 8 rows (two vector reads per k);
+// the eight warps' partial tiles are summed in shared memory at the end
+constexpr int kThinRows = 8, kThinK = 128;
+
+template <typename R>
+__global__ void __launch_bounds__(NTH) sls_tri_thin_kernel(int N, int r, int n, int c, R alpha,
+                                                           const R* __restrict__ X,
+                                                           const R* __restrict__ Y, const R* d1,
+                                                           const R* d2, R* out, long long zoff) {
+  constexpr int VPL = sizeof(R) == 4 ? 4 : 2, CW = 32 * VPL, NW = NTH / 32;
+  __shared__ R part[NW][kThinRows][CW];
+  __shared__ __align__(16) R xs[kThinK][kThinRows];
+  const long long z = blockIdx.z + zoff;
+  const long long T = (long long)(N + 1) * (N + 2) / 2;
+  const long long b = z / T, t = z % T;
+  int k, j;
+  unpack_block(t, k, j);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cl = blockIdx.x * CW + lane * VPL;
+  bool cv[VPL];
+#pragma unroll
+  for (int v = 0; v < VPL; ++v) cv[v] = cl + v < c;
+  R acc[kThinRows][VPL] = {};
+  for (int i = j; i <= k; ++i) {
+    const R* Xb = X + (b * T + tri_index(k, i)) * r * n;
+    const R* Yb = Y + (b * T + tri_index(i, j)) * n * c;
+    for (int kc = 0; kc < n; kc += kThinK) {
+      const int kn = min(kThinK, n - kc);
+      __syncthreads();                         // the previous panel's readers are done
+      for (int e = threadIdx.x; e < kThinRows * kThinK; e += NTH) {
+        const int rr = e / kThinK, kk = e % kThinK;
+        xs[kk][rr] = (rr < r && kk < kn) ? alpha * Xb[(size_t)rr * n + kc + kk] : R(0);
+      }
+      __syncthreads();
+      const R* yrow = Yb + (size_t)(kc + warp) * c + cl;
+      for (int kk = warp; kk < kn; kk += NW, yrow += (size_t)NW * c) {
+        R yv[VPL], xv[kThinRows];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) yv[v] = cv[v] ? yrow[v] : R(0);
+        ld4(&xs[kk][0], xv);
+        ld4(&xs[kk][4], xv + 4);
+#pragma unroll
+        for (int rr = 0; rr < kThinRows; ++rr)
+#pragma unroll
+          for (int v = 0; v < VPL; ++v) acc[rr][v] = fma(xv[rr], yv[v], acc[rr][v]);
+      }
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < kThinRows; ++rr)
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) part[warp][rr][lane * VPL + v] = acc[rr][v];
+  __syncthreads();
+  for (int e = threadIdx.x; e < kThinRows * CW; e += NTH) {
+    const int rr = e / CW, cc = e % CW, gc = blockIdx.x * CW + cc;
+    if (rr >= r || gc >= c) continue;
+    R sum = R(0);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) sum += part[w][rr][cc];
+    const long long o = (b * T + t) * r * c + (long long)rr * c + gc;
+    if (d1) sum += d1[o];
+    if (d2) sum += d2[o];
+    out[o] = sum;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -368,19 +482,33 @@ inline cs_status launched(const char* what) {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+template <class G>
 inline dim3 tiles(int M, int N, long long z) {
-  return dim3((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM), (unsigned)z);
+  return dim3((unsigned)((N + G::BN - 1) / G::BN), (unsigned)((M + G::BM - 1) / G::BM), (unsigned)z);
 }
 
-template <typename R>
-cs_status gemm(Gemm<R> g, long long batch, cudaStream_t st) {
+// f(geometry) with the tile geometry for products of M rows in real type R
+template <typename R, typename F>
+cs_status with_geom(int M, F&& f) {
+  if (M <= 16) return f(GShort{});
+  if constexpr (sizeof(R) == 4) return f(GBig{});
+  else return f(GMid{});
+}
+
+template <typename R, class G>
+cs_status gemm_with(Gemm<R> g, long long batch, cudaStream_t st) {
   for (long long z0 = 0; z0 < batch; z0 += kMaxZ) {
     g.zoff = z0;
-    sls_gemm_kernel<R><<<tiles(g.M, g.N, std::min(kMaxZ, batch - z0)), NTH, 0, st>>>(g);
+    sls_gemm_kernel<R, G><<<tiles<G>(g.M, g.N, std::min(kMaxZ, batch - z0)), NTH, 0, st>>>(g);
     cs_status r = launched("sls_gemm_kernel");
     if (r) return r;
   }
   return CS_OK;
+}
+
+template <typename R>
+cs_status gemm(Gemm<R> g, long long batch, cudaStream_t st) {
+  return with_geom<R>(g.M, [&](auto geo) -> cs_status { return gemm_with<R, decltype(geo)>(g, batch, st); });
 }
 
 template <typename R>
@@ -402,12 +530,14 @@ Gemm<R> gemm_desc(int M, int N, R* c, long long sc, int ldc) {
 // gain kernel: right-hand-side columns per pass that fit the shared-memory budget
 inline int gain_cols(int n, int p, size_t rb) {
   const long long room = (long long)(kGainSmemBudget / rb) - (long long)p * p - p;
-  long long cw = room > 0 ? room / p : 0;
-  cw = std::min<long long>(std::min<long long>(cw, NTH), n);
-  return (int)cw;
+  long long cw = room > 0 ? room / p - 8 : 0;
+  cw = std::min<long long>(std::min<long long>(cw, NTH / 4), n);
+  return (int)std::max<long long>(cw, 0);
 }
 
-inline size_t gain_smem(int p, int cw, size_t rb) { return ((size_t)p * p + p + (size_t)p * cw) * rb; }
+inline size_t gain_smem(int p, int cw, size_t rb) {
+  return ((size_t)p * p + p + (size_t)p * (cw + 8)) * rb;
+}
 
 struct ObsWs {
   size_t t1, s, w, t2, abar, total;
@@ -434,15 +564,19 @@ cs_status response_levels(int B, int N, int n, const R* Acl, R* Phi, cudaStream_
     cs_status r = launched("sls_identity_kernel");
     if (r) return r;
   }
-  for (int d = 1; d <= N; ++d) {
-    const long long items = (long long)B * (N - d + 1);
-    for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
-      sls_level_kernel<R><<<tiles(n, n, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, n, d, Acl, Phi, z0);
-      cs_status r = launched("sls_level_kernel");
-      if (r) return r;
+  return with_geom<R>(n, [&](auto geo) -> cs_status {
+    using G = decltype(geo);
+    for (int d = 1; d <= N; ++d) {
+      const long long items = (long long)B * (N - d + 1);
+      for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+        sls_level_kernel<R, G><<<tiles<G>(n, n, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, n, d, Acl,
+                                                                                          Phi, z0);
+        cs_status r = launched("sls_level_kernel");
+        if (r) return r;
+      }
     }
-  }
-  return CS_OK;
+    return CS_OK;
+  });
 }
 
 template <typename R>
@@ -523,11 +657,16 @@ cs_status observer(int B, int N, int n, int p, int nw, int ne, int n0, const R* 
   }
   if ((r = response_levels<R>(B, N, n, Abar, PX, st))) return r;
   const long long T = (long long)(N + 1) * (N + 2) / 2, items = (long long)B * T;
-  for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
-    sls_phiy_kernel<R><<<tiles(n, p, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, n, p, PX, L, PY, z0);
-    if ((r = launched("sls_phiy_kernel"))) return r;
-  }
-  return CS_OK;
+  return with_geom<R>(n, [&](auto geo) -> cs_status {
+    using G = decltype(geo);
+    for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+      sls_phiy_kernel<R, G><<<tiles<G>(n, p, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, n, p, PX, L, PY,
+                                                                                         z0);
+      cs_status q = launched("sls_phiy_kernel");
+      if (q) return q;
+    }
+    return CS_OK;
+  });
 }
 
 template <typename R>
@@ -538,29 +677,48 @@ cs_status closed_loop(int B, int N, int n, int m, int p, const R* A, const R* PB
   R* MX = reinterpret_cast<R*>(ws);
   R* MY = reinterpret_cast<R*>(ws + align256((size_t)B * T * n * n * sizeof(R)));
   cs_status r;
-  for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
-    const long long zc = std::min(kMaxZ, items - z0);
-    sls_shift_kernel<R><<<tiles(n, n, zc), NTH, 0, st>>>(N, n, n, A, PX, MX, z0);
-    if ((r = launched("sls_shift_kernel"))) return r;
-    sls_shift_kernel<R><<<tiles(n, p, zc), NTH, 0, st>>>(N, n, p, A, PY, MY, z0);
-    if ((r = launched("sls_shift_kernel"))) return r;
-  }
-  for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
-    const long long zc = std::min(kMaxZ, items - z0);
-    // Phi^xw = Phibar^x + Phihat^x - Phibar^x (M Phihat^x)
-    sls_tri_kernel<R><<<tiles(n, n, zc), NTH, 0, st>>>(N, n, n, n, R(-1), PBX, MX, PBX, PX, XW, z0);
-    if ((r = launched("sls_tri_kernel"))) return r;
-    // Phi^uw = Phibar^u - Phibar^u (M Phihat^x)
-    sls_tri_kernel<R><<<tiles(m, n, zc), NTH, 0, st>>>(N, m, n, n, R(-1), PBU, MX, PBU, nullptr, UW, z0);
-    if ((r = launched("sls_tri_kernel"))) return r;
-    // Phi^xe = Phihat^y - Phibar^x (M Phihat^y)
-    sls_tri_kernel<R><<<tiles(n, p, zc), NTH, 0, st>>>(N, n, n, p, R(-1), PBX, MY, PY, nullptr, XE, z0);
-    if ((r = launched("sls_tri_kernel"))) return r;
-    // Phi^ue = -Phibar^u (M Phihat^y)
-    sls_tri_kernel<R><<<tiles(m, p, zc), NTH, 0, st>>>(N, m, n, p, R(-1), PBU, MY, nullptr, nullptr, UE, z0);
-    if ((r = launched("sls_tri_kernel"))) return r;
-  }
-  return CS_OK;
+  // (M Phihat^x) and (M Phihat^y)
+  r = with_geom<R>(n, [&](auto geo) -> cs_status {
+    using G = decltype(geo);
+    for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+      const long long zc = std::min(kMaxZ, items - z0);
+      sls_shift_kernel<R, G><<<tiles<G>(n, n, zc), NTH, 0, st>>>(N, n, n, A, PX, MX, z0);
+      cs_status q = launched("sls_shift_kernel");
+      if (q) return q;
+      sls_shift_kernel<R, G><<<tiles<G>(n, p, zc), NTH, 0, st>>>(N, n, p, A, PY, MY, z0);
+      if ((q = launched("sls_shift_kernel"))) return q;
+    }
+    return CS_OK;
+  });
+  if (r) return r;
+  // out = -(X (M Y)) + d1 + d2 over the blocks, X blocks rows x n
+  auto tri = [&](int rows, int c, const R* X, const R* Y, const R* d1, const R* d2, R* out) {
+    if (rows <= kThinRows) {
+      constexpr int CW = sizeof(R) == 4 ? 128 : 64;
+      for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+        const dim3 grid((unsigned)((c + CW - 1) / CW), 1, (unsigned)std::min(kMaxZ, items - z0));
+        sls_tri_thin_kernel<R><<<grid, NTH, 0, st>>>(N, rows, n, c, R(-1), X, Y, d1, d2, out, z0);
+        cs_status q = launched("sls_tri_thin_kernel");
+        if (q) return q;
+      }
+      return CS_OK;
+    }
+    return with_geom<R>(rows, [&](auto geo) -> cs_status {
+      using G = decltype(geo);
+      for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+        const long long zc = std::min(kMaxZ, items - z0);
+        sls_tri_kernel<R, G><<<tiles<G>(rows, c, zc), NTH, 0, st>>>(N, rows, n, c, R(-1), X, Y, d1, d2, out,
+                                                                    z0);
+        cs_status q = launched("sls_tri_kernel");
+        if (q) return q;
+      }
+      return CS_OK;
+    });
+  };
+  if ((r = tri(n, n, PBX, MX, PBX, PX, XW))) return r;         // Phi^xw
+  if ((r = tri(m, n, PBU, MX, PBU, nullptr, UW))) return r;    // Phi^uw
+  if ((r = tri(n, p, PBX, MY, PY, nullptr, XE))) return r;     // Phi^xe
+  return tri(m, p, PBU, MY, nullptr, nullptr, UE);             // Phi^ue
 }
 
 cs_status check_sizes(int B, int N, int n, int real_bytes) {
