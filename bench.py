@@ -110,6 +110,8 @@ KERNEL_SOURCES = {
     # the cloth VJP kernel's device code and its own launcher (the packed serving kernel, built
     # from the same headers, has a launcher of its own in the same file)
     "cloth": ["common.cuh", "rope.cuh", "cloth_band.cuh", "cloth.cuh", ("launch_cloth.cuh", "launch_cloth_vjp")],
+    # the observer stage's kernels and launchers
+    "sls": ["sls.cu"],
 }
 
 
@@ -129,7 +131,8 @@ def kernel_source_hash(kernel: str):
     """hash of the kernel family's sources with // comments and blank lines removed (editing a
     comment does not invalidate a measured figure)"""
     h = hashlib.sha256()
-    for entry in KERNEL_SOURCES["cloth" if kernel.startswith("cloth") else "rope"]:
+    fam = "cloth" if kernel.startswith("cloth") else "sls" if kernel.startswith("sls") else "rope"
+    for entry in KERNEL_SOURCES[fam]:
         for line in _source_lines(entry):
             code = line.split("//", 1)[0].rstrip()
             if code:
@@ -395,7 +398,10 @@ def sls_leg(args, flush, stream, world):
                 observer=dict(ms_per_step=1e3 * t_obs, value=world * B / t_obs, unit="trajectories/s",
                               roofline=roof(f_obs, t_obs)),
                 closed_loop=dict(ms_per_step=1e3 * t_cl, value=world * B / t_cl, unit="trajectories/s",
-                                 roofline=roof(f_cl, t_cl)),
+                                 roofline=roof(f_cl, t_cl),
+                                 dominant_kernel=dict(
+                                     kernel="sls_tri_kernel (the Phi^xw launch)",
+                                     dram_bytes_per_launch=load_traffic("sls_tri_kernel", f"rope{nv}_b{B}_h{H}"))),
                 status_nonzero=flagged, linearize_status_nonzero=lin_flagged)
 
 
