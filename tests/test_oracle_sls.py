@@ -185,3 +185,49 @@ def test_closed_loop_maps_satisfy_both_affine_constraints():
     assert np.allclose(left, np.hstack([I, np.zeros(((N + 1) * n, (N + 1) * p))]), atol=1e-10)
     right = Phi @ np.vstack([M, -_dense_C(C)])
     assert np.allclose(right, np.vstack([I, np.zeros(((N + 1) * m, (N + 1) * n))]), atol=1e-10)
+
+
+def _closed_loop_system(seed, n=4, p=3, m=2, N=5):
+    A, C, E, F, Xi = _system(seed, n, p, N)
+    rng = np.random.default_rng(seed + 100)
+    Bm = rng.normal(size=(N, n, m))
+    K = 0.2 * rng.normal(size=(N + 1, m, n))
+    PBX, PBU = sls.state_feedback_responses(A, Bm, K)
+    Pi, L = sls.kalman_recursion(A, C, E, F, Xi)
+    PX, PY = sls.observer_responses(A, C, L)
+    return dict(A=A, C=C, E=E, F=F, Bm=Bm, K=K, L=L,
+                maps=sls.closed_loop_maps(A, PBX, PBU, PX, PY))
+
+
+def simulate_observer_controller(s, x0, w, e):
+    """The observer-based controller u_k = K_k xhat_k with the predictor xhat_{j+1} = A_j xhat_j
+    + B_j u_j - L_{j+1}^T (y_j - C_j xhat_j), y_j = C_j x_j + e_j, on x_{j+1} = A_j x_j + B_j u_j
+    + w_j, xhat_0 = 0: states x_0..x_N and controls u_0..u_N."""
+    A, C, Bm, K, L = s["A"], s["C"], s["Bm"], s["K"], s["L"]
+    N = A.shape[0]
+    x, xh, xs, us = x0, np.zeros_like(x0), [x0], []
+    for j in range(N):
+        u = K[j] @ xh
+        y = C[j] @ x + e[j]
+        xh = A[j] @ xh + Bm[j] @ u - L[j].T @ (y - C[j] @ xh)
+        x = A[j] @ x + Bm[j] @ u + w[j]
+        xs.append(x)
+        us.append(u)
+    us.append(K[N] @ xh)
+    return np.concatenate(xs), np.concatenate(us)
+
+
+def test_closed_loop_maps_reproduce_the_observer_based_controller():
+    """The assembled maps are the responses of the controller u = K xhat with the Kalman predictor:
+    simulating that controller under random disturbances gives x = Phi^xw dx + Phi^xe dy and
+    u = Phi^uw dx + Phi^ue dy (dx_0 = x_0, dx_{j+1} = w_j, dy_{j+1} = e_j)."""
+    n, p, N = 4, 3, 5
+    s = _closed_loop_system(11)
+    rng = np.random.default_rng(12)
+    x0, w, e = rng.normal(size=n), rng.normal(size=(N, n)), rng.normal(size=(N, p))
+    xs, us = simulate_observer_controller(s, x0, w, e)
+    XW, UW, XE, UE = s["maps"]
+    dx = np.concatenate([x0, w.ravel()])
+    dy = np.concatenate([np.zeros(p), e.ravel()])
+    assert np.allclose(XW @ dx + XE @ dy, xs, atol=1e-12)
+    assert np.allclose(UW @ dx + UE @ dy, us, atol=1e-12)
