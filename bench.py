@@ -384,6 +384,32 @@ def sls_leg(args, flush, stream, world):
                                            stream)), world) / args.steps
     t_cl = max_over_ranks(sum(time_device(lambda: gsls.closed_loop(A, PBX, PBU, PX, PY), args.steps,
                                           flush, stream)), world) / args.steps
+    # reachable tubes and the tightened margins of the node heights (z_i >= 0: -z_i <= 0) on the
+    # closed-loop maps, and the conformal radius of 1000 one-step transitions of the rope
+    maps = gsls.closed_loop(A, PBX, PBU, PX, PY)
+    Ccon = torch.zeros(nv, n + m, **f32)
+    Ccon[torch.arange(nv), 3 * torch.arange(nv) + 2] = -1.0
+    bcon = torch.zeros(nv, **f32)
+    zc, vc = torch.nan_to_num(Z).contiguous(), V.contiguous()
+    for _ in range(max(1, args.warmup)):
+        tau, margin = gsls.tubes(*maps, E, F, Ccon, bcon, zc, vc)
+    t_tub = max_over_ranks(sum(time_device(lambda: gsls.tubes(*maps, E, F, Ccon, bcon, zc, vc), args.steps,
+                                           flush, stream)), world) / args.steps
+    tube_max = float(tau[:, -1, :3 * nv].max())
+    robust_rows = float((margin >= 0).float().mean())
+    del maps
+    ncal = 1000
+    rng = np.random.default_rng(scenes.BASE_SEED + 503)
+    pick = rng.integers(0, B, ncal), rng.integers(0, H, ncal)
+    qcal = zc[torch.tensor(pick[0], device="cuda"), torch.tensor(pick[1], device="cuda")].contiguous()
+    ucal = vc[torch.tensor(pick[0], device="cuda"), torch.tensor(pick[1], device="cuda")][:, None].contiguous()
+    s1 = Sim(sc, real_bytes=4, max_batch=ncal, max_horizon=1)
+    _, fpred, _ = s1.rollout(qcal, ucal)
+    qnext = (fpred + torch.tensor(0.003 * rng.standard_normal(fpred.shape), **f32)).contiguous()
+    radius, _ = gsls.conformal_radius(qnext, fpred.contiguous(), 0.1, H)
+    t_cp = max_over_ranks(sum(time_device(lambda: gsls.conformal_radius(qnext, fpred, 0.1, H), args.steps,
+                                          flush, stream)), world) / args.steps
+    del s1
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak = sms * 128 * 2 * 2032e6 / 1e12
     f_obs = flops.sls_observer_flops(H, n, p, n, p, n) * B
@@ -402,6 +428,16 @@ def sls_leg(args, flush, stream, world):
                                  dominant_kernel=dict(
                                      kernel="sls_tri_kernel (the Phi^xw launch)",
                                      dram_bytes_per_launch=load_traffic("sls_tri_kernel", f"rope{nv}_b{B}_h{H}"))),
+                tubes=dict(ms_per_step=1e3 * t_tub, value=world * B / t_tub, unit="trajectories/s",
+                           roofline=roof(flops.sls_tubes_flops(H, n, m, p, n, p, nv) * B, t_tub),
+                           what=f"sls_tubes: row-wise tubes of [x; u] and the margins of {nv} node-height "
+                                "constraints over the 20 steps",
+                           final_tube_max_m=tube_max, margins_nonnegative_fraction=robust_rows),
+                conformal=dict(ms_per_step=1e3 * t_cp, calibration_samples=ncal, delta=0.1, horizon=H,
+                               radius_m=float(radius.cpu()[0]),
+                               what="sls_conformal_radius over one-step transitions of the rope from "
+                                    "states of the nominal trajectories (f from sim_rollout, next "
+                                    "perceived states with 3 mm noise per coordinate)"),
                 status_nonzero=flagged, linearize_status_nonzero=lin_flagged)
 
 

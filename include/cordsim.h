@@ -357,6 +357,39 @@ cs_status sls_closed_loop(int B, int N, int n, int m, int p, int real_bytes, con
                           const void* PhiY, void* PhiXW, void* PhiUW, void* PhiXE, void* PhiUE,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/* Device bytes of scratch sls_tubes needs (0 for invalid sizes). */
+size_t sls_tubes_workspace(int B, int N, int n, int m, int p, int nw, int ne, int nc, int real_bytes);
+
+/* Reachable tubes and constraint tightening (Sec. 4.2 eq. of_optimization_tightening1/2) from the
+ * closed-loop maps sls_closed_loop writes and the disturbance scalings E [B][N][n][nw],
+ * F [B][N][p][ne] of sls_observer.  The disturbances w_j, e_j of step j reach time k through the
+ * blocks (k, j + 1) (j = 0..k-1); the initial estimation error is not in the sums.
+ *   tau    [B][N+1][n+m]  tau_k = sum_j ||[Phi^xw; Phi^uw]_{k,j+1} E_j||_{2,r}
+ *                                + ||[Phi^xe; Phi^ue]_{k,j+1} F_j||_{2,r} (row-wise 2-norms of the
+ *                         rows of [x_k; u_k]); tau_0 = 0
+ *   margin [B][N][nc]     -b_i - c_i^T [z_k; v_k] - sum_j (|c_i^T Phi^w_{k,j+1} E_j|_2 +
+ *                         |c_i^T Phi^e_{k,j+1} F_j|_2), k = 0..N-1: the constraint c_i^T [x; u]
+ *                         <= -b_i holds for every disturbance in the unit balls when it is >= 0
+ *   Ccon [nc][n+m], bcon [nc] (shared by the trajectories), nominal z [B][N+1][n], v [B][N][m];
+ *   with nc = 0 these and margin may be NULL.
+ * Errors: as sls_closed_loop; nc in [0, 4096]. */
+cs_status sls_tubes(int B, int N, int n, int m, int p, int nw, int ne, int nc, int real_bytes,
+                    const void* PhiXW, const void* PhiUW, const void* PhiXE, const void* PhiUE,
+                    const void* E, const void* F, const void* Ccon, const void* bcon,
+                    const void* z, const void* v, void* tau, void* margin, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* Conformal radius (Sec. 4.4): scores s_i = ||q_next_i - f_pred_i||_2 of n_cal calibration
+ * transitions (q_next [n_cal][dim] the next perceived states, f_pred [n_cal][dim] the model's
+ * predictions, e.g. sim_rollout with H = 1), and radius[0] = s_(k), the k-th smallest score with
+ * k = ceil((n_cal + 1)(1 - delta / T)) (at least 1; +inf when k > n_cal).  scores [n_cal] may be
+ * NULL; radius is a device pointer to one real.  A NaN score sorts as +inf.
+ * Errors: CS_ERR_INVALID_ARG (n_cal not in [1, 8192], dim not in [1, 2^20], delta not in (0, 1),
+ * T < 1, NULL q_next, f_pred or radius), CS_ERR_CUDA. */
+cs_status sls_conformal_radius(int n_cal, int dim, int real_bytes, const void* q_next,
+                               const void* f_pred, double delta, int T, void* scores,
+                               void* radius, void* stream);
+
 /* Number of kernel launches the library made on the calling thread since the last call
  * (instrumentation for benchmarks). */
 int64_t cs_launch_count(void);

@@ -102,6 +102,10 @@ SIGNATURES = {
     "sls_response": (C.c_int, [C.c_int] * 4 + [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sls_closed_loop_workspace": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "sls_closed_loop": (C.c_int, [C.c_int] * 6 + [C.c_void_p] * 9 + [C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sls_tubes_workspace": (C.c_size_t, [C.c_int] * 9),
+    "sls_tubes": (C.c_int, [C.c_int] * 9 + [C.c_void_p] * 12 + [C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sls_conformal_radius": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
+                                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cs_launch_count": (C.c_int64, []),
     "cs_last_error": (C.c_char_p, []),
 }

@@ -469,6 +469,140 @@ __global__ void __launch_bounds__(NTH) sls_tri_thin_kernel(int N, int r, int n, 
 }
 
 // ---------------------------------------------------------------------------------------------
+// Reachable tubes and constraint tightening (Sec. 4.2 eq. of_optimization_tightening1/2) and the
+// conformal radius (Sec. 4.4)
+// ---------------------------------------------------------------------------------------------
+
+// row sums of squares of X_{k,j} S_{j-1} for blocks j >= 1 (X blocks r x kd packed, S [B][N][kd][c]):
+// ssq[b][t][column tile][row], one tile product per CTA, the 16 threads of a row group summing
+// their squares by shuffles
+template <typename R, class G>
+__global__ void __launch_bounds__(NTH, 2) sls_rownorm_kernel(int N, int r, int kd, int c,
+                                                             const R* __restrict__ X,
+                                                             const R* __restrict__ S, R* ssq,
+                                                             int nct, long long zoff) {
+  __shared__ __align__(16) Tile<R, G> sm;
+  const long long z = blockIdx.z + zoff;
+  const long long T = (long long)(N + 1) * (N + 2) / 2;
+  const long long b = z / T, t = z % T;
+  int k, j;
+  unpack_block(t, k, j);
+  const int r0 = blockIdx.y * G::BM, c0 = blockIdx.x * G::BN;
+  R acc[G::RM][G::RN] = {};
+  if (j > 0)
+    tile_mma<R, G>(acc, X + (b * T + t) * r * kd, kd, 0, R(1), S + (b * N + j - 1) * kd * c, c, 0, r, c, kd,
+                   r0, c0, sm);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < G::RM; ++u) {
+    R q = R(0);
+#pragma unroll
+    for (int v = 0; v < G::RN; ++v) q = fma(acc[u][v], acc[u][v], q);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    const int i = r0 + row_of<G>(ty, u);
+    if (tx == 0 && i < r) ssq[((b * T + t) * nct + blockIdx.x) * r + i] = q;
+  }
+}
+
+// the row-wise 2-norm of block (k, j): sqrt of its column tiles' sums of squares
+template <typename R>
+__device__ __forceinline__ R block_row_norm(const R* ssq, long long bt, int nct, int r, int i) {
+  R q = R(0);
+  for (int ct = 0; ct < nct; ++ct) q += ssq[(bt * nct + ct) * r + i];
+  return sqrt(q);
+}
+
+// tau[b][k][i] = sum_{j=1..k} |row i of Phi^w_{k,j} E_{j-1}| + |row i of Phi^e_{k,j} F_{j-1}|,
+// rows i < n from the x blocks, n <= i < n + m from the u blocks
+template <typename R>
+__global__ void sls_tube_sum_kernel(long long B, int N, int n, int m, int nxw, int nuw, int nxe, int nue,
+                                    const R* sxw, const R* suw, const R* sxe, const R* sue, R* tau) {
+  const long long T = (long long)(N + 1) * (N + 2) / 2, per = (long long)(N + 1) * (n + m);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < B * per;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / per;
+    const int k = (int)(e % per) / (n + m), i = (int)(e % per) % (n + m);
+    R acc = R(0);
+    for (int j = 1; j <= k; ++j) {
+      const long long bt = b * T + tri_index(k, j);
+      acc += i < n ? block_row_norm(sxw, bt, nxw, n, i) + block_row_norm(sxe, bt, nxe, n, i)
+                   : block_row_norm(suw, bt, nuw, m, i - n) + block_row_norm(sue, bt, nue, m, i - n);
+    }
+    tau[e] = acc;
+  }
+}
+
+// margin[b][k][i] = -b_i - c_i^T [z_k; v_k] - sum_{j=1..k} (|c_i^T Phi^w_{k,j} E_{j-1}| +
+// |c_i^T Phi^e_{k,j} F_{j-1}|), k = 0..N-1; the c_i^T Phi products are the rows of the G blocks
+template <typename R>
+__global__ void sls_margin_kernel(long long B, int N, int n, int m, int nc, int ncw, int nce,
+                                  const R* sgw, const R* sge, const R* Ccon, const R* bcon,
+                                  const R* zn, const R* vn, R* margin) {
+  const long long T = (long long)(N + 1) * (N + 2) / 2, per = (long long)N * nc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < B * per;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / per;
+    const int k = (int)(e % per) / nc, i = (int)(e % per) % nc;
+    const R* ci = Ccon + (size_t)i * (n + m);
+    const R* zk = zn + (b * (N + 1) + k) * n;
+    const R* vk = vn + (b * N + k) * m;
+    R lin = R(0);
+    for (int q = 0; q < n; ++q) lin = fma(ci[q], zk[q], lin);
+    for (int q = 0; q < m; ++q) lin = fma(ci[n + q], vk[q], lin);
+    R acc = R(0);
+    for (int j = 1; j <= k; ++j) {
+      const long long bt = b * T + tri_index(k, j);
+      acc += block_row_norm(sgw, bt, ncw, nc, i) + block_row_norm(sge, bt, nce, nc, i);
+    }
+    margin[e] = -bcon[i] - lin - acc;
+  }
+}
+
+// conformal radius: scores s_i = |q_next_i - f_pred_i|_2 (NaN read as +inf), sorted in shared
+// memory by a bitonic network over np (a power of two) entries padded with +inf, then the
+// kth-smallest (1-based, kth >= 1; past ncal: +inf)
+template <typename R>
+__global__ void __launch_bounds__(1024) sls_conformal_kernel(int ncal, int dim, int np, int kth,
+                                                             const R* __restrict__ qn,
+                                                             const R* __restrict__ fp, R* scores,
+                                                             R* radius) {
+  extern __shared__ __align__(16) unsigned char sls_smem[];
+  R* sc = reinterpret_cast<R*>(sls_smem);
+  const R inf = R(INFINITY);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    R v = inf;
+    if (i < ncal) {
+      R q = R(0);
+      for (int d = 0; d < dim; ++d) {
+        const R x = qn[(size_t)i * dim + d] - fp[(size_t)i * dim + d];
+        q = fma(x, x, q);
+      }
+      v = sqrt(q);
+      if (scores) scores[i] = v;
+      if (!(v == v)) v = inf;
+    }
+    sc[i] = v;
+  }
+  __syncthreads();
+  for (int size = 2; size <= np; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int q = i ^ stride;
+        if (q > i) {
+          const R a = sc[i], c = sc[q];
+          if ((a > c) == ((i & size) == 0)) {
+            sc[i] = c;
+            sc[q] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) radius[0] = kth <= ncal ? sc[kth - 1] : inf;
+}
+
+// ---------------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------------
 
@@ -721,6 +855,101 @@ cs_status closed_loop(int B, int N, int n, int m, int p, const R* A, const R* PB
   return tri(m, p, PBU, MY, nullptr, nullptr, UE);             // Phi^ue
 }
 
+// tile width (columns) of the row-norm products with `rows` rows
+template <typename R>
+inline int geom_bn(int rows) {
+  return rows <= 16 ? GShort::BN : (sizeof(R) == 4 ? GBig::BN : GMid::BN);
+}
+
+struct TubeWs {
+  int nxw, nuw, nxe, nue, ngw, nge;       // column tiles of each product
+  size_t sxw, suw, sxe, sue, gw, ge, sgw, sge, total;
+};
+
+template <typename R>
+TubeWs tube_ws(long long B, int N, int n, int m, int p, int nw, int ne, int nc) {
+  const size_t T = (size_t)(N + 1) * (N + 2) / 2, rb = sizeof(R);
+  TubeWs w;
+  w.nxw = (nw + geom_bn<R>(n) - 1) / geom_bn<R>(n);
+  w.nuw = (nw + geom_bn<R>(m) - 1) / geom_bn<R>(m);
+  w.nxe = (ne + geom_bn<R>(n) - 1) / geom_bn<R>(n);
+  w.nue = (ne + geom_bn<R>(m) - 1) / geom_bn<R>(m);
+  w.ngw = nc > 0 ? (nw + geom_bn<R>(nc) - 1) / geom_bn<R>(nc) : 0;
+  w.nge = nc > 0 ? (ne + geom_bn<R>(nc) - 1) / geom_bn<R>(nc) : 0;
+  size_t off = 0;
+  auto take = [&](size_t elems) { const size_t o = off; off = align256(off + elems * rb); return o; };
+  w.sxw = take(B * T * w.nxw * n);
+  w.suw = take(B * T * w.nuw * m);
+  w.sxe = take(B * T * w.nxe * n);
+  w.sue = take(B * T * w.nue * m);
+  w.gw = take(B * T * (size_t)nc * n);
+  w.ge = take(B * T * (size_t)nc * p);
+  w.sgw = take(B * T * w.ngw * nc);
+  w.sge = take(B * T * w.nge * nc);
+  w.total = off;
+  return w;
+}
+
+template <typename R>
+cs_status rownorms(int B, int N, int r, int kd, int c, const R* X, const R* S, R* ssq, int nct,
+                   cudaStream_t st) {
+  const long long items = (long long)B * (N + 1) * (N + 2) / 2;
+  return with_geom<R>(r, [&](auto geo) -> cs_status {
+    using G = decltype(geo);
+    for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
+      sls_rownorm_kernel<R, G><<<tiles<G>(r, c, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, r, kd, c, X, S,
+                                                                                          ssq, nct, z0);
+      cs_status q = launched("sls_rownorm_kernel");
+      if (q) return q;
+    }
+    return CS_OK;
+  });
+}
+
+template <typename R>
+cs_status tubes(int B, int N, int n, int m, int p, int nw, int ne, int nc, const R* XW, const R* UW,
+                const R* XE, const R* UE, const R* E, const R* F, const R* Ccon, const R* bcon,
+                const R* zn, const R* vn, R* tau, R* margin, unsigned char* ws, cudaStream_t st) {
+  const TubeWs w = tube_ws<R>(B, N, n, m, p, nw, ne, nc);
+  auto at = [&](size_t o) { return reinterpret_cast<R*>(ws + o); };
+  cs_status r;
+  if ((r = rownorms<R>(B, N, n, n, nw, XW, E, at(w.sxw), w.nxw, st))) return r;
+  if ((r = rownorms<R>(B, N, m, n, nw, UW, E, at(w.suw), w.nuw, st))) return r;
+  if ((r = rownorms<R>(B, N, n, p, ne, XE, F, at(w.sxe), w.nxe, st))) return r;
+  if ((r = rownorms<R>(B, N, m, p, ne, UE, F, at(w.sue), w.nue, st))) return r;
+  const long long T = (long long)(N + 1) * (N + 2) / 2;
+  {
+    const long long tot = (long long)B * (N + 1) * (n + m);
+    const int grid = (int)std::min<long long>((tot + 255) / 256, 148LL * 16);
+    sls_tube_sum_kernel<R><<<grid, 256, 0, st>>>(B, N, n, m, w.nxw, w.nuw, w.nxe, w.nue, at(w.sxw), at(w.suw),
+                                                 at(w.sxe), at(w.sue), tau);
+    if ((r = launched("sls_tube_sum_kernel"))) return r;
+  }
+  if (nc == 0) return CS_OK;
+  // G^w = C_x Phi^xw + C_u Phi^uw (nc x n), G^e = C_x Phi^xe + C_u Phi^ue (nc x p), every block
+  {
+    Gemm<R> g = gemm_desc<R>(nc, n, at(w.gw), (long long)nc * n, n);
+    g.pr[g.np++] = prod<R>(Ccon, 0, n + m, 0, XW, (long long)n * n, n, 0, n);
+    g.pr[g.np++] = prod<R>(Ccon + n, 0, n + m, 0, UW, (long long)m * n, n, 0, m);
+    if ((r = gemm(g, B * T, st))) return r;
+  }
+  {
+    Gemm<R> g = gemm_desc<R>(nc, p, at(w.ge), (long long)nc * p, p);
+    g.pr[g.np++] = prod<R>(Ccon, 0, n + m, 0, XE, (long long)n * p, p, 0, n);
+    g.pr[g.np++] = prod<R>(Ccon + n, 0, n + m, 0, UE, (long long)m * p, p, 0, m);
+    if ((r = gemm(g, B * T, st))) return r;
+  }
+  if ((r = rownorms<R>(B, N, nc, n, nw, at(w.gw), E, at(w.sgw), w.ngw, st))) return r;
+  if ((r = rownorms<R>(B, N, nc, p, ne, at(w.ge), F, at(w.sge), w.nge, st))) return r;
+  const long long tot = (long long)B * N * nc;
+  const int grid = (int)std::min<long long>((tot + 255) / 256, 148LL * 16);
+  sls_margin_kernel<R><<<grid, 256, 0, st>>>(B, N, n, m, nc, w.ngw, w.nge, at(w.sgw), at(w.sge), Ccon, bcon,
+                                             zn, vn, margin);
+  return launched("sls_margin_kernel");
+}
+
+constexpr int kConformalMax = 8192;   // calibration samples one shared-memory sort holds (64 KB in FP64)
+
 cs_status check_sizes(int B, int N, int n, int real_bytes) {
   if (B < 0) return cs_fail(CS_ERR_INVALID_ARG, "B must be >= 0");
   if (N < 1 || n < 1) return cs_fail(CS_ERR_INVALID_ARG, "N and n must be >= 1");
@@ -801,6 +1030,75 @@ cs_status sls_closed_loop(int B, int N, int n, int m, int p, int real_bytes, con
   return closed_loop<double>(B, N, n, m, p, (const double*)A, (const double*)PhiBarX,
                              (const double*)PhiBarU, (const double*)PhiX, (const double*)PhiY,
                              (double*)PhiXW, (double*)PhiUW, (double*)PhiXE, (double*)PhiUE, ws, st);
+}
+
+size_t sls_tubes_workspace(int B, int N, int n, int m, int p, int nw, int ne, int nc, int real_bytes) {
+  if (B < 0 || N < 1 || n < 1 || m < 1 || p < 1 || nw < 1 || ne < 1 || nc < 0 ||
+      (real_bytes != 4 && real_bytes != 8))
+    return 0;
+  return real_bytes == 4 ? tube_ws<float>(B, N, n, m, p, nw, ne, nc).total
+                         : tube_ws<double>(B, N, n, m, p, nw, ne, nc).total;
+}
+
+cs_status sls_tubes(int B, int N, int n, int m, int p, int nw, int ne, int nc, int real_bytes,
+                    const void* PhiXW, const void* PhiUW, const void* PhiXE, const void* PhiUE,
+                    const void* E, const void* F, const void* Ccon, const void* bcon, const void* z,
+                    const void* v, void* tau, void* margin, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+  cs_status r = check_sizes(B, N, n, real_bytes);
+  if (r) return r;
+  if (m < 1 || p < 1 || nw < 1 || ne < 1 || nc < 0 || m > 4096 || p > 4096 || nw > 4096 || ne > 4096 ||
+      nc > 4096)
+    return cs_fail(CS_ERR_INVALID_ARG, "m, p, nw, ne must be in [1, 4096] and nc in [0, 4096]");
+  if (B > 0 && (!PhiXW || !PhiUW || !PhiXE || !PhiUE || !E || !F || !tau || !workspace))
+    return cs_fail(CS_ERR_INVALID_ARG, "null pointer");
+  if (B > 0 && nc > 0 && (!Ccon || !bcon || !z || !v || !margin))
+    return cs_fail(CS_ERR_INVALID_ARG, "null constraint pointer with nc > 0");
+  if (workspace_bytes < sls_tubes_workspace(B, N, n, m, p, nw, ne, nc, real_bytes))
+    return cs_fail(CS_ERR_INVALID_ARG, "workspace smaller than sls_tubes_workspace()");
+  if (B == 0) return CS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* ws = (unsigned char*)workspace;
+  if (real_bytes == 4)
+    return tubes<float>(B, N, n, m, p, nw, ne, nc, (const float*)PhiXW, (const float*)PhiUW,
+                        (const float*)PhiXE, (const float*)PhiUE, (const float*)E, (const float*)F,
+                        (const float*)Ccon, (const float*)bcon, (const float*)z, (const float*)v,
+                        (float*)tau, (float*)margin, ws, st);
+  return tubes<double>(B, N, n, m, p, nw, ne, nc, (const double*)PhiXW, (const double*)PhiUW,
+                       (const double*)PhiXE, (const double*)PhiUE, (const double*)E, (const double*)F,
+                       (const double*)Ccon, (const double*)bcon, (const double*)z, (const double*)v,
+                       (double*)tau, (double*)margin, ws, st);
+}
+
+cs_status sls_conformal_radius(int n_cal, int dim, int real_bytes, const void* q_next, const void* f_pred,
+                               double delta, int T, void* scores, void* radius, void* stream) {
+  if (n_cal < 1 || n_cal > kConformalMax || dim < 1 || dim > (1 << 20))
+    return cs_fail(CS_ERR_INVALID_ARG, "n_cal must be in [1, 8192] and dim in [1, 2^20]");
+  if (real_bytes != 4 && real_bytes != 8) return cs_fail(CS_ERR_INVALID_ARG, "real_bytes must be 4 or 8");
+  if (!(delta > 0.0 && delta < 1.0) || T < 1)
+    return cs_fail(CS_ERR_INVALID_ARG, "delta must be in (0, 1) and T >= 1");
+  if (!q_next || !f_pred || !radius) return cs_fail(CS_ERR_INVALID_ARG, "null pointer");
+  long long kth = (long long)std::ceil((n_cal + 1.0) * (1.0 - delta / T));
+  kth = std::max<long long>(kth, 1);
+  const int k = (int)std::min<long long>(kth, (long long)n_cal + 1);
+  int np = 1;
+  while (np < n_cal) np <<= 1;
+  const size_t smem = (size_t)np * real_bytes;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (real_bytes == 4) {
+    cudaError_t e = cudaFuncSetAttribute(sls_conformal_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cs_cuda_fail(e, "cudaFuncSetAttribute");
+    sls_conformal_kernel<float><<<1, 1024, smem, st>>>(n_cal, dim, np, k, (const float*)q_next,
+                                                       (const float*)f_pred, (float*)scores, (float*)radius);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(sls_conformal_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cs_cuda_fail(e, "cudaFuncSetAttribute");
+    sls_conformal_kernel<double><<<1, 1024, smem, st>>>(n_cal, dim, np, k, (const double*)q_next,
+                                                        (const double*)f_pred, (double*)scores, (double*)radius);
+  }
+  return launched("sls_conformal_kernel");
 }
 
 }  // extern "C"

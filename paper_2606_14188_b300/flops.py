@@ -150,3 +150,15 @@ def sls_closed_loop_flops(N: int, n: int, m: int, p: int) -> float:
     s3 = sum((N + 1 - d) * (d + 1) for d in range(N + 1))
     return (tri * (_mm(n, n, n) + _mm(n, p, n))
             + s3 * (_mm(n, n, n) + _mm(m, n, n) + _mm(n, p, n) + _mm(m, p, n)))
+
+
+def sls_tubes_flops(N: int, n: int, m: int, p: int, nw: int, ne: int, nc: int) -> float:
+    """One trajectory of sls_tubes: the products Phi_{k,j} E_{j-1}, Phi_{k,j} F_{j-1} of the blocks
+    below the diagonal with their row sums of squares; for nc constraints the rows
+    C [Phi^x; Phi^u] of every block and their products with E, F."""
+    tri = N * (N + 1) / 2.0
+    T = (N + 1) * (N + 2) / 2.0
+    tubes = tri * ((_mm(n, nw, n) + _mm(m, nw, n)) + (_mm(n, ne, p) + _mm(m, ne, p)) + 2.0 * (n + m) * (nw + ne))
+    cons = T * (_mm(nc, n, n) + _mm(nc, n, m) + _mm(nc, p, n) + _mm(nc, p, m)) + \
+        tri * (_mm(nc, nw, n) + _mm(nc, ne, p) + 2.0 * nc * (nw + ne))
+    return tubes + (cons if nc > 0 else 0.0)

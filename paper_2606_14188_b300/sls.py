@@ -1,9 +1,12 @@
-"""Output-feedback SLS observer stage over libcordsim (argument marshalling only; every step runs in
-the library's CUDA kernels, on the current torch stream).
+"""Output-feedback SLS observer stage, reachable tubes and conformal radius over libcordsim
+(argument marshalling only; every step runs in the library's CUDA kernels, on the current torch
+stream).
 
     Pi, L, PhiX, PhiY, status = observer(A, C, E, F, Xi)     # Kalman recursion + observer responses
     Phi = response(Acl)                                       # closed-loop response of given Acl_j
     XW, UW, XE, UE = closed_loop(A, PhiBarX, PhiBarU, PhiX, PhiY)
+    tau, margin = tubes(XW, UW, XE, UE, E, F, Ccon, bcon, z, v)  # reachable tubes, tightening
+    radius, scores = conformal_radius(q_next, f_pred, delta, T) # conformal radius
 
 Block lower-triangular operators over times 0..N are packed [B][T][r][c], block (k, j) at index
 k (k + 1) / 2 + j, T = (N + 1)(N + 2) / 2; unpack() turns them into dense block matrices.
@@ -96,6 +99,49 @@ def closed_loop(A, PBX, PBU, PX, PY):
     L.check(lib.sls_closed_loop(B, N, n, m, p, rb, _p(A), _p(PBX), _p(PBU), _p(PX), _p(PY), _p(XW),
                                 _p(UW), _p(XE), _p(UE), _p(ws), wsb, _stream()), "sls_closed_loop")
     return XW, UW, XE, UE
+
+
+def tubes(XW, UW, XE, UE, E, F, Ccon=None, bcon=None, z=None, v=None):
+    """Closed-loop maps (as closed_loop returns them), E [B][N][n][nw], F [B][N][p][ne] ->
+    tau [B][N+1][n+m] (row-wise tube widths) and, with constraints Ccon [nc][n+m], bcon [nc] and
+    the nominal z [B][N+1][n], v [B][N][m], margin [B][N][nc] (else None)."""
+    cons = Ccon is not None
+    ts = (XW, UW, XE, UE, E, F) + ((Ccon, bcon, z, v) if cons else ())
+    rb = _rb(*ts)
+    B, T, n = XW.shape[0], XW.shape[1], XW.shape[2]
+    N, m, p = E.shape[1], UW.shape[2], XE.shape[3]
+    nw, ne = E.shape[3], F.shape[3]
+    nc = Ccon.shape[0] if cons else 0
+    if (T != n_blocks(N) or UW.shape != (B, T, m, n) or XE.shape != (B, T, n, p) or UE.shape != (B, T, m, p)
+            or E.shape[:3] != (B, N, n) or F.shape[:3] != (B, N, p)):
+        raise ValueError("inconsistent shapes")
+    if cons and (Ccon.shape != (nc, n + m) or bcon.shape != (nc,) or z.shape != (B, N + 1, n)
+                 or v.shape != (B, N, m)):
+        raise ValueError("inconsistent constraint shapes")
+    tau = torch.empty(B, N + 1, n + m, dtype=XW.dtype, device=XW.device)
+    margin = torch.empty(B, N, nc, dtype=XW.dtype, device=XW.device) if cons else None
+    lib = L.lib()
+    wsb = lib.sls_tubes_workspace(B, N, n, m, p, nw, ne, nc, rb)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=XW.device)
+    nul = C.c_void_p(None)
+    L.check(lib.sls_tubes(B, N, n, m, p, nw, ne, nc, rb, _p(XW), _p(UW), _p(XE), _p(UE), _p(E), _p(F),
+                          *((_p(Ccon), _p(bcon), _p(z), _p(v)) if cons else (nul, nul, nul, nul)),
+                          _p(tau), _p(margin) if cons else nul, _p(ws), wsb, _stream()), "sls_tubes")
+    return tau, margin
+
+
+def conformal_radius(q_next, f_pred, delta: float, T: int):
+    """q_next, f_pred [n_cal][dim] -> radius (a one-element tensor on the device: the
+    ceil((n_cal + 1)(1 - delta / T))-th smallest score, +inf past n_cal) and the scores [n_cal]."""
+    rb = _rb(q_next, f_pred)
+    if q_next.shape != f_pred.shape or q_next.dim() != 2:
+        raise ValueError("q_next and f_pred must be [n_cal][dim] of one shape")
+    ncal, dim = q_next.shape
+    scores = torch.empty(ncal, dtype=q_next.dtype, device=q_next.device)
+    radius = torch.empty(1, dtype=q_next.dtype, device=q_next.device)
+    L.check(L.lib().sls_conformal_radius(ncal, dim, rb, _p(q_next), _p(f_pred), float(delta), int(T),
+                                         _p(scores), _p(radius), _stream()), "sls_conformal_radius")
+    return radius, scores
 
 
 def unpack(blocks, N: int):

@@ -193,3 +193,29 @@ def test_sls_argument_errors_without_gpu():
     assert lib.sls_closed_loop(2, 3, 10, 0, 4, 8, *([f] * 9), f, cw, None) == 1
     assert lib.sls_closed_loop(2, 3, 10, 6, 4, 8, *([f] * 9), f, cw - 1, None) == 1
     assert lib.sls_closed_loop(0, 3, 10, 6, 4, 8, *([None] * 9), None, 0, None) == 0
+
+
+def test_tube_and_conformal_argument_errors_without_gpu():
+    """sls_tubes and sls_conformal_radius check sizes, pointers, the workspace and the miscoverage
+    level before any device call (the pointers below are never dereferenced)."""
+    lib = L.lib()
+    f = C.c_void_p(256)
+    ws = lib.sls_tubes_workspace(2, 3, 10, 2, 4, 10, 4, 5, 4)
+    assert ws > 0 and lib.sls_tubes_workspace(2, 3, 10, 2, 4, 10, 4, -1, 4) == 0
+
+    def tub(nc=5, cons=f, wsb=ws, m=2):
+        return lib.sls_tubes(2, 3, 10, m, 4, 10, 4, nc, 4, f, f, f, f, f, f, cons, cons, cons, cons, f,
+                             cons, f, wsb, None)
+
+    assert tub(m=0) == 1
+    assert tub(nc=-1) == 1
+    assert tub(cons=None) == 1 and b"constraint" in lib.cs_last_error()
+    assert tub(wsb=ws - 1) == 1 and b"workspace" in lib.cs_last_error()
+    cr = lib.sls_conformal_radius
+    assert cr(0, 3, 4, f, f, 0.1, 1, None, f, None) == 1
+    assert cr(8193, 3, 4, f, f, 0.1, 1, None, f, None) == 1
+    assert cr(10, 3, 4, f, f, 0.0, 1, None, f, None) == 1
+    assert cr(10, 3, 4, f, f, 1.0, 1, None, f, None) == 1
+    assert cr(10, 3, 4, f, f, 0.1, 0, None, f, None) == 1
+    assert cr(10, 3, 4, f, f, 0.1, 1, None, None, None) == 1
+    assert cr(10, 3, 2, f, f, 0.1, 1, None, f, None) == 1

@@ -14,7 +14,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import grad as ograd, sim as osim, sls  # noqa: E402
+from oracle import grad as ograd, sim as osim, sls, tubes  # noqa: E402
 from paper_2606_14188_b300 import scenes  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -156,7 +156,8 @@ def test_closed_loop_maps_match_the_oracle_and_satisfy_the_constraints(rb):
 def test_full_size_observer_and_closed_loop_fp32_sampled():
     """The 256-trajectory x 20-step, 126-state launch the benchmark times (FP32): the rope's own
     Jacobians on three sampled trajectories (the others repeat trajectory 0 to fill the launch),
-    the observer and the closed-loop maps of those three compared with the oracle."""
+    the observer, the closed-loop maps and the reachable tubes of those three compared with the
+    oracle."""
     B, H = 256, 20
     picks = [0, 127, 255]
     sys3, Bm3 = _rope_inputs(3, H, seed=21)
@@ -183,6 +184,7 @@ def test_full_size_observer_and_closed_loop_fp32_sampled():
     kidx = torch.tensor([k for k in range(H + 1) for _ in range(k + 1)], device="cuda")
     PBU = torch.einsum("btmn,btnc->btmc", Kt[:, kidx], PBX).contiguous()
     XW, UW, XE, UE = gsls.closed_loop(A, PBX, PBU, out[2], out[3])
+    tau, _ = gsls.tubes(XW, UW, XE, UE, _t(full["E"], 4), _t(full["F"], 4))
     for i, b in enumerate(picks):
         PBXr, PBUr = _feedback_responses(full["A"][b], Bm[b], K[b])
         assert _rel(gsls.unpack(PBX[b:b + 1], H)[0].cpu().numpy(), PBXr) <= 1e-3
@@ -191,6 +193,8 @@ def test_full_size_observer_and_closed_loop_fp32_sampled():
         ref = sls.closed_loop_maps(full["A"][b], PBXr, PBUr, PX, PY)
         for g, r in zip((XW, UW, XE, UE), ref):
             assert _rel(gsls.unpack(g[b:b + 1], H)[0].cpu().numpy(), r) <= 1e-3, b
+        tref = tubes.tube_widths(*ref, full["E"][b], full["F"][b], H)
+        assert _rel(tau[b].cpu().numpy(), tref) <= 1e-3, b
     assert T == 231
 
 
