@@ -110,8 +110,9 @@ KERNEL_SOURCES = {
     # the cloth VJP kernel's device code and its own launcher (the packed serving kernel, built
     # from the same headers, has a launcher of its own in the same file)
     "cloth": ["common.cuh", "rope.cuh", "cloth_band.cuh", "cloth.cuh", ("launch_cloth.cuh", "launch_cloth_vjp")],
-    # the observer stage's kernels and launchers
-    "sls": ["sls.cu"],
+    # the observer stage's block-triangular product: its tile routine and the kernel
+    "sls_tri": [("sls.cu", "row_of"), ("sls.cu", "col_of"), ("sls.cu", "tile_mma"), ("sls.cu", "tile_store"),
+                ("sls.cu", "sls_tri_kernel")],
 }
 
 
@@ -131,7 +132,7 @@ def kernel_source_hash(kernel: str):
     """hash of the kernel family's sources with // comments and blank lines removed (editing a
     comment does not invalidate a measured figure)"""
     h = hashlib.sha256()
-    fam = "cloth" if kernel.startswith("cloth") else "sls" if kernel.startswith("sls") else "rope"
+    fam = "cloth" if kernel.startswith("cloth") else "sls_tri" if kernel.startswith("sls_tri") else "rope"
     for entry in KERNEL_SOURCES[fam]:
         for line in _source_lines(entry):
             code = line.split("//", 1)[0].rstrip()
