@@ -442,6 +442,33 @@ def sls_leg(args, flush, stream, world):
                 status_nonzero=flagged, linearize_status_nonzero=lin_flagged)
 
 
+def apg_leg(args, flush, stream, world):
+    """The analytic policy gradient on the headline's rollouts: a tanh policy of 64 hidden units
+    in the loop of the 1024 x 64-node x 50-step rope rollouts, the planning loss and dL/dtheta
+    through the simulator (apg_rollout_grad; every step one rollout step and one adjoint step)."""
+    import torch
+    from paper_2606_14188_b300.sim import Sim
+    w = scenes.workload(2, B=args.rollouts, H=args.rope_horizon)
+    sc, B, H = w["scene"], w["B"], w["H"]
+    nv = sc["params"]["n_nodes"]
+    hidden = 64
+    s = Sim(sc, real_bytes=4, max_batch=B, max_horizon=H)
+    nth = hidden * s.nq + 7 * hidden + 6
+    rng = np.random.default_rng(scenes.BASE_SEED + 504)
+    th = torch.tensor(0.05 * rng.standard_normal(nth) / np.sqrt(s.nq), dtype=torch.float32, device="cuda")
+    q0 = torch.tensor(w["q0"], dtype=torch.float32, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        Lv, dth, _, st = s.apg_grad(q0, th, hidden, H)
+    t = max_over_ranks(sum(time_device(lambda: s.apg_grad(q0, th, hidden, H), args.steps, flush, stream)),
+                       world) / args.steps
+    done = int(torch.count_nonzero(st == 0).item())
+    return dict(workload=f"rope{nv}_b{B}_h{H}, tanh policy of {hidden} hidden units", ms_per_step=1e3 * t,
+                value=world * done * nv * H / t, unit=UNIT, status_nonzero=B - done,
+                dtheta_finite=bool(torch.isfinite(dth).all().item()),
+                what="apg_rollout_grad: closed-loop forward and surrogate adjoint with the policy's "
+                     "derivatives in the chain, node-steps of the completed rollouts per second")
+
+
 def _cloth_sample_job(steps):
     from oracle import grad as ograd, sim as osim
     w = scenes.workload(3, B=1, H=steps)
@@ -801,6 +828,9 @@ def run_ours(args):
     inertial = inertial_leg(args, flush, stream, world)
     _leg("inertial variant", t_leg)
     t_leg = time.perf_counter()
+    apg_out = apg_leg(args, flush, stream, world)
+    _leg("policy gradient", t_leg)
+    t_leg = time.perf_counter()
     served = served_leg(args) if args.served_requests > 0 else None
     _leg("served", t_leg)
     t_leg = time.perf_counter()
@@ -853,7 +883,7 @@ def run_ours(args):
                         what="sim_rollout_vjp on the same rollouts with checkpoint_every = 1 (every "
                              "step's record stored, no segment recompute); not the headline, whose "
                              "workload checkpoints every 7 steps"),
-                    linearize=lin, sls_observer_stage=sls_out, inertial_variant=inertial, served=served, cloth=cloth,
+                    linearize=lin, sls_observer_stage=sls_out, inertial_variant=inertial, policy_gradient=apg_out, served=served, cloth=cloth,
                     gpu_launches=launches, clocks=clocks,
                     status_nonzero=int(np.count_nonzero(status)),
                     node_steps_counted=f"{int(np.count_nonzero(status == 0))} of {B} rollouts "

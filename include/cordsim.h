@@ -390,6 +390,28 @@ cs_status sls_conformal_radius(int n_cal, int dim, int real_bytes, const void* q
                                const void* f_pred, double delta, int T, void* scores,
                                void* radius, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Analytic policy gradient (Sec. 4.3): a policy in the loop of the batched rollout and the
+ * gradient of the closed-loop planning loss through the simulator (eq. diff-sim).  The policy,
+ * shared by the rollouts, is one tanh hidden layer of `hidden` units,
+ *   u = W2 tanh(W1 q + b1) + b2,   theta = [W1 (hidden x n_q), b1 (hidden), W2 (6 x hidden), b2 (6)]
+ * (device, the handle's real type, row-major, packed in that order: n_theta = hidden n_q +
+ * 7 hidden + 6).  The rollout runs q_{t+1} = f(q_t, pi(q_t)), t = 0..H-1, in the nonsmooth model;
+ * the loss is the planning loss `loss` (HOST pointer: goal on q_H, obstacle penalty on q_1..q_H,
+ * effort w_u |u_t|^2) of that trajectory, and the gradient is the surrogate one (the smooth step's
+ * Jacobians along the nonsmooth trajectory), with the policy's derivatives in the chain.  Each
+ * step runs as a one-step sim_rollout and a one-step sim_rollout_vjp (every state a checkpoint).
+ *   q0 [B][n_q]; L [B] (may be NULL; NaN for a flagged rollout); dtheta [n_theta], summed over
+ *   the rollouts whose status stayed 0; dq0 [B][n_q] (may be NULL; zero for a flagged rollout);
+ *   status [B] (may be NULL): the OR of the steps' CS_ST_* bits.
+ * Errors: CS_ERR_INVALID_ARG (NULL handle, q0, theta, loss, dtheta or workspace; B not in
+ * [1, max_batch]; H < 1; hidden not in [1, 1024]; the loss checks of sim_rollout_vjp; a
+ * workspace smaller than apg_workspace()), and those of sim_rollout and sim_rollout_vjp. */
+size_t apg_workspace(const cs_sim* sim, int B, int H, int hidden);
+cs_status apg_rollout_grad(cs_sim* sim, int B, int H, int hidden, const void* q0, const void* theta,
+                           const cs_loss* loss, void* L, void* dtheta, void* dq0, int32_t* status,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
 /* Number of kernel launches the library made on the calling thread since the last call
  * (instrumentation for benchmarks). */
 int64_t cs_launch_count(void);

@@ -106,6 +106,10 @@ SIGNATURES = {
     "sls_tubes": (C.c_int, [C.c_int] * 9 + [C.c_void_p] * 12 + [C.c_void_p, C.c_size_t, C.c_void_p]),
     "sls_conformal_radius": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double,
                                        C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "apg_workspace": (C.c_size_t, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "apg_rollout_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.POINTER(cs_loss), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_size_t, C.c_void_p]),
     "cs_launch_count": (C.c_int64, []),
     "cs_last_error": (C.c_char_p, []),
 }

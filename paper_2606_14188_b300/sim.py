@@ -184,6 +184,27 @@ class Sim:
                 "sim_rollout_vjp")
         return Lv, dU, dq0, status
 
+    def apg_grad(self, q0, theta, hidden: int, H: int):
+        """Analytic policy gradient: the closed-loop rollout of the tanh policy theta (packed
+        [W1 (hidden x n_q), b1, W2 (6 x hidden), b2]) from q0 [B][n_q] over H steps and the
+        gradient of the scene's planning loss -> L [B], dL/dtheta [n_theta], dL/dq0 [B][n_q],
+        status [B]."""
+        B = q0.shape[0]
+        nth = hidden * self.nq + 7 * hidden + 6
+        self._t(q0, (B, self.nq), "q0")
+        self._t(theta, (nth,), "theta")
+        Lv = self._new(B)
+        dth = self._new(nth)
+        dq0 = self._new(B, self.nq)
+        status = torch.zeros(B, dtype=torch.int32, device="cuda")
+        lib = L.lib()
+        wsb = lib.apg_workspace(self._h, B, H, hidden)
+        ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device="cuda")
+        L.check(lib.apg_rollout_grad(self._h, B, H, hidden, _ptr(q0), _ptr(theta), C.byref(self.loss),
+                                     _ptr(Lv), _ptr(dth), _ptr(dq0), _ptr(status), _ptr(ws), wsb,
+                                     _stream()), "apg_rollout_grad")
+        return Lv, dth, dq0, status
+
     def linearize(self, Z, V):
         B, H = V.shape[0], V.shape[1]
         self._t(Z, (B, H + 1, self.nq), "z")

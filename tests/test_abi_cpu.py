@@ -219,3 +219,12 @@ def test_tube_and_conformal_argument_errors_without_gpu():
     assert cr(10, 3, 4, f, f, 0.1, 0, None, f, None) == 1
     assert cr(10, 3, 4, f, f, 0.1, 1, None, None, None) == 1
     assert cr(10, 3, 2, f, f, 0.1, 1, None, f, None) == 1
+
+
+def test_apg_argument_errors_without_gpu():
+    """apg_rollout_grad rejects a NULL handle and NULL arguments before any device call."""
+    lib = L.lib()
+    f = C.c_void_p(256)
+    assert lib.apg_workspace(None, 1, 1, 1) == 0
+    assert lib.apg_rollout_grad(None, 1, 1, 8, f, f, None, None, f, None, None, f, 1 << 20, None) == 1
+    assert b"null" in lib.cs_last_error()
