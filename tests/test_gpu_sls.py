@@ -220,3 +220,41 @@ def test_empty_batch_is_a_no_op():
     sysd = scenes.sls_random_system(1, 2, 4, 2, 4, 2, 4)
     out = _g().observer(*(_t(sysd[k][:0], 8) for k in ("A", "C", "E", "F", "Xi")))
     assert out[0].shape == (0, 3, 4, 4)
+
+
+@pytest.mark.parametrize("rb,p", [(4, 221), (8, 155)])
+def test_observer_at_the_largest_innovation_the_gain_solve_holds(rb, p):
+    """p at the gain kernel's shared-memory limit (221 in FP32, 155 in FP64: one right-hand side
+    per pass), a state larger than it, against the oracle."""
+    B, N, n = 1, 2, p + 9
+    sysd = scenes.sls_random_system(B, N, n, p, n, p, n, seed=p)
+    out = _g().observer(*(_t(sysd[k], rb) for k in ("A", "C", "E", "F", "Xi")))
+    _check_observer(out, sysd, range(B), rb, N)
+
+
+def test_observer_and_tubes_in_the_inertial_state():
+    """The 246-dimensional inertial rope state (positions and velocities of 40 nodes, grippers)
+    with the 120 node positions observed, FP32, against the oracle; the tubes' process scaling
+    spans three 128-wide column tiles (nw = 300)."""
+    from oracle import tubes as otubes
+    B, N, n, p, m, nw = 2, 4, 246, 120, 6, 300
+    sysd = scenes.sls_random_system(B, N, n, p, nw, p, n, seed=81)
+    gsls = _g()
+    A = _t(sysd["A"], 4)
+    out = gsls.observer(A, *(_t(sysd[k], 4) for k in ("C", "E", "F", "Xi")))
+    _check_observer(out, sysd, range(B), 4, N)
+    rng = np.random.default_rng(82)
+    Bm = rng.normal(size=(B, N, n, m)) / np.sqrt(n)
+    K = scenes.sls_feedback_gains(B, N, m, n, seed=83)
+    PB = [sls.state_feedback_responses(sysd["A"][b], Bm[b], K[b]) for b in range(B)]
+    maps = gsls.closed_loop(A, gsls.pack(_t(np.stack([q[0] for q in PB]), 4), N, n, n),
+                            gsls.pack(_t(np.stack([q[1] for q in PB]), 4), N, m, n), out[2], out[3])
+    tau, _ = gsls.tubes(*maps, _t(sysd["E"], 4), _t(sysd["F"], 4))
+    for b in range(B):
+        Pi, L = sls.kalman_recursion(*(sysd[k][b] for k in ("A", "C", "E", "F", "Xi")))
+        PX, PY = sls.observer_responses(sysd["A"][b], sysd["C"][b], L)
+        ref = sls.closed_loop_maps(sysd["A"][b], PB[b][0], PB[b][1], PX, PY)
+        for g, r in zip(maps, ref):
+            assert _rel(gsls.unpack(g[b:b + 1], N)[0].cpu().numpy(), r) <= 1e-3, b
+        tref = otubes.tube_widths(*ref, sysd["E"][b], sysd["F"][b], N)
+        assert _rel(tau[b].cpu().numpy(), tref) <= 1e-3, b
