@@ -385,6 +385,20 @@ def sls_leg(args, flush, stream, world):
                                            stream)), world) / args.steps
     t_cl = max_over_ranks(sum(time_device(lambda: gsls.closed_loop(A, PBX, PBU, PX, PY), args.steps,
                                           flush, stream)), world) / args.steps
+    # the covariances alone by the associative scan of the combination rules (logarithmic depth)
+    for _ in range(max(1, args.warmup)):
+        _, st_scan = gsls.kalman_scan(A, Cm, E, F, Xi)
+    t_scan = max_over_ranks(sum(time_device(lambda: gsls.kalman_scan(A, Cm, E, F, Xi), args.steps, flush,
+                                            stream)), world) / args.steps
+    # one trajectory (a single plan's nominal): the horizon is the only parallel direction there
+    one = [x[:1].contiguous() for x in (A, Cm, E, F, Xi)]
+    for _ in range(max(1, args.warmup)):
+        gsls.observer(*one)
+        gsls.kalman_scan(*one)
+    t_obs1 = max_over_ranks(sum(time_device(lambda: gsls.observer(*one), args.steps, flush, stream)),
+                            world) / args.steps
+    t_scan1 = max_over_ranks(sum(time_device(lambda: gsls.kalman_scan(*one), args.steps, flush, stream)),
+                             world) / args.steps
     # reachable tubes and the tightened margins of the node heights (z_i >= 0: -z_i <= 0) on the
     # closed-loop maps, and the conformal radius of 1000 one-step transitions of the rope
     maps = gsls.closed_loop(A, PBX, PBU, PX, PY)
@@ -429,6 +443,11 @@ def sls_leg(args, flush, stream, world):
                                  dominant_kernel=dict(
                                      kernel="sls_tri_kernel (the Phi^xw launch)",
                                      dram_bytes_per_launch=load_traffic("sls_tri_kernel", f"rope{nv}_b{B}_h{H}"))),
+                kalman_scan=dict(ms_per_step=1e3 * t_scan, value=world * B / t_scan, unit="trajectories/s",
+                                 status_nonzero=int(torch.count_nonzero(st_scan).item()),
+                                 what="sls_kalman_scan: Pi_0..Pi_20 by the associative scan (5 levels); "
+                                      "the observer call forms them step by step",
+                                 one_trajectory=dict(scan_ms=1e3 * t_scan1, observer_ms=1e3 * t_obs1)),
                 tubes=dict(ms_per_step=1e3 * t_tub, value=world * B / t_tub, unit="trajectories/s",
                            roofline=roof(flops.sls_tubes_flops(H, n, m, p, n, p, nv) * B, t_tub),
                            what=f"sls_tubes: row-wise tubes of [x; u] and the margins of {nv} node-height "

@@ -334,6 +334,22 @@ cs_status sls_observer(int B, int N, int n, int p, int nw, int ne, int n0, int r
                        void* Pi, void* L, void* PhiX, void* PhiY, int32_t* status,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/* Device bytes of scratch sls_kalman_scan needs (0 for invalid sizes). */
+size_t sls_kalman_scan_workspace(int B, int N, int n, int p, int real_bytes);
+
+/* The covariances Pi [B][N+1][n][n] of sls_observer by the associative scan of eq.
+ * combination_rules with eq. initialization: the elements are the prior (0, 0, Xi Xi^T) and, per
+ * step j, (A_j^T, C_j^T (F_j F_j^T)^{-1} C_j, E_j E_j^T); Pi_j is the composition of the first j + 1
+ * elements, the later step on the left, formed in ceil(log2(N + 1)) levels (each a batch of
+ * products and one LU solve with (I + Dtil Ptil) per element pair).  Same inputs as
+ * sls_observer; F_j F_j^T must be positive definite (else CS_ST_NOTPD, and NaN from there);
+ * status [B] may be NULL.  n is limited by the LU solve's shared memory (n^2 + 10 n reals within
+ * 200 KB: n <= 221 in FP32, 155 in FP64).  Errors: as sls_observer. */
+cs_status sls_kalman_scan(int B, int N, int n, int p, int nw, int ne, int n0, int real_bytes,
+                          const void* A, const void* C, const void* E, const void* F, const void* Xi,
+                          void* Pi, int32_t* status, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
 /* Closed-loop response of x_{k+1} = Acl_k x_k + delta_{k+1}, the products that eq.
  * backward_propagations forms, for given closed-loop matrices:
  *   Acl [B][N][n][n];  Phi [B][T][n][n], Phi_{k,k} = I, Phi_{k,j} = Phi_{k,j+1} Acl_j.

@@ -110,6 +110,8 @@ SIGNATURES = {
     "apg_rollout_grad": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                    C.POINTER(cs_loss), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_size_t, C.c_void_p]),
+    "sls_kalman_scan_workspace": (C.c_size_t, [C.c_int] * 5),
+    "sls_kalman_scan": (C.c_int, [C.c_int] * 8 + [C.c_void_p] * 7 + [C.c_void_p, C.c_size_t, C.c_void_p]),
     "cs_launch_count": (C.c_int64, []),
     "cs_last_error": (C.c_char_p, []),
 }

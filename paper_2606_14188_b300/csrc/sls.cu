@@ -469,6 +469,180 @@ __global__ void __launch_bounds__(NTH) sls_tri_thin_kernel(int N, int r, int n, 
 }
 
 // ---------------------------------------------------------------------------------------------
+// The Kalman covariances by the associative scan of eq. combination_rules (eq. initialization)
+// ---------------------------------------------------------------------------------------------
+
+// elements of every trajectory: XA[b][0] = XD[b][0] = 0, XA[b][j+1] = A_j^T; Ct[b][j] = C_j^T
+// (n x p)
+template <typename R>
+__global__ void sls_scan_build_kernel(long long B, int N, int n, int p, const R* __restrict__ A,
+                                      const R* __restrict__ Cm, R* XA, R* XD, R* Ct) {
+  const long long nn = (long long)n * n, np_ = (long long)n * p;
+  const long long tot_a = B * (N + 1) * nn, tot_c = B * N * np_;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_a + tot_c;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < tot_a) {
+      const long long bi = e / nn;
+      const int r = (int)((e % nn) / n), c = (int)(e % n);
+      const long long b = bi / (N + 1);
+      const int i = (int)(bi % (N + 1));
+      XA[e] = i == 0 ? R(0) : A[(b * N + i - 1) * nn + (long long)c * n + r];
+      if (i == 0) XD[e] = R(0);
+    } else {
+      const long long f = e - tot_a;             // Ct[b][j][r][c] = C[b][j][c][r]
+      const long long bj = f / np_;
+      const int r = (int)((f % np_) / p), c = (int)(f % p);
+      Ct[f] = Cm[bj * np_ + (long long)c * n + r];
+    }
+  }
+}
+
+// (I + M_z) [X1 | X2] = [B1 | B2] for z = blockIdx.x + zoff (n x n blocks, stride n^2): LU with
+// partial pivoting in shared memory (four barriers per column; ties to the lower row), then the
+// right-hand sides cw columns at a time, four threads per column as in the gain solve; a zero
+// pivot writes NaN and flags CS_ST_NOTPD on the trajectory (z + d) / N1
+template <typename R>
+__global__ void __launch_bounds__(NTH) sls_lu_solve_kernel(int n, int cw, const R* __restrict__ M,
+                                                           const R* __restrict__ B1, const R* __restrict__ B2,
+                                                           R* X1, R* X2, int32_t* status, int N1, int d,
+                                                           long long zoff) {
+  extern __shared__ __align__(16) unsigned char sls_smem[];
+  R* a = reinterpret_cast<R*>(sls_smem);      // n x n, row stride n
+  R* x = a + (size_t)n * n;                   // n x cw, row stride cw + 8
+  int* perm = reinterpret_cast<int*>(x + (size_t)n * (cw + 8));
+  __shared__ R wbest[NTH / 32];
+  __shared__ int wbi[NTH / 32], piv, bad;
+  const long long z = blockIdx.x + zoff;
+  const long long nn = (long long)n * n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const R* Mz = M + z * nn;
+  for (int e = tid; e < n * n; e += NTH) a[e] = Mz[e] + ((e / n == e % n) ? R(1) : R(0));
+  if (tid == 0) bad = 0;
+  for (int i = tid; i < n; i += NTH) perm[i] = i;
+  __syncthreads();
+  for (int c = 0; c < n; ++c) {
+    R best = R(-1);
+    int bi = c;
+    for (int i = c + tid; i < n; i += NTH) {
+      const R v = fabs(a[(size_t)i * n + c]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const R ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { wbest[warp] = best; wbi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      R b0 = wbest[0];
+      int i0 = wbi[0];
+      for (int w = 1; w < NTH / 32; ++w)
+        if (wbest[w] > b0 || (wbest[w] == b0 && wbi[w] < i0)) { b0 = wbest[w]; i0 = wbi[w]; }
+      piv = i0;
+      if (!(b0 > R(0))) bad = 1;
+      const int t = perm[c]; perm[c] = perm[i0]; perm[i0] = t;
+    }
+    __syncthreads();
+    const int pr = piv;
+    if (pr != c)
+      for (int j = tid; j < n; j += NTH) {
+        const R t = a[(size_t)c * n + j];
+        a[(size_t)c * n + j] = a[(size_t)pr * n + j];
+        a[(size_t)pr * n + j] = t;
+      }
+    __syncthreads();
+    R dcc = a[(size_t)c * n + c];
+    if (!(fabs(dcc) > R(0))) dcc = R(1);
+    const R rd = R(1) / dcc;
+    for (int i = c + 1 + tid; i < n; i += NTH) a[(size_t)i * n + c] *= rd;
+    __syncthreads();
+    for (int i = c + 1 + (tid >> 4); i < n; i += 16) {
+      const R lic = a[(size_t)i * n + c];
+      for (int j = c + 1 + (tid & 15); j < n; j += 16) a[(size_t)i * n + j] -= lic * a[(size_t)c * n + j];
+    }
+    __syncthreads();
+  }
+  const int xs = cw + 8, col = tid >> 2, part = tid & 3;
+  const R nan = R(NAN);
+  for (int c0 = 0; c0 < 2 * n; c0 += cw) {
+    const int cn = min(cw, 2 * n - c0);
+    for (int e = tid; e < n * cn; e += NTH) {
+      const int i = e / cn, t = e % cn, cc = c0 + t;
+      const R* src = cc < n ? B1 + z * nn + cc : B2 + z * nn + (cc - n);
+      x[(size_t)i * xs + t] = src[(size_t)perm[i] * n];
+    }
+    __syncthreads();
+    const bool act = col < cn;
+    R* xc = x + col;
+    for (int i = 0; i < n; ++i) {             // unit lower L y = P b
+      const R* ai = a + (size_t)i * n;
+      R s = R(0);
+      if (act)
+        for (int k = part; k < i; k += 4) s -= ai[k] * xc[(size_t)k * xs];
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (act && part == (i & 3)) xc[(size_t)i * xs] += s;
+    }
+    for (int i = n - 1; i >= 0; --i) {        // U x = y
+      const R* ai = a + (size_t)i * n;
+      R s = R(0);
+      if (act)
+        for (int k = i + 1 + ((part - i - 1) & 3); k < n; k += 4) s -= ai[k] * xc[(size_t)k * xs];
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (act && part == (i & 3)) xc[(size_t)i * xs] = (xc[(size_t)i * xs] + s) / ai[i];
+    }
+    __syncthreads();
+    for (int e = tid; e < n * cn; e += NTH) {
+      const int i = e / cn, t = e % cn, cc = c0 + t;
+      R* dst = cc < n ? X1 + z * nn + cc : X2 + z * nn + (cc - n);
+      dst[(size_t)i * n] = bad ? nan : x[(size_t)i * xs + t];
+    }
+    __syncthreads();
+  }
+  // pairs across two trajectories (local index below d) are discarded by the caller: no flag
+  if (tid == 0 && bad && status && (z + d) % N1 >= d) atomicOr(status + (z + d) / N1, CS_ST_NOTPD);
+}
+
+// XD[b][j+1] = Dt[b][j], XP[b][j+1] = Pt[b][j]: the step elements, formed for all (b, j) at once,
+// into the scan's layout (the prior first)
+template <typename R>
+__global__ void sls_scan_place_kernel(long long B, int N, int n, const R* Dt, const R* Pt, R* XD, R* XP) {
+  const long long nn = (long long)n * n, per = (long long)N * nn;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < B * per;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / per, o = (b * (N + 1) + 1) * nn + e % per;
+    XD[o] = Dt[e];
+    XP[o] = Pt[e];
+  }
+}
+
+// status[b] |= the flags of trajectory b's N step solves
+__global__ void sls_flag_rows_kernel(int B, int N, const int32_t* fl, int32_t* status) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    int32_t f = 0;
+    for (int j = 0; j < N; ++j) f |= fl[(size_t)b * N + j];
+    status[b] |= f;
+  }
+}
+
+// Y[b][i] = X[b][i] for i < d (the elements a level leaves as they are), three arrays
+template <typename R>
+__global__ void sls_scan_keep_kernel(long long B, int N, int n, int d, const R* XA, const R* XD,
+                                     const R* XP, R* YA, R* YD, R* YP) {
+  const long long nn = (long long)n * n, per = (long long)d * nn;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < B * per;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long o = (e / per) * (N + 1) * nn + e % per;
+    YA[o] = XA[o];
+    YD[o] = XD[o];
+    YP[o] = XP[o];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Reachable tubes and constraint tightening (Sec. 4.2 eq. of_optimization_tightening1/2) and the
 // conformal radius (Sec. 4.4)
 // ---------------------------------------------------------------------------------------------
@@ -948,6 +1122,150 @@ cs_status tubes(int B, int N, int n, int m, int p, int nw, int ne, int nc, const
   return launched("sls_margin_kernel");
 }
 
+struct ScanWs {
+  size_t xa, xd, xp, ya, yd, yp, m, r2, sa, sd, t, ct, rm, lp, fl, total;
+};
+
+template <typename R>
+ScanWs scan_ws(long long B, int N, int n, int p) {
+  ScanWs w;
+  size_t off = 0;
+  auto take = [&](size_t elems) { const size_t o = off; off = align256(off + elems * sizeof(R)); return o; };
+  const size_t E = (size_t)B * (N + 1) * n * n;
+  w.xa = take(E); w.xd = take(E); w.xp = take(E);
+  w.ya = take(E); w.yd = take(E); w.yp = take(E);
+  w.m = take(E); w.r2 = take(E); w.sa = take(E); w.sd = take(E); w.t = take(E);
+  w.ct = take((size_t)N * B * n * p);
+  w.rm = take((size_t)N * B * p * p);
+  w.lp = take((size_t)N * B * p * n);
+  w.fl = take((size_t)N * B);                       // int32 flags of the (trajectory, step) solves
+  w.total = off;
+  return w;
+}
+
+// LU solve: right-hand-side columns per pass within the shared-memory budget
+inline int lu_cols(int n, size_t rb) {
+  const long long room = (long long)(kGainSmemBudget / rb) - (long long)n * n - n;
+  long long cw = room > 0 ? room / n - 8 : 0;
+  cw = std::min<long long>(std::min<long long>(cw, NTH / 4), 2LL * n);
+  return (int)std::max<long long>(cw, 0);
+}
+
+inline size_t lu_smem(int n, int cw, size_t rb) {
+  return ((size_t)n * n + (size_t)n * (cw + 8)) * rb + (size_t)n * sizeof(int);
+}
+
+template <typename R>
+cs_status kalman_scan(int B, int N, int n, int p, int nw, int ne, int n0, const R* A, const R* Cm, const R* E,
+                      const R* F, const R* Xi, R* Pi, int32_t* status, unsigned char* ws, cudaStream_t st) {
+  const ScanWs w = scan_ws<R>(B, N, n, p);
+  auto at = [&](size_t o) { return reinterpret_cast<R*>(ws + o); };
+  R *XA = at(w.xa), *XD = at(w.xd), *XP = at(w.xp), *YA = at(w.ya), *YD = at(w.yd), *YP = at(w.yp);
+  const long long nn = (long long)n * n, sE = (long long)(N + 1) * nn;
+  cs_status r;
+  if (status) {
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, st);
+    if (e != cudaSuccess) return cs_cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (B == 0) return CS_OK;
+  const int gcw = gain_cols(n, p, sizeof(R)), lcw = lu_cols(n, sizeof(R));
+  const size_t gsm = gain_smem(p, gcw, sizeof(R)), lsm = lu_smem(n, lcw, sizeof(R));
+  cudaError_t e = cudaFuncSetAttribute(sls_gain_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+  if (e != cudaSuccess) return cs_cuda_fail(e, "cudaFuncSetAttribute");
+  e = cudaFuncSetAttribute(sls_lu_solve_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
+  if (e != cudaSuccess) return cs_cuda_fail(e, "cudaFuncSetAttribute");
+  // elements: the prior (0, 0, Xi Xi^T), step j (A_j^T, C_j^T (F_j F_j^T)^{-1} C_j, E_j E_j^T)
+  sls_scan_build_kernel<R><<<148 * 8, 256, 0, st>>>(B, N, n, p, A, Cm, XA, XD, at(w.ct));
+  if ((r = launched("sls_scan_build_kernel"))) return r;
+  {
+    Gemm<R> g = gemm_desc<R>(n, n, XP, sE, n);
+    g.pr[g.np++] = prod<R>(Xi, (long long)n * n0, n0, 0, Xi, (long long)n * n0, n0, 1, n0);
+    if ((r = gemm(g, B, st))) return r;
+  }
+  // the step elements of all (trajectory, step) at once, then placed after each prior: E E^T into
+  // the M slots, F F^T, the gain solve Lp = -(F F^T)^{-1} C, Dtil = C^T (F F^T)^{-1} C = -C^T Lp into
+  // the R2 slots
+  const long long BN = (long long)B * N;
+  {
+    Gemm<R> g = gemm_desc<R>(n, n, at(w.m), nn, n);
+    g.pr[g.np++] = prod<R>(E, (long long)n * nw, nw, 0, E, (long long)n * nw, nw, 1, nw);
+    if ((r = gemm(g, BN, st))) return r;
+  }
+  {
+    Gemm<R> g = gemm_desc<R>(p, p, at(w.rm), (long long)p * p, p);
+    g.pr[g.np++] = prod<R>(F, (long long)p * ne, ne, 0, F, (long long)p * ne, ne, 1, ne);
+    if ((r = gemm(g, BN, st))) return r;
+  }
+  int32_t* fl = reinterpret_cast<int32_t*>(ws + w.fl);
+  if ((e = cudaMemsetAsync(fl, 0, sizeof(int32_t) * (size_t)BN, st)) != cudaSuccess)
+    return cs_cuda_fail(e, "cudaMemsetAsync");
+  for (long long z0 = 0; z0 < BN; z0 += kMaxZ) {
+    const long long zc = std::min(kMaxZ, BN - z0);
+    sls_gain_kernel<R><<<(unsigned)zc, NTH, gsm, st>>>(p, n, gcw, at(w.rm) + z0 * p * p, at(w.ct) + z0 * n * p,
+                                                       at(w.lp) + z0 * p * n, (long long)p * n, fl + z0);
+    if ((r = launched("sls_gain_kernel"))) return r;
+  }
+  if (status) {
+    sls_flag_rows_kernel<<<(B + 255) / 256, 256, 0, st>>>(B, N, fl, status);
+    if ((r = launched("sls_flag_rows_kernel"))) return r;
+  }
+  {
+    Gemm<R> g = gemm_desc<R>(n, n, at(w.r2), nn, n);
+    g.pr[g.np++] = prod<R>(Cm, (long long)p * n, n, 1, at(w.lp), (long long)p * n, n, 0, p, R(-1));
+    if ((r = gemm(g, BN, st))) return r;
+  }
+  sls_scan_place_kernel<R><<<148 * 8, 256, 0, st>>>(B, N, n, at(w.r2), at(w.m), XD, XP);
+  if ((r = launched("sls_scan_place_kernel"))) return r;
+  // levels: x_i <- x_i (x) x_{i-d} for i >= d (the later step on the left), d = 1, 2, 4, ...
+  for (int d = 1; d <= N; d <<= 1) {
+    const long long Z = (long long)B * (N + 1) - d, off = (long long)d * nn;
+    {  // M = D1 P2
+      Gemm<R> g = gemm_desc<R>(n, n, at(w.m), nn, n);
+      g.pr[g.np++] = prod<R>(XD + off, nn, n, 0, XP, nn, n, 0, n);
+      if ((r = gemm(g, Z, st))) return r;
+    }
+    {  // R2 = D1 A2^T
+      Gemm<R> g = gemm_desc<R>(n, n, at(w.r2), nn, n);
+      g.pr[g.np++] = prod<R>(XD + off, nn, n, 0, XA, nn, n, 1, n);
+      if ((r = gemm(g, Z, st))) return r;
+    }
+    for (long long z0 = 0; z0 < Z; z0 += kMaxZ) {  // [Xa | Xd] = (I + D1 P2)^{-1} [A1 | D1 A2^T]
+      sls_lu_solve_kernel<R><<<(unsigned)std::min(kMaxZ, Z - z0), NTH, lsm, st>>>(
+          n, lcw, at(w.m), XA + off, at(w.r2), at(w.sa), at(w.sd), status, N + 1, d, z0);
+      if ((r = launched("sls_lu_solve_kernel"))) return r;
+    }
+    {  // T = P2 Xa
+      Gemm<R> g = gemm_desc<R>(n, n, at(w.t), nn, n);
+      g.pr[g.np++] = prod<R>(XP, nn, n, 0, at(w.sa), nn, n, 0, n);
+      if ((r = gemm(g, Z, st))) return r;
+    }
+    {  // Ptil = A1^T T + P1
+      Gemm<R> g = gemm_desc<R>(n, n, YP + off, nn, n);
+      g.pr[g.np++] = prod<R>(XA + off, nn, n, 1, at(w.t), nn, n, 0, n);
+      g.d = XP + off; g.sd = nn; g.ldd = n;
+      if ((r = gemm(g, Z, st))) return r;
+    }
+    {  // Atil = A2 Xa
+      Gemm<R> g = gemm_desc<R>(n, n, YA + off, nn, n);
+      g.pr[g.np++] = prod<R>(XA, nn, n, 0, at(w.sa), nn, n, 0, n);
+      if ((r = gemm(g, Z, st))) return r;
+    }
+    {  // Dtil = A2 Xd + D2
+      Gemm<R> g = gemm_desc<R>(n, n, YD + off, nn, n);
+      g.pr[g.np++] = prod<R>(XA, nn, n, 0, at(w.sd), nn, n, 0, n);
+      g.d = XD; g.sd = nn; g.ldd = n;
+      if ((r = gemm(g, Z, st))) return r;
+    }
+    sls_scan_keep_kernel<R><<<148 * 8, 256, 0, st>>>(B, N, n, d, XA, XD, XP, YA, YD, YP);
+    if ((r = launched("sls_scan_keep_kernel"))) return r;
+    std::swap(XA, YA);
+    std::swap(XD, YD);
+    std::swap(XP, YP);
+  }
+  e = cudaMemcpyAsync(Pi, XP, sizeof(R) * (size_t)B * sE, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? CS_OK : cs_cuda_fail(e, "cudaMemcpyAsync");
+}
+
 constexpr int kConformalMax = 8192;   // calibration samples one shared-memory sort holds (64 KB in FP64)
 
 cs_status check_sizes(int B, int N, int n, int real_bytes) {
@@ -1099,6 +1417,35 @@ cs_status sls_conformal_radius(int n_cal, int dim, int real_bytes, const void* q
                                                         (const double*)f_pred, (double*)scores, (double*)radius);
   }
   return launched("sls_conformal_kernel");
+}
+
+size_t sls_kalman_scan_workspace(int B, int N, int n, int p, int real_bytes) {
+  if (B < 0 || N < 1 || n < 1 || p < 1 || (real_bytes != 4 && real_bytes != 8)) return 0;
+  return real_bytes == 4 ? scan_ws<float>(B, N, n, p).total : scan_ws<double>(B, N, n, p).total;
+}
+
+cs_status sls_kalman_scan(int B, int N, int n, int p, int nw, int ne, int n0, int real_bytes, const void* A,
+                          const void* C, const void* E, const void* F, const void* Xi, void* Pi, int32_t* status,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+  cs_status r = check_sizes(B, N, n, real_bytes);
+  if (r) return r;
+  if (p < 1 || nw < 1 || ne < 1 || n0 < 1 || p > 4096 || nw > 4096 || ne > 4096 || n0 > 4096)
+    return cs_fail(CS_ERR_INVALID_ARG, "p, nw, ne and n0 must be in [1, 4096]");
+  if (gain_cols(n, p, (size_t)real_bytes) < 1)
+    return cs_fail(CS_ERR_INVALID_ARG, "p too large for the gain kernel's shared memory");
+  if (lu_cols(n, (size_t)real_bytes) < 1)
+    return cs_fail(CS_ERR_INVALID_ARG, "n too large for the scan's shared-memory LU");
+  if (B > 0 && (!A || !C || !E || !F || !Xi || !Pi || !workspace))
+    return cs_fail(CS_ERR_INVALID_ARG, "null pointer");
+  if (workspace_bytes < sls_kalman_scan_workspace(B, N, n, p, real_bytes))
+    return cs_fail(CS_ERR_INVALID_ARG, "workspace smaller than sls_kalman_scan_workspace()");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* ws = (unsigned char*)workspace;
+  if (real_bytes == 4)
+    return kalman_scan<float>(B, N, n, p, nw, ne, n0, (const float*)A, (const float*)C, (const float*)E,
+                              (const float*)F, (const float*)Xi, (float*)Pi, status, ws, st);
+  return kalman_scan<double>(B, N, n, p, nw, ne, n0, (const double*)A, (const double*)C, (const double*)E,
+                             (const double*)F, (const double*)Xi, (double*)Pi, status, ws, st);
 }
 
 }  // extern "C"

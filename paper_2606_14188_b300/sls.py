@@ -3,6 +3,7 @@
 stream).
 
     Pi, L, PhiX, PhiY, status = observer(A, C, E, F, Xi)     # Kalman recursion + observer responses
+    Pi, status = kalman_scan(A, C, E, F, Xi)                  # the same Pi by the associative scan
     Phi = response(Acl)                                       # closed-loop response of given Acl_j
     XW, UW, XE, UE = closed_loop(A, PhiBarX, PhiBarU, PhiX, PhiY)
     tau, margin = tubes(XW, UW, XE, UE, E, F, Ccon, bcon, z, v)  # reachable tubes, tightening
@@ -69,6 +70,25 @@ def observer(A, Cm, E, F, Xi):
     L.check(lib.sls_observer(B, N, n, p, nw, ne, n0, rb, _p(A), _p(Cm), _p(E), _p(F), _p(Xi), _p(Pi),
                              _p(Lg), _p(PX), _p(PY), _p(status), _p(ws), wsb, _stream()), "sls_observer")
     return Pi, Lg, PX, PY, status
+
+
+def kalman_scan(A, Cm, E, F, Xi):
+    """The covariances Pi [B][N+1][n][n] of observer() by the associative scan of the combination
+    rules (logarithmic depth in N) -> (Pi, status)."""
+    rb = _rb(A, Cm, E, F, Xi)
+    B, N, n = A.shape[0], A.shape[1], A.shape[2]
+    p, nw, ne, n0 = Cm.shape[2], E.shape[3], F.shape[3], Xi.shape[2]
+    if (A.shape != (B, N, n, n) or Cm.shape != (B, N, p, n) or E.shape[:3] != (B, N, n)
+            or F.shape[:3] != (B, N, p) or Xi.shape[:2] != (B, n)):
+        raise ValueError("inconsistent shapes")
+    Pi = torch.empty(B, N + 1, n, n, dtype=A.dtype, device=A.device)
+    status = torch.zeros(B, dtype=torch.int32, device=A.device)
+    lib = L.lib()
+    wsb = lib.sls_kalman_scan_workspace(B, N, n, p, rb)
+    ws = torch.empty(max(wsb, 1), dtype=torch.uint8, device=A.device)
+    L.check(lib.sls_kalman_scan(B, N, n, p, nw, ne, n0, rb, _p(A), _p(Cm), _p(E), _p(F), _p(Xi), _p(Pi),
+                                _p(status), _p(ws), wsb, _stream()), "sls_kalman_scan")
+    return Pi, status
 
 
 def response(Acl):

@@ -258,3 +258,41 @@ def test_observer_and_tubes_in_the_inertial_state():
             assert _rel(gsls.unpack(g[b:b + 1], N)[0].cpu().numpy(), r) <= 1e-3, b
         tref = otubes.tube_widths(*ref, sysd["E"][b], sysd["F"][b], N)
         assert _rel(tau[b].cpu().numpy(), tref) <= 1e-3, b
+
+
+@pytest.mark.parametrize("rb", [8, 4])
+@pytest.mark.parametrize("B,N,n,p", [(3, 5, 12, 8), (2, 9, 70, 65), (1, 1, 1, 1)])
+def test_kalman_scan_matches_the_recursion(rb, B, N, n, p):
+    """The covariances by the GPU's associative scan (eq. combination_rules) against the oracle's
+    step-by-step recursion: several levels, a horizon that is not a power of two, 1 x 1."""
+    sysd = scenes.sls_random_system(B, N, n, p, n, p, n, seed=3 * n + N)
+    Pi, st = _g().kalman_scan(*(_t(sysd[k], rb) for k in ("A", "C", "E", "F", "Xi")))
+    assert np.all(st.cpu().numpy() == 0)
+    for b in range(B):
+        ref, _ = sls.kalman_recursion(*(sysd[k][b] for k in ("A", "C", "E", "F", "Xi")))
+        assert _rel(Pi[b].cpu().numpy(), ref) <= TOL[rb]["pi"], b
+
+
+@pytest.mark.parametrize("rb", [8, 4])
+def test_kalman_scan_on_rope40_jacobians(rb):
+    sysd, _ = _rope_inputs(2, 20)
+    Pi, st = _g().kalman_scan(*(_t(sysd[k], rb) for k in ("A", "C", "E", "F", "Xi")))
+    assert np.all(st.cpu().numpy() == 0)
+    for b in range(2):
+        ref, _ = sls.kalman_recursion(*(sysd[k][b] for k in ("A", "C", "E", "F", "Xi")))
+        e = _rel(Pi[b].cpu().numpy(), ref)
+        print("rope40 scan Pi error", rb, e)
+        assert e <= TOL[rb]["pi"], b
+
+
+def test_kalman_scan_flags_a_singular_observation_noise():
+    """F_j = 0 at one step of trajectory 1: its scan element needs (F_j F_j^T)^{-1}, the trajectory
+    is flagged CS_ST_NOTPD; trajectory 0 is unaffected."""
+    B, N, n, p = 2, 4, 10, 4
+    sysd = scenes.sls_random_system(B, N, n, p, n, p, n, seed=33)
+    sysd["F"][1, 2] = 0.0
+    Pi, st = _g().kalman_scan(*(_t(sysd[k], 8) for k in ("A", "C", "E", "F", "Xi")))
+    s = st.cpu().numpy()
+    assert s[0] == 0 and s[1] & 8
+    ref, _ = sls.kalman_recursion(*(sysd[k][0] for k in ("A", "C", "E", "F", "Xi")))
+    assert _rel(Pi[0].cpu().numpy(), ref) <= 1e-10
