@@ -12,8 +12,10 @@
 // operator and the output tiles are the grid; the horizon is the sequential direction:
 //   Kalman   per step j, five batched products and one gain solve (a CTA per trajectory:
 //            Cholesky factor of the innovation matrix in shared memory, a thread per gain column);
-//   Phihat^x one launch per block diagonal d = k - j: Phihat^x_{k,j} = Phihat^x_{k,j+1} Abar_j for
-//            all (trajectory, k) at once, the products the paper's propagation forms, in N launches;
+//   Phihat^x the products Abar_{k-1} ... Abar_j of every block by doubling, the associative scan of
+//            the paper's propagation: distance 1 from Abar, then each level the blocks of distance
+//            (2^(m-1), 2^m] as Phi_{k,j+h} Phi_{j+h,j}, all trajectories at once: ceil(log2 N) + 1
+//            launches;
 //   assembly block lower-triangular products sum_i X_{k,i} Y_{i,j}, a CTA per output block tile
 //            (blocks of at most 8 rows: split over the warps along K instead).
 // The paper forms the horizon direction by associative scans to reach logarithmic depth for one
@@ -322,24 +324,31 @@ __global__ void sls_identity_kernel(long long nb, int N, int n, R* Phi) {
   }
 }
 
-// diagonal d >= 1: Phi_{k,k-d} = Phi_{k,k-d+1} Acl_{k-d}, items (b, k), k = d..N
+// one doubling level of the closed-loop products (the associative scan of eq.
+// backward_propagations, combination Phi_{k,i} Phi_{i,j}): every block (k, j) at distance
+// k - j in [lo, hi] of every trajectory, Phi_{k,j} = Phi_{k,j+h} Phi_{j+h,j} (both at smaller
+// distances, formed by earlier levels), or for h = 0 (distance 1) Phi_{k,k-1} = Phi_{k,k} Acl_{k-1}
 template <typename R, class G>
-__global__ void __launch_bounds__(NTH, 2) sls_level_kernel(int N, int n, int d, const R* __restrict__ Acl,
-                                                        R* Phi, long long zoff) {
+__global__ void __launch_bounds__(NTH, 2) sls_level_kernel(int N, int n, int lo, int hi, int h,
+                                                        const R* __restrict__ Acl, R* Phi, long long zoff) {
   __shared__ __align__(16) Tile<R, G> sm;
   const long long z = blockIdx.z + zoff;
-  const int per = N - d + 1;
+  long long per = 0;
+  for (int dd = lo; dd <= hi; ++dd) per += N - dd + 1;
   const long long b = z / per;
-  const int k = d + (int)(z % per), j = k - d;
-  const long long T = (long long)(N + 1) * (N + 2) / 2;
-  R* base = Phi + b * T * n * n;
-  const R* X = base + tri_index(k, j + 1) * n * n;
-  const R* Y = Acl + (b * N + j) * n * n;
+  long long o = z % per;
+  int d = lo;
+  while (o >= N - d + 1) { o -= N - d + 1; ++d; }
+  const int k = d + (int)o, j = k - d;
+  const long long T = (long long)(N + 1) * (N + 2) / 2, nn = (long long)n * n;
+  R* base = Phi + b * T * nn;
+  const R* X = base + tri_index(k, j + (h > 0 ? h : 1)) * nn;
+  const R* Y = h > 0 ? base + tri_index(j + h, j) * nn : Acl + (b * N + j) * nn;
   const int r0 = blockIdx.y * G::BM, c0 = blockIdx.x * G::BN;
   R acc[G::RM][G::RN] = {};
   tile_mma<R, G>(acc, X, n, 0, R(1), Y, n, 0, n, n, n, r0, c0, sm);
-  tile_store<R, G>(acc, base + tri_index(k, j) * n * n, n, (const R*)nullptr, 0, (const R*)nullptr, 0, n, n,
-             r0, c0);
+  tile_store<R, G>(acc, base + tri_index(k, j) * nn, n, (const R*)nullptr, 0, (const R*)nullptr, 0, n, n, r0,
+                   c0);
 }
 
 // Phihat^y_{k,j} = Phihat^x_{k,j} L_j^T (L_j = Lg[j - 1], p x n), zero for j = 0
@@ -872,13 +881,16 @@ cs_status response_levels(int B, int N, int n, const R* Acl, R* Phi, cudaStream_
     cs_status r = launched("sls_identity_kernel");
     if (r) return r;
   }
+  // doubling levels: distance 1 from Acl, then distances (2^(m-1), 2^m] from two earlier blocks:
+  // ceil(log2 N) + 1 launches
   return with_geom<R>(n, [&](auto geo) -> cs_status {
     using G = decltype(geo);
-    for (int d = 1; d <= N; ++d) {
-      const long long items = (long long)B * (N - d + 1);
+    for (int lo = 1, hi = 1, h = 0; lo <= N; h = hi, lo = hi + 1, hi = std::min(2 * hi, N)) {
+      long long items = 0;
+      for (int d = lo; d <= hi; ++d) items += (long long)B * (N - d + 1);
       for (long long z0 = 0; z0 < items; z0 += kMaxZ) {
-        sls_level_kernel<R, G><<<tiles<G>(n, n, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, n, d, Acl,
-                                                                                          Phi, z0);
+        sls_level_kernel<R, G><<<tiles<G>(n, n, std::min(kMaxZ, items - z0)), NTH, 0, st>>>(N, n, lo, hi, h,
+                                                                                          Acl, Phi, z0);
         cs_status r = launched("sls_level_kernel");
         if (r) return r;
       }
